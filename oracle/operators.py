@@ -1,0 +1,205 @@
+"""Response operators of ab initio TDDFT and of the ris model (oracle, FP64, CPU).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Definitions followed
+  * Eq. hessian (Sec. 2.2.1): (A+B)_ia,jb = Delta_ia d_ij d_ab + 2 f^xc + 2(ia|jb)
+    - c_x[(ib|ja) + (ij|ab)] and (A-B)_ia,jb = Delta d d + c_x[(ib|ja) - (ij|ab)],
+    with Delta_ia = eps_a - eps_i.  f^xc is zero because the integrals are given,
+    not generated (the ris model neglects it too, Sec. 2.2.2).
+  * Eq. pqrs: (pq|rs) is a four-index Coulomb integral; with density fitting it
+    is sum_P L^P_pq L^P_rs (Eq. pqrs_approx with the metric folded into L).
+  * Coulomb prefactor: the printed Eq. hessian has 2(ia|jb) in A+B; the
+    restricted-singlet convention has 2(ia|jb) in A and in B separately.  The
+    prefactor is a parameter c_J of A and B:
+        A = Delta + c_J (ia|jb) - a_x (ij|ab),    B = c_J (ia|jb) - a_x (ib|ja),
+    so c_J = 1 is the equation as printed and c_J = 2 the singlet convention
+    (default).  Both sides always take the same c_J.
+  * Eq. TDDFT-ris_approx and Sec. 3.1-3.2: the ris operator uses its own
+    minimal auxiliary factors; the Coulomb part uses all of them (s, p, d per
+    atom), the exchange part only the s rows, and exchange integrals drop
+    virtual orbitals with eps_a > eps_HOMO + t_cut and occupied orbitals with
+    eps_i < eps_LUMO - t_cut (t_cut = 40 eV).  Coulomb is not truncated.
+
+Two independent routes are given for every operator: a dense builder that
+takes the four-index integral tensor over all orbitals and reads the Hessian
+elements off it by orbital index (small sizes only), and a matrix-free
+product over the three-index blocks (any size).  Tests pin each against the
+other and against closed forms.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+# ----------------------------------------------------------------------------
+# Orbital-energy differences (Eq. hessian, first term)
+
+def delta(eps_occ: np.ndarray, eps_vir: np.ndarray) -> np.ndarray:
+    """Delta_ia = eps_a - eps_i, flattened with a fastest: index ia = i*n_vir + a."""
+    return (eps_vir[None, :] - eps_occ[:, None]).reshape(-1)
+
+
+# ----------------------------------------------------------------------------
+# Dense route: four-index integrals by orbital index (small problems only)
+
+def eri_from_factors(L_full: np.ndarray) -> np.ndarray:
+    """(pq|rs) = sum_P L^P_pq L^P_rs over all orbitals (Eq. pqrs with density fitting)."""
+    n = L_full.shape[1]
+    flat = L_full.reshape(L_full.shape[0], n * n)
+    return (flat.T @ flat).reshape(n, n, n, n)
+
+
+def dense_A_B(eps_occ, eps_vir, eri, a_x, c_J):
+    """A and B of Eq. hessian (f^xc = 0) read element by element from (pq|rs).
+
+    Orbitals are ordered occupied first, so virtual a is orbital n_occ + a.
+    """
+    no, nv = eps_occ.size, eps_vir.size
+    occ = np.arange(no)
+    vir = no + np.arange(nv)
+    # (ia|jb), (ij|ab), (ib|ja) as [i, a, j, b] arrays
+    ia_jb = eri[np.ix_(occ, vir, occ, vir)]
+    ij_ab = eri[np.ix_(occ, occ, vir, vir)].transpose(0, 2, 1, 3)
+    ib_ja = eri[np.ix_(occ, vir, occ, vir)].transpose(0, 3, 2, 1)
+    ov = no * nv
+    A = c_J * ia_jb.reshape(ov, ov) - a_x * ij_ab.reshape(ov, ov)
+    B = c_J * ia_jb.reshape(ov, ov) - a_x * ib_ja.reshape(ov, ov)
+    A[np.diag_indices(ov)] += delta(eps_occ, eps_vir)
+    return A, B
+
+
+def window(eps_occ, eps_vir, t_cut):
+    """Exchange energy window of Sec. 3.1: keep occupied eps_i >= eps_LUMO - t_cut
+    and virtual eps_a <= eps_HOMO + t_cut (the others are dropped)."""
+    keep_o = eps_occ >= eps_vir[0] - t_cut
+    keep_v = eps_vir <= eps_occ[-1] + t_cut
+    return keep_o, keep_v
+
+
+def dense_ris_A_B(prob, t_cut=None):
+    """A and B of the ris model (Eq. TDDFT-ris_approx, rid structure of Sec. 3.2)
+    from four-index integrals of its own factors, by orbital index.
+
+    Coulomb-type integrals use every ris row; exchange-type integrals use the
+    s rows listed in ``ris_K_index`` and only orbitals inside the window.
+    """
+    Lr = prob.extra["Lr_full"]
+    eri_J = eri_from_factors(Lr)
+    eri_K = eri_from_factors(Lr[prob.ris_K_index])
+    t = prob.t_cut_ha if t_cut is None else t_cut
+    ko, kv = window(prob.eps_occ, prob.eps_vir, t)
+    no, nv = prob.n_occ, prob.n_vir
+    mask_o = ko.astype(float)
+    mask_v = kv.astype(float)
+    # zero every exchange integral that touches a dropped orbital
+    m = np.concatenate([mask_o, mask_v])
+    eri_K = eri_K * m[:, None, None, None] * m[None, :, None, None] * m[None, None, :, None] * m[None, None, None, :]
+    AJ, BJ = dense_A_B(prob.eps_occ, prob.eps_vir, eri_J, 0.0, prob.coulomb_factor)
+    AK, BK = dense_A_B(prob.eps_occ, prob.eps_vir, eri_K, prob.a_x, 0.0)
+    d = np.diag_indices(no * nv)
+    AK[d] -= delta(prob.eps_occ, prob.eps_vir)
+    return AJ + AK, BJ + BK
+
+
+# ----------------------------------------------------------------------------
+# Matrix-free route over the three-index blocks (Coulomb J, exchange K1, K2)
+
+def _chunks(n, size):
+    for p0 in range(0, n, size):
+        yield p0, min(n, p0 + size)
+
+
+def coulomb(L_ov, X, chunk=256):
+    """J(X)_ia = sum_jb (ia|jb) X_jb = sum_P L^P_ia sum_jb L^P_jb X_jb.  X: [m][ov]."""
+    n_aux = L_ov.shape[0]
+    flat = L_ov.reshape(n_aux, -1)
+    out = np.zeros_like(X)
+    for p0, p1 in _chunks(n_aux, chunk):
+        t = flat[p0:p1] @ X.T            # [P][m]
+        out += t.T @ flat[p0:p1]
+    return out
+
+
+def exchange_K1(L_oo, L_vv, X, chunk=64):
+    """K1(X)_ib = sum_ja (ij|ab) X_ja = sum_P sum_j L^P_ij sum_a X_ja L^P_ab."""
+    n_aux, no, _ = L_oo.shape
+    nv = L_vv.shape[1]
+    m = X.shape[0]
+    X3 = X.reshape(m, no, nv)
+    out = np.zeros((m, no, nv))
+    for p0, p1 in _chunks(n_aux, chunk):
+        # Z^P_(n,i,a) = sum_j L^P_ij X_(n,j,a)
+        Z = np.einsum("pij,nja->npia", L_oo[p0:p1], X3, optimize=True)
+        # sum over P and a of Z^P_(n,i,a) L^P_ab
+        Zr = Z.transpose(0, 2, 1, 3).reshape(m * no, (p1 - p0) * nv)
+        out += (Zr @ L_vv[p0:p1].reshape((p1 - p0) * nv, nv)).reshape(m, no, nv)
+    return out.reshape(m, no * nv)
+
+
+def exchange_K2(L_ov, X, chunk=64):
+    """K2(X)_ia = sum_jb (ib|ja) X_jb = sum_P sum_j (sum_b L^P_ib X_jb) L^P_ja."""
+    n_aux, no, nv = L_ov.shape
+    m = X.shape[0]
+    X3 = X.reshape(m, no, nv)
+    out = np.zeros((m, no, nv))
+    for p0, p1 in _chunks(n_aux, chunk):
+        Lc = L_ov[p0:p1]
+        Q = np.einsum("pib,njb->npij", Lc, X3, optimize=True)
+        out += np.einsum("npij,pja->nia", Q, Lc, optimize=True)
+    return out.reshape(m, no * nv)
+
+
+class Operator:
+    """Matrix-free A, A+B and A-B over density-fitted factors.
+
+    ``Lx_oo``/``Lx_vv``/``Lx_ov`` are the exchange factor blocks (possibly
+    window-restricted, zero outside the window), ``Lj_ov`` the Coulomb block.
+    """
+
+    def __init__(self, eps_occ, eps_vir, Lj_ov, Lx_oo, Lx_ov, Lx_vv, a_x, c_J):
+        self.d = delta(eps_occ, eps_vir)
+        self.Lj_ov, self.Lx_oo, self.Lx_ov, self.Lx_vv = Lj_ov, Lx_oo, Lx_ov, Lx_vv
+        self.a_x, self.c_J = a_x, c_J
+        self.n_occ, self.n_vir = eps_occ.size, eps_vir.size
+
+    def _parts(self, X, need_k2):
+        X = np.atleast_2d(X)
+        J = coulomb(self.Lj_ov, X)
+        K1 = exchange_K1(self.Lx_oo, self.Lx_vv, X) if self.a_x != 0.0 else np.zeros_like(X)
+        K2 = exchange_K2(self.Lx_ov, X) if (need_k2 and self.a_x != 0.0) else np.zeros_like(X)
+        return X, J, K1, K2
+
+    def tda(self, X):
+        """A X with A = Delta + c_J (ia|jb) - a_x (ij|ab)  (Eq. TDA uses A alone)."""
+        X, J, K1, _ = self._parts(X, False)
+        return self.d * X + self.c_J * J - self.a_x * K1
+
+    def apb_amb(self, X):
+        """((A+B) X, (A-B) X) from Eq. hessian with f^xc = 0."""
+        X, J, K1, K2 = self._parts(X, True)
+        apb = self.d * X + 2.0 * self.c_J * J - self.a_x * (K1 + K2)
+        amb = self.d * X + self.a_x * (K2 - K1)
+        return apb, amb
+
+
+def exact_operator(prob) -> Operator:
+    """The ab initio (RI) operator from the exact factors."""
+    return Operator(prob.eps_occ, prob.eps_vir, prob.L_ov, prob.L_oo, prob.L_ov, prob.L_vv,
+                    prob.a_x, prob.coulomb_factor)
+
+
+def ris_operator(prob, t_cut=None, K_index=None) -> Operator:
+    """The ris preconditioner operator T (Sec. 2.2.2, rid = (d, s) of Sec. 3.2).
+
+    Coulomb from every ris row; exchange from the s rows only, with the
+    occupied and virtual orbitals outside the t_cut window zeroed (Sec. 3.1).
+    """
+    t = prob.t_cut_ha if t_cut is None else t_cut
+    ko, kv = window(prob.eps_occ, prob.eps_vir, t)
+    idx = prob.ris_K_index if K_index is None else K_index
+    Koo = prob.Lr_oo[idx] * ko[None, :, None] * ko[None, None, :]
+    Kvv = prob.Lr_vv[idx] * kv[None, :, None] * kv[None, None, :]
+    Kov = prob.Lr_ov[idx] * ko[None, :, None] * kv[None, None, :]
+    return Operator(prob.eps_occ, prob.eps_vir, prob.Lr_ov, Koo, Kov, Kvv,
+                    prob.a_x, prob.coulomb_factor)

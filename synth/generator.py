@@ -1,0 +1,157 @@
+"""Seeded synthetic inputs for the TDDFT response problem.
+
+This module only draws numbers: orbital energies, three-index factors L^P_pq,
+the minimal-auxiliary ("ris") factors and dipole vectors.  It contains none of
+the response-method arithmetic, so both the CPU oracle and the CUDA path read
+their inputs from here and share nothing else.
+
+Shapes follow the paper's statement of the problem with the integral
+generation abstracted away (Sec. 2.2, Eqs. hessian and pqrs_approx): the
+Coulomb-type integral is (pq|rs) = sum_P L^P_pq L^P_rs, so every factor block
+is an [n_aux][p][q] array, symmetric in (p, q) for each P.
+
+Generator conventions (each one a stated reading, not taken from the paper):
+
+* every random stream is numpy ``Generator(Philox(key=(seed, index)))`` so a
+  P-slice of the factors can be regenerated on its own;
+* L^P over all n_mo = n_occ + n_vir orbitals is a symmetric matrix whose upper
+  triangle (diagonal included) is N(0, 1), scaled by amp * exp(-P / d) with the
+  decay length d = 60 * n_aux / 200 ("decay scaled to n_aux");
+* the amplitude is amp = 0.1 * sqrt(S(200, 60) / S(n_aux, d)), S(n, d) =
+  sum_{P<n} exp(-2P/d), which keeps A-B and A+B positive definite (the literal
+  0.3 gives indefinite Hessians, so it is only kept as an optional TDA input);
+* the ris Coulomb factors are sqrt(0.9) times the leading n_ris rows of the
+  exact factors plus an independent symmetric N(0, (0.1 sigma_P)^2)
+  perturbation; the ris exchange factors are the s-type rows, one per atom,
+  which are rows 0, 9, 18, ... of the ris Coulomb set (9 functions per atom:
+  one s, three p, five d).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+HARTREE_PER_EV = 1.0 / 27.211386245988
+
+
+def _rng(seed: int, index: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=np.array([seed, index], dtype=np.uint64)))
+
+
+def default_amplitude(n_aux: int) -> float:
+    """Amplitude that keeps the synthetic Hessians positive definite."""
+    d = 60.0 * n_aux / 200.0
+    s_ref = sum(math.exp(-2.0 * p / 60.0) for p in range(200))
+    s_n = sum(math.exp(-2.0 * p / d) for p in range(n_aux))
+    return 0.1 * math.sqrt(s_ref / s_n)
+
+
+@dataclass
+class Problem:
+    """One synthetic TDDFT response problem (all arrays float64, C order)."""
+
+    n_occ: int
+    n_vir: int
+    n_aux: int
+    n_ris: int
+    eps_occ: np.ndarray            # [n_occ], ascending
+    eps_vir: np.ndarray            # [n_vir], ascending
+    L_oo: np.ndarray               # [n_aux][n_occ][n_occ]
+    L_ov: np.ndarray               # [n_aux][n_occ][n_vir]
+    L_vv: np.ndarray               # [n_aux][n_vir][n_vir]
+    Lr_ov: np.ndarray              # [n_ris][n_occ][n_vir]   ris Coulomb rows
+    Lr_oo: np.ndarray              # [n_ris][n_occ][n_occ]
+    Lr_vv: np.ndarray              # [n_ris][n_vir][n_vir]
+    ris_K_index: np.ndarray        # [n_ris_K] int32: rows of the ris set used for exchange
+    a_x: float = 0.25
+    coulomb_factor: float = 2.0
+    t_cut_ha: float = 40.0 * HARTREE_PER_EV
+    amplitude: float = 0.0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_ov(self) -> int:
+        return self.n_occ * self.n_vir
+
+    @property
+    def n_ris_K(self) -> int:
+        return int(self.ris_K_index.shape[0])
+
+
+def _symmetric_rows(seed: int, n_rows: int, n: int, scale: np.ndarray, row0: int = 0) -> np.ndarray:
+    out = np.empty((n_rows, n, n))
+    iu = np.triu_indices(n)
+    for r in range(n_rows):
+        g = _rng(seed, row0 + r).standard_normal(iu[0].size)
+        m = np.zeros((n, n))
+        m[iu] = g
+        m = m + np.triu(m, 1).T
+        out[r] = m * scale[r]
+    return out
+
+
+def orbital_energies(seed: int, n_occ: int, n_vir: int):
+    g = _rng(seed, 0)
+    eo = np.sort(g.uniform(-0.8, -0.3, n_occ))
+    ev = np.sort(g.uniform(0.05, 1.5, n_vir))
+    return eo, ev
+
+
+def make_problem(n_occ: int, n_vir: int, n_aux: int, n_ris: int, seeds=(0, 1, 2),
+                 a_x: float = 0.25, coulomb_factor: float = 2.0,
+                 amplitude: Optional[float] = None, ris_noise: float = 0.1,
+                 ris_scale: float = 0.9) -> Problem:
+    """Draw one problem.  ``seeds`` = (orbital energies, exact factors, ris perturbation)."""
+    if n_ris % 9 != 0:
+        raise ValueError("n_ris must be 9 * n_atom (s, p, d functions per atom)")
+    s_eps, s_L, s_ris = seeds
+    eo, ev = orbital_energies(s_eps, n_occ, n_vir)
+    n_mo = n_occ + n_vir
+    amp = default_amplitude(n_aux) if amplitude is None else float(amplitude)
+    d = 60.0 * n_aux / 200.0
+    sigma = amp * np.exp(-np.arange(n_aux) / d)
+    L = _symmetric_rows(s_L, n_aux, n_mo, sigma)
+    o, v = slice(0, n_occ), slice(n_occ, n_mo)
+    n_r = min(n_ris, n_aux)
+    noise = _symmetric_rows(s_ris, n_ris, n_mo, ris_noise * np.resize(sigma[:n_r], n_ris))
+    Lr = np.zeros((n_ris, n_mo, n_mo))
+    Lr[:n_r] = math.sqrt(ris_scale) * L[:n_r]
+    Lr += noise
+    k_index = np.arange(0, n_ris, 9, dtype=np.int32)
+    return Problem(
+        n_occ=n_occ, n_vir=n_vir, n_aux=n_aux, n_ris=n_ris,
+        eps_occ=eo, eps_vir=ev,
+        L_oo=np.ascontiguousarray(L[:, o, o]), L_ov=np.ascontiguousarray(L[:, o, v]),
+        L_vv=np.ascontiguousarray(L[:, v, v]),
+        Lr_ov=np.ascontiguousarray(Lr[:, o, v]), Lr_oo=np.ascontiguousarray(Lr[:, o, o]),
+        Lr_vv=np.ascontiguousarray(Lr[:, v, v]), ris_K_index=k_index,
+        a_x=a_x, coulomb_factor=coulomb_factor, amplitude=amp,
+        extra={"L_full": L if n_mo <= 80 else None, "Lr_full": Lr if n_mo <= 80 else None},
+    )
+
+
+def dipoles(seed: int, n_dip: int, n_ov: int, sigma: float = 0.1) -> np.ndarray:
+    """Dipole right-hand sides mu^u_ia ~ N(0, sigma^2), shape [n_dip][n_ov]."""
+    return _rng(seed, 0).normal(0.0, sigma, size=(n_dip, n_ov))
+
+
+# Named workloads.  Sizes are the response-problem shapes (occupied, virtual,
+# exact auxiliary and ris auxiliary counts) of the paper's benchmark regime.
+CONFIGS = {
+    "tda_small": dict(n_occ=10, n_vir=40, n_aux=200, n_ris=90, seeds=(0, 1, 2),
+                      n_states=5, mu_seed=3),
+    "rpa_polar_medium": dict(n_occ=60, n_vir=400, n_aux=2000, n_ris=360, seeds=(10, 11, 12),
+                             n_states=10, mu_seed=13, omegas=(0.0, 0.05, 0.1), n_dip=3),
+    "large_mixed": dict(n_occ=150, n_vir=1350, n_aux=6000, n_ris=1350, seeds=(20, 21, 22),
+                        n_states=20, mu_seed=23),
+}
+
+
+def make_config(name: str, **over) -> Problem:
+    c = dict(CONFIGS[name])
+    c.update(over)
+    return make_problem(c["n_occ"], c["n_vir"], c["n_aux"], c["n_ris"], seeds=c["seeds"],
+                        **{k: c[k] for k in ("a_x", "coulomb_factor", "amplitude") if k in c})
