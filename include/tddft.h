@@ -1,0 +1,200 @@
+/*
+ * tddft.h - C ABI of the GB300 rid-preconditioned Davidson solver for the
+ * TDDFT response problem (arXiv 2404.17133).
+ *
+ * The library solves, on one GPU:
+ *   - the Tamm-Dancoff eigenproblem  A X = Omega X            (Eq. TDA)
+ *   - the Casida eigenproblem [[A,B],[B,A]](X;Y) = Omega diag(1,-1)(X;Y)
+ *                                                              (Eq. Casida)
+ *   - the dynamic polarizability alpha_vu(omega) of Eq. TDDFT_polar
+ * by the preconditioned Davidson algorithm of Sec. 2.1 (Eqs. 1-4,
+ * Eq. residual, Eq. precondition), with either the diagonal preconditioner
+ * or the rid preconditioner (Sec. 3: an inner Krylov solve with the
+ * minimal-auxiliary ris operator, Eq. TDDFT-ris_approx, (l_J, l_K) = (d, s),
+ * exchange energy window t_cut of Sec. 3.1).
+ *
+ * Operator (Eq. hessian with f^xc = 0 and density-fitted integrals,
+ * (pq|rs) = sum_P L^P_pq L^P_rs, Eq. pqrs / Eq. pqrs_approx):
+ *   A   = Delta + c_J (ia|jb) - a_x (ij|ab)
+ *   B   = c_J (ia|jb) - a_x (ib|ja)
+ *   Delta_ia = eps_a - eps_i
+ * c_J is `coulomb_factor`: 2 is the restricted-singlet convention (default),
+ * 1 reproduces Eq. hessian as printed (2(ia|jb) in A+B).
+ *
+ * Conventions for every call:
+ *   - Index order: a singles vector is [n_occ][n_vir] row-major, ia = i*n_vir+a.
+ *     Factor blocks are [P][p][q] row-major and symmetric in (p,q) for each P.
+ *   - Ownership: input arrays stay owned by the caller; tddft_create copies
+ *     and converts them, so they may be freed when it returns.  Output arrays
+ *     are caller-allocated.  The context owns every device allocation it makes.
+ *   - Errors: every call returns a tddft_status and never aborts the process;
+ *     tddft_last_error() returns a message for the last failing call on that
+ *     context.  TDDFT_ERR_NOCONV still fills the outputs with the last Ritz data.
+ *   - Threading: a context is used by one host thread at a time, except that
+ *     tddft_submit/tddft_poll may be called from any thread.
+ */
+#ifndef TDDFT_H
+#define TDDFT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tddft_ctx tddft_ctx;
+
+typedef enum {
+  TDDFT_OK = 0,
+  TDDFT_PENDING = 1,          /* tddft_poll: request not finished yet          */
+  TDDFT_ERR_ARG = -1,         /* bad argument (null pointer, size, option)     */
+  TDDFT_ERR_OOM = -2,         /* device memory budget or allocation exceeded   */
+  TDDFT_ERR_CUDA = -3,        /* a CUDA runtime call failed                    */
+  TDDFT_ERR_NOCONV = -4,      /* max_iter reached; outputs hold the last data  */
+  TDDFT_ERR_INDEFINITE = -5,  /* A-B or A+B (projected) not positive definite, */
+                              /* or non-finite values in the inputs / Ritz data*/
+  TDDFT_ERR_TIMEOUT = -6,     /* tddft_poll waited timeout_ms without result   */
+  TDDFT_ERR_BUSY = -7         /* request queue full                            */
+} tddft_status;
+
+typedef enum { TDDFT_F64 = 0, TDDFT_F32 = 1 } tddft_dtype;
+
+typedef enum { TDDFT_PRECOND_DIAG = 0, TDDFT_PRECOND_RID = 1 } tddft_precond;
+
+/* Arithmetic of the solve.
+ * PLAIN: every step in FP64 (factors, products, subspace algebra).
+ * MIXED: exact products with FP32 factors and FP32 accumulation, or with
+ *        BF16 hi+lo split factors on the tcgen05 tensor cores (three products
+ *        hi*hi + hi*lo + lo*hi, FP32 accumulation) when `tensor_cores` is set;
+ *        the ris inner solve on BF16 factors with FP32 accumulation; FP64 for
+ *        the subspace eigenproblem, Gram-Schmidt and the final residual check,
+ *        which recomputes the converged residuals with an FP32-or-better
+ *        product ("certification").                                         */
+typedef enum { TDDFT_PLAIN = 0, TDDFT_MIXED = 1 } tddft_precision;
+
+typedef struct {
+  int n_occ, n_vir;           /* occupied / virtual orbitals                  */
+  int n_aux;                  /* exact auxiliary functions P                  */
+  int n_aux_ris_J;            /* ris auxiliary functions (Coulomb, 9/atom)    */
+  int n_aux_ris_K;            /* ris exchange rows (s functions, 1/atom)      */
+  double a_x;                 /* exact-exchange fraction c_x                  */
+  double coulomb_factor;      /* c_J, see above (2.0 default)                 */
+  double t_cut_ha;            /* exchange energy cutoff, Hartree (40 eV)      */
+  int precisions;             /* bit0: keep FP64 factors (PLAIN solves);      */
+                              /* bit1: keep FP32/BF16 factors (MIXED solves)  */
+  double hbm_budget_gb;       /* refuse create (TDDFT_ERR_OOM) above this;    */
+                              /* 0 = free device memory minus 2 GB            */
+} tddft_desc;
+
+typedef struct {
+  int precond;                /* tddft_precond                                */
+  int n_states;               /* roots wanted                                 */
+  int n_extra_guess;          /* -1: paper rule (rid: +min(n,3), diag: +8)    */
+  double tol;                 /* outer residual threshold (1e-5, Sec. 3)      */
+  double inner_tol;           /* ris inner solve, relative (1e-2, Sec. 3.1)   */
+  double guess_tol;           /* ris initial-guess solve (1e-3, Sec. 3.1)     */
+  int max_iter;               /* outer iterations (50)                        */
+  int inner_max_iter;         /* ris inner iterations (20, Sec. 3.1)          */
+  int max_subspace;           /* collapse above this many vectors (0: auto)   */
+  int precision;              /* tddft_precision                              */
+  int tensor_cores;           /* MIXED only: tcgen05 BF16 hi+lo exchange      */
+  int outputs_on_device;      /* 1: omega/X/Y/resid/alpha are device pointers */
+} tddft_opts;
+
+typedef struct {
+  int n_iter;                 /* outer Davidson iterations                    */
+  int n_matvec;               /* exact operator products (vectors)            */
+  int n_ris_matvec;           /* ris operator products (vectors)              */
+  int converged;              /* 1 if every root / system met tol             */
+  int n_restart;              /* subspace collapses                           */
+  int gpu_launches;           /* kernels launched by this solve               */
+  double max_resid;           /* largest final residual norm                  */
+  double max_resid_certified; /* MIXED: after the FP32-or-better re-check     */
+  double t_total_s, t_matvec_s, t_precond_s;  /* wall times (host clock)     */
+} tddft_stats;
+
+/* Fill `opts` with the paper's defaults (Sec. 3.1-3.2): rid, tol 1e-5,
+ * inner tol 1e-2 / 20 iterations, guess tol 1e-3, N_init rule, PLAIN.      */
+void tddft_default_opts(tddft_opts* opts);
+
+/* Fill `desc` defaults: a_x 0.25, c_J 2, t_cut 40 eV, both precisions.     */
+void tddft_default_desc(tddft_desc* desc);
+
+/* Create a context: upload and convert the orbital energies and factors.
+ *   eps_occ [n_occ], eps_vir [n_vir]      ascending orbital energies (FP64)
+ *   L_oo [n_aux][n_occ][n_occ], L_ov [n_aux][n_occ][n_vir],
+ *   L_vv [n_aux][n_vir][n_vir]            exact factors (Eq. pqrs_approx)
+ *   Lr_ov [n_aux_ris_J][n_occ][n_vir]     ris Coulomb factors (all rows)
+ *   Lr_oo [n_aux_ris_K][n_occ][n_occ],
+ *   Lr_vv [n_aux_ris_K][n_vir][n_vir]     ris exchange factors (s rows only)
+ *   ris_K_index [n_aux_ris_K]             row of Lr_ov that each exchange row
+ *                                         is (its ov block for (ib|ja))
+ *   dtype                                 element type of all factor arrays
+ *   inputs_on_device                      1: every array pointer is device memory
+ *   cuda_stream                           cudaStream_t to run on (NULL: own one)
+ * The t_cut window is applied here to the ris exchange rows.
+ * Returns TDDFT_ERR_ARG on bad sizes or null pointers, TDDFT_ERR_OOM when the
+ * resident factor copies exceed desc->hbm_budget_gb or the free memory.    */
+tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const double* eps_vir,
+                          const void* L_oo, const void* L_ov, const void* L_vv,
+                          const void* Lr_oo, const void* Lr_ov, const void* Lr_vv,
+                          const int* ris_K_index, tddft_dtype dtype, int inputs_on_device,
+                          void* cuda_stream, tddft_ctx** out);
+
+/* TDA excitation energies (Eq. TDA).  omega [n_states] ascending, X
+ * [n_states][n_occ*n_vir] unit-norm eigenvectors (may be NULL), resid
+ * [n_states] final |R_n| (may be NULL), stats may be NULL.                 */
+tddft_status tddft_solve_tda(tddft_ctx* ctx, const tddft_opts* opts, double* omega, double* X,
+                             double* resid, tddft_stats* stats);
+
+/* Casida excitation energies (Eq. Casida), X and Y normalised so that
+ * X^T X - Y^T Y = 1 (each may be NULL).  The residual of root n is
+ * sqrt(|(A+B)(X+Y) - Omega(X-Y)|^2 + |(A-B)(X-Y) - Omega(X+Y)|^2).         */
+tddft_status tddft_solve_rpa(tddft_ctx* ctx, const tddft_opts* opts, double* omega, double* X,
+                             double* Y, double* resid, tddft_stats* stats);
+
+/* Dynamic polarizability (Eq. TDDFT_polar) for n_dip dipole vectors mu
+ * [n_dip][n_occ*n_vir] at n_freq frequencies omega [n_freq] (Hartree):
+ * alpha [n_freq][n_dip][n_dip], alpha_vu = mu_v^T (X_u + Y_u).  The system
+ * residual is divided by |2 mu_u| before the tol test.                    */
+tddft_status tddft_solve_polar(tddft_ctx* ctx, const tddft_opts* opts, const double* mu,
+                               int n_dip, const double* omega, int n_freq, double* alpha,
+                               tddft_stats* stats);
+
+/* One operator product on m vectors (for tests and measurement):
+ *   kind 0: A X (exact), 1: ((A+B)X, (A-B)X) exact, 2: T_A X (ris),
+ *   kind 3: ((T_A+T_B)X, (T_A-T_B)X) ris.
+ * X [m][ov]; out0 [m][ov]; out1 [m][ov] for kinds 1 and 3 (else NULL).
+ * precision / tensor_cores as in tddft_opts; on_device: pointers are device
+ * memory.  Results are FP64.                                               */
+tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cores,
+                         const double* X, int m, double* out0, double* out1, int on_device);
+
+/* Asynchronous requests.  kind: 0 TDA, 1 RPA, 2 polar.  `req` points to a
+ * tddft_request whose arrays must stay valid until tddft_poll returns a final
+ * status for the ticket.  A worker thread owned by the context runs the
+ * requests in arrival order.  tddft_poll waits at most timeout_ms (0: do not
+ * wait) and returns TDDFT_PENDING, TDDFT_ERR_TIMEOUT, or the request's status. */
+typedef struct {
+  tddft_opts opts;
+  double* omega; double* X; double* Y; double* resid;      /* eigen requests */
+  const double* mu; int n_dip; const double* freqs; int n_freq; double* alpha;  /* polar */
+  tddft_stats stats;                                       /* filled on completion */
+} tddft_request;
+
+tddft_status tddft_submit(tddft_ctx* ctx, int kind, tddft_request* req,
+                          unsigned long long* ticket);
+tddft_status tddft_poll(tddft_ctx* ctx, unsigned long long ticket, int timeout_ms);
+
+/* Release every device allocation and the worker thread. NULL is a no-op.  */
+void tddft_destroy(tddft_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failing create when
+ * ctx is NULL).  Valid until the next call on the same context.            */
+const char* tddft_last_error(const tddft_ctx* ctx);
+
+/* Device resident bytes held by the context (factor copies + workspace).   */
+unsigned long long tddft_device_bytes(const tddft_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDDFT_H */

@@ -36,8 +36,11 @@ Readings where the paper is silent (each listed in the design notes):
     for the polarizability the solution of the T system to 1e-3 (diag:
     (Delta -+ omega)^-1 mu)
   * vectors whose norm after two Gram-Schmidt passes is below 1e-8 of the
-    input norm are dropped; when the subspace would exceed ``max_subspace``
-    it is collapsed to the current N_keep lowest Ritz vectors
+    input norm are dropped; the subspace holds at most MAX_SUBSPACE vectors:
+    before it would overflow, an eigen solve collapses it onto the Ritz
+    vectors of the wanted roots (Casida: their X+Y and X-Y), a
+    polarizability solve restarts it from the current solutions U and W,
+    and an inner solve stops with its current solution
 """
 from __future__ import annotations
 
@@ -47,6 +50,7 @@ import numpy as np
 
 DROP_TOL = 1e-8
 SHIFT_GUARD = 1e-8
+MAX_SUBSPACE = 160   # subspace vectors kept before a collapse / restart
 
 
 @dataclass
@@ -133,7 +137,7 @@ def inner_solve_tda(T, d, R, omega, tol=1e-2, max_iter=20):
     TS = T.tda(S)
     n_mv = S.shape[0]
     rn = np.linalg.norm(R, axis=1)
-    for _ in range(max_iter):
+    for it in range(max_iter):
         t = S @ TS.T
         lam, Q = np.linalg.eigh(0.5 * (t + t.T))
         h = S @ R.T                                  # [k][n]
@@ -141,7 +145,9 @@ def inner_solve_tda(T, d, R, omega, tol=1e-2, max_iter=20):
         v = y.T @ S
         res = y.T @ TS - omega[:, None] * v - R
         ok = np.linalg.norm(res, axis=1) <= tol * rn
-        if ok.all():
+        if ok.all() or it == max_iter - 1:
+            break
+        if S.shape[0] + int((~ok).sum()) > MAX_SUBSPACE:
             break
         new = mgs(S, res[~ok] / _guard(d[None, :] - omega[~ok, None]))
         if new.shape[0] == 0:
@@ -174,7 +180,7 @@ def inner_solve_paired(T, d, gp, gm, shifts, tol=1e-2, max_iter=20):
     TP, TM = T.apb_amb(S)
     n_mv = S.shape[0]
     gn = np.sqrt(np.linalg.norm(gp, axis=1) ** 2 + np.linalg.norm(gm, axis=1) ** 2)
-    for _ in range(max_iter):
+    for it in range(max_iter):
         fac = _paired_factors(S @ TP.T, S @ TM.T)
         hp = S @ gp.T
         hm = S @ gm.T
@@ -189,7 +195,9 @@ def inner_solve_paired(T, d, gp, gm, shifts, tol=1e-2, max_iter=20):
             rm[n] = wc @ TM - s * U[n] - gm[n]
         rn = np.sqrt(np.linalg.norm(rp, axis=1) ** 2 + np.linalg.norm(rm, axis=1) ** 2)
         ok = rn <= tol * gn
-        if ok.all():
+        if ok.all() or it == max_iter - 1:
+            break
+        if S.shape[0] + 2 * int((~ok).sum()) > MAX_SUBSPACE:
             break
         nu, nw = _diag_paired(d, rp[~ok], rm[~ok], shifts[~ok])
         new = mgs(S, np.vstack([nu, nw]))
@@ -266,8 +274,7 @@ def davidson_tda(op, n_states, precond, guess, tol=1e-5, max_iter=50, max_subspa
     AV = op.tda(V)
     n_mv = V.shape[0]
     ov = V.shape[1]
-    max_subspace = max_subspace or max(200, 20 * n_states)
-    n_keep = n_keep or V.shape[0]
+    max_subspace = max_subspace or MAX_SUBSPACE
     hist = []
     for k in range(1, max_iter + 1):
         a = V @ AV.T                                  # Eq. 1
@@ -286,9 +293,10 @@ def davidson_tda(op, n_states, precond, guess, tol=1e-5, max_iter=50, max_subspa
         new = mgs(V, cand)
         if new.shape[0] == 0:
             break
-        if V.shape[0] + new.shape[0] > max_subspace:
-            kk = min(max(n_keep, n_states), V.shape[0])
-            V, AV = x[:, :kk].T @ V, x[:, :kk].T @ AV
+        if V.shape[0] + int(todo.sum()) > max_subspace:
+            # collapse onto the Ritz vectors of the wanted roots
+            V, AV = X, AX
+            new = mgs(V, new)
         V = np.vstack([V, new])
         AV = np.vstack([AV, op.tda(new)])
         n_mv += new.shape[0]
@@ -318,8 +326,7 @@ def davidson_rpa(op, n_states, precond, guess, tol=1e-5, max_iter=50, max_subspa
     V = mgs(None, guess)
     P, M = op.apb_amb(V)
     n_mv = V.shape[0]
-    max_subspace = max_subspace or max(200, 20 * n_states)
-    n_keep = n_keep or V.shape[0]
+    max_subspace = max_subspace or MAX_SUBSPACE
     hist = []
     for k in range(1, max_iter + 1):
         om, u, w, S, Si, lam, Z = _rpa_ritz(V, P, M, n_states)
@@ -336,12 +343,11 @@ def davidson_rpa(op, n_states, precond, guess, tol=1e-5, max_iter=50, max_subspa
         new = mgs(V, np.vstack([nu, nw]))
         if new.shape[0] == 0:
             break
-        if V.shape[0] + new.shape[0] > max_subspace:
-            kk = min(max(n_keep, n_states), V.shape[0])
-            # collapse onto the lowest Ritz pairs' X+Y and X-Y directions
-            coef = np.concatenate([(S @ Z[:, :kk]), (Si @ Z[:, :kk])], axis=1)
-            q, _ = np.linalg.qr(coef)
-            V, P, M = q.T @ V, q.T @ P, q.T @ M
+        if V.shape[0] + 2 * int(todo.sum()) > max_subspace:
+            # collapse onto the X+Y and X-Y directions of the wanted roots
+            V = mgs(None, np.vstack([U, W]))
+            P, M = op.apb_amb(V)
+            n_mv += V.shape[0]
             new = mgs(V, new)
         V = np.vstack([V, new])
         p, m = op.apb_amb(new)
@@ -388,6 +394,11 @@ def polar_solve(op, mu, omegas, precond, guess, tol=1e-5, max_iter=50):
             return res
         todo = r >= tol
         nu, nw = precond.paired(Rp[todo], Rm[todo], om_all[todo])
+        if V.shape[0] + 2 * int(todo.sum()) > MAX_SUBSPACE:
+            # restart from the current solutions of every system
+            V = mgs(None, np.vstack([U, W]))
+            P, M = op.apb_amb(V)
+            n_mv += V.shape[0]
         new = mgs(V, np.vstack([nu, nw]))
         if new.shape[0] == 0:
             break

@@ -1,0 +1,276 @@
+"""Python binding of the C ABI in include/tddft.h (ctypes; argument marshalling only).
+
+Every computation happens in the CUDA library.  Importing this module loads the
+in-tree shared library and raises ImportError if it has not been built; there
+is no fallback implementation.
+
+Arrays may be numpy arrays (host) or torch CUDA tensors (device); a call uses
+the device form of the C ABI when its inputs are CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIBPATH
+
+if not os.path.exists(LIBPATH):
+    raise ImportError("CUDA library not built: %s (run paper_2404_17133_gb300.build.build())" % LIBPATH)
+
+_lib = C.CDLL(LIBPATH)
+
+OK, PENDING = 0, 1
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOCONV, ERR_INDEFINITE, ERR_TIMEOUT, ERR_BUSY = -1, -2, -3, -4, -5, -6, -7
+F64, F32 = 0, 1
+DIAG, RID = 0, 1
+PLAIN, MIXED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_NOCONV",
+                -5: "ERR_INDEFINITE", -6: "ERR_TIMEOUT", -7: "ERR_BUSY"}
+
+
+class Desc(C.Structure):
+    _fields_ = [("n_occ", C.c_int), ("n_vir", C.c_int), ("n_aux", C.c_int),
+                ("n_aux_ris_J", C.c_int), ("n_aux_ris_K", C.c_int),
+                ("a_x", C.c_double), ("coulomb_factor", C.c_double), ("t_cut_ha", C.c_double),
+                ("precisions", C.c_int), ("hbm_budget_gb", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("precond", C.c_int), ("n_states", C.c_int), ("n_extra_guess", C.c_int),
+                ("tol", C.c_double), ("inner_tol", C.c_double), ("guess_tol", C.c_double),
+                ("max_iter", C.c_int), ("inner_max_iter", C.c_int), ("max_subspace", C.c_int),
+                ("precision", C.c_int), ("tensor_cores", C.c_int), ("outputs_on_device", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_iter", C.c_int), ("n_matvec", C.c_int), ("n_ris_matvec", C.c_int),
+                ("converged", C.c_int), ("n_restart", C.c_int), ("gpu_launches", C.c_int),
+                ("max_resid", C.c_double), ("max_resid_certified", C.c_double),
+                ("t_total_s", C.c_double), ("t_matvec_s", C.c_double), ("t_precond_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(C.Structure):
+    _fields_ = [("opts", Opts),
+                ("omega", C.c_void_p), ("X", C.c_void_p), ("Y", C.c_void_p), ("resid", C.c_void_p),
+                ("mu", C.c_void_p), ("n_dip", C.c_int), ("freqs", C.c_void_p), ("n_freq", C.c_int),
+                ("alpha", C.c_void_p), ("stats", Stats)]
+
+
+_vp, _ip, _dp = C.c_void_p, C.c_int, C.c_void_p
+_lib.tddft_default_opts.argtypes = [C.POINTER(Opts)]
+_lib.tddft_default_opts.restype = None
+_lib.tddft_default_desc.argtypes = [C.POINTER(Desc)]
+_lib.tddft_default_desc.restype = None
+_lib.tddft_create.argtypes = [C.POINTER(Desc), _dp, _dp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _ip, _ip,
+                              _vp, C.POINTER(_vp)]
+_lib.tddft_create.restype = C.c_int
+_lib.tddft_solve_tda.argtypes = [_vp, C.POINTER(Opts), _dp, _dp, _dp, C.POINTER(Stats)]
+_lib.tddft_solve_tda.restype = C.c_int
+_lib.tddft_solve_rpa.argtypes = [_vp, C.POINTER(Opts), _dp, _dp, _dp, _dp, C.POINTER(Stats)]
+_lib.tddft_solve_rpa.restype = C.c_int
+_lib.tddft_solve_polar.argtypes = [_vp, C.POINTER(Opts), _dp, _ip, _dp, _ip, _dp, C.POINTER(Stats)]
+_lib.tddft_solve_polar.restype = C.c_int
+_lib.tddft_apply.argtypes = [_vp, _ip, _ip, _ip, _dp, _ip, _dp, _dp, _ip]
+_lib.tddft_apply.restype = C.c_int
+_lib.tddft_submit.argtypes = [_vp, _ip, C.POINTER(Request), C.POINTER(C.c_ulonglong)]
+_lib.tddft_submit.restype = C.c_int
+_lib.tddft_poll.argtypes = [_vp, C.c_ulonglong, _ip]
+_lib.tddft_poll.restype = C.c_int
+_lib.tddft_destroy.argtypes = [_vp]
+_lib.tddft_destroy.restype = None
+_lib.tddft_last_error.argtypes = [_vp]
+_lib.tddft_last_error.restype = C.c_char_p
+_lib.tddft_device_bytes.argtypes = [_vp]
+_lib.tddft_device_bytes.restype = C.c_ulonglong
+
+EXPORTED = ["tddft_default_opts", "tddft_default_desc", "tddft_create", "tddft_solve_tda",
+            "tddft_solve_rpa", "tddft_solve_polar", "tddft_apply", "tddft_submit", "tddft_poll",
+            "tddft_destroy", "tddft_last_error", "tddft_device_bytes"]
+
+
+class TddftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def lib():
+    return _lib
+
+
+def _is_cuda(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _ptr(x, dtype=np.float64):
+    """(pointer, keepalive) for a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None, None
+    if _is_cuda(x) or hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(C.c_void_p), a
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _lib.tddft_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One context: resident factors + the request queue (include/tddft.h)."""
+
+    def __init__(self, n_occ, n_vir, eps_occ, eps_vir, L_oo, L_ov, L_vv, Lr_oo, Lr_ov, Lr_vv,
+                 ris_K_index, a_x=0.25, coulomb_factor=2.0, t_cut_ha=None, precisions=3,
+                 hbm_budget_gb=0.0, dtype=F64, stream=None):
+        d = Desc()
+        _lib.tddft_default_desc(C.byref(d))
+        d.n_occ, d.n_vir = int(n_occ), int(n_vir)
+        d.n_aux = int(L_ov.shape[0])
+        d.n_aux_ris_J = int(Lr_ov.shape[0]) if Lr_ov is not None else 0
+        d.n_aux_ris_K = int(len(ris_K_index)) if ris_K_index is not None else 0
+        d.a_x, d.coulomb_factor = float(a_x), float(coulomb_factor)
+        if t_cut_ha is not None:
+            d.t_cut_ha = float(t_cut_ha)
+        d.precisions, d.hbm_budget_gb = int(precisions), float(hbm_budget_gb)
+        self.desc = d
+        self.n_ov = d.n_occ * d.n_vir
+        on_dev = _is_cuda(L_ov)
+        fdt = np.float64 if dtype == F64 else np.float32
+        keep = []
+        ptrs = []
+        for arr, dt in ((eps_occ, np.float64), (eps_vir, np.float64), (L_oo, fdt), (L_ov, fdt),
+                        (L_vv, fdt), (Lr_oo, fdt), (Lr_ov, fdt), (Lr_vv, fdt), (ris_K_index, np.int32)):
+            p, k = _ptr(arr, dt)
+            ptrs.append(p)
+            keep.append(k)
+        h = C.c_void_p()
+        st = _lib.tddft_create(C.byref(d), *ptrs, int(dtype), 1 if on_dev else 0,
+                               C.c_void_p(stream) if stream else None, C.byref(h))
+        if st != OK:
+            raise TddftError(st, _lib.tddft_last_error(None).decode())
+        self.h = h
+        self._pending = {}
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        return cls(prob.n_occ, prob.n_vir, prob.eps_occ, prob.eps_vir, prob.L_oo, prob.L_ov, prob.L_vv,
+                   prob.Lr_oo[prob.ris_K_index], prob.Lr_ov, prob.Lr_vv[prob.ris_K_index],
+                   prob.ris_K_index, a_x=prob.a_x, coulomb_factor=prob.coulomb_factor,
+                   t_cut_ha=prob.t_cut_ha, **kw)
+
+    def _check(self, st, allow_noconv=True):
+        if st == OK or (allow_noconv and st == ERR_NOCONV):
+            return st
+        raise TddftError(st, _lib.tddft_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.tddft_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def device_bytes(self):
+        return _lib.tddft_device_bytes(self.h)
+
+    def solve_tda(self, opts: Opts, want_vectors=True):
+        k = opts.n_states
+        om, rs = np.zeros(k), np.zeros(k)
+        X = np.zeros((k, self.n_ov)) if want_vectors else None
+        st = Stats()
+        s = _lib.tddft_solve_tda(self.h, C.byref(opts), om.ctypes.data_as(C.c_void_p),
+                                 X.ctypes.data_as(C.c_void_p) if X is not None else None,
+                                 rs.ctypes.data_as(C.c_void_p), C.byref(st))
+        self._check(s)
+        return dict(status=s, omega=om, X=X, resid=rs, stats=st.as_dict())
+
+    def solve_rpa(self, opts: Opts, want_vectors=True):
+        k = opts.n_states
+        om, rs = np.zeros(k), np.zeros(k)
+        X = np.zeros((k, self.n_ov)) if want_vectors else None
+        Y = np.zeros((k, self.n_ov)) if want_vectors else None
+        st = Stats()
+        vp = lambda a: a.ctypes.data_as(C.c_void_p) if a is not None else None
+        s = _lib.tddft_solve_rpa(self.h, C.byref(opts), vp(om), vp(X), vp(Y), vp(rs), C.byref(st))
+        self._check(s)
+        return dict(status=s, omega=om, X=X, Y=Y, resid=rs, stats=st.as_dict())
+
+    def solve_polar(self, opts: Opts, mu, omegas):
+        mu = np.ascontiguousarray(np.atleast_2d(mu), dtype=np.float64)
+        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        nd, nf = mu.shape[0], om.size
+        alpha = np.zeros((nf, nd, nd))
+        st = Stats()
+        s = _lib.tddft_solve_polar(self.h, C.byref(opts), mu.ctypes.data_as(C.c_void_p), nd,
+                                   om.ctypes.data_as(C.c_void_p), nf, alpha.ctypes.data_as(C.c_void_p),
+                                   C.byref(st))
+        self._check(s)
+        return dict(status=s, alpha=alpha, stats=st.as_dict())
+
+    def apply(self, kind, X, precision=PLAIN, tensor_cores=False):
+        """kind 0: A X, 1: ((A+B)X, (A-B)X), 2: T X (ris), 3: ris pair."""
+        if _is_cuda(X):
+            import torch
+            out0 = torch.empty_like(X)
+            out1 = torch.empty_like(X) if kind in (1, 3) else None
+            s = _lib.tddft_apply(self.h, kind, precision, int(bool(tensor_cores)), C.c_void_p(X.data_ptr()),
+                                 X.shape[0], C.c_void_p(out0.data_ptr()),
+                                 C.c_void_p(out1.data_ptr()) if out1 is not None else None, 1)
+        else:
+            X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.float64)
+            out0 = np.zeros_like(X)
+            out1 = np.zeros_like(X) if kind in (1, 3) else None
+            s = _lib.tddft_apply(self.h, kind, precision, int(bool(tensor_cores)),
+                                 X.ctypes.data_as(C.c_void_p), X.shape[0], out0.ctypes.data_as(C.c_void_p),
+                                 out1.ctypes.data_as(C.c_void_p) if out1 is not None else None, 0)
+        self._check(s, allow_noconv=False)
+        return (out0, out1) if out1 is not None else out0
+
+    # -- asynchronous requests ------------------------------------------------
+    def submit(self, kind, opts: Opts, mu=None, omegas=None):
+        """kind 0 TDA, 1 RPA, 2 polar.  Returns a ticket; buffers are kept alive here."""
+        r = Request()
+        r.opts = opts
+        bufs = {}
+        if kind in (0, 1):
+            k = opts.n_states
+            bufs["omega"], bufs["resid"] = np.zeros(k), np.zeros(k)
+            r.omega = bufs["omega"].ctypes.data
+            r.resid = bufs["resid"].ctypes.data
+        else:
+            mu = np.ascontiguousarray(np.atleast_2d(mu), dtype=np.float64)
+            om = np.ascontiguousarray(omegas, dtype=np.float64)
+            bufs["mu"], bufs["freqs"] = mu, om
+            bufs["alpha"] = np.zeros((om.size, mu.shape[0], mu.shape[0]))
+            r.mu, r.n_dip, r.freqs, r.n_freq = mu.ctypes.data, mu.shape[0], om.ctypes.data, om.size
+            r.alpha = bufs["alpha"].ctypes.data
+        t = C.c_ulonglong()
+        s = _lib.tddft_submit(self.h, kind, C.byref(r), C.byref(t))
+        self._check(s, allow_noconv=False)
+        self._pending[t.value] = (r, bufs, kind)
+        return t.value
+
+    def poll(self, ticket, timeout_ms=0):
+        """Returns None while pending; else the result dict (status included)."""
+        s = _lib.tddft_poll(self.h, ticket, int(timeout_ms))
+        if s in (PENDING, ERR_TIMEOUT):
+            return None
+        r, bufs, kind = self._pending.pop(ticket)
+        out = dict(status=s, stats=r.stats.as_dict())
+        if s not in (OK, ERR_NOCONV):
+            out["error"] = _lib.tddft_last_error(self.h).decode()
+        out.update({k: v for k, v in bufs.items() if k in ("omega", "resid", "alpha")})
+        return out

@@ -1,0 +1,514 @@
+// C ABI (include/tddft.h): argument checking, factor staging, the request
+// queue, and the translation of internal errors into status codes.  No call
+// lets a C++ exception or a CUDA error escape; each returns a tddft_status.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "ctx.cuh"
+#include "vecops.cuh"
+
+using namespace tddft;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+tddft_status fail(Ctx* c, const std::exception& e, tddft_status st) {
+  if (c) c->err = e.what();
+  else g_create_error = e.what();
+  return st;
+}
+
+// Copy `rows` rows of `row_elems` elements from a host or device array of type
+// `tin` into device copies, chunk by chunk (bounded staging memory).
+struct StageTarget {
+  void* dst;        // device
+  DType tout;       // F64, F32 or BF16
+  __nv_bfloat16* lo = nullptr;  // if set: BF16 hi (dst) + lo split
+};
+
+void stage_rows(const void* src, DType tin, bool on_device, long long rows, long long row_elems,
+                const std::vector<StageTarget>& targets, cudaStream_t s) {
+  if (rows == 0 || targets.empty()) return;
+  const size_t es = dtype_size(tin);
+  const long long total = rows * row_elems;
+  long long chunk = (256ll << 20) / (long long)es;   // elements per staging chunk
+  if (chunk > total) chunk = total;
+  DevBuf stage;
+  if (!on_device) stage = DevBuf((size_t)chunk * es, s);
+  for (long long off = 0; off < total; off += chunk) {
+    long long n = std::min(chunk, total - off);
+    const void* in;
+    if (on_device) {
+      in = (const char*)src + off * es;
+    } else {
+      TD_CUDA(cudaMemcpyAsync(stage.p, (const char*)src + off * es, (size_t)n * es,
+                              cudaMemcpyHostToDevice, s));
+      in = stage.p;
+    }
+    for (const auto& t : targets) {
+      void* out = (char*)t.dst + off * dtype_size(t.tout);
+      if (t.lo) split_bf16(in, tin, (__nv_bfloat16*)out, t.lo + off, n, s);
+      else convert(in, tin, out, t.tout, n, s);
+    }
+    if (!on_device) TD_CUDA(cudaStreamSynchronize(s));  // staging buffer reused
+  }
+}
+
+void worker_loop(Ctx* c) {
+  cudaSetDevice(c->device);
+  for (;;) {
+    unsigned long long t;
+    Request* r;
+    {
+      std::unique_lock<std::mutex> lk(c->mu);
+      c->cv_work.wait(lk, [&] { return c->stopping || !c->queue.empty(); });
+      if (c->stopping && c->queue.empty()) return;
+      t = c->queue.front();
+      c->queue.pop_front();
+      r = &c->requests[t];
+    }
+    tddft_status st;
+    try {
+      tddft_request* q = r->req;
+      std::lock_guard<std::mutex> run(c->run_mu);
+      if (r->kind == 0) st = run_tda(*c, q->opts, q->omega, q->X, q->resid, &q->stats);
+      else if (r->kind == 1) st = run_rpa(*c, q->opts, q->omega, q->X, q->Y, q->resid, &q->stats);
+      else st = run_polar(*c, q->opts, q->mu, q->n_dip, q->freqs, q->n_freq, q->alpha, &q->stats);
+    } catch (const Error& e) {
+      std::lock_guard<std::mutex> lk(c->mu);
+      c->err = e.what();
+      st = e.status;
+    } catch (const std::exception& e) {
+      std::lock_guard<std::mutex> lk(c->mu);
+      c->err = e.what();
+      st = TDDFT_ERR_CUDA;
+    }
+    {
+      std::lock_guard<std::mutex> lk(c->mu);
+      r->status = st;
+      r->done = true;
+    }
+    c->cv_done.notify_all();
+  }
+}
+
+}  // namespace
+
+namespace tddft {
+
+FactorSet Ctx::exact(int precision) const {
+  FactorSet f;
+  f.nJ = naux;
+  f.nK = naux;
+  if (precision == TDDFT_PLAIN) {
+    f.dt = DType::F64;
+    f.Jov = x64_ov.p; f.Koo = x64_oo.p; f.Kvv = x64_vv.p; f.Kov = x64_ov.p;
+  } else {
+    f.dt = DType::F32;
+    f.Jov = x32_ov.p; f.Koo = x32_oo.p; f.Kvv = x32_vv.p; f.Kov = x32_ov.p;
+    f.Kvv_hi = x16_vv_hi.as<__nv_bfloat16>();
+    f.Kvv_lo = x16_vv_lo.as<__nv_bfloat16>();
+  }
+  return f;
+}
+
+FactorSet Ctx::ris(int precision) const {
+  FactorSet f;
+  f.nJ = nJ;
+  f.nK = nK;
+  if (precision == TDDFT_PLAIN) {
+    f.dt = DType::F64;
+    f.Jov = r64_J.p; f.Koo = r64_Koo.p; f.Kvv = r64_Kvv.p; f.Kov = r64_Kov.p;
+  } else {
+    f.dt = DType::BF16;
+    f.Jov = r16_J.p; f.Koo = r16_Koo.p; f.Kvv = r16_Kvv.p; f.Kov = r16_Kov.p;
+  }
+  return f;
+}
+
+}  // namespace tddft
+
+extern "C" {
+
+void tddft_default_opts(tddft_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precond = TDDFT_PRECOND_RID;
+  o->n_states = 5;
+  o->n_extra_guess = -1;
+  o->tol = 1e-5;
+  o->inner_tol = 1e-2;
+  o->guess_tol = 1e-3;
+  o->max_iter = 50;
+  o->inner_max_iter = 20;
+  o->max_subspace = 0;
+  o->precision = TDDFT_PLAIN;
+  o->tensor_cores = 0;
+  o->outputs_on_device = 0;
+}
+
+void tddft_default_desc(tddft_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->a_x = 0.25;
+  d->coulomb_factor = 2.0;
+  d->t_cut_ha = 40.0 / 27.211386245988;
+  d->precisions = 3;
+  d->hbm_budget_gb = 0.0;
+}
+
+tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const double* eps_vir,
+                          const void* L_oo, const void* L_ov, const void* L_vv, const void* Lr_oo,
+                          const void* Lr_ov, const void* Lr_vv, const int* ris_K_index,
+                          tddft_dtype dtype, int inputs_on_device, void* cuda_stream,
+                          tddft_ctx** out) {
+  Ctx* c = nullptr;
+  try {
+    TD_REQUIRE(out != nullptr && desc != nullptr, TDDFT_ERR_ARG, "null desc or out pointer");
+    *out = nullptr;
+    const tddft_desc& d = *desc;
+    TD_REQUIRE(d.n_occ >= 1 && d.n_vir >= 1 && d.n_aux >= 1 && d.n_aux_ris_J >= 0 &&
+                   d.n_aux_ris_K >= 0 && d.n_aux_ris_K <= d.n_aux_ris_J,
+               TDDFT_ERR_ARG, "bad sizes in tddft_desc");
+    TD_REQUIRE((long long)d.n_occ * d.n_vir < (1ll << 31), TDDFT_ERR_ARG, "n_occ*n_vir too large");
+    TD_REQUIRE(eps_occ && eps_vir && L_oo && L_ov && L_vv, TDDFT_ERR_ARG, "null exact-factor input");
+    TD_REQUIRE(d.n_aux_ris_J == 0 || Lr_ov, TDDFT_ERR_ARG, "null ris Coulomb factors");
+    TD_REQUIRE(d.n_aux_ris_K == 0 || (Lr_oo && Lr_vv && ris_K_index), TDDFT_ERR_ARG,
+               "null ris exchange factors");
+    TD_REQUIRE(dtype == TDDFT_F64 || dtype == TDDFT_F32, TDDFT_ERR_ARG, "unknown dtype");
+    TD_REQUIRE((d.precisions & 3) != 0, TDDFT_ERR_ARG, "precisions must keep at least one copy");
+    TD_REQUIRE(std::isfinite(d.a_x) && std::isfinite(d.coulomb_factor) && std::isfinite(d.t_cut_ha),
+               TDDFT_ERR_ARG, "non-finite a_x / coulomb_factor / t_cut");
+
+    c = new Ctx();
+    TD_CUDA(cudaGetDevice(&c->device));
+    if (cuda_stream) {
+      c->s = (cudaStream_t)cuda_stream;
+    } else {
+      TD_CUDA(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    cudaStream_t s = c->s;
+    c->no = d.n_occ; c->nv = d.n_vir; c->ov = d.n_occ * d.n_vir;
+    c->naux = d.n_aux; c->nJ = d.n_aux_ris_J; c->nK = d.n_aux_ris_K;
+    c->a_x = d.a_x; c->c_J = d.coulomb_factor; c->t_cut = d.t_cut_ha;
+    c->precisions = d.precisions & 3;
+    const int no = c->no, nv = c->nv, ov = c->ov;
+    const DType tin = dtype == TDDFT_F64 ? DType::F64 : DType::F32;
+    const bool dev = inputs_on_device != 0;
+
+    // orbital energies (host copy for the window and the guess order)
+    std::vector<double> eo(no), ev(nv);
+    cudaMemcpyKind k = dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    TD_CUDA(cudaMemcpy(eo.data(), eps_occ, no * 8, k));
+    TD_CUDA(cudaMemcpy(ev.data(), eps_vir, nv * 8, k));
+    for (double x : eo) TD_REQUIRE(std::isfinite(x), TDDFT_ERR_ARG, "non-finite orbital energy");
+    for (double x : ev) TD_REQUIRE(std::isfinite(x), TDDFT_ERR_ARG, "non-finite orbital energy");
+    TD_REQUIRE(std::is_sorted(eo.begin(), eo.end()) && std::is_sorted(ev.begin(), ev.end()),
+               TDDFT_ERR_ARG, "orbital energies must be ascending");
+    std::vector<int> kidx;
+    if (d.n_aux_ris_K > 0) {
+      kidx.resize(d.n_aux_ris_K);
+      TD_CUDA(cudaMemcpy(kidx.data(), ris_K_index, kidx.size() * 4, k));
+      for (int r : kidx) TD_REQUIRE(r >= 0 && r < d.n_aux_ris_J, TDDFT_ERR_ARG, "ris_K_index out of range");
+    }
+
+    // memory admission
+    const bool p64 = c->precisions & 1, pmx = c->precisions & 2;
+    const double nvv = (double)d.n_aux * nv * nv, noo = (double)d.n_aux * no * no, nov = (double)d.n_aux * ov;
+    const double nr = (double)d.n_aux_ris_J * ov + (double)d.n_aux_ris_K * (no * no + nv * nv + ov);
+    double bytes = 0.0;
+    if (p64) bytes += 8.0 * (nvv + noo + nov + nr);
+    if (pmx) bytes += 4.0 * (nvv + noo + nov) + 4.0 * nvv + 2.0 * nr;
+    size_t fr = 0, tot = 0;
+    TD_CUDA(cudaMemGetInfo(&fr, &tot));
+    double budget = d.hbm_budget_gb > 0 ? d.hbm_budget_gb * 1e9 : (double)fr - 2e9;
+    if (bytes > budget) {
+      throw Error(TDDFT_ERR_OOM, "factor copies need " + std::to_string(bytes / 1e9) +
+                                     " GB, budget " + std::to_string(budget / 1e9) + " GB");
+    }
+    c->device_bytes = (unsigned long long)bytes;
+
+    c->eps_o = DevBuf(no * 8, s);
+    c->eps_v = DevBuf(nv * 8, s);
+    c->delta = DevBuf((size_t)ov * 8, s);
+    TD_CUDA(cudaMemcpyAsync(c->eps_o.p, eo.data(), no * 8, cudaMemcpyHostToDevice, s));
+    TD_CUDA(cudaMemcpyAsync(c->eps_v.p, ev.data(), nv * 8, cudaMemcpyHostToDevice, s));
+    delta_kernel(c->eps_o.as<double>(), c->eps_v.as<double>(), no, nv, c->delta.as<double>(), s);
+    {
+      // order of Delta ascending (ties by index), for the unit-vector guesses
+      std::vector<double> dl(ov);
+      for (int i = 0; i < no; ++i)
+        for (int a = 0; a < nv; ++a) dl[(size_t)i * nv + a] = ev[a] - eo[i];
+      std::vector<int> ord(ov);
+      std::iota(ord.begin(), ord.end(), 0);
+      c->n_order = std::min(ov, 4096);
+      std::partial_sort(ord.begin(), ord.begin() + c->n_order, ord.end(), [&](int x, int y) {
+        return dl[x] < dl[y] || (dl[x] == dl[y] && x < y);
+      });
+      c->order = DevBuf(c->n_order * 4, s);
+      TD_CUDA(cudaMemcpyAsync(c->order.p, ord.data(), c->n_order * 4, cudaMemcpyHostToDevice, s));
+      TD_CUDA(cudaStreamSynchronize(s));
+    }
+
+    // exact factors
+    const long long A = d.n_aux;
+    if (p64) {
+      c->x64_oo = DevBuf(A * no * no * 8, s);
+      c->x64_ov = DevBuf(A * ov * 8, s);
+      c->x64_vv = DevBuf(A * nv * nv * 8, s);
+    }
+    if (pmx) {
+      c->x32_oo = DevBuf(A * no * no * 4, s);
+      c->x32_ov = DevBuf(A * ov * 4, s);
+      c->x32_vv = DevBuf(A * nv * nv * 4, s);
+      c->x16_vv_hi = DevBuf(A * nv * nv * 2, s);
+      c->x16_vv_lo = DevBuf(A * nv * nv * 2, s);
+    }
+    auto targets = [&](DevBuf& t64, DevBuf& t32) {
+      std::vector<StageTarget> v;
+      if (p64) v.push_back({t64.p, DType::F64});
+      if (pmx) v.push_back({t32.p, DType::F32});
+      return v;
+    };
+    stage_rows(L_oo, tin, dev, A, (long long)no * no, targets(c->x64_oo, c->x32_oo), s);
+    stage_rows(L_ov, tin, dev, A, ov, targets(c->x64_ov, c->x32_ov), s);
+    {
+      auto v = targets(c->x64_vv, c->x32_vv);
+      if (pmx) v.push_back({c->x16_vv_hi.p, DType::BF16, c->x16_vv_lo.as<__nv_bfloat16>()});
+      stage_rows(L_vv, tin, dev, A, (long long)nv * nv, v, s);
+    }
+
+    // ris factors (Coulomb rows all; exchange rows windowed, Sec. 3.1)
+    const long long RJ = d.n_aux_ris_J, RK = d.n_aux_ris_K;
+    if (RJ > 0) {
+      if (p64) c->r64_J = DevBuf(RJ * ov * 8, s);
+      if (pmx) c->r16_J = DevBuf(RJ * ov * 2, s);
+      std::vector<StageTarget> v;
+      if (p64) v.push_back({c->r64_J.p, DType::F64});
+      if (pmx) v.push_back({c->r16_J.p, DType::BF16});
+      stage_rows(Lr_ov, tin, dev, RJ, ov, v, s);
+    }
+    if (RK > 0) {
+      std::vector<unsigned char> mo(no), mv(nv);
+      for (int i = 0; i < no; ++i) mo[i] = eo[i] >= ev[0] - d.t_cut_ha;
+      for (int a = 0; a < nv; ++a) mv[a] = ev[a] <= eo[no - 1] + d.t_cut_ha;
+      DevBuf dmo(no, s), dmv(nv, s);
+      TD_CUDA(cudaMemcpyAsync(dmo.p, mo.data(), no, cudaMemcpyHostToDevice, s));
+      TD_CUDA(cudaMemcpyAsync(dmv.p, mv.data(), nv, cudaMemcpyHostToDevice, s));
+      if (p64) {
+        c->r64_Koo = DevBuf(RK * no * no * 8, s);
+        c->r64_Kvv = DevBuf(RK * nv * nv * 8, s);
+        c->r64_Kov = DevBuf(RK * ov * 8, s);
+      }
+      if (pmx) {
+        c->r16_Koo = DevBuf(RK * no * no * 2, s);
+        c->r16_Kvv = DevBuf(RK * nv * nv * 2, s);
+        c->r16_Kov = DevBuf(RK * ov * 2, s);
+      }
+      std::vector<StageTarget> voo, vvv;
+      if (p64) { voo.push_back({c->r64_Koo.p, DType::F64}); vvv.push_back({c->r64_Kvv.p, DType::F64}); }
+      if (pmx) { voo.push_back({c->r16_Koo.p, DType::BF16}); vvv.push_back({c->r16_Kvv.p, DType::BF16}); }
+      stage_rows(Lr_oo, tin, dev, RK, (long long)no * no, voo, s);
+      stage_rows(Lr_vv, tin, dev, RK, (long long)nv * nv, vvv, s);
+      for (long long r = 0; r < RK; ++r) {
+        if (p64)
+          TD_CUDA(cudaMemcpyAsync(c->r64_Kov.as<double>() + r * ov, c->r64_J.as<double>() + (long long)kidx[r] * ov,
+                                  (size_t)ov * 8, cudaMemcpyDeviceToDevice, s));
+        if (pmx)
+          TD_CUDA(cudaMemcpyAsync(c->r16_Kov.as<__nv_bfloat16>() + r * ov,
+                                  c->r16_J.as<__nv_bfloat16>() + (long long)kidx[r] * ov, (size_t)ov * 2,
+                                  cudaMemcpyDeviceToDevice, s));
+      }
+      if (p64) {
+        mask_block(c->r64_Koo.p, DType::F64, (int)RK, no, no, dmo.as<unsigned char>(), dmo.as<unsigned char>(), s);
+        mask_block(c->r64_Kvv.p, DType::F64, (int)RK, nv, nv, dmv.as<unsigned char>(), dmv.as<unsigned char>(), s);
+        mask_block(c->r64_Kov.p, DType::F64, (int)RK, no, nv, dmo.as<unsigned char>(), dmv.as<unsigned char>(), s);
+      }
+      if (pmx) {
+        mask_block(c->r16_Koo.p, DType::BF16, (int)RK, no, no, dmo.as<unsigned char>(), dmo.as<unsigned char>(), s);
+        mask_block(c->r16_Kvv.p, DType::BF16, (int)RK, nv, nv, dmv.as<unsigned char>(), dmv.as<unsigned char>(), s);
+        mask_block(c->r16_Kov.p, DType::BF16, (int)RK, no, nv, dmo.as<unsigned char>(), dmv.as<unsigned char>(), s);
+      }
+      TD_CUDA(cudaStreamSynchronize(s));
+    }
+    // reject non-finite factors
+    {
+      DevBuf flag(4, s);
+      TD_CUDA(cudaMemsetAsync(flag.p, 0, 4, s));
+      if (p64) {
+        check_finite(c->x64_ov.p, DType::F64, A * ov, flag.as<int>(), s);
+        check_finite(c->x64_oo.p, DType::F64, A * no * no, flag.as<int>(), s);
+        check_finite(c->x64_vv.p, DType::F64, A * nv * nv, flag.as<int>(), s);
+      } else {
+        check_finite(c->x32_ov.p, DType::F32, A * ov, flag.as<int>(), s);
+        check_finite(c->x32_oo.p, DType::F32, A * no * no, flag.as<int>(), s);
+        check_finite(c->x32_vv.p, DType::F32, A * nv * nv, flag.as<int>(), s);
+      }
+      int fh = 0;
+      TD_CUDA(cudaMemcpyAsync(&fh, flag.p, 4, cudaMemcpyDeviceToHost, s));
+      TD_CUDA(cudaStreamSynchronize(s));
+      TD_REQUIRE(fh == 0, TDDFT_ERR_INDEFINITE, "non-finite values in the factors");
+    }
+    c->worker = std::thread(worker_loop, c);
+    *out = reinterpret_cast<tddft_ctx*>(c);
+    return TDDFT_OK;
+  } catch (const Error& e) {
+    tddft_status st = e.status;
+    g_create_error = e.what();
+    if (c) tddft_destroy(reinterpret_cast<tddft_ctx*>(c));
+    return st;
+  } catch (const std::exception& e) {
+    g_create_error = e.what();
+    if (c) tddft_destroy(reinterpret_cast<tddft_ctx*>(c));
+    return TDDFT_ERR_CUDA;
+  }
+}
+
+#define TD_API_BODY(ctxp, ...)                                                           \
+  Ctx* c = reinterpret_cast<Ctx*>(ctxp);                                                  \
+  if (!c) return TDDFT_ERR_ARG;                                                           \
+  try {                                                                                   \
+    __VA_ARGS__;                                                                          \
+  } catch (const Error& e) {                                                              \
+    return fail(c, e, e.status);                                                          \
+  } catch (const std::exception& e) {                                                     \
+    return fail(c, e, TDDFT_ERR_CUDA);                                                    \
+  }
+
+tddft_status tddft_solve_tda(tddft_ctx* ctx, const tddft_opts* opts, double* omega, double* X,
+                             double* resid, tddft_stats* stats) {
+  TD_API_BODY(ctx, {
+    TD_REQUIRE(opts != nullptr, TDDFT_ERR_ARG, "null opts");
+    std::lock_guard<std::mutex> run(c->run_mu);
+    return run_tda(*c, *opts, omega, X, resid, stats);
+  })
+}
+
+tddft_status tddft_solve_rpa(tddft_ctx* ctx, const tddft_opts* opts, double* omega, double* X,
+                             double* Y, double* resid, tddft_stats* stats) {
+  TD_API_BODY(ctx, {
+    TD_REQUIRE(opts != nullptr, TDDFT_ERR_ARG, "null opts");
+    std::lock_guard<std::mutex> run(c->run_mu);
+    return run_rpa(*c, *opts, omega, X, Y, resid, stats);
+  })
+}
+
+tddft_status tddft_solve_polar(tddft_ctx* ctx, const tddft_opts* opts, const double* mu, int n_dip,
+                               const double* omega, int n_freq, double* alpha, tddft_stats* stats) {
+  TD_API_BODY(ctx, {
+    TD_REQUIRE(opts != nullptr, TDDFT_ERR_ARG, "null opts");
+    std::lock_guard<std::mutex> run(c->run_mu);
+    return run_polar(*c, *opts, mu, n_dip, omega, n_freq, alpha, stats);
+  })
+}
+
+tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cores, const double* X,
+                         int m, double* out0, double* out1, int on_device) {
+  TD_API_BODY(ctx, {
+    TD_REQUIRE(kind >= 0 && kind <= 3, TDDFT_ERR_ARG, "kind must be 0..3");
+    TD_REQUIRE(precision == TDDFT_PLAIN || precision == TDDFT_MIXED, TDDFT_ERR_ARG, "bad precision");
+    TD_REQUIRE((c->precisions & (precision == TDDFT_PLAIN ? 1 : 2)) != 0, TDDFT_ERR_ARG,
+               "context lacks the factor copies for this precision");
+    TD_REQUIRE(!(tensor_cores && precision != TDDFT_MIXED), TDDFT_ERR_ARG, "tensor_cores needs MIXED");
+    TD_REQUIRE(m >= 0 && X && out0 && ((kind & 1) == 0 || out1), TDDFT_ERR_ARG, "bad buffers");
+    if (m == 0) return TDDFT_OK;
+    std::lock_guard<std::mutex> run(c->run_mu);
+    cudaStream_t s = c->s;
+    const size_t n = (size_t)m * c->ov;
+    const bool ris = kind >= 2;
+    const bool paired = kind & 1;
+    FactorSet f = ris ? c->ris(precision) : c->exact(precision);
+    DevBuf xb, o0, o1;
+    const double* Xd = X;
+    double* d0 = out0;
+    double* d1 = out1;
+    if (!on_device) {
+      xb = DevBuf(n * 8, s);
+      TD_CUDA(cudaMemcpyAsync(xb.p, X, n * 8, cudaMemcpyHostToDevice, s));
+      Xd = xb.as<double>();
+      o0 = DevBuf(n * 8, s);
+      d0 = o0.as<double>();
+      if (paired) { o1 = DevBuf(n * 8, s); d1 = o1.as<double>(); }
+    }
+    g_launches = 0;
+    apply_operator(c->dims(), f, Xd, m, paired ? OpMode::PAIRED : OpMode::TDA, d0, paired ? d1 : nullptr,
+                   tensor_cores != 0 && !ris, s);
+    if (!on_device) {
+      TD_CUDA(cudaMemcpyAsync(out0, d0, n * 8, cudaMemcpyDeviceToHost, s));
+      if (paired) TD_CUDA(cudaMemcpyAsync(out1, d1, n * 8, cudaMemcpyDeviceToHost, s));
+    }
+    TD_CUDA(cudaStreamSynchronize(s));
+    return TDDFT_OK;
+  })
+}
+
+tddft_status tddft_submit(tddft_ctx* ctx, int kind, tddft_request* req, unsigned long long* ticket) {
+  TD_API_BODY(ctx, {
+    TD_REQUIRE(req && ticket && kind >= 0 && kind <= 2, TDDFT_ERR_ARG, "bad request");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->queue.size() >= 4096) return TDDFT_ERR_BUSY;
+    unsigned long long t = c->next_ticket++;
+    Request r;
+    r.kind = kind;
+    r.req = req;
+    c->requests[t] = r;
+    c->queue.push_back(t);
+    *ticket = t;
+    c->cv_work.notify_one();
+    return TDDFT_OK;
+  })
+}
+
+tddft_status tddft_poll(tddft_ctx* ctx, unsigned long long ticket, int timeout_ms) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return TDDFT_ERR_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  auto it = c->requests.find(ticket);
+  if (it == c->requests.end()) return TDDFT_ERR_ARG;
+  if (!it->second.done && timeout_ms > 0) {
+    c->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+      auto j = c->requests.find(ticket);
+      return j != c->requests.end() && j->second.done;
+    });
+    it = c->requests.find(ticket);
+  }
+  if (!it->second.done) return timeout_ms > 0 ? TDDFT_ERR_TIMEOUT : TDDFT_PENDING;
+  tddft_status st = it->second.status;
+  c->requests.erase(it);
+  return st;
+}
+
+void tddft_destroy(tddft_ctx* ctx) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->stopping = true;
+  }
+  c->cv_work.notify_all();
+  if (c->worker.joinable()) c->worker.join();
+  if (c->s) cudaStreamSynchronize(c->s);
+  cudaStream_t s = c->s;
+  bool own = c->own_stream;
+  delete c;  // DevBuf destructors free on the stream
+  if (s) cudaStreamSynchronize(s);
+  if (own && s) cudaStreamDestroy(s);
+}
+
+const char* tddft_last_error(const tddft_ctx* ctx) {
+  const Ctx* c = reinterpret_cast<const Ctx*>(ctx);
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+unsigned long long tddft_device_bytes(const tddft_ctx* ctx) {
+  const Ctx* c = reinterpret_cast<const Ctx*>(ctx);
+  return c ? c->device_bytes : 0ull;
+}
+
+}  // extern "C"

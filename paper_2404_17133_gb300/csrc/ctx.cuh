@@ -1,0 +1,97 @@
+// Solver context: resident factor copies, orbital data and the request queue.
+#pragma once
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+#include "common.cuh"
+
+namespace tddft {
+
+// One operator's factors in one element type.
+//   Coulomb   J(X)_ia  = sum_P Jov[P][ia] sum_jb Jov[P][jb] X_jb            (nJ rows)
+//   exchange  K1(X)_ib = sum_P sum_j Koo[P][i][j] sum_a X_ja Kvv[P][a][b]      (nK rows)
+//             K2(X)_ia = sum_P sum_j (sum_b Kov[P][i][b] X_jb) Kov[P][j][a]
+struct FactorSet {
+  DType dt = DType::F64;
+  int nJ = 0, nK = 0;
+  const void* Jov = nullptr;
+  const void* Koo = nullptr;
+  const void* Kvv = nullptr;
+  const void* Kov = nullptr;
+  // BF16 hi/lo split of Kvv for the tensor-core exchange (exact operator only)
+  const __nv_bfloat16* Kvv_hi = nullptr;
+  const __nv_bfloat16* Kvv_lo = nullptr;
+};
+
+struct OpDims {
+  int no = 0, nv = 0, ov = 0;
+  double a_x = 0.0, c_J = 2.0;
+  const double* delta = nullptr;  // device [ov]
+};
+
+enum class OpMode { TDA, PAIRED };
+
+// out0 = A X (TDA) or (A+B) X and out1 = (A-B) X (PAIRED); X, out FP64 [m][ov].
+// tensor_cores: K1's dominant contraction on tcgen05 (BF16 hi+lo), needs Kvv_hi/lo.
+void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m, OpMode mode,
+                    double* out0, double* out1, bool tensor_cores, cudaStream_t s);
+
+struct Request {
+  int kind = 0;
+  tddft_request* req = nullptr;
+  tddft_status status = TDDFT_PENDING;
+  bool done = false;
+};
+
+struct Ctx {
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int no = 0, nv = 0, ov = 0, naux = 0, nJ = 0, nK = 0;
+  double a_x = 0.25, c_J = 2.0, t_cut = 0.0;
+  int precisions = 3;
+  // orbital data
+  DevBuf eps_o, eps_v, delta;
+  DevBuf order;                   // int32 indices of Delta ascending (first n_order)
+  int n_order = 0;
+  // exact factors
+  DevBuf x64_oo, x64_ov, x64_vv;
+  DevBuf x32_oo, x32_ov, x32_vv;
+  DevBuf x16_vv_hi, x16_vv_lo;
+  // ris factors: Coulomb ov (all rows), exchange oo/vv/ov (s rows, windowed)
+  DevBuf r64_J, r64_Koo, r64_Kvv, r64_Kov;
+  DevBuf r16_J, r16_Koo, r16_Kvv, r16_Kov;
+  unsigned long long device_bytes = 0;
+  std::string err;
+  // request queue
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<unsigned long long> queue;
+  std::map<unsigned long long, Request> requests;
+  unsigned long long next_ticket = 1;
+  std::thread worker;
+  bool stopping = false;
+  std::mutex run_mu;  // one solve at a time on the context's stream
+
+  OpDims dims() const {
+    OpDims d;
+    d.no = no; d.nv = nv; d.ov = ov; d.a_x = a_x; d.c_J = c_J;
+    d.delta = delta.as<double>();
+    return d;
+  }
+  FactorSet exact(int precision) const;  // PLAIN -> FP64, MIXED -> FP32 (+ BF16 split)
+  FactorSet ris(int precision) const;    // PLAIN -> FP64, MIXED -> BF16
+};
+
+tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, double* resid,
+                     tddft_stats* st);
+tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, double* Y,
+                     double* resid, tddft_stats* st);
+tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
+                       const double* freqs, int n_freq, double* alpha, tddft_stats* st);
+
+}  // namespace tddft

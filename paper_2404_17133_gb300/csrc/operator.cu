@@ -1,0 +1,156 @@
+// On-the-fly response products over density-fitted factors (Eq. hessian with
+// (pq|rs) = sum_P L^P_pq L^P_rs, Eq. pqrs_approx):
+//   A X     = Delta X + c_J J(X) - a_x K1(X)                      (Eq. TDA)
+//   (A+B) X = Delta X + 2 c_J J(X) - a_x (K1(X) + K2(X))
+//   (A-B) X = Delta X + a_x (K2(X) - K1(X))
+// with J(X)_ia = sum_jb (ia|jb) X_jb, K1(X)_ib = sum_ja (ij|ab) X_ja,
+// K2(X)_ia = sum_jb (ib|ja) X_jb.  The four-index integrals are never formed;
+// each term is a pair of contractions over P:
+//   J : t[P][n] = sum_ia L_ov[P][ia] X[n][ia];  J[n][ia] = sum_P t[P][n] L_ov[P][ia]
+//   K1: Z[n][i][P][a] = sum_j L_oo[P][i][j] X[n][j][a]   (batched over P, n)
+//       K1[(n,i)][b] = sum_(P,a) Z[(n,i)][(P,a)] L_vv[P][a][b]   (one tall-K GEMM)
+//   K2: Q[n][i][P][j] = sum_b L_ov[P][i][b] X[n][j][b]
+//       K2[(n,i)][a] = sum_(P,j) Q[(n,i)][(P,j)] L_ov[P][j][a]
+// P is processed in chunks so the intermediates stay within a bounded
+// workspace; K1's second contraction (about 90% of the flops) optionally runs
+// on the tcgen05 tensor cores.
+#include "ctx.cuh"
+#include "tc_gemm.cuh"
+#include "vecops.cuh"
+
+namespace tddft {
+
+namespace {
+constexpr size_t kChunkBytes = 512ull << 20;
+
+int chunk_rows(int nrows, long long per_row_bytes, int m) {
+  long long pc = (long long)(kChunkBytes / (per_row_bytes > 0 ? per_row_bytes : 1));
+  if (pc < 1) pc = 1;
+  if (pc > nrows) pc = nrows;
+  long long bmax = 65535 / (m > 0 ? m : 1);
+  if (pc > bmax) pc = bmax;
+  return (int)(pc < 1 ? 1 : pc);
+}
+}  // namespace
+
+void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m, OpMode mode,
+                    double* out0, double* out1, bool tensor_cores, cudaStream_t s) {
+  if (m <= 0) return;
+  const int no = d.no, nv = d.nv, ov = d.ov;
+  const bool f64 = (f.dt == DType::F64);
+  const DType tw = f64 ? DType::F64 : DType::F32;  // working / accumulation type
+  const size_t ew = dtype_size(tw);
+  const long long mov = (long long)m * ov;
+
+  const void* Xw = X;
+  DevBuf xbuf;
+  if (!f64) {
+    xbuf = DevBuf(mov * 4, s);
+    cast_f64_to_f32(X, xbuf.as<float>(), mov, s);
+    Xw = xbuf.p;
+  }
+
+  // ---- Coulomb
+  DevBuf Jb;
+  if (f.nJ > 0 && d.c_J != 0.0) {
+    DevBuf t((size_t)f.nJ * m * ew, s);
+    Jb = DevBuf(mov * ew, s);
+    GemmDesc g;
+    g.acc64 = f64;
+    g.M = f.nJ; g.N = m; g.K = ov;
+    g.A = f.Jov; g.ta = f.dt; g.sam = ov; g.sak = 1;
+    g.B = Xw; g.tb = tw; g.sbk = 1; g.sbn = ov;
+    g.C = t.p; g.tc = tw; g.scm = m; g.scn = 1;
+    gemm_splitk(g, auto_splits(g.M, g.N, g.K), s);
+    GemmDesc h;
+    h.acc64 = f64;
+    h.M = m; h.N = ov; h.K = f.nJ;
+    h.A = t.p; h.ta = tw; h.sam = 1; h.sak = m;
+    h.B = f.Jov; h.tb = f.dt; h.sbk = ov; h.sbn = 1;
+    h.C = Jb.p; h.tc = tw; h.scm = ov; h.scn = 1;
+    gemm(h, s);
+  }
+
+  // ---- exchange
+  DevBuf K1b, K2b;
+  const bool need_k2 = (mode == OpMode::PAIRED);
+  if (f.nK > 0 && d.a_x != 0.0) {
+    K1b = DevBuf(mov * ew, s);
+    if (need_k2) K2b = DevBuf(mov * ew, s);
+    const int pc = chunk_rows(f.nK, (long long)m * ov * (long long)ew, m);
+    DevBuf Zb((size_t)m * no * pc * nv * ew, s);
+    DevBuf Qb;
+    if (need_k2) Qb = DevBuf((size_t)m * no * pc * no * ew, s);
+    DevBuf Zhi, Zlo;
+    const bool use_tc = tensor_cores && !f64 && f.Kvv_hi && f.Kvv_lo;
+    if (use_tc) {
+      Zhi = DevBuf((size_t)m * no * pc * nv * 2, s);
+      Zlo = DevBuf((size_t)m * no * pc * nv * 2, s);
+    }
+    const size_t es = dtype_size(f.dt);
+    for (int p0 = 0; p0 < f.nK; p0 += pc) {
+      const int pn = (f.nK - p0 < pc) ? f.nK - p0 : pc;
+      // Z[n][i][P][a] = sum_j Koo[P][i][j] X[n][j][a]
+      GemmDesc z;
+      z.acc64 = f64;
+      z.M = no; z.N = nv; z.K = no;
+      z.A = (const char*)f.Koo + (size_t)p0 * no * no * es; z.ta = f.dt; z.sam = no; z.sak = 1;
+      z.B = Xw; z.tb = tw; z.sbk = nv; z.sbn = 1;
+      z.C = Zb.p; z.tc = tw; z.scm = (long long)pn * nv; z.scn = 1;
+      z.nb0 = pn; z.nb1 = m;
+      z.sA0 = (long long)no * no; z.sB0 = 0; z.sC0 = nv;
+      z.sA1 = 0; z.sB1 = ov; z.sC1 = (long long)no * pn * nv;
+      gemm(z, s);
+      const int Mz = m * no;
+      const long long Kz = (long long)pn * nv;
+      if (use_tc) {
+        split_bf16(Zb.p, DType::F32, Zhi.as<__nv_bfloat16>(), Zlo.as<__nv_bfloat16>(), (long long)Mz * Kz, s);
+        tc_exchange_k1(Zhi.as<__nv_bfloat16>(), Zlo.as<__nv_bfloat16>(), Mz, pn, nv,
+                       f.Kvv_hi + (size_t)p0 * nv * nv, f.Kvv_lo + (size_t)p0 * nv * nv,
+                       K1b.as<float>(), p0 > 0, s);
+      } else {
+        GemmDesc k;
+        k.acc64 = f64;
+        k.M = Mz; k.N = nv; k.K = (int)Kz;
+        k.A = Zb.p; k.ta = tw; k.sam = Kz; k.sak = 1;
+        k.B = (const char*)f.Kvv + (size_t)p0 * nv * nv * es; k.tb = f.dt; k.sbk = nv; k.sbn = 1;
+        k.C = K1b.p; k.tc = tw; k.scm = nv; k.scn = 1;
+        k.beta = (p0 > 0) ? 1.0 : 0.0;
+        gemm_splitk(k, auto_splits(k.M, k.N, k.K), s);
+      }
+      if (need_k2) {
+        // Q[n][i][P][j] = sum_b Kov[P][i][b] X[n][j][b]
+        GemmDesc q;
+        q.acc64 = f64;
+        q.M = no; q.N = no; q.K = nv;
+        q.A = (const char*)f.Kov + (size_t)p0 * ov * es; q.ta = f.dt; q.sam = nv; q.sak = 1;
+        q.B = Xw; q.tb = tw; q.sbk = 1; q.sbn = nv;
+        q.C = Qb.p; q.tc = tw; q.scm = (long long)pn * no; q.scn = 1;
+        q.nb0 = pn; q.nb1 = m;
+        q.sA0 = ov; q.sB0 = 0; q.sC0 = no;
+        q.sA1 = 0; q.sB1 = ov; q.sC1 = (long long)no * pn * no;
+        gemm(q, s);
+        GemmDesc k2;
+        k2.acc64 = f64;
+        k2.M = m * no; k2.N = nv; k2.K = pn * no;
+        k2.A = Qb.p; k2.ta = tw; k2.sam = (long long)pn * no; k2.sak = 1;
+        k2.B = (const char*)f.Kov + (size_t)p0 * ov * es; k2.tb = f.dt; k2.sbk = nv; k2.sbn = 1;
+        k2.C = K2b.p; k2.tc = tw; k2.scm = nv; k2.scn = 1;
+        k2.beta = (p0 > 0) ? 1.0 : 0.0;
+        gemm_splitk(k2, auto_splits(k2.M, k2.N, k2.K), s);
+      }
+    }
+  }
+
+  const void* J = Jb.p;
+  const void* K1 = K1b.p;
+  const void* K2 = K2b.p;
+  if (mode == OpMode::TDA) {
+    combine(X, d.delta, J, K1, nullptr, tw, d.c_J, -d.a_x, 0.0, m, ov, out0, s);
+  } else {
+    combine(X, d.delta, J, K1, K2, tw, 2.0 * d.c_J, -d.a_x, -d.a_x, m, ov, out0, s);
+    combine(X, d.delta, nullptr, K1, K2, tw, 0.0, -d.a_x, d.a_x, m, ov, out1, s);
+  }
+}
+
+}  // namespace tddft

@@ -1,0 +1,44 @@
+// Small dense subspace algebra (projected matrices of size n <= kSmallMax).
+#pragma once
+#include "common.cuh"
+
+namespace tddft {
+
+constexpr int kSmallMax = 160;   // largest projected matrix (subspace) handled
+constexpr int kWantMax = 64;     // largest number of refined eigenpairs
+
+// FP32 eigendecomposition of a symmetric FP64 matrix H (n x n, leading dim ldh):
+// eigenvalues ascending in lam32[n]; eigenvectors as rows vec32[j*n + r].
+void eig32(const double* H, int ldh, int n, float* lam32, float* vec32, cudaStream_t s);
+
+// FP64 eigenpairs (lowest k) of H refined from the FP32 decomposition:
+// lam[k] ascending, vecs[i*n + r] (row i = eigenvector i, orthonormal).
+// `rounds` Newton-type correction rounds, then Cholesky-QR and an FP64
+// Rayleigh-Ritz on the k-dimensional space.  scratch: >= 2*k*n doubles.
+void refine_lowest(const double* H, int ldh, int n, int k, const float* lam32, const float* vec32,
+                   double* lam, double* vecs, double* scratch, int rounds, cudaStream_t s);
+
+// Y[r] = (H - sigma[r] I)^-1 B[r] for r < nr (rows of length n), from the FP32
+// decomposition plus `nref` FP64 residual-correction rounds (kept only while
+// they reduce the residual).
+void shifted_solve(const double* H, int ldh, int n, const float* lam32, const float* vec32,
+                   const double* sigma, int nr, const double* B, double* Y, int nref,
+                   cudaStream_t s);
+
+// In-place FP64 Cholesky H = L L^T (lower, zeroed above the diagonal).
+// info[0] = 0 on success, j+1 when pivot j is not positive / not finite.
+void cholesky(double* H, int ldh, int n, int* info, cudaStream_t s);
+
+// Triangular solves with the lower factor L (n x n, ldl) for nr right-hand
+// sides stored as rows of B (in place): trans = 0: L x = b; 1: L^T x = b.
+void trsv_rows(const double* L, int ldl, int n, double* B, int nr, int trans, cudaStream_t s);
+
+// Orthonormalisation helper for a block of candidate rows (Gram matrix
+// G = C C^T given): pivot-dropping Cholesky G = R^T R over the candidates in
+// order; a candidate whose remaining squared norm is below
+// drop2 * norm0sq[j] is dropped.  Writes T (nc x nc, row-major) with
+// C_new = T C orthonormal (zero rows for dropped) and keep[j] flags.
+void chol_drop(const double* G, int nc, const double* norm0sq, double drop2, double* T,
+               int* keep, cudaStream_t s);
+
+}  // namespace tddft

@@ -1,0 +1,911 @@
+// Preconditioned Davidson drivers (Sec. 2.1) for the TDA eigenproblem (Eq. TDA),
+// the Casida eigenproblem (Eq. Casida) and the polarizability linear systems
+// (Eq. TDDFT_polar), with the diagonal and the rid preconditioners (Sec. 3).
+//
+// Everything the algorithm computes stays on the device; per iteration the host
+// reads back only the Ritz values and residual norms (a few hundred bytes) to
+// decide convergence, locking and the next launch sizes.  Each step maps to
+// kernels as follows:
+//   Eq. 1   projected matrix, new columns only     split-K FP64 GEMM + sym_fill
+//   Eq. 2   subspace eigenproblem                  eig32 (FP32 Jacobi) + FP64 refinement
+//   Eq. 3   Ritz vectors X = V x, A X = (A V) x    FP64 GEMM
+//   Eq. residual                                    resid kernels + row norms
+//   Eq. precondition                                diag: element-wise; rid: inner
+//                                                   Galerkin solve with the ris operator
+//   Gram-Schmidt + append                           block Gram-Schmidt (two passes of
+//                                                   projection + pivot-dropping Cholesky)
+// The Casida problem uses one subspace V for X+Y and X-Y with a+ = V^T(A+B)V,
+// a- = V^T(A-B)V, solved in the symmetric form L^T a+ L y = Omega^2 y (a- = L L^T).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <functional>
+#include <numeric>
+
+#include "ctx.cuh"
+#include "small.cuh"
+#include "vecops.cuh"
+
+namespace tddft {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+inline double since(Clock::time_point t0) {
+  return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+constexpr double kDrop2 = 1e-16;   // drop a direction below 1e-8 of its norm
+
+template <typename T>
+std::vector<T> d2h(const T* p, size_t n, cudaStream_t s) {
+  std::vector<T> h(n);
+  if (n) {
+    TD_CUDA(cudaMemcpyAsync(h.data(), p, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    TD_CUDA(cudaStreamSynchronize(s));
+  }
+  return h;
+}
+
+template <typename T>
+void h2d(T* p, const std::vector<T>& h, cudaStream_t s) {
+  if (!h.empty()) TD_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+struct Counters {
+  long long mv = 0;      // exact operator vectors
+  long long ris_mv = 0;  // ris operator vectors
+  double t_mv = 0.0, t_pre = 0.0;
+  int restarts = 0;
+};
+
+using TdaOp = std::function<void(const double* X, int m, double* out)>;
+using PairOp = std::function<void(const double* X, int m, double* P, double* M)>;
+// TDA preconditioner: (R [nu][ov], shifts dev/host) -> out [nu][ov]
+using TdaPre = std::function<void(const double* R, const double* sh, const std::vector<double>& shh,
+                                  int nu, double* out)>;
+// paired preconditioner: (g+ , g-, shifts) -> (u, w) each [nu][ov]
+using PairPre = std::function<void(const double* gp, const double* gm, const double* sh,
+                                   const std::vector<double>& shh, int nu, double* u, double* w)>;
+
+// ---------------------------------------------------------------------------
+// Subspace helpers (FP64)
+
+// a[r][col0 + j] = V[r] . Wn[j]  for r < N, j < k
+void proj_cols(const double* V, int N, const double* Wn, int k, int ov, double* a, int ld, int col0,
+               cudaStream_t s) {
+  gemm_splitk_f64(N, k, ov, V, ov, 1, Wn, 1, ov, a + col0, ld, 1, 1.0, 0.0, s);
+}
+
+// G[i][j] = A[i] . B[j]  (rows of length ov), G row stride ldg
+void gram(const double* A, int ka, const double* B, int kb, int ov, double* G, int ldg, cudaStream_t s) {
+  gemm_splitk_f64(ka, kb, ov, A, ov, 1, B, 1, ov, G, ldg, 1, 1.0, 0.0, s);
+}
+
+// out[j] = alpha * sum_r coef[j][r] V[r] + beta * out[j]   (coef row stride ldc)
+void combo(const double* coef, int ldc, int k, int N, const double* V, int ov, double* out,
+           double alpha, double beta, cudaStream_t s) {
+  GemmDesc g;
+  g.M = k; g.N = ov; g.K = N;
+  g.A = coef; g.sam = ldc; g.sak = 1;
+  g.B = V; g.sbk = ov; g.sbn = 1;
+  g.C = out; g.scm = ov; g.scn = 1;
+  g.alpha = alpha; g.beta = beta;
+  gemm(g, s);
+}
+
+// small dense product C = A * B with general strides (FP64)
+void small_mm(int M, int N, int K, const double* A, long long sam, long long sak, const double* B,
+              long long sbk, long long sbn, double* C, long long scm, cudaStream_t s) {
+  GemmDesc g;
+  g.M = M; g.N = N; g.K = K;
+  g.A = A; g.sam = sam; g.sak = sak;
+  g.B = B; g.sbk = sbk; g.sbn = sbn;
+  g.C = C; g.scm = scm; g.scn = 1;
+  gemm(g, s);
+}
+
+// Orthonormalise the candidate rows `cand` [nc][ov] against V (N rows) and each
+// other, two passes; append the survivors at V[N...].  Returns their number.
+int orth_append(double* V, int N, double* cand, int nc, int ov, cudaStream_t s) {
+  if (nc <= 0) return 0;
+  TD_REQUIRE(nc <= 112, TDDFT_ERR_ARG, "too many new directions in one iteration");
+  DevBuf n0(nc * 8, s), ones(nc * 8, s), G((size_t)nc * nc * 8, s), T((size_t)nc * nc * 8, s);
+  DevBuf keep(nc * 4, s), tmp((size_t)nc * ov * 8, s);
+  DevBuf coef(N > 0 ? (size_t)N * nc * 8 : 8, s);
+  row_sumsq(cand, ov, nc, ov, n0.as<double>(), s);
+  h2d(ones.as<double>(), std::vector<double>(nc, 1.0), s);
+  double* cur = cand;
+  double* oth = tmp.as<double>();
+  for (int pass = 0; pass < 2; ++pass) {
+    if (N > 0) {
+      gram(V, N, cur, nc, ov, coef.as<double>(), nc, s);          // coef[r][j] = V[r].cur[j]
+      GemmDesc g;                                                   // cur[j] -= sum_r coef[r][j] V[r]
+      g.M = nc; g.N = ov; g.K = N;
+      g.A = coef.p; g.sam = 1; g.sak = nc;
+      g.B = V; g.sbk = ov; g.sbn = 1;
+      g.C = cur; g.scm = ov; g.scn = 1;
+      g.alpha = -1.0; g.beta = 1.0;
+      gemm(g, s);
+    }
+    gram(cur, nc, cur, nc, ov, G.as<double>(), nc, s);
+    chol_drop(G.as<double>(), nc, pass == 0 ? n0.as<double>() : ones.as<double>(), kDrop2,
+              T.as<double>(), keep.as<int>(), s);
+    combo(T.as<double>(), nc, nc, nc, cur, ov, oth, 1.0, 0.0, s);
+    std::swap(cur, oth);
+  }
+  std::vector<int> kh = d2h(keep.as<int>(), nc, s);
+  std::vector<int> idx;
+  for (int j = 0; j < nc; ++j)
+    if (kh[j]) idx.push_back(j);
+  if (!idx.empty()) {
+    DevBuf di(idx.size() * 4, s);
+    h2d(di.as<int>(), idx, s);
+    gather_rows(cur, di.as<int>(), (int)idx.size(), ov, V + (size_t)N * ov, s);
+  }
+  return (int)idx.size();
+}
+
+void check_finite_host(const std::vector<double>& v, const char* what) {
+  for (double x : v)
+    if (!std::isfinite(x))
+      throw Error(TDDFT_ERR_INDEFINITE, std::string("non-finite values in ") + what);
+}
+
+std::vector<double> sqrt_all(const std::vector<double>& v) {
+  std::vector<double> r(v.size());
+  for (size_t i = 0; i < v.size(); ++i) r[i] = std::sqrt(v[i]);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// TDA Davidson (Sec. 2.1) on a generic symmetric operator.
+
+struct TdaOut {
+  std::vector<double> omega, resid;
+  DevBuf X;     // [k][ov] Ritz vectors
+  int n_iter = 0;
+  bool converged = false;
+};
+
+TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, int ng, int k,
+                    double tol, int max_iter, int cap, int rounds, Counters& cnt, bool exact_op,
+                    cudaStream_t s) {
+  TdaOut o;
+  k = std::min(k, ov);
+  cap = std::min(cap, kSmallMax);
+  TD_REQUIRE(k >= 1 && k <= kWantMax, TDDFT_ERR_ARG, "n_states out of range");
+  TD_REQUIRE(cap >= 2 * k, TDDFT_ERR_ARG, "max_subspace must be at least 2*n_states");
+  DevBuf V((size_t)cap * ov * 8, s), W((size_t)cap * ov * 8, s);
+  DevBuf a((size_t)cap * cap * 8, s), lam32(cap * 4, s), vec32((size_t)cap * cap * 4, s);
+  DevBuf lam(k * 8, s), x((size_t)k * cap * 8, s), scr((size_t)2 * k * cap * 8, s);
+  DevBuf X((size_t)k * ov * 8, s), AX((size_t)k * ov * 8, s), R((size_t)k * ov * 8, s);
+  DevBuf rn(k * 8, s), Ru((size_t)k * ov * 8, s), omu(k * 8, s), cand((size_t)k * ov * 8, s);
+  DevBuf iu(k * 4, s);
+  double* Vp = V.as<double>();
+  double* Wp = W.as<double>();
+
+  int N = orth_append(Vp, 0, guess, std::min(ng, cap), ov, s);
+  TD_REQUIRE(N >= 1, TDDFT_ERR_ARG, "initial guess is empty");
+  auto mv = [&](int r0, int m) {
+    auto t0 = Clock::now();
+    A(Vp + (size_t)r0 * ov, m, Wp + (size_t)r0 * ov);
+    TD_CUDA(cudaStreamSynchronize(s));
+    if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
+  };
+  mv(0, N);
+  int n_old = 0, n_new = N;
+  std::vector<double> om(k), rr(k);
+  int kk = std::min(k, N);
+  for (int it = 1; it <= max_iter; ++it) {
+    o.n_iter = it;
+    proj_cols(Vp, N, Wp + (size_t)n_old * ov, n_new, ov, a.as<double>(), cap, n_old, s);   // Eq. 1
+    sym_fill(a.as<double>(), cap, n_old, n_new, s);
+    kk = std::min(k, N);
+    eig32(a.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);               // Eq. 2
+    refine_lowest(a.as<double>(), cap, N, kk, lam32.as<float>(), vec32.as<float>(), lam.as<double>(),
+                  x.as<double>(), scr.as<double>(), rounds, s);
+    combo(x.as<double>(), N, kk, N, Vp, ov, X.as<double>(), 1.0, 0.0, s);                // Eq. 3
+    combo(x.as<double>(), N, kk, N, Wp, ov, AX.as<double>(), 1.0, 0.0, s);
+    resid_tda(X.as<double>(), AX.as<double>(), lam.as<double>(), kk, ov, R.as<double>(), s);  // Eq. residual
+    row_sumsq(R.as<double>(), ov, kk, ov, rn.as<double>(), s);
+    om = d2h(lam.as<double>(), kk, s);
+    rr = sqrt_all(d2h(rn.as<double>(), kk, s));
+    check_finite_host(om, "Ritz values");
+    check_finite_host(rr, "residual norms");
+    std::vector<int> todo;
+    for (int j = 0; j < kk; ++j)
+      if (!(rr[j] < tol)) todo.push_back(j);
+    if (todo.empty() && kk == k) { o.converged = true; break; }
+    if (it == max_iter) break;
+    const int nu = (int)todo.size();
+    std::vector<double> omh(nu);
+    for (int j = 0; j < nu; ++j) omh[j] = om[todo[j]];
+    h2d(iu.as<int>(), todo, s);
+    gather_rows(R.as<double>(), iu.as<int>(), nu, ov, Ru.as<double>(), s);
+    h2d(omu.as<double>(), omh, s);
+    auto tp = Clock::now();
+    pre(Ru.as<double>(), omu.as<double>(), omh, nu, cand.as<double>());                   // Eq. precondition
+    TD_CUDA(cudaStreamSynchronize(s));
+    cnt.t_pre += since(tp);
+    if (N + nu > cap) {
+      // collapse onto the current Ritz vectors of the wanted roots
+      TD_CUDA(cudaMemcpyAsync(Vp, X.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
+      TD_CUDA(cudaMemcpyAsync(Wp, AX.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
+      N = kk;
+      n_old = 0;
+      n_new = kk;
+      proj_cols(Vp, N, Wp, N, ov, a.as<double>(), cap, 0, s);
+      sym_fill(a.as<double>(), cap, 0, N, s);
+      n_old = N;
+      n_new = 0;
+      cnt.restarts++;
+    }
+    int nacc = orth_append(Vp, N, cand.as<double>(), nu, ov, s);
+    if (nacc == 0) break;
+    mv(N, nacc);
+    n_old = N;
+    n_new = nacc;
+    N += nacc;
+  }
+  o.omega = om;
+  o.resid = rr;
+  o.X = std::move(X);
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// Paired subspace algebra shared by the Casida eigenproblem and the paired
+// linear systems: a+ = V^T P, a- = V^T M, a- = L L^T, H = L^T a+ L.
+
+struct PairedSpace {
+  int ov, cap;
+  cudaStream_t s;
+  DevBuf V, P, M, ap, am, L, tmp, H, lam32, vec32;
+  int N = 0, n_old = 0, n_new = 0;
+  DevBuf info;
+  PairedSpace(int ov_, int cap_, cudaStream_t s_) : ov(ov_), cap(cap_), s(s_) {
+    V = DevBuf((size_t)cap * ov * 8, s);
+    P = DevBuf((size_t)cap * ov * 8, s);
+    M = DevBuf((size_t)cap * ov * 8, s);
+    ap = DevBuf((size_t)cap * cap * 8, s);
+    am = DevBuf((size_t)cap * cap * 8, s);
+    L = DevBuf((size_t)cap * cap * 8, s);
+    tmp = DevBuf((size_t)cap * cap * 8, s);
+    H = DevBuf((size_t)cap * cap * 8, s);
+    lam32 = DevBuf(cap * 4, s);
+    vec32 = DevBuf((size_t)cap * cap * 4, s);
+    info = DevBuf(4, s);
+  }
+  double* v() { return V.as<double>(); }
+  double* p() { return P.as<double>(); }
+  double* m() { return M.as<double>(); }
+  // project the new vectors, factor, form H and its FP32 decomposition
+  void update() {
+    proj_cols(v(), N, p() + (size_t)n_old * ov, n_new, ov, ap.as<double>(), cap, n_old, s);
+    proj_cols(v(), N, m() + (size_t)n_old * ov, n_new, ov, am.as<double>(), cap, n_old, s);
+    sym_fill(ap.as<double>(), cap, n_old, n_new, s);
+    sym_fill(am.as<double>(), cap, n_old, n_new, s);
+    TD_CUDA(cudaMemcpyAsync(L.p, am.p, (size_t)cap * cap * 8, cudaMemcpyDeviceToDevice, s));
+    cholesky(L.as<double>(), cap, N, info.as<int>(), s);
+    // tmp = a+ L ; H = L^T tmp
+    small_mm(N, N, N, ap.as<double>(), cap, 1, L.as<double>(), cap, 1, tmp.as<double>(), cap, s);
+    small_mm(N, N, N, L.as<double>(), 1, cap, tmp.as<double>(), cap, 1, H.as<double>(), cap, s);
+    eig32(H.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);
+    n_old = N;
+    n_new = 0;
+  }
+  void check_definite() {
+    int inf = d2h(info.as<int>(), 1, s)[0];
+    if (inf != 0)
+      throw Error(TDDFT_ERR_INDEFINITE, "projected A-B is not positive definite (pivot " +
+                                            std::to_string(inf - 1) + ")");
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Paired Galerkin linear solve (Eq. TDDFT_polar, and the paired form of
+// Eq. precondition):  T+ u - s w = g+,  T- w - s u = g-  for nr right-hand
+// sides in one shared subspace.
+
+struct PairedLinOut {
+  int n_iter = 0;
+  bool converged = false;
+  std::vector<double> resid;
+};
+
+PairedLinOut paired_linear(int ov, const PairOp& op, const PairPre& pre, const double* gp,
+                           const double* gm, const std::vector<double>& shifts, int nr,
+                           double* init, int ni, double tol, int max_iter, int cap, int nref,
+                           bool exact_op, Counters& cnt, double* Uout, double* Wout,
+                           cudaStream_t s) {
+  PairedLinOut o;
+  cap = std::min(cap, kSmallMax);
+  PairedSpace sp(ov, cap, s);
+  DevBuf sh(nr * 8, s), sig2(nr * 8, s);
+  std::vector<double> s2(nr);
+  for (int r = 0; r < nr; ++r) s2[r] = shifts[r] * shifts[r];
+  h2d(sh.as<double>(), shifts, s);
+  h2d(sig2.as<double>(), s2, s);
+  DevBuf hp((size_t)nr * cap * 8, s), hm((size_t)nr * cap * 8, s), rhs((size_t)nr * cap * 8, s);
+  DevBuf ut((size_t)nr * cap * 8, s), uc((size_t)nr * cap * 8, s), wc((size_t)nr * cap * 8, s);
+  DevBuf Rp((size_t)nr * ov * 8, s), Rm((size_t)nr * ov * 8, s), PU((size_t)nr * ov * 8, s),
+      MW((size_t)nr * ov * 8, s);
+  DevBuf gn(nr * 8, s), gn2(nr * 8, s), rn1(nr * 8, s), rn2(nr * 8, s);
+  DevBuf iu(nr * 4, s), shu(nr * 8, s), gpu_(((size_t)nr) * ov * 8, s), gmu((size_t)nr * ov * 8, s);
+  DevBuf cand((size_t)2 * nr * ov * 8, s);
+  row_sumsq(gp, ov, nr, ov, gn.as<double>(), s);
+  std::vector<double> gnh = d2h(gn.as<double>(), nr, s);
+  if (gm) {
+    row_sumsq(gm, ov, nr, ov, gn2.as<double>(), s);
+    std::vector<double> t = d2h(gn2.as<double>(), nr, s);
+    for (int r = 0; r < nr; ++r) gnh[r] += t[r];
+  }
+  for (auto& v : gnh) v = std::sqrt(v);
+
+  sp.N = orth_append(sp.v(), 0, init, std::min(ni, cap), ov, s);
+  TD_REQUIRE(sp.N >= 1, TDDFT_ERR_ARG, "paired solve: empty initial subspace");
+  auto mv = [&](int r0, int m) {
+    auto t0 = Clock::now();
+    op(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
+    TD_CUDA(cudaStreamSynchronize(s));
+    if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
+  };
+  mv(0, sp.N);
+  sp.n_old = 0;
+  sp.n_new = sp.N;
+  std::vector<double> rr(nr, 0.0);
+  for (int it = 1; it <= max_iter; ++it) {
+    o.n_iter = it;
+    sp.update();
+    sp.check_definite();
+    const int N = sp.N;
+    double* Lp = sp.L.as<double>();
+    // h+ = V g+ , h- = V g-   ([nr][N])
+    gram(gp, nr, sp.v(), N, ov, hp.as<double>(), N, s);
+    // rhs = L^T h+  (rows): rhs[r][i] = sum_q h+[r][q] L[q][i]
+    small_mm(nr, N, N, hp.as<double>(), N, 1, Lp, cap, 1, rhs.as<double>(), N, s);
+    if (gm) {
+      gram(gm, nr, sp.v(), N, ov, hm.as<double>(), N, s);
+      trsv_rows(Lp, cap, N, hm.as<double>(), nr, 0, s);                 // z- = L^-1 h-
+      axpy_rows(rhs.as<double>(), hm.as<double>(), sh.as<double>(), nr, N, s);
+    }
+    shifted_solve(sp.H.as<double>(), cap, N, sp.lam32.as<float>(), sp.vec32.as<float>(),
+                  sig2.as<double>(), nr, rhs.as<double>(), ut.as<double>(), nref, s);
+    // u = L u~ : u[r][i] = sum_q L[i][q] u~[r][q]
+    small_mm(nr, N, N, ut.as<double>(), N, 1, Lp, 1, cap, uc.as<double>(), N, s);
+    // w = L^-T (z- + s u~)
+    if (gm) TD_CUDA(cudaMemcpyAsync(wc.p, hm.p, (size_t)nr * N * 8, cudaMemcpyDeviceToDevice, s));
+    else TD_CUDA(cudaMemsetAsync(wc.p, 0, (size_t)nr * N * 8, s));
+    axpy_rows(wc.as<double>(), ut.as<double>(), sh.as<double>(), nr, N, s);
+    trsv_rows(Lp, cap, N, wc.as<double>(), nr, 1, s);
+    combo(uc.as<double>(), N, nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
+    combo(wc.as<double>(), N, nr, N, sp.v(), ov, Wout, 1.0, 0.0, s);
+    combo(uc.as<double>(), N, nr, N, sp.p(), ov, PU.as<double>(), 1.0, 0.0, s);
+    combo(wc.as<double>(), N, nr, N, sp.m(), ov, MW.as<double>(), 1.0, 0.0, s);
+    resid_paired(Uout, Wout, PU.as<double>(), MW.as<double>(), sh.as<double>(), gp, gm, nr, ov,
+                 Rp.as<double>(), Rm.as<double>(), s);
+    row_sumsq(Rp.as<double>(), ov, nr, ov, rn1.as<double>(), s);
+    row_sumsq(Rm.as<double>(), ov, nr, ov, rn2.as<double>(), s);
+    std::vector<double> a1 = d2h(rn1.as<double>(), nr, s), a2 = d2h(rn2.as<double>(), nr, s);
+    std::vector<int> todo;
+    for (int r = 0; r < nr; ++r) {
+      rr[r] = std::sqrt(a1[r] + a2[r]) / (gnh[r] > 0 ? gnh[r] : 1.0);
+      if (!(rr[r] <= tol)) todo.push_back(r);
+    }
+    check_finite_host(rr, "linear-system residuals");
+    if (todo.empty()) { o.converged = true; break; }
+    if (it == max_iter) break;
+    const int nu = (int)todo.size();
+    std::vector<double> shh(nu);
+    for (int j = 0; j < nu; ++j) shh[j] = shifts[todo[j]];
+    h2d(iu.as<int>(), todo, s);
+    h2d(shu.as<double>(), shh, s);
+    gather_rows(Rp.as<double>(), iu.as<int>(), nu, ov, gpu_.as<double>(), s);
+    gather_rows(Rm.as<double>(), iu.as<int>(), nu, ov, gmu.as<double>(), s);
+    auto tp = Clock::now();
+    pre(gpu_.as<double>(), gmu.as<double>(), shu.as<double>(), shh, nu, cand.as<double>(),
+        cand.as<double>() + (size_t)nu * ov);
+    TD_CUDA(cudaStreamSynchronize(s));
+    cnt.t_pre += since(tp);
+    if (sp.N + 2 * nu > cap) {
+      if (!exact_op) break;   // inner solve: return the current approximate solution
+      // restart the subspace from the current solutions U and W of every system
+      DevBuf rst((size_t)2 * nr * ov * 8, s);
+      TD_CUDA(cudaMemcpyAsync(rst.p, Uout, (size_t)nr * ov * 8, cudaMemcpyDeviceToDevice, s));
+      TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)nr * ov, Wout, (size_t)nr * ov * 8,
+                              cudaMemcpyDeviceToDevice, s));
+      sp.N = orth_append(sp.v(), 0, rst.as<double>(), 2 * nr, ov, s);
+      mv(0, sp.N);
+      sp.n_old = 0;
+      sp.n_new = sp.N;
+      cnt.restarts++;
+    }
+    int nacc = orth_append(sp.v(), sp.N, cand.as<double>(), 2 * nu, ov, s);
+    if (nacc == 0) break;
+    mv(sp.N, nacc);
+    sp.n_new += nacc;
+    sp.N += nacc;
+  }
+  o.resid = rr;
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// Casida Davidson (paired eigenproblem).
+
+struct RpaOut {
+  std::vector<double> omega, resid;
+  DevBuf U, W;
+  int n_iter = 0;
+  bool converged = false;
+};
+
+RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess, int ng, int k,
+                    double tol, int max_iter, int cap, int rounds, Counters& cnt, bool exact_op,
+                    cudaStream_t s) {
+  RpaOut o;
+  k = std::min(k, ov);
+  cap = std::min(cap, kSmallMax);
+  TD_REQUIRE(k >= 1 && k <= kWantMax, TDDFT_ERR_ARG, "n_states out of range");
+  TD_REQUIRE(cap >= 4 * k, TDDFT_ERR_ARG, "max_subspace must be at least 4*n_states");
+  PairedSpace sp(ov, cap, s);
+  DevBuf lamH(k * 8, s), y((size_t)k * cap * 8, s), scr((size_t)2 * k * cap * 8, s);
+  DevBuf uc((size_t)k * cap * 8, s), wc((size_t)k * cap * 8, s), isq(k * 8, s), iom(k * 8, s),
+      omd(k * 8, s);
+  DevBuf U((size_t)k * ov * 8, s), W((size_t)k * ov * 8, s), PU((size_t)k * ov * 8, s),
+      MW((size_t)k * ov * 8, s), Rp((size_t)k * ov * 8, s), Rm((size_t)k * ov * 8, s);
+  DevBuf rn1(k * 8, s), rn2(k * 8, s), iu(k * 4, s), shu(k * 8, s);
+  DevBuf gpu_((size_t)k * ov * 8, s), gmu((size_t)k * ov * 8, s), cand((size_t)2 * k * ov * 8, s);
+  DevBuf rst((size_t)2 * k * ov * 8, s);
+
+  sp.N = orth_append(sp.v(), 0, guess, std::min(ng, cap), ov, s);
+  TD_REQUIRE(sp.N >= 1, TDDFT_ERR_ARG, "initial guess is empty");
+  auto mv = [&](int r0, int m) {
+    auto t0 = Clock::now();
+    op(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
+    TD_CUDA(cudaStreamSynchronize(s));
+    if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
+  };
+  mv(0, sp.N);
+  sp.n_old = 0;
+  sp.n_new = sp.N;
+  std::vector<double> om(k), rr(k);
+  int kk = k;
+  for (int it = 1; it <= max_iter; ++it) {
+    o.n_iter = it;
+    sp.update();
+    sp.check_definite();
+    const int N = sp.N;
+    kk = std::min(k, N);
+    double* Lp = sp.L.as<double>();
+    refine_lowest(sp.H.as<double>(), cap, N, kk, sp.lam32.as<float>(), sp.vec32.as<float>(),
+                  lamH.as<double>(), y.as<double>(), scr.as<double>(), rounds, s);
+    std::vector<double> l2 = d2h(lamH.as<double>(), kk, s);
+    check_finite_host(l2, "Casida Ritz values");
+    if (!(l2[0] > 0.0))
+      throw Error(TDDFT_ERR_INDEFINITE, "projected Casida problem has a non-positive Omega^2");
+    std::vector<double> isqh(kk), iomh(kk);
+    for (int j = 0; j < kk; ++j) {
+      om[j] = std::sqrt(l2[j]);
+      isqh[j] = 1.0 / std::sqrt(om[j]);
+      iomh[j] = 1.0 / om[j];
+    }
+    h2d(isq.as<double>(), isqh, s);
+    h2d(iom.as<double>(), iomh, s);
+    h2d(omd.as<double>(), std::vector<double>(om.begin(), om.begin() + kk), s);
+    // u = L y / sqrt(Omega) ; w = a+ u / Omega
+    small_mm(kk, N, N, y.as<double>(), N, 1, Lp, 1, cap, uc.as<double>(), N, s);
+    scale_rows(uc.as<double>(), isq.as<double>(), kk, N, s);
+    small_mm(kk, N, N, uc.as<double>(), N, 1, sp.ap.as<double>(), cap, 1, wc.as<double>(), N, s);
+    scale_rows(wc.as<double>(), iom.as<double>(), kk, N, s);
+    combo(uc.as<double>(), N, kk, N, sp.v(), ov, U.as<double>(), 1.0, 0.0, s);
+    combo(wc.as<double>(), N, kk, N, sp.v(), ov, W.as<double>(), 1.0, 0.0, s);
+    combo(uc.as<double>(), N, kk, N, sp.p(), ov, PU.as<double>(), 1.0, 0.0, s);
+    combo(wc.as<double>(), N, kk, N, sp.m(), ov, MW.as<double>(), 1.0, 0.0, s);
+    resid_paired(U.as<double>(), W.as<double>(), PU.as<double>(), MW.as<double>(), omd.as<double>(),
+                 nullptr, nullptr, kk, ov, Rp.as<double>(), Rm.as<double>(), s);
+    row_sumsq(Rp.as<double>(), ov, kk, ov, rn1.as<double>(), s);
+    row_sumsq(Rm.as<double>(), ov, kk, ov, rn2.as<double>(), s);
+    std::vector<double> a1 = d2h(rn1.as<double>(), kk, s), a2 = d2h(rn2.as<double>(), kk, s);
+    std::vector<int> todo;
+    for (int j = 0; j < kk; ++j) {
+      rr[j] = std::sqrt(a1[j] + a2[j]);
+      if (!(rr[j] < tol)) todo.push_back(j);
+    }
+    check_finite_host(rr, "Casida residual norms");
+    if (todo.empty() && kk == k) { o.converged = true; break; }
+    if (it == max_iter) break;
+    const int nu = (int)todo.size();
+    std::vector<double> shh(nu);
+    for (int j = 0; j < nu; ++j) shh[j] = om[todo[j]];
+    h2d(iu.as<int>(), todo, s);
+    h2d(shu.as<double>(), shh, s);
+    gather_rows(Rp.as<double>(), iu.as<int>(), nu, ov, gpu_.as<double>(), s);
+    gather_rows(Rm.as<double>(), iu.as<int>(), nu, ov, gmu.as<double>(), s);
+    auto tp = Clock::now();
+    pre(gpu_.as<double>(), gmu.as<double>(), shu.as<double>(), shh, nu, cand.as<double>(),
+        cand.as<double>() + (size_t)nu * ov);
+    TD_CUDA(cudaStreamSynchronize(s));
+    cnt.t_pre += since(tp);
+    if (sp.N + 2 * nu > cap) {
+      // restart from the X+Y and X-Y directions of the wanted roots
+      TD_CUDA(cudaMemcpyAsync(rst.p, U.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
+      TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)kk * ov, W.p, (size_t)kk * ov * 8,
+                              cudaMemcpyDeviceToDevice, s));
+      sp.N = orth_append(sp.v(), 0, rst.as<double>(), 2 * kk, ov, s);
+      mv(0, sp.N);
+      sp.n_old = 0;
+      sp.n_new = sp.N;
+      cnt.restarts++;
+    }
+    int nacc = orth_append(sp.v(), sp.N, cand.as<double>(), 2 * nu, ov, s);
+    if (nacc == 0) break;
+    mv(sp.N, nacc);
+    sp.n_new += nacc;
+    sp.N += nacc;
+  }
+  o.omega = om;
+  o.resid = rr;
+  o.U = std::move(U);
+  o.W = std::move(W);
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// rid inner solves (Eq. precondition with the ris operator, Sec. 3.1)
+
+// (T - s_n) v_n = R_n by one block Galerkin subspace, diag-preconditioned
+// expansion, stopped at |res_n| <= tol |R_n| or max_iter iterations.
+void inner_tda(int ov, const TdaOp& T, const double* delta, const double* R, const double* sh,
+               const std::vector<double>& shh, int nu, double tol, int max_iter, int nref,
+               Counters& cnt, double* out, cudaStream_t s) {
+  const int cap = kSmallMax;
+  DevBuf S((size_t)cap * ov * 8, s), TS((size_t)cap * ov * 8, s), t((size_t)cap * cap * 8, s);
+  DevBuf lam32(cap * 4, s), vec32((size_t)cap * cap * 4, s), h((size_t)nu * cap * 8, s),
+      y((size_t)nu * cap * 8, s);
+  DevBuf Tv((size_t)nu * ov * 8, s), res((size_t)nu * ov * 8, s), rn(nu * 8, s), r0(nu * 8, s);
+  DevBuf cand((size_t)nu * ov * 8, s), iu(nu * 4, s), shu(nu * 8, s), resu((size_t)nu * ov * 8, s);
+  row_sumsq(R, ov, nu, ov, r0.as<double>(), s);
+  std::vector<double> r0h = sqrt_all(d2h(r0.as<double>(), nu, s));
+  precond_tda(R, sh, delta, nu, ov, cand.as<double>(), s);
+  int N = orth_append(S.as<double>(), 0, cand.as<double>(), nu, ov, s);
+  if (N == 0) { TD_CUDA(cudaMemsetAsync(out, 0, (size_t)nu * ov * 8, s)); return; }
+  T(S.as<double>(), N, TS.as<double>());
+  cnt.ris_mv += N;
+  int n_old = 0, n_new = N;
+  for (int it = 0; it < max_iter; ++it) {
+    proj_cols(S.as<double>(), N, TS.as<double>() + (size_t)n_old * ov, n_new, ov, t.as<double>(), cap,
+              n_old, s);
+    sym_fill(t.as<double>(), cap, n_old, n_new, s);
+    gram(R, nu, S.as<double>(), N, ov, h.as<double>(), N, s);           // h[n][r] = R_n . S_r
+    eig32(t.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);
+    shifted_solve(t.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), sh, nu,
+                  h.as<double>(), y.as<double>(), nref, s);
+    combo(y.as<double>(), N, nu, N, S.as<double>(), ov, out, 1.0, 0.0, s);
+    combo(y.as<double>(), N, nu, N, TS.as<double>(), ov, Tv.as<double>(), 1.0, 0.0, s);
+    resid_shift(Tv.as<double>(), out, sh, R, nu, ov, res.as<double>(), s);
+    row_sumsq(res.as<double>(), ov, nu, ov, rn.as<double>(), s);
+    std::vector<double> rh = sqrt_all(d2h(rn.as<double>(), nu, s));
+    std::vector<int> todo;
+    for (int j = 0; j < nu; ++j)
+      if (!(rh[j] <= tol * r0h[j])) todo.push_back(j);
+    if (todo.empty() || it == max_iter - 1) break;
+    const int m = (int)todo.size();
+    std::vector<double> sm(m);
+    for (int j = 0; j < m; ++j) sm[j] = shh[todo[j]];
+    h2d(iu.as<int>(), todo, s);
+    h2d(shu.as<double>(), sm, s);
+    gather_rows(res.as<double>(), iu.as<int>(), m, ov, resu.as<double>(), s);
+    precond_tda(resu.as<double>(), shu.as<double>(), delta, m, ov, cand.as<double>(), s);
+    if (N + m > cap) break;
+    int nacc = orth_append(S.as<double>(), N, cand.as<double>(), m, ov, s);
+    if (nacc == 0) break;
+    T(S.as<double>() + (size_t)N * ov, nacc, TS.as<double>() + (size_t)N * ov);
+    cnt.ris_mv += nacc;
+    n_old = N;
+    n_new = nacc;
+    N += nacc;
+  }
+}
+
+struct Plan {
+  int precond, k, k0, max_iter, inner_max_iter, cap, rounds, nref_inner, nref_outer;
+  double tol, inner_tol, guess_tol;
+  bool mixed, tc;
+};
+
+Plan make_plan(const Ctx& c, const tddft_opts& o) {
+  TD_REQUIRE(o.n_states >= 1, TDDFT_ERR_ARG, "n_states must be positive");
+  TD_REQUIRE(o.precond == TDDFT_PRECOND_DIAG || o.precond == TDDFT_PRECOND_RID, TDDFT_ERR_ARG,
+             "unknown preconditioner");
+  TD_REQUIRE(o.precision == TDDFT_PLAIN || o.precision == TDDFT_MIXED, TDDFT_ERR_ARG,
+             "unknown precision");
+  TD_REQUIRE(o.tol > 0 && o.inner_tol > 0 && o.guess_tol > 0 && o.max_iter >= 1 &&
+                 o.inner_max_iter >= 1, TDDFT_ERR_ARG, "tolerances / iteration limits must be positive");
+  const int need = o.precision == TDDFT_PLAIN ? 1 : 2;
+  TD_REQUIRE((c.precisions & need) != 0, TDDFT_ERR_ARG,
+             "context was created without the factor copies for this precision");
+  TD_REQUIRE(!(o.tensor_cores && o.precision != TDDFT_MIXED), TDDFT_ERR_ARG,
+             "tensor_cores needs the MIXED precision");
+  Plan p;
+  p.precond = o.precond;
+  p.k = std::min(o.n_states, c.ov);
+  TD_REQUIRE(p.k <= kWantMax, TDDFT_ERR_ARG, "n_states above the supported maximum (64)");
+  int extra = o.n_extra_guess >= 0 ? o.n_extra_guess
+                                   : (o.precond == TDDFT_PRECOND_RID ? std::min(p.k, 3) : 8);
+  p.k0 = std::min(p.k + extra, c.ov);
+  p.max_iter = o.max_iter;
+  p.inner_max_iter = o.inner_max_iter;
+  p.cap = o.max_subspace > 0 ? std::min(o.max_subspace, kSmallMax) : kSmallMax;
+  p.tol = o.tol;
+  p.inner_tol = o.inner_tol;
+  p.guess_tol = o.guess_tol;
+  p.mixed = o.precision == TDDFT_MIXED;
+  p.tc = o.tensor_cores != 0;
+  p.rounds = 3;
+  p.nref_inner = p.mixed ? 0 : 2;
+  p.nref_outer = 4;
+  return p;
+}
+
+void fill_stats(tddft_stats* st, int n_iter, const Counters& cnt, bool conv,
+                const std::vector<double>& resid, double cert, Clock::time_point t0) {
+  if (!st) return;
+  st->n_iter = n_iter;
+  st->n_matvec = (int)cnt.mv;
+  st->n_ris_matvec = (int)cnt.ris_mv;
+  st->converged = conv ? 1 : 0;
+  st->n_restart = cnt.restarts;
+  double m = 0.0;
+  for (double r : resid) m = std::max(m, r);
+  st->max_resid = m;
+  st->max_resid_certified = cert;
+  st->t_total_s = since(t0);
+  st->t_matvec_s = cnt.t_mv;
+  st->t_precond_s = cnt.t_pre;
+  st->gpu_launches = (int)g_launches;
+}
+
+void copy_out(double* dst, const double* src, size_t n, bool on_device, cudaStream_t s) {
+  if (!dst) return;
+  TD_CUDA(cudaMemcpyAsync(dst, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+}  // namespace
+
+// ===========================================================================
+
+tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, double* resid,
+                     tddft_stats* st) {
+  auto t0 = Clock::now();
+  g_launches = 0;
+  const Plan p = make_plan(c, o);
+  const int ov = c.ov;
+  cudaStream_t s = c.s;
+  Counters cnt;
+  const OpDims dims = c.dims();
+  const FactorSet Fx = c.exact(o.precision);
+  const FactorSet Fr = c.ris(o.precision);
+  TdaOp A = [&](const double* Xi, int m, double* out) {
+    apply_operator(dims, Fx, Xi, m, OpMode::TDA, out, nullptr, p.tc, s);
+  };
+  TdaOp T = [&](const double* Xi, int m, double* out) {
+    apply_operator(dims, Fr, Xi, m, OpMode::TDA, out, nullptr, false, s);
+  };
+  TdaPre diag = [&](const double* R, const double* sh, const std::vector<double>&, int nu, double* out) {
+    precond_tda(R, sh, c.delta.as<double>(), nu, ov, out, s);
+  };
+  TdaPre rid = [&](const double* R, const double* sh, const std::vector<double>& shh, int nu, double* out) {
+    inner_tda(ov, T, c.delta.as<double>(), R, sh, shh, nu, p.inner_tol, p.inner_max_iter,
+              p.nref_inner, cnt, out, s);
+  };
+  // initial guess (Sec. 2.1: low-lying eigenvectors of T)
+  DevBuf guess;
+  int ng = p.k0;
+  if (p.precond == TDDFT_PRECOND_RID) {
+    const int kg = std::min(p.k0 + 8, ov);
+    DevBuf unit((size_t)kg * ov * 8, s);
+    TD_REQUIRE(kg <= c.n_order, TDDFT_ERR_ARG, "too many initial guesses");
+    unit_rows(unit.as<double>(), kg, ov, c.order.as<int>(), s);
+    TdaOut g = davidson_tda(ov, T, diag, unit.as<double>(), kg, p.k0, p.guess_tol, p.max_iter, p.cap,
+                            p.rounds, cnt, false, s);
+    guess = std::move(g.X);
+  } else {
+    TD_REQUIRE(p.k0 <= c.n_order, TDDFT_ERR_ARG, "too many initial guesses");
+    guess = DevBuf((size_t)p.k0 * ov * 8, s);
+    unit_rows(guess.as<double>(), p.k0, ov, c.order.as<int>(), s);
+  }
+  TdaOut r = davidson_tda(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, guess.as<double>(), ng,
+                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s);
+  double cert = -1.0;
+  if (p.mixed) {
+    // re-check the converged residuals with the FP64 (else FP32 SIMT) operator
+    const FactorSet Fc = (c.precisions & 1) ? c.exact(TDDFT_PLAIN) : c.exact(TDDFT_MIXED);
+    DevBuf AX((size_t)p.k * ov * 8, s), R((size_t)p.k * ov * 8, s), rn(p.k * 8, s), om(p.k * 8, s);
+    apply_operator(dims, Fc, r.X.as<double>(), p.k, OpMode::TDA, AX.as<double>(), nullptr, false, s);
+    h2d(om.as<double>(), r.omega, s);
+    resid_tda(r.X.as<double>(), AX.as<double>(), om.as<double>(), p.k, ov, R.as<double>(), s);
+    row_sumsq(R.as<double>(), ov, p.k, ov, rn.as<double>(), s);
+    for (double v : sqrt_all(d2h(rn.as<double>(), p.k, s))) cert = std::max(cert, v);
+  }
+  const bool dev = o.outputs_on_device != 0;
+  if (omega) {
+    if (dev) { DevBuf t(p.k * 8, s); h2d(t.as<double>(), r.omega, s); copy_out(omega, t.as<double>(), p.k, true, s); TD_CUDA(cudaStreamSynchronize(s)); }
+    else std::copy(r.omega.begin(), r.omega.end(), omega);
+  }
+  if (resid) {
+    if (dev) { DevBuf t(p.k * 8, s); h2d(t.as<double>(), r.resid, s); copy_out(resid, t.as<double>(), p.k, true, s); TD_CUDA(cudaStreamSynchronize(s)); }
+    else std::copy(r.resid.begin(), r.resid.end(), resid);
+  }
+  copy_out(X, r.X.as<double>(), (size_t)p.k * ov, dev, s);
+  TD_CUDA(cudaStreamSynchronize(s));
+  fill_stats(st, r.n_iter, cnt, r.converged, r.resid, cert, t0);
+  return r.converged ? TDDFT_OK : TDDFT_ERR_NOCONV;
+}
+
+namespace {
+PairOp make_pair_op(const OpDims& dims, const FactorSet& F, bool tc, cudaStream_t s) {
+  return [dims, F, tc, s](const double* Xi, int m, double* P, double* M) {
+    apply_operator(dims, F, Xi, m, OpMode::PAIRED, P, M, tc, s);
+  };
+}
+}  // namespace
+
+tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, double* Y,
+                     double* resid, tddft_stats* st) {
+  auto t0 = Clock::now();
+  g_launches = 0;
+  const Plan p = make_plan(c, o);
+  const int ov = c.ov;
+  cudaStream_t s = c.s;
+  Counters cnt;
+  const OpDims dims = c.dims();
+  PairOp A = make_pair_op(dims, c.exact(o.precision), p.tc, s);
+  PairOp T = make_pair_op(dims, c.ris(o.precision), false, s);
+  const double* dl = c.delta.as<double>();
+  PairPre diag = [&](const double* gp, const double* gm, const double* sh, const std::vector<double>&,
+                     int nu, double* u, double* w) { precond_paired(gp, gm, sh, dl, nu, ov, u, w, s); };
+  PairPre rid = [&](const double* gp, const double* gm, const double* sh,
+                    const std::vector<double>& shh, int nu, double* u, double* w) {
+    DevBuf init((size_t)2 * nu * ov * 8, s);
+    precond_paired(gp, gm, sh, dl, nu, ov, init.as<double>(), init.as<double>() + (size_t)nu * ov, s);
+    paired_linear(ov, T, diag, gp, gm, shh, nu, init.as<double>(), 2 * nu, p.inner_tol,
+                  p.inner_max_iter, kSmallMax, p.nref_inner, false, cnt, u, w, s);
+  };
+  DevBuf guess;
+  int ng = p.k0;
+  if (p.precond == TDDFT_PRECOND_RID) {
+    const int kg = std::min(p.k0 + 8, ov);
+    TD_REQUIRE(kg <= c.n_order, TDDFT_ERR_ARG, "too many initial guesses");
+    DevBuf unit((size_t)kg * ov * 8, s);
+    unit_rows(unit.as<double>(), kg, ov, c.order.as<int>(), s);
+    RpaOut g = davidson_rpa(ov, T, diag, unit.as<double>(), kg, p.k0, p.guess_tol, p.max_iter, p.cap,
+                            p.rounds, cnt, false, s);
+    guess = DevBuf((size_t)2 * p.k0 * ov * 8, s);
+    TD_CUDA(cudaMemcpyAsync(guess.p, g.U.p, (size_t)p.k0 * ov * 8, cudaMemcpyDeviceToDevice, s));
+    TD_CUDA(cudaMemcpyAsync(guess.as<double>() + (size_t)p.k0 * ov, g.W.p, (size_t)p.k0 * ov * 8,
+                            cudaMemcpyDeviceToDevice, s));
+    ng = 2 * p.k0;
+  } else {
+    TD_REQUIRE(p.k0 <= c.n_order, TDDFT_ERR_ARG, "too many initial guesses");
+    guess = DevBuf((size_t)p.k0 * ov * 8, s);
+    unit_rows(guess.as<double>(), p.k0, ov, c.order.as<int>(), s);
+  }
+  RpaOut r = davidson_rpa(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, guess.as<double>(), ng,
+                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s);
+  double cert = -1.0;
+  if (p.mixed) {
+    const FactorSet Fc = (c.precisions & 1) ? c.exact(TDDFT_PLAIN) : c.exact(TDDFT_MIXED);
+    const int k = p.k;
+    DevBuf PU((size_t)k * ov * 8, s), MU((size_t)k * ov * 8, s), PW((size_t)k * ov * 8, s),
+        MW((size_t)k * ov * 8, s), Rp((size_t)k * ov * 8, s), Rm((size_t)k * ov * 8, s);
+    DevBuf a1(k * 8, s), a2(k * 8, s), om(k * 8, s);
+    apply_operator(dims, Fc, r.U.as<double>(), k, OpMode::PAIRED, PU.as<double>(), MU.as<double>(), false, s);
+    apply_operator(dims, Fc, r.W.as<double>(), k, OpMode::PAIRED, PW.as<double>(), MW.as<double>(), false, s);
+    h2d(om.as<double>(), r.omega, s);
+    resid_paired(r.U.as<double>(), r.W.as<double>(), PU.as<double>(), MW.as<double>(), om.as<double>(),
+                 nullptr, nullptr, k, ov, Rp.as<double>(), Rm.as<double>(), s);
+    row_sumsq(Rp.as<double>(), ov, k, ov, a1.as<double>(), s);
+    row_sumsq(Rm.as<double>(), ov, k, ov, a2.as<double>(), s);
+    auto h1 = d2h(a1.as<double>(), k, s), h2 = d2h(a2.as<double>(), k, s);
+    for (int j = 0; j < k; ++j) cert = std::max(cert, std::sqrt(h1[j] + h2[j]));
+  }
+  const bool dev = o.outputs_on_device != 0;
+  if (omega) {
+    if (dev) { DevBuf t(p.k * 8, s); h2d(t.as<double>(), r.omega, s); copy_out(omega, t.as<double>(), p.k, true, s); TD_CUDA(cudaStreamSynchronize(s)); }
+    else std::copy(r.omega.begin(), r.omega.end(), omega);
+  }
+  if (resid) {
+    if (dev) { DevBuf t(p.k * 8, s); h2d(t.as<double>(), r.resid, s); copy_out(resid, t.as<double>(), p.k, true, s); TD_CUDA(cudaStreamSynchronize(s)); }
+    else std::copy(r.resid.begin(), r.resid.end(), resid);
+  }
+  if (X || Y) {
+    DevBuf Xd((size_t)p.k * ov * 8, s), Yd((size_t)p.k * ov * 8, s);
+    half_sum_diff(r.U.as<double>(), r.W.as<double>(), (long long)p.k * ov, Xd.as<double>(), Yd.as<double>(), s);
+    copy_out(X, Xd.as<double>(), (size_t)p.k * ov, dev, s);
+    copy_out(Y, Yd.as<double>(), (size_t)p.k * ov, dev, s);
+    TD_CUDA(cudaStreamSynchronize(s));
+  }
+  TD_CUDA(cudaStreamSynchronize(s));
+  fill_stats(st, r.n_iter, cnt, r.converged, r.resid, cert, t0);
+  return r.converged ? TDDFT_OK : TDDFT_ERR_NOCONV;
+}
+
+tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
+                       const double* freqs, int n_freq, double* alpha, tddft_stats* st) {
+  auto t0 = Clock::now();
+  g_launches = 0;
+  tddft_opts oo = o;
+  if (oo.n_states < 1) oo.n_states = 1;
+  const Plan p = make_plan(c, oo);
+  TD_REQUIRE(n_dip >= 1 && n_freq >= 1 && mu && freqs, TDDFT_ERR_ARG, "polar: need dipoles and frequencies");
+  const int nr = n_dip * n_freq;
+  TD_REQUIRE(2 * nr <= 112, TDDFT_ERR_ARG, "polar: too many right-hand sides");
+  const int ov = c.ov;
+  cudaStream_t s = c.s;
+  Counters cnt;
+  const OpDims dims = c.dims();
+  PairOp A = make_pair_op(dims, c.exact(o.precision), p.tc, s);
+  PairOp T = make_pair_op(dims, c.ris(o.precision), false, s);
+  const double* dl = c.delta.as<double>();
+  const bool dev = o.outputs_on_device != 0;
+  // right-hand sides 2 mu for every (omega_f, mu_u): row f*n_dip + u
+  DevBuf mud((size_t)n_dip * ov * 8, s), b((size_t)nr * ov * 8, s);
+  TD_CUDA(cudaMemcpyAsync(mud.p, mu, (size_t)n_dip * ov * 8, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  std::vector<double> fh(n_freq);
+  if (dev) fh = d2h(freqs, n_freq, s);
+  else fh.assign(freqs, freqs + n_freq);
+  std::vector<double> sh(nr), two(nr, 2.0);
+  DevBuf twod(nr * 8, s), shd(nr * 8, s);
+  for (int f = 0; f < n_freq; ++f)
+    for (int u = 0; u < n_dip; ++u) sh[f * n_dip + u] = fh[f];
+  TD_CUDA(cudaMemsetAsync(b.p, 0, (size_t)nr * ov * 8, s));
+  h2d(twod.as<double>(), two, s);
+  h2d(shd.as<double>(), sh, s);
+  for (int f = 0; f < n_freq; ++f)
+    axpy_rows(b.as<double>() + (size_t)f * n_dip * ov, mud.as<double>(), twod.as<double>(), n_dip, ov, s);
+  PairPre diag = [&](const double* gp, const double* gm, const double* shv, const std::vector<double>&,
+                     int nu, double* u, double* w) { precond_paired(gp, gm, shv, dl, nu, ov, u, w, s); };
+  PairPre rid = [&](const double* gp, const double* gm, const double* shv,
+                    const std::vector<double>& shh, int nu, double* u, double* w) {
+    DevBuf init((size_t)2 * nu * ov * 8, s);
+    precond_paired(gp, gm, shv, dl, nu, ov, init.as<double>(), init.as<double>() + (size_t)nu * ov, s);
+    paired_linear(ov, T, diag, gp, gm, shh, nu, init.as<double>(), 2 * nu, p.inner_tol,
+                  p.inner_max_iter, kSmallMax, p.nref_inner, false, cnt, u, w, s);
+  };
+  // initial directions
+  DevBuf init((size_t)2 * nr * ov * 8, s);
+  double* iu = init.as<double>();
+  double* iw = iu + (size_t)nr * ov;
+  if (p.precond == TDDFT_PRECOND_RID) {
+    DevBuf d0((size_t)2 * nr * ov * 8, s);
+    precond_paired(b.as<double>(), nullptr, shd.as<double>(), dl, nr, ov, d0.as<double>(),
+                   d0.as<double>() + (size_t)nr * ov, s);
+    paired_linear(ov, T, diag, b.as<double>(), nullptr, sh, nr, d0.as<double>(), 2 * nr,
+                  p.guess_tol, p.max_iter, kSmallMax, p.nref_inner, false, cnt, iu, iw, s);
+  } else {
+    precond_paired(b.as<double>(), nullptr, shd.as<double>(), dl, nr, ov, iu, iw, s);
+  }
+  DevBuf U((size_t)nr * ov * 8, s), W((size_t)nr * ov * 8, s);
+  PairedLinOut r = paired_linear(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, b.as<double>(),
+                                 nullptr, sh, nr, iu, 2 * nr, p.tol, p.max_iter, p.cap, p.nref_outer,
+                                 true, cnt, U.as<double>(), W.as<double>(), s);
+  // alpha[f][v][u] = mu_v . U[f*n_dip + u]
+  DevBuf G((size_t)n_dip * nr * 8, s);
+  gram(mud.as<double>(), n_dip, U.as<double>(), nr, ov, G.as<double>(), nr, s);
+  std::vector<double> gh = d2h(G.as<double>(), (size_t)n_dip * nr, s);
+  std::vector<double> al((size_t)n_freq * n_dip * n_dip);
+  for (int f = 0; f < n_freq; ++f)
+    for (int v = 0; v < n_dip; ++v)
+      for (int u = 0; u < n_dip; ++u) al[((size_t)f * n_dip + v) * n_dip + u] = gh[(size_t)v * nr + f * n_dip + u];
+  if (alpha) {
+    if (dev) { DevBuf t(al.size() * 8, s); h2d(t.as<double>(), al, s); copy_out(alpha, t.as<double>(), al.size(), true, s); }
+    else std::copy(al.begin(), al.end(), alpha);
+  }
+  TD_CUDA(cudaStreamSynchronize(s));
+  fill_stats(st, r.n_iter, cnt, r.converged, r.resid, -1.0, t0);
+  return r.converged ? TDDFT_OK : TDDFT_ERR_NOCONV;
+}
+
+}  // namespace tddft

@@ -1,0 +1,343 @@
+// Streaming kernels over singles vectors and factor staging.  All are bound by
+// HBM bandwidth (or, for FP64 arithmetic, by the FP64 pipe): grid-stride loops,
+// coalesced along the contiguous index, grids sized to a multiple of the SM count.
+#include "vecops.cuh"
+
+namespace tddft {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(long long n) {
+  long long g = (n + kThreads - 1) / kThreads;
+  const long long cap = 152LL * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+__device__ __forceinline__ double guard(double d) {
+  if (fabs(d) < 1e-8) return d < 0 ? -1e-8 : 1e-8;
+  return d;
+}
+
+template <typename T> __device__ __forceinline__ double ldd(const T* p, long long i);
+template <> __device__ __forceinline__ double ldd<double>(const double* p, long long i) { return p[i]; }
+template <> __device__ __forceinline__ double ldd<float>(const float* p, long long i) { return (double)p[i]; }
+template <> __device__ __forceinline__ double ldd<__nv_bfloat16>(const __nv_bfloat16* p, long long i) {
+  return (double)__bfloat162float(p[i]);
+}
+
+__global__ void k_delta(const double* eo, const double* ev, int no, int nv, double* d) {
+  long long n = (long long)no * nv;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t / nv), a = (int)(t % nv);
+    d[t] = ev[a] - eo[i];
+  }
+}
+
+__global__ void k_unit_rows(double* out, int k, int n, const int* idx) {
+  long long tot = (long long)k * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(t / n), e = (int)(t % n);
+    out[t] = (e == idx[r]) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_row_sumsq(const double* X, long long ldx, int n, double* out) {
+  __shared__ double red[32];
+  const double* x = X + blockIdx.x * ldx;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) acc += x[e] * x[e];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+  }
+}
+
+__global__ void k_resid_tda(const double* X, const double* AX, const double* om, int k, int n, double* R) {
+  long long tot = (long long)k * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(t / n);
+    R[t] = AX[t] - om[r] * X[t];
+  }
+}
+
+__global__ void k_resid_paired(const double* U, const double* W, const double* PU, const double* MW,
+                               const double* sh, const double* b, const double* bm, int k, int n,
+                               double* Rp, double* Rm) {
+  long long tot = (long long)k * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(t / n);
+    double s = sh[r];
+    Rp[t] = PU[t] - s * W[t] - (b ? b[t] : 0.0);
+    Rm[t] = MW[t] - s * U[t] - (bm ? bm[t] : 0.0);
+  }
+}
+
+__global__ void k_precond_tda(const double* R, const double* om, const double* d, int k, int n, double* out) {
+  long long tot = (long long)k * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(t / n), e = (int)(t % n);
+    out[t] = R[t] / guard(d[e] - om[r]);
+  }
+}
+
+__global__ void k_precond_paired(const double* gp, const double* gm, const double* sh, const double* d,
+                                 int k, int n, double* ou, double* ow) {
+  long long tot = (long long)k * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(t / n), e = (int)(t % n);
+    double g2 = gm ? gm[t] : 0.0;
+    double rx = 0.5 * (gp[t] + g2), ry = 0.5 * (gp[t] - g2);
+    double x = rx / guard(d[e] - sh[r]);
+    double y = ry / guard(d[e] + sh[r]);
+    ou[t] = x + y;
+    ow[t] = x - y;
+  }
+}
+
+__global__ void k_gather_rows(const double* src, const int* idx, int k, int n, double* dst) {
+  long long tot = (long long)k * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(t / n), e = (int)(t % n);
+    dst[t] = src[(long long)idx[r] * n + e];
+  }
+}
+
+__global__ void k_sym_fill(double* a, int ld, int n_old, int n_new) {
+  int N = n_old + n_new;
+  long long tot = (long long)N * n_new;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(t / n_new), j = (int)(t % n_new);
+    int c = n_old + j;
+    if (r < n_old) {
+      a[(long long)c * ld + r] = a[(long long)r * ld + c];
+    } else if (r < c) {
+      double v = 0.5 * (a[(long long)r * ld + c] + a[(long long)c * ld + r]);
+      a[(long long)r * ld + c] = v;
+      a[(long long)c * ld + r] = v;
+    }
+  }
+}
+
+__global__ void k_scale_rows(double* X, const double* sc, int k, int n) {
+  long long tot = (long long)k * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
+    X[t] *= sc[t / n];
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(const TI* in, TO* out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = (TO)ldd<TI>(in, t);
+}
+
+template <typename TI>
+__global__ void k_to_bf16(const TI* in, __nv_bfloat16* out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = __double2bfloat16(ldd<TI>(in, t));
+}
+
+template <typename TI>
+__global__ void k_split(const TI* in, __nv_bfloat16* hi, __nv_bfloat16* lo, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double v = ldd<TI>(in, t);
+    __nv_bfloat16 h = __double2bfloat16(v);
+    hi[t] = h;
+    lo[t] = __double2bfloat16(v - (double)__bfloat162float(h));
+  }
+}
+
+template <typename T>
+__global__ void k_mask(T* L, int rows, int n1, int n2, const unsigned char* m1, const unsigned char* m2) {
+  long long tot = (long long)rows * n1 * n2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    long long pq = t % ((long long)n1 * n2);
+    int p = (int)(pq / n2), q = (int)(pq % n2);
+    if (!(m1[p] && m2[q])) L[t] = (T)0.0f;
+  }
+}
+
+template <typename TW>
+__global__ void k_combine(const double* X, const double* d, const TW* J, const TW* K1, const TW* K2,
+                          double cj, double c1, double c2, long long m, int n, double* out) {
+  long long tot = m * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    double v = d[t % n] * X[t];
+    if (J) v += cj * ldd<TW>(J, t);
+    if (K1) v += c1 * ldd<TW>(K1, t);
+    if (K2) v += c2 * ldd<TW>(K2, t);
+    out[t] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_reduce_parts(T* buf, int parts, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double acc = (double)buf[t];
+    for (int p = 1; p < parts; ++p) acc += (double)buf[p * n + t];
+    buf[t] = (T)acc;
+  }
+}
+
+template <typename T>
+__global__ void k_check_finite(const T* X, long long n, int* flag) {
+  int bad = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double v = ldd<T>(X, t);
+    if (!isfinite(v)) bad = 1;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+#define TD_GRID(n) grid_for(n), kThreads, 0, s
+
+}  // namespace
+
+void delta_kernel(const double* eo, const double* ev, int no, int nv, double* d, cudaStream_t s) {
+  k_delta<<<TD_GRID((long long)no * nv)>>>(eo, ev, no, nv, d);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void unit_rows(double* out, int k, int n, const int* idx, cudaStream_t s) {
+  k_unit_rows<<<TD_GRID((long long)k * n)>>>(out, k, n, idx);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void row_sumsq(const double* X, long long ldx, int k, int n, double* out, cudaStream_t s) {
+  if (k <= 0) return;
+  k_row_sumsq<<<k, 1024, 0, s>>>(X, ldx, n, out);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void resid_tda(const double* X, const double* AX, const double* om, int k, int n, double* R, cudaStream_t s) {
+  k_resid_tda<<<TD_GRID((long long)k * n)>>>(X, AX, om, k, n, R);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void resid_paired(const double* U, const double* W, const double* PU, const double* MW, const double* sh,
+                  const double* b, const double* bm, int k, int n, double* Rp, double* Rm, cudaStream_t s) {
+  k_resid_paired<<<TD_GRID((long long)k * n)>>>(U, W, PU, MW, sh, b, bm, k, n, Rp, Rm);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void precond_tda(const double* R, const double* om, const double* d, int k, int n, double* out, cudaStream_t s) {
+  k_precond_tda<<<TD_GRID((long long)k * n)>>>(R, om, d, k, n, out);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void precond_paired(const double* gp, const double* gm, const double* sh, const double* d, int k, int n,
+                    double* ou, double* ow, cudaStream_t s) {
+  k_precond_paired<<<TD_GRID((long long)k * n)>>>(gp, gm, sh, d, k, n, ou, ow);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void gather_rows(const double* src, const int* idx, int k, int n, double* dst, cudaStream_t s) {
+  if (k <= 0) return;
+  k_gather_rows<<<TD_GRID((long long)k * n)>>>(src, idx, k, n, dst);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void sym_fill(double* a, int ld, int n_old, int n_new, cudaStream_t s) {
+  if (n_new <= 0) return;
+  k_sym_fill<<<TD_GRID((long long)(n_old + n_new) * n_new)>>>(a, ld, n_old, n_new);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void scale_rows(double* X, const double* sc, int k, int n, cudaStream_t s) {
+  k_scale_rows<<<TD_GRID((long long)k * n)>>>(X, sc, k, n);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void cast_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s) {
+  k_convert<double, float><<<TD_GRID(n)>>>(in, out, n);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void cast_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s) {
+  k_convert<float, double><<<TD_GRID(n)>>>(in, out, n);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void convert(const void* in, DType tin, void* out, DType tout, long long n, cudaStream_t s) {
+  if (tout == DType::BF16) { cast_to_bf16(in, tin, (__nv_bfloat16*)out, n, s); return; }
+  if (tin == DType::F64 && tout == DType::F64) TD_CUDA(cudaMemcpyAsync(out, in, n * 8, cudaMemcpyDeviceToDevice, s));
+  else if (tin == DType::F32 && tout == DType::F32) TD_CUDA(cudaMemcpyAsync(out, in, n * 4, cudaMemcpyDeviceToDevice, s));
+  else if (tin == DType::F64 && tout == DType::F32) { k_convert<double, float><<<TD_GRID(n)>>>((const double*)in, (float*)out, n); count_launch(); }
+  else if (tin == DType::F32 && tout == DType::F64) { k_convert<float, double><<<TD_GRID(n)>>>((const float*)in, (double*)out, n); count_launch(); }
+  else throw Error(TDDFT_ERR_ARG, "convert: unsupported types");
+  TD_LAUNCH_CHECK();
+}
+void cast_to_bf16(const void* in, DType tin, __nv_bfloat16* out, long long n, cudaStream_t s) {
+  if (tin == DType::F64) k_to_bf16<double><<<TD_GRID(n)>>>((const double*)in, out, n);
+  else k_to_bf16<float><<<TD_GRID(n)>>>((const float*)in, out, n);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void split_bf16(const void* in, DType tin, __nv_bfloat16* hi, __nv_bfloat16* lo, long long n, cudaStream_t s) {
+  if (tin == DType::F64) k_split<double><<<TD_GRID(n)>>>((const double*)in, hi, lo, n);
+  else k_split<float><<<TD_GRID(n)>>>((const float*)in, hi, lo, n);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void mask_block(void* L, DType t, int rows, int n1, int n2, const unsigned char* m1, const unsigned char* m2,
+                cudaStream_t s) {
+  long long tot = (long long)rows * n1 * n2;
+  if (tot == 0) return;
+  if (t == DType::F64) k_mask<double><<<TD_GRID(tot)>>>((double*)L, rows, n1, n2, m1, m2);
+  else if (t == DType::F32) k_mask<float><<<TD_GRID(tot)>>>((float*)L, rows, n1, n2, m1, m2);
+  else k_mask<__nv_bfloat16><<<TD_GRID(tot)>>>((__nv_bfloat16*)L, rows, n1, n2, m1, m2);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void combine(const double* X, const double* d, const void* J, const void* K1, const void* K2, DType tw,
+             double cj, double c1, double c2, long long m, int n, double* out, cudaStream_t s) {
+  if (tw == DType::F64)
+    k_combine<double><<<TD_GRID(m * n)>>>(X, d, (const double*)J, (const double*)K1, (const double*)K2, cj, c1, c2, m, n, out);
+  else
+    k_combine<float><<<TD_GRID(m * n)>>>(X, d, (const float*)J, (const float*)K1, (const float*)K2, cj, c1, c2, m, n, out);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void reduce_parts(void* buf, DType t, int parts, long long n, cudaStream_t s) {
+  if (parts <= 1) return;
+  if (t == DType::F64) k_reduce_parts<double><<<TD_GRID(n)>>>((double*)buf, parts, n);
+  else k_reduce_parts<float><<<TD_GRID(n)>>>((float*)buf, parts, n);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void check_finite(const void* X, DType t, long long n, int* flag, cudaStream_t s) {
+  if (n <= 0) return;
+  if (t == DType::F64) k_check_finite<double><<<TD_GRID(n)>>>((const double*)X, n, flag);
+  else if (t == DType::F32) k_check_finite<float><<<TD_GRID(n)>>>((const float*)X, n, flag);
+  else k_check_finite<__nv_bfloat16><<<TD_GRID(n)>>>((const __nv_bfloat16*)X, n, flag);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+
+
+namespace {
+__global__ void k_axpy_rows(double* out, const double* X, const double* sc, int k, int n) {
+  long long tot = (long long)k * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
+    out[t] += sc[t / n] * X[t];
+}
+__global__ void k_half_sum_diff(const double* U, const double* W, long long n, double* X, double* Y) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double u = U[t], w = W[t];
+    if (X) X[t] = 0.5 * (u + w);
+    if (Y) Y[t] = 0.5 * (u - w);
+  }
+}
+__global__ void k_resid_shift(const double* Y, const double* X, const double* sh, const double* B, int k, int n, double* out) {
+  long long tot = (long long)k * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
+    out[t] = Y[t] - sh[t / n] * X[t] - (B ? B[t] : 0.0);
+}
+}  // namespace
+
+void axpy_rows(double* out, const double* X, const double* sc, int k, int n, cudaStream_t s) {
+  if (k <= 0) return;
+  k_axpy_rows<<<TD_GRID((long long)k * n)>>>(out, X, sc, k, n);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void half_sum_diff(const double* U, const double* W, long long n, double* X, double* Y, cudaStream_t s) {
+  if (n <= 0) return;
+  k_half_sum_diff<<<TD_GRID(n)>>>(U, W, n, X, Y);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void resid_shift(const double* Y, const double* X, const double* sh, const double* B, int k, int n, double* out, cudaStream_t s) {
+  if (k <= 0) return;
+  k_resid_shift<<<TD_GRID((long long)k * n)>>>(Y, X, sh, B, k, n, out);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+
+}  // namespace tddft

@@ -1,0 +1,179 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (see the design notes for the derivation):
+  * operator products, PLAIN (FP64): 1e-11 relative to max |out| -- rounding order only;
+  * operator products, MIXED exact (FP32 factors, FP32 accumulation): 2e-5 relative;
+  * ris products, MIXED (BF16 factors): 2e-2 relative (preconditioner only);
+  * excitation energies: 1e-6 Ha (PLAIN), 1e-5 Ha (MIXED);
+  * polarizabilities: 1e-6 relative (PLAIN), 1e-5 relative (MIXED).
+"""
+import numpy as np
+import pytest
+
+from oracle import davidson as DV
+from oracle import dense as D
+from oracle import operators as O
+from synth.generator import dipoles, make_config, make_problem
+
+pytestmark = pytest.mark.gpu
+
+OMEGAS = [0.0, 0.05, 0.1]
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2404_17133_gb300 import api as a
+    return a
+
+
+def _dense(p):
+    A, B = O.dense_A_B(p.eps_occ, p.eps_vir, O.eri_from_factors(p.extra["L_full"]), p.a_x,
+                       p.coulomb_factor)
+    return A, B
+
+
+PROBLEMS = {
+    "tda_small": lambda: make_config("tda_small"),
+    "ragged": lambda: make_problem(3, 7, 5, 9, seeds=(30, 31, 32)),
+    "odd": lambda: make_problem(7, 33, 37, 27, seeds=(40, 41, 42)),
+}
+
+
+@pytest.fixture(scope="module", params=list(PROBLEMS))
+def case(request, api):
+    p = PROBLEMS[request.param]()
+    s = api.Solver.from_problem(p)
+    yield request.param, p, s
+    s.close()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def test_operator_products(case, api):
+    name, p, s = case
+    X = np.random.default_rng(7).standard_normal((5, p.n_ov))
+    op, T = O.exact_operator(p), O.ris_operator(p)
+    ref_tda = op.tda(X)
+    ref_p, ref_m = op.apb_amb(X)
+    rt = T.tda(X)
+    rtp, rtm = T.apb_amb(X)
+    assert _rel(s.apply(0, X), ref_tda) < 1e-11
+    gp, gm = s.apply(1, X)
+    assert _rel(gp, ref_p) < 1e-11 and _rel(gm, ref_m) < 1e-11
+    assert _rel(s.apply(2, X), rt) < 1e-11
+    gp, gm = s.apply(3, X)
+    assert _rel(gp, rtp) < 1e-11 and _rel(gm, rtm) < 1e-11
+    # mixed: FP32 exact, BF16 ris
+    assert _rel(s.apply(0, X, precision=api.MIXED), ref_tda) < 2e-5
+    gp, gm = s.apply(1, X, precision=api.MIXED)
+    assert _rel(gp, ref_p) < 2e-5 and _rel(gm, ref_m) < 2e-5
+    assert _rel(s.apply(2, X, precision=api.MIXED), rt) < 2e-2
+
+
+@pytest.mark.parametrize("pc", ["diag", "rid"])
+@pytest.mark.parametrize("prec", ["plain", "mixed"])
+def test_tda(case, api, pc, prec):
+    name, p, s = case
+    A, _ = _dense(p)
+    k = min(5, p.n_ov - 1)
+    ref_w, ref_X = D.tda(A, k)
+    o = api.default_opts(n_states=k, precond=api.RID if pc == "rid" else api.DIAG,
+                         precision=api.PLAIN if prec == "plain" else api.MIXED)
+    r = s.solve_tda(o)
+    tol = 1e-6 if prec == "plain" else 1e-5
+    assert r["status"] == api.OK
+    assert np.max(np.abs(r["omega"] - ref_w)) < tol
+    assert np.max(r["resid"]) < 1e-5
+    ov = np.abs(np.sum(r["X"] * ref_X, axis=1))
+    assert np.all(ov > 1 - 1e-6)
+
+
+@pytest.mark.parametrize("pc", ["diag", "rid"])
+@pytest.mark.parametrize("prec", ["plain", "mixed"])
+def test_rpa(case, api, pc, prec):
+    name, p, s = case
+    A, B = _dense(p)
+    k = min(5, p.n_ov - 1)
+    ref_w, ref_X, ref_Y = D.casida(A, B, k)
+    o = api.default_opts(n_states=k, precond=api.RID if pc == "rid" else api.DIAG,
+                         precision=api.PLAIN if prec == "plain" else api.MIXED)
+    r = s.solve_rpa(o)
+    tol = 1e-6 if prec == "plain" else 1e-5
+    assert r["status"] == api.OK
+    assert np.max(np.abs(r["omega"] - ref_w)) < tol
+    X, Y = r["X"], r["Y"]
+    assert np.allclose(np.sum(X * X, 1) - np.sum(Y * Y, 1), 1.0, atol=1e-6)
+    ovl = np.abs(np.sum(X * ref_X, 1) + np.sum(Y * ref_Y, 1))
+    assert np.all(ovl > 1 - 1e-5)
+
+
+@pytest.mark.parametrize("pc", ["diag", "rid"])
+@pytest.mark.parametrize("prec", ["plain", "mixed"])
+def test_polar(case, api, pc, prec):
+    name, p, s = case
+    A, B = _dense(p)
+    mu = dipoles(3, 3, p.n_ov)
+    ref = D.polar(A, B, mu, OMEGAS)
+    o = api.default_opts(precond=api.RID if pc == "rid" else api.DIAG,
+                         precision=api.PLAIN if prec == "plain" else api.MIXED)
+    r = s.solve_polar(o, mu, OMEGAS)
+    tol = 1e-6 if prec == "plain" else 1e-5
+    assert r["status"] == api.OK
+    assert _rel(r["alpha"], ref) < tol
+
+
+def test_iterations_match_oracle_and_rid_wins(api):
+    p = make_config("tda_small")
+    s = api.Solver.from_problem(p)
+    op, T = O.exact_operator(p), O.ris_operator(p)
+    try:
+        for pc, code in (("diag", api.DIAG), ("rid", api.RID)):
+            ref = DV.solve_tda(p, op, T, 5, precond=pc)
+            r = s.solve_tda(api.default_opts(n_states=5, precond=code))
+            assert abs(r["stats"]["n_iter"] - ref.n_iter) <= 1, (pc, r["stats"]["n_iter"], ref.n_iter)
+        it = {pc: s.solve_tda(api.default_opts(n_states=5, precond=c))["stats"]["n_iter"]
+              for pc, c in (("diag", api.DIAG), ("rid", api.RID))}
+        assert it["rid"] <= it["diag"]
+        it = {pc: s.solve_rpa(api.default_opts(n_states=5, precond=c))["stats"]["n_iter"]
+              for pc, c in (("diag", api.DIAG), ("rid", api.RID))}
+        assert it["rid"] <= it["diag"]
+    finally:
+        s.close()
+
+
+def test_zero_factors_give_delta(api):
+    p = make_problem(4, 9, 3, 9, seeds=(50, 51, 52), amplitude=0.0, ris_noise=0.0)
+    d = np.sort(O.delta(p.eps_occ, p.eps_vir))
+    s = api.Solver.from_problem(p)
+    try:
+        for pc in (api.DIAG, api.RID):
+            r = s.solve_tda(api.default_opts(n_states=4, precond=pc))
+            assert np.allclose(r["omega"], d[:4], atol=1e-10)
+            r = s.solve_rpa(api.default_opts(n_states=4, precond=pc))
+            assert np.allclose(r["omega"], d[:4], atol=1e-10)
+    finally:
+        s.close()
+
+
+def test_single_state_and_T_equal_A(api):
+    p = make_config("tda_small")
+    # ris factors = exact factors, every row used for exchange, no window: T = A
+    L = p.extra["L_full"]
+    no = p.n_occ
+    s = api.Solver(p.n_occ, p.n_vir, p.eps_occ, p.eps_vir, p.L_oo, p.L_ov, p.L_vv,
+                   p.L_oo, p.L_ov, p.L_vv, np.arange(p.n_aux, dtype=np.int32), a_x=p.a_x,
+                   coulomb_factor=p.coulomb_factor, t_cut_ha=1e9)
+    try:
+        r = s.solve_tda(api.default_opts(n_states=1, precond=api.RID, guess_tol=1e-9))
+        A, _ = _dense(p)
+        assert r["stats"]["n_iter"] == 1
+        assert abs(r["omega"][0] - np.linalg.eigvalsh(A)[0]) < 1e-8
+    finally:
+        s.close()
