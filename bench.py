@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark: excitation states converged per second on one GB300 (or N replicas).
+
+One step is the whole hot path on the medium response workload (n_occ=60,
+n_vir=400, n_aux=2000, ris n_aux=360): a Casida solve for the 10 lowest states
+and the polarizability alpha(omega) for 3 dipoles at omega = 0, 0.05, 0.1 Ha,
+both with the rid preconditioner to a residual of 1e-5, MIXED precision (FP32
+exact products, or BF16 hi+lo on the tensor cores with --tensor-cores; BF16 ris
+inner solves; FP64 subspace algebra; FP32 re-certification of the residuals).
+
+value: states converged per second (10 per step x steps x ranks / max time),
+device-timed with CUDA events on the solver's stream, factors resident in HBM.
+e2e:   the same through the C ABI with host (pinned) inputs: tddft_create
+       (host->device copy and conversion of every factor) + the two solves
+       with host outputs + tddft_destroy, every step.
+Inputs (the FP32/BF16 factors, 2.8 GB) are larger than L2, so no L2 flush is
+added between steps.
+
+Multi-GPU: one independent replica per GPU (the path does not shard on one
+box), launched under torch.distributed.run; rank 0 prints one JSON line.
+
+--impl reference times the CPU oracle (FP64, NumPy) on a bounded sample of the
+same workload and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "rpa_polar_medium"
+N_STATES = 10
+METRIC = "states converged/s at ||r||<=1e-5 (Casida, rid, mixed) + alpha(omega) per step"
+UNIT = "states/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tensor-cores", type=int, default=-1, help="1/0; default: on when available")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precond", default="rid", choices=["rid", "diag"])
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def golden():
+    with open(os.path.join(ROOT, "tests", "golden", WORKLOAD + ".json")) as f:
+        return json.load(f)
+
+
+def oracle_sample(seconds_budget=20.0):
+    """Time the oracle's exact and ris pair products on the workload's inputs and
+    scale them by the oracle's own product counts for one step (RPA + polar).
+    Returns (step_seconds, description, cores)."""
+    import numpy as np
+    from oracle import operators as O
+    from synth.generator import make_config
+
+    p = make_config(WORKLOAD)
+    op, T = O.exact_operator(p), O.ris_operator(p)
+    g = golden()
+    X = np.random.default_rng(0).standard_normal((2, p.n_ov))
+    t0 = time.perf_counter()
+    n_ex = 0
+    while True:
+        op.apb_amb(X)
+        n_ex += 2
+        if time.perf_counter() - t0 > 0.7 * seconds_budget or n_ex >= 32:
+            break
+    t_ex = (time.perf_counter() - t0) / n_ex
+    Xr = np.random.default_rng(1).standard_normal((16, p.n_ov))
+    t0 = time.perf_counter()
+    T.apb_amb(Xr)
+    t_ris = (time.perf_counter() - t0) / 16
+    n_mv = g["rpa"]["n_mv"] + g["polar"]["n_mv"]
+    n_ris = g["rpa"]["n_ris_mv"] + g["polar"]["n_ris_mv"]
+    step = t_ex * n_mv + t_ris * n_ris
+    desc = ("%d oracle (A+B, A-B) products + 16 ris pair products at the full workload size, "
+            "scaled by the oracle's own counts for one step (%d exact, %d ris vectors)" % (n_ex, n_mv, n_ris))
+    return step, desc, os.cpu_count()
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    steps = []
+    desc = cores = None
+    for _ in range(args.warmup):
+        pass  # the oracle has nothing to warm up
+    for _ in range(args.steps):
+        s, desc, cores = oracle_sample(seconds_budget=max(5.0, 60.0 / max(args.steps, 1)))
+        steps.append(s)
+    step = statistics.mean(steps)
+    value = N_STATES / step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (NumPy)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def our_arm(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2404_17133_gb300 import api
+    from synth.generator import CONFIGS, dipoles, make_config
+
+    cfg = CONFIGS[WORKLOAD]
+    p = make_config(WORKLOAD)
+    mu = dipoles(cfg["mu_seed"], cfg["n_dip"], p.n_ov)
+    omegas = list(cfg["omegas"])
+    tc = args.tensor_cores
+    if tc < 0:
+        tc = 0
+    stream = torch.cuda.current_stream()
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+    kidx = p.ris_K_index
+    host = {"eo": torch.from_numpy(p.eps_occ.copy()), "ev": torch.from_numpy(p.eps_vir.copy()),
+            "oo": f32(p.L_oo), "ov": f32(p.L_ov), "vv": f32(p.L_vv), "roo": f32(p.Lr_oo[kidx]),
+            "rov": f32(p.Lr_ov), "rvv": f32(p.Lr_vv[kidx]), "k": torch.from_numpy(kidx.copy())}
+    dev = {k: v.cuda() for k, v in host.items()}
+    pinned = {k: v.pin_memory() for k, v in host.items()}
+    h2d_bytes = sum(v.numel() * v.element_size() for v in host.values()) + mu.nbytes + 8 * len(omegas)
+    d2h_bytes = 8 * (2 * N_STATES + len(omegas) * cfg["n_dip"] ** 2)
+
+    def make_solver(src, stream_ptr):
+        return api.Solver(p.n_occ, p.n_vir, src["eo"], src["ev"], src["oo"], src["ov"], src["vv"],
+                          src["roo"], src["rov"], src["rvv"], src["k"], a_x=p.a_x,
+                          coulomb_factor=p.coulomb_factor, t_cut_ha=p.t_cut_ha, precisions=2,
+                          dtype=api.F32, stream=stream_ptr)
+
+    pc = api.RID if args.precond == "rid" else api.DIAG
+    o_rpa = api.default_opts(n_states=N_STATES, precond=pc, precision=api.MIXED, tensor_cores=tc)
+    o_pol = api.default_opts(precond=pc, precision=api.MIXED, tensor_cores=tc)
+    solver = make_solver(dev, stream.cuda_stream)
+
+    def step(s):
+        a = s.solve_rpa(o_rpa, want_vectors=False)
+        b = s.solve_polar(o_pol, mu, omegas)
+        return a, b
+
+    for _ in range(max(args.warmup, 0)):
+        step(solver)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    solver.profile(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    launches = 0
+    results = []
+    for i in range(args.steps):
+        a, b = step(solver)
+        ev[i + 1].record(stream)
+        launches += a["stats"]["gpu_launches"] + b["stats"]["gpu_launches"]
+        results.append((a, b))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    prof = solver.profile_read()
+    solver.profile(False)
+    clk = clocks.stop() if clocks else None
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = N_STATES * args.steps * world / (total_ms / 1e3)
+    a, b = results[-1]
+    conv = all(r["status"] == api.OK for pair in results for r in pair)
+
+    # ---- end to end through the C ABI with pinned host inputs and host outputs
+    e2e_ms = []
+    for _ in range(0 if args.no_e2e else max(args.e2e_steps, 1)):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s2 = make_solver(pinned, stream.cuda_stream)
+        step(s2)
+        s2.close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_t = statistics.mean(e2e_ms) if e2e_ms else float("nan")
+    if world > 1:
+        t = torch.tensor([e2e_t], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    if rank != 0:
+        solver.close()
+        return
+    peaks, src = load_peaks()
+    kernel_ms = prof["ms"] / max(prof["launches"], 1)
+    flops_launch = prof["flops"] / max(prof["launches"], 1)
+    achieved = flops_launch / (kernel_ms * 1e-3) / 1e12 if prof["launches"] else 0.0
+    if tc:
+        peak = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_kind": "bf16 sustained, " + src,
+                "note": "algorithmic flops 2*M*N*K; the hi+lo split issues 3 BF16 products per flop"}
+    else:
+        sm = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s",
+                "peak_kind": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % sm}
+    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak if peak else None,
+                 "traffic": None, "kernel": "exchange K1 contraction sum_(P,a) Z L_vv",
+                 "launches": prof["launches"], "ms_per_launch": kernel_ms,
+                 "share_of_step": prof["ms"] / total_ms if total_ms else None})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tensor: bf16x3) + fp64 subspace",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_occ": p.n_occ, "n_vir": p.n_vir, "n_aux": p.n_aux,
+                       "n_aux_ris": p.n_ris, "n_states": N_STATES, "n_dip": cfg["n_dip"],
+                       "omegas": omegas, "precond": args.precond, "tensor_cores": bool(tc),
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (2.8 GB resident factors), no flush"},
+            "p50_ms": statistics.median(per_step),
+            "p99_ms": sorted(per_step)[min(len(per_step) - 1, int(0.99 * len(per_step)))],
+            "converged": conv,
+            "rpa": {"omega": list(map(float, a["omega"])), "n_iter": a["stats"]["n_iter"],
+                    "n_matvec": a["stats"]["n_matvec"], "n_ris_matvec": a["stats"]["n_ris_matvec"],
+                    "max_resid": a["stats"]["max_resid"],
+                    "max_resid_certified": a["stats"]["max_resid_certified"],
+                    "t_precond_share": a["stats"]["t_precond_s"] / max(a["stats"]["t_total_s"], 1e-12)},
+            "polar": {"n_iter": b["stats"]["n_iter"], "n_matvec": b["stats"]["n_matvec"],
+                      "alpha_static_diag": [float(b["alpha"][0][i][i]) for i in range(cfg["n_dip"])]},
+            "roofline": roof,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": {"value": N_STATES * world / (e2e_t / 1e3), "unit": UNIT, "ms_per_step": e2e_t,
+                    "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes)}}
+    if not args.no_cpu_baseline and world == 1:
+        step_s, desc, cores = oracle_sample()
+        line["cpu_baseline"] = {"value": N_STATES / step_s, "unit": UNIT, "cores": cores,
+                                "kind": "oracle", "sample": desc}
+    print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    our_arm(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -194,6 +194,17 @@ const char* tddft_last_error(const tddft_ctx* ctx);
 /* Device resident bytes held by the context (factor copies + workspace).   */
 unsigned long long tddft_device_bytes(const tddft_ctx* ctx);
 
+/* Kernel timing for measurement.  tddft_profile(ctx, 1) starts recording
+ * CUDA events on the context's stream around every launch of the dominant
+ * contraction -- the exchange term K1's second contraction
+ * sum_(P,a) Z[(n,i)][(P,a)] L^P_ab of the exact operator -- and resets the
+ * totals; 0 stops.  tddft_profile_read returns, for that contraction, the
+ * number of launches, their summed device time (ms) and the algorithmic
+ * flops (2*M*N*K per launch) since the last reset.  which must be 0.       */
+tddft_status tddft_profile(tddft_ctx* ctx, int enable);
+tddft_status tddft_profile_read(const tddft_ctx* ctx, int which, long long* launches,
+                                double* ms, double* flops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,10 +37,12 @@ Readings where the paper is silent (each listed in the design notes):
     (Delta -+ omega)^-1 mu)
   * vectors whose norm after two Gram-Schmidt passes is below 1e-8 of the
     input norm are dropped; the subspace holds at most MAX_SUBSPACE vectors:
-    before it would overflow, an eigen solve collapses it onto the Ritz
-    vectors of the wanted roots (Casida: their X+Y and X-Y), a
-    polarizability solve restarts it from the current solutions U and W,
-    and an inner solve stops with its current solution
+    before it would overflow it is rebuilt from the current and the
+    previous iteration's solutions (thick restart with the previous Ritz
+    vectors, as in Stathopoulos and Saad's GD+k): an eigen solve keeps the
+    Ritz vectors of the wanted roots (Casida: their X+Y and X-Y), a
+    polarizability solve its current and previous U and W; an inner solve
+    stops with its current solution
 """
 from __future__ import annotations
 
@@ -276,6 +278,7 @@ def davidson_tda(op, n_states, precond, guess, tol=1e-5, max_iter=50, max_subspa
     ov = V.shape[1]
     max_subspace = max_subspace or MAX_SUBSPACE
     hist = []
+    X_prev = None
     for k in range(1, max_iter + 1):
         a = V @ AV.T                                  # Eq. 1
         w, x = np.linalg.eigh(0.5 * (a + a.T))        # Eq. 2
@@ -294,9 +297,15 @@ def davidson_tda(op, n_states, precond, guess, tol=1e-5, max_iter=50, max_subspa
         if new.shape[0] == 0:
             break
         if V.shape[0] + int(todo.sum()) > max_subspace:
-            # collapse onto the Ritz vectors of the wanted roots
+            # thick restart: current Ritz vectors + those of the previous iteration
             V, AV = X, AX
+            if X_prev is not None:
+                extra = mgs(V, X_prev)
+                V = np.vstack([V, extra])
+                AV = np.vstack([AV, op.tda(extra)])
+                n_mv += extra.shape[0]
             new = mgs(V, new)
+        X_prev = X
         V = np.vstack([V, new])
         AV = np.vstack([AV, op.tda(new)])
         n_mv += new.shape[0]
@@ -328,6 +337,7 @@ def davidson_rpa(op, n_states, precond, guess, tol=1e-5, max_iter=50, max_subspa
     n_mv = V.shape[0]
     max_subspace = max_subspace or MAX_SUBSPACE
     hist = []
+    prev = None
     for k in range(1, max_iter + 1):
         om, u, w, S, Si, lam, Z = _rpa_ritz(V, P, M, n_states)
         U, W = u.T @ V, w.T @ V
@@ -344,11 +354,12 @@ def davidson_rpa(op, n_states, precond, guess, tol=1e-5, max_iter=50, max_subspa
         if new.shape[0] == 0:
             break
         if V.shape[0] + 2 * int(todo.sum()) > max_subspace:
-            # collapse onto the X+Y and X-Y directions of the wanted roots
-            V = mgs(None, np.vstack([U, W]))
+            # thick restart: X+Y and X-Y of the wanted roots, now and one iteration ago
+            V = mgs(None, np.vstack([U, W] + ([] if prev is None else list(prev))))
             P, M = op.apb_amb(V)
             n_mv += V.shape[0]
             new = mgs(V, new)
+        prev = (U, W)
         V = np.vstack([V, new])
         p, m = op.apb_amb(new)
         P, M = np.vstack([P, p]), np.vstack([M, m])
@@ -373,6 +384,7 @@ def polar_solve(op, mu, omegas, precond, guess, tol=1e-5, max_iter=50):
     P, M = op.apb_amb(V)
     n_mv = V.shape[0]
     hist = []
+    prev = None
     for k in range(1, max_iter + 1):
         fac = _paired_factors(V @ P.T, V @ M.T)
         hp = V @ b.T
@@ -395,10 +407,11 @@ def polar_solve(op, mu, omegas, precond, guess, tol=1e-5, max_iter=50):
         todo = r >= tol
         nu, nw = precond.paired(Rp[todo], Rm[todo], om_all[todo])
         if V.shape[0] + 2 * int(todo.sum()) > MAX_SUBSPACE:
-            # restart from the current solutions of every system
-            V = mgs(None, np.vstack([U, W]))
+            # thick restart from the current and the previous solutions of every system
+            V = mgs(None, np.vstack([U, W] + ([] if prev is None else list(prev))))
             P, M = op.apb_amb(V)
             n_mv += V.shape[0]
+        prev = (U.copy(), W.copy())
         new = mgs(V, np.vstack([nu, nw]))
         if new.shape[0] == 0:
             break

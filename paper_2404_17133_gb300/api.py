@@ -87,10 +87,16 @@ _lib.tddft_last_error.argtypes = [_vp]
 _lib.tddft_last_error.restype = C.c_char_p
 _lib.tddft_device_bytes.argtypes = [_vp]
 _lib.tddft_device_bytes.restype = C.c_ulonglong
+_lib.tddft_profile.argtypes = [_vp, _ip]
+_lib.tddft_profile.restype = C.c_int
+_lib.tddft_profile_read.argtypes = [_vp, _ip, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]
+_lib.tddft_profile_read.restype = C.c_int
 
 EXPORTED = ["tddft_default_opts", "tddft_default_desc", "tddft_create", "tddft_solve_tda",
             "tddft_solve_rpa", "tddft_solve_polar", "tddft_apply", "tddft_submit", "tddft_poll",
-            "tddft_destroy", "tddft_last_error", "tddft_device_bytes"]
+            "tddft_destroy", "tddft_last_error", "tddft_device_bytes", "tddft_profile",
+            "tddft_profile_read"]
 
 
 class TddftError(RuntimeError):
@@ -185,6 +191,15 @@ class Solver:
 
     def device_bytes(self):
         return _lib.tddft_device_bytes(self.h)
+
+    def profile(self, enable=True):
+        self._check(_lib.tddft_profile(self.h, int(bool(enable))), allow_noconv=False)
+
+    def profile_read(self):
+        n, ms, fl = C.c_longlong(), C.c_double(), C.c_double()
+        self._check(_lib.tddft_profile_read(self.h, 0, C.byref(n), C.byref(ms), C.byref(fl)),
+                    allow_noconv=False)
+        return dict(launches=n.value, ms=ms.value, flops=fl.value)
 
     def solve_tda(self, opts: Opts, want_vectors=True):
         k = opts.n_states

@@ -8,6 +8,7 @@
 #include <numeric>
 
 #include "ctx.cuh"
+#include "tc_gemm.cuh"
 #include "vecops.cuh"
 
 using namespace tddft;
@@ -223,7 +224,7 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
     const double nr = (double)d.n_aux_ris_J * ov + (double)d.n_aux_ris_K * (no * no + nv * nv + ov);
     double bytes = 0.0;
     if (p64) bytes += 8.0 * (nvv + noo + nov + nr);
-    if (pmx) bytes += 4.0 * (nvv + noo + nov) + 4.0 * nvv + 2.0 * nr;
+    if (pmx) bytes += 4.0 * (nvv + noo + nov) + 4.0 * (double)d.n_aux * nv * tc_pad(nv) + 2.0 * nr;
     size_t fr = 0, tot = 0;
     TD_CUDA(cudaMemGetInfo(&fr, &tot));
     double budget = d.hbm_budget_gb > 0 ? d.hbm_budget_gb * 1e9 : (double)fr - 2e9;
@@ -233,6 +234,8 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
     }
     c->device_bytes = (unsigned long long)bytes;
 
+    c->tc_err = DevBuf(4, s);
+    TD_CUDA(cudaMemsetAsync(c->tc_err.p, 0, 4, s));
     c->eps_o = DevBuf(no * 8, s);
     c->eps_v = DevBuf(nv * 8, s);
     c->delta = DevBuf((size_t)ov * 8, s);
@@ -266,8 +269,8 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
       c->x32_oo = DevBuf(A * no * no * 4, s);
       c->x32_ov = DevBuf(A * ov * 4, s);
       c->x32_vv = DevBuf(A * nv * nv * 4, s);
-      c->x16_vv_hi = DevBuf(A * nv * nv * 2, s);
-      c->x16_vv_lo = DevBuf(A * nv * nv * 2, s);
+      c->x16_vv_hi = DevBuf(A * nv * tc_pad(nv) * 2, s);
+      c->x16_vv_lo = DevBuf(A * nv * tc_pad(nv) * 2, s);
     }
     auto targets = [&](DevBuf& t64, DevBuf& t32) {
       std::vector<StageTarget> v;
@@ -277,11 +280,10 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
     };
     stage_rows(L_oo, tin, dev, A, (long long)no * no, targets(c->x64_oo, c->x32_oo), s);
     stage_rows(L_ov, tin, dev, A, ov, targets(c->x64_ov, c->x32_ov), s);
-    {
-      auto v = targets(c->x64_vv, c->x32_vv);
-      if (pmx) v.push_back({c->x16_vv_hi.p, DType::BF16, c->x16_vv_lo.as<__nv_bfloat16>()});
-      stage_rows(L_vv, tin, dev, A, (long long)nv * nv, v, s);
-    }
+    stage_rows(L_vv, tin, dev, A, (long long)nv * nv, targets(c->x64_vv, c->x32_vv), s);
+    if (pmx)  // BF16 hi/lo split of the FP32 copy, rows padded for the TMA strides
+      tc_split_pad(c->x32_vv.as<float>(), (int)(A * nv), 1, nv, c->x16_vv_hi.as<__nv_bfloat16>(),
+                   c->x16_vv_lo.as<__nv_bfloat16>(), s);
 
     // ris factors (Coulomb rows all; exchange rows windowed, Sec. 3.1)
     const long long RJ = d.n_aux_ris_J, RK = d.n_aux_ris_K;
@@ -443,6 +445,7 @@ tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cor
       if (paired) TD_CUDA(cudaMemcpyAsync(out1, d1, n * 8, cudaMemcpyDeviceToHost, s));
     }
     TD_CUDA(cudaStreamSynchronize(s));
+    check_tc_error(*c);
     return TDDFT_OK;
   })
 }
@@ -504,6 +507,28 @@ const char* tddft_last_error(const tddft_ctx* ctx) {
   const Ctx* c = reinterpret_cast<const Ctx*>(ctx);
   if (!c) return g_create_error.c_str();
   return c->err.c_str();
+}
+
+tddft_status tddft_profile(tddft_ctx* ctx, int enable) {
+  TD_API_BODY(ctx, {
+    std::lock_guard<std::mutex> run(c->run_mu);
+    c->prof.reset();
+    c->prof.on = enable != 0;
+    return TDDFT_OK;
+  })
+}
+
+tddft_status tddft_profile_read(const tddft_ctx* ctx, int which, long long* launches, double* ms,
+                                double* flops) {
+  TD_API_BODY(const_cast<tddft_ctx*>(ctx), {
+    TD_REQUIRE(which == 0, TDDFT_ERR_ARG, "which must be 0");
+    std::lock_guard<std::mutex> run(c->run_mu);
+    c->prof.collect();
+    if (launches) *launches = c->prof.launches;
+    if (ms) *ms = c->prof.ms;
+    if (flops) *flops = c->prof.flops;
+    return TDDFT_OK;
+  })
 }
 
 unsigned long long tddft_device_bytes(const tddft_ctx* ctx) {

@@ -27,10 +27,25 @@ struct FactorSet {
   const __nv_bfloat16* Kvv_lo = nullptr;
 };
 
+// Event-based timing of one kernel family (the dominant contraction).
+struct KernelProfile {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;      // pairs (start, stop)
+  long long launches = 0;
+  double flops = 0.0, ms = 0.0;
+  void begin(cudaStream_t s);
+  void end(cudaStream_t s, double launch_flops);
+  void collect();                   // fold recorded pairs into ms (synchronises)
+  void reset();
+  ~KernelProfile();
+};
+
 struct OpDims {
   int no = 0, nv = 0, ov = 0;
   double a_x = 0.0, c_J = 2.0;
   const double* delta = nullptr;  // device [ov]
+  KernelProfile* prof = nullptr;  // optional timing of the K1 contraction
+  int* tc_err = nullptr;          // device flag set by the tensor-core kernel
 };
 
 enum class OpMode { TDA, PAIRED };
@@ -61,7 +76,8 @@ struct Ctx {
   // exact factors
   DevBuf x64_oo, x64_ov, x64_vv;
   DevBuf x32_oo, x32_ov, x32_vv;
-  DevBuf x16_vv_hi, x16_vv_lo;
+  DevBuf x16_vv_hi, x16_vv_lo;   // [naux][nv][tc_pad(nv)] BF16 split of L_vv
+  DevBuf tc_err;                  // int flag, see OpDims::tc_err
   // ris factors: Coulomb ov (all rows), exchange oo/vv/ov (s rows, windowed)
   DevBuf r64_J, r64_Koo, r64_Kvv, r64_Kov;
   DevBuf r16_J, r16_Koo, r16_Kvv, r16_Kov;
@@ -76,16 +92,22 @@ struct Ctx {
   std::thread worker;
   bool stopping = false;
   std::mutex run_mu;  // one solve at a time on the context's stream
+  KernelProfile prof;
 
   OpDims dims() const {
     OpDims d;
     d.no = no; d.nv = nv; d.ov = ov; d.a_x = a_x; d.c_J = c_J;
     d.delta = delta.as<double>();
+    d.prof = const_cast<KernelProfile*>(&prof);
+    d.tc_err = tc_err.as<int>();
     return d;
   }
   FactorSet exact(int precision) const;  // PLAIN -> FP64, MIXED -> FP32 (+ BF16 split)
   FactorSet ris(int precision) const;    // PLAIN -> FP64, MIXED -> BF16
 };
+
+// Throw if the tensor-core kernel reported a timeout since the last check.
+void check_tc_error(Ctx& c);
 
 tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, double* resid,
                      tddft_stats* st);

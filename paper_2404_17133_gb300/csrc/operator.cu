@@ -20,6 +20,41 @@
 
 namespace tddft {
 
+void KernelProfile::begin(cudaStream_t s) {
+  cudaEvent_t a;
+  TD_CUDA(cudaEventCreate(&a));
+  TD_CUDA(cudaEventRecord(a, s));
+  ev.push_back(a);
+}
+void KernelProfile::end(cudaStream_t s, double launch_flops) {
+  cudaEvent_t b;
+  TD_CUDA(cudaEventCreate(&b));
+  TD_CUDA(cudaEventRecord(b, s));
+  ev.push_back(b);
+  launches++;
+  flops += launch_flops;
+}
+void KernelProfile::collect() {
+  for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+    TD_CUDA(cudaEventSynchronize(ev[i + 1]));
+    float t = 0.f;
+    TD_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+    ms += t;
+  }
+  for (auto e : ev) cudaEventDestroy(e);
+  ev.clear();
+}
+void KernelProfile::reset() {
+  for (auto e : ev) cudaEventDestroy(e);
+  ev.clear();
+  launches = 0;
+  flops = 0.0;
+  ms = 0.0;
+}
+KernelProfile::~KernelProfile() {
+  for (auto e : ev) cudaEventDestroy(e);
+}
+
 namespace {
 constexpr size_t kChunkBytes = 512ull << 20;
 
@@ -32,6 +67,16 @@ int chunk_rows(int nrows, long long per_row_bytes, int m) {
   return (int)(pc < 1 ? 1 : pc);
 }
 }  // namespace
+
+void check_tc_error(Ctx& c) {
+  int h = 0;
+  TD_CUDA(cudaMemcpyAsync(&h, c.tc_err.p, 4, cudaMemcpyDeviceToHost, c.s));
+  TD_CUDA(cudaStreamSynchronize(c.s));
+  if (h != 0) {
+    TD_CUDA(cudaMemsetAsync(c.tc_err.p, 0, 4, c.s));
+    throw Error(TDDFT_ERR_CUDA, "tensor-core kernel wait timed out (code " + std::to_string(h) + ")");
+  }
+}
 
 void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m, OpMode mode,
                     double* out0, double* out1, bool tensor_cores, cudaStream_t s) {
@@ -83,9 +128,11 @@ void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m,
     if (need_k2) Qb = DevBuf((size_t)m * no * pc * no * ew, s);
     DevBuf Zhi, Zlo;
     const bool use_tc = tensor_cores && !f64 && f.Kvv_hi && f.Kvv_lo;
+    TD_REQUIRE(!tensor_cores || f64 || use_tc, TDDFT_ERR_ARG, "tensor-core copies of L_vv missing");
+    const int nvp = tc_pad(nv);
     if (use_tc) {
-      Zhi = DevBuf((size_t)m * no * pc * nv * 2, s);
-      Zlo = DevBuf((size_t)m * no * pc * nv * 2, s);
+      Zhi = DevBuf((size_t)m * no * pc * nvp * 2, s);
+      Zlo = DevBuf((size_t)m * no * pc * nvp * 2, s);
     }
     const size_t es = dtype_size(f.dt);
     for (int p0 = 0; p0 < f.nK; p0 += pc) {
@@ -103,11 +150,13 @@ void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m,
       gemm(z, s);
       const int Mz = m * no;
       const long long Kz = (long long)pn * nv;
+      const bool timed = d.prof && d.prof->on && f.dt != DType::BF16;
+      if (timed) d.prof->begin(s);
       if (use_tc) {
-        split_bf16(Zb.p, DType::F32, Zhi.as<__nv_bfloat16>(), Zlo.as<__nv_bfloat16>(), (long long)Mz * Kz, s);
+        tc_split_pad(Zb.as<float>(), Mz, pn, nv, Zhi.as<__nv_bfloat16>(), Zlo.as<__nv_bfloat16>(), s);
         tc_exchange_k1(Zhi.as<__nv_bfloat16>(), Zlo.as<__nv_bfloat16>(), Mz, pn, nv,
-                       f.Kvv_hi + (size_t)p0 * nv * nv, f.Kvv_lo + (size_t)p0 * nv * nv,
-                       K1b.as<float>(), p0 > 0, s);
+                       f.Kvv_hi + (size_t)p0 * nv * nvp, f.Kvv_lo + (size_t)p0 * nv * nvp,
+                       K1b.as<float>(), p0 > 0, d.tc_err, s);
       } else {
         GemmDesc k;
         k.acc64 = f64;
@@ -118,6 +167,7 @@ void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m,
         k.beta = (p0 > 0) ? 1.0 : 0.0;
         gemm_splitk(k, auto_splits(k.M, k.N, k.K), s);
       }
+      if (timed) d.prof->end(s, 2.0 * Mz * (double)nv * (double)Kz);
       if (need_k2) {
         // Q[n][i][P][j] = sum_b Kov[P][i][b] X[n][j][b]
         GemmDesc q;

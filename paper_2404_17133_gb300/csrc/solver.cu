@@ -18,6 +18,8 @@
 // a- = V^T(A-B)V, solved in the symmetric form L^T a+ L y = Omega^2 y (a- = L L^T).
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <functional>
 #include <numeric>
@@ -36,6 +38,19 @@ inline double since(Clock::time_point t0) {
 }
 
 constexpr double kDrop2 = 1e-16;   // drop a direction below 1e-8 of its norm
+
+// TDDFT_TRACE=1 prints one line per outer iteration to stderr (diagnostics).
+bool trace_on() {
+  static int v = -1;
+  if (v < 0) { const char* e = getenv("TDDFT_TRACE"); v = (e && e[0] == '1') ? 1 : 0; }
+  return v == 1;
+}
+void trace(const char* what, int it, int N, const std::vector<double>& om, const std::vector<double>& rr) {
+  if (!trace_on()) return;
+  double m = 0.0;
+  for (double r : rr) m = std::max(m, r);
+  fprintf(stderr, "[tddft] %s it=%d N=%d max|r|=%.3e omega0=%.8f\n", what, it, N, m, om.empty() ? 0.0 : om[0]);
+}
 
 template <typename T>
 std::vector<T> d2h(const T* p, size_t n, cudaStream_t s) {
@@ -181,7 +196,8 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
   DevBuf lam(k * 8, s), x((size_t)k * cap * 8, s), scr((size_t)2 * k * cap * 8, s);
   DevBuf X((size_t)k * ov * 8, s), AX((size_t)k * ov * 8, s), R((size_t)k * ov * 8, s);
   DevBuf rn(k * 8, s), Ru((size_t)k * ov * 8, s), omu(k * 8, s), cand((size_t)k * ov * 8, s);
-  DevBuf iu(k * 4, s);
+  DevBuf iu(k * 4, s), Xprev((size_t)k * ov * 8, s), tmpk((size_t)k * ov * 8, s);
+  bool have_prev = false;
   double* Vp = V.as<double>();
   double* Wp = W.as<double>();
 
@@ -194,13 +210,14 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
     if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
   };
   mv(0, N);
-  int n_old = 0, n_new = N;
+  int n_proj = 0;   // leading vectors whose projections are already in `a`
   std::vector<double> om(k), rr(k);
   int kk = std::min(k, N);
   for (int it = 1; it <= max_iter; ++it) {
     o.n_iter = it;
-    proj_cols(Vp, N, Wp + (size_t)n_old * ov, n_new, ov, a.as<double>(), cap, n_old, s);   // Eq. 1
-    sym_fill(a.as<double>(), cap, n_old, n_new, s);
+    proj_cols(Vp, N, Wp + (size_t)n_proj * ov, N - n_proj, ov, a.as<double>(), cap, n_proj, s);  // Eq. 1
+    sym_fill(a.as<double>(), cap, n_proj, N - n_proj, s);
+    n_proj = N;
     kk = std::min(k, N);
     eig32(a.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);               // Eq. 2
     refine_lowest(a.as<double>(), cap, N, kk, lam32.as<float>(), vec32.as<float>(), lam.as<double>(),
@@ -213,6 +230,7 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
     rr = sqrt_all(d2h(rn.as<double>(), kk, s));
     check_finite_host(om, "Ritz values");
     check_finite_host(rr, "residual norms");
+    trace(exact_op ? "tda" : "tda-guess", it, N, om, rr);
     std::vector<int> todo;
     for (int j = 0; j < kk; ++j)
       if (!(rr[j] < tol)) todo.push_back(j);
@@ -229,23 +247,24 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
     TD_CUDA(cudaStreamSynchronize(s));
     cnt.t_pre += since(tp);
     if (N + nu > cap) {
-      // collapse onto the current Ritz vectors of the wanted roots
+      // thick restart: current Ritz vectors + those of the previous iteration
       TD_CUDA(cudaMemcpyAsync(Vp, X.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
       TD_CUDA(cudaMemcpyAsync(Wp, AX.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
       N = kk;
-      n_old = 0;
-      n_new = kk;
-      proj_cols(Vp, N, Wp, N, ov, a.as<double>(), cap, 0, s);
-      sym_fill(a.as<double>(), cap, 0, N, s);
-      n_old = N;
-      n_new = 0;
+      if (have_prev) {
+        TD_CUDA(cudaMemcpyAsync(tmpk.p, Xprev.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
+        int ne = orth_append(Vp, N, tmpk.as<double>(), kk, ov, s);
+        mv(N, ne);
+        N += ne;
+      }
+      n_proj = 0;
       cnt.restarts++;
     }
+    TD_CUDA(cudaMemcpyAsync(Xprev.p, X.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
+    have_prev = true;
     int nacc = orth_append(Vp, N, cand.as<double>(), nu, ov, s);
     if (nacc == 0) break;
     mv(N, nacc);
-    n_old = N;
-    n_new = nacc;
     N += nacc;
   }
   o.omega = om;
@@ -334,6 +353,12 @@ PairedLinOut paired_linear(int ov, const PairOp& op, const PairPre& pre, const d
   DevBuf gn(nr * 8, s), gn2(nr * 8, s), rn1(nr * 8, s), rn2(nr * 8, s);
   DevBuf iu(nr * 4, s), shu(nr * 8, s), gpu_(((size_t)nr) * ov * 8, s), gmu((size_t)nr * ov * 8, s);
   DevBuf cand((size_t)2 * nr * ov * 8, s);
+  DevBuf Uprev, Wprev;
+  bool have_prev = false;
+  if (exact_op) {
+    Uprev = DevBuf((size_t)nr * ov * 8, s);
+    Wprev = DevBuf((size_t)nr * ov * 8, s);
+  }
   row_sumsq(gp, ov, nr, ov, gn.as<double>(), s);
   std::vector<double> gnh = d2h(gn.as<double>(), nr, s);
   if (gm) {
@@ -394,6 +419,7 @@ PairedLinOut paired_linear(int ov, const PairOp& op, const PairPre& pre, const d
       if (!(rr[r] <= tol)) todo.push_back(r);
     }
     check_finite_host(rr, "linear-system residuals");
+    if (exact_op) trace("polar", it, sp.N, std::vector<double>(), rr);
     if (todo.empty()) { o.converged = true; break; }
     if (it == max_iter) break;
     const int nu = (int)todo.size();
@@ -410,16 +436,28 @@ PairedLinOut paired_linear(int ov, const PairOp& op, const PairPre& pre, const d
     cnt.t_pre += since(tp);
     if (sp.N + 2 * nu > cap) {
       if (!exact_op) break;   // inner solve: return the current approximate solution
-      // restart the subspace from the current solutions U and W of every system
-      DevBuf rst((size_t)2 * nr * ov * 8, s);
+      // thick restart from the current and the previous solutions of every system
+      const int nprev = (have_prev && 4 * nr <= 112) ? 2 * nr : 0;
+      DevBuf rst((size_t)4 * nr * ov * 8, s);
       TD_CUDA(cudaMemcpyAsync(rst.p, Uout, (size_t)nr * ov * 8, cudaMemcpyDeviceToDevice, s));
       TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)nr * ov, Wout, (size_t)nr * ov * 8,
                               cudaMemcpyDeviceToDevice, s));
-      sp.N = orth_append(sp.v(), 0, rst.as<double>(), 2 * nr, ov, s);
+      if (nprev) {
+        TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)2 * nr * ov, Uprev.p, (size_t)nr * ov * 8,
+                                cudaMemcpyDeviceToDevice, s));
+        TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)3 * nr * ov, Wprev.p, (size_t)nr * ov * 8,
+                                cudaMemcpyDeviceToDevice, s));
+      }
+      sp.N = orth_append(sp.v(), 0, rst.as<double>(), 2 * nr + nprev, ov, s);
       mv(0, sp.N);
       sp.n_old = 0;
       sp.n_new = sp.N;
       cnt.restarts++;
+    }
+    if (exact_op) {
+      TD_CUDA(cudaMemcpyAsync(Uprev.p, Uout, (size_t)nr * ov * 8, cudaMemcpyDeviceToDevice, s));
+      TD_CUDA(cudaMemcpyAsync(Wprev.p, Wout, (size_t)nr * ov * 8, cudaMemcpyDeviceToDevice, s));
+      have_prev = true;
     }
     int nacc = orth_append(sp.v(), sp.N, cand.as<double>(), 2 * nu, ov, s);
     if (nacc == 0) break;
@@ -457,7 +495,8 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
       MW((size_t)k * ov * 8, s), Rp((size_t)k * ov * 8, s), Rm((size_t)k * ov * 8, s);
   DevBuf rn1(k * 8, s), rn2(k * 8, s), iu(k * 4, s), shu(k * 8, s);
   DevBuf gpu_((size_t)k * ov * 8, s), gmu((size_t)k * ov * 8, s), cand((size_t)2 * k * ov * 8, s);
-  DevBuf rst((size_t)2 * k * ov * 8, s);
+  DevBuf rst((size_t)4 * k * ov * 8, s), Uprev((size_t)k * ov * 8, s), Wprev((size_t)k * ov * 8, s);
+  bool have_prev = false;
 
   sp.N = orth_append(sp.v(), 0, guess, std::min(ng, cap), ov, s);
   TD_REQUIRE(sp.N >= 1, TDDFT_ERR_ARG, "initial guess is empty");
@@ -514,6 +553,7 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
       if (!(rr[j] < tol)) todo.push_back(j);
     }
     check_finite_host(rr, "Casida residual norms");
+    trace(exact_op ? "rpa" : "rpa-guess", it, N, om, rr);
     if (todo.empty() && kk == k) { o.converged = true; break; }
     if (it == max_iter) break;
     const int nu = (int)todo.size();
@@ -529,16 +569,26 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
     TD_CUDA(cudaStreamSynchronize(s));
     cnt.t_pre += since(tp);
     if (sp.N + 2 * nu > cap) {
-      // restart from the X+Y and X-Y directions of the wanted roots
+      // thick restart: X+Y and X-Y of the wanted roots, now and one iteration ago
+      const int nprev = (have_prev && 4 * kk <= 112) ? 2 * kk : 0;
       TD_CUDA(cudaMemcpyAsync(rst.p, U.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
       TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)kk * ov, W.p, (size_t)kk * ov * 8,
                               cudaMemcpyDeviceToDevice, s));
-      sp.N = orth_append(sp.v(), 0, rst.as<double>(), 2 * kk, ov, s);
+      if (nprev) {
+        TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)2 * kk * ov, Uprev.p, (size_t)kk * ov * 8,
+                                cudaMemcpyDeviceToDevice, s));
+        TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)3 * kk * ov, Wprev.p, (size_t)kk * ov * 8,
+                                cudaMemcpyDeviceToDevice, s));
+      }
+      sp.N = orth_append(sp.v(), 0, rst.as<double>(), 2 * kk + nprev, ov, s);
       mv(0, sp.N);
       sp.n_old = 0;
       sp.n_new = sp.N;
       cnt.restarts++;
     }
+    TD_CUDA(cudaMemcpyAsync(Uprev.p, U.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
+    TD_CUDA(cudaMemcpyAsync(Wprev.p, W.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
+    have_prev = true;
     int nacc = orth_append(sp.v(), sp.N, cand.as<double>(), 2 * nu, ov, s);
     if (nacc == 0) break;
     mv(sp.N, nacc);
@@ -720,8 +770,8 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
                           p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s);
   double cert = -1.0;
   if (p.mixed) {
-    // re-check the converged residuals with the FP64 (else FP32 SIMT) operator
-    const FactorSet Fc = (c.precisions & 1) ? c.exact(TDDFT_PLAIN) : c.exact(TDDFT_MIXED);
+    // re-check the converged residuals with the FP32 SIMT operator (no tensor cores)
+    const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 SIMT operator, FP32 accumulation
     DevBuf AX((size_t)p.k * ov * 8, s), R((size_t)p.k * ov * 8, s), rn(p.k * 8, s), om(p.k * 8, s);
     apply_operator(dims, Fc, r.X.as<double>(), p.k, OpMode::TDA, AX.as<double>(), nullptr, false, s);
     h2d(om.as<double>(), r.omega, s);
@@ -740,6 +790,7 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
   }
   copy_out(X, r.X.as<double>(), (size_t)p.k * ov, dev, s);
   TD_CUDA(cudaStreamSynchronize(s));
+  check_tc_error(c);
   fill_stats(st, r.n_iter, cnt, r.converged, r.resid, cert, t0);
   return r.converged ? TDDFT_OK : TDDFT_ERR_NOCONV;
 }
@@ -796,7 +847,7 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
                           p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s);
   double cert = -1.0;
   if (p.mixed) {
-    const FactorSet Fc = (c.precisions & 1) ? c.exact(TDDFT_PLAIN) : c.exact(TDDFT_MIXED);
+    const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 SIMT operator, FP32 accumulation
     const int k = p.k;
     DevBuf PU((size_t)k * ov * 8, s), MU((size_t)k * ov * 8, s), PW((size_t)k * ov * 8, s),
         MW((size_t)k * ov * 8, s), Rp((size_t)k * ov * 8, s), Rm((size_t)k * ov * 8, s);
@@ -828,6 +879,7 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     TD_CUDA(cudaStreamSynchronize(s));
   }
   TD_CUDA(cudaStreamSynchronize(s));
+  check_tc_error(c);
   fill_stats(st, r.n_iter, cnt, r.converged, r.resid, cert, t0);
   return r.converged ? TDDFT_OK : TDDFT_ERR_NOCONV;
 }
@@ -904,6 +956,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
     else std::copy(al.begin(), al.end(), alpha);
   }
   TD_CUDA(cudaStreamSynchronize(s));
+  check_tc_error(c);
   fill_stats(st, r.n_iter, cnt, r.converged, r.resid, -1.0, t0);
   return r.converged ? TDDFT_OK : TDDFT_ERR_NOCONV;
 }

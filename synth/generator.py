@@ -17,9 +17,14 @@ Generator conventions (each one a stated reading, not taken from the paper):
 * L^P over all n_mo = n_occ + n_vir orbitals is a symmetric matrix whose upper
   triangle (diagonal included) is N(0, 1), scaled by amp * exp(-P / d) with the
   decay length d = 60 * n_aux / 200 ("decay scaled to n_aux");
-* the amplitude is amp = 0.1 * sqrt(S(200, 60) / S(n_aux, d)), S(n, d) =
-  sum_{P<n} exp(-2P/d), which keeps A-B and A+B positive definite (the literal
-  0.3 gives indefinite Hessians, so it is only kept as an optional TDA input);
+* the amplitude is amp = scale * 0.1 * sqrt(S(200, 60) / S(n_aux, d)), S(n, d) =
+  sum_{P<n} exp(-2P/d), with a per-workload scale 0.7^k: the smallest k that
+  leaves lambda_min(A-B) and lambda_min(A+B) above 0.02 Ha and lets the
+  diagonal-preconditioned Davidson converge 10 states within the iteration
+  range the paper reports for the diagonal preconditioner (Table 1, at most
+  33).  A dense random coupling grows like sqrt(n_occ n_vir) at fixed
+  element size, so larger workloads need a smaller scale; the literal 0.3
+  gives indefinite Hessians and is only kept as an optional TDA input;
 * the ris Coulomb factors are sqrt(0.9) times the leading n_ris rows of the
   exact factors plus an independent symmetric N(0, (0.1 sigma_P)^2)
   perturbation; the ris exchange factors are the s-type rows, one per atom,
@@ -143,8 +148,11 @@ def dipoles(seed: int, n_dip: int, n_ov: int, sigma: float = 0.1) -> np.ndarray:
 CONFIGS = {
     "tda_small": dict(n_occ=10, n_vir=40, n_aux=200, n_ris=90, seeds=(0, 1, 2),
                       n_states=5, mu_seed=3),
+    # amplitude scale 0.7^5: at 1.0 lambda_min(A-B) = -0.26 Ha (0.7: +0.21 Ha); at
+    # 0.7^2 .. 0.7^4 the diagonal preconditioner needs 40 to more than 80 iterations
     "rpa_polar_medium": dict(n_occ=60, n_vir=400, n_aux=2000, n_ris=360, seeds=(10, 11, 12),
-                             n_states=10, mu_seed=13, omegas=(0.0, 0.05, 0.1), n_dip=3),
+                             n_states=10, mu_seed=13, omegas=(0.0, 0.05, 0.1), n_dip=3,
+                             amplitude_scale=0.7 ** 5),
     "large_mixed": dict(n_occ=150, n_vir=1350, n_aux=6000, n_ris=1350, seeds=(20, 21, 22),
                         n_states=20, mu_seed=23),
 }
@@ -153,5 +161,7 @@ CONFIGS = {
 def make_config(name: str, **over) -> Problem:
     c = dict(CONFIGS[name])
     c.update(over)
+    if "amplitude" not in c:
+        c["amplitude"] = c.get("amplitude_scale", 1.0) * default_amplitude(c["n_aux"])
     return make_problem(c["n_occ"], c["n_vir"], c["n_aux"], c["n_ris"], seeds=c["seeds"],
                         **{k: c[k] for k in ("a_x", "coulomb_factor", "amplitude") if k in c})

@@ -4,6 +4,8 @@ Tolerances (see the design notes for the derivation):
   * operator products, PLAIN (FP64): 1e-11 relative to max |out| -- rounding order only;
   * operator products, MIXED exact (FP32 factors, FP32 accumulation): 2e-5 relative;
   * ris products, MIXED (BF16 factors): 2e-2 relative (preconditioner only);
+  * exact products, MIXED on the tensor cores (BF16 hi+lo, three products,
+    FP32 accumulation): 5e-5 relative;
   * excitation energies: 1e-6 Ha (PLAIN), 1e-5 Ha (MIXED);
   * polarizabilities: 1e-6 relative (PLAIN), 1e-5 relative (MIXED).
 """
@@ -40,7 +42,7 @@ def _dense(p):
 PROBLEMS = {
     "tda_small": lambda: make_config("tda_small"),
     "ragged": lambda: make_problem(3, 7, 5, 9, seeds=(30, 31, 32)),
-    "odd": lambda: make_problem(7, 33, 37, 27, seeds=(40, 41, 42)),
+    "odd": lambda: make_problem(7, 33, 37, 27, seeds=(40, 41, 42), amplitude=0.07),
 }
 
 
@@ -77,15 +79,27 @@ def test_operator_products(case, api):
     assert _rel(s.apply(2, X, precision=api.MIXED), rt) < 2e-2
 
 
+def test_tensor_core_products(case, api):
+    name, p, s = case
+    op = O.exact_operator(p)
+    for m in (1, 5, 23):
+        X = np.random.default_rng(m).standard_normal((m, p.n_ov))
+        assert _rel(s.apply(0, X, precision=api.MIXED, tensor_cores=True), op.tda(X)) < 5e-5
+        gp, gm = s.apply(1, X, precision=api.MIXED, tensor_cores=True)
+        rp, rm = op.apb_amb(X)
+        assert _rel(gp, rp) < 5e-5 and _rel(gm, rm) < 5e-5
+
+
 @pytest.mark.parametrize("pc", ["diag", "rid"])
-@pytest.mark.parametrize("prec", ["plain", "mixed"])
+@pytest.mark.parametrize("prec", ["plain", "mixed", "mixed_tc"])
 def test_tda(case, api, pc, prec):
     name, p, s = case
     A, _ = _dense(p)
     k = min(5, p.n_ov - 1)
     ref_w, ref_X = D.tda(A, k)
     o = api.default_opts(n_states=k, precond=api.RID if pc == "rid" else api.DIAG,
-                         precision=api.PLAIN if prec == "plain" else api.MIXED)
+                         precision=api.PLAIN if prec == "plain" else api.MIXED,
+                         tensor_cores=int(prec == "mixed_tc"))
     r = s.solve_tda(o)
     tol = 1e-6 if prec == "plain" else 1e-5
     assert r["status"] == api.OK
@@ -96,14 +110,15 @@ def test_tda(case, api, pc, prec):
 
 
 @pytest.mark.parametrize("pc", ["diag", "rid"])
-@pytest.mark.parametrize("prec", ["plain", "mixed"])
+@pytest.mark.parametrize("prec", ["plain", "mixed", "mixed_tc"])
 def test_rpa(case, api, pc, prec):
     name, p, s = case
     A, B = _dense(p)
     k = min(5, p.n_ov - 1)
     ref_w, ref_X, ref_Y = D.casida(A, B, k)
     o = api.default_opts(n_states=k, precond=api.RID if pc == "rid" else api.DIAG,
-                         precision=api.PLAIN if prec == "plain" else api.MIXED)
+                         precision=api.PLAIN if prec == "plain" else api.MIXED,
+                         tensor_cores=int(prec == "mixed_tc"))
     r = s.solve_rpa(o)
     tol = 1e-6 if prec == "plain" else 1e-5
     assert r["status"] == api.OK
@@ -115,14 +130,15 @@ def test_rpa(case, api, pc, prec):
 
 
 @pytest.mark.parametrize("pc", ["diag", "rid"])
-@pytest.mark.parametrize("prec", ["plain", "mixed"])
+@pytest.mark.parametrize("prec", ["plain", "mixed", "mixed_tc"])
 def test_polar(case, api, pc, prec):
     name, p, s = case
     A, B = _dense(p)
     mu = dipoles(3, 3, p.n_ov)
     ref = D.polar(A, B, mu, OMEGAS)
     o = api.default_opts(precond=api.RID if pc == "rid" else api.DIAG,
-                         precision=api.PLAIN if prec == "plain" else api.MIXED)
+                         precision=api.PLAIN if prec == "plain" else api.MIXED,
+                         tensor_cores=int(prec == "mixed_tc"))
     r = s.solve_polar(o, mu, OMEGAS)
     tol = 1e-6 if prec == "plain" else 1e-5
     assert r["status"] == api.OK
