@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tensor-cores", type=int, default=-1, help="1/0; default: on when available")
+    ap.add_argument("--tensor-cores", type=int, default=-1, help="1/0 (default 1: tcgen05 exchange)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -187,7 +187,7 @@ def our_arm(args, rank, world, local):
     omegas = list(cfg["omegas"])
     tc = args.tensor_cores
     if tc < 0:
-        tc = 0
+        tc = 1
     stream = torch.cuda.current_stream()
     f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
     kidx = p.ris_K_index

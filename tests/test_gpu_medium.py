@@ -1,0 +1,70 @@
+"""Full-size parity on the medium workload (n_occ=60, n_vir=400, n_aux=2000,
+ris n_aux=360), in the launch configuration bench.py times (MIXED precision,
+tcgen05 exchange, rid), against oracle results stored in
+tests/golden/rpa_polar_medium.json (written by tests/golden/make_golden.py,
+which calls only the oracle).  Tolerances: 1e-5 Ha for excitation energies and
+1e-5 relative for polarizabilities (MIXED form); operator products on sampled
+vectors against the oracle's FP64 product: 5e-5 relative (BF16 hi+lo)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import operators as O
+from synth.generator import CONFIGS, dipoles, make_config
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "rpa_polar_medium.json")
+
+
+@pytest.fixture(scope="module")
+def setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2404_17133_gb300 import api
+    with open(GOLD) as f:
+        gold = json.load(f)
+    p = make_config("rpa_polar_medium")
+    c = CONFIGS["rpa_polar_medium"]
+    mu = dipoles(c["mu_seed"], c["n_dip"], p.n_ov)
+    cs = gold["checksums"]
+    assert abs(p.L_ov.sum() - cs["L_ov"]) < 1e-9 * max(1.0, abs(cs["L_ov"])), "generator changed"
+    assert abs(mu.sum() - cs["mu"]) < 1e-9 * max(1.0, abs(cs["mu"])), "generator changed"
+    s = api.Solver.from_problem(p, precisions=2, dtype=api.F32)
+    yield api, p, mu, gold, s
+    s.close()
+
+
+def test_sampled_products_full_size(setup):
+    api, p, mu, gold, s = setup
+    X = np.random.default_rng(3).standard_normal((2, p.n_ov))
+    rp, rm = O.exact_operator(p).apb_amb(X)
+    gp, gm = s.apply(1, X, precision=api.MIXED, tensor_cores=True)
+    rel = lambda a, b: float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    assert rel(gp, rp) < 5e-5 and rel(gm, rm) < 5e-5
+
+
+def test_rpa_full_size(setup):
+    api, p, mu, gold, s = setup
+    o = api.default_opts(n_states=10, precond=api.RID, precision=api.MIXED, tensor_cores=1)
+    r = s.solve_rpa(o, want_vectors=False)
+    assert r["status"] == api.OK
+    assert np.max(np.abs(r["omega"] - np.array(gold["rpa"]["omega"]))) < 1e-5
+    assert r["stats"]["max_resid_certified"] < 1e-5
+    # BF16 hi+lo products round differently from FP64, which can move the
+    # iteration where the last root crosses the threshold by a few steps
+    assert abs(r["stats"]["n_iter"] - gold["rpa"]["n_iter"]) <= 4
+
+
+def test_polar_full_size(setup):
+    api, p, mu, gold, s = setup
+    o = api.default_opts(precond=api.RID, precision=api.MIXED, tensor_cores=1)
+    r = s.solve_polar(o, mu, list(CONFIGS["rpa_polar_medium"]["omegas"]))
+    ref = np.array(gold["polar"]["alpha"])
+    assert r["status"] == api.OK
+    assert np.max(np.abs(r["alpha"] - ref)) / np.max(np.abs(ref)) < 1e-5
+    assert abs(r["stats"]["n_iter"] - gold["polar"]["n_iter"]) <= 4
