@@ -194,6 +194,29 @@ const char* tddft_last_error(const tddft_ctx* ctx);
 /* Device resident bytes held by the context (factor copies + workspace).   */
 unsigned long long tddft_device_bytes(const tddft_ctx* ctx);
 
+/* tddft_apply without device allocation.  (No counterpart in the paper: this
+ * is an interface for callers of this library.)  Some callers cannot allocate
+ * device memory when they need a product -- another runtime owns the device's
+ * memory pool, a real-time loop cannot take an allocation's latency or its
+ * out-of-memory failure, or allocation calls are not allowed in the calling
+ * context.  This entry point computes the same products as tddft_apply
+ * (kinds 0-3, PLAIN = FP64 or MIXED = FP32 SIMT; no tensor-core path) and keeps
+ * every intermediate in one 64 MiB array of device memory that the library
+ * declares statically: every GPU that loads the library holds those 64 MiB
+ * until the process exits.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *   X, out0, out1: DEVICE pointers, [m][ov] FP64 (out1 for kinds 1 and 3).
+ * The work is queued on the context's stream; results are valid once that
+ * stream has been synchronised.  The first call on a device looks up the
+ * array's device address (once per device, with that device made current);
+ * make that first call before any stream capture.  All calls in the process
+ * share the one array and it keeps the previous call's contents, so calls
+ * whose work overlaps on the GPU (for example from two contexts on different
+ * streams) race with each other.  A product whose intermediates do not fit in
+ * 64 MiB is rejected with TDDFT_ERR_ARG (use tddft_apply).                  */
+tddft_status tddft_apply_noalloc(tddft_ctx* ctx, int kind, int precision, const double* X, int m,
+                                 double* out0, double* out1);
+
 /* Kernel timing for measurement.  tddft_profile(ctx, 1) starts recording
  * CUDA events on the context's stream around every launch of the dominant
  * contraction -- the exchange term K1's second contraction

@@ -87,6 +87,8 @@ _lib.tddft_last_error.argtypes = [_vp]
 _lib.tddft_last_error.restype = C.c_char_p
 _lib.tddft_device_bytes.argtypes = [_vp]
 _lib.tddft_device_bytes.restype = C.c_ulonglong
+_lib.tddft_apply_noalloc.argtypes = [_vp, _ip, _ip, _dp, _ip, _dp, _dp]
+_lib.tddft_apply_noalloc.restype = C.c_int
 _lib.tddft_profile.argtypes = [_vp, _ip]
 _lib.tddft_profile.restype = C.c_int
 _lib.tddft_profile_read.argtypes = [_vp, _ip, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
@@ -96,7 +98,7 @@ _lib.tddft_profile_read.restype = C.c_int
 EXPORTED = ["tddft_default_opts", "tddft_default_desc", "tddft_create", "tddft_solve_tda",
             "tddft_solve_rpa", "tddft_solve_polar", "tddft_apply", "tddft_submit", "tddft_poll",
             "tddft_destroy", "tddft_last_error", "tddft_device_bytes", "tddft_profile",
-            "tddft_profile_read"]
+            "tddft_profile_read", "tddft_apply_noalloc"]
 
 
 class TddftError(RuntimeError):
