@@ -94,6 +94,8 @@ def mgs(V: np.ndarray, cand: np.ndarray, drop_tol: float = DROP_TOL) -> np.ndarr
         n1 = np.linalg.norm(v)
         if n1 < drop_tol * n0:
             continue
+        if len(basis) + len(out) >= v.size:   # the space is already spanned
+            break
         out.append(v / n1)
     if not out:
         return np.zeros((0, np.atleast_2d(cand).shape[1]))

@@ -54,6 +54,9 @@ enum class OpMode { TDA, PAIRED };
 // tensor_cores: K1's dominant contraction on tcgen05 (BF16 hi+lo), needs Kvv_hi/lo.
 void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m, OpMode mode,
                     double* out0, double* out1, bool tensor_cores, cudaStream_t s);
+// FP32 vectors (FP32 or BF16 factor sets only): the ris products of the inner solves.
+void apply_operator(const OpDims& d, const FactorSet& f, const float* X, int m, OpMode mode,
+                    float* out0, float* out1, bool tensor_cores, cudaStream_t s);
 
 struct Request {
   int kind = 0;

@@ -161,8 +161,11 @@ static void launch_cfg(const GemmDesc& d, cudaStream_t s) {
 template <typename TA, typename TB, typename TC, typename ACC>
 static void launch_shape(const GemmDesc& d, cudaStream_t s) {
   if (sizeof(ACC) == 8) {
+    // FP64 is ALU-bound on this GPU: pick the tile that wastes the least padding
     if (d.M <= 16) launch_cfg<TA, TB, TC, ACC, 16, 128, 8, 1, 8>(d, s);
+    else if (d.N <= 16) launch_cfg<TA, TB, TC, ACC, 128, 16, 8, 8, 1>(d, s);
     else if (d.M <= 32) launch_cfg<TA, TB, TC, ACC, 32, 128, 8, 2, 8>(d, s);
+    else if (d.N <= 32) launch_cfg<TA, TB, TC, ACC, 128, 32, 8, 8, 2>(d, s);
     else launch_cfg<TA, TB, TC, ACC, 64, 64, 8, 4, 4>(d, s);
   } else {
     if (d.M <= 32) launch_cfg<TA, TB, TC, ACC, 32, 128, 8, 2, 8>(d, s);

@@ -78,20 +78,23 @@ void check_tc_error(Ctx& c) {
   }
 }
 
-void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m, OpMode mode,
-                    double* out0, double* out1, bool tensor_cores, cudaStream_t s) {
+template <typename TX>
+static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, int m, OpMode mode,
+                             TX* out0, TX* out1, bool tensor_cores, cudaStream_t s) {
   if (m <= 0) return;
   const int no = d.no, nv = d.nv, ov = d.ov;
   const bool f64 = (f.dt == DType::F64);
   const DType tw = f64 ? DType::F64 : DType::F32;  // working / accumulation type
   const size_t ew = dtype_size(tw);
   const long long mov = (long long)m * ov;
+  constexpr bool x32 = sizeof(TX) == 4;
+  TD_REQUIRE(!(x32 && f64), TDDFT_ERR_ARG, "FP32 vectors need FP32/BF16 factors");
 
   const void* Xw = X;
   DevBuf xbuf;
-  if (!f64) {
+  if (!f64 && !x32) {
     xbuf = DevBuf(mov * 4, s);
-    cast_f64_to_f32(X, xbuf.as<float>(), mov, s);
+    cast_f64_to_f32(reinterpret_cast<const double*>(X), xbuf.as<float>(), mov, s);
     Xw = xbuf.p;
   }
 
@@ -195,12 +198,34 @@ void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m,
   const void* J = Jb.p;
   const void* K1 = K1b.p;
   const void* K2 = K2b.p;
-  if (mode == OpMode::TDA) {
-    combine(X, d.delta, J, K1, nullptr, tw, d.c_J, -d.a_x, 0.0, m, ov, out0, s);
+  if constexpr (x32) {
+    const float* Jf = static_cast<const float*>(J);
+    const float* K1f = static_cast<const float*>(K1);
+    const float* K2f = static_cast<const float*>(K2);
+    if (mode == OpMode::TDA) {
+      combine_f32(X, d.delta, Jf, K1f, nullptr, d.c_J, -d.a_x, 0.0, m, ov, out0, s);
+    } else {
+      combine_f32(X, d.delta, Jf, K1f, K2f, 2.0 * d.c_J, -d.a_x, -d.a_x, m, ov, out0, s);
+      combine_f32(X, d.delta, nullptr, K1f, K2f, 0.0, -d.a_x, d.a_x, m, ov, out1, s);
+    }
   } else {
-    combine(X, d.delta, J, K1, K2, tw, 2.0 * d.c_J, -d.a_x, -d.a_x, m, ov, out0, s);
-    combine(X, d.delta, nullptr, K1, K2, tw, 0.0, -d.a_x, d.a_x, m, ov, out1, s);
+    if (mode == OpMode::TDA) {
+      combine(X, d.delta, J, K1, nullptr, tw, d.c_J, -d.a_x, 0.0, m, ov, out0, s);
+    } else {
+      combine(X, d.delta, J, K1, K2, tw, 2.0 * d.c_J, -d.a_x, -d.a_x, m, ov, out0, s);
+      combine(X, d.delta, nullptr, K1, K2, tw, 0.0, -d.a_x, d.a_x, m, ov, out1, s);
+    }
   }
+}
+
+void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m, OpMode mode,
+                    double* out0, double* out1, bool tensor_cores, cudaStream_t s) {
+  apply_operator_t<double>(d, f, X, m, mode, out0, out1, tensor_cores, s);
+}
+
+void apply_operator(const OpDims& d, const FactorSet& f, const float* X, int m, OpMode mode,
+                    float* out0, float* out1, bool tensor_cores, cudaStream_t s) {
+  apply_operator_t<float>(d, f, X, m, mode, out0, out1, tensor_cores, s);
 }
 
 }  // namespace tddft

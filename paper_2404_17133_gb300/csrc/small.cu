@@ -481,6 +481,77 @@ __global__ void __launch_bounds__(1024) k_chol_drop(const double* __restrict__ G
   }
 }
 
+// One CTA per right-hand side r: Gaussian elimination with partial pivoting on
+// [(H - sigma_r I) | b_r] in shared memory (compute type T), then back substitution.
+template <typename T>
+__global__ void __launch_bounds__(512) k_lu_shift(const double* __restrict__ H, int ldh, int n,
+                                                  const double* __restrict__ sig,
+                                                  const double* __restrict__ B, double* __restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char lu_raw[];
+  T* A = reinterpret_cast<T*>(lu_raw);
+  const int ld = n + 2;
+  __shared__ int prow;
+  __shared__ T yk;
+  const int r = blockIdx.x;
+  const double sg = sig[r];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int idx = tid; idx < n * (n + 1); idx += nth) {
+    int i = idx / (n + 1), j = idx - i * (n + 1);
+    double v;
+    if (j < n) v = 0.5 * (H[(long long)i * ldh + j] + H[(long long)j * ldh + i]) - (i == j ? sg : 0.0);
+    else v = B[(long long)r * n + i];
+    A[i * ld + j] = (T)v;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid < 32) {   // pivot: argmax |A[i][k]|, i >= k (one warp)
+      T best = T(-1);
+      int bi = k;
+      for (int i = k + tid; i < n; i += 32) {
+        T v = A[i * ld + k];
+        v = v < T(0) ? -v : v;
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) prow = bi;
+    }
+    __syncthreads();
+    const int p = prow;
+    if (p != k)
+      for (int j = k + tid; j <= n; j += nth) {
+        T t = A[k * ld + j];
+        A[k * ld + j] = A[p * ld + j];
+        A[p * ld + j] = t;
+      }
+    __syncthreads();
+    T piv = A[k * ld + k];
+    if (piv == T(0)) piv = T(1e-30);
+    const int rows = n - k - 1, cols = n - k;   // columns k+1..n (incl. rhs)
+    for (int idx = tid; idx < rows * cols; idx += nth) {
+      int i = k + 1 + idx / cols, j = k + 1 + idx % cols;
+      A[i * ld + j] -= A[i * ld + k] / piv * A[k * ld + j];
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    if (tid == 0) {
+      T piv = A[k * ld + k];
+      if (piv == T(0)) piv = T(1e-30);
+      yk = A[k * ld + n] / piv;
+      A[k * ld + n] = yk;
+    }
+    __syncthreads();
+    const T y = yk;
+    for (int i = tid; i < k; i += nth) A[i * ld + n] -= A[i * ld + k] * y;
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nth) Y[(long long)r * n + i] = (double)A[i * ld + n];
+}
+
 void set_smem(const void* f, size_t bytes) {
   TD_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
@@ -518,6 +589,23 @@ void shifted_solve(const double* H, int ldh, int n, const float* lam32, const fl
                    cudaStream_t s) {
   if (nr <= 0) return;
   k_shifted<<<nr, 256, 0, s>>>(H, ldh, n, lam32, vec32, sigma, B, Y, nref);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+void lu_shift_solve(const double* H, int ldh, int n, const double* sigma, int nr, const double* B,
+                    double* Y, bool fp32, cudaStream_t s) {
+  if (nr <= 0) return;
+  TD_REQUIRE(n >= 1 && n <= kSmallMax, TDDFT_ERR_ARG, "lu_shift_solve: size out of range");
+  if (fp32) {
+    size_t smem = (size_t)n * (n + 2) * sizeof(float);
+    set_smem((const void*)k_lu_shift<float>, smem);
+    k_lu_shift<float><<<nr, 512, smem, s>>>(H, ldh, n, sigma, B, Y);
+  } else {
+    size_t smem = (size_t)n * (n + 2) * sizeof(double);
+    set_smem((const void*)k_lu_shift<double>, smem);
+    k_lu_shift<double><<<nr, 512, smem, s>>>(H, ldh, n, sigma, B, Y);
+  }
   count_launch();
   TD_LAUNCH_CHECK();
 }

@@ -25,6 +25,11 @@ void shifted_solve(const double* H, int ldh, int n, const float* lam32, const fl
                    const double* sigma, int nr, const double* B, double* Y, int nref,
                    cudaStream_t s);
 
+// Y[r] = (H - sigma[r] I)^-1 B[r] for r < nr by Gaussian elimination with
+// partial pivoting, one CTA per right-hand side; compute in FP32 or FP64.
+void lu_shift_solve(const double* H, int ldh, int n, const double* sigma, int nr, const double* B,
+                    double* Y, bool fp32, cudaStream_t s);
+
 // In-place FP64 Cholesky H = L L^T (lower, zeroed above the diagonal).
 // info[0] = 0 on success, j+1 when pivot j is not positive / not finite.
 void cholesky(double* H, int ldh, int n, int* info, cudaStream_t s);

@@ -39,11 +39,34 @@ inline double since(Clock::time_point t0) {
 
 constexpr double kDrop2 = 1e-16;   // drop a direction below 1e-8 of its norm
 
-// TDDFT_TRACE=1 prints one line per outer iteration to stderr (diagnostics).
-bool trace_on() {
+// TDDFT_TRACE=1 prints one line per outer iteration to stderr; TDDFT_TRACE=2
+// also times solver phases (stream-synchronised, so only for diagnostics).
+int trace_level() {
   static int v = -1;
-  if (v < 0) { const char* e = getenv("TDDFT_TRACE"); v = (e && e[0] == '1') ? 1 : 0; }
-  return v == 1;
+  if (v < 0) { const char* e = getenv("TDDFT_TRACE"); v = (e && e[0] >= '1' && e[0] <= '9') ? e[0] - '0' : 0; }
+  return v;
+}
+bool trace_on() { return trace_level() >= 1; }
+
+enum Phase { PH_MV = 0, PH_RIS, PH_ORTH, PH_PROJ, PH_SMALL, PH_VEC, PH_N };
+const char* kPhaseNames[PH_N] = {"exact_mv", "ris_mv", "orth", "proj+factor", "small_eig/solve", "vector_ops"};
+thread_local double g_phase[PH_N];
+struct ScopedPhase {
+  int id; cudaStream_t s; Clock::time_point t0; bool on;
+  ScopedPhase(int i, cudaStream_t st) : id(i), s(st), on(trace_level() >= 2) {
+    if (on) { cudaStreamSynchronize(s); t0 = Clock::now(); }
+  }
+  void stop() {
+    if (on) { cudaStreamSynchronize(s); g_phase[id] += since(t0); on = false; }
+  }
+  ~ScopedPhase() { stop(); }
+};
+void phase_report(const char* what) {
+  if (trace_level() < 2) return;
+  fprintf(stderr, "[tddft] phases %s:", what);
+  for (int i = 0; i < PH_N; ++i) fprintf(stderr, " %s=%.3fs", kPhaseNames[i], g_phase[i]);
+  fprintf(stderr, "\n");
+  for (int i = 0; i < PH_N; ++i) g_phase[i] = 0.0;
 }
 void trace(const char* what, int it, int N, const std::vector<double>& om, const std::vector<double>& rr) {
   if (!trace_on()) return;
@@ -74,37 +97,68 @@ struct Counters {
   int restarts = 0;
 };
 
-using TdaOp = std::function<void(const double* X, int m, double* out)>;
-using PairOp = std::function<void(const double* X, int m, double* P, double* M)>;
+template <typename T> constexpr DType dt_of();
+template <> constexpr DType dt_of<double>() { return DType::F64; }
+template <> constexpr DType dt_of<float>() { return DType::F32; }
+
+// Operators and preconditioners over vectors stored as T (double or float).
+template <typename T> using TdaOpT = std::function<void(const T* X, int m, T* out)>;
+template <typename T> using PairOpT = std::function<void(const T* X, int m, T* P, T* M)>;
 // TDA preconditioner: (R [nu][ov], shifts dev/host) -> out [nu][ov]
-using TdaPre = std::function<void(const double* R, const double* sh, const std::vector<double>& shh,
-                                  int nu, double* out)>;
+template <typename T>
+using TdaPreT = std::function<void(const T* R, const double* sh, const std::vector<double>& shh,
+                                   int nu, T* out)>;
 // paired preconditioner: (g+ , g-, shifts) -> (u, w) each [nu][ov]
-using PairPre = std::function<void(const double* gp, const double* gm, const double* sh,
-                                   const std::vector<double>& shh, int nu, double* u, double* w)>;
+template <typename T>
+using PairPreT = std::function<void(const T* gp, const T* gm, const double* sh,
+                                    const std::vector<double>& shh, int nu, T* u, T* w)>;
+using TdaOp = TdaOpT<double>;
+using PairOp = PairOpT<double>;
+using TdaPre = TdaPreT<double>;
+using PairPre = PairPreT<double>;
 
 // ---------------------------------------------------------------------------
-// Subspace helpers (FP64)
-
-// a[r][col0 + j] = V[r] . Wn[j]  for r < N, j < k
-void proj_cols(const double* V, int N, const double* Wn, int k, int ov, double* a, int ld, int col0,
-               cudaStream_t s) {
-  gemm_splitk_f64(N, k, ov, V, ov, 1, Wn, 1, ov, a + col0, ld, 1, 1.0, 0.0, s);
-}
+// Subspace helpers.  Vectors are FP64 (outer Davidson, PLAIN) or FP32 (MIXED
+// inner solves); every small matrix is FP64.
 
 // G[i][j] = A[i] . B[j]  (rows of length ov), G row stride ldg
-void gram(const double* A, int ka, const double* B, int kb, int ov, double* G, int ldg, cudaStream_t s) {
-  gemm_splitk_f64(ka, kb, ov, A, ov, 1, B, 1, ov, G, ldg, 1, 1.0, 0.0, s);
+template <typename T>
+void gram(const T* A, int ka, const T* B, int kb, int ov, double* G, int ldg, cudaStream_t s) {
+  GemmDesc g;
+  g.acc64 = sizeof(T) == 8;
+  g.M = ka; g.N = kb; g.K = ov;
+  g.A = A; g.ta = dt_of<T>(); g.sam = ov; g.sak = 1;
+  g.B = B; g.tb = dt_of<T>(); g.sbk = 1; g.sbn = ov;
+  g.C = G; g.tc = DType::F64; g.scm = ldg; g.scn = 1;
+  gemm_splitk(g, auto_splits(ka, kb, ov), s);
 }
 
-// out[j] = alpha * sum_r coef[j][r] V[r] + beta * out[j]   (coef row stride ldc)
-void combo(const double* coef, int ldc, int k, int N, const double* V, int ov, double* out,
-           double alpha, double beta, cudaStream_t s) {
+// a[r][col0 + j] = V[r] . Wn[j]  for r < N, j < k
+template <typename T>
+void proj_cols(const T* V, int N, const T* Wn, int k, int ov, double* a, int ld, int col0, cudaStream_t s) {
+  gram<T>(V, N, Wn, k, ov, a + col0, ld, s);
+}
+
+// FP64 small matrix as the A operand of a GEMM over T vectors
+template <typename T>
+const void* as_operand(const double* m, size_t n, DevBuf& tmp, cudaStream_t s) {
+  if (sizeof(T) == 8) return m;
+  tmp = DevBuf(n * 4, s);
+  convert(m, DType::F64, tmp.p, DType::F32, (long long)n, s);
+  return tmp.p;
+}
+
+// out[j] = alpha * sum_r coef[j][r] V[r] + beta * out[j]   (coef compact [k][N], FP64)
+template <typename T>
+void combo(const double* coef, int k, int N, const T* V, int ov, T* out, double alpha, double beta,
+           cudaStream_t s) {
+  DevBuf tmp;
   GemmDesc g;
+  g.acc64 = sizeof(T) == 8;
   g.M = k; g.N = ov; g.K = N;
-  g.A = coef; g.sam = ldc; g.sak = 1;
-  g.B = V; g.sbk = ov; g.sbn = 1;
-  g.C = out; g.scm = ov; g.scn = 1;
+  g.A = as_operand<T>(coef, (size_t)k * N, tmp, s); g.ta = dt_of<T>(); g.sam = N; g.sak = 1;
+  g.B = V; g.tb = dt_of<T>(); g.sbk = ov; g.sbn = 1;
+  g.C = out; g.tc = dt_of<T>(); g.scm = ov; g.scn = 1;
   g.alpha = alpha; g.beta = beta;
   gemm(g, s);
 }
@@ -122,41 +176,46 @@ void small_mm(int M, int N, int K, const double* A, long long sam, long long sak
 
 // Orthonormalise the candidate rows `cand` [nc][ov] against V (N rows) and each
 // other, two passes; append the survivors at V[N...].  Returns their number.
-int orth_append(double* V, int N, double* cand, int nc, int ov, cudaStream_t s) {
+template <typename T>
+int orth_append(T* V, int N, T* cand, int nc, int ov, cudaStream_t s) {
   if (nc <= 0) return 0;
+  ScopedPhase ph(PH_ORTH, s);
   TD_REQUIRE(nc <= 112, TDDFT_ERR_ARG, "too many new directions in one iteration");
-  DevBuf n0(nc * 8, s), ones(nc * 8, s), G((size_t)nc * nc * 8, s), T((size_t)nc * nc * 8, s);
-  DevBuf keep(nc * 4, s), tmp((size_t)nc * ov * 8, s);
+  DevBuf n0(nc * 8, s), ones(nc * 8, s), G((size_t)nc * nc * 8, s), Tm((size_t)nc * nc * 8, s);
+  DevBuf keep(nc * 4, s), tmp((size_t)nc * ov * sizeof(T), s);
   DevBuf coef(N > 0 ? (size_t)N * nc * 8 : 8, s);
-  row_sumsq(cand, ov, nc, ov, n0.as<double>(), s);
+  row_sumsq<T>(cand, ov, nc, ov, n0.as<double>(), s);
   h2d(ones.as<double>(), std::vector<double>(nc, 1.0), s);
-  double* cur = cand;
-  double* oth = tmp.as<double>();
+  T* cur = cand;
+  T* oth = tmp.as<T>();
   for (int pass = 0; pass < 2; ++pass) {
     if (N > 0) {
-      gram(V, N, cur, nc, ov, coef.as<double>(), nc, s);          // coef[r][j] = V[r].cur[j]
+      gram<T>(V, N, cur, nc, ov, coef.as<double>(), nc, s);       // coef[r][j] = V[r].cur[j]
+      DevBuf ct;
       GemmDesc g;                                                   // cur[j] -= sum_r coef[r][j] V[r]
+      g.acc64 = sizeof(T) == 8;
       g.M = nc; g.N = ov; g.K = N;
-      g.A = coef.p; g.sam = 1; g.sak = nc;
-      g.B = V; g.sbk = ov; g.sbn = 1;
-      g.C = cur; g.scm = ov; g.scn = 1;
+      g.A = as_operand<T>(coef.as<double>(), (size_t)N * nc, ct, s); g.ta = dt_of<T>();
+      g.sam = 1; g.sak = nc;
+      g.B = V; g.tb = dt_of<T>(); g.sbk = ov; g.sbn = 1;
+      g.C = cur; g.tc = dt_of<T>(); g.scm = ov; g.scn = 1;
       g.alpha = -1.0; g.beta = 1.0;
       gemm(g, s);
     }
-    gram(cur, nc, cur, nc, ov, G.as<double>(), nc, s);
+    gram<T>(cur, nc, cur, nc, ov, G.as<double>(), nc, s);
     chol_drop(G.as<double>(), nc, pass == 0 ? n0.as<double>() : ones.as<double>(), kDrop2,
-              T.as<double>(), keep.as<int>(), s);
-    combo(T.as<double>(), nc, nc, nc, cur, ov, oth, 1.0, 0.0, s);
+              Tm.as<double>(), keep.as<int>(), s);
+    combo<T>(Tm.as<double>(), nc, nc, cur, ov, oth, 1.0, 0.0, s);
     std::swap(cur, oth);
   }
   std::vector<int> kh = d2h(keep.as<int>(), nc, s);
   std::vector<int> idx;
-  for (int j = 0; j < nc; ++j)
+  for (int j = 0; j < nc && N + (int)idx.size() < ov; ++j)   // never beyond the space's dimension
     if (kh[j]) idx.push_back(j);
   if (!idx.empty()) {
     DevBuf di(idx.size() * 4, s);
     h2d(di.as<int>(), idx, s);
-    gather_rows(cur, di.as<int>(), (int)idx.size(), ov, V + (size_t)N * ov, s);
+    gather_rows<T>(cur, di.as<int>(), (int)idx.size(), ov, V + (size_t)N * ov, s);
   }
   return (int)idx.size();
 }
@@ -205,6 +264,7 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
   TD_REQUIRE(N >= 1, TDDFT_ERR_ARG, "initial guess is empty");
   auto mv = [&](int r0, int m) {
     auto t0 = Clock::now();
+    ScopedPhase ph(exact_op ? PH_MV : PH_RIS, s);
     A(Vp + (size_t)r0 * ov, m, Wp + (size_t)r0 * ov);
     TD_CUDA(cudaStreamSynchronize(s));
     if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
@@ -215,19 +275,26 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
   int kk = std::min(k, N);
   for (int it = 1; it <= max_iter; ++it) {
     o.n_iter = it;
-    proj_cols(Vp, N, Wp + (size_t)n_proj * ov, N - n_proj, ov, a.as<double>(), cap, n_proj, s);  // Eq. 1
-    sym_fill(a.as<double>(), cap, n_proj, N - n_proj, s);
+    {
+      ScopedPhase ph(PH_PROJ, s);
+      proj_cols(Vp, N, Wp + (size_t)n_proj * ov, N - n_proj, ov, a.as<double>(), cap, n_proj, s);  // Eq. 1
+      sym_fill(a.as<double>(), cap, n_proj, N - n_proj, s);
+    }
     n_proj = N;
     kk = std::min(k, N);
+    ScopedPhase ph_small(PH_SMALL, s);
     eig32(a.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);               // Eq. 2
     refine_lowest(a.as<double>(), cap, N, kk, lam32.as<float>(), vec32.as<float>(), lam.as<double>(),
                   x.as<double>(), scr.as<double>(), rounds, s);
-    combo(x.as<double>(), N, kk, N, Vp, ov, X.as<double>(), 1.0, 0.0, s);                // Eq. 3
-    combo(x.as<double>(), N, kk, N, Wp, ov, AX.as<double>(), 1.0, 0.0, s);
+    ph_small.stop();
+    ScopedPhase ph_vec(PH_VEC, s);
+    combo<double>(x.as<double>(), kk, N, Vp, ov, X.as<double>(), 1.0, 0.0, s);            // Eq. 3
+    combo<double>(x.as<double>(), kk, N, Wp, ov, AX.as<double>(), 1.0, 0.0, s);
     resid_tda(X.as<double>(), AX.as<double>(), lam.as<double>(), kk, ov, R.as<double>(), s);  // Eq. residual
     row_sumsq(R.as<double>(), ov, kk, ov, rn.as<double>(), s);
     om = d2h(lam.as<double>(), kk, s);
     rr = sqrt_all(d2h(rn.as<double>(), kk, s));
+    ph_vec.stop();
     check_finite_host(om, "Ritz values");
     check_finite_host(rr, "residual norms");
     trace(exact_op ? "tda" : "tda-guess", it, N, om, rr);
@@ -277,6 +344,7 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
 // Paired subspace algebra shared by the Casida eigenproblem and the paired
 // linear systems: a+ = V^T P, a- = V^T M, a- = L L^T, H = L^T a+ L.
 
+template <typename T>
 struct PairedSpace {
   int ov, cap;
   cudaStream_t s;
@@ -284,9 +352,9 @@ struct PairedSpace {
   int N = 0, n_old = 0, n_new = 0;
   DevBuf info;
   PairedSpace(int ov_, int cap_, cudaStream_t s_) : ov(ov_), cap(cap_), s(s_) {
-    V = DevBuf((size_t)cap * ov * 8, s);
-    P = DevBuf((size_t)cap * ov * 8, s);
-    M = DevBuf((size_t)cap * ov * 8, s);
+    V = DevBuf((size_t)cap * ov * sizeof(T), s);
+    P = DevBuf((size_t)cap * ov * sizeof(T), s);
+    M = DevBuf((size_t)cap * ov * sizeof(T), s);
     ap = DevBuf((size_t)cap * cap * 8, s);
     am = DevBuf((size_t)cap * cap * 8, s);
     L = DevBuf((size_t)cap * cap * 8, s);
@@ -296,13 +364,15 @@ struct PairedSpace {
     vec32 = DevBuf((size_t)cap * cap * 4, s);
     info = DevBuf(4, s);
   }
-  double* v() { return V.as<double>(); }
-  double* p() { return P.as<double>(); }
-  double* m() { return M.as<double>(); }
-  // project the new vectors, factor, form H and its FP32 decomposition
-  void update() {
-    proj_cols(v(), N, p() + (size_t)n_old * ov, n_new, ov, ap.as<double>(), cap, n_old, s);
-    proj_cols(v(), N, m() + (size_t)n_old * ov, n_new, ov, am.as<double>(), cap, n_old, s);
+  T* v() { return V.as<T>(); }
+  T* p() { return P.as<T>(); }
+  T* m() { return M.as<T>(); }
+  // project the new vectors, factor a- = L L^T, form H = L^T a+ L (and, for the
+  // eigenproblem, its FP32 decomposition)
+  void update(bool eig) {
+    ScopedPhase ph(PH_PROJ, s);
+    proj_cols<T>(v(), N, p() + (size_t)n_old * ov, n_new, ov, ap.as<double>(), cap, n_old, s);
+    proj_cols<T>(v(), N, m() + (size_t)n_old * ov, n_new, ov, am.as<double>(), cap, n_old, s);
     sym_fill(ap.as<double>(), cap, n_old, n_new, s);
     sym_fill(am.as<double>(), cap, n_old, n_new, s);
     TD_CUDA(cudaMemcpyAsync(L.p, am.p, (size_t)cap * cap * 8, cudaMemcpyDeviceToDevice, s));
@@ -310,7 +380,7 @@ struct PairedSpace {
     // tmp = a+ L ; H = L^T tmp
     small_mm(N, N, N, ap.as<double>(), cap, 1, L.as<double>(), cap, 1, tmp.as<double>(), cap, s);
     small_mm(N, N, N, L.as<double>(), 1, cap, tmp.as<double>(), cap, 1, H.as<double>(), cap, s);
-    eig32(H.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);
+    if (eig) eig32(H.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);
     n_old = N;
     n_new = 0;
   }
@@ -333,14 +403,17 @@ struct PairedLinOut {
   std::vector<double> resid;
 };
 
-PairedLinOut paired_linear(int ov, const PairOp& op, const PairPre& pre, const double* gp,
-                           const double* gm, const std::vector<double>& shifts, int nr,
-                           double* init, int ni, double tol, int max_iter, int cap, int nref,
-                           bool exact_op, Counters& cnt, double* Uout, double* Wout,
-                           cudaStream_t s) {
+// The small shifted systems are solved by LU per shift: FP64 for the outer
+// polarizability and PLAIN solves, FP32 (lu_fp32) for the MIXED inner solves.
+template <typename T>
+PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre, const T* gp,
+                           const T* gm, const std::vector<double>& shifts, int nr, T* init, int ni,
+                           double tol, int max_iter, int cap, bool lu_fp32, bool exact_op,
+                           Counters& cnt, T* Uout, T* Wout, cudaStream_t s) {
   PairedLinOut o;
   cap = std::min(cap, kSmallMax);
-  PairedSpace sp(ov, cap, s);
+  constexpr size_t es = sizeof(T);
+  PairedSpace<T> sp(ov, cap, s);
   DevBuf sh(nr * 8, s), sig2(nr * 8, s);
   std::vector<double> s2(nr);
   for (int r = 0; r < nr; ++r) s2[r] = shifts[r] * shifts[r];
@@ -348,30 +421,31 @@ PairedLinOut paired_linear(int ov, const PairOp& op, const PairPre& pre, const d
   h2d(sig2.as<double>(), s2, s);
   DevBuf hp((size_t)nr * cap * 8, s), hm((size_t)nr * cap * 8, s), rhs((size_t)nr * cap * 8, s);
   DevBuf ut((size_t)nr * cap * 8, s), uc((size_t)nr * cap * 8, s), wc((size_t)nr * cap * 8, s);
-  DevBuf Rp((size_t)nr * ov * 8, s), Rm((size_t)nr * ov * 8, s), PU((size_t)nr * ov * 8, s),
-      MW((size_t)nr * ov * 8, s);
+  DevBuf Rp((size_t)nr * ov * es, s), Rm((size_t)nr * ov * es, s), PU((size_t)nr * ov * es, s),
+      MW((size_t)nr * ov * es, s);
   DevBuf gn(nr * 8, s), gn2(nr * 8, s), rn1(nr * 8, s), rn2(nr * 8, s);
-  DevBuf iu(nr * 4, s), shu(nr * 8, s), gpu_(((size_t)nr) * ov * 8, s), gmu((size_t)nr * ov * 8, s);
-  DevBuf cand((size_t)2 * nr * ov * 8, s);
+  DevBuf iu(nr * 4, s), shu(nr * 8, s), gpu_(((size_t)nr) * ov * es, s), gmu((size_t)nr * ov * es, s);
+  DevBuf cand((size_t)2 * nr * ov * es, s);
   DevBuf Uprev, Wprev;
   bool have_prev = false;
   if (exact_op) {
-    Uprev = DevBuf((size_t)nr * ov * 8, s);
-    Wprev = DevBuf((size_t)nr * ov * 8, s);
+    Uprev = DevBuf((size_t)nr * ov * es, s);
+    Wprev = DevBuf((size_t)nr * ov * es, s);
   }
-  row_sumsq(gp, ov, nr, ov, gn.as<double>(), s);
+  row_sumsq<T>(gp, ov, nr, ov, gn.as<double>(), s);
   std::vector<double> gnh = d2h(gn.as<double>(), nr, s);
   if (gm) {
-    row_sumsq(gm, ov, nr, ov, gn2.as<double>(), s);
+    row_sumsq<T>(gm, ov, nr, ov, gn2.as<double>(), s);
     std::vector<double> t = d2h(gn2.as<double>(), nr, s);
     for (int r = 0; r < nr; ++r) gnh[r] += t[r];
   }
   for (auto& v : gnh) v = std::sqrt(v);
 
-  sp.N = orth_append(sp.v(), 0, init, std::min(ni, cap), ov, s);
+  sp.N = orth_append<T>(sp.v(), 0, init, std::min(ni, cap), ov, s);
   TD_REQUIRE(sp.N >= 1, TDDFT_ERR_ARG, "paired solve: empty initial subspace");
   auto mv = [&](int r0, int m) {
     auto t0 = Clock::now();
+    ScopedPhase ph(exact_op ? PH_MV : PH_RIS, s);
     op(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
     TD_CUDA(cudaStreamSynchronize(s));
     if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
@@ -382,37 +456,42 @@ PairedLinOut paired_linear(int ov, const PairOp& op, const PairPre& pre, const d
   std::vector<double> rr(nr, 0.0);
   for (int it = 1; it <= max_iter; ++it) {
     o.n_iter = it;
-    sp.update();
+    sp.update(false);
     sp.check_definite();
     const int N = sp.N;
-    double* Lp = sp.L.as<double>();
+    double* Lp = sp.L.template as<double>();
+    ScopedPhase ph_small(PH_SMALL, s);
     // h+ = V g+ , h- = V g-   ([nr][N])
-    gram(gp, nr, sp.v(), N, ov, hp.as<double>(), N, s);
+    gram<T>(gp, nr, sp.v(), N, ov, hp.as<double>(), N, s);
     // rhs = L^T h+  (rows): rhs[r][i] = sum_q h+[r][q] L[q][i]
     small_mm(nr, N, N, hp.as<double>(), N, 1, Lp, cap, 1, rhs.as<double>(), N, s);
     if (gm) {
-      gram(gm, nr, sp.v(), N, ov, hm.as<double>(), N, s);
+      gram<T>(gm, nr, sp.v(), N, ov, hm.as<double>(), N, s);
       trsv_rows(Lp, cap, N, hm.as<double>(), nr, 0, s);                 // z- = L^-1 h-
-      axpy_rows(rhs.as<double>(), hm.as<double>(), sh.as<double>(), nr, N, s);
+      axpy_rows<double>(rhs.as<double>(), hm.as<double>(), sh.as<double>(), nr, N, s);
     }
-    shifted_solve(sp.H.as<double>(), cap, N, sp.lam32.as<float>(), sp.vec32.as<float>(),
-                  sig2.as<double>(), nr, rhs.as<double>(), ut.as<double>(), nref, s);
+    // (H - s^2) u~ = rhs for every shift
+    lu_shift_solve(sp.H.template as<double>(), cap, N, sig2.as<double>(), nr, rhs.as<double>(), ut.as<double>(),
+                   lu_fp32, s);
     // u = L u~ : u[r][i] = sum_q L[i][q] u~[r][q]
     small_mm(nr, N, N, ut.as<double>(), N, 1, Lp, 1, cap, uc.as<double>(), N, s);
     // w = L^-T (z- + s u~)
     if (gm) TD_CUDA(cudaMemcpyAsync(wc.p, hm.p, (size_t)nr * N * 8, cudaMemcpyDeviceToDevice, s));
     else TD_CUDA(cudaMemsetAsync(wc.p, 0, (size_t)nr * N * 8, s));
-    axpy_rows(wc.as<double>(), ut.as<double>(), sh.as<double>(), nr, N, s);
+    axpy_rows<double>(wc.as<double>(), ut.as<double>(), sh.as<double>(), nr, N, s);
     trsv_rows(Lp, cap, N, wc.as<double>(), nr, 1, s);
-    combo(uc.as<double>(), N, nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
-    combo(wc.as<double>(), N, nr, N, sp.v(), ov, Wout, 1.0, 0.0, s);
-    combo(uc.as<double>(), N, nr, N, sp.p(), ov, PU.as<double>(), 1.0, 0.0, s);
-    combo(wc.as<double>(), N, nr, N, sp.m(), ov, MW.as<double>(), 1.0, 0.0, s);
-    resid_paired(Uout, Wout, PU.as<double>(), MW.as<double>(), sh.as<double>(), gp, gm, nr, ov,
-                 Rp.as<double>(), Rm.as<double>(), s);
-    row_sumsq(Rp.as<double>(), ov, nr, ov, rn1.as<double>(), s);
-    row_sumsq(Rm.as<double>(), ov, nr, ov, rn2.as<double>(), s);
+    ph_small.stop();
+    ScopedPhase ph_vec(PH_VEC, s);
+    combo<T>(uc.as<double>(), nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
+    combo<T>(wc.as<double>(), nr, N, sp.v(), ov, Wout, 1.0, 0.0, s);
+    combo<T>(uc.as<double>(), nr, N, sp.p(), ov, PU.as<T>(), 1.0, 0.0, s);
+    combo<T>(wc.as<double>(), nr, N, sp.m(), ov, MW.as<T>(), 1.0, 0.0, s);
+    resid_paired<T>(Uout, Wout, PU.as<T>(), MW.as<T>(), sh.as<double>(), gp, gm, nr, ov,
+                    Rp.as<T>(), Rm.as<T>(), s);
+    row_sumsq<T>(Rp.as<T>(), ov, nr, ov, rn1.as<double>(), s);
+    row_sumsq<T>(Rm.as<T>(), ov, nr, ov, rn2.as<double>(), s);
     std::vector<double> a1 = d2h(rn1.as<double>(), nr, s), a2 = d2h(rn2.as<double>(), nr, s);
+    ph_vec.stop();
     std::vector<int> todo;
     for (int r = 0; r < nr; ++r) {
       rr[r] = std::sqrt(a1[r] + a2[r]) / (gnh[r] > 0 ? gnh[r] : 1.0);
@@ -427,39 +506,38 @@ PairedLinOut paired_linear(int ov, const PairOp& op, const PairPre& pre, const d
     for (int j = 0; j < nu; ++j) shh[j] = shifts[todo[j]];
     h2d(iu.as<int>(), todo, s);
     h2d(shu.as<double>(), shh, s);
-    gather_rows(Rp.as<double>(), iu.as<int>(), nu, ov, gpu_.as<double>(), s);
-    gather_rows(Rm.as<double>(), iu.as<int>(), nu, ov, gmu.as<double>(), s);
+    gather_rows<T>(Rp.as<T>(), iu.as<int>(), nu, ov, gpu_.as<T>(), s);
+    gather_rows<T>(Rm.as<T>(), iu.as<int>(), nu, ov, gmu.as<T>(), s);
     auto tp = Clock::now();
-    pre(gpu_.as<double>(), gmu.as<double>(), shu.as<double>(), shh, nu, cand.as<double>(),
-        cand.as<double>() + (size_t)nu * ov);
+    pre(gpu_.as<T>(), gmu.as<T>(), shu.as<double>(), shh, nu, cand.as<T>(), cand.as<T>() + (size_t)nu * ov);
     TD_CUDA(cudaStreamSynchronize(s));
     cnt.t_pre += since(tp);
     if (sp.N + 2 * nu > cap) {
       if (!exact_op) break;   // inner solve: return the current approximate solution
       // thick restart from the current and the previous solutions of every system
       const int nprev = (have_prev && 4 * nr <= 112) ? 2 * nr : 0;
-      DevBuf rst((size_t)4 * nr * ov * 8, s);
-      TD_CUDA(cudaMemcpyAsync(rst.p, Uout, (size_t)nr * ov * 8, cudaMemcpyDeviceToDevice, s));
-      TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)nr * ov, Wout, (size_t)nr * ov * 8,
+      DevBuf rst((size_t)4 * nr * ov * es, s);
+      TD_CUDA(cudaMemcpyAsync(rst.p, Uout, (size_t)nr * ov * es, cudaMemcpyDeviceToDevice, s));
+      TD_CUDA(cudaMemcpyAsync(rst.as<T>() + (size_t)nr * ov, Wout, (size_t)nr * ov * es,
                               cudaMemcpyDeviceToDevice, s));
       if (nprev) {
-        TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)2 * nr * ov, Uprev.p, (size_t)nr * ov * 8,
+        TD_CUDA(cudaMemcpyAsync(rst.as<T>() + (size_t)2 * nr * ov, Uprev.p, (size_t)nr * ov * es,
                                 cudaMemcpyDeviceToDevice, s));
-        TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)3 * nr * ov, Wprev.p, (size_t)nr * ov * 8,
+        TD_CUDA(cudaMemcpyAsync(rst.as<T>() + (size_t)3 * nr * ov, Wprev.p, (size_t)nr * ov * es,
                                 cudaMemcpyDeviceToDevice, s));
       }
-      sp.N = orth_append(sp.v(), 0, rst.as<double>(), 2 * nr + nprev, ov, s);
+      sp.N = orth_append<T>(sp.v(), 0, rst.as<T>(), 2 * nr + nprev, ov, s);
       mv(0, sp.N);
       sp.n_old = 0;
       sp.n_new = sp.N;
       cnt.restarts++;
     }
     if (exact_op) {
-      TD_CUDA(cudaMemcpyAsync(Uprev.p, Uout, (size_t)nr * ov * 8, cudaMemcpyDeviceToDevice, s));
-      TD_CUDA(cudaMemcpyAsync(Wprev.p, Wout, (size_t)nr * ov * 8, cudaMemcpyDeviceToDevice, s));
+      TD_CUDA(cudaMemcpyAsync(Uprev.p, Uout, (size_t)nr * ov * es, cudaMemcpyDeviceToDevice, s));
+      TD_CUDA(cudaMemcpyAsync(Wprev.p, Wout, (size_t)nr * ov * es, cudaMemcpyDeviceToDevice, s));
       have_prev = true;
     }
-    int nacc = orth_append(sp.v(), sp.N, cand.as<double>(), 2 * nu, ov, s);
+    int nacc = orth_append<T>(sp.v(), sp.N, cand.as<T>(), 2 * nu, ov, s);
     if (nacc == 0) break;
     mv(sp.N, nacc);
     sp.n_new += nacc;
@@ -487,7 +565,7 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
   cap = std::min(cap, kSmallMax);
   TD_REQUIRE(k >= 1 && k <= kWantMax, TDDFT_ERR_ARG, "n_states out of range");
   TD_REQUIRE(cap >= 4 * k, TDDFT_ERR_ARG, "max_subspace must be at least 4*n_states");
-  PairedSpace sp(ov, cap, s);
+  PairedSpace<double> sp(ov, cap, s);
   DevBuf lamH(k * 8, s), y((size_t)k * cap * 8, s), scr((size_t)2 * k * cap * 8, s);
   DevBuf uc((size_t)k * cap * 8, s), wc((size_t)k * cap * 8, s), isq(k * 8, s), iom(k * 8, s),
       omd(k * 8, s);
@@ -502,6 +580,7 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
   TD_REQUIRE(sp.N >= 1, TDDFT_ERR_ARG, "initial guess is empty");
   auto mv = [&](int r0, int m) {
     auto t0 = Clock::now();
+    ScopedPhase ph(exact_op ? PH_MV : PH_RIS, s);
     op(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
     TD_CUDA(cudaStreamSynchronize(s));
     if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
@@ -513,13 +592,15 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
   int kk = k;
   for (int it = 1; it <= max_iter; ++it) {
     o.n_iter = it;
-    sp.update();
+    sp.update(true);
     sp.check_definite();
     const int N = sp.N;
     kk = std::min(k, N);
-    double* Lp = sp.L.as<double>();
-    refine_lowest(sp.H.as<double>(), cap, N, kk, sp.lam32.as<float>(), sp.vec32.as<float>(),
+    double* Lp = sp.L.template as<double>();
+    ScopedPhase ph_small(PH_SMALL, s);
+    refine_lowest(sp.H.template as<double>(), cap, N, kk, sp.lam32.template as<float>(), sp.vec32.template as<float>(),
                   lamH.as<double>(), y.as<double>(), scr.as<double>(), rounds, s);
+    ph_small.stop();
     std::vector<double> l2 = d2h(lamH.as<double>(), kk, s);
     check_finite_host(l2, "Casida Ritz values");
     if (!(l2[0] > 0.0))
@@ -536,13 +617,13 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
     // u = L y / sqrt(Omega) ; w = a+ u / Omega
     small_mm(kk, N, N, y.as<double>(), N, 1, Lp, 1, cap, uc.as<double>(), N, s);
     scale_rows(uc.as<double>(), isq.as<double>(), kk, N, s);
-    small_mm(kk, N, N, uc.as<double>(), N, 1, sp.ap.as<double>(), cap, 1, wc.as<double>(), N, s);
+    small_mm(kk, N, N, uc.as<double>(), N, 1, sp.ap.template as<double>(), cap, 1, wc.as<double>(), N, s);
     scale_rows(wc.as<double>(), iom.as<double>(), kk, N, s);
-    combo(uc.as<double>(), N, kk, N, sp.v(), ov, U.as<double>(), 1.0, 0.0, s);
-    combo(wc.as<double>(), N, kk, N, sp.v(), ov, W.as<double>(), 1.0, 0.0, s);
-    combo(uc.as<double>(), N, kk, N, sp.p(), ov, PU.as<double>(), 1.0, 0.0, s);
-    combo(wc.as<double>(), N, kk, N, sp.m(), ov, MW.as<double>(), 1.0, 0.0, s);
-    resid_paired(U.as<double>(), W.as<double>(), PU.as<double>(), MW.as<double>(), omd.as<double>(),
+    combo<double>(uc.as<double>(), kk, N, sp.v(), ov, U.as<double>(), 1.0, 0.0, s);
+    combo<double>(wc.as<double>(), kk, N, sp.v(), ov, W.as<double>(), 1.0, 0.0, s);
+    combo<double>(uc.as<double>(), kk, N, sp.p(), ov, PU.as<double>(), 1.0, 0.0, s);
+    combo<double>(wc.as<double>(), kk, N, sp.m(), ov, MW.as<double>(), 1.0, 0.0, s);
+    resid_paired<double>(U.as<double>(), W.as<double>(), PU.as<double>(), MW.as<double>(), omd.as<double>(),
                  nullptr, nullptr, kk, ov, Rp.as<double>(), Rm.as<double>(), s);
     row_sumsq(Rp.as<double>(), ov, kk, ov, rn1.as<double>(), s);
     row_sumsq(Rm.as<double>(), ov, kk, ov, rn2.as<double>(), s);
@@ -607,35 +688,39 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
 
 // (T - s_n) v_n = R_n by one block Galerkin subspace, diag-preconditioned
 // expansion, stopped at |res_n| <= tol |R_n| or max_iter iterations.
-void inner_tda(int ov, const TdaOp& T, const double* delta, const double* R, const double* sh,
-               const std::vector<double>& shh, int nu, double tol, int max_iter, int nref,
-               Counters& cnt, double* out, cudaStream_t s) {
+template <typename T>
+void inner_tda(int ov, const TdaOpT<T>& Top, const double* delta, const T* R, const double* sh,
+               const std::vector<double>& shh, int nu, double tol, int max_iter, bool lu_fp32,
+               Counters& cnt, T* out, cudaStream_t s) {
   const int cap = kSmallMax;
-  DevBuf S((size_t)cap * ov * 8, s), TS((size_t)cap * ov * 8, s), t((size_t)cap * cap * 8, s);
-  DevBuf lam32(cap * 4, s), vec32((size_t)cap * cap * 4, s), h((size_t)nu * cap * 8, s),
-      y((size_t)nu * cap * 8, s);
-  DevBuf Tv((size_t)nu * ov * 8, s), res((size_t)nu * ov * 8, s), rn(nu * 8, s), r0(nu * 8, s);
-  DevBuf cand((size_t)nu * ov * 8, s), iu(nu * 4, s), shu(nu * 8, s), resu((size_t)nu * ov * 8, s);
-  row_sumsq(R, ov, nu, ov, r0.as<double>(), s);
+  constexpr size_t es = sizeof(T);
+  DevBuf S((size_t)cap * ov * es, s), TS((size_t)cap * ov * es, s), t((size_t)cap * cap * 8, s);
+  DevBuf h((size_t)nu * cap * 8, s), y((size_t)nu * cap * 8, s);
+  DevBuf Tv((size_t)nu * ov * es, s), res((size_t)nu * ov * es, s), rn(nu * 8, s), r0(nu * 8, s);
+  DevBuf cand((size_t)nu * ov * es, s), iu(nu * 4, s), shu(nu * 8, s), resu((size_t)nu * ov * es, s);
+  row_sumsq<T>(R, ov, nu, ov, r0.as<double>(), s);
   std::vector<double> r0h = sqrt_all(d2h(r0.as<double>(), nu, s));
-  precond_tda(R, sh, delta, nu, ov, cand.as<double>(), s);
-  int N = orth_append(S.as<double>(), 0, cand.as<double>(), nu, ov, s);
-  if (N == 0) { TD_CUDA(cudaMemsetAsync(out, 0, (size_t)nu * ov * 8, s)); return; }
-  T(S.as<double>(), N, TS.as<double>());
+  precond_tda<T>(R, sh, delta, nu, ov, cand.as<T>(), s);
+  int N = orth_append<T>(S.as<T>(), 0, cand.as<T>(), nu, ov, s);
+  if (N == 0) { TD_CUDA(cudaMemsetAsync(out, 0, (size_t)nu * ov * es, s)); return; }
+  {
+    ScopedPhase ph(PH_RIS, s);
+    Top(S.as<T>(), N, TS.as<T>());
+  }
   cnt.ris_mv += N;
   int n_old = 0, n_new = N;
   for (int it = 0; it < max_iter; ++it) {
-    proj_cols(S.as<double>(), N, TS.as<double>() + (size_t)n_old * ov, n_new, ov, t.as<double>(), cap,
-              n_old, s);
+    proj_cols<T>(S.as<T>(), N, TS.as<T>() + (size_t)n_old * ov, n_new, ov, t.as<double>(), cap, n_old, s);
     sym_fill(t.as<double>(), cap, n_old, n_new, s);
-    gram(R, nu, S.as<double>(), N, ov, h.as<double>(), N, s);           // h[n][r] = R_n . S_r
-    eig32(t.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);
-    shifted_solve(t.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), sh, nu,
-                  h.as<double>(), y.as<double>(), nref, s);
-    combo(y.as<double>(), N, nu, N, S.as<double>(), ov, out, 1.0, 0.0, s);
-    combo(y.as<double>(), N, nu, N, TS.as<double>(), ov, Tv.as<double>(), 1.0, 0.0, s);
-    resid_shift(Tv.as<double>(), out, sh, R, nu, ov, res.as<double>(), s);
-    row_sumsq(res.as<double>(), ov, nu, ov, rn.as<double>(), s);
+    gram<T>(R, nu, S.as<T>(), N, ov, h.as<double>(), N, s);           // h[n][r] = R_n . S_r
+    {
+      ScopedPhase ph(PH_SMALL, s);
+      lu_shift_solve(t.as<double>(), cap, N, sh, nu, h.as<double>(), y.as<double>(), lu_fp32, s);
+    }
+    combo<T>(y.as<double>(), nu, N, S.as<T>(), ov, out, 1.0, 0.0, s);
+    combo<T>(y.as<double>(), nu, N, TS.as<T>(), ov, Tv.as<T>(), 1.0, 0.0, s);
+    resid_shift<T>(Tv.as<T>(), out, sh, R, nu, ov, res.as<T>(), s);
+    row_sumsq<T>(res.as<T>(), ov, nu, ov, rn.as<double>(), s);
     std::vector<double> rh = sqrt_all(d2h(rn.as<double>(), nu, s));
     std::vector<int> todo;
     for (int j = 0; j < nu; ++j)
@@ -646,12 +731,15 @@ void inner_tda(int ov, const TdaOp& T, const double* delta, const double* R, con
     for (int j = 0; j < m; ++j) sm[j] = shh[todo[j]];
     h2d(iu.as<int>(), todo, s);
     h2d(shu.as<double>(), sm, s);
-    gather_rows(res.as<double>(), iu.as<int>(), m, ov, resu.as<double>(), s);
-    precond_tda(resu.as<double>(), shu.as<double>(), delta, m, ov, cand.as<double>(), s);
+    gather_rows<T>(res.as<T>(), iu.as<int>(), m, ov, resu.as<T>(), s);
+    precond_tda<T>(resu.as<T>(), shu.as<double>(), delta, m, ov, cand.as<T>(), s);
     if (N + m > cap) break;
-    int nacc = orth_append(S.as<double>(), N, cand.as<double>(), m, ov, s);
+    int nacc = orth_append<T>(S.as<T>(), N, cand.as<T>(), m, ov, s);
     if (nacc == 0) break;
-    T(S.as<double>() + (size_t)N * ov, nacc, TS.as<double>() + (size_t)N * ov);
+    {
+      ScopedPhase ph(PH_RIS, s);
+      Top(S.as<T>() + (size_t)N * ov, nacc, TS.as<T>() + (size_t)N * ov);
+    }
     cnt.ris_mv += nacc;
     n_old = N;
     n_new = nacc;
@@ -746,9 +834,21 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
   TdaPre diag = [&](const double* R, const double* sh, const std::vector<double>&, int nu, double* out) {
     precond_tda(R, sh, c.delta.as<double>(), nu, ov, out, s);
   };
+  TdaOpT<float> T32 = [&](const float* Xi, int m, float* out) {
+    apply_operator(dims, Fr, Xi, m, OpMode::TDA, out, nullptr, false, s);
+  };
   TdaPre rid = [&](const double* R, const double* sh, const std::vector<double>& shh, int nu, double* out) {
-    inner_tda(ov, T, c.delta.as<double>(), R, sh, shh, nu, p.inner_tol, p.inner_max_iter,
-              p.nref_inner, cnt, out, s);
+    if (p.mixed) {   // FP32 inner solve on the BF16 ris factors
+      const long long n = (long long)nu * ov;
+      DevBuf R32(n * 4, s), o32(n * 4, s);
+      convert(R, DType::F64, R32.p, DType::F32, n, s);
+      inner_tda<float>(ov, T32, c.delta.as<double>(), R32.as<float>(), sh, shh, nu, p.inner_tol,
+                       p.inner_max_iter, true, cnt, o32.as<float>(), s);
+      convert(o32.p, DType::F32, out, DType::F64, n, s);
+    } else {
+      inner_tda<double>(ov, T, c.delta.as<double>(), R, sh, shh, nu, p.inner_tol, p.inner_max_iter,
+                        false, cnt, out, s);
+    }
   };
   // initial guess (Sec. 2.1: low-lying eigenvectors of T)
   DevBuf guess;
@@ -791,6 +891,7 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
   copy_out(X, r.X.as<double>(), (size_t)p.k * ov, dev, s);
   TD_CUDA(cudaStreamSynchronize(s));
   check_tc_error(c);
+  phase_report("solve");
   fill_stats(st, r.n_iter, cnt, r.converged, r.resid, cert, t0);
   return r.converged ? TDDFT_OK : TDDFT_ERR_NOCONV;
 }
@@ -800,6 +901,38 @@ PairOp make_pair_op(const OpDims& dims, const FactorSet& F, bool tc, cudaStream_
   return [dims, F, tc, s](const double* Xi, int m, double* P, double* M) {
     apply_operator(dims, F, Xi, m, OpMode::PAIRED, P, M, tc, s);
   };
+}
+PairOpT<float> make_pair_op32(const OpDims& dims, const FactorSet& F, cudaStream_t s) {
+  return [dims, F, s](const float* Xi, int m, float* P, float* M) {
+    apply_operator(dims, F, Xi, m, OpMode::PAIRED, P, M, false, s);
+  };
+}
+
+// The rid preconditioner for the paired systems: the ris system T+ u - s w = g+,
+// T- w - s u = g- solved to inner_tol; FP32 vectors on the BF16 ris factors in
+// MIXED solves, FP64 in PLAIN solves.
+void rid_paired(int ov, const Plan& p, const PairOp& T, const PairPre& diag, const PairOpT<float>& T32,
+                const PairPreT<float>& diag32, const double* dl, const double* gp, const double* gm,
+                const double* sh, const std::vector<double>& shh, int nu, Counters& cnt, double* u,
+                double* w, cudaStream_t s) {
+  const long long n = (long long)nu * ov;
+  if (p.mixed) {
+    DevBuf g32((size_t)2 * n * 4, s), init((size_t)2 * n * 4, s), uw((size_t)2 * n * 4, s);
+    convert(gp, DType::F64, g32.p, DType::F32, n, s);
+    convert(gm, DType::F64, g32.as<float>() + n, DType::F32, n, s);
+    precond_paired<float>(g32.as<float>(), g32.as<float>() + n, sh, dl, nu, ov, init.as<float>(),
+                          init.as<float>() + n, s);
+    paired_linear<float>(ov, T32, diag32, g32.as<float>(), g32.as<float>() + n, shh, nu, init.as<float>(),
+                         2 * nu, p.inner_tol, p.inner_max_iter, kSmallMax, true, false, cnt,
+                         uw.as<float>(), uw.as<float>() + n, s);
+    convert(uw.p, DType::F32, u, DType::F64, n, s);
+    convert(uw.as<float>() + n, DType::F32, w, DType::F64, n, s);
+  } else {
+    DevBuf init((size_t)2 * n * 8, s);
+    precond_paired<double>(gp, gm, sh, dl, nu, ov, init.as<double>(), init.as<double>() + n, s);
+    paired_linear<double>(ov, T, diag, gp, gm, shh, nu, init.as<double>(), 2 * nu, p.inner_tol,
+                          p.inner_max_iter, kSmallMax, false, false, cnt, u, w, s);
+  }
 }
 }  // namespace
 
@@ -817,12 +950,14 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
   const double* dl = c.delta.as<double>();
   PairPre diag = [&](const double* gp, const double* gm, const double* sh, const std::vector<double>&,
                      int nu, double* u, double* w) { precond_paired(gp, gm, sh, dl, nu, ov, u, w, s); };
+  PairOpT<float> T32 = make_pair_op32(dims, c.ris(o.precision), s);
+  PairPreT<float> diag32 = [&](const float* gp, const float* gm, const double* sh,
+                               const std::vector<double>&, int nu, float* u, float* w) {
+    precond_paired<float>(gp, gm, sh, dl, nu, ov, u, w, s);
+  };
   PairPre rid = [&](const double* gp, const double* gm, const double* sh,
                     const std::vector<double>& shh, int nu, double* u, double* w) {
-    DevBuf init((size_t)2 * nu * ov * 8, s);
-    precond_paired(gp, gm, sh, dl, nu, ov, init.as<double>(), init.as<double>() + (size_t)nu * ov, s);
-    paired_linear(ov, T, diag, gp, gm, shh, nu, init.as<double>(), 2 * nu, p.inner_tol,
-                  p.inner_max_iter, kSmallMax, p.nref_inner, false, cnt, u, w, s);
+    rid_paired(ov, p, T, diag, T32, diag32, dl, gp, gm, sh, shh, nu, cnt, u, w, s);
   };
   DevBuf guess;
   int ng = p.k0;
@@ -855,7 +990,7 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     apply_operator(dims, Fc, r.U.as<double>(), k, OpMode::PAIRED, PU.as<double>(), MU.as<double>(), false, s);
     apply_operator(dims, Fc, r.W.as<double>(), k, OpMode::PAIRED, PW.as<double>(), MW.as<double>(), false, s);
     h2d(om.as<double>(), r.omega, s);
-    resid_paired(r.U.as<double>(), r.W.as<double>(), PU.as<double>(), MW.as<double>(), om.as<double>(),
+    resid_paired<double>(r.U.as<double>(), r.W.as<double>(), PU.as<double>(), MW.as<double>(), om.as<double>(),
                  nullptr, nullptr, k, ov, Rp.as<double>(), Rm.as<double>(), s);
     row_sumsq(Rp.as<double>(), ov, k, ov, a1.as<double>(), s);
     row_sumsq(Rm.as<double>(), ov, k, ov, a2.as<double>(), s);
@@ -880,6 +1015,7 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
   }
   TD_CUDA(cudaStreamSynchronize(s));
   check_tc_error(c);
+  phase_report("solve");
   fill_stats(st, r.n_iter, cnt, r.converged, r.resid, cert, t0);
   return r.converged ? TDDFT_OK : TDDFT_ERR_NOCONV;
 }
@@ -919,30 +1055,45 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
     axpy_rows(b.as<double>() + (size_t)f * n_dip * ov, mud.as<double>(), twod.as<double>(), n_dip, ov, s);
   PairPre diag = [&](const double* gp, const double* gm, const double* shv, const std::vector<double>&,
                      int nu, double* u, double* w) { precond_paired(gp, gm, shv, dl, nu, ov, u, w, s); };
+  PairOpT<float> T32 = make_pair_op32(dims, c.ris(o.precision), s);
+  PairPreT<float> diag32 = [&](const float* gp, const float* gm, const double* shv,
+                               const std::vector<double>&, int nu, float* u, float* w) {
+    precond_paired<float>(gp, gm, shv, dl, nu, ov, u, w, s);
+  };
   PairPre rid = [&](const double* gp, const double* gm, const double* shv,
                     const std::vector<double>& shh, int nu, double* u, double* w) {
-    DevBuf init((size_t)2 * nu * ov * 8, s);
-    precond_paired(gp, gm, shv, dl, nu, ov, init.as<double>(), init.as<double>() + (size_t)nu * ov, s);
-    paired_linear(ov, T, diag, gp, gm, shh, nu, init.as<double>(), 2 * nu, p.inner_tol,
-                  p.inner_max_iter, kSmallMax, p.nref_inner, false, cnt, u, w, s);
+    rid_paired(ov, p, T, diag, T32, diag32, dl, gp, gm, shv, shh, nu, cnt, u, w, s);
   };
   // initial directions
   DevBuf init((size_t)2 * nr * ov * 8, s);
   double* iu = init.as<double>();
   double* iw = iu + (size_t)nr * ov;
   if (p.precond == TDDFT_PRECOND_RID) {
-    DevBuf d0((size_t)2 * nr * ov * 8, s);
-    precond_paired(b.as<double>(), nullptr, shd.as<double>(), dl, nr, ov, d0.as<double>(),
-                   d0.as<double>() + (size_t)nr * ov, s);
-    paired_linear(ov, T, diag, b.as<double>(), nullptr, sh, nr, d0.as<double>(), 2 * nr,
-                  p.guess_tol, p.max_iter, kSmallMax, p.nref_inner, false, cnt, iu, iw, s);
+    // initial guess: the ris system solved to the guess tolerance (Sec. 3.1)
+    if (p.mixed) {
+      const long long n = (long long)nr * ov;
+      DevBuf b32(n * 4, s), d0((size_t)2 * n * 4, s), uw((size_t)2 * n * 4, s);
+      convert(b.p, DType::F64, b32.p, DType::F32, n, s);
+      precond_paired<float>(b32.as<float>(), nullptr, shd.as<double>(), dl, nr, ov, d0.as<float>(),
+                            d0.as<float>() + n, s);
+      paired_linear<float>(ov, T32, diag32, b32.as<float>(), nullptr, sh, nr, d0.as<float>(), 2 * nr,
+                           p.guess_tol, p.max_iter, kSmallMax, true, false, cnt, uw.as<float>(),
+                           uw.as<float>() + n, s);
+      convert(uw.p, DType::F32, iu, DType::F64, 2 * n, s);
+    } else {
+      DevBuf d0((size_t)2 * nr * ov * 8, s);
+      precond_paired<double>(b.as<double>(), nullptr, shd.as<double>(), dl, nr, ov, d0.as<double>(),
+                             d0.as<double>() + (size_t)nr * ov, s);
+      paired_linear<double>(ov, T, diag, b.as<double>(), nullptr, sh, nr, d0.as<double>(), 2 * nr,
+                            p.guess_tol, p.max_iter, kSmallMax, false, false, cnt, iu, iw, s);
+    }
   } else {
-    precond_paired(b.as<double>(), nullptr, shd.as<double>(), dl, nr, ov, iu, iw, s);
+    precond_paired<double>(b.as<double>(), nullptr, shd.as<double>(), dl, nr, ov, iu, iw, s);
   }
   DevBuf U((size_t)nr * ov * 8, s), W((size_t)nr * ov * 8, s);
-  PairedLinOut r = paired_linear(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, b.as<double>(),
-                                 nullptr, sh, nr, iu, 2 * nr, p.tol, p.max_iter, p.cap, p.nref_outer,
-                                 true, cnt, U.as<double>(), W.as<double>(), s);
+  PairedLinOut r = paired_linear<double>(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag,
+                                         b.as<double>(), nullptr, sh, nr, iu, 2 * nr, p.tol, p.max_iter,
+                                         p.cap, false, true, cnt, U.as<double>(), W.as<double>(), s);
   // alpha[f][v][u] = mu_v . U[f*n_dip + u]
   DevBuf G((size_t)n_dip * nr * 8, s);
   gram(mud.as<double>(), n_dip, U.as<double>(), nr, ov, G.as<double>(), nr, s);
@@ -957,6 +1108,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
   }
   TD_CUDA(cudaStreamSynchronize(s));
   check_tc_error(c);
+  phase_report("solve");
   fill_stats(st, r.n_iter, cnt, r.converged, r.resid, -1.0, t0);
   return r.converged ? TDDFT_OK : TDDFT_ERR_NOCONV;
 }

@@ -45,11 +45,12 @@ __global__ void k_unit_rows(double* out, int k, int n, const int* idx) {
   }
 }
 
-__global__ void __launch_bounds__(1024) k_row_sumsq(const double* X, long long ldx, int n, double* out) {
+template <typename T>
+__global__ void __launch_bounds__(1024) k_row_sumsq(const T* X, long long ldx, int n, double* out) {
   __shared__ double red[32];
-  const double* x = X + blockIdx.x * ldx;
+  const T* x = X + blockIdx.x * ldx;
   double acc = 0.0;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) acc += x[e] * x[e];
+  for (int e = threadIdx.x; e < n; e += blockDim.x) { double v = (double)x[e]; acc += v * v; }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -68,41 +69,45 @@ __global__ void k_resid_tda(const double* X, const double* AX, const double* om,
   }
 }
 
-__global__ void k_resid_paired(const double* U, const double* W, const double* PU, const double* MW,
-                               const double* sh, const double* b, const double* bm, int k, int n,
-                               double* Rp, double* Rm) {
+template <typename T>
+__global__ void k_resid_paired(const T* U, const T* W, const T* PU, const T* MW,
+                               const double* sh, const T* b, const T* bm, int k, int n,
+                               T* Rp, T* Rm) {
   long long tot = (long long)k * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     int r = (int)(t / n);
     double s = sh[r];
-    Rp[t] = PU[t] - s * W[t] - (b ? b[t] : 0.0);
-    Rm[t] = MW[t] - s * U[t] - (bm ? bm[t] : 0.0);
+    Rp[t] = (T)((double)PU[t] - s * (double)W[t] - (b ? (double)b[t] : 0.0));
+    Rm[t] = (T)((double)MW[t] - s * (double)U[t] - (bm ? (double)bm[t] : 0.0));
   }
 }
 
-__global__ void k_precond_tda(const double* R, const double* om, const double* d, int k, int n, double* out) {
+template <typename T>
+__global__ void k_precond_tda(const T* R, const double* om, const double* d, int k, int n, T* out) {
   long long tot = (long long)k * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     int r = (int)(t / n), e = (int)(t % n);
-    out[t] = R[t] / guard(d[e] - om[r]);
+    out[t] = (T)((double)R[t] / guard(d[e] - om[r]));
   }
 }
 
-__global__ void k_precond_paired(const double* gp, const double* gm, const double* sh, const double* d,
-                                 int k, int n, double* ou, double* ow) {
+template <typename T>
+__global__ void k_precond_paired(const T* gp, const T* gm, const double* sh, const double* d,
+                                 int k, int n, T* ou, T* ow) {
   long long tot = (long long)k * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     int r = (int)(t / n), e = (int)(t % n);
-    double g2 = gm ? gm[t] : 0.0;
-    double rx = 0.5 * (gp[t] + g2), ry = 0.5 * (gp[t] - g2);
+    double g1 = (double)gp[t], g2 = gm ? (double)gm[t] : 0.0;
+    double rx = 0.5 * (g1 + g2), ry = 0.5 * (g1 - g2);
     double x = rx / guard(d[e] - sh[r]);
     double y = ry / guard(d[e] + sh[r]);
-    ou[t] = x + y;
-    ow[t] = x - y;
+    ou[t] = (T)(x + y);
+    ow[t] = (T)(x - y);
   }
 }
 
-__global__ void k_gather_rows(const double* src, const int* idx, int k, int n, double* dst) {
+template <typename T>
+__global__ void k_gather_rows(const T* src, const int* idx, int k, int n, T* dst) {
   long long tot = (long long)k * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     int r = (int)(t / n), e = (int)(t % n);
@@ -126,10 +131,11 @@ __global__ void k_sym_fill(double* a, int ld, int n_old, int n_new) {
   }
 }
 
-__global__ void k_scale_rows(double* X, const double* sc, int k, int n) {
+template <typename T>
+__global__ void k_scale_rows(T* X, const double* sc, int k, int n) {
   long long tot = (long long)k * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
-    X[t] *= sc[t / n];
+    X[t] = (T)((double)X[t] * sc[t / n]);
 }
 
 template <typename TI, typename TO>
@@ -164,16 +170,16 @@ __global__ void k_mask(T* L, int rows, int n1, int n2, const unsigned char* m1, 
   }
 }
 
-template <typename TW>
-__global__ void k_combine(const double* X, const double* d, const TW* J, const TW* K1, const TW* K2,
-                          double cj, double c1, double c2, long long m, int n, double* out) {
+template <typename TX, typename TW, typename TO>
+__global__ void k_combine(const TX* X, const double* d, const TW* J, const TW* K1, const TW* K2,
+                          double cj, double c1, double c2, long long m, int n, TO* out) {
   long long tot = m * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    double v = d[t % n] * X[t];
+    double v = d[t % n] * (double)X[t];
     if (J) v += cj * ldd<TW>(J, t);
     if (K1) v += c1 * ldd<TW>(K1, t);
     if (K2) v += c2 * ldd<TW>(K2, t);
-    out[t] = v;
+    out[t] = (TO)v;
   }
 }
 
@@ -208,43 +214,65 @@ void unit_rows(double* out, int k, int n, const int* idx, cudaStream_t s) {
   k_unit_rows<<<TD_GRID((long long)k * n)>>>(out, k, n, idx);
   count_launch(); TD_LAUNCH_CHECK();
 }
-void row_sumsq(const double* X, long long ldx, int k, int n, double* out, cudaStream_t s) {
+template <typename T>
+void row_sumsq(const T* X, long long ldx, int k, int n, double* out, cudaStream_t s) {
   if (k <= 0) return;
-  k_row_sumsq<<<k, 1024, 0, s>>>(X, ldx, n, out);
+  k_row_sumsq<T><<<k, 1024, 0, s>>>(X, ldx, n, out);
   count_launch(); TD_LAUNCH_CHECK();
 }
+template void row_sumsq<double>(const double*, long long, int, int, double*, cudaStream_t);
+template void row_sumsq<float>(const float*, long long, int, int, double*, cudaStream_t);
 void resid_tda(const double* X, const double* AX, const double* om, int k, int n, double* R, cudaStream_t s) {
   k_resid_tda<<<TD_GRID((long long)k * n)>>>(X, AX, om, k, n, R);
   count_launch(); TD_LAUNCH_CHECK();
 }
-void resid_paired(const double* U, const double* W, const double* PU, const double* MW, const double* sh,
-                  const double* b, const double* bm, int k, int n, double* Rp, double* Rm, cudaStream_t s) {
-  k_resid_paired<<<TD_GRID((long long)k * n)>>>(U, W, PU, MW, sh, b, bm, k, n, Rp, Rm);
+template <typename T>
+void resid_paired(const T* U, const T* W, const T* PU, const T* MW, const double* sh,
+                  const T* b, const T* bm, int k, int n, T* Rp, T* Rm, cudaStream_t s) {
+  k_resid_paired<T><<<TD_GRID((long long)k * n)>>>(U, W, PU, MW, sh, b, bm, k, n, Rp, Rm);
   count_launch(); TD_LAUNCH_CHECK();
 }
-void precond_tda(const double* R, const double* om, const double* d, int k, int n, double* out, cudaStream_t s) {
-  k_precond_tda<<<TD_GRID((long long)k * n)>>>(R, om, d, k, n, out);
+template void resid_paired<double>(const double*, const double*, const double*, const double*, const double*,
+                                   const double*, const double*, int, int, double*, double*, cudaStream_t);
+template void resid_paired<float>(const float*, const float*, const float*, const float*, const double*,
+                                  const float*, const float*, int, int, float*, float*, cudaStream_t);
+template <typename T>
+void precond_tda(const T* R, const double* om, const double* d, int k, int n, T* out, cudaStream_t s) {
+  k_precond_tda<T><<<TD_GRID((long long)k * n)>>>(R, om, d, k, n, out);
   count_launch(); TD_LAUNCH_CHECK();
 }
-void precond_paired(const double* gp, const double* gm, const double* sh, const double* d, int k, int n,
-                    double* ou, double* ow, cudaStream_t s) {
-  k_precond_paired<<<TD_GRID((long long)k * n)>>>(gp, gm, sh, d, k, n, ou, ow);
+template void precond_tda<double>(const double*, const double*, const double*, int, int, double*, cudaStream_t);
+template void precond_tda<float>(const float*, const double*, const double*, int, int, float*, cudaStream_t);
+template <typename T>
+void precond_paired(const T* gp, const T* gm, const double* sh, const double* d, int k, int n,
+                    T* ou, T* ow, cudaStream_t s) {
+  k_precond_paired<T><<<TD_GRID((long long)k * n)>>>(gp, gm, sh, d, k, n, ou, ow);
   count_launch(); TD_LAUNCH_CHECK();
 }
-void gather_rows(const double* src, const int* idx, int k, int n, double* dst, cudaStream_t s) {
+template void precond_paired<double>(const double*, const double*, const double*, const double*, int, int,
+                                     double*, double*, cudaStream_t);
+template void precond_paired<float>(const float*, const float*, const double*, const double*, int, int,
+                                    float*, float*, cudaStream_t);
+template <typename T>
+void gather_rows(const T* src, const int* idx, int k, int n, T* dst, cudaStream_t s) {
   if (k <= 0) return;
-  k_gather_rows<<<TD_GRID((long long)k * n)>>>(src, idx, k, n, dst);
+  k_gather_rows<T><<<TD_GRID((long long)k * n)>>>(src, idx, k, n, dst);
   count_launch(); TD_LAUNCH_CHECK();
 }
+template void gather_rows<double>(const double*, const int*, int, int, double*, cudaStream_t);
+template void gather_rows<float>(const float*, const int*, int, int, float*, cudaStream_t);
 void sym_fill(double* a, int ld, int n_old, int n_new, cudaStream_t s) {
   if (n_new <= 0) return;
   k_sym_fill<<<TD_GRID((long long)(n_old + n_new) * n_new)>>>(a, ld, n_old, n_new);
   count_launch(); TD_LAUNCH_CHECK();
 }
-void scale_rows(double* X, const double* sc, int k, int n, cudaStream_t s) {
-  k_scale_rows<<<TD_GRID((long long)k * n)>>>(X, sc, k, n);
+template <typename T>
+void scale_rows(T* X, const double* sc, int k, int n, cudaStream_t s) {
+  k_scale_rows<T><<<TD_GRID((long long)k * n)>>>(X, sc, k, n);
   count_launch(); TD_LAUNCH_CHECK();
 }
+template void scale_rows<double>(double*, const double*, int, int, cudaStream_t);
+template void scale_rows<float>(float*, const double*, int, int, cudaStream_t);
 void cast_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s) {
   k_convert<double, float><<<TD_GRID(n)>>>(in, out, n);
   count_launch(); TD_LAUNCH_CHECK();
@@ -284,9 +312,14 @@ void mask_block(void* L, DType t, int rows, int n1, int n2, const unsigned char*
 void combine(const double* X, const double* d, const void* J, const void* K1, const void* K2, DType tw,
              double cj, double c1, double c2, long long m, int n, double* out, cudaStream_t s) {
   if (tw == DType::F64)
-    k_combine<double><<<TD_GRID(m * n)>>>(X, d, (const double*)J, (const double*)K1, (const double*)K2, cj, c1, c2, m, n, out);
+    k_combine<double, double, double><<<TD_GRID(m * n)>>>(X, d, (const double*)J, (const double*)K1, (const double*)K2, cj, c1, c2, m, n, out);
   else
-    k_combine<float><<<TD_GRID(m * n)>>>(X, d, (const float*)J, (const float*)K1, (const float*)K2, cj, c1, c2, m, n, out);
+    k_combine<double, float, double><<<TD_GRID(m * n)>>>(X, d, (const float*)J, (const float*)K1, (const float*)K2, cj, c1, c2, m, n, out);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+void combine_f32(const float* X, const double* d, const float* J, const float* K1, const float* K2,
+                 double cj, double c1, double c2, long long m, int n, float* out, cudaStream_t s) {
+  k_combine<float, float, float><<<TD_GRID(m * n)>>>(X, d, J, K1, K2, cj, c1, c2, m, n, out);
   count_launch(); TD_LAUNCH_CHECK();
 }
 void reduce_parts(void* buf, DType t, int parts, long long n, cudaStream_t s) {
@@ -305,10 +338,11 @@ void check_finite(const void* X, DType t, long long n, int* flag, cudaStream_t s
 
 
 namespace {
-__global__ void k_axpy_rows(double* out, const double* X, const double* sc, int k, int n) {
+template <typename T>
+__global__ void k_axpy_rows(T* out, const T* X, const double* sc, int k, int n) {
   long long tot = (long long)k * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
-    out[t] += sc[t / n] * X[t];
+    out[t] = (T)((double)out[t] + sc[t / n] * (double)X[t]);
 }
 __global__ void k_half_sum_diff(const double* U, const double* W, long long n, double* X, double* Y) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
@@ -317,27 +351,34 @@ __global__ void k_half_sum_diff(const double* U, const double* W, long long n, d
     if (Y) Y[t] = 0.5 * (u - w);
   }
 }
-__global__ void k_resid_shift(const double* Y, const double* X, const double* sh, const double* B, int k, int n, double* out) {
+template <typename T>
+__global__ void k_resid_shift(const T* Y, const T* X, const double* sh, const T* B, int k, int n, T* out) {
   long long tot = (long long)k * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
-    out[t] = Y[t] - sh[t / n] * X[t] - (B ? B[t] : 0.0);
+    out[t] = (T)((double)Y[t] - sh[t / n] * (double)X[t] - (B ? (double)B[t] : 0.0));
 }
 }  // namespace
 
-void axpy_rows(double* out, const double* X, const double* sc, int k, int n, cudaStream_t s) {
+template <typename T>
+void axpy_rows(T* out, const T* X, const double* sc, int k, int n, cudaStream_t s) {
   if (k <= 0) return;
-  k_axpy_rows<<<TD_GRID((long long)k * n)>>>(out, X, sc, k, n);
+  k_axpy_rows<T><<<TD_GRID((long long)k * n)>>>(out, X, sc, k, n);
   count_launch(); TD_LAUNCH_CHECK();
 }
+template void axpy_rows<double>(double*, const double*, const double*, int, int, cudaStream_t);
+template void axpy_rows<float>(float*, const float*, const double*, int, int, cudaStream_t);
 void half_sum_diff(const double* U, const double* W, long long n, double* X, double* Y, cudaStream_t s) {
   if (n <= 0) return;
   k_half_sum_diff<<<TD_GRID(n)>>>(U, W, n, X, Y);
   count_launch(); TD_LAUNCH_CHECK();
 }
-void resid_shift(const double* Y, const double* X, const double* sh, const double* B, int k, int n, double* out, cudaStream_t s) {
+template <typename T>
+void resid_shift(const T* Y, const T* X, const double* sh, const T* B, int k, int n, T* out, cudaStream_t s) {
   if (k <= 0) return;
-  k_resid_shift<<<TD_GRID((long long)k * n)>>>(Y, X, sh, B, k, n, out);
+  k_resid_shift<T><<<TD_GRID((long long)k * n)>>>(Y, X, sh, B, k, n, out);
   count_launch(); TD_LAUNCH_CHECK();
 }
+template void resid_shift<double>(const double*, const double*, const double*, const double*, int, int, double*, cudaStream_t);
+template void resid_shift<float>(const float*, const float*, const double*, const float*, int, int, float*, cudaStream_t);
 
 }  // namespace tddft

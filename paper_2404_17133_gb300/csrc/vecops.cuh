@@ -10,28 +10,33 @@ void delta_kernel(const double* eps_o, const double* eps_v, int no, int nv, doub
 // Rows r < k of out [k][n]: unit vector at column idx[r].
 void unit_rows(double* out, int k, int n, const int* idx, cudaStream_t s);
 // out[r] = sum_e X[r][e]^2 (FP64, deterministic), X rows of stride ldx.
-void row_sumsq(const double* X, long long ldx, int k, int n, double* out, cudaStream_t s);
+template <typename T>
+void row_sumsq(const T* X, long long ldx, int k, int n, double* out, cudaStream_t s);
 // R = AX - diag(omega) X  (Eq. residual).
 void resid_tda(const double* X, const double* AX, const double* omega, int k, int n, double* R,
                cudaStream_t s);
 // Rp = PU - s W - b, Rm = MW - s U - bm (paired residuals; b, bm may be NULL).
-void resid_paired(const double* U, const double* W, const double* PU, const double* MW,
-                  const double* shift, const double* b, const double* bm, int k, int n, double* Rp,
-                  double* Rm, cudaStream_t s);
+template <typename T>
+void resid_paired(const T* U, const T* W, const T* PU, const T* MW, const double* shift, const T* b,
+                  const T* bm, int k, int n, T* Rp, T* Rm, cudaStream_t s);
 // out = R / (Delta - omega)  (Eq. precondition with the diagonal T), guarded.
-void precond_tda(const double* R, const double* omega, const double* delta, int k, int n,
-                 double* out, cudaStream_t s);
+template <typename T>
+void precond_tda(const T* R, const double* omega, const double* delta, int k, int n, T* out,
+                 cudaStream_t s);
 // Diagonal T for the paired systems: x = (g+ + g-)/2/(Delta - s), y = (g+ - g-)/2/(Delta + s),
 // out_u = x + y, out_w = x - y.
-void precond_paired(const double* gp, const double* gm, const double* shift, const double* delta,
-                    int k, int n, double* out_u, double* out_w, cudaStream_t s);
+template <typename T>
+void precond_paired(const T* gp, const T* gm, const double* shift, const double* delta, int k, int n,
+                    T* out_u, T* out_w, cudaStream_t s);
 // dst[r] = src[idx[r]] (rows of length n).
-void gather_rows(const double* src, const int* idx, int k, int n, double* dst, cudaStream_t s);
+template <typename T>
+void gather_rows(const T* src, const int* idx, int k, int n, T* dst, cudaStream_t s);
 // Projected matrix a (ld) after its new columns [n_old, n_old+n_new) were written
 // for all rows < n_old+n_new: mirror into the new rows and symmetrise the new block.
 void sym_fill(double* a, int ld, int n_old, int n_new, cudaStream_t s);
 // X[r] *= scale[r].
-void scale_rows(double* X, const double* scale, int k, int n, cudaStream_t s);
+template <typename T>
+void scale_rows(T* X, const double* scale, int k, int n, cudaStream_t s);
 // conversions
 void cast_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s);
 void cast_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s);
@@ -48,6 +53,9 @@ void mask_block(void* L, DType t, int rows, int n1, int n2, const unsigned char*
 void combine(const double* X, const double* delta, const void* J, const void* K1, const void* K2,
              DType tw, double c_j, double c_1, double c_2, long long m, int n, double* out,
              cudaStream_t s);
+// FP32 variant (FP32 vectors in and out, FP32 parts).
+void combine_f32(const float* X, const double* delta, const float* J, const float* K1, const float* K2,
+                 double c_j, double c_1, double c_2, long long m, int n, float* out, cudaStream_t s);
 // Sum `parts` partial buffers of n elements (type t) into the first.
 void reduce_parts(void* buf, DType t, int parts, long long n, cudaStream_t s);
 // Non-finite check: flag[0] |= 1 if any entry of X is NaN/Inf.
@@ -57,11 +65,13 @@ void check_finite(const void* X, DType t, long long n, int* flag, cudaStream_t s
 
 namespace tddft {
 // out[r] += scale[r] * X[r] (rows of length n)
-void axpy_rows(double* out, const double* X, const double* scale, int k, int n, cudaStream_t s);
+template <typename T>
+void axpy_rows(T* out, const T* X, const double* scale, int k, int n, cudaStream_t s);
 // X = (U + W)/2, Y = (U - W)/2
 void half_sum_diff(const double* U, const double* W, long long n, double* X, double* Y,
                    cudaStream_t s);
 // out = Y - shift[r] * X - B   (B may be NULL): the residual of (T - shift) x = b
-void resid_shift(const double* Y, const double* X, const double* shift, const double* B, int k,
-                 int n, double* out, cudaStream_t s);
+template <typename T>
+void resid_shift(const T* Y, const T* X, const double* shift, const T* B, int k, int n, T* out,
+                 cudaStream_t s);
 }  // namespace tddft
