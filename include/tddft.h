@@ -163,8 +163,9 @@ tddft_status tddft_solve_polar(tddft_ctx* ctx, const tddft_opts* opts, const dou
  *   kind 0: A X (exact), 1: ((A+B)X, (A-B)X) exact, 2: T_A X (ris),
  *   kind 3: ((T_A+T_B)X, (T_A-T_B)X) ris.
  * X [m][ov]; out0 [m][ov]; out1 [m][ov] for kinds 1 and 3 (else NULL).
- * precision / tensor_cores as in tddft_opts; on_device: pointers are device
- * memory.  Results are FP64.                                               */
+ * precision / tensor_cores as in tddft_opts (for the ris kinds the tensor
+ * cores form one BF16 product); on_device: pointers are device memory.
+ * Results are FP64.                                                        */
 tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cores,
                          const double* X, int m, double* out0, double* out1, int on_device);
 

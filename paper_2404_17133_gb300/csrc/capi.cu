@@ -113,6 +113,12 @@ FactorSet Ctx::exact(int precision) const {
     f.Jov = x32_ov.p; f.Koo = x32_oo.p; f.Kvv = x32_vv.p; f.Kov = x32_ov.p;
     f.Kvv_hi = x16_vv_hi.as<__nv_bfloat16>();
     f.Kvv_lo = x16_vv_lo.as<__nv_bfloat16>();
+    f.Kvo_hi = x16_vo_hi.as<__nv_bfloat16>();
+    f.Kvo_lo = x16_vo_lo.as<__nv_bfloat16>();
+    f.Koo_hi = x16_oo_hi.as<__nv_bfloat16>();
+    f.Koo_lo = x16_oo_lo.as<__nv_bfloat16>();
+    f.Kovp_hi = x16_ov_hi.as<__nv_bfloat16>();
+    f.Kovp_lo = x16_ov_lo.as<__nv_bfloat16>();
   }
   return f;
 }
@@ -127,6 +133,10 @@ FactorSet Ctx::ris(int precision) const {
   } else {
     f.dt = DType::BF16;
     f.Jov = r16_J.p; f.Koo = r16_Koo.p; f.Kvv = r16_Kvv.p; f.Kov = r16_Kov.p;
+    f.Kvv_hi = r16_vvp.as<__nv_bfloat16>();
+    f.Kvo_hi = r16_vo.as<__nv_bfloat16>();
+    f.Koo_hi = r16_oop.as<__nv_bfloat16>();
+    f.Kovp_hi = r16_ovp.as<__nv_bfloat16>();
   }
   return f;
 }
@@ -224,7 +234,10 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
     const double nr = (double)d.n_aux_ris_J * ov + (double)d.n_aux_ris_K * (no * no + nv * nv + ov);
     double bytes = 0.0;
     if (p64) bytes += 8.0 * (nvv + noo + nov + nr);
-    if (pmx) bytes += 4.0 * (nvv + noo + nov) + 4.0 * (double)d.n_aux * nv * tc_pad(nv) + 2.0 * nr;
+    if (pmx)
+      bytes += 4.0 * (nvv + noo + nov) +
+               4.0 * (double)d.n_aux * (nv * (tc_pad(nv) + tc_pad(no)) + no * (tc_pad(no) + tc_pad(nv))) +
+               2.0 * nr + 2.0 * (double)d.n_aux_ris_K * (nv * (tc_pad(nv) + tc_pad(no)) + no * (tc_pad(no) + tc_pad(nv)));
     size_t fr = 0, tot = 0;
     TD_CUDA(cudaMemGetInfo(&fr, &tot));
     double budget = d.hbm_budget_gb > 0 ? d.hbm_budget_gb * 1e9 : (double)fr - 2e9;
@@ -281,9 +294,22 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
     stage_rows(L_oo, tin, dev, A, (long long)no * no, targets(c->x64_oo, c->x32_oo), s);
     stage_rows(L_ov, tin, dev, A, ov, targets(c->x64_ov, c->x32_ov), s);
     stage_rows(L_vv, tin, dev, A, (long long)nv * nv, targets(c->x64_vv, c->x32_vv), s);
-    if (pmx)  // BF16 hi/lo split of the FP32 copy, rows padded for the TMA strides
+    if (pmx) {  // BF16 hi/lo splits of the FP32 copies, rows padded for the TMA strides
       tc_split_pad(c->x32_vv.as<float>(), (int)(A * nv), 1, nv, c->x16_vv_hi.as<__nv_bfloat16>(),
                    c->x16_vv_lo.as<__nv_bfloat16>(), s);
+      c->x16_vo_hi = DevBuf(A * nv * tc_pad(no) * 2, s);
+      c->x16_vo_lo = DevBuf(A * nv * tc_pad(no) * 2, s);
+      tc_transpose_split(c->x32_ov.p, DType::F32, (int)A, no, nv, c->x16_vo_hi.as<__nv_bfloat16>(),
+                         c->x16_vo_lo.as<__nv_bfloat16>(), s);
+      c->x16_oo_hi = DevBuf(A * no * tc_pad(no) * 2, s);
+      c->x16_oo_lo = DevBuf(A * no * tc_pad(no) * 2, s);
+      tc_pad_split(c->x32_oo.p, DType::F32, A * no, no, c->x16_oo_hi.as<__nv_bfloat16>(),
+                   c->x16_oo_lo.as<__nv_bfloat16>(), s);
+      c->x16_ov_hi = DevBuf(A * no * tc_pad(nv) * 2, s);
+      c->x16_ov_lo = DevBuf(A * no * tc_pad(nv) * 2, s);
+      tc_pad_split(c->x32_ov.p, DType::F32, A * no, nv, c->x16_ov_hi.as<__nv_bfloat16>(),
+                   c->x16_ov_lo.as<__nv_bfloat16>(), s);
+    }
 
     // ris factors (Coulomb rows all; exchange rows windowed, Sec. 3.1)
     const long long RJ = d.n_aux_ris_J, RK = d.n_aux_ris_K;
@@ -335,6 +361,17 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
         mask_block(c->r16_Koo.p, DType::BF16, (int)RK, no, no, dmo.as<unsigned char>(), dmo.as<unsigned char>(), s);
         mask_block(c->r16_Kvv.p, DType::BF16, (int)RK, nv, nv, dmv.as<unsigned char>(), dmv.as<unsigned char>(), s);
         mask_block(c->r16_Kov.p, DType::BF16, (int)RK, no, nv, dmo.as<unsigned char>(), dmv.as<unsigned char>(), s);
+        // padded tensor-core copies (vv is symmetric, so its transpose is itself)
+        c->r16_vvp = DevBuf(RK * nv * tc_pad(nv) * 2, s);
+        c->r16_vo = DevBuf(RK * nv * tc_pad(no) * 2, s);
+        tc_transpose_split(c->r16_Kvv.p, DType::BF16, (int)RK, nv, nv, c->r16_vvp.as<__nv_bfloat16>(),
+                           nullptr, s);
+        tc_transpose_split(c->r16_Kov.p, DType::BF16, (int)RK, no, nv, c->r16_vo.as<__nv_bfloat16>(),
+                           nullptr, s);
+        c->r16_oop = DevBuf(RK * no * tc_pad(no) * 2, s);
+        c->r16_ovp = DevBuf(RK * no * tc_pad(nv) * 2, s);
+        tc_pad_split(c->r16_Koo.p, DType::BF16, RK * no, no, c->r16_oop.as<__nv_bfloat16>(), nullptr, s);
+        tc_pad_split(c->r16_Kov.p, DType::BF16, RK * no, nv, c->r16_ovp.as<__nv_bfloat16>(), nullptr, s);
       }
       TD_CUDA(cudaStreamSynchronize(s));
     }
@@ -439,7 +476,7 @@ tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cor
     }
     g_launches = 0;
     apply_operator(c->dims(), f, Xd, m, paired ? OpMode::PAIRED : OpMode::TDA, d0, paired ? d1 : nullptr,
-                   tensor_cores != 0 && !ris, s);
+                   tensor_cores != 0, s);
     if (!on_device) {
       TD_CUDA(cudaMemcpyAsync(out0, d0, n * 8, cudaMemcpyDeviceToHost, s));
       if (paired) TD_CUDA(cudaMemcpyAsync(out1, d1, n * 8, cudaMemcpyDeviceToHost, s));

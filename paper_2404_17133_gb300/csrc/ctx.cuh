@@ -22,9 +22,18 @@ struct FactorSet {
   const void* Koo = nullptr;
   const void* Kvv = nullptr;
   const void* Kov = nullptr;
-  // BF16 hi/lo split of Kvv for the tensor-core exchange (exact operator only)
+  // Tensor-core operands (rows padded to tc_pad): Kvv as [P][b][a] and Kov
+  // transposed as [P][a][j]; hi + lo split for the exact operator, hi only
+  // (plain BF16) for the ris operator.
   const __nv_bfloat16* Kvv_hi = nullptr;
   const __nv_bfloat16* Kvv_lo = nullptr;
+  const __nv_bfloat16* Kvo_hi = nullptr;
+  const __nv_bfloat16* Kvo_lo = nullptr;
+  // stage-1 operands: Koo as [P][i][pad(j)], Kov as [P][i][pad(b)]
+  const __nv_bfloat16* Koo_hi = nullptr;
+  const __nv_bfloat16* Koo_lo = nullptr;
+  const __nv_bfloat16* Kovp_hi = nullptr;
+  const __nv_bfloat16* Kovp_lo = nullptr;
 };
 
 // Event-based timing of one kernel family (the dominant contraction).
@@ -80,10 +89,14 @@ struct Ctx {
   DevBuf x64_oo, x64_ov, x64_vv;
   DevBuf x32_oo, x32_ov, x32_vv;
   DevBuf x16_vv_hi, x16_vv_lo;   // [naux][nv][tc_pad(nv)] BF16 split of L_vv
+  DevBuf x16_vo_hi, x16_vo_lo;   // [naux][nv][tc_pad(no)] BF16 split of L_ov transposed
+  DevBuf x16_oo_hi, x16_oo_lo;   // [naux][no][tc_pad(no)]
+  DevBuf x16_ov_hi, x16_ov_lo;   // [naux][no][tc_pad(nv)]
   DevBuf tc_err;                  // int flag, see OpDims::tc_err
   // ris factors: Coulomb ov (all rows), exchange oo/vv/ov (s rows, windowed)
   DevBuf r64_J, r64_Koo, r64_Kvv, r64_Kov;
   DevBuf r16_J, r16_Koo, r16_Kvv, r16_Kov;
+  DevBuf r16_vvp, r16_vo, r16_oop, r16_ovp;   // tensor-core copies of the ris exchange rows
   unsigned long long device_bytes = 0;
   std::string err;
   // request queue

@@ -12,8 +12,8 @@
 //   K2: Q[n][i][P][j] = sum_b L_ov[P][i][b] X[n][j][b]
 //       K2[(n,i)][a] = sum_(P,j) Q[(n,i)][(P,j)] L_ov[P][j][a]
 // P is processed in chunks so the intermediates stay within a bounded
-// workspace; K1's second contraction (about 90% of the flops) optionally runs
-// on the tcgen05 tensor cores.
+// workspace; the second contractions of K1 and K2 (most of the flops) run on the
+// tcgen05 tensor cores when asked (MIXED precision).
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
 #include "vecops.cuh"
@@ -125,42 +125,75 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
   if (f.nK > 0 && d.a_x != 0.0) {
     K1b = DevBuf(mov * ew, s);
     if (need_k2) K2b = DevBuf(mov * ew, s);
+    const bool use_tc = tensor_cores && !f64 && f.Kvv_hi && f.Kvo_hi && f.Koo_hi && f.Kovp_hi;
+    TD_REQUIRE(!tensor_cores || f64 || use_tc, TDDFT_ERR_ARG, "tensor-core factor copies missing");
     const int pc = chunk_rows(f.nK, (long long)m * ov * (long long)ew, m);
-    DevBuf Zb((size_t)m * no * pc * nv * ew, s);
-    DevBuf Qb;
-    if (need_k2) Qb = DevBuf((size_t)m * no * pc * no * ew, s);
-    DevBuf Zhi, Zlo;
-    const bool use_tc = tensor_cores && !f64 && f.Kvv_hi && f.Kvv_lo;
-    TD_REQUIRE(!tensor_cores || f64 || use_tc, TDDFT_ERR_ARG, "tensor-core copies of L_vv missing");
-    const int nvp = tc_pad(nv);
-    if (use_tc) {
-      Zhi = DevBuf((size_t)m * no * pc * nvp * 2, s);
-      Zlo = DevBuf((size_t)m * no * pc * nvp * 2, s);
-    }
     const size_t es = dtype_size(f.dt);
-    for (int p0 = 0; p0 < f.nK; p0 += pc) {
-      const int pn = (f.nK - p0 < pc) ? f.nK - p0 : pc;
-      // Z[n][i][P][a] = sum_j Koo[P][i][j] X[n][j][a]
-      GemmDesc z;
-      z.acc64 = f64;
-      z.M = no; z.N = nv; z.K = no;
-      z.A = (const char*)f.Koo + (size_t)p0 * no * no * es; z.ta = f.dt; z.sam = no; z.sak = 1;
-      z.B = Xw; z.tb = tw; z.sbk = nv; z.sbn = 1;
-      z.C = Zb.p; z.tc = tw; z.scm = (long long)pn * nv; z.scn = 1;
-      z.nb0 = pn; z.nb1 = m;
-      z.sA0 = (long long)no * no; z.sB0 = 0; z.sC0 = nv;
-      z.sA1 = 0; z.sB1 = ov; z.sC1 = (long long)no * pn * nv;
-      gemm(z, s);
+    if (use_tc) {
+      // Both contractions of K1 and of K2 on the tensor cores.  The trial block
+      // enters twice: transposed per vector ([(n,a)][j]) for Z = L_oo X and as is
+      // ([(n,j)][b]) for Q = L_ov X^T; exact factors are hi + lo splits.
+      const bool split = f.Kvv_lo != nullptr;
+      const int nvp = tc_pad(nv), nop = tc_pad(no);
+      const DType xt = x32 ? DType::F32 : DType::F64;
+      DevBuf Xt_hi((size_t)m * nv * nop * 2, s), Xt_lo, Xs_hi, Xs_lo;
+      if (split) Xt_lo = DevBuf((size_t)m * nv * nop * 2, s);
+      tc_transpose_split(X, xt, m, no, nv, Xt_hi.as<__nv_bfloat16>(), Xt_lo.as<__nv_bfloat16>(), s);
+      if (need_k2) {
+        Xs_hi = DevBuf((size_t)m * no * nvp * 2, s);
+        if (split) Xs_lo = DevBuf((size_t)m * no * nvp * 2, s);
+        tc_pad_split(X, xt, (long long)m * no, nv, Xs_hi.as<__nv_bfloat16>(), Xs_lo.as<__nv_bfloat16>(), s);
+      }
+      DevBuf Zhi((size_t)m * no * pc * nvp * 2, s), Zlo, Qhi, Qlo;
+      if (split) Zlo = DevBuf((size_t)m * no * pc * nvp * 2, s);
+      if (need_k2) {
+        Qhi = DevBuf((size_t)m * no * pc * nop * 2, s);
+        if (split) Qlo = DevBuf((size_t)m * no * pc * nop * 2, s);
+      }
       const int Mz = m * no;
-      const long long Kz = (long long)pn * nv;
-      const bool timed = d.prof && d.prof->on && f.dt != DType::BF16;
-      if (timed) d.prof->begin(s);
-      if (use_tc) {
-        tc_split_pad(Zb.as<float>(), Mz, pn, nv, Zhi.as<__nv_bfloat16>(), Zlo.as<__nv_bfloat16>(), s);
-        tc_exchange_k1(Zhi.as<__nv_bfloat16>(), Zlo.as<__nv_bfloat16>(), Mz, pn, nv,
-                       f.Kvv_hi + (size_t)p0 * nv * nvp, f.Kvv_lo + (size_t)p0 * nv * nvp,
-                       K1b.as<float>(), p0 > 0, d.tc_err, s);
-      } else {
+      for (int p0 = 0; p0 < f.nK; p0 += pc) {
+        const int pn = (f.nK - p0 < pc) ? f.nK - p0 : pc;
+        const __nv_bfloat16* oo_lo = split ? f.Koo_lo + (size_t)p0 * no * nop : nullptr;
+        tc_stage1(Xt_hi.as<__nv_bfloat16>(), Xt_lo.as<__nv_bfloat16>(), m * nv, no,
+                  f.Koo_hi + (size_t)p0 * no * nop, oo_lo, no, pn, nv, Zhi.as<__nv_bfloat16>(),
+                  Zlo.as<__nv_bfloat16>(), d.tc_err, s);
+        const bool timed = d.prof && d.prof->on && f.dt != DType::BF16;
+        if (timed) d.prof->begin(s);
+        tc_contract(Zhi.as<__nv_bfloat16>(), Zlo.as<__nv_bfloat16>(), Mz, pn, nv,
+                    f.Kvv_hi + (size_t)p0 * nv * nvp, split ? f.Kvv_lo + (size_t)p0 * nv * nvp : nullptr,
+                    nv, K1b.as<float>(), p0 > 0, d.tc_err, s);
+        if (timed) d.prof->end(s, 2.0 * Mz * (double)nv * (double)pn * nv);
+        if (need_k2) {
+          const __nv_bfloat16* ov_lo = split ? f.Kovp_lo + (size_t)p0 * no * nvp : nullptr;
+          tc_stage1(Xs_hi.as<__nv_bfloat16>(), Xs_lo.as<__nv_bfloat16>(), m * no, nv,
+                    f.Kovp_hi + (size_t)p0 * no * nvp, ov_lo, no, pn, no, Qhi.as<__nv_bfloat16>(),
+                    Qlo.as<__nv_bfloat16>(), d.tc_err, s);
+          tc_contract(Qhi.as<__nv_bfloat16>(), Qlo.as<__nv_bfloat16>(), Mz, pn, no,
+                      f.Kvo_hi + (size_t)p0 * nv * nop, split ? f.Kvo_lo + (size_t)p0 * nv * nop : nullptr,
+                      nv, K2b.as<float>(), p0 > 0, d.tc_err, s);
+        }
+      }
+    } else {
+      DevBuf Zb((size_t)m * no * pc * nv * ew, s);
+      DevBuf Qb;
+      if (need_k2) Qb = DevBuf((size_t)m * no * pc * no * ew, s);
+      for (int p0 = 0; p0 < f.nK; p0 += pc) {
+        const int pn = (f.nK - p0 < pc) ? f.nK - p0 : pc;
+        // Z[n][i][P][a] = sum_j Koo[P][i][j] X[n][j][a]
+        GemmDesc z;
+        z.acc64 = f64;
+        z.M = no; z.N = nv; z.K = no;
+        z.A = (const char*)f.Koo + (size_t)p0 * no * no * es; z.ta = f.dt; z.sam = no; z.sak = 1;
+        z.B = Xw; z.tb = tw; z.sbk = nv; z.sbn = 1;
+        z.C = Zb.p; z.tc = tw; z.scm = (long long)pn * nv; z.scn = 1;
+        z.nb0 = pn; z.nb1 = m;
+        z.sA0 = (long long)no * no; z.sB0 = 0; z.sC0 = nv;
+        z.sA1 = 0; z.sB1 = ov; z.sC1 = (long long)no * pn * nv;
+        gemm(z, s);
+        const int Mz = m * no;
+        const long long Kz = (long long)pn * nv;
+        const bool timed = d.prof && d.prof->on && f.dt != DType::BF16;
+        if (timed) d.prof->begin(s);
         GemmDesc k;
         k.acc64 = f64;
         k.M = Mz; k.N = nv; k.K = (int)Kz;
@@ -169,28 +202,28 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
         k.C = K1b.p; k.tc = tw; k.scm = nv; k.scn = 1;
         k.beta = (p0 > 0) ? 1.0 : 0.0;
         gemm_splitk(k, auto_splits(k.M, k.N, k.K), s);
-      }
-      if (timed) d.prof->end(s, 2.0 * Mz * (double)nv * (double)Kz);
-      if (need_k2) {
-        // Q[n][i][P][j] = sum_b Kov[P][i][b] X[n][j][b]
-        GemmDesc q;
-        q.acc64 = f64;
-        q.M = no; q.N = no; q.K = nv;
-        q.A = (const char*)f.Kov + (size_t)p0 * ov * es; q.ta = f.dt; q.sam = nv; q.sak = 1;
-        q.B = Xw; q.tb = tw; q.sbk = 1; q.sbn = nv;
-        q.C = Qb.p; q.tc = tw; q.scm = (long long)pn * no; q.scn = 1;
-        q.nb0 = pn; q.nb1 = m;
-        q.sA0 = ov; q.sB0 = 0; q.sC0 = no;
-        q.sA1 = 0; q.sB1 = ov; q.sC1 = (long long)no * pn * no;
-        gemm(q, s);
-        GemmDesc k2;
-        k2.acc64 = f64;
-        k2.M = m * no; k2.N = nv; k2.K = pn * no;
-        k2.A = Qb.p; k2.ta = tw; k2.sam = (long long)pn * no; k2.sak = 1;
-        k2.B = (const char*)f.Kov + (size_t)p0 * ov * es; k2.tb = f.dt; k2.sbk = nv; k2.sbn = 1;
-        k2.C = K2b.p; k2.tc = tw; k2.scm = nv; k2.scn = 1;
-        k2.beta = (p0 > 0) ? 1.0 : 0.0;
-        gemm_splitk(k2, auto_splits(k2.M, k2.N, k2.K), s);
+        if (timed) d.prof->end(s, 2.0 * Mz * (double)nv * (double)Kz);
+        if (need_k2) {
+          // Q[n][i][P][j] = sum_b Kov[P][i][b] X[n][j][b]
+          GemmDesc q;
+          q.acc64 = f64;
+          q.M = no; q.N = no; q.K = nv;
+          q.A = (const char*)f.Kov + (size_t)p0 * ov * es; q.ta = f.dt; q.sam = nv; q.sak = 1;
+          q.B = Xw; q.tb = tw; q.sbk = 1; q.sbn = nv;
+          q.C = Qb.p; q.tc = tw; q.scm = (long long)pn * no; q.scn = 1;
+          q.nb0 = pn; q.nb1 = m;
+          q.sA0 = ov; q.sB0 = 0; q.sC0 = no;
+          q.sA1 = 0; q.sB1 = ov; q.sC1 = (long long)no * pn * no;
+          gemm(q, s);
+          GemmDesc k2;
+          k2.acc64 = f64;
+          k2.M = m * no; k2.N = nv; k2.K = pn * no;
+          k2.A = Qb.p; k2.ta = tw; k2.sam = (long long)pn * no; k2.sak = 1;
+          k2.B = (const char*)f.Kov + (size_t)p0 * ov * es; k2.tb = f.dt; k2.sbk = nv; k2.sbn = 1;
+          k2.C = K2b.p; k2.tc = tw; k2.scm = nv; k2.scn = 1;
+          k2.beta = (p0 > 0) ? 1.0 : 0.0;
+          gemm_splitk(k2, auto_splits(k2.M, k2.N, k2.K), s);
+        }
       }
     }
   }

@@ -835,7 +835,7 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     precond_tda(R, sh, c.delta.as<double>(), nu, ov, out, s);
   };
   TdaOpT<float> T32 = [&](const float* Xi, int m, float* out) {
-    apply_operator(dims, Fr, Xi, m, OpMode::TDA, out, nullptr, false, s);
+    apply_operator(dims, Fr, Xi, m, OpMode::TDA, out, nullptr, p.tc, s);
   };
   TdaPre rid = [&](const double* R, const double* sh, const std::vector<double>& shh, int nu, double* out) {
     if (p.mixed) {   // FP32 inner solve on the BF16 ris factors
@@ -902,9 +902,9 @@ PairOp make_pair_op(const OpDims& dims, const FactorSet& F, bool tc, cudaStream_
     apply_operator(dims, F, Xi, m, OpMode::PAIRED, P, M, tc, s);
   };
 }
-PairOpT<float> make_pair_op32(const OpDims& dims, const FactorSet& F, cudaStream_t s) {
-  return [dims, F, s](const float* Xi, int m, float* P, float* M) {
-    apply_operator(dims, F, Xi, m, OpMode::PAIRED, P, M, false, s);
+PairOpT<float> make_pair_op32(const OpDims& dims, const FactorSet& F, bool tc, cudaStream_t s) {
+  return [dims, F, tc, s](const float* Xi, int m, float* P, float* M) {
+    apply_operator(dims, F, Xi, m, OpMode::PAIRED, P, M, tc, s);
   };
 }
 
@@ -950,7 +950,7 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
   const double* dl = c.delta.as<double>();
   PairPre diag = [&](const double* gp, const double* gm, const double* sh, const std::vector<double>&,
                      int nu, double* u, double* w) { precond_paired(gp, gm, sh, dl, nu, ov, u, w, s); };
-  PairOpT<float> T32 = make_pair_op32(dims, c.ris(o.precision), s);
+  PairOpT<float> T32 = make_pair_op32(dims, c.ris(o.precision), p.tc, s);
   PairPreT<float> diag32 = [&](const float* gp, const float* gm, const double* sh,
                                const std::vector<double>&, int nu, float* u, float* w) {
     precond_paired<float>(gp, gm, sh, dl, nu, ov, u, w, s);
@@ -1055,7 +1055,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
     axpy_rows(b.as<double>() + (size_t)f * n_dip * ov, mud.as<double>(), twod.as<double>(), n_dip, ov, s);
   PairPre diag = [&](const double* gp, const double* gm, const double* shv, const std::vector<double>&,
                      int nu, double* u, double* w) { precond_paired(gp, gm, shv, dl, nu, ov, u, w, s); };
-  PairOpT<float> T32 = make_pair_op32(dims, c.ris(o.precision), s);
+  PairOpT<float> T32 = make_pair_op32(dims, c.ris(o.precision), p.tc, s);
   PairPreT<float> diag32 = [&](const float* gp, const float* gm, const double* shv,
                                const std::vector<double>&, int nu, float* u, float* w) {
     precond_paired<float>(gp, gm, shv, dl, nu, ov, u, w, s);

@@ -1,18 +1,22 @@
-// tcgen05 tensor-core kernel for the exchange contraction of the exact operator,
-//   K1[(n,i)][b] = sum_P sum_a Z[(n,i)][P][a] L^P_ab           (Eq. hessian, (ij|ab) term)
-// the dominant cost of every response product (about 90% of its flops).
+// tcgen05 tensor-core contraction over the auxiliary index,
+//   C[m][n] (+)= sum_P sum_k A[m][P][k] B[P][n][k],
+// used for the exchange terms of the response products (Eq. hessian):
+//   K1[(n,i)][b] = sum_P sum_a Z[(n,i)][P][a] L^P_ab      ((ij|ab) term, k = a)
+//   K2[(n,i)][a] = sum_P sum_j Q[(n,i)][P][j] L^P_ja      ((ib|ja) term, k = j)
+// K1's contraction is the dominant cost of every product (about 70-90% of flops).
 //
-// Operands are split into BF16 hi + lo parts (x = hi + lo exactly to ~2^-17);
+// Exact operator: operands split into BF16 hi + lo parts (x = hi + lo to ~2^-17);
 // each tile pair contributes hi*hi + hi*lo + lo*hi (the lo*lo term is below the
-// FP32 accumulator's resolution) so the product has ~FP32 accuracy at BF16
-// tensor-core rate.
+// FP32 accumulator's resolution), so the product has ~FP32 accuracy at BF16
+// tensor-core rate.  ris operator: one BF16 product (its factors are BF16).
 //
-// Layout / mapping (all K-major, so both operands stream along a):
-//   A = Z  viewed as a 3-D tensor (a: nv, P: pn, row: M), row pitch pn*nvp
-//   B = L  viewed as a 3-D tensor (a: nv, b: nv, P: pn); L^P is symmetric so the
-//          row b of L^P read along a is the column b of the GEMM's B operand
-//   K loop: for each P in the CTA's split range, a-blocks of 64 (128 bytes, one
-//          128B-swizzle atom); TMA zero-fills a >= nv, b >= nv and rows >= M.
+// Layout / mapping (all K-major, so both operands stream along k):
+//   A viewed as a 3-D tensor (k: Kin, P: pn, row: M), row pitch pn*ldk
+//   B viewed as a 3-D tensor (k: Kin, n: N, P: pn), rows of ldk; for K1 the
+//          rows of the symmetric L^P are its columns, for K2 B is L^P_ov
+//          stored transposed ([P][a][j])
+//   K loop: for each P in the CTA's split range, k-blocks of 64 (128 bytes, one
+//          128B-swizzle atom); TMA zero-fills k >= Kin, n >= N and rows >= M.
 // CTA = 128 x 128 output tile, 6 warps: warp 0 issues TMA loads, warp 1 owns the
 // tensor memory and one elected lane issues tcgen05.mma, warps 2-5 drain the
 // FP32 accumulator from TMEM.  A 3-stage mbarrier ring connects producer and MMA;
@@ -34,17 +38,19 @@ namespace {
 constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 64;                       // bf16 elements per 128-byte row
-constexpr int STAGES = 3;
 constexpr int A_BYTES = BM * BK * 2;          // 16 KB per hi or lo tile
 constexpr int B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+template <bool SPLIT> struct Cfg {
+  static constexpr int STAGE_BYTES = SPLIT ? 2 * A_BYTES + 2 * B_BYTES : A_BYTES + B_BYTES;
+  static constexpr int STAGES = SPLIT ? 3 : 6;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+};
 constexpr int THREADS = 192;
 constexpr long long WAIT_LIMIT = 1ll << 23;
 
 struct Params {
   int M, N;          // output rows / columns
-  int nab;           // a-blocks per P
+  int nab;           // k-blocks per P
   int total;         // pn * nab steps
   int per_split;     // steps per split
   float* part;       // [splits][M][N]
@@ -114,10 +120,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+template <bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
 k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
              const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
              Params p) {
+  constexpr int STAGES = Cfg<SPLIT>::STAGES;
+  constexpr int STAGE_BYTES = Cfg<SPLIT>::STAGE_BYTES;
+  constexpr int B_OFF = SPLIT ? 2 * A_BYTES : A_BYTES;   // first B tile in a stage
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -158,9 +168,11 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       unsigned char* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
       tma_load_3d(st, &mA_hi, &full[s], a0, P, m0);
-      tma_load_3d(st + A_BYTES, &mA_lo, &full[s], a0, P, m0);
-      tma_load_3d(st + 2 * A_BYTES, &mB_hi, &full[s], a0, n0, P);
-      tma_load_3d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], a0, n0, P);
+      tma_load_3d(st + B_OFF, &mB_hi, &full[s], a0, n0, P);
+      if (SPLIT) {
+        tma_load_3d(st + A_BYTES, &mA_lo, &full[s], a0, P, m0);
+        tma_load_3d(st + B_OFF + B_BYTES, &mB_lo, &full[s], a0, n0, P);
+      }
     }
     // let the copies already issued land before the CTA can exit
     for (int i = max(0, nk - STAGES); i < nk; ++i) {
@@ -174,14 +186,16 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       if (!mbar_wait(&full[s], (uint32_t)(i / STAGES) & 1u)) { atomicOr(p.err, 4); ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       unsigned char* st = smem + s * STAGE_BYTES;
-      const uint64_t ah = sdesc(st), al = sdesc(st + A_BYTES);
-      const uint64_t bh = sdesc(st + 2 * A_BYTES), bl = sdesc(st + 2 * A_BYTES + B_BYTES);
+      const uint64_t ah = sdesc(st), bh = sdesc(st + B_OFF);
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 16 bf16 = 32 bytes along K
         mma_bf16(tmem, ah + off, bh + off, (i > 0 || kk > 0) ? 1u : 0u);
-        mma_bf16(tmem, ah + off, bl + off, 1u);
-        mma_bf16(tmem, al + off, bh + off, 1u);
+        if (SPLIT) {
+          const uint64_t al = sdesc(st + A_BYTES), bl = sdesc(st + B_OFF + B_BYTES);
+          mma_bf16(tmem, ah + off, bl + off, 1u);
+          mma_bf16(tmem, al + off, bh + off, 1u);
+        }
       }
       mma_commit(&empty[s]);
     }
@@ -231,6 +245,166 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Stage-1 contractions of the exchange terms, batched over P:
+//   C_P[r][c] = sum_(k<K) A[r][k] B_P[c][k]   (r < M, c < N <= 256)
+// written as BF16 hi (+ lo) into the stage-2 operand layout
+//   out[(g*N + c)][P][ri] with r = g*R + ri, row pitch pn*ldo (ldo = pad8(R)):
+//   K1: A = X^T per trial vector ([(n,a)][j]), B_P = L^P_oo ([i][j]) -> Z[(n,i)][P][a]
+//   K2: A = X ([(n,j)][b]),            B_P = L^P_ov ([i][b]) -> Q[(n,i)][P][j]
+// Persistent over P: the CTA owns one M-tile and the P range blockIdx.y*ppc ...;
+// k-blocks of A and B_P stream through a TMA/mbarrier ring; the TMEM
+// accumulator is double-buffered so the epilogue of one P overlaps the MMAs of
+// the next (tmem_full / tmem_empty barriers).
+struct S1Params {
+  int M, N, R, ldo, pn, ppc, nkb;
+  int nb;              // MMA N (multiple of 16, >= N)
+  int acc_cols;        // TMEM columns per accumulator buffer
+  int stages, stage_bytes, a_bytes, b_bytes;
+  __nv_bfloat16* out_hi;
+  __nv_bfloat16* out_lo;
+  int* err;
+};
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(THREADS, 1)
+k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
+            const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
+            S1Params p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + p.stages * p.stage_bytes);
+  uint64_t* empty = full + p.stages;
+  uint64_t* tfull = empty + p.stages;      // [2]
+  uint64_t* tempty = tfull + 2;            // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM;
+  const int P0 = blockIdx.y * p.ppc;
+  const int nP = max(0, min(p.pn, P0 + p.ppc) - P0);
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(p.nb >> 3) << 17) |
+                         ((uint32_t)(BM >> 4) << 24);
+  const int b_off = SPLIT ? 2 * p.a_bytes : p.a_bytes;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)), "r"(2 * p.acc_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int nsteps = nP * p.nkb;
+
+  if (warp == 0 && lane == 0) {
+    for (int i = 0; i < nsteps; ++i) {
+      const int s = i % p.stages;
+      if (!mbar_wait(&empty[s], ((uint32_t)(i / p.stages) & 1u) ^ 1u)) { atomicOr(p.err, 16); break; }
+      const int P = P0 + i / p.nkb, k0 = (i % p.nkb) * BK;
+      unsigned char* st = smem + s * p.stage_bytes;
+      mbar_expect_tx(&full[s], p.stage_bytes);
+      tma_load_3d(st, &mA_hi, &full[s], k0, m0, 0);
+      tma_load_3d(st + b_off, &mB_hi, &full[s], k0, 0, P);
+      if (SPLIT) {
+        tma_load_3d(st + p.a_bytes, &mA_lo, &full[s], k0, m0, 0);
+        tma_load_3d(st + b_off + p.b_bytes, &mB_lo, &full[s], k0, 0, P);
+      }
+    }
+    for (int i = max(0, nsteps - p.stages); i < nsteps; ++i)
+      if (!mbar_wait(&full[i % p.stages], (uint32_t)(i / p.stages) & 1u)) { atomicOr(p.err, 32); break; }
+  } else if (warp == 1 && lane == 0) {
+    for (int j = 0; j < nP; ++j) {
+      const int buf = j & 1;
+      // wait until the epilogue has drained this accumulator buffer (use j/2 - 1)
+      if (!mbar_wait(&tempty[buf], ((uint32_t)(j >> 1) & 1u) ^ 1u)) { atomicOr(p.err, 64); break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc = tmem + (uint32_t)(buf * p.acc_cols);
+      for (int kb = 0; kb < p.nkb; ++kb) {
+        const int i = j * p.nkb + kb;
+        const int s = i % p.stages;
+        if (!mbar_wait(&full[s], (uint32_t)(i / p.stages) & 1u)) { atomicOr(p.err, 128); break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* st = smem + s * p.stage_bytes;
+        const uint64_t ah = sdesc(st), bh = sdesc(st + b_off);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t off = (uint64_t)(kk * 32) >> 4;
+          asm volatile(
+              "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
+              "l"(ah + off), "l"(bh + off), "r"(idesc), "r"((kb > 0 || kk > 0) ? 1u : 0u));
+          if (SPLIT) {
+            const uint64_t al = sdesc(st + p.a_bytes), bl = sdesc(st + b_off + p.b_bytes);
+            asm volatile(
+                "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
+                "l"(ah + off), "l"(bl + off), "r"(idesc), "r"(1u));
+            asm volatile(
+                "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
+                "l"(al + off), "l"(bh + off), "r"(idesc), "r"(1u));
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&tfull[buf]);
+    }
+  } else if (warp >= 2) {
+    const int q = warp & 3;
+    const int r = m0 + q * 32 + lane;
+    const int g = r / p.R, ri = r - (r / p.R) * p.R;
+    for (int j = 0; j < nP; ++j) {
+      const int buf = j & 1;
+      bool ok = mbar_wait(&tfull[buf], (uint32_t)(j >> 1) & 1u);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) { if (lane == 0) atomicOr(p.err, 256); break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int P = P0 + j;
+      for (int c0 = 0; c0 < p.N; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * p.acc_cols + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+            " [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (r < p.M) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const int c = c0 + t;
+            if (c < p.N) {
+              const size_t o = (((size_t)g * p.N + c) * p.pn + P) * p.ldo + ri;
+              const float x = __uint_as_float(v[t]);
+              const __nv_bfloat16 h = __float2bfloat16_rn(x);
+              p.out_hi[o] = h;
+              if (SPLIT) p.out_lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[buf])) : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * p.acc_cols));
+  }
+}
+
 // Sum the split partials into out (FP32), accumulating when asked.
 __global__ void k_sum_splits(const float* __restrict__ part, int S, long long MN, float* out,
                              int accumulate) {
@@ -254,7 +428,27 @@ __global__ void k_split_pad(const float* __restrict__ Z, int M, int pn, int nv, 
     if (a < nv) v = Z[rp * nv + a];
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     hi[t] = h;
-    lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
+    if (lo) lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// Transpose + split of factor rows: src [rows][n1][n2] -> dst [rows][n2][pad8(n1)]
+// (dst[r][b][a] = src[r][a][b]; pads zero).  lo may be NULL (plain BF16).
+template <typename TS>
+__global__ void k_transpose_split(const TS* __restrict__ src, int rows, int n1, int n2, int ld,
+                                  __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  const long long tot = (long long)rows * n2 * ld;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(t % ld);
+    const long long rb = t / ld;
+    const int b = (int)(rb % n2);
+    const long long r = rb / n2;
+    float v = 0.f;
+    if (a < n1) v = (float)src[(r * n1 + a) * n2 + b];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[t] = h;
+    if (lo) lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
   }
 }
 
@@ -303,44 +497,151 @@ void tc_split_pad(const float* Z, int M, int pn, int nv, __nv_bfloat16* hi, __nv
   TD_LAUNCH_CHECK();
 }
 
-void tc_exchange_k1(const __nv_bfloat16* Zhi, const __nv_bfloat16* Zlo, int M, int pn, int nv,
-                    const __nv_bfloat16* Lhi, const __nv_bfloat16* Llo, float* out, bool accumulate,
-                    int* err, cudaStream_t s) {
-  if (M <= 0 || pn <= 0) return;
-  const int nvp = tc_pad(nv);
-  const int nab = (nv + BK - 1) / BK;
+void tc_transpose_split(const void* src, DType ts, int rows, int n1, int n2, __nv_bfloat16* hi,
+                        __nv_bfloat16* lo, cudaStream_t s) {
+  const int ld = tc_pad(n1);
+  const long long tot = (long long)rows * n2 * ld;
+  long long g = (tot + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (ts == DType::F32)
+    k_transpose_split<float><<<(unsigned)g, 256, 0, s>>>((const float*)src, rows, n1, n2, ld, hi, lo);
+  else if (ts == DType::BF16)
+    k_transpose_split<__nv_bfloat16><<<(unsigned)g, 256, 0, s>>>((const __nv_bfloat16*)src, rows, n1, n2,
+                                                                 ld, hi, lo);
+  else
+    k_transpose_split<double><<<(unsigned)g, 256, 0, s>>>((const double*)src, rows, n1, n2, ld, hi, lo);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int pn, int Kin,
+                 const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, float* out,
+                 bool accumulate, int* err, cudaStream_t s) {
+  if (M <= 0 || pn <= 0 || N <= 0) return;
+  const bool split = (Alo != nullptr);
+  TD_REQUIRE(split == (Blo != nullptr), TDDFT_ERR_ARG, "tc_contract: hi/lo operands mismatch");
+  const int ldk = tc_pad(Kin);
+  const int nab = (Kin + BK - 1) / BK;
   const int total = pn * nab;
-  const int mt = (M + BM - 1) / BM, nt = (nv + BN - 1) / BN;
+  const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
   int splits = (2 * 152 + mt * nt - 1) / (mt * nt);
   if (splits > total) splits = total;
   if (splits < 1) splits = 1;
   const int per = (total + splits - 1) / splits;
   splits = (total + per - 1) / per;
 
-  const cuuint64_t dA[3] = {(cuuint64_t)nv, (cuuint64_t)pn, (cuuint64_t)M};
-  const cuuint64_t sA[2] = {(cuuint64_t)nvp * 2, (cuuint64_t)pn * nvp * 2};
+  const cuuint64_t dA[3] = {(cuuint64_t)Kin, (cuuint64_t)pn, (cuuint64_t)M};
+  const cuuint64_t sA[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)pn * ldk * 2};
   const cuuint32_t bA[3] = {BK, 1, BM};
-  const cuuint64_t dB[3] = {(cuuint64_t)nv, (cuuint64_t)nv, (cuuint64_t)pn};
-  const cuuint64_t sB[2] = {(cuuint64_t)nvp * 2, (cuuint64_t)nv * nvp * 2};
+  const cuuint64_t dB[3] = {(cuuint64_t)Kin, (cuuint64_t)N, (cuuint64_t)pn};
+  const cuuint64_t sB[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)N * ldk * 2};
   const cuuint32_t bB[3] = {BK, BN, 1};
-  CUtensorMap mAh = make_map(Zhi, dA, sA, bA), mAl = make_map(Zlo, dA, sA, bA);
-  CUtensorMap mBh = make_map(Lhi, dB, sB, bB), mBl = make_map(Llo, dB, sB, bB);
+  CUtensorMap mAh = make_map(Ahi, dA, sA, bA), mBh = make_map(Bhi, dB, sB, bB);
+  CUtensorMap mAl = split ? make_map(Alo, dA, sA, bA) : mAh;
+  CUtensorMap mBl = split ? make_map(Blo, dB, sB, bB) : mBh;
 
-  DevBuf part((size_t)splits * M * nv * 4, s);
-  Params p{M, nv, nab, total, per, part.as<float>(), err};
-  static bool attr = false;
-  if (!attr) {
-    TD_CUDA(cudaFuncSetAttribute(k1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
-  }
+  DevBuf part((size_t)splits * M * N * 4, s);
+  Params p{M, N, nab, total, per, part.as<float>(), err};
   dim3 grid(nt, mt, splits);
-  k1_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, p);
+  if (split) {
+    static bool attr = false;
+    if (!attr) {
+      TD_CUDA(cudaFuncSetAttribute(k1_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Cfg<true>::SMEM_BYTES));
+      attr = true;
+    }
+    k1_tc_kernel<true><<<grid, THREADS, Cfg<true>::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, p);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      TD_CUDA(cudaFuncSetAttribute(k1_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Cfg<false>::SMEM_BYTES));
+      attr = true;
+    }
+    k1_tc_kernel<false><<<grid, THREADS, Cfg<false>::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, p);
+  }
   count_launch();
   TD_LAUNCH_CHECK();
-  const long long MN = (long long)M * nv;
+  const long long MN = (long long)M * N;
   long long g = (MN + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
   k_sum_splits<<<(unsigned)g, 256, 0, s>>>(part.as<float>(), splits, MN, out, accumulate ? 1 : 0);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
+               const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, int pn, int R,
+               __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int* err, cudaStream_t s) {
+  if (M <= 0 || pn <= 0 || N <= 0) return;
+  TD_REQUIRE(N <= 256, TDDFT_ERR_ARG, "tc_stage1: N above 256");
+  const bool split = (Alo != nullptr);
+  TD_REQUIRE(split == (Blo != nullptr) && split == (out_lo != nullptr), TDDFT_ERR_ARG,
+             "tc_stage1: hi/lo operands mismatch");
+  const int ldk = tc_pad(K);
+  const int nb = (N + 15) & ~15;
+  int acc_cols = 32;
+  while (acc_cols < nb) acc_cols *= 2;
+  const int a_bytes = BM * BK * 2, b_bytes = nb * BK * 2;
+  const int stage_bytes = split ? 2 * (a_bytes + b_bytes) : a_bytes + b_bytes;
+  int stages = (200 * 1024) / stage_bytes;
+  if (stages > 6) stages = 6;
+  TD_REQUIRE(stages >= 2, TDDFT_ERR_ARG, "tc_stage1: tile too large");
+  const int smem = stages * stage_bytes + 1024 + 256;
+  const int mt = (M + BM - 1) / BM;
+  int groups = (2 * 152 + mt - 1) / mt;
+  if (groups > pn) groups = pn;
+  const int ppc = (pn + groups - 1) / groups;
+  groups = (pn + ppc - 1) / ppc;
+
+  const cuuint64_t dA[3] = {(cuuint64_t)K, (cuuint64_t)M, 1};
+  const cuuint64_t sA[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)M * ldk * 2};
+  const cuuint32_t bA[3] = {BK, BM, 1};
+  const cuuint64_t dB[3] = {(cuuint64_t)K, (cuuint64_t)N, (cuuint64_t)pn};
+  const cuuint64_t sB[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)N * ldk * 2};
+  const cuuint32_t bB[3] = {BK, (cuuint32_t)nb, 1};
+  CUtensorMap mAh = make_map(Ahi, dA, sA, bA), mBh = make_map(Bhi, dB, sB, bB);
+  CUtensorMap mAl = split ? make_map(Alo, dA, sA, bA) : mAh;
+  CUtensorMap mBl = split ? make_map(Blo, dB, sB, bB) : mBh;
+  S1Params p{M, N, R, tc_pad(R), pn, ppc, (K + BK - 1) / BK, nb, acc_cols, stages, stage_bytes,
+             a_bytes, b_bytes, out_hi, out_lo, err};
+  dim3 grid(mt, groups, 1);
+  if (split) {
+    TD_CUDA(cudaFuncSetAttribute(k_stage1_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_stage1_tc<true><<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
+  } else {
+    TD_CUDA(cudaFuncSetAttribute(k_stage1_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_stage1_tc<false><<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
+  }
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+// F64/F32 rows [rows][n] -> BF16 hi (+ lo) [rows][tc_pad(n)]
+template <typename TS>
+__global__ void k_pad_split(const TS* __restrict__ src, long long rows, int n, int ld,
+                            __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  const long long tot = rows * ld;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(t % ld);
+    const long long r = t / ld;
+    const float v = a < n ? (float)src[r * n + a] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[t] = h;
+    if (lo) lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+void tc_pad_split(const void* src, DType ts, long long rows, int n, __nv_bfloat16* hi,
+                  __nv_bfloat16* lo, cudaStream_t s) {
+  const int ld = tc_pad(n);
+  const long long tot = rows * ld;
+  long long g = (tot + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (ts == DType::F64) k_pad_split<double><<<(unsigned)g, 256, 0, s>>>((const double*)src, rows, n, ld, hi, lo);
+  else if (ts == DType::F32) k_pad_split<float><<<(unsigned)g, 256, 0, s>>>((const float*)src, rows, n, ld, hi, lo);
+  else k_pad_split<__nv_bfloat16><<<(unsigned)g, 256, 0, s>>>((const __nv_bfloat16*)src, rows, n, ld, hi, lo);
   count_launch();
   TD_LAUNCH_CHECK();
 }

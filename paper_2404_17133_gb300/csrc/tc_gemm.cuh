@@ -8,18 +8,36 @@ namespace tddft {
 // every TMA stride is a multiple of 16 bytes.
 int tc_pad(int nv);
 
-// FP32 Z [M][pn][nv] -> BF16 hi + lo [M][pn][tc_pad(nv)] (pads zero).
+// FP32 Z [M][pn][nv] -> BF16 hi (+ lo unless NULL) [M][pn][tc_pad(nv)] (pads zero).
 void tc_split_pad(const float* Z, int M, int pn, int nv, __nv_bfloat16* hi, __nv_bfloat16* lo,
                   cudaStream_t s);
 
-// K1[(n,i)][b] (+)= sum_(P,a) Z[(n,i)][P][a] Kvv[P][a][b] for one chunk of pn
-// auxiliary rows, with Z and Kvv each split as hi + lo BF16 and the three
-// products hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory.
-//   Zhi/Zlo [M][pn][tc_pad(nv)]; Kvv_hi/lo [pn][nv][tc_pad(nv)] (symmetric in a,b);
-//   out [M][nv] FP32, accumulated into when `accumulate`.  Timeouts of the
-//   kernel's internal waits are reported by OR-ing a nonzero code into *err.
-void tc_exchange_k1(const __nv_bfloat16* Zhi, const __nv_bfloat16* Zlo, int M, int pn, int nv,
-                    const __nv_bfloat16* Kvv_hi, const __nv_bfloat16* Kvv_lo, float* out,
-                    bool accumulate, int* err, cudaStream_t s);
+// Factor rows src [rows][n1][n2] (F64, F32 or BF16) -> BF16 hi (+ lo unless NULL)
+// [rows][n2][tc_pad(n1)], transposed in the last two indices.
+void tc_transpose_split(const void* src, DType ts, int rows, int n1, int n2, __nv_bfloat16* hi,
+                        __nv_bfloat16* lo, cudaStream_t s);
+
+// C[m][n] (+)= sum_(P<pn) sum_(k<Kin) A[m][P][k] B[P][n][k] on the tcgen05 tensor
+// cores.  A: [M][pn][tc_pad(Kin)] BF16, B: [pn][N][tc_pad(Kin)] BF16, C: [M][N] FP32,
+// accumulated into when `accumulate`.  With Alo/Blo (both or neither) the operands
+// are hi + lo splits and the three products hi*hi + hi*lo + lo*hi are formed;
+// without, one BF16 product.  Timeouts of the kernel's internal waits are
+// reported by OR-ing a nonzero code into *err.
+void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int pn, int Kin,
+                 const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, float* out,
+                 bool accumulate, int* err, cudaStream_t s);
+
+// Rows src [rows][n] (F64, F32 or BF16) -> BF16 hi (+ lo unless NULL) [rows][tc_pad(n)].
+void tc_pad_split(const void* src, DType ts, long long rows, int n, __nv_bfloat16* hi,
+                  __nv_bfloat16* lo, cudaStream_t s);
+
+// Stage-1 exchange contraction on the tensor cores, batched over P:
+//   C_P[r][c] = sum_(k<K) A[r][k] B_P[c][k],  A: [M][tc_pad(K)], B: [pn][N][tc_pad(K)],
+// written as BF16 hi (+ lo) to out[(g*N + c)][P][ri] (r = g*R + ri, row pitch
+// pn*tc_pad(R)) -- the A operand layout of tc_contract.  N <= 256.  With lo
+// operands the three hi/lo products are formed.
+void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
+               const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, int pn, int R,
+               __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int* err, cudaStream_t s);
 
 }  // namespace tddft

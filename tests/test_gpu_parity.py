@@ -5,7 +5,7 @@ Tolerances (see the design notes for the derivation):
   * operator products, MIXED exact (FP32 factors, FP32 accumulation): 2e-5 relative;
   * ris products, MIXED (BF16 factors): 2e-2 relative (preconditioner only);
   * exact products, MIXED on the tensor cores (BF16 hi+lo, three products,
-    FP32 accumulation): 5e-5 relative;
+    FP32 accumulation): 5e-5 relative; ris products on the tensor cores: 2e-2;
   * excitation energies: 1e-6 Ha (PLAIN), 1e-5 Ha (MIXED);
   * polarizabilities: 1e-6 relative (PLAIN), 1e-5 relative (MIXED).
 """
@@ -88,6 +88,12 @@ def test_tensor_core_products(case, api):
         gp, gm = s.apply(1, X, precision=api.MIXED, tensor_cores=True)
         rp, rm = op.apb_amb(X)
         assert _rel(gp, rp) < 5e-5 and _rel(gm, rm) < 5e-5
+        # ris operator on the tensor cores: one BF16 product (preconditioner only)
+        T = O.ris_operator(p)
+        assert _rel(s.apply(2, X, precision=api.MIXED, tensor_cores=True), T.tda(X)) < 2e-2
+        tp, tm = s.apply(3, X, precision=api.MIXED, tensor_cores=True)
+        rtp, rtm = T.apb_amb(X)
+        assert _rel(tp, rtp) < 2e-2 and _rel(tm, rtm) < 2e-2
 
 
 @pytest.mark.parametrize("pc", ["diag", "rid"])
