@@ -33,6 +33,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -53,6 +55,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precond", default="rid", choices=["rid", "diag"])
+    ap.add_argument("--apply-only", type=int, default=0, metavar="K",
+                    help="time K exact pair products ((A+B)X, (A-B)X) of 2*n_states device vectors "
+                         "and exit (a short program for kernel profiling)")
     return ap.parse_args()
 
 
@@ -169,7 +174,6 @@ def reference_arm(args, rank, world):
 
 
 def our_arm(args, rank, world, local):
-    import numpy as np
     import torch
 
     torch.cuda.set_device(local)
@@ -209,6 +213,10 @@ def our_arm(args, rank, world, local):
     o_rpa = api.default_opts(n_states=N_STATES, precond=pc, precision=api.MIXED, tensor_cores=tc)
     o_pol = api.default_opts(precond=pc, precision=api.MIXED, tensor_cores=tc)
     solver = make_solver(dev, stream.cuda_stream)
+    if args.apply_only > 0:
+        apply_only(args, api, solver, p, tc, stream)
+        solver.close()
+        return
 
     def step(s):
         a = s.solve_rpa(o_rpa, want_vectors=False)
@@ -316,6 +324,22 @@ def our_arm(args, rank, world, local):
     solver.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def apply_only(args, api, solver, p, tc, stream):
+    """K exact pair products on 2*n_states device vectors, each timed with CUDA events."""
+    import torch
+    X = torch.from_numpy(np.random.default_rng(7).standard_normal((2 * N_STATES, p.n_ov))).cuda()
+    ms = []
+    for _ in range(args.apply_only):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.apply(1, X, precision=api.MIXED, tensor_cores=bool(tc))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"apply_only": args.apply_only, "m": 2 * N_STATES, "ms": ms,
+                      "workload": WORKLOAD, "tensor_cores": bool(tc)}), flush=True)
 
 
 def main():

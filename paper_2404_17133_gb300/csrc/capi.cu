@@ -197,6 +197,15 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
 
     c = new Ctx();
     TD_CUDA(cudaGetDevice(&c->device));
+    {
+      // Solves allocate and free many small stream-ordered work buffers; keep the
+      // device pool's memory mapped across synchronisations instead of returning
+      // it to the driver at every sync (the default threshold of 0).
+      cudaMemPool_t pool;
+      TD_CUDA(cudaDeviceGetDefaultMemPool(&pool, c->device));
+      uint64_t keep = ~0ull;
+      TD_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
     if (cuda_stream) {
       c->s = (cudaStream_t)cuda_stream;
     } else {

@@ -48,12 +48,22 @@ int trace_level() {
 }
 bool trace_on() { return trace_level() >= 1; }
 
-enum Phase { PH_MV = 0, PH_RIS, PH_ORTH, PH_PROJ, PH_SMALL, PH_VEC, PH_N };
-const char* kPhaseNames[PH_N] = {"exact_mv", "ris_mv", "orth", "proj+factor", "small_eig/solve", "vector_ops"};
+enum Phase { PH_MV = 0, PH_RIS, PH_ORTH, PH_PROJ, PH_SMALL, PH_VEC, PH_ORTH_IN, PH_PROJ_IN, PH_SMALL_IN,
+             PH_VEC_IN, PH_EIG, PH_CHOL, PH_SMM, PH_LU, PH_TRSV, PH_N };
+const char* kPhaseNames[PH_N] = {"exact_mv", "ris_mv", "orth", "proj+factor", "small", "vec", "orth_in",
+                                 "proj+factor_in", "small_in", "vec_in", "[eig32]", "[chol]", "[small_mm]",
+                                 "[lu]", "[trsv]"};
 thread_local double g_phase[PH_N];
+thread_local int g_inner = 0;   // > 0 inside the ris inner solves and guesses
+struct InnerScope {
+  InnerScope() { ++g_inner; }
+  ~InnerScope() { --g_inner; }
+};
 struct ScopedPhase {
   int id; cudaStream_t s; Clock::time_point t0; bool on;
   ScopedPhase(int i, cudaStream_t st) : id(i), s(st), on(trace_level() >= 2) {
+    if (i >= PH_EIG && trace_level() < 3) on = false;
+    if (g_inner > 0 && i >= PH_ORTH && i <= PH_VEC) id = i + (PH_ORTH_IN - PH_ORTH);
     if (on) { cudaStreamSynchronize(s); t0 = Clock::now(); }
   }
   void stop() {
@@ -246,6 +256,8 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
                     double tol, int max_iter, int cap, int rounds, Counters& cnt, bool exact_op,
                     cudaStream_t s) {
   TdaOut o;
+  if (!exact_op) ++g_inner;
+  struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
   k = std::min(k, ov);
   cap = std::min(cap, kSmallMax);
   TD_REQUIRE(k >= 1 && k <= kWantMax, TDDFT_ERR_ARG, "n_states out of range");
@@ -283,7 +295,10 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
     n_proj = N;
     kk = std::min(k, N);
     ScopedPhase ph_small(PH_SMALL, s);
-    eig32(a.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);               // Eq. 2
+    {
+      ScopedPhase f(trace_level() >= 3 ? PH_EIG : PH_N - 1, s);
+      eig32(a.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);             // Eq. 2
+    }
     refine_lowest(a.as<double>(), cap, N, kk, lam32.as<float>(), vec32.as<float>(), lam.as<double>(),
                   x.as<double>(), scr.as<double>(), rounds, s);
     ph_small.stop();
@@ -376,11 +391,20 @@ struct PairedSpace {
     sym_fill(ap.as<double>(), cap, n_old, n_new, s);
     sym_fill(am.as<double>(), cap, n_old, n_new, s);
     TD_CUDA(cudaMemcpyAsync(L.p, am.p, (size_t)cap * cap * 8, cudaMemcpyDeviceToDevice, s));
-    cholesky(L.as<double>(), cap, N, info.as<int>(), s);
-    // tmp = a+ L ; H = L^T tmp
-    small_mm(N, N, N, ap.as<double>(), cap, 1, L.as<double>(), cap, 1, tmp.as<double>(), cap, s);
-    small_mm(N, N, N, L.as<double>(), 1, cap, tmp.as<double>(), cap, 1, H.as<double>(), cap, s);
-    if (eig) eig32(H.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);
+    {
+      ScopedPhase f(trace_level() >= 3 ? PH_CHOL : PH_N - 1, s);
+      cholesky(L.as<double>(), cap, N, info.as<int>(), s);
+    }
+    {
+      ScopedPhase f(trace_level() >= 3 ? PH_SMM : PH_N - 1, s);
+      // tmp = a+ L ; H = L^T tmp
+      small_mm(N, N, N, ap.as<double>(), cap, 1, L.as<double>(), cap, 1, tmp.as<double>(), cap, s);
+      small_mm(N, N, N, L.as<double>(), 1, cap, tmp.as<double>(), cap, 1, H.as<double>(), cap, s);
+    }
+    if (eig) {
+      ScopedPhase f(trace_level() >= 3 ? PH_EIG : PH_N - 1, s);
+      eig32(H.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);
+    }
     n_old = N;
     n_new = 0;
   }
@@ -411,6 +435,8 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
                            double tol, int max_iter, int cap, bool lu_fp32, bool exact_op,
                            Counters& cnt, T* Uout, T* Wout, cudaStream_t s) {
   PairedLinOut o;
+  if (!exact_op) ++g_inner;
+  struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
   cap = std::min(cap, kSmallMax);
   constexpr size_t es = sizeof(T);
   PairedSpace<T> sp(ov, cap, s);
@@ -471,15 +497,21 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
       axpy_rows<double>(rhs.as<double>(), hm.as<double>(), sh.as<double>(), nr, N, s);
     }
     // (H - s^2) u~ = rhs for every shift
-    lu_shift_solve(sp.H.template as<double>(), cap, N, sig2.as<double>(), nr, rhs.as<double>(), ut.as<double>(),
-                   lu_fp32, s);
+    {
+      ScopedPhase f(trace_level() >= 3 ? PH_LU : PH_N - 1, s);
+      lu_shift_solve(sp.H.template as<double>(), cap, N, sig2.as<double>(), nr, rhs.as<double>(),
+                     ut.as<double>(), lu_fp32, s);
+    }
     // u = L u~ : u[r][i] = sum_q L[i][q] u~[r][q]
     small_mm(nr, N, N, ut.as<double>(), N, 1, Lp, 1, cap, uc.as<double>(), N, s);
     // w = L^-T (z- + s u~)
     if (gm) TD_CUDA(cudaMemcpyAsync(wc.p, hm.p, (size_t)nr * N * 8, cudaMemcpyDeviceToDevice, s));
     else TD_CUDA(cudaMemsetAsync(wc.p, 0, (size_t)nr * N * 8, s));
     axpy_rows<double>(wc.as<double>(), ut.as<double>(), sh.as<double>(), nr, N, s);
-    trsv_rows(Lp, cap, N, wc.as<double>(), nr, 1, s);
+    {
+      ScopedPhase f(trace_level() >= 3 ? PH_TRSV : PH_N - 1, s);
+      trsv_rows(Lp, cap, N, wc.as<double>(), nr, 1, s);
+    }
     ph_small.stop();
     ScopedPhase ph_vec(PH_VEC, s);
     combo<T>(uc.as<double>(), nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
@@ -561,6 +593,8 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
                     double tol, int max_iter, int cap, int rounds, Counters& cnt, bool exact_op,
                     cudaStream_t s) {
   RpaOut o;
+  if (!exact_op) ++g_inner;
+  struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
   k = std::min(k, ov);
   cap = std::min(cap, kSmallMax);
   TD_REQUIRE(k >= 1 && k <= kWantMax, TDDFT_ERR_ARG, "n_states out of range");
@@ -692,6 +726,7 @@ template <typename T>
 void inner_tda(int ov, const TdaOpT<T>& Top, const double* delta, const T* R, const double* sh,
                const std::vector<double>& shh, int nu, double tol, int max_iter, bool lu_fp32,
                Counters& cnt, T* out, cudaStream_t s) {
+  InnerScope inner_scope;
   const int cap = kSmallMax;
   constexpr size_t es = sizeof(T);
   DevBuf S((size_t)cap * ov * es, s), TS((size_t)cap * ov * es, s), t((size_t)cap * cap * 8, s);
