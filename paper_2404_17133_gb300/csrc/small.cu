@@ -359,28 +359,29 @@ __global__ void __launch_bounds__(256) k_shifted(const double* __restrict__ H, i
   for (int t = tid; t < n; t += blockDim.x) Y[(long long)rr * n + t] = best[t];
 }
 
-__global__ void __launch_bounds__(1024) k_cholesky(double* __restrict__ H, int ldh, int n,
+template <typename S>
+__global__ void __launch_bounds__(1024) k_cholesky(S* __restrict__ H, int ldh, int n,
                                                    int* __restrict__ info) {
-  extern __shared__ double smc[];
+  extern __shared__ __align__(16) unsigned char chol_raw[];
+  S* A = reinterpret_cast<S*>(chol_raw);
   __shared__ int bad;
   const int ld = n + 1;
-  double* A = smc;
   const int tid = threadIdx.x;
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     int r = idx / n, c = idx - r * n;
-    A[r * ld + c] = 0.5 * (H[(long long)r * ldh + c] + H[(long long)c * ldh + r]);
+    A[r * ld + c] = S(0.5) * (H[(long long)r * ldh + c] + H[(long long)c * ldh + r]);
   }
   if (tid == 0) bad = 0;
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     if (tid == 0) {
-      double d = A[j * ld + j];
-      if (!(d > 0.0) || !isfinite(d)) bad = j + 1;
+      S d = A[j * ld + j];
+      if (!(d > S(0)) || !isfinite(d)) bad = j + 1;
       else A[j * ld + j] = sqrt(d);
     }
     __syncthreads();
     if (bad) break;
-    double piv = A[j * ld + j];
+    S piv = A[j * ld + j];
     for (int r = j + 1 + tid; r < n; r += blockDim.x) A[r * ld + j] /= piv;
     __syncthreads();
     const int m = n - j - 1;
@@ -393,15 +394,16 @@ __global__ void __launch_bounds__(1024) k_cholesky(double* __restrict__ H, int l
   if (tid == 0) info[0] = bad;
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     int r = idx / n, c = idx - r * n;
-    H[(long long)r * ldh + c] = (c <= r && !bad) ? A[r * ld + c] : 0.0;
+    H[(long long)r * ldh + c] = (c <= r && !bad) ? A[r * ld + c] : S(0);
   }
 }
 
-__global__ void __launch_bounds__(256) k_trsv(const double* __restrict__ L, int ldl, int n,
-                                              double* __restrict__ B, int trans) {
-  __shared__ double b[kSmallMax];
-  __shared__ double xj;
-  double* row = B + (long long)blockIdx.x * n;
+template <typename S>
+__global__ void __launch_bounds__(256) k_trsv(const S* __restrict__ L, int ldl, int n,
+                                              S* __restrict__ B, int trans) {
+  __shared__ S b[kSmallMax];
+  __shared__ S xj;
+  S* row = B + (long long)blockIdx.x * n;
   for (int t = threadIdx.x; t < n; t += blockDim.x) b[t] = row[t];
   __syncthreads();
   if (!trans) {
@@ -484,9 +486,9 @@ __global__ void __launch_bounds__(1024) k_chol_drop(const double* __restrict__ G
 // One CTA per right-hand side r: Gaussian elimination with partial pivoting on
 // [(H - sigma_r I) | b_r] in shared memory (compute type T), then back substitution.
 template <typename T>
-__global__ void __launch_bounds__(512) k_lu_shift(const double* __restrict__ H, int ldh, int n,
+__global__ void __launch_bounds__(512) k_lu_shift(const T* __restrict__ H, int ldh, int n,
                                                   const double* __restrict__ sig,
-                                                  const double* __restrict__ B, double* __restrict__ Y) {
+                                                  const T* __restrict__ B, T* __restrict__ Y) {
   extern __shared__ __align__(16) unsigned char lu_raw[];
   T* A = reinterpret_cast<T*>(lu_raw);
   const int ld = n + 2;
@@ -497,10 +499,10 @@ __global__ void __launch_bounds__(512) k_lu_shift(const double* __restrict__ H, 
   const int tid = threadIdx.x, nth = blockDim.x;
   for (int idx = tid; idx < n * (n + 1); idx += nth) {
     int i = idx / (n + 1), j = idx - i * (n + 1);
-    double v;
-    if (j < n) v = 0.5 * (H[(long long)i * ldh + j] + H[(long long)j * ldh + i]) - (i == j ? sg : 0.0);
+    T v;
+    if (j < n) v = T(0.5) * (H[(long long)i * ldh + j] + H[(long long)j * ldh + i]) - (i == j ? T(sg) : T(0));
     else v = B[(long long)r * n + i];
-    A[i * ld + j] = (T)v;
+    A[i * ld + j] = v;
   }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(512) k_lu_shift(const double* __restrict__ H, 
     for (int i = tid; i < k; i += nth) A[i * ld + n] -= A[i * ld + k] * y;
     __syncthreads();
   }
-  for (int i = tid; i < n; i += nth) Y[(long long)r * n + i] = (double)A[i * ld + n];
+  for (int i = tid; i < n; i += nth) Y[(long long)r * n + i] = A[i * ld + n];
 }
 
 void set_smem(const void* f, size_t bytes) {
@@ -593,39 +595,44 @@ void shifted_solve(const double* H, int ldh, int n, const float* lam32, const fl
   TD_LAUNCH_CHECK();
 }
 
-void lu_shift_solve(const double* H, int ldh, int n, const double* sigma, int nr, const double* B,
-                    double* Y, bool fp32, cudaStream_t s) {
+template <typename S>
+void lu_shift_solve(const S* H, int ldh, int n, const double* sigma, int nr, const S* B, S* Y,
+                    cudaStream_t s) {
   if (nr <= 0) return;
   TD_REQUIRE(n >= 1 && n <= kSmallMax, TDDFT_ERR_ARG, "lu_shift_solve: size out of range");
-  if (fp32) {
-    size_t smem = (size_t)n * (n + 2) * sizeof(float);
-    set_smem((const void*)k_lu_shift<float>, smem);
-    k_lu_shift<float><<<nr, 512, smem, s>>>(H, ldh, n, sigma, B, Y);
-  } else {
-    size_t smem = (size_t)n * (n + 2) * sizeof(double);
-    set_smem((const void*)k_lu_shift<double>, smem);
-    k_lu_shift<double><<<nr, 512, smem, s>>>(H, ldh, n, sigma, B, Y);
-  }
+  size_t smem = (size_t)n * (n + 2) * sizeof(S);
+  set_smem((const void*)k_lu_shift<S>, smem);
+  k_lu_shift<S><<<nr, 512, smem, s>>>(H, ldh, n, sigma, B, Y);
   count_launch();
   TD_LAUNCH_CHECK();
 }
+template void lu_shift_solve<float>(const float*, int, int, const double*, int, const float*, float*,
+                                    cudaStream_t);
+template void lu_shift_solve<double>(const double*, int, int, const double*, int, const double*, double*,
+                                     cudaStream_t);
 
-void cholesky(double* H, int ldh, int n, int* info, cudaStream_t s) {
+template <typename S>
+void cholesky(S* H, int ldh, int n, int* info, cudaStream_t s) {
   TD_REQUIRE(n >= 1 && n <= kSmallMax, TDDFT_ERR_ARG, "cholesky: size out of range");
-  size_t smem = (size_t)n * (n + 1) * sizeof(double);
-  set_smem((const void*)k_cholesky, smem);
-  k_cholesky<<<1, 1024, smem, s>>>(H, ldh, n, info);
+  size_t smem = (size_t)n * (n + 1) * sizeof(S);
+  set_smem((const void*)k_cholesky<S>, smem);
+  k_cholesky<S><<<1, 1024, smem, s>>>(H, ldh, n, info);
   count_launch();
   TD_LAUNCH_CHECK();
 }
+template void cholesky<float>(float*, int, int, int*, cudaStream_t);
+template void cholesky<double>(double*, int, int, int*, cudaStream_t);
 
-void trsv_rows(const double* L, int ldl, int n, double* B, int nr, int trans, cudaStream_t s) {
+template <typename S>
+void trsv_rows(const S* L, int ldl, int n, S* B, int nr, int trans, cudaStream_t s) {
   if (nr <= 0) return;
   TD_REQUIRE(n <= kSmallMax, TDDFT_ERR_ARG, "trsv: size out of range");
-  k_trsv<<<nr, 256, 0, s>>>(L, ldl, n, B, trans);
+  k_trsv<S><<<nr, 256, 0, s>>>(L, ldl, n, B, trans);
   count_launch();
   TD_LAUNCH_CHECK();
 }
+template void trsv_rows<float>(const float*, int, int, float*, int, int, cudaStream_t);
+template void trsv_rows<double>(const double*, int, int, double*, int, int, cudaStream_t);
 
 void chol_drop(const double* G, int nc, const double* norm0sq, double drop2, double* T, int* keep,
                cudaStream_t s) {

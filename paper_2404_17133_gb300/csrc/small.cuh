@@ -26,17 +26,21 @@ void shifted_solve(const double* H, int ldh, int n, const float* lam32, const fl
                    cudaStream_t s);
 
 // Y[r] = (H - sigma[r] I)^-1 B[r] for r < nr by Gaussian elimination with
-// partial pivoting, one CTA per right-hand side; compute in FP32 or FP64.
-void lu_shift_solve(const double* H, int ldh, int n, const double* sigma, int nr, const double* B,
-                    double* Y, bool fp32, cudaStream_t s);
+// partial pivoting, one CTA per right-hand side; storage and compute type S
+// (float or double).
+template <typename S>
+void lu_shift_solve(const S* H, int ldh, int n, const double* sigma, int nr, const S* B, S* Y,
+                    cudaStream_t s);
 
-// In-place FP64 Cholesky H = L L^T (lower, zeroed above the diagonal).
+// In-place Cholesky H = L L^T (lower, zeroed above the diagonal), type S.
 // info[0] = 0 on success, j+1 when pivot j is not positive / not finite.
-void cholesky(double* H, int ldh, int n, int* info, cudaStream_t s);
+template <typename S>
+void cholesky(S* H, int ldh, int n, int* info, cudaStream_t s);
 
 // Triangular solves with the lower factor L (n x n, ldl) for nr right-hand
 // sides stored as rows of B (in place): trans = 0: L x = b; 1: L^T x = b.
-void trsv_rows(const double* L, int ldl, int n, double* B, int nr, int trans, cudaStream_t s);
+template <typename S>
+void trsv_rows(const S* L, int ldl, int n, S* B, int nr, int trans, cudaStream_t s);
 
 // Orthonormalisation helper for a block of candidate rows (Gram matrix
 // G = C C^T given): pivot-dropping Cholesky G = R^T R over the candidates in

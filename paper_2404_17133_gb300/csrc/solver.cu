@@ -25,6 +25,7 @@
 #include <numeric>
 
 #include "ctx.cuh"
+#include "skinny.cuh"
 #include "small.cuh"
 #include "vecops.cuh"
 
@@ -131,56 +132,36 @@ using PairPre = PairPreT<double>;
 // Subspace helpers.  Vectors are FP64 (outer Davidson, PLAIN) or FP32 (MIXED
 // inner solves); every small matrix is FP64.
 
-// G[i][j] = A[i] . B[j]  (rows of length ov), G row stride ldg
-template <typename T>
-void gram(const T* A, int ka, const T* B, int kb, int ov, double* G, int ldg, cudaStream_t s) {
-  GemmDesc g;
-  g.acc64 = sizeof(T) == 8;
-  g.M = ka; g.N = kb; g.K = ov;
-  g.A = A; g.ta = dt_of<T>(); g.sam = ov; g.sak = 1;
-  g.B = B; g.tb = dt_of<T>(); g.sbk = 1; g.sbn = ov;
-  g.C = G; g.tc = DType::F64; g.scm = ldg; g.scn = 1;
-  gemm_splitk(g, auto_splits(ka, kb, ov), s);
+// G[i][j] = A[i] . B[j]  (rows of length ov), G (type S) row stride ldg; accumulated
+// in the vectors' precision
+template <typename T, typename S>
+void gram(const T* A, int ka, const T* B, int kb, int ov, S* G, int ldg, cudaStream_t s) {
+  sk_gram<T>(A, ov, ka, B, ov, kb, ov, G, dt_of<S>(), ldg, 1.0, 0.0, s);
 }
 
 // a[r][col0 + j] = V[r] . Wn[j]  for r < N, j < k
 template <typename T>
-void proj_cols(const T* V, int N, const T* Wn, int k, int ov, double* a, int ld, int col0, cudaStream_t s) {
-  gram<T>(V, N, Wn, k, ov, a + col0, ld, s);
+void proj_cols(const T* V, int N, const T* Wn, int k, int ov, T* a, int ld, int col0, cudaStream_t s) {
+  gram<T, T>(V, N, Wn, k, ov, a + col0, ld, s);
 }
 
-// FP64 small matrix as the A operand of a GEMM over T vectors
-template <typename T>
-const void* as_operand(const double* m, size_t n, DevBuf& tmp, cudaStream_t s) {
-  if (sizeof(T) == 8) return m;
-  tmp = DevBuf(n * 4, s);
-  convert(m, DType::F64, tmp.p, DType::F32, (long long)n, s);
-  return tmp.p;
-}
-
-// out[j] = alpha * sum_r coef[j][r] V[r] + beta * out[j]   (coef compact [k][N], FP64)
-template <typename T>
-void combo(const double* coef, int k, int N, const T* V, int ov, T* out, double alpha, double beta,
+// out[j] = alpha * sum_r coef[j][r] V[r] + beta * out[j]   (coef compact [k][N], type S)
+template <typename T, typename S>
+void combo(const S* coef, int k, int N, const T* V, int ov, T* out, double alpha, double beta,
            cudaStream_t s) {
-  DevBuf tmp;
-  GemmDesc g;
-  g.acc64 = sizeof(T) == 8;
-  g.M = k; g.N = ov; g.K = N;
-  g.A = as_operand<T>(coef, (size_t)k * N, tmp, s); g.ta = dt_of<T>(); g.sam = N; g.sak = 1;
-  g.B = V; g.tb = dt_of<T>(); g.sbk = ov; g.sbn = 1;
-  g.C = out; g.tc = dt_of<T>(); g.scm = ov; g.scn = 1;
-  g.alpha = alpha; g.beta = beta;
-  gemm(g, s);
+  sk_combo<T>(coef, dt_of<S>(), N, 1, k, N, V, ov, ov, out, ov, alpha, beta, s);
 }
 
-// small dense product C = A * B with general strides (FP64)
-void small_mm(int M, int N, int K, const double* A, long long sam, long long sak, const double* B,
-              long long sbk, long long sbn, double* C, long long scm, cudaStream_t s) {
+// small dense product C = A * B with general strides (type S)
+template <typename S>
+void small_mm(int M, int N, int K, const S* A, long long sam, long long sak, const S* B,
+              long long sbk, long long sbn, S* C, long long scm, cudaStream_t s) {
   GemmDesc g;
+  g.acc64 = sizeof(S) == 8;
   g.M = M; g.N = N; g.K = K;
-  g.A = A; g.sam = sam; g.sak = sak;
-  g.B = B; g.sbk = sbk; g.sbn = sbn;
-  g.C = C; g.scm = scm; g.scn = 1;
+  g.A = A; g.ta = dt_of<S>(); g.sam = sam; g.sak = sak;
+  g.B = B; g.tb = dt_of<S>(); g.sbk = sbk; g.sbn = sbn;
+  g.C = C; g.tc = dt_of<S>(); g.scm = scm; g.scn = 1;
   gemm(g, s);
 }
 
@@ -200,22 +181,14 @@ int orth_append(T* V, int N, T* cand, int nc, int ov, cudaStream_t s) {
   T* oth = tmp.as<T>();
   for (int pass = 0; pass < 2; ++pass) {
     if (N > 0) {
-      gram<T>(V, N, cur, nc, ov, coef.as<double>(), nc, s);       // coef[r][j] = V[r].cur[j]
-      DevBuf ct;
-      GemmDesc g;                                                   // cur[j] -= sum_r coef[r][j] V[r]
-      g.acc64 = sizeof(T) == 8;
-      g.M = nc; g.N = ov; g.K = N;
-      g.A = as_operand<T>(coef.as<double>(), (size_t)N * nc, ct, s); g.ta = dt_of<T>();
-      g.sam = 1; g.sak = nc;
-      g.B = V; g.tb = dt_of<T>(); g.sbk = ov; g.sbn = 1;
-      g.C = cur; g.tc = dt_of<T>(); g.scm = ov; g.scn = 1;
-      g.alpha = -1.0; g.beta = 1.0;
-      gemm(g, s);
+      gram<T, double>(V, N, cur, nc, ov, coef.as<double>(), nc, s);   // coef[r][j] = V[r].cur[j]
+      // cur[j] -= sum_r coef[r][j] V[r]
+      sk_combo<T>(coef.p, DType::F64, 1, nc, nc, N, V, ov, ov, cur, ov, -1.0, 1.0, s);
     }
-    gram<T>(cur, nc, cur, nc, ov, G.as<double>(), nc, s);
+    gram<T, double>(cur, nc, cur, nc, ov, G.as<double>(), nc, s);
     chol_drop(G.as<double>(), nc, pass == 0 ? n0.as<double>() : ones.as<double>(), kDrop2,
               Tm.as<double>(), keep.as<int>(), s);
-    combo<T>(Tm.as<double>(), nc, nc, cur, ov, oth, 1.0, 0.0, s);
+    combo<T, double>(Tm.as<double>(), nc, nc, cur, ov, oth, 1.0, 0.0, s);
     std::swap(cur, oth);
   }
   std::vector<int> kh = d2h(keep.as<int>(), nc, s);
@@ -303,8 +276,8 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
                   x.as<double>(), scr.as<double>(), rounds, s);
     ph_small.stop();
     ScopedPhase ph_vec(PH_VEC, s);
-    combo<double>(x.as<double>(), kk, N, Vp, ov, X.as<double>(), 1.0, 0.0, s);            // Eq. 3
-    combo<double>(x.as<double>(), kk, N, Wp, ov, AX.as<double>(), 1.0, 0.0, s);
+    combo<double, double>(x.as<double>(), kk, N, Vp, ov, X.as<double>(), 1.0, 0.0, s);    // Eq. 3
+    combo<double, double>(x.as<double>(), kk, N, Wp, ov, AX.as<double>(), 1.0, 0.0, s);
     resid_tda(X.as<double>(), AX.as<double>(), lam.as<double>(), kk, ov, R.as<double>(), s);  // Eq. residual
     row_sumsq(R.as<double>(), ov, kk, ov, rn.as<double>(), s);
     om = d2h(lam.as<double>(), kk, s);
@@ -357,7 +330,9 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
 
 // ---------------------------------------------------------------------------
 // Paired subspace algebra shared by the Casida eigenproblem and the paired
-// linear systems: a+ = V^T P, a- = V^T M, a- = L L^T, H = L^T a+ L.
+// linear systems: a+ = V^T P, a- = V^T M, a- = L L^T, H = L^T a+ L.  The small
+// matrices have the vectors' type T: FP64 in the outer solves, FP32 in the
+// MIXED inner solves (which stop at a relative residual of about 1e-2).
 
 template <typename T>
 struct PairedSpace {
@@ -370,11 +345,11 @@ struct PairedSpace {
     V = DevBuf((size_t)cap * ov * sizeof(T), s);
     P = DevBuf((size_t)cap * ov * sizeof(T), s);
     M = DevBuf((size_t)cap * ov * sizeof(T), s);
-    ap = DevBuf((size_t)cap * cap * 8, s);
-    am = DevBuf((size_t)cap * cap * 8, s);
-    L = DevBuf((size_t)cap * cap * 8, s);
-    tmp = DevBuf((size_t)cap * cap * 8, s);
-    H = DevBuf((size_t)cap * cap * 8, s);
+    ap = DevBuf((size_t)cap * cap * sizeof(T), s);
+    am = DevBuf((size_t)cap * cap * sizeof(T), s);
+    L = DevBuf((size_t)cap * cap * sizeof(T), s);
+    tmp = DevBuf((size_t)cap * cap * sizeof(T), s);
+    H = DevBuf((size_t)cap * cap * sizeof(T), s);
     lam32 = DevBuf(cap * 4, s);
     vec32 = DevBuf((size_t)cap * cap * 4, s);
     info = DevBuf(4, s);
@@ -386,24 +361,28 @@ struct PairedSpace {
   // eigenproblem, its FP32 decomposition)
   void update(bool eig) {
     ScopedPhase ph(PH_PROJ, s);
-    proj_cols<T>(v(), N, p() + (size_t)n_old * ov, n_new, ov, ap.as<double>(), cap, n_old, s);
-    proj_cols<T>(v(), N, m() + (size_t)n_old * ov, n_new, ov, am.as<double>(), cap, n_old, s);
-    sym_fill(ap.as<double>(), cap, n_old, n_new, s);
-    sym_fill(am.as<double>(), cap, n_old, n_new, s);
-    TD_CUDA(cudaMemcpyAsync(L.p, am.p, (size_t)cap * cap * 8, cudaMemcpyDeviceToDevice, s));
+    proj_cols<T>(v(), N, p() + (size_t)n_old * ov, n_new, ov, ap.as<T>(), cap, n_old, s);
+    proj_cols<T>(v(), N, m() + (size_t)n_old * ov, n_new, ov, am.as<T>(), cap, n_old, s);
+    sym_fill<T>(ap.as<T>(), cap, n_old, n_new, s);
+    sym_fill<T>(am.as<T>(), cap, n_old, n_new, s);
+    TD_CUDA(cudaMemcpyAsync(L.p, am.p, (size_t)cap * cap * sizeof(T), cudaMemcpyDeviceToDevice, s));
     {
       ScopedPhase f(trace_level() >= 3 ? PH_CHOL : PH_N - 1, s);
-      cholesky(L.as<double>(), cap, N, info.as<int>(), s);
+      cholesky<T>(L.as<T>(), cap, N, info.as<int>(), s);
     }
     {
       ScopedPhase f(trace_level() >= 3 ? PH_SMM : PH_N - 1, s);
       // tmp = a+ L ; H = L^T tmp
-      small_mm(N, N, N, ap.as<double>(), cap, 1, L.as<double>(), cap, 1, tmp.as<double>(), cap, s);
-      small_mm(N, N, N, L.as<double>(), 1, cap, tmp.as<double>(), cap, 1, H.as<double>(), cap, s);
+      small_mm<T>(N, N, N, ap.as<T>(), cap, 1, L.as<T>(), cap, 1, tmp.as<T>(), cap, s);
+      small_mm<T>(N, N, N, L.as<T>(), 1, cap, tmp.as<T>(), cap, 1, H.as<T>(), cap, s);
     }
-    if (eig) {
-      ScopedPhase f(trace_level() >= 3 ? PH_EIG : PH_N - 1, s);
-      eig32(H.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);
+    if constexpr (sizeof(T) == 8) {
+      if (eig) {
+        ScopedPhase f(trace_level() >= 3 ? PH_EIG : PH_N - 1, s);
+        eig32(H.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);
+      }
+    } else {
+      TD_REQUIRE(!eig, TDDFT_ERR_ARG, "FP32 paired space: no eigensolver");
     }
     n_old = N;
     n_new = 0;
@@ -427,12 +406,13 @@ struct PairedLinOut {
   std::vector<double> resid;
 };
 
-// The small shifted systems are solved by LU per shift: FP64 for the outer
-// polarizability and PLAIN solves, FP32 (lu_fp32) for the MIXED inner solves.
+// The small shifted systems are solved by LU per shift in the vectors' type:
+// FP64 for the outer polarizability and PLAIN solves, FP32 for the MIXED inner
+// solves.
 template <typename T>
 PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre, const T* gp,
                            const T* gm, const std::vector<double>& shifts, int nr, T* init, int ni,
-                           double tol, int max_iter, int cap, bool lu_fp32, bool exact_op,
+                           double tol, int max_iter, int cap, bool exact_op,
                            Counters& cnt, T* Uout, T* Wout, cudaStream_t s) {
   PairedLinOut o;
   if (!exact_op) ++g_inner;
@@ -445,8 +425,8 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
   for (int r = 0; r < nr; ++r) s2[r] = shifts[r] * shifts[r];
   h2d(sh.as<double>(), shifts, s);
   h2d(sig2.as<double>(), s2, s);
-  DevBuf hp((size_t)nr * cap * 8, s), hm((size_t)nr * cap * 8, s), rhs((size_t)nr * cap * 8, s);
-  DevBuf ut((size_t)nr * cap * 8, s), uc((size_t)nr * cap * 8, s), wc((size_t)nr * cap * 8, s);
+  DevBuf hp((size_t)nr * cap * es, s), hm((size_t)nr * cap * es, s), rhs((size_t)nr * cap * es, s);
+  DevBuf ut((size_t)nr * cap * es, s), uc((size_t)nr * cap * es, s), wc((size_t)nr * cap * es, s);
   DevBuf Rp((size_t)nr * ov * es, s), Rm((size_t)nr * ov * es, s), PU((size_t)nr * ov * es, s),
       MW((size_t)nr * ov * es, s);
   DevBuf gn(nr * 8, s), gn2(nr * 8, s), rn1(nr * 8, s), rn2(nr * 8, s);
@@ -485,39 +465,38 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
     sp.update(false);
     sp.check_definite();
     const int N = sp.N;
-    double* Lp = sp.L.template as<double>();
+    T* Lp = sp.L.template as<T>();
     ScopedPhase ph_small(PH_SMALL, s);
     // h+ = V g+ , h- = V g-   ([nr][N])
-    gram<T>(gp, nr, sp.v(), N, ov, hp.as<double>(), N, s);
+    gram<T, T>(gp, nr, sp.v(), N, ov, hp.as<T>(), N, s);
     // rhs = L^T h+  (rows): rhs[r][i] = sum_q h+[r][q] L[q][i]
-    small_mm(nr, N, N, hp.as<double>(), N, 1, Lp, cap, 1, rhs.as<double>(), N, s);
+    small_mm<T>(nr, N, N, hp.as<T>(), N, 1, Lp, cap, 1, rhs.as<T>(), N, s);
     if (gm) {
-      gram<T>(gm, nr, sp.v(), N, ov, hm.as<double>(), N, s);
-      trsv_rows(Lp, cap, N, hm.as<double>(), nr, 0, s);                 // z- = L^-1 h-
-      axpy_rows<double>(rhs.as<double>(), hm.as<double>(), sh.as<double>(), nr, N, s);
+      gram<T, T>(gm, nr, sp.v(), N, ov, hm.as<T>(), N, s);
+      trsv_rows<T>(Lp, cap, N, hm.as<T>(), nr, 0, s);                   // z- = L^-1 h-
+      axpy_rows<T>(rhs.as<T>(), hm.as<T>(), sh.as<double>(), nr, N, s);
     }
     // (H - s^2) u~ = rhs for every shift
     {
       ScopedPhase f(trace_level() >= 3 ? PH_LU : PH_N - 1, s);
-      lu_shift_solve(sp.H.template as<double>(), cap, N, sig2.as<double>(), nr, rhs.as<double>(),
-                     ut.as<double>(), lu_fp32, s);
+      lu_shift_solve<T>(sp.H.template as<T>(), cap, N, sig2.as<double>(), nr, rhs.as<T>(), ut.as<T>(), s);
     }
     // u = L u~ : u[r][i] = sum_q L[i][q] u~[r][q]
-    small_mm(nr, N, N, ut.as<double>(), N, 1, Lp, 1, cap, uc.as<double>(), N, s);
+    small_mm<T>(nr, N, N, ut.as<T>(), N, 1, Lp, 1, cap, uc.as<T>(), N, s);
     // w = L^-T (z- + s u~)
-    if (gm) TD_CUDA(cudaMemcpyAsync(wc.p, hm.p, (size_t)nr * N * 8, cudaMemcpyDeviceToDevice, s));
-    else TD_CUDA(cudaMemsetAsync(wc.p, 0, (size_t)nr * N * 8, s));
-    axpy_rows<double>(wc.as<double>(), ut.as<double>(), sh.as<double>(), nr, N, s);
+    if (gm) TD_CUDA(cudaMemcpyAsync(wc.p, hm.p, (size_t)nr * N * es, cudaMemcpyDeviceToDevice, s));
+    else TD_CUDA(cudaMemsetAsync(wc.p, 0, (size_t)nr * N * es, s));
+    axpy_rows<T>(wc.as<T>(), ut.as<T>(), sh.as<double>(), nr, N, s);
     {
       ScopedPhase f(trace_level() >= 3 ? PH_TRSV : PH_N - 1, s);
-      trsv_rows(Lp, cap, N, wc.as<double>(), nr, 1, s);
+      trsv_rows<T>(Lp, cap, N, wc.as<T>(), nr, 1, s);
     }
     ph_small.stop();
     ScopedPhase ph_vec(PH_VEC, s);
-    combo<T>(uc.as<double>(), nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
-    combo<T>(wc.as<double>(), nr, N, sp.v(), ov, Wout, 1.0, 0.0, s);
-    combo<T>(uc.as<double>(), nr, N, sp.p(), ov, PU.as<T>(), 1.0, 0.0, s);
-    combo<T>(wc.as<double>(), nr, N, sp.m(), ov, MW.as<T>(), 1.0, 0.0, s);
+    combo<T, T>(uc.as<T>(), nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
+    combo<T, T>(wc.as<T>(), nr, N, sp.v(), ov, Wout, 1.0, 0.0, s);
+    combo<T, T>(uc.as<T>(), nr, N, sp.p(), ov, PU.as<T>(), 1.0, 0.0, s);
+    combo<T, T>(wc.as<T>(), nr, N, sp.m(), ov, MW.as<T>(), 1.0, 0.0, s);
     resid_paired<T>(Uout, Wout, PU.as<T>(), MW.as<T>(), sh.as<double>(), gp, gm, nr, ov,
                     Rp.as<T>(), Rm.as<T>(), s);
     row_sumsq<T>(Rp.as<T>(), ov, nr, ov, rn1.as<double>(), s);
@@ -649,14 +628,14 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
     h2d(iom.as<double>(), iomh, s);
     h2d(omd.as<double>(), std::vector<double>(om.begin(), om.begin() + kk), s);
     // u = L y / sqrt(Omega) ; w = a+ u / Omega
-    small_mm(kk, N, N, y.as<double>(), N, 1, Lp, 1, cap, uc.as<double>(), N, s);
+    small_mm<double>(kk, N, N, y.as<double>(), N, 1, Lp, 1, cap, uc.as<double>(), N, s);
     scale_rows(uc.as<double>(), isq.as<double>(), kk, N, s);
-    small_mm(kk, N, N, uc.as<double>(), N, 1, sp.ap.template as<double>(), cap, 1, wc.as<double>(), N, s);
+    small_mm<double>(kk, N, N, uc.as<double>(), N, 1, sp.ap.template as<double>(), cap, 1, wc.as<double>(), N, s);
     scale_rows(wc.as<double>(), iom.as<double>(), kk, N, s);
-    combo<double>(uc.as<double>(), kk, N, sp.v(), ov, U.as<double>(), 1.0, 0.0, s);
-    combo<double>(wc.as<double>(), kk, N, sp.v(), ov, W.as<double>(), 1.0, 0.0, s);
-    combo<double>(uc.as<double>(), kk, N, sp.p(), ov, PU.as<double>(), 1.0, 0.0, s);
-    combo<double>(wc.as<double>(), kk, N, sp.m(), ov, MW.as<double>(), 1.0, 0.0, s);
+    combo<double, double>(uc.as<double>(), kk, N, sp.v(), ov, U.as<double>(), 1.0, 0.0, s);
+    combo<double, double>(wc.as<double>(), kk, N, sp.v(), ov, W.as<double>(), 1.0, 0.0, s);
+    combo<double, double>(uc.as<double>(), kk, N, sp.p(), ov, PU.as<double>(), 1.0, 0.0, s);
+    combo<double, double>(wc.as<double>(), kk, N, sp.m(), ov, MW.as<double>(), 1.0, 0.0, s);
     resid_paired<double>(U.as<double>(), W.as<double>(), PU.as<double>(), MW.as<double>(), omd.as<double>(),
                  nullptr, nullptr, kk, ov, Rp.as<double>(), Rm.as<double>(), s);
     row_sumsq(Rp.as<double>(), ov, kk, ov, rn1.as<double>(), s);
@@ -724,13 +703,13 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
 // expansion, stopped at |res_n| <= tol |R_n| or max_iter iterations.
 template <typename T>
 void inner_tda(int ov, const TdaOpT<T>& Top, const double* delta, const T* R, const double* sh,
-               const std::vector<double>& shh, int nu, double tol, int max_iter, bool lu_fp32,
+               const std::vector<double>& shh, int nu, double tol, int max_iter,
                Counters& cnt, T* out, cudaStream_t s) {
   InnerScope inner_scope;
   const int cap = kSmallMax;
   constexpr size_t es = sizeof(T);
-  DevBuf S((size_t)cap * ov * es, s), TS((size_t)cap * ov * es, s), t((size_t)cap * cap * 8, s);
-  DevBuf h((size_t)nu * cap * 8, s), y((size_t)nu * cap * 8, s);
+  DevBuf S((size_t)cap * ov * es, s), TS((size_t)cap * ov * es, s), t((size_t)cap * cap * es, s);
+  DevBuf h((size_t)nu * cap * es, s), y((size_t)nu * cap * es, s);
   DevBuf Tv((size_t)nu * ov * es, s), res((size_t)nu * ov * es, s), rn(nu * 8, s), r0(nu * 8, s);
   DevBuf cand((size_t)nu * ov * es, s), iu(nu * 4, s), shu(nu * 8, s), resu((size_t)nu * ov * es, s);
   row_sumsq<T>(R, ov, nu, ov, r0.as<double>(), s);
@@ -745,15 +724,15 @@ void inner_tda(int ov, const TdaOpT<T>& Top, const double* delta, const T* R, co
   cnt.ris_mv += N;
   int n_old = 0, n_new = N;
   for (int it = 0; it < max_iter; ++it) {
-    proj_cols<T>(S.as<T>(), N, TS.as<T>() + (size_t)n_old * ov, n_new, ov, t.as<double>(), cap, n_old, s);
-    sym_fill(t.as<double>(), cap, n_old, n_new, s);
-    gram<T>(R, nu, S.as<T>(), N, ov, h.as<double>(), N, s);           // h[n][r] = R_n . S_r
+    proj_cols<T>(S.as<T>(), N, TS.as<T>() + (size_t)n_old * ov, n_new, ov, t.as<T>(), cap, n_old, s);
+    sym_fill<T>(t.as<T>(), cap, n_old, n_new, s);
+    gram<T, T>(R, nu, S.as<T>(), N, ov, h.as<T>(), N, s);             // h[n][r] = R_n . S_r
     {
       ScopedPhase ph(PH_SMALL, s);
-      lu_shift_solve(t.as<double>(), cap, N, sh, nu, h.as<double>(), y.as<double>(), lu_fp32, s);
+      lu_shift_solve<T>(t.as<T>(), cap, N, sh, nu, h.as<T>(), y.as<T>(), s);
     }
-    combo<T>(y.as<double>(), nu, N, S.as<T>(), ov, out, 1.0, 0.0, s);
-    combo<T>(y.as<double>(), nu, N, TS.as<T>(), ov, Tv.as<T>(), 1.0, 0.0, s);
+    combo<T, T>(y.as<T>(), nu, N, S.as<T>(), ov, out, 1.0, 0.0, s);
+    combo<T, T>(y.as<T>(), nu, N, TS.as<T>(), ov, Tv.as<T>(), 1.0, 0.0, s);
     resid_shift<T>(Tv.as<T>(), out, sh, R, nu, ov, res.as<T>(), s);
     row_sumsq<T>(res.as<T>(), ov, nu, ov, rn.as<double>(), s);
     std::vector<double> rh = sqrt_all(d2h(rn.as<double>(), nu, s));
@@ -878,11 +857,11 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
       DevBuf R32(n * 4, s), o32(n * 4, s);
       convert(R, DType::F64, R32.p, DType::F32, n, s);
       inner_tda<float>(ov, T32, c.delta.as<double>(), R32.as<float>(), sh, shh, nu, p.inner_tol,
-                       p.inner_max_iter, true, cnt, o32.as<float>(), s);
+                       p.inner_max_iter, cnt, o32.as<float>(), s);
       convert(o32.p, DType::F32, out, DType::F64, n, s);
     } else {
       inner_tda<double>(ov, T, c.delta.as<double>(), R, sh, shh, nu, p.inner_tol, p.inner_max_iter,
-                        false, cnt, out, s);
+                        cnt, out, s);
     }
   };
   // initial guess (Sec. 2.1: low-lying eigenvectors of T)
@@ -958,7 +937,7 @@ void rid_paired(int ov, const Plan& p, const PairOp& T, const PairPre& diag, con
     precond_paired<float>(g32.as<float>(), g32.as<float>() + n, sh, dl, nu, ov, init.as<float>(),
                           init.as<float>() + n, s);
     paired_linear<float>(ov, T32, diag32, g32.as<float>(), g32.as<float>() + n, shh, nu, init.as<float>(),
-                         2 * nu, p.inner_tol, p.inner_max_iter, kSmallMax, true, false, cnt,
+                         2 * nu, p.inner_tol, p.inner_max_iter, kSmallMax, false, cnt,
                          uw.as<float>(), uw.as<float>() + n, s);
     convert(uw.p, DType::F32, u, DType::F64, n, s);
     convert(uw.as<float>() + n, DType::F32, w, DType::F64, n, s);
@@ -966,7 +945,7 @@ void rid_paired(int ov, const Plan& p, const PairOp& T, const PairPre& diag, con
     DevBuf init((size_t)2 * n * 8, s);
     precond_paired<double>(gp, gm, sh, dl, nu, ov, init.as<double>(), init.as<double>() + n, s);
     paired_linear<double>(ov, T, diag, gp, gm, shh, nu, init.as<double>(), 2 * nu, p.inner_tol,
-                          p.inner_max_iter, kSmallMax, false, false, cnt, u, w, s);
+                          p.inner_max_iter, kSmallMax, false, cnt, u, w, s);
   }
 }
 }  // namespace
@@ -1112,7 +1091,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
       precond_paired<float>(b32.as<float>(), nullptr, shd.as<double>(), dl, nr, ov, d0.as<float>(),
                             d0.as<float>() + n, s);
       paired_linear<float>(ov, T32, diag32, b32.as<float>(), nullptr, sh, nr, d0.as<float>(), 2 * nr,
-                           p.guess_tol, p.max_iter, kSmallMax, true, false, cnt, uw.as<float>(),
+                           p.guess_tol, p.max_iter, kSmallMax, false, cnt, uw.as<float>(),
                            uw.as<float>() + n, s);
       convert(uw.p, DType::F32, iu, DType::F64, 2 * n, s);
     } else {
@@ -1120,7 +1099,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
       precond_paired<double>(b.as<double>(), nullptr, shd.as<double>(), dl, nr, ov, d0.as<double>(),
                              d0.as<double>() + (size_t)nr * ov, s);
       paired_linear<double>(ov, T, diag, b.as<double>(), nullptr, sh, nr, d0.as<double>(), 2 * nr,
-                            p.guess_tol, p.max_iter, kSmallMax, false, false, cnt, iu, iw, s);
+                            p.guess_tol, p.max_iter, kSmallMax, false, cnt, iu, iw, s);
     }
   } else {
     precond_paired<double>(b.as<double>(), nullptr, shd.as<double>(), dl, nr, ov, iu, iw, s);
@@ -1128,7 +1107,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
   DevBuf U((size_t)nr * ov * 8, s), W((size_t)nr * ov * 8, s);
   PairedLinOut r = paired_linear<double>(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag,
                                          b.as<double>(), nullptr, sh, nr, iu, 2 * nr, p.tol, p.max_iter,
-                                         p.cap, false, true, cnt, U.as<double>(), W.as<double>(), s);
+                                         p.cap, true, cnt, U.as<double>(), W.as<double>(), s);
   // alpha[f][v][u] = mu_v . U[f*n_dip + u]
   DevBuf G((size_t)n_dip * nr * 8, s);
   gram(mud.as<double>(), n_dip, U.as<double>(), nr, ov, G.as<double>(), nr, s);

@@ -115,7 +115,8 @@ __global__ void k_gather_rows(const T* src, const int* idx, int k, int n, T* dst
   }
 }
 
-__global__ void k_sym_fill(double* a, int ld, int n_old, int n_new) {
+template <typename S>
+__global__ void k_sym_fill(S* a, int ld, int n_old, int n_new) {
   int N = n_old + n_new;
   long long tot = (long long)N * n_new;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
@@ -124,7 +125,7 @@ __global__ void k_sym_fill(double* a, int ld, int n_old, int n_new) {
     if (r < n_old) {
       a[(long long)c * ld + r] = a[(long long)r * ld + c];
     } else if (r < c) {
-      double v = 0.5 * (a[(long long)r * ld + c] + a[(long long)c * ld + r]);
+      S v = S(0.5) * (a[(long long)r * ld + c] + a[(long long)c * ld + r]);
       a[(long long)r * ld + c] = v;
       a[(long long)c * ld + r] = v;
     }
@@ -261,11 +262,14 @@ void gather_rows(const T* src, const int* idx, int k, int n, T* dst, cudaStream_
 }
 template void gather_rows<double>(const double*, const int*, int, int, double*, cudaStream_t);
 template void gather_rows<float>(const float*, const int*, int, int, float*, cudaStream_t);
-void sym_fill(double* a, int ld, int n_old, int n_new, cudaStream_t s) {
+template <typename S>
+void sym_fill(S* a, int ld, int n_old, int n_new, cudaStream_t s) {
   if (n_new <= 0) return;
-  k_sym_fill<<<TD_GRID((long long)(n_old + n_new) * n_new)>>>(a, ld, n_old, n_new);
+  k_sym_fill<S><<<TD_GRID((long long)(n_old + n_new) * n_new)>>>(a, ld, n_old, n_new);
   count_launch(); TD_LAUNCH_CHECK();
 }
+template void sym_fill<double>(double*, int, int, int, cudaStream_t);
+template void sym_fill<float>(float*, int, int, int, cudaStream_t);
 template <typename T>
 void scale_rows(T* X, const double* sc, int k, int n, cudaStream_t s) {
   k_scale_rows<T><<<TD_GRID((long long)k * n)>>>(X, sc, k, n);

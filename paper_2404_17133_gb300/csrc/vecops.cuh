@@ -33,7 +33,8 @@ template <typename T>
 void gather_rows(const T* src, const int* idx, int k, int n, T* dst, cudaStream_t s);
 // Projected matrix a (ld) after its new columns [n_old, n_old+n_new) were written
 // for all rows < n_old+n_new: mirror into the new rows and symmetrise the new block.
-void sym_fill(double* a, int ld, int n_old, int n_new, cudaStream_t s);
+template <typename S>
+void sym_fill(S* a, int ld, int n_old, int n_new, cudaStream_t s);
 // X[r] *= scale[r].
 template <typename T>
 void scale_rows(T* X, const double* scale, int k, int n, cudaStream_t s);
