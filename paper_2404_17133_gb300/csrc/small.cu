@@ -49,7 +49,10 @@ template <> __device__ __forceinline__ double big_theta<double>() { return 1e150
 
 // Parallel cyclic Jacobi on the symmetric matrix A (n x n, shared memory,
 // leading dimension ld) accumulating Q <- Q G.  Each round applies n/2
-// disjoint rotations (circle-method pairing); a sweep is n-1 rounds.
+// disjoint rotations (circle-method pairing); a sweep is n-1 rounds.  The
+// two-sided update of a round is done block by block: the 2x2 block of rows
+// (p_i, q_i) and columns (p_j, q_j) becomes R_i X R_j^T, so a round needs one
+// pass over A (and Q) and two barriers.
 template <typename T>
 __device__ void jacobi_cta(T* A, T* Q, int n, int ld, double frob, int max_sweeps, double stop_rel,
                            int* pp, int* qq, T* cc, T* ss, unsigned* smax) {
@@ -83,33 +86,36 @@ __device__ void jacobi_cta(T* A, T* Q, int n, int ld, double frob, int max_sweep
         pp[i] = p; qq[i] = q; cc[i] = c; ss[i] = s;
       }
       __syncthreads();
-      for (int idx = tid; idx < half * NP; idx += nth) {
-        int i = idx / NP, j = idx - i * NP;
-        T s = ss[i];
-        if (s == T(0)) continue;
-        T c = cc[i];
-        int p = pp[i], q = qq[i];
-        T ap = A[p * ld + j], aq = A[q * ld + j];
-        A[p * ld + j] = c * ap - s * aq;
-        A[q * ld + j] = s * ap + c * aq;
+      // A <- G^T A G, block by block
+      for (int idx = tid; idx < half * half; idx += nth) {
+        const int bi = idx / half, bj = idx - bi * half;
+        const T si = ss[bi], sj = ss[bj];
+        if (si == T(0) && sj == T(0)) continue;
+        const T ci = cc[bi], cj = cc[bj];
+        const int pi = pp[bi], qi = qq[bi], pj = pp[bj], qj = qq[bj];
+        const T x00 = A[pi * ld + pj], x01 = A[pi * ld + qj];
+        const T x10 = A[qi * ld + pj], x11 = A[qi * ld + qj];
+        // rows: R_i = [[c, -s], [s, c]]
+        const T y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
+        const T y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
+        // columns: times [[c, s], [-s, c]]
+        T z00 = cj * y00 - sj * y01, z01 = sj * y00 + cj * y01;
+        T z10 = cj * y10 - sj * y11, z11 = sj * y10 + cj * y11;
+        if (bi == bj) { z01 = T(0); z10 = T(0); }   // the rotation annihilates a_pq
+        A[pi * ld + pj] = z00; A[pi * ld + qj] = z01;
+        A[qi * ld + pj] = z10; A[qi * ld + qj] = z11;
       }
-      __syncthreads();
+      // Q <- Q G (columns p_j, q_j of every row)
       for (int idx = tid; idx < half * NP; idx += nth) {
-        int i = idx / NP, j = idx - i * NP;
-        T s = ss[i];
-        if (s == T(0)) continue;
-        T c = cc[i];
-        int p = pp[i], q = qq[i];
-        T ap = A[j * ld + p], aq = A[j * ld + q];
-        A[j * ld + p] = c * ap - s * aq;
-        A[j * ld + q] = s * ap + c * aq;
-        T qp = Q[j * ld + p], qv = Q[j * ld + q];
-        Q[j * ld + p] = c * qp - s * qv;
-        Q[j * ld + q] = s * qp + c * qv;
+        const int bj = idx / NP, row = idx - bj * NP;
+        const T sj = ss[bj];
+        if (sj == T(0)) continue;
+        const T cj = cc[bj];
+        const int pj = pp[bj], qj = qq[bj];
+        const T qp = Q[row * ld + pj], qv = Q[row * ld + qj];
+        Q[row * ld + pj] = cj * qp - sj * qv;
+        Q[row * ld + qj] = sj * qp + cj * qv;
       }
-      __syncthreads();
-      for (int i = tid; i < half; i += nth)
-        if (ss[i] != T(0)) { A[pp[i] * ld + qq[i]] = T(0); A[qq[i] * ld + pp[i]] = T(0); }
       __syncthreads();
     }
     float m = __uint_as_float(*smax);
@@ -447,7 +453,8 @@ __global__ void __launch_bounds__(1024) k_chol_drop(const double* __restrict__ G
   for (int j = 0; j < nc; ++j) {
     if (tid == 0) {
       double d = R[j * ld + j];
-      kj = (isfinite(d) && d > drop2 * norm0sq[j] && d > 0.0) ? 1 : 0;
+      const double n0 = norm0sq ? norm0sq[j] : 1.0;
+      kj = (isfinite(d) && d > drop2 * n0 && d > 0.0) ? 1 : 0;
       dj = kj ? sqrt(d) : 0.0;
       keep[j] = kj;
     }
@@ -483,6 +490,61 @@ __global__ void __launch_bounds__(1024) k_chol_drop(const double* __restrict__ G
   }
 }
 
+// Gaussian elimination with partial pivoting on the augmented matrix [M | b]
+// held in shared memory (n rows, row stride ld >= n + 1, compute type T), then
+// back substitution; the solution replaces column n.  Called by all threads of
+// the CTA.
+template <typename T>
+__device__ void lu_solve_smem(T* A, int ld, int n, int* prow, T* yk) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int k = 0; k < n; ++k) {
+    if (tid < 32) {   // pivot: argmax |A[i][k]|, i >= k (one warp)
+      T best = T(-1);
+      int bi = k;
+      for (int i = k + tid; i < n; i += 32) {
+        T v = A[i * ld + k];
+        v = v < T(0) ? -v : v;
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) *prow = bi;
+    }
+    __syncthreads();
+    const int p = *prow;
+    if (p != k)
+      for (int j = k + tid; j <= n; j += nth) {
+        T t = A[k * ld + j];
+        A[k * ld + j] = A[p * ld + j];
+        A[p * ld + j] = t;
+      }
+    __syncthreads();
+    T piv = A[k * ld + k];
+    if (piv == T(0)) piv = T(1e-30);
+    const int rows = n - k - 1, cols = n - k;   // columns k+1..n (incl. rhs)
+    for (int idx = tid; idx < rows * cols; idx += nth) {
+      int i = k + 1 + idx / cols, j = k + 1 + idx % cols;
+      A[i * ld + j] -= A[i * ld + k] / piv * A[k * ld + j];
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    if (tid == 0) {
+      T piv = A[k * ld + k];
+      if (piv == T(0)) piv = T(1e-30);
+      *yk = A[k * ld + n] / piv;
+      A[k * ld + n] = *yk;
+    }
+    __syncthreads();
+    const T y = *yk;
+    for (int i = tid; i < k; i += nth) A[i * ld + n] -= A[i * ld + k] * y;
+    __syncthreads();
+  }
+}
+
 // One CTA per right-hand side r: Gaussian elimination with partial pivoting on
 // [(H - sigma_r I) | b_r] in shared memory (compute type T), then back substitution.
 template <typename T>
@@ -505,53 +567,83 @@ __global__ void __launch_bounds__(512) k_lu_shift(const T* __restrict__ H, int l
     A[i * ld + j] = v;
   }
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    if (tid < 32) {   // pivot: argmax |A[i][k]|, i >= k (one warp)
-      T best = T(-1);
-      int bi = k;
-      for (int i = k + tid; i < n; i += 32) {
-        T v = A[i * ld + k];
-        v = v < T(0) ? -v : v;
-        if (v > best) { best = v; bi = i; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (tid == 0) prow = bi;
-    }
-    __syncthreads();
-    const int p = prow;
-    if (p != k)
-      for (int j = k + tid; j <= n; j += nth) {
-        T t = A[k * ld + j];
-        A[k * ld + j] = A[p * ld + j];
-        A[p * ld + j] = t;
-      }
-    __syncthreads();
-    T piv = A[k * ld + k];
-    if (piv == T(0)) piv = T(1e-30);
-    const int rows = n - k - 1, cols = n - k;   // columns k+1..n (incl. rhs)
-    for (int idx = tid; idx < rows * cols; idx += nth) {
-      int i = k + 1 + idx / cols, j = k + 1 + idx % cols;
-      A[i * ld + j] -= A[i * ld + k] / piv * A[k * ld + j];
-    }
-    __syncthreads();
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    if (tid == 0) {
-      T piv = A[k * ld + k];
-      if (piv == T(0)) piv = T(1e-30);
-      yk = A[k * ld + n] / piv;
-      A[k * ld + n] = yk;
-    }
-    __syncthreads();
-    const T y = yk;
-    for (int i = tid; i < k; i += nth) A[i * ld + n] -= A[i * ld + k] * y;
-    __syncthreads();
-  }
+  lu_solve_smem<T>(A, ld, n, &prow, &yk);
   for (int i = tid; i < n; i += nth) Y[(long long)r * n + i] = A[i * ld + n];
+}
+
+// Triangular solve by one warp on a vector b[n] in shared memory with the lower
+// factor L (global, row stride ldl): trans = 0: L x = b; 1: L^T x = b.
+template <typename T>
+__device__ void warp_trsv(const T* __restrict__ L, int ldl, int n, T* b, int trans) {
+  const int lane = threadIdx.x & 31;
+  if (!trans) {
+    for (int j = 0; j < n; ++j) {
+      const T xj = b[j] / L[(long long)j * ldl + j];
+      __syncwarp();
+      if (lane == 0) b[j] = xj;
+      for (int r = j + 1 + lane; r < n; r += 32) b[r] -= L[(long long)r * ldl + j] * xj;
+      __syncwarp();
+    }
+  } else {
+    for (int j = n - 1; j >= 0; --j) {
+      const T xj = b[j] / L[(long long)j * ldl + j];
+      __syncwarp();
+      if (lane == 0) b[j] = xj;
+      for (int r = lane; r < j; r += 32) b[r] -= L[(long long)j * ldl + r] * xj;
+      __syncwarp();
+    }
+  }
+}
+
+// The small part of one paired Galerkin iteration for system r (one CTA each),
+// with a- = L L^T and H = L^T a+ L:
+//   z = L^-1 h-,  rhs = L^T h+ + s z,  (H - s^2) u~ = rhs,  u = L u~,
+//   w = L^-T (z + s u~)          (h- absent: z = 0)
+template <typename T>
+__global__ void __launch_bounds__(512) k_paired_small(const T* __restrict__ L, const T* __restrict__ H,
+                                                      int ld, int n, const T* __restrict__ hp,
+                                                      const T* __restrict__ hm, const double* __restrict__ sh,
+                                                      T* __restrict__ uc, T* __restrict__ wc) {
+  extern __shared__ __align__(16) unsigned char ps_raw[];
+  const int la = n + 2;
+  T* A = reinterpret_cast<T*>(ps_raw);   // [n][n+2] augmented system
+  T* z = A + (size_t)n * la;             // [n]
+  T* hv = z + n;                         // [n]
+  __shared__ int prow;
+  __shared__ T yk;
+  const int r = blockIdx.x;
+  const T s = (T)sh[r];
+  const T s2 = (T)(sh[r] * sh[r]);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < n; i += nth) {
+    z[i] = hm ? hm[(long long)r * n + i] : T(0);
+    hv[i] = hp[(long long)r * n + i];
+  }
+  for (int idx = tid; idx < n * n; idx += nth) {
+    int i = idx / n, j = idx - i * n;
+    A[i * la + j] = T(0.5) * (H[(long long)i * ld + j] + H[(long long)j * ld + i]) - (i == j ? s2 : T(0));
+  }
+  __syncthreads();
+  if (hm && tid < 32) warp_trsv<T>(L, ld, n, z, 0);
+  __syncthreads();
+  for (int i = tid; i < n; i += nth) {   // rhs_i = sum_q h+_q L[q][i] + s z_i
+    T acc = s * z[i];
+    for (int q = i; q < n; ++q) acc += hv[q] * L[(long long)q * ld + i];
+    A[i * la + n] = acc;
+  }
+  __syncthreads();
+  lu_solve_smem<T>(A, la, n, &prow, &yk);
+  // u = L u~ ; z <- z + s u~
+  for (int i = tid; i < n; i += nth) {
+    T acc = T(0);
+    for (int q = 0; q <= i; ++q) acc += L[(long long)i * ld + q] * A[q * la + n];
+    uc[(long long)r * n + i] = acc;
+    hv[i] = z[i] + s * A[i * la + n];
+  }
+  __syncthreads();
+  if (tid < 32) warp_trsv<T>(L, ld, n, hv, 1);
+  __syncthreads();
+  for (int i = tid; i < n; i += nth) wc[(long long)r * n + i] = hv[i];
 }
 
 void set_smem(const void* f, size_t bytes) {
@@ -610,6 +702,22 @@ template void lu_shift_solve<float>(const float*, int, int, const double*, int, 
                                     cudaStream_t);
 template void lu_shift_solve<double>(const double*, int, int, const double*, int, const double*, double*,
                                      cudaStream_t);
+
+template <typename S>
+void paired_small_solve(const S* L, const S* H, int ld, int n, const S* hp, const S* hm, const double* sh,
+                        int nr, S* uc, S* wc, cudaStream_t s) {
+  if (nr <= 0) return;
+  TD_REQUIRE(n >= 1 && n <= kSmallMax, TDDFT_ERR_ARG, "paired_small_solve: size out of range");
+  size_t smem = ((size_t)n * (n + 2) + 2 * (size_t)n) * sizeof(S);
+  set_smem((const void*)k_paired_small<S>, smem);
+  k_paired_small<S><<<nr, 512, smem, s>>>(L, H, ld, n, hp, hm, sh, uc, wc);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+template void paired_small_solve<float>(const float*, const float*, int, int, const float*, const float*,
+                                        const double*, int, float*, float*, cudaStream_t);
+template void paired_small_solve<double>(const double*, const double*, int, int, const double*,
+                                         const double*, const double*, int, double*, double*, cudaStream_t);
 
 template <typename S>
 void cholesky(S* H, int ldh, int n, int* info, cudaStream_t s) {

@@ -32,6 +32,15 @@ template <typename S>
 void lu_shift_solve(const S* H, int ldh, int n, const double* sigma, int nr, const S* B, S* Y,
                     cudaStream_t s);
 
+// Small part of one paired Galerkin iteration, one CTA per system r < nr, with
+// a- = L L^T (L lower) and H = L^T a+ L (both n x n, row stride ld):
+//   z = L^-1 h-[r],  (H - s_r^2) u~ = L^T h+[r] + s_r z  (LU, partial pivoting),
+//   uc[r] = L u~,  wc[r] = L^-T (z + s_r u~)      (hm NULL: z = 0).
+// hp, hm, uc, wc: [nr][n]; sh: shifts s_r (device).  Type S throughout.
+template <typename S>
+void paired_small_solve(const S* L, const S* H, int ld, int n, const S* hp, const S* hm, const double* sh,
+                        int nr, S* uc, S* wc, cudaStream_t s);
+
 // In-place Cholesky H = L L^T (lower, zeroed above the diagonal), type S.
 // info[0] = 0 on success, j+1 when pivot j is not positive / not finite.
 template <typename S>
@@ -45,7 +54,7 @@ void trsv_rows(const S* L, int ldl, int n, S* B, int nr, int trans, cudaStream_t
 // Orthonormalisation helper for a block of candidate rows (Gram matrix
 // G = C C^T given): pivot-dropping Cholesky G = R^T R over the candidates in
 // order; a candidate whose remaining squared norm is below
-// drop2 * norm0sq[j] is dropped.  Writes T (nc x nc, row-major) with
+// drop2 * norm0sq[j] is dropped (norm0sq NULL: unit norms).  Writes T (nc x nc, row-major) with
 // C_new = T C orthonormal (zero rows for dropped) and keep[j] flags.
 void chol_drop(const double* G, int nc, const double* norm0sq, double drop2, double* T,
                int* keep, cudaStream_t s);

@@ -20,6 +20,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <cmath>
 #include <functional>
 #include <numeric>
@@ -165,18 +166,16 @@ void small_mm(int M, int N, int K, const S* A, long long sam, long long sak, con
   gemm(g, s);
 }
 
-// Orthonormalise the candidate rows `cand` [nc][ov] against V (N rows) and each
-// other, two passes; append the survivors at V[N...].  Returns their number.
+// Two passes of block Gram-Schmidt of the candidate rows `cand` [nc][ov]
+// against V (N orthonormal rows) and each other; the result overwrites cand and
+// keep[j] (device) flags the survivors (dropped rows are zero).
 template <typename T>
-int orth_append(T* V, int N, T* cand, int nc, int ov, cudaStream_t s) {
-  if (nc <= 0) return 0;
-  ScopedPhase ph(PH_ORTH, s);
+void orth_block(const T* V, int N, T* cand, int nc, int ov, int* keep, cudaStream_t s) {
   TD_REQUIRE(nc <= 112, TDDFT_ERR_ARG, "too many new directions in one iteration");
-  DevBuf n0(nc * 8, s), ones(nc * 8, s), G((size_t)nc * nc * 8, s), Tm((size_t)nc * nc * 8, s);
-  DevBuf keep(nc * 4, s), tmp((size_t)nc * ov * sizeof(T), s);
+  DevBuf n0(nc * 8, s), G((size_t)nc * nc * 8, s), Tm((size_t)nc * nc * 8, s);
+  DevBuf tmp((size_t)nc * ov * sizeof(T), s);
   DevBuf coef(N > 0 ? (size_t)N * nc * 8 : 8, s);
   row_sumsq<T>(cand, ov, nc, ov, n0.as<double>(), s);
-  h2d(ones.as<double>(), std::vector<double>(nc, 1.0), s);
   T* cur = cand;
   T* oth = tmp.as<T>();
   for (int pass = 0; pass < 2; ++pass) {
@@ -186,11 +185,21 @@ int orth_append(T* V, int N, T* cand, int nc, int ov, cudaStream_t s) {
       sk_combo<T>(coef.p, DType::F64, 1, nc, nc, N, V, ov, ov, cur, ov, -1.0, 1.0, s);
     }
     gram<T, double>(cur, nc, cur, nc, ov, G.as<double>(), nc, s);
-    chol_drop(G.as<double>(), nc, pass == 0 ? n0.as<double>() : ones.as<double>(), kDrop2,
-              Tm.as<double>(), keep.as<int>(), s);
+    chol_drop(G.as<double>(), nc, pass == 0 ? n0.as<double>() : nullptr, kDrop2, Tm.as<double>(), keep, s);
     combo<T, double>(Tm.as<double>(), nc, nc, cur, ov, oth, 1.0, 0.0, s);
     std::swap(cur, oth);
   }
+  // two swaps: the result is back in cand
+}
+
+// Orthonormalise `cand` against V and append the survivors at V[N...].
+// Returns their number (never more than ov - N).
+template <typename T>
+int orth_append(T* V, int N, T* cand, int nc, int ov, cudaStream_t s) {
+  if (nc <= 0) return 0;
+  ScopedPhase ph(PH_ORTH, s);
+  DevBuf keep(nc * 4, s);
+  orth_block<T>(V, N, cand, nc, ov, keep.as<int>(), s);
   std::vector<int> kh = d2h(keep.as<int>(), nc, s);
   std::vector<int> idx;
   for (int j = 0; j < nc && N + (int)idx.size() < ov; ++j)   // never beyond the space's dimension
@@ -198,9 +207,20 @@ int orth_append(T* V, int N, T* cand, int nc, int ov, cudaStream_t s) {
   if (!idx.empty()) {
     DevBuf di(idx.size() * 4, s);
     h2d(di.as<int>(), idx, s);
-    gather_rows<T>(cur, di.as<int>(), (int)idx.size(), ov, V + (size_t)N * ov, s);
+    gather_rows<T>(cand, di.as<int>(), (int)idx.size(), ov, V + (size_t)N * ov, s);
   }
   return (int)idx.size();
+}
+
+// The same without a host round trip: the survivors are compacted, in order,
+// into V[N...] (V must have room for nc rows there) and their number is left in
+// count[0] on the device; the caller caps it at ov - N when it reads it.
+template <typename T>
+void orth_append_async(T* V, int N, T* cand, int nc, int ov, int* keep, int* count, cudaStream_t s) {
+  if (nc <= 0) { TD_CUDA(cudaMemsetAsync(count, 0, sizeof(int), s)); return; }
+  ScopedPhase ph(PH_ORTH, s);
+  orth_block<T>(V, N, cand, nc, ov, keep, s);
+  compact_rows<T>(cand, keep, nc, ov, V + (size_t)N * ov, count, s);
 }
 
 void check_finite_host(const std::vector<double>& v, const char* what) {
@@ -341,8 +361,9 @@ struct PairedSpace {
   DevBuf V, P, M, ap, am, L, tmp, H, lam32, vec32;
   int N = 0, n_old = 0, n_new = 0;
   DevBuf info;
-  PairedSpace(int ov_, int cap_, cudaStream_t s_) : ov(ov_), cap(cap_), s(s_) {
-    V = DevBuf((size_t)cap * ov * sizeof(T), s);
+  // `slack` extra rows of V receive candidate directions before they are accepted
+  PairedSpace(int ov_, int cap_, cudaStream_t s_, int slack = 0) : ov(ov_), cap(cap_), s(s_) {
+    V = DevBuf((size_t)(cap + slack) * ov * sizeof(T), s);
     P = DevBuf((size_t)cap * ov * sizeof(T), s);
     M = DevBuf((size_t)cap * ov * sizeof(T), s);
     ap = DevBuf((size_t)cap * cap * sizeof(T), s);
@@ -419,14 +440,18 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
   struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
   cap = std::min(cap, kSmallMax);
   constexpr size_t es = sizeof(T);
-  PairedSpace<T> sp(ov, cap, s);
+  // Inner solves (ris operator) select, precondition and orthonormalise the new
+  // directions on the device and read back one status block per iteration.
+  const bool dev_select = !exact_op;
+  PairedSpace<T> sp(ov, cap, s, dev_select ? 2 * nr : 0);
   DevBuf sh(nr * 8, s), sig2(nr * 8, s);
   std::vector<double> s2(nr);
   for (int r = 0; r < nr; ++r) s2[r] = shifts[r] * shifts[r];
   h2d(sh.as<double>(), shifts, s);
   h2d(sig2.as<double>(), s2, s);
-  DevBuf hp((size_t)nr * cap * es, s), hm((size_t)nr * cap * es, s), rhs((size_t)nr * cap * es, s);
-  DevBuf ut((size_t)nr * cap * es, s), uc((size_t)nr * cap * es, s), wc((size_t)nr * cap * es, s);
+  // h+ and h- (and u, w coefficients) share one buffer so that, when g- follows
+  // g+ in memory, one Gram product forms both
+  DevBuf hpm((size_t)2 * nr * cap * es, s), ucw((size_t)2 * nr * cap * es, s);
   DevBuf Rp((size_t)nr * ov * es, s), Rm((size_t)nr * ov * es, s), PU((size_t)nr * ov * es, s),
       MW((size_t)nr * ov * es, s);
   DevBuf gn(nr * 8, s), gn2(nr * 8, s), rn1(nr * 8, s), rn2(nr * 8, s);
@@ -446,6 +471,18 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
     for (int r = 0; r < nr; ++r) gnh[r] += t[r];
   }
   for (auto& v : gnh) v = std::sqrt(v);
+  // status block read once per iteration: rn1[nr], rn2[nr] (doubles), then the
+  // Cholesky info and the number of accepted directions (ints)
+  DevBuf stat((size_t)2 * nr * 8 + 8, s), gdev(nr * 8, s), keep(2 * nr * 4, s);
+  double* rn1p = dev_select ? stat.as<double>() : rn1.as<double>();
+  double* rn2p = dev_select ? stat.as<double>() + nr : rn2.as<double>();
+  int* st_info = reinterpret_cast<int*>(stat.as<double>() + 2 * nr);
+  int* st_count = st_info + 1;
+  if (dev_select) {
+    std::vector<double> g1(nr);
+    for (int r = 0; r < nr; ++r) g1[r] = gnh[r] > 0 ? gnh[r] : 1.0;
+    h2d(gdev.as<double>(), g1, s);
+  }
 
   sp.N = orth_append<T>(sp.v(), 0, init, std::min(ni, cap), ov, s);
   TD_REQUIRE(sp.N >= 1, TDDFT_ERR_ARG, "paired solve: empty initial subspace");
@@ -453,8 +490,13 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
     auto t0 = Clock::now();
     ScopedPhase ph(exact_op ? PH_MV : PH_RIS, s);
     op(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
-    TD_CUDA(cudaStreamSynchronize(s));
-    if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
+    if (exact_op) {
+      TD_CUDA(cudaStreamSynchronize(s));
+      cnt.mv += m;
+      cnt.t_mv += since(t0);
+    } else {
+      cnt.ris_mv += m;
+    }
   };
   mv(0, sp.N);
   sp.n_old = 0;
@@ -463,46 +505,64 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
   for (int it = 1; it <= max_iter; ++it) {
     o.n_iter = it;
     sp.update(false);
-    sp.check_definite();
+    if (!dev_select) sp.check_definite();
     const int N = sp.N;
     T* Lp = sp.L.template as<T>();
     ScopedPhase ph_small(PH_SMALL, s);
-    // h+ = V g+ , h- = V g-   ([nr][N])
-    gram<T, T>(gp, nr, sp.v(), N, ov, hp.as<T>(), N, s);
-    // rhs = L^T h+  (rows): rhs[r][i] = sum_q h+[r][q] L[q][i]
-    small_mm<T>(nr, N, N, hp.as<T>(), N, 1, Lp, cap, 1, rhs.as<T>(), N, s);
-    if (gm) {
-      gram<T, T>(gm, nr, sp.v(), N, ov, hm.as<T>(), N, s);
-      trsv_rows<T>(Lp, cap, N, hm.as<T>(), nr, 0, s);                   // z- = L^-1 h-
-      axpy_rows<T>(rhs.as<T>(), hm.as<T>(), sh.as<double>(), nr, N, s);
+    // h+ = V g+ , h- = V g-   ([nr][N] each, h- right after h+)
+    T* hp = hpm.as<T>();
+    T* hm = hp + (size_t)nr * N;
+    if (gm == gp + (size_t)nr * ov) {
+      gram<T, T>(gp, 2 * nr, sp.v(), N, ov, hp, N, s);
+    } else {
+      gram<T, T>(gp, nr, sp.v(), N, ov, hp, N, s);
+      if (gm) gram<T, T>(gm, nr, sp.v(), N, ov, hm, N, s);
     }
-    // (H - s^2) u~ = rhs for every shift
+    // per system: z- = L^-1 h-, (H - s^2) u~ = L^T h+ + s z-, u = L u~, w = L^-T (z- + s u~)
+    T* uc = ucw.as<T>();
+    T* wc = uc + (size_t)nr * N;
     {
       ScopedPhase f(trace_level() >= 3 ? PH_LU : PH_N - 1, s);
-      lu_shift_solve<T>(sp.H.template as<T>(), cap, N, sig2.as<double>(), nr, rhs.as<T>(), ut.as<T>(), s);
-    }
-    // u = L u~ : u[r][i] = sum_q L[i][q] u~[r][q]
-    small_mm<T>(nr, N, N, ut.as<T>(), N, 1, Lp, 1, cap, uc.as<T>(), N, s);
-    // w = L^-T (z- + s u~)
-    if (gm) TD_CUDA(cudaMemcpyAsync(wc.p, hm.p, (size_t)nr * N * es, cudaMemcpyDeviceToDevice, s));
-    else TD_CUDA(cudaMemsetAsync(wc.p, 0, (size_t)nr * N * es, s));
-    axpy_rows<T>(wc.as<T>(), ut.as<T>(), sh.as<double>(), nr, N, s);
-    {
-      ScopedPhase f(trace_level() >= 3 ? PH_TRSV : PH_N - 1, s);
-      trsv_rows<T>(Lp, cap, N, wc.as<T>(), nr, 1, s);
+      paired_small_solve<T>(Lp, sp.H.template as<T>(), cap, N, hp, gm ? hm : nullptr, sh.as<double>(), nr,
+                            uc, wc, s);
     }
     ph_small.stop();
     ScopedPhase ph_vec(PH_VEC, s);
-    combo<T, T>(uc.as<T>(), nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
-    combo<T, T>(wc.as<T>(), nr, N, sp.v(), ov, Wout, 1.0, 0.0, s);
-    combo<T, T>(uc.as<T>(), nr, N, sp.p(), ov, PU.as<T>(), 1.0, 0.0, s);
-    combo<T, T>(wc.as<T>(), nr, N, sp.m(), ov, MW.as<T>(), 1.0, 0.0, s);
+    if (Wout == Uout + (size_t)nr * ov) {
+      combo<T, T>(uc, 2 * nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
+    } else {
+      combo<T, T>(uc, nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
+      combo<T, T>(wc, nr, N, sp.v(), ov, Wout, 1.0, 0.0, s);
+    }
+    combo<T, T>(uc, nr, N, sp.p(), ov, PU.as<T>(), 1.0, 0.0, s);
+    combo<T, T>(wc, nr, N, sp.m(), ov, MW.as<T>(), 1.0, 0.0, s);
     resid_paired<T>(Uout, Wout, PU.as<T>(), MW.as<T>(), sh.as<double>(), gp, gm, nr, ov,
                     Rp.as<T>(), Rm.as<T>(), s);
-    row_sumsq<T>(Rp.as<T>(), ov, nr, ov, rn1.as<double>(), s);
-    row_sumsq<T>(Rm.as<T>(), ov, nr, ov, rn2.as<double>(), s);
-    std::vector<double> a1 = d2h(rn1.as<double>(), nr, s), a2 = d2h(rn2.as<double>(), nr, s);
-    ph_vec.stop();
+    row_sumsq<T>(Rp.as<T>(), ov, nr, ov, rn1p, s);
+    row_sumsq<T>(Rm.as<T>(), ov, nr, ov, rn2p, s);
+    std::vector<double> a1, a2;
+    int dev_count = 0;
+    if (dev_select) {
+      // every system's new directions, the converged ones zeroed (and so dropped)
+      ph_vec.stop();
+      pre(Rp.as<T>(), Rm.as<T>(), sh.as<double>(), shifts, nr, cand.as<T>(), cand.as<T>() + (size_t)nr * ov);
+      zero_converged<T>(cand.as<T>(), 2 * nr, nr, ov, rn1p, rn2p, gdev.as<double>(), tol, s);
+      orth_append_async<T>(sp.v(), N, cand.as<T>(), 2 * nr, ov, keep.as<int>(), st_count, s);
+      TD_CUDA(cudaMemcpyAsync(st_info, sp.info.p, sizeof(int), cudaMemcpyDeviceToDevice, s));
+      std::vector<double> blk = d2h(stat.as<double>(), (size_t)2 * nr + 1, s);
+      int ints[2];
+      std::memcpy(ints, &blk[2 * nr], sizeof(ints));
+      if (ints[0] != 0)
+        throw Error(TDDFT_ERR_INDEFINITE, "projected A-B is not positive definite (pivot " +
+                                              std::to_string(ints[0] - 1) + ")");
+      dev_count = ints[1];
+      a1.assign(blk.begin(), blk.begin() + nr);
+      a2.assign(blk.begin() + nr, blk.begin() + 2 * nr);
+    } else {
+      a1 = d2h(rn1p, nr, s);
+      a2 = d2h(rn2p, nr, s);
+      ph_vec.stop();
+    }
     std::vector<int> todo;
     for (int r = 0; r < nr; ++r) {
       rr[r] = std::sqrt(a1[r] + a2[r]) / (gnh[r] > 0 ? gnh[r] : 1.0);
@@ -513,6 +573,15 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
     if (todo.empty()) { o.converged = true; break; }
     if (it == max_iter) break;
     const int nu = (int)todo.size();
+    if (dev_select) {
+      if (sp.N + 2 * nu > cap) break;   // inner solve: return the current approximate solution
+      const int nacc = std::min(dev_count, ov - sp.N);   // already in V[N...]
+      if (nacc == 0) break;
+      mv(sp.N, nacc);
+      sp.n_new += nacc;
+      sp.N += nacc;
+      continue;
+    }
     std::vector<double> shh(nu);
     for (int j = 0; j < nu; ++j) shh[j] = shifts[todo[j]];
     h2d(iu.as<int>(), todo, s);
@@ -700,20 +769,27 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
 // rid inner solves (Eq. precondition with the ris operator, Sec. 3.1)
 
 // (T - s_n) v_n = R_n by one block Galerkin subspace, diag-preconditioned
-// expansion, stopped at |res_n| <= tol |R_n| or max_iter iterations.
+// expansion, stopped at |res_n| <= tol |R_n| or max_iter iterations.  New
+// directions are selected, preconditioned and orthonormalised on the device;
+// the host reads one status block (residual norms, accepted count) per iteration.
 template <typename T>
 void inner_tda(int ov, const TdaOpT<T>& Top, const double* delta, const T* R, const double* sh,
                const std::vector<double>& shh, int nu, double tol, int max_iter,
                Counters& cnt, T* out, cudaStream_t s) {
+  (void)shh;
   InnerScope inner_scope;
   const int cap = kSmallMax;
   constexpr size_t es = sizeof(T);
-  DevBuf S((size_t)cap * ov * es, s), TS((size_t)cap * ov * es, s), t((size_t)cap * cap * es, s);
+  DevBuf S((size_t)(cap + nu) * ov * es, s), TS((size_t)cap * ov * es, s), t((size_t)cap * cap * es, s);
   DevBuf h((size_t)nu * cap * es, s), y((size_t)nu * cap * es, s);
-  DevBuf Tv((size_t)nu * ov * es, s), res((size_t)nu * ov * es, s), rn(nu * 8, s), r0(nu * 8, s);
-  DevBuf cand((size_t)nu * ov * es, s), iu(nu * 4, s), shu(nu * 8, s), resu((size_t)nu * ov * es, s);
+  DevBuf Tv((size_t)nu * ov * es, s), res((size_t)nu * ov * es, s), r0(nu * 8, s);
+  DevBuf cand((size_t)nu * ov * es, s), keep(nu * 4, s), stat((size_t)nu * 8 + 8, s);
+  double* rn = stat.as<double>();
+  int* st_count = reinterpret_cast<int*>(stat.as<double>() + nu);
   row_sumsq<T>(R, ov, nu, ov, r0.as<double>(), s);
   std::vector<double> r0h = sqrt_all(d2h(r0.as<double>(), nu, s));
+  for (auto& v : r0h) v = v > 0 ? v : 1.0;
+  h2d(r0.as<double>(), r0h, s);
   precond_tda<T>(R, sh, delta, nu, ov, cand.as<T>(), s);
   int N = orth_append<T>(S.as<T>(), 0, cand.as<T>(), nu, ov, s);
   if (N == 0) { TD_CUDA(cudaMemsetAsync(out, 0, (size_t)nu * ov * es, s)); return; }
@@ -734,21 +810,22 @@ void inner_tda(int ov, const TdaOpT<T>& Top, const double* delta, const T* R, co
     combo<T, T>(y.as<T>(), nu, N, S.as<T>(), ov, out, 1.0, 0.0, s);
     combo<T, T>(y.as<T>(), nu, N, TS.as<T>(), ov, Tv.as<T>(), 1.0, 0.0, s);
     resid_shift<T>(Tv.as<T>(), out, sh, R, nu, ov, res.as<T>(), s);
-    row_sumsq<T>(res.as<T>(), ov, nu, ov, rn.as<double>(), s);
-    std::vector<double> rh = sqrt_all(d2h(rn.as<double>(), nu, s));
-    std::vector<int> todo;
+    row_sumsq<T>(res.as<T>(), ov, nu, ov, rn, s);
+    const bool last = it == max_iter - 1;
+    if (!last) {
+      precond_tda<T>(res.as<T>(), sh, delta, nu, ov, cand.as<T>(), s);
+      zero_converged<T>(cand.as<T>(), nu, nu, ov, rn, nullptr, r0.as<double>(), tol, s);
+      orth_append_async<T>(S.as<T>(), N, cand.as<T>(), nu, ov, keep.as<int>(), st_count, s);
+    }
+    std::vector<double> blk = d2h(stat.as<double>(), (size_t)nu + 1, s);
+    int m = 0;
     for (int j = 0; j < nu; ++j)
-      if (!(rh[j] <= tol * r0h[j])) todo.push_back(j);
-    if (todo.empty() || it == max_iter - 1) break;
-    const int m = (int)todo.size();
-    std::vector<double> sm(m);
-    for (int j = 0; j < m; ++j) sm[j] = shh[todo[j]];
-    h2d(iu.as<int>(), todo, s);
-    h2d(shu.as<double>(), sm, s);
-    gather_rows<T>(res.as<T>(), iu.as<int>(), m, ov, resu.as<T>(), s);
-    precond_tda<T>(resu.as<T>(), shu.as<double>(), delta, m, ov, cand.as<T>(), s);
+      if (!(std::sqrt(blk[j]) / r0h[j] <= tol)) ++m;
+    if (m == 0 || last) break;
     if (N + m > cap) break;
-    int nacc = orth_append<T>(S.as<T>(), N, cand.as<T>(), m, ov, s);
+    int dev_count;
+    std::memcpy(&dev_count, &blk[nu], sizeof(int));
+    const int nacc = std::min(dev_count, ov - N);   // already in S[N...]
     if (nacc == 0) break;
     {
       ScopedPhase ph(PH_RIS, s);

@@ -1,6 +1,8 @@
 // Streaming kernels over singles vectors and factor staging.  All are bound by
 // HBM bandwidth (or, for FP64 arithmetic, by the FP64 pipe): grid-stride loops,
 // coalesced along the contiguous index, grids sized to a multiple of the SM count.
+#include <algorithm>
+
 #include "vecops.cuh"
 
 namespace tddft {
@@ -113,6 +115,43 @@ __global__ void k_gather_rows(const T* src, const int* idx, int k, int n, T* dst
     int r = (int)(t / n), e = (int)(t % n);
     dst[t] = src[(long long)idx[r] * n + e];
   }
+}
+
+// Row r of src goes to row (number of kept rows before r) of dst when keep[r].
+// Grid: x over column blocks, y over source rows.
+template <typename T>
+__global__ void k_compact_rows(const T* __restrict__ src, const int* __restrict__ keep, int nc, int n,
+                               T* __restrict__ dst, int* __restrict__ count) {
+  const int r = blockIdx.y;
+  __shared__ int pos;
+  if (threadIdx.x == 0) {
+    int p = 0;
+    for (int q = 0; q < r; ++q) p += keep[q] ? 1 : 0;
+    pos = p;
+    if (r == nc - 1 && blockIdx.x == 0) *count = p + (keep[r] ? 1 : 0);
+  }
+  __syncthreads();
+  if (!keep[r]) return;
+  const T* in = src + (long long)r * n;
+  T* out = dst + (long long)pos * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = in[e];
+}
+
+// Zero row r of X (rows of length n; row r uses flag index r % nr) when the
+// relative residual sqrt(a1[q] + a2[q]) / g[q] is at most tol (a2 may be NULL).
+template <typename T>
+__global__ void k_zero_converged(T* X, int rows, int nr, int n, const double* __restrict__ a1,
+                                 const double* __restrict__ a2, const double* __restrict__ g, double tol) {
+  const int r = blockIdx.y;
+  const int q = r % nr;
+  const double rr = sqrt(a1[q] + (a2 ? a2[q] : 0.0)) / g[q];
+  if (!(rr <= tol)) return;
+  T* x = X + (long long)r * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    x[e] = T(0);
 }
 
 template <typename S>
@@ -262,6 +301,31 @@ void gather_rows(const T* src, const int* idx, int k, int n, T* dst, cudaStream_
 }
 template void gather_rows<double>(const double*, const int*, int, int, double*, cudaStream_t);
 template void gather_rows<float>(const float*, const int*, int, int, float*, cudaStream_t);
+template <typename T>
+void compact_rows(const T* src, const int* keep, int nc, int n, T* dst, int* count, cudaStream_t s) {
+  if (nc <= 0) { TD_CUDA(cudaMemsetAsync(count, 0, sizeof(int), s)); return; }
+  TD_REQUIRE(nc <= 65535, TDDFT_ERR_ARG, "compact_rows: too many rows");
+  dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 64), nc);
+  k_compact_rows<T><<<grid, 256, 0, s>>>(src, keep, nc, n, dst, count);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+template void compact_rows<double>(const double*, const int*, int, int, double*, int*, cudaStream_t);
+template void compact_rows<float>(const float*, const int*, int, int, float*, int*, cudaStream_t);
+
+template <typename T>
+void zero_converged(T* X, int rows, int nr, int n, const double* a1, const double* a2, const double* g,
+                    double tol, cudaStream_t s) {
+  if (rows <= 0) return;
+  TD_REQUIRE(rows <= 65535 && nr >= 1, TDDFT_ERR_ARG, "zero_converged: bad rows");
+  dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 64), rows);
+  k_zero_converged<T><<<grid, 256, 0, s>>>(X, rows, nr, n, a1, a2, g, tol);
+  count_launch(); TD_LAUNCH_CHECK();
+}
+template void zero_converged<double>(double*, int, int, int, const double*, const double*, const double*,
+                                     double, cudaStream_t);
+template void zero_converged<float>(float*, int, int, int, const double*, const double*, const double*,
+                                    double, cudaStream_t);
+
 template <typename S>
 void sym_fill(S* a, int ld, int n_old, int n_new, cudaStream_t s) {
   if (n_new <= 0) return;

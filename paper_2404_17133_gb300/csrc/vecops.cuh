@@ -28,6 +28,15 @@ void precond_tda(const T* R, const double* omega, const double* delta, int k, in
 template <typename T>
 void precond_paired(const T* gp, const T* gm, const double* shift, const double* delta, int k, int n,
                     T* out_u, T* out_w, cudaStream_t s);
+// Stream compaction of rows: the rows r < nc of src with keep[r] != 0 go, in
+// order, to the leading rows of dst; count[0] = their number.
+template <typename T>
+void compact_rows(const T* src, const int* keep, int nc, int n, T* dst, int* count, cudaStream_t s);
+// Zero row r of X [rows][n] when sqrt(a1[q] + a2[q]) / g[q] <= tol, q = r % nr
+// (a2 may be NULL): masks the directions of converged systems on the device.
+template <typename T>
+void zero_converged(T* X, int rows, int nr, int n, const double* a1, const double* a2, const double* g,
+                    double tol, cudaStream_t s);
 // dst[r] = src[idx[r]] (rows of length n).
 template <typename T>
 void gather_rows(const T* src, const int* idx, int k, int n, T* dst, cudaStream_t s);
