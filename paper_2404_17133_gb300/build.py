@@ -18,7 +18,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIBNAME = "libtddft_gb300.so"
 LIBPATH = os.path.join(LIBDIR, LIBNAME)
 
-SOURCES = ["gemm.cu", "small.cu", "vecops.cu", "operator.cu", "tc_gemm.cu", "skinny.cu", "solver.cu", "capi.cu",
+SOURCES = ["devpool.cu", "gemm.cu", "small.cu", "vecops.cu", "operator.cu", "tc_gemm.cu", "skinny.cu", "solver.cu", "capi.cu",
            "apply_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

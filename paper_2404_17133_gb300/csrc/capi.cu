@@ -545,6 +545,7 @@ void tddft_destroy(tddft_ctx* ctx) {
   cudaStream_t s = c->s;
   bool own = c->own_stream;
   delete c;  // DevBuf destructors free on the stream
+  if (s) pool_trim(s);
   if (s) cudaStreamSynchronize(s);
   if (own && s) cudaStreamDestroy(s);
 }

@@ -44,6 +44,18 @@ extern thread_local long long g_launches;
 inline void count_launch(int n = 1) { g_launches += n; }
 
 // --------------------------------------------------------------------------
+// Stream-ordered work buffers.  Blocks up to 64 MiB are cached per stream after
+// release and handed out again to later requests of the same size class on the
+// same stream (stream order makes the reuse safe), so the many small buffers
+// of an iterative solve cost no allocator calls; larger blocks go straight to
+// cudaMallocAsync / cudaFreeAsync.  pool_trim returns a stream's cached blocks.
+void* pool_get(size_t bytes, cudaStream_t s);
+void pool_put(void* p, size_t bytes, cudaStream_t s);
+void pool_trim(cudaStream_t s);
+
+// Raise a kernel's dynamic shared-memory limit (once per kernel, size and device).
+void ensure_smem(const void* kernel, size_t bytes);
+
 // Device buffer owned by host code (stream-ordered allocation).
 struct DevBuf {
   void* p = nullptr;
@@ -51,7 +63,7 @@ struct DevBuf {
   cudaStream_t s = nullptr;
   DevBuf() = default;
   DevBuf(size_t n, cudaStream_t st) : bytes(n), s(st) {
-    if (n) TD_CUDA(cudaMallocAsync(&p, n, st));
+    if (n) p = pool_get(n, st);
   }
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
@@ -66,7 +78,7 @@ struct DevBuf {
   }
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFreeAsync(p, s);
+    if (p) pool_put(p, bytes, s);
     p = nullptr; bytes = 0;
   }
   template <typename T> T* as() const { return static_cast<T*>(p); }

@@ -15,6 +15,7 @@
 // workspace; the second contractions of K1 and K2 (most of the flops) run on the
 // tcgen05 tensor cores when asked (MIXED precision).
 #include "ctx.cuh"
+#include "skinny.cuh"
 #include "tc_gemm.cuh"
 #include "vecops.cuh"
 
@@ -101,22 +102,11 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
   // ---- Coulomb
   DevBuf Jb;
   if (f.nJ > 0 && d.c_J != 0.0) {
+    // t[P][n] = sum_ia L_ov[P][ia] X[n][ia];  J[n][ia] = sum_P t[P][n] L_ov[P][ia]
     DevBuf t((size_t)f.nJ * m * ew, s);
     Jb = DevBuf(mov * ew, s);
-    GemmDesc g;
-    g.acc64 = f64;
-    g.M = f.nJ; g.N = m; g.K = ov;
-    g.A = f.Jov; g.ta = f.dt; g.sam = ov; g.sak = 1;
-    g.B = Xw; g.tb = tw; g.sbk = 1; g.sbn = ov;
-    g.C = t.p; g.tc = tw; g.scm = m; g.scn = 1;
-    gemm_splitk(g, auto_splits(g.M, g.N, g.K), s);
-    GemmDesc h;
-    h.acc64 = f64;
-    h.M = m; h.N = ov; h.K = f.nJ;
-    h.A = t.p; h.ta = tw; h.sam = 1; h.sak = m;
-    h.B = f.Jov; h.tb = f.dt; h.sbk = ov; h.sbn = 1;
-    h.C = Jb.p; h.tc = tw; h.scm = ov; h.scn = 1;
-    gemm(h, s);
+    sk_gram(f.Jov, f.dt, ov, f.nJ, Xw, tw, ov, m, ov, t.p, tw, m, 1.0, 0.0, s);
+    sk_combo(t.p, tw, 1, m, m, f.nJ, f.Jov, f.dt, ov, ov, Jb.p, tw, ov, 1.0, 0.0, s);
   }
 
   // ---- exchange

@@ -404,6 +404,78 @@ __global__ void __launch_bounds__(1024) k_cholesky(S* __restrict__ H, int ldh, i
   }
 }
 
+// Bordered Cholesky: rows < n0 of L already hold the factor of the leading
+// block; rows n0..n-1 hold the new rows of the matrix (all n columns).  Each new
+// row is first solved against the old factor by its own warp (forward
+// substitution, no block barriers), then the new diagonal block is factored
+// column by column.  Entries above the diagonal in the first n columns are zeroed.
+template <typename S>
+__global__ void __launch_bounds__(1024) k_chol_border(S* __restrict__ Lg, int ld, int n0, int n,
+                                                      int* __restrict__ info) {
+  extern __shared__ __align__(16) unsigned char cb_raw[];
+  S* L = reinterpret_cast<S*>(cb_raw);   // [n][n] working copy (row stride n)
+  __shared__ int bad;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx / n, c = idx - r * n;
+    L[idx] = Lg[(long long)r * ld + c];
+  }
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  // phase 1: L[i][j], j < n0, for every new row i
+  for (int i = n0 + warp; i < n; i += nw) {
+    S* Li = L + i * n;
+    for (int j = 0; j < n0; ++j) {
+      const S* Lj = L + j * n;
+      S acc = S(0);
+      for (int q = lane; q < j; q += 32) acc += Li[q] * Lj[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      const S v = (Li[j] - acc) / Lj[j];
+      __syncwarp();
+      if (lane == 0) Li[j] = v;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // phase 2: the new diagonal block, column by column
+  for (int j = n0; j < n; ++j) {
+    S* Lj = L + j * n;
+    if (warp == 0) {
+      S acc = S(0);
+      for (int q = lane; q < j; q += 32) acc += Lj[q] * Lj[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      const S d = Lj[j] - acc;
+      __syncwarp();
+      if (lane == 0) {
+        if (!(d > S(0)) || !isfinite(d)) bad = j + 1;
+        else Lj[j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    for (int i = j + 1 + warp; i < n; i += nw) {
+      S* Li = L + i * n;
+      S acc = S(0);
+      for (int q = lane; q < j; q += 32) acc += Li[q] * Lj[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      const S v = (Li[j] - acc) / Lj[j];
+      __syncwarp();
+      if (lane == 0) Li[j] = v;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) info[0] = bad;
+  if (bad) return;
+  // write back, zero above the diagonal
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx / n, c = idx - r * n;
+    Lg[(long long)r * ld + c] = c <= r ? L[idx] : S(0);
+  }
+}
+
 template <typename S>
 __global__ void __launch_bounds__(256) k_trsv(const S* __restrict__ L, int ldl, int n,
                                               S* __restrict__ B, int trans) {
@@ -492,57 +564,68 @@ __global__ void __launch_bounds__(1024) k_chol_drop(const double* __restrict__ G
 
 // Gaussian elimination with partial pivoting on the augmented matrix [M | b]
 // held in shared memory (n rows, row stride ld >= n + 1, compute type T), then
-// back substitution; the solution replaces column n.  Called by all threads of
-// the CTA.
+// back substitution; the solution replaces column n (in the original row order).
+// Rows are not moved: perm[] (shared, >= n ints) records the pivot order, so an
+// elimination step is one pivot search (warp 0) and one update pass.  Called by
+// all threads of the CTA.
 template <typename T>
-__device__ void lu_solve_smem(T* A, int ld, int n, int* prow, T* yk) {
-  const int tid = threadIdx.x, nth = blockDim.x;
+__device__ void lu_solve_smem(T* A, int ld, int n, int* perm, T* y) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < n; i += blockDim.x) perm[i] = i;
+  __syncthreads();
   for (int k = 0; k < n; ++k) {
-    if (tid < 32) {   // pivot: argmax |A[i][k]|, i >= k (one warp)
+    if (warp == 0) {   // pivot: argmax |A[perm[i]][k]|, i >= k
       T best = T(-1);
       int bi = k;
-      for (int i = k + tid; i < n; i += 32) {
-        T v = A[i * ld + k];
+      for (int i = k + lane; i < n; i += 32) {
+        T v = A[perm[i] * ld + k];
         v = v < T(0) ? -v : v;
         if (v > best) { best = v; bi = i; }
       }
+#pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         T ob = __shfl_xor_sync(0xffffffffu, best, o);
         int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (tid == 0) *prow = bi;
-    }
-    __syncthreads();
-    const int p = *prow;
-    if (p != k)
-      for (int j = k + tid; j <= n; j += nth) {
-        T t = A[k * ld + j];
-        A[k * ld + j] = A[p * ld + j];
-        A[p * ld + j] = t;
+      if (lane == 0 && bi != k) {
+        const int t = perm[k];
+        perm[k] = perm[bi];
+        perm[bi] = t;
       }
+    }
     __syncthreads();
-    T piv = A[k * ld + k];
+    const int pk = perm[k];
+    const T* prow = A + pk * ld;
+    T piv = prow[k];
     if (piv == T(0)) piv = T(1e-30);
-    const int rows = n - k - 1, cols = n - k;   // columns k+1..n (incl. rhs)
-    for (int idx = tid; idx < rows * cols; idx += nth) {
-      int i = k + 1 + idx / cols, j = k + 1 + idx % cols;
-      A[i * ld + j] -= A[i * ld + k] / piv * A[k * ld + j];
+    const T inv = T(1) / piv;
+    for (int i = k + 1 + warp; i < n; i += nw) {
+      T* row = A + perm[i] * ld;
+      const T l = row[k] * inv;
+      for (int j = k + 1 + lane; j <= n; j += 32) row[j] -= l * prow[j];
     }
     __syncthreads();
   }
-  for (int k = n - 1; k >= 0; --k) {
-    if (tid == 0) {
-      T piv = A[k * ld + k];
+  // back substitution by one warp: y_k = (b_k - sum_{j>k} U_kj y_j) / U_kk
+  if (warp == 0) {
+    for (int k = n - 1; k >= 0; --k) {
+      const T* row = A + perm[k] * ld;
+      T piv = row[k];
       if (piv == T(0)) piv = T(1e-30);
-      *yk = A[k * ld + n] / piv;
-      A[k * ld + n] = *yk;
+      const T yk = row[n] / piv;
+      __syncwarp();
+      for (int i = lane; i < k; i += 32) {
+        T* ri = A + perm[i] * ld;
+        ri[n] -= ri[k] * yk;
+      }
+      if (lane == 0) y[k] = yk;
+      __syncwarp();
     }
-    __syncthreads();
-    const T y = *yk;
-    for (int i = tid; i < k; i += nth) A[i * ld + n] -= A[i * ld + k] * y;
-    __syncthreads();
   }
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) A[i * ld + n] = y[i];
+  __syncthreads();
 }
 
 // One CTA per right-hand side r: Gaussian elimination with partial pivoting on
@@ -554,8 +637,8 @@ __global__ void __launch_bounds__(512) k_lu_shift(const T* __restrict__ H, int l
   extern __shared__ __align__(16) unsigned char lu_raw[];
   T* A = reinterpret_cast<T*>(lu_raw);
   const int ld = n + 2;
-  __shared__ int prow;
-  __shared__ T yk;
+  __shared__ int perm[kSmallMax];
+  __shared__ T yv[kSmallMax];
   const int r = blockIdx.x;
   const double sg = sig[r];
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -567,7 +650,7 @@ __global__ void __launch_bounds__(512) k_lu_shift(const T* __restrict__ H, int l
     A[i * ld + j] = v;
   }
   __syncthreads();
-  lu_solve_smem<T>(A, ld, n, &prow, &yk);
+  lu_solve_smem<T>(A, ld, n, perm, yv);
   for (int i = tid; i < n; i += nth) Y[(long long)r * n + i] = A[i * ld + n];
 }
 
@@ -600,7 +683,7 @@ __device__ void warp_trsv(const T* __restrict__ L, int ldl, int n, T* b, int tra
 //   z = L^-1 h-,  rhs = L^T h+ + s z,  (H - s^2) u~ = rhs,  u = L u~,
 //   w = L^-T (z + s u~)          (h- absent: z = 0)
 template <typename T>
-__global__ void __launch_bounds__(512) k_paired_small(const T* __restrict__ L, const T* __restrict__ H,
+__global__ void __launch_bounds__(512) k_paired_small(const T* __restrict__ Lg, const T* __restrict__ H,
                                                       int ld, int n, const T* __restrict__ hp,
                                                       const T* __restrict__ hm, const double* __restrict__ sh,
                                                       T* __restrict__ uc, T* __restrict__ wc) {
@@ -609,8 +692,20 @@ __global__ void __launch_bounds__(512) k_paired_small(const T* __restrict__ L, c
   T* A = reinterpret_cast<T*>(ps_raw);   // [n][n+2] augmented system
   T* z = A + (size_t)n * la;             // [n]
   T* hv = z + n;                         // [n]
-  __shared__ int prow;
-  __shared__ T yk;
+  // FP32: a copy of L in shared memory (row stride n + 1, so that column walks
+  // are free of bank conflicts); FP64 (too large): L read from global memory
+  constexpr bool kLs = sizeof(T) == 4;
+  if (kLs) {
+    T* Ls = hv + n;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int r = idx / n, c = idx - r * n;
+      Ls[r * (n + 1) + c] = Lg[(long long)r * ld + c];
+    }
+  }
+  const T* L = kLs ? hv + n : Lg;
+  const int ll = kLs ? n + 1 : ld;
+  __shared__ int perm[kSmallMax];
+  __shared__ T yv[kSmallMax];
   const int r = blockIdx.x;
   const T s = (T)sh[r];
   const T s2 = (T)(sh[r] * sh[r]);
@@ -624,30 +719,30 @@ __global__ void __launch_bounds__(512) k_paired_small(const T* __restrict__ L, c
     A[i * la + j] = T(0.5) * (H[(long long)i * ld + j] + H[(long long)j * ld + i]) - (i == j ? s2 : T(0));
   }
   __syncthreads();
-  if (hm && tid < 32) warp_trsv<T>(L, ld, n, z, 0);
+  if (hm && tid < 32) warp_trsv<T>(L, ll, n, z, 0);
   __syncthreads();
   for (int i = tid; i < n; i += nth) {   // rhs_i = sum_q h+_q L[q][i] + s z_i
     T acc = s * z[i];
-    for (int q = i; q < n; ++q) acc += hv[q] * L[(long long)q * ld + i];
+    for (int q = i; q < n; ++q) acc += hv[q] * L[(long long)q * ll + i];
     A[i * la + n] = acc;
   }
   __syncthreads();
-  lu_solve_smem<T>(A, la, n, &prow, &yk);
+  lu_solve_smem<T>(A, la, n, perm, yv);
   // u = L u~ ; z <- z + s u~
   for (int i = tid; i < n; i += nth) {
     T acc = T(0);
-    for (int q = 0; q <= i; ++q) acc += L[(long long)i * ld + q] * A[q * la + n];
+    for (int q = 0; q <= i; ++q) acc += L[(long long)i * ll + q] * A[q * la + n];
     uc[(long long)r * n + i] = acc;
     hv[i] = z[i] + s * A[i * la + n];
   }
   __syncthreads();
-  if (tid < 32) warp_trsv<T>(L, ld, n, hv, 1);
+  if (tid < 32) warp_trsv<T>(L, ll, n, hv, 1);
   __syncthreads();
   for (int i = tid; i < n; i += nth) wc[(long long)r * n + i] = hv[i];
 }
 
 void set_smem(const void* f, size_t bytes) {
-  TD_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  ensure_smem(f, bytes);
 }
 
 }  // namespace
@@ -708,7 +803,7 @@ void paired_small_solve(const S* L, const S* H, int ld, int n, const S* hp, cons
                         int nr, S* uc, S* wc, cudaStream_t s) {
   if (nr <= 0) return;
   TD_REQUIRE(n >= 1 && n <= kSmallMax, TDDFT_ERR_ARG, "paired_small_solve: size out of range");
-  size_t smem = ((size_t)n * (n + 2) + 2 * (size_t)n) * sizeof(S);
+  size_t smem = ((size_t)n * (n + 2) + 2 * (size_t)n + (sizeof(S) == 4 ? (size_t)n * (n + 1) : 0)) * sizeof(S);
   set_smem((const void*)k_paired_small<S>, smem);
   k_paired_small<S><<<nr, 512, smem, s>>>(L, H, ld, n, hp, hm, sh, uc, wc);
   count_launch();
@@ -729,6 +824,18 @@ void cholesky(S* H, int ldh, int n, int* info, cudaStream_t s) {
   TD_LAUNCH_CHECK();
 }
 template void cholesky<float>(float*, int, int, int*, cudaStream_t);
+
+template <typename S>
+void cholesky_border(S* L, int ld, int n0, int n, int* info, cudaStream_t s) {
+  TD_REQUIRE(n >= 1 && n <= kSmallMax && n0 >= 0 && n0 <= n, TDDFT_ERR_ARG, "cholesky_border: bad sizes");
+  const size_t smem = (size_t)n * n * sizeof(S);
+  ensure_smem((const void*)k_chol_border<S>, smem);
+  k_chol_border<S><<<1, 1024, smem, s>>>(L, ld, n0, n, info);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+template void cholesky_border<float>(float*, int, int, int, int*, cudaStream_t);
+template void cholesky_border<double>(double*, int, int, int, int*, cudaStream_t);
 template void cholesky<double>(double*, int, int, int*, cudaStream_t);
 
 template <typename S>

@@ -46,6 +46,13 @@ void paired_small_solve(const S* L, const S* H, int ld, int n, const S* hp, cons
 template <typename S>
 void cholesky(S* H, int ldh, int n, int* info, cudaStream_t s);
 
+// Bordered Cholesky: rows < n0 of L (row stride ld) hold the lower factor of
+// the leading n0 x n0 block; rows n0..n-1 hold rows n0..n-1 of the matrix.  On
+// return rows n0..n-1 hold the factor's new rows (zero above the diagonal).
+// info[0] = 0 on success, j+1 when pivot j is not positive / not finite.
+template <typename S>
+void cholesky_border(S* L, int ld, int n0, int n, int* info, cudaStream_t s);
+
 // Triangular solves with the lower factor L (n x n, ldl) for nr right-hand
 // sides stored as rows of B (in place): trans = 0: L x = b; 1: L^T x = b.
 template <typename S>

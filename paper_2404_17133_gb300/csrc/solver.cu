@@ -386,10 +386,14 @@ struct PairedSpace {
     proj_cols<T>(v(), N, m() + (size_t)n_old * ov, n_new, ov, am.as<T>(), cap, n_old, s);
     sym_fill<T>(ap.as<T>(), cap, n_old, n_new, s);
     sym_fill<T>(am.as<T>(), cap, n_old, n_new, s);
-    TD_CUDA(cudaMemcpyAsync(L.p, am.p, (size_t)cap * cap * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    // a- = L L^T: the leading n_old rows of L are kept (the basis grows by
+    // bordering); the new rows of a- are copied in and factored
+    TD_CUDA(cudaMemcpy2DAsync(L.as<T>() + (size_t)n_old * cap, cap * sizeof(T),
+                              am.as<T>() + (size_t)n_old * cap, cap * sizeof(T), N * sizeof(T), n_new,
+                              cudaMemcpyDeviceToDevice, s));
     {
       ScopedPhase f(trace_level() >= 3 ? PH_CHOL : PH_N - 1, s);
-      cholesky<T>(L.as<T>(), cap, N, info.as<int>(), s);
+      cholesky_border<T>(L.as<T>(), cap, n_old, N, info.as<int>(), s);
     }
     {
       ScopedPhase f(trace_level() >= 3 ? PH_SMM : PH_N - 1, s);

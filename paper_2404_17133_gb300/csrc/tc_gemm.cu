@@ -544,20 +544,10 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
   Params p{M, N, nab, total, per, part.as<float>(), err};
   dim3 grid(nt, mt, splits);
   if (split) {
-    static bool attr = false;
-    if (!attr) {
-      TD_CUDA(cudaFuncSetAttribute(k1_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   Cfg<true>::SMEM_BYTES));
-      attr = true;
-    }
+    ensure_smem((const void*)k1_tc_kernel<true>, Cfg<true>::SMEM_BYTES);
     k1_tc_kernel<true><<<grid, THREADS, Cfg<true>::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, p);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      TD_CUDA(cudaFuncSetAttribute(k1_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   Cfg<false>::SMEM_BYTES));
-      attr = true;
-    }
+    ensure_smem((const void*)k1_tc_kernel<false>, Cfg<false>::SMEM_BYTES);
     k1_tc_kernel<false><<<grid, THREADS, Cfg<false>::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, p);
   }
   count_launch();
@@ -607,10 +597,10 @@ void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
              a_bytes, b_bytes, out_hi, out_lo, err};
   dim3 grid(mt, groups, 1);
   if (split) {
-    TD_CUDA(cudaFuncSetAttribute(k_stage1_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ensure_smem((const void*)k_stage1_tc<true>, smem);
     k_stage1_tc<true><<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
   } else {
-    TD_CUDA(cudaFuncSetAttribute(k_stage1_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ensure_smem((const void*)k_stage1_tc<false>, smem);
     k_stage1_tc<false><<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
   }
   count_launch();

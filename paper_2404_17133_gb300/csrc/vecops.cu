@@ -51,8 +51,17 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_row_sumsq(const T* X, long long ldx, int n, double* out) {
   __shared__ double red[32];
   const T* x = X + blockIdx.x * ldx;
-  double acc = 0.0;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) { double v = (double)x[e]; acc += v * v; }
+  // per-thread partials in the row's precision (FP32 rows: FP32 FMA rate); four
+  // independent accumulators keep four loads in flight
+  T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+  const int st = blockDim.x;
+  int e = threadIdx.x;
+  for (; e + 3 * st < n; e += 4 * st) {
+    const T v0 = x[e], v1 = x[e + st], v2 = x[e + 2 * st], v3 = x[e + 3 * st];
+    p0 = fma(v0, v0, p0); p1 = fma(v1, v1, p1); p2 = fma(v2, v2, p2); p3 = fma(v3, v3, p3);
+  }
+  for (; e < n; e += st) { const T v = x[e]; p0 = fma(v, v, p0); }
+  double acc = ((double)p0 + (double)p1) + ((double)p2 + (double)p3);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();

@@ -9,7 +9,8 @@ void delta_kernel(const double* eps_o, const double* eps_v, int no, int nv, doub
                   cudaStream_t s);
 // Rows r < k of out [k][n]: unit vector at column idx[r].
 void unit_rows(double* out, int k, int n, const int* idx, cudaStream_t s);
-// out[r] = sum_e X[r][e]^2 (FP64, deterministic), X rows of stride ldx.
+// out[r] = sum_e X[r][e]^2 (deterministic; per-thread partial sums in T, the
+// block sum in FP64), X rows of stride ldx.
 template <typename T>
 void row_sumsq(const T* X, long long ldx, int k, int n, double* out, cudaStream_t s);
 // R = AX - diag(omega) X  (Eq. residual).
