@@ -4,15 +4,19 @@
 One step is the whole hot path on the medium response workload (n_occ=60,
 n_vir=400, n_aux=2000, ris n_aux=360): a Casida solve for the 10 lowest states
 and the polarizability alpha(omega) for 3 dipoles at omega = 0, 0.05, 0.1 Ha,
-both with the rid preconditioner to a residual of 1e-5, MIXED precision (FP32
-exact products, or BF16 hi+lo on the tensor cores with --tensor-cores; BF16 ris
-inner solves; FP64 subspace algebra; FP32 re-certification of the residuals).
+both with the rid preconditioner to a residual of 1e-5, MIXED precision (exact
+products as BF16 hi+lo on the tcgen05 tensor cores, FP32 accumulation; ris
+inner solves with FP32 vectors on the BF16 ris factors; FP64 outer subspace
+algebra; FP32 re-certification of the converged residuals).
 
 value: states converged per second (10 per step x steps x ranks / max time),
-device-timed with CUDA events on the solver's stream, factors resident in HBM.
+device-timed with CUDA events on the solver's stream, factors resident in HBM;
+p50/p99 over the per-step times (30 steps by default).
 e2e:   the same through the C ABI with host (pinned) inputs: tddft_create
        (host->device copy and conversion of every factor) + the two solves
        with host outputs + tddft_destroy, every step.
+plain: the same step in the plain FP64 form on the same GPU (FP64 factors,
+       vectors and inner solves, SIMT contractions), for mixed vs plain.
 Inputs (the FP32/BF16 factors, 2.8 GB) are larger than L2, so no L2 flush is
 added between steps.
 
@@ -47,13 +51,15 @@ UNIT = "states/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tensor-cores", type=int, default=-1, help="1/0 (default 1: tcgen05 exchange)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=1,
+                    help="steps of the plain FP64 form timed for the mixed-vs-plain comparison (0: skip)")
     ap.add_argument("--precond", default="rid", choices=["rid", "diag"])
     ap.add_argument("--apply-only", type=int, default=0, metavar="K",
                     help="time K exact pair products ((A+B)X, (A-B)X) of 2*n_states device vectors "
@@ -242,7 +248,7 @@ def our_arm(args, rank, world, local):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    prof = solver.profile_read()
+    prof = solver.profile_read(0 if tc else 1)
     solver.profile(False)
     clk = clocks.stop() if clocks else None
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
@@ -268,6 +274,36 @@ def our_arm(args, rank, world, local):
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_t = statistics.mean(e2e_ms) if e2e_ms else float("nan")
+
+    # ---- the plain FP64 form of the same step (FP64 inputs, FP64 everywhere, SIMT)
+    plain = None
+    if args.plain_steps > 0 and rank == 0:
+        f64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+        sp = api.Solver(p.n_occ, p.n_vir, dev["eo"], dev["ev"], f64(p.L_oo), f64(p.L_ov), f64(p.L_vv),
+                        f64(p.Lr_oo[kidx]), f64(p.Lr_ov), f64(p.Lr_vv[kidx]), dev["k"], a_x=p.a_x,
+                        coulomb_factor=p.coulomb_factor, t_cut_ha=p.t_cut_ha, precisions=1, dtype=api.F64,
+                        stream=stream.cuda_stream)
+        o_rpa_p = api.default_opts(n_states=N_STATES, precond=pc, precision=api.PLAIN)
+        o_pol_p = api.default_opts(precond=pc, precision=api.PLAIN)
+        pms, pit = [], []
+        for _ in range(args.plain_steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ra = sp.solve_rpa(o_rpa_p, want_vectors=False)
+            rb = sp.solve_polar(o_pol_p, mu, omegas)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pms.append(e0.elapsed_time(e1))
+            pit.append((ra["stats"]["n_iter"], rb["stats"]["n_iter"]))
+        sp.close()
+        pm = statistics.mean(pms)
+        plain = {"value": N_STATES / (pm / 1e3), "unit": UNIT, "ms_per_step": pm, "steps": args.plain_steps,
+                 "dtype": "f64", "rpa_n_iter": pit[-1][0], "polar_n_iter": pit[-1][1],
+                 "max_abs_omega_diff_vs_mixed": float(np.max(np.abs(np.asarray(ra["omega"]) -
+                                                                    np.asarray(results[-1][0]["omega"])))),
+                 "note": "same step in the plain form: FP64 factors and vectors, SIMT contractions, "
+                         "FP64 inner solves; warm kernels, one step"}
     if world > 1:
         t = torch.tensor([e2e_t], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -312,6 +348,8 @@ def our_arm(args, rank, world, local):
             "polar": {"n_iter": b["stats"]["n_iter"], "n_matvec": b["stats"]["n_matvec"],
                       "alpha_static_diag": [float(b["alpha"][0][i][i]) for i in range(cfg["n_dip"])]},
             "roofline": roof,
+            "plain": plain,
+            "speedup_vs_plain": (plain["ms_per_step"] / (total_ms / args.steps)) if plain else None,
             "gpu_launches": launches,
             "clocks": clk,
             "e2e": {"value": N_STATES * world / (e2e_t / 1e3), "unit": UNIT, "ms_per_step": e2e_t,

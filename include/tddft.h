@@ -224,7 +224,10 @@ tddft_status tddft_apply_noalloc(tddft_ctx* ctx, int kind, int precision, const 
  * sum_(P,a) Z[(n,i)][(P,a)] L^P_ab of the exact operator -- and resets the
  * totals; 0 stops.  tddft_profile_read returns, for that contraction, the
  * number of launches, their summed device time (ms) and the algorithmic
- * flops (2*M*N*K per launch) since the last reset.  which must be 0.       */
+ * flops (2*M*N*K per launch) since the last reset: which = 0 for the
+ * tcgen05 kernel (tensor_cores on), 1 for the SIMT kernel (tensor cores off,
+ * and the FP32 re-certification of MIXED residuals).  Other values:
+ * TDDFT_ERR_ARG.                                                          */
 tddft_status tddft_profile(tddft_ctx* ctx, int enable);
 tddft_status tddft_profile_read(const tddft_ctx* ctx, int which, long long* launches,
                                 double* ms, double* flops);

@@ -197,9 +197,10 @@ class Solver:
     def profile(self, enable=True):
         self._check(_lib.tddft_profile(self.h, int(bool(enable))), allow_noconv=False)
 
-    def profile_read(self):
+    def profile_read(self, which=0):
+        """which 0: the tcgen05 K1 contraction; 1: the SIMT one."""
         n, ms, fl = C.c_longlong(), C.c_double(), C.c_double()
-        self._check(_lib.tddft_profile_read(self.h, 0, C.byref(n), C.byref(ms), C.byref(fl)),
+        self._check(_lib.tddft_profile_read(self.h, which, C.byref(n), C.byref(ms), C.byref(fl)),
                     allow_noconv=False)
         return dict(launches=n.value, ms=ms.value, flops=fl.value)
 

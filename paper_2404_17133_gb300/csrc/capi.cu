@@ -560,7 +560,8 @@ tddft_status tddft_profile(tddft_ctx* ctx, int enable) {
   TD_API_BODY(ctx, {
     std::lock_guard<std::mutex> run(c->run_mu);
     c->prof.reset();
-    c->prof.on = enable != 0;
+    c->prof_simt.reset();
+    c->prof.on = c->prof_simt.on = enable != 0;
     return TDDFT_OK;
   })
 }
@@ -568,12 +569,13 @@ tddft_status tddft_profile(tddft_ctx* ctx, int enable) {
 tddft_status tddft_profile_read(const tddft_ctx* ctx, int which, long long* launches, double* ms,
                                 double* flops) {
   TD_API_BODY(const_cast<tddft_ctx*>(ctx), {
-    TD_REQUIRE(which == 0, TDDFT_ERR_ARG, "which must be 0");
+    TD_REQUIRE(which == 0 || which == 1, TDDFT_ERR_ARG, "which must be 0 or 1");
     std::lock_guard<std::mutex> run(c->run_mu);
-    c->prof.collect();
-    if (launches) *launches = c->prof.launches;
-    if (ms) *ms = c->prof.ms;
-    if (flops) *flops = c->prof.flops;
+    KernelProfile& kp = which == 0 ? c->prof : c->prof_simt;
+    kp.collect();
+    if (launches) *launches = kp.launches;
+    if (ms) *ms = kp.ms;
+    if (flops) *flops = kp.flops;
     return TDDFT_OK;
   })
 }

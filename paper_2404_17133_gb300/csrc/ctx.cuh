@@ -53,7 +53,8 @@ struct OpDims {
   int no = 0, nv = 0, ov = 0;
   double a_x = 0.0, c_J = 2.0;
   const double* delta = nullptr;  // device [ov]
-  KernelProfile* prof = nullptr;  // optional timing of the K1 contraction
+  KernelProfile* prof = nullptr;       // optional timing of the K1 contraction (tcgen05)
+  KernelProfile* prof_simt = nullptr;  // the same for the SIMT contraction
   int* tc_err = nullptr;          // device flag set by the tensor-core kernel
 };
 
@@ -108,13 +109,14 @@ struct Ctx {
   std::thread worker;
   bool stopping = false;
   std::mutex run_mu;  // one solve at a time on the context's stream
-  KernelProfile prof;
+  KernelProfile prof, prof_simt;
 
   OpDims dims() const {
     OpDims d;
     d.no = no; d.nv = nv; d.ov = ov; d.a_x = a_x; d.c_J = c_J;
     d.delta = delta.as<double>();
     d.prof = const_cast<KernelProfile*>(&prof);
+    d.prof_simt = const_cast<KernelProfile*>(&prof_simt);
     d.tc_err = tc_err.as<int>();
     return d;
   }

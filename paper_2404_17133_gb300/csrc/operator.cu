@@ -148,11 +148,10 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
                   f.Koo_hi + (size_t)p0 * no * nop, oo_lo, no, pn, nv, Zhi.as<__nv_bfloat16>(),
                   Zlo.as<__nv_bfloat16>(), d.tc_err, s);
         const bool timed = d.prof && d.prof->on && f.dt != DType::BF16;
-        if (timed) d.prof->begin(s);
         tc_contract(Zhi.as<__nv_bfloat16>(), Zlo.as<__nv_bfloat16>(), Mz, pn, nv,
                     f.Kvv_hi + (size_t)p0 * nv * nvp, split ? f.Kvv_lo + (size_t)p0 * nv * nvp : nullptr,
-                    nv, K1b.as<float>(), p0 > 0, d.tc_err, s);
-        if (timed) d.prof->end(s, 2.0 * Mz * (double)nv * (double)pn * nv);
+                    nv, K1b.as<float>(), p0 > 0, d.tc_err, s, timed ? d.prof : nullptr,
+                    2.0 * Mz * (double)nv * (double)pn * nv);
         if (need_k2) {
           const __nv_bfloat16* ov_lo = split ? f.Kovp_lo + (size_t)p0 * no * nvp : nullptr;
           tc_stage1(Xs_hi.as<__nv_bfloat16>(), Xs_lo.as<__nv_bfloat16>(), m * no, nv,
@@ -182,8 +181,8 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
         gemm(z, s);
         const int Mz = m * no;
         const long long Kz = (long long)pn * nv;
-        const bool timed = d.prof && d.prof->on && f.dt != DType::BF16;
-        if (timed) d.prof->begin(s);
+        const bool timed = d.prof_simt && d.prof_simt->on && f.dt != DType::BF16;
+        if (timed) d.prof_simt->begin(s);
         GemmDesc k;
         k.acc64 = f64;
         k.M = Mz; k.N = nv; k.K = (int)Kz;
@@ -192,7 +191,7 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
         k.C = K1b.p; k.tc = tw; k.scm = nv; k.scn = 1;
         k.beta = (p0 > 0) ? 1.0 : 0.0;
         gemm_splitk(k, auto_splits(k.M, k.N, k.K), s);
-        if (timed) d.prof->end(s, 2.0 * Mz * (double)nv * (double)Kz);
+        if (timed) d.prof_simt->end(s, 2.0 * Mz * (double)nv * (double)Kz);
         if (need_k2) {
           // Q[n][i][P][j] = sum_b Kov[P][i][b] X[n][j][b]
           GemmDesc q;

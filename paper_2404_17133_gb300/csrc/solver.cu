@@ -140,10 +140,10 @@ void gram(const T* A, int ka, const T* B, int kb, int ov, S* G, int ldg, cudaStr
   sk_gram<T>(A, ov, ka, B, ov, kb, ov, G, dt_of<S>(), ldg, 1.0, 0.0, s);
 }
 
-// a[r][col0 + j] = V[r] . Wn[j]  for r < N, j < k
-template <typename T>
-void proj_cols(const T* V, int N, const T* Wn, int k, int ov, T* a, int ld, int col0, cudaStream_t s) {
-  gram<T, T>(V, N, Wn, k, ov, a + col0, ld, s);
+// a[r][col0 + j] = V[r] . Wn[j]  for r < N, j < k  (a of type S)
+template <typename T, typename S>
+void proj_cols(const T* V, int N, const T* Wn, int k, int ov, S* a, int ld, int col0, cudaStream_t s) {
+  gram<T, S>(V, N, Wn, k, ov, a + col0, ld, s);
 }
 
 // out[j] = alpha * sum_r coef[j][r] V[r] + beta * out[j]   (coef compact [k][N], type S)
@@ -221,6 +221,28 @@ void orth_append_async(T* V, int N, T* cand, int nc, int ov, int* keep, int* cou
   ScopedPhase ph(PH_ORTH, s);
   orth_block<T>(V, N, cand, nc, ov, keep, s);
   compact_rows<T>(cand, keep, nc, ov, V + (size_t)N * ov, count, s);
+}
+
+// Orthonormalise `cand` against V (N rows) and each other and compact the
+// survivors, in order, into `out` without appending them; returns their number
+// (at most ov - N).  Used before a thick restart, so that the new directions
+// are free of the whole subspace that produced them.
+template <typename T>
+int orth_compact(const T* V, int N, T* cand, int nc, int ov, T* out, cudaStream_t s) {
+  if (nc <= 0) return 0;
+  ScopedPhase ph(PH_ORTH, s);
+  DevBuf keep(nc * 4, s);
+  orth_block<T>(V, N, cand, nc, ov, keep.as<int>(), s);
+  std::vector<int> kh = d2h(keep.as<int>(), nc, s);
+  std::vector<int> idx;
+  for (int j = 0; j < nc && N + (int)idx.size() < ov; ++j)
+    if (kh[j]) idx.push_back(j);
+  if (!idx.empty()) {
+    DevBuf di(idx.size() * 4, s);
+    h2d(di.as<int>(), idx, s);
+    gather_rows<T>(cand, di.as<int>(), (int)idx.size(), ov, out, s);
+  }
+  return (int)idx.size();
 }
 
 void check_finite_host(const std::vector<double>& v, const char* what) {
@@ -321,7 +343,15 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
     pre(Ru.as<double>(), omu.as<double>(), omh, nu, cand.as<double>());                   // Eq. precondition
     TD_CUDA(cudaStreamSynchronize(s));
     cnt.t_pre += since(tp);
+    double* cnew = cand.as<double>();
+    int nnew = nu;
+    DevBuf cfree;
     if (N + nu > cap) {
+      // the new directions, orthonormalised against the full subspace first
+      cfree = DevBuf((size_t)nu * ov * 8, s);
+      nnew = orth_compact<double>(Vp, N, cand.as<double>(), nu, ov, cfree.as<double>(), s);
+      if (nnew == 0) break;
+      cnew = cfree.as<double>();
       // thick restart: current Ritz vectors + those of the previous iteration
       TD_CUDA(cudaMemcpyAsync(Vp, X.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
       TD_CUDA(cudaMemcpyAsync(Wp, AX.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
@@ -337,7 +367,7 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
     }
     TD_CUDA(cudaMemcpyAsync(Xprev.p, X.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
     have_prev = true;
-    int nacc = orth_append(Vp, N, cand.as<double>(), nu, ov, s);
+    int nacc = orth_append(Vp, N, cnew, nnew, ov, s);
     if (nacc == 0) break;
     mv(N, nacc);
     N += nacc;
@@ -354,7 +384,7 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
 // matrices have the vectors' type T: FP64 in the outer solves, FP32 in the
 // MIXED inner solves (which stop at a relative residual of about 1e-2).
 
-template <typename T>
+template <typename T, typename S = T>
 struct PairedSpace {
   int ov, cap;
   cudaStream_t s;
@@ -366,11 +396,11 @@ struct PairedSpace {
     V = DevBuf((size_t)(cap + slack) * ov * sizeof(T), s);
     P = DevBuf((size_t)cap * ov * sizeof(T), s);
     M = DevBuf((size_t)cap * ov * sizeof(T), s);
-    ap = DevBuf((size_t)cap * cap * sizeof(T), s);
-    am = DevBuf((size_t)cap * cap * sizeof(T), s);
-    L = DevBuf((size_t)cap * cap * sizeof(T), s);
-    tmp = DevBuf((size_t)cap * cap * sizeof(T), s);
-    H = DevBuf((size_t)cap * cap * sizeof(T), s);
+    ap = DevBuf((size_t)cap * cap * sizeof(S), s);
+    am = DevBuf((size_t)cap * cap * sizeof(S), s);
+    L = DevBuf((size_t)cap * cap * sizeof(S), s);
+    tmp = DevBuf((size_t)cap * cap * sizeof(S), s);
+    H = DevBuf((size_t)cap * cap * sizeof(S), s);
     lam32 = DevBuf(cap * 4, s);
     vec32 = DevBuf((size_t)cap * cap * 4, s);
     info = DevBuf(4, s);
@@ -382,26 +412,26 @@ struct PairedSpace {
   // eigenproblem, its FP32 decomposition)
   void update(bool eig) {
     ScopedPhase ph(PH_PROJ, s);
-    proj_cols<T>(v(), N, p() + (size_t)n_old * ov, n_new, ov, ap.as<T>(), cap, n_old, s);
-    proj_cols<T>(v(), N, m() + (size_t)n_old * ov, n_new, ov, am.as<T>(), cap, n_old, s);
-    sym_fill<T>(ap.as<T>(), cap, n_old, n_new, s);
-    sym_fill<T>(am.as<T>(), cap, n_old, n_new, s);
+    proj_cols<T, S>(v(), N, p() + (size_t)n_old * ov, n_new, ov, ap.as<S>(), cap, n_old, s);
+    proj_cols<T, S>(v(), N, m() + (size_t)n_old * ov, n_new, ov, am.as<S>(), cap, n_old, s);
+    sym_fill<S>(ap.as<S>(), cap, n_old, n_new, s);
+    sym_fill<S>(am.as<S>(), cap, n_old, n_new, s);
     // a- = L L^T: the leading n_old rows of L are kept (the basis grows by
     // bordering); the new rows of a- are copied in and factored
-    TD_CUDA(cudaMemcpy2DAsync(L.as<T>() + (size_t)n_old * cap, cap * sizeof(T),
-                              am.as<T>() + (size_t)n_old * cap, cap * sizeof(T), N * sizeof(T), n_new,
+    TD_CUDA(cudaMemcpy2DAsync(L.as<S>() + (size_t)n_old * cap, cap * sizeof(S),
+                              am.as<S>() + (size_t)n_old * cap, cap * sizeof(S), N * sizeof(S), n_new,
                               cudaMemcpyDeviceToDevice, s));
     {
       ScopedPhase f(trace_level() >= 3 ? PH_CHOL : PH_N - 1, s);
-      cholesky_border<T>(L.as<T>(), cap, n_old, N, info.as<int>(), s);
+      cholesky_border<S>(L.as<S>(), cap, n_old, N, info.as<int>(), s);
     }
     {
       ScopedPhase f(trace_level() >= 3 ? PH_SMM : PH_N - 1, s);
       // tmp = a+ L ; H = L^T tmp
-      small_mm<T>(N, N, N, ap.as<T>(), cap, 1, L.as<T>(), cap, 1, tmp.as<T>(), cap, s);
-      small_mm<T>(N, N, N, L.as<T>(), 1, cap, tmp.as<T>(), cap, 1, H.as<T>(), cap, s);
+      small_mm<S>(N, N, N, ap.as<S>(), cap, 1, L.as<S>(), cap, 1, tmp.as<S>(), cap, s);
+      small_mm<S>(N, N, N, L.as<S>(), 1, cap, tmp.as<S>(), cap, 1, H.as<S>(), cap, s);
     }
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (sizeof(S) == 8) {
       if (eig) {
         ScopedPhase f(trace_level() >= 3 ? PH_EIG : PH_N - 1, s);
         eig32(H.as<double>(), cap, N, lam32.as<float>(), vec32.as<float>(), s);
@@ -434,7 +464,7 @@ struct PairedLinOut {
 // The small shifted systems are solved by LU per shift in the vectors' type:
 // FP64 for the outer polarizability and PLAIN solves, FP32 for the MIXED inner
 // solves.
-template <typename T>
+template <typename T, typename S = T>
 PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre, const T* gp,
                            const T* gm, const std::vector<double>& shifts, int nr, T* init, int ni,
                            double tol, int max_iter, int cap, bool exact_op,
@@ -447,7 +477,7 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
   // Inner solves (ris operator) select, precondition and orthonormalise the new
   // directions on the device and read back one status block per iteration.
   const bool dev_select = !exact_op;
-  PairedSpace<T> sp(ov, cap, s, dev_select ? 2 * nr : 0);
+  PairedSpace<T, S> sp(ov, cap, s, dev_select ? 2 * nr : 0);
   DevBuf sh(nr * 8, s), sig2(nr * 8, s);
   std::vector<double> s2(nr);
   for (int r = 0; r < nr; ++r) s2[r] = shifts[r] * shifts[r];
@@ -455,7 +485,7 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
   h2d(sig2.as<double>(), s2, s);
   // h+ and h- (and u, w coefficients) share one buffer so that, when g- follows
   // g+ in memory, one Gram product forms both
-  DevBuf hpm((size_t)2 * nr * cap * es, s), ucw((size_t)2 * nr * cap * es, s);
+  DevBuf hpm((size_t)2 * nr * cap * sizeof(S), s), ucw((size_t)2 * nr * cap * sizeof(S), s);
   DevBuf Rp((size_t)nr * ov * es, s), Rm((size_t)nr * ov * es, s), PU((size_t)nr * ov * es, s),
       MW((size_t)nr * ov * es, s);
   DevBuf gn(nr * 8, s), gn2(nr * 8, s), rn1(nr * 8, s), rn2(nr * 8, s);
@@ -511,35 +541,35 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
     sp.update(false);
     if (!dev_select) sp.check_definite();
     const int N = sp.N;
-    T* Lp = sp.L.template as<T>();
+    S* Lp = sp.L.template as<S>();
     ScopedPhase ph_small(PH_SMALL, s);
     // h+ = V g+ , h- = V g-   ([nr][N] each, h- right after h+)
-    T* hp = hpm.as<T>();
-    T* hm = hp + (size_t)nr * N;
+    S* hp = hpm.as<S>();
+    S* hm = hp + (size_t)nr * N;
     if (gm == gp + (size_t)nr * ov) {
-      gram<T, T>(gp, 2 * nr, sp.v(), N, ov, hp, N, s);
+      gram<T, S>(gp, 2 * nr, sp.v(), N, ov, hp, N, s);
     } else {
-      gram<T, T>(gp, nr, sp.v(), N, ov, hp, N, s);
-      if (gm) gram<T, T>(gm, nr, sp.v(), N, ov, hm, N, s);
+      gram<T, S>(gp, nr, sp.v(), N, ov, hp, N, s);
+      if (gm) gram<T, S>(gm, nr, sp.v(), N, ov, hm, N, s);
     }
     // per system: z- = L^-1 h-, (H - s^2) u~ = L^T h+ + s z-, u = L u~, w = L^-T (z- + s u~)
-    T* uc = ucw.as<T>();
-    T* wc = uc + (size_t)nr * N;
+    S* uc = ucw.as<S>();
+    S* wc = uc + (size_t)nr * N;
     {
       ScopedPhase f(trace_level() >= 3 ? PH_LU : PH_N - 1, s);
-      paired_small_solve<T>(Lp, sp.H.template as<T>(), cap, N, hp, gm ? hm : nullptr, sh.as<double>(), nr,
+      paired_small_solve<S>(Lp, sp.H.template as<S>(), cap, N, hp, gm ? hm : nullptr, sh.as<double>(), nr,
                             uc, wc, s);
     }
     ph_small.stop();
     ScopedPhase ph_vec(PH_VEC, s);
     if (Wout == Uout + (size_t)nr * ov) {
-      combo<T, T>(uc, 2 * nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
+      combo<T, S>(uc, 2 * nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
     } else {
-      combo<T, T>(uc, nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
-      combo<T, T>(wc, nr, N, sp.v(), ov, Wout, 1.0, 0.0, s);
+      combo<T, S>(uc, nr, N, sp.v(), ov, Uout, 1.0, 0.0, s);
+      combo<T, S>(wc, nr, N, sp.v(), ov, Wout, 1.0, 0.0, s);
     }
-    combo<T, T>(uc, nr, N, sp.p(), ov, PU.as<T>(), 1.0, 0.0, s);
-    combo<T, T>(wc, nr, N, sp.m(), ov, MW.as<T>(), 1.0, 0.0, s);
+    combo<T, S>(uc, nr, N, sp.p(), ov, PU.as<T>(), 1.0, 0.0, s);
+    combo<T, S>(wc, nr, N, sp.m(), ov, MW.as<T>(), 1.0, 0.0, s);
     resid_paired<T>(Uout, Wout, PU.as<T>(), MW.as<T>(), sh.as<double>(), gp, gm, nr, ov,
                     Rp.as<T>(), Rm.as<T>(), s);
     row_sumsq<T>(Rp.as<T>(), ov, nr, ov, rn1p, s);
@@ -735,7 +765,15 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
         cand.as<double>() + (size_t)nu * ov);
     TD_CUDA(cudaStreamSynchronize(s));
     cnt.t_pre += since(tp);
+    double* cnew = cand.as<double>();
+    int nnew = 2 * nu;
+    DevBuf cfree;
     if (sp.N + 2 * nu > cap) {
+      // the new directions, orthonormalised against the full subspace first
+      cfree = DevBuf((size_t)2 * nu * ov * 8, s);
+      nnew = orth_compact<double>(sp.v(), sp.N, cand.as<double>(), 2 * nu, ov, cfree.as<double>(), s);
+      if (nnew == 0) break;
+      cnew = cfree.as<double>();
       // thick restart: X+Y and X-Y of the wanted roots, now and one iteration ago
       const int nprev = (have_prev && 4 * kk <= 112) ? 2 * kk : 0;
       TD_CUDA(cudaMemcpyAsync(rst.p, U.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
@@ -756,7 +794,7 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
     TD_CUDA(cudaMemcpyAsync(Uprev.p, U.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
     TD_CUDA(cudaMemcpyAsync(Wprev.p, W.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
     have_prev = true;
-    int nacc = orth_append(sp.v(), sp.N, cand.as<double>(), 2 * nu, ov, s);
+    int nacc = orth_append(sp.v(), sp.N, cnew, nnew, ov, s);
     if (nacc == 0) break;
     mv(sp.N, nacc);
     sp.n_new += nacc;
@@ -776,7 +814,7 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
 // expansion, stopped at |res_n| <= tol |R_n| or max_iter iterations.  New
 // directions are selected, preconditioned and orthonormalised on the device;
 // the host reads one status block (residual norms, accepted count) per iteration.
-template <typename T>
+template <typename T, typename S = T>
 void inner_tda(int ov, const TdaOpT<T>& Top, const double* delta, const T* R, const double* sh,
                const std::vector<double>& shh, int nu, double tol, int max_iter,
                Counters& cnt, T* out, cudaStream_t s) {
@@ -784,8 +822,8 @@ void inner_tda(int ov, const TdaOpT<T>& Top, const double* delta, const T* R, co
   InnerScope inner_scope;
   const int cap = kSmallMax;
   constexpr size_t es = sizeof(T);
-  DevBuf S((size_t)(cap + nu) * ov * es, s), TS((size_t)cap * ov * es, s), t((size_t)cap * cap * es, s);
-  DevBuf h((size_t)nu * cap * es, s), y((size_t)nu * cap * es, s);
+  DevBuf Sb((size_t)(cap + nu) * ov * es, s), TS((size_t)cap * ov * es, s), t((size_t)cap * cap * sizeof(S), s);
+  DevBuf h((size_t)nu * cap * sizeof(S), s), y((size_t)nu * cap * sizeof(S), s);
   DevBuf Tv((size_t)nu * ov * es, s), res((size_t)nu * ov * es, s), r0(nu * 8, s);
   DevBuf cand((size_t)nu * ov * es, s), keep(nu * 4, s), stat((size_t)nu * 8 + 8, s);
   double* rn = stat.as<double>();
@@ -795,31 +833,31 @@ void inner_tda(int ov, const TdaOpT<T>& Top, const double* delta, const T* R, co
   for (auto& v : r0h) v = v > 0 ? v : 1.0;
   h2d(r0.as<double>(), r0h, s);
   precond_tda<T>(R, sh, delta, nu, ov, cand.as<T>(), s);
-  int N = orth_append<T>(S.as<T>(), 0, cand.as<T>(), nu, ov, s);
+  int N = orth_append<T>(Sb.as<T>(), 0, cand.as<T>(), nu, ov, s);
   if (N == 0) { TD_CUDA(cudaMemsetAsync(out, 0, (size_t)nu * ov * es, s)); return; }
   {
     ScopedPhase ph(PH_RIS, s);
-    Top(S.as<T>(), N, TS.as<T>());
+    Top(Sb.as<T>(), N, TS.as<T>());
   }
   cnt.ris_mv += N;
   int n_old = 0, n_new = N;
   for (int it = 0; it < max_iter; ++it) {
-    proj_cols<T>(S.as<T>(), N, TS.as<T>() + (size_t)n_old * ov, n_new, ov, t.as<T>(), cap, n_old, s);
-    sym_fill<T>(t.as<T>(), cap, n_old, n_new, s);
-    gram<T, T>(R, nu, S.as<T>(), N, ov, h.as<T>(), N, s);             // h[n][r] = R_n . S_r
+    proj_cols<T, S>(Sb.as<T>(), N, TS.as<T>() + (size_t)n_old * ov, n_new, ov, t.as<S>(), cap, n_old, s);
+    sym_fill<S>(t.as<S>(), cap, n_old, n_new, s);
+    gram<T, S>(R, nu, Sb.as<T>(), N, ov, h.as<S>(), N, s);             // h[n][r] = R_n . S_r
     {
       ScopedPhase ph(PH_SMALL, s);
-      lu_shift_solve<T>(t.as<T>(), cap, N, sh, nu, h.as<T>(), y.as<T>(), s);
+      lu_shift_solve<S>(t.as<S>(), cap, N, sh, nu, h.as<S>(), y.as<S>(), s);
     }
-    combo<T, T>(y.as<T>(), nu, N, S.as<T>(), ov, out, 1.0, 0.0, s);
-    combo<T, T>(y.as<T>(), nu, N, TS.as<T>(), ov, Tv.as<T>(), 1.0, 0.0, s);
+    combo<T, S>(y.as<S>(), nu, N, Sb.as<T>(), ov, out, 1.0, 0.0, s);
+    combo<T, S>(y.as<S>(), nu, N, TS.as<T>(), ov, Tv.as<T>(), 1.0, 0.0, s);
     resid_shift<T>(Tv.as<T>(), out, sh, R, nu, ov, res.as<T>(), s);
     row_sumsq<T>(res.as<T>(), ov, nu, ov, rn, s);
     const bool last = it == max_iter - 1;
     if (!last) {
       precond_tda<T>(res.as<T>(), sh, delta, nu, ov, cand.as<T>(), s);
       zero_converged<T>(cand.as<T>(), nu, nu, ov, rn, nullptr, r0.as<double>(), tol, s);
-      orth_append_async<T>(S.as<T>(), N, cand.as<T>(), nu, ov, keep.as<int>(), st_count, s);
+      orth_append_async<T>(Sb.as<T>(), N, cand.as<T>(), nu, ov, keep.as<int>(), st_count, s);
     }
     std::vector<double> blk = d2h(stat.as<double>(), (size_t)nu + 1, s);
     int m = 0;
@@ -833,7 +871,7 @@ void inner_tda(int ov, const TdaOpT<T>& Top, const double* delta, const T* R, co
     if (nacc == 0) break;
     {
       ScopedPhase ph(PH_RIS, s);
-      Top(S.as<T>() + (size_t)N * ov, nacc, TS.as<T>() + (size_t)N * ov);
+      Top(Sb.as<T>() + (size_t)N * ov, nacc, TS.as<T>() + (size_t)N * ov);
     }
     cnt.ris_mv += nacc;
     n_old = N;
@@ -937,8 +975,8 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
       const long long n = (long long)nu * ov;
       DevBuf R32(n * 4, s), o32(n * 4, s);
       convert(R, DType::F64, R32.p, DType::F32, n, s);
-      inner_tda<float>(ov, T32, c.delta.as<double>(), R32.as<float>(), sh, shh, nu, p.inner_tol,
-                       p.inner_max_iter, cnt, o32.as<float>(), s);
+      inner_tda<float, float>(ov, T32, c.delta.as<double>(), R32.as<float>(), sh, shh, nu, p.inner_tol,
+                              p.inner_max_iter, cnt, o32.as<float>(), s);
       convert(o32.p, DType::F32, out, DType::F64, n, s);
     } else {
       inner_tda<double>(ov, T, c.delta.as<double>(), R, sh, shh, nu, p.inner_tol, p.inner_max_iter,
@@ -1017,7 +1055,7 @@ void rid_paired(int ov, const Plan& p, const PairOp& T, const PairPre& diag, con
     convert(gm, DType::F64, g32.as<float>() + n, DType::F32, n, s);
     precond_paired<float>(g32.as<float>(), g32.as<float>() + n, sh, dl, nu, ov, init.as<float>(),
                           init.as<float>() + n, s);
-    paired_linear<float>(ov, T32, diag32, g32.as<float>(), g32.as<float>() + n, shh, nu, init.as<float>(),
+    paired_linear<float, float>(ov, T32, diag32, g32.as<float>(), g32.as<float>() + n, shh, nu, init.as<float>(),
                          2 * nu, p.inner_tol, p.inner_max_iter, kSmallMax, false, cnt,
                          uw.as<float>(), uw.as<float>() + n, s);
     convert(uw.p, DType::F32, u, DType::F64, n, s);
@@ -1171,7 +1209,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
       convert(b.p, DType::F64, b32.p, DType::F32, n, s);
       precond_paired<float>(b32.as<float>(), nullptr, shd.as<double>(), dl, nr, ov, d0.as<float>(),
                             d0.as<float>() + n, s);
-      paired_linear<float>(ov, T32, diag32, b32.as<float>(), nullptr, sh, nr, d0.as<float>(), 2 * nr,
+      paired_linear<float, float>(ov, T32, diag32, b32.as<float>(), nullptr, sh, nr, d0.as<float>(), 2 * nr,
                            p.guess_tol, p.max_iter, kSmallMax, false, cnt, uw.as<float>(),
                            uw.as<float>() + n, s);
       convert(uw.p, DType::F32, iu, DType::F64, 2 * n, s);

@@ -17,9 +17,9 @@
 //          stored transposed ([P][a][j])
 //   K loop: for each P in the CTA's split range, k-blocks of 64 (128 bytes, one
 //          128B-swizzle atom); TMA zero-fills k >= Kin, n >= N and rows >= M.
-// CTA = 128 x 128 output tile, 6 warps: warp 0 issues TMA loads, warp 1 owns the
+// CTA = 128 x 256 output tile, 6 warps: warp 0 issues TMA loads, warp 1 owns the
 // tensor memory and one elected lane issues tcgen05.mma, warps 2-5 drain the
-// FP32 accumulator from TMEM.  A 3-stage mbarrier ring connects producer and MMA;
+// FP32 accumulator from TMEM.  A 2-stage (hi+lo) or 4-stage mbarrier ring connects producer and MMA;
 // tcgen05.commit releases a stage when its MMAs have read it.
 // Split-K: blockIdx.z takes a contiguous range of (P, a-block) steps and writes
 // its own FP32 partial tile; a fixed-order reduction sums the partials.
@@ -28,6 +28,7 @@
 // code in `err` and leaves the loop; the host turns it into TDDFT_ERR_CUDA.
 #include <cuda.h>
 
+#include "ctx.cuh"
 #include "tc_gemm.cuh"
 #include "vecops.cuh"
 
@@ -36,13 +37,13 @@ namespace tddft {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 128;
+constexpr int BN = 256;                      // 128 x 256 MMA tiles (full tcgen05 rate per CTA)
 constexpr int BK = 64;                       // bf16 elements per 128-byte row
 constexpr int A_BYTES = BM * BK * 2;          // 16 KB per hi or lo tile
 constexpr int B_BYTES = BN * BK * 2;
 template <bool SPLIT> struct Cfg {
   static constexpr int STAGE_BYTES = SPLIT ? 2 * A_BYTES + 2 * B_BYTES : A_BYTES + B_BYTES;
-  static constexpr int STAGES = SPLIT ? 3 : 6;
+  static constexpr int STAGES = SPLIT ? 2 : 4;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 };
 constexpr int THREADS = 192;
@@ -230,10 +231,17 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
         for (int j = 0; j < 16; ++j) v[j] = 0u;
       }
       if (row < p.M) {
+        const int col0 = n0 + c;
+        float* o = out + (size_t)row * p.N + col0;
+        if ((p.N & 3) == 0 && col0 + 16 <= p.N) {   // 16-byte aligned: four vector stores
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c + j;
-          if (col < p.N) out[(size_t)row * p.N + col] = __uint_as_float(v[j]);
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4*>(o + j) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                            __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (col0 + j < p.N) o[j] = __uint_as_float(v[j]);
         }
       }
     }
@@ -516,7 +524,7 @@ void tc_transpose_split(const void* src, DType ts, int rows, int n1, int n2, __n
 
 void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int pn, int Kin,
                  const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, float* out,
-                 bool accumulate, int* err, cudaStream_t s) {
+                 bool accumulate, int* err, cudaStream_t s, KernelProfile* prof, double prof_flops) {
   if (M <= 0 || pn <= 0 || N <= 0) return;
   const bool split = (Alo != nullptr);
   TD_REQUIRE(split == (Blo != nullptr), TDDFT_ERR_ARG, "tc_contract: hi/lo operands mismatch");
@@ -543,13 +551,14 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
   DevBuf part((size_t)splits * M * N * 4, s);
   Params p{M, N, nab, total, per, part.as<float>(), err};
   dim3 grid(nt, mt, splits);
-  if (split) {
-    ensure_smem((const void*)k1_tc_kernel<true>, Cfg<true>::SMEM_BYTES);
+  if (split) ensure_smem((const void*)k1_tc_kernel<true>, Cfg<true>::SMEM_BYTES);
+  else ensure_smem((const void*)k1_tc_kernel<false>, Cfg<false>::SMEM_BYTES);
+  if (prof) prof->begin(s);
+  if (split)
     k1_tc_kernel<true><<<grid, THREADS, Cfg<true>::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, p);
-  } else {
-    ensure_smem((const void*)k1_tc_kernel<false>, Cfg<false>::SMEM_BYTES);
+  else
     k1_tc_kernel<false><<<grid, THREADS, Cfg<false>::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, p);
-  }
+  if (prof) prof->end(s, prof_flops);
   count_launch();
   TD_LAUNCH_CHECK();
   const long long MN = (long long)M * N;
