@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel-breakdown", action="store_true",
+                    help="run one warm step under the CUDA activity profiler and print per-kernel totals")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="steps of the plain FP64 form timed for the mixed-vs-plain comparison (0: skip)")
     ap.add_argument("--precond", default="rid", choices=["rid", "diag"])
@@ -223,6 +225,10 @@ def our_arm(args, rank, world, local):
         apply_only(args, api, solver, p, tc, stream)
         solver.close()
         return
+    if args.kernel_breakdown:
+        kernel_breakdown(solver, o_rpa, o_pol, mu, omegas)
+        solver.close()
+        return
 
     def step(s):
         a = s.solve_rpa(o_rpa, want_vectors=False)
@@ -378,6 +384,41 @@ def apply_only(args, api, solver, p, tc, stream):
         ms.append(e0.elapsed_time(e1))
     print(json.dumps({"apply_only": args.apply_only, "m": 2 * N_STATES, "ms": ms,
                       "workload": WORKLOAD, "tensor_cores": bool(tc)}), flush=True)
+
+
+def kernel_breakdown(solver, o_rpa, o_pol, mu, omegas):
+    """One warm step under the CUDA activity profiler (CUPTI): every kernel and
+    copy with its device time; printed as one JSON line."""
+    import collections
+    import re
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+
+    def step():
+        solver.solve_rpa(o_rpa, want_vectors=False)
+        solver.solve_polar(o_pol, mu, omegas)
+
+    step()
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        t0 = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    ev = [e for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA]
+    tot, cnt = collections.defaultdict(float), collections.Counter()
+    span0, span1 = float("inf"), 0.0
+    for e in ev:
+        nm = e.name.replace("(anonymous namespace)::", "").replace("void ", "").replace("tddft::", "")
+        nm = re.sub(r"\(.*", "", nm)
+        tot[nm] += e.time_range.elapsed_us()
+        cnt[nm] += 1
+        span0, span1 = min(span0, e.time_range.start), max(span1, e.time_range.end)
+    busy = sum(tot.values())
+    rows = [{"kernel": k, "launches": cnt[k], "ms": round(v / 1e3, 3), "share": round(v / busy, 4)}
+            for k, v in sorted(tot.items(), key=lambda x: -x[1])]
+    print(json.dumps({"kernel_breakdown": rows, "busy_ms": busy / 1e3, "span_ms": (span1 - span0) / 1e3,
+                      "wall_ms": wall * 1e3, "workload": WORKLOAD}), flush=True)
 
 
 def main():

@@ -173,14 +173,26 @@ class Operator:
     def tda(self, X):
         """A X with A = Delta + c_J (ia|jb) - a_x (ij|ab)  (Eq. TDA uses A alone)."""
         X, J, K1, _ = self._parts(X, False)
-        return self.d * X + self.c_J * J - self.a_x * K1
+        return tda_from_parts(self.d, X, J, K1, self.a_x, self.c_J)
 
     def apb_amb(self, X):
         """((A+B) X, (A-B) X) from Eq. hessian with f^xc = 0."""
         X, J, K1, K2 = self._parts(X, True)
-        apb = self.d * X + 2.0 * self.c_J * J - self.a_x * (K1 + K2)
-        amb = self.d * X + self.a_x * (K2 - K1)
-        return apb, amb
+        return pair_from_parts(self.d, X, J, K1, K2, self.a_x, self.c_J)
+
+
+def tda_from_parts(d, X, J, K1, a_x, c_J):
+    """A X = Delta X + c_J J(X) - a_x K1(X)  (Eq. hessian, A alone)."""
+    return d * X + c_J * J - a_x * K1
+
+
+def pair_from_parts(d, X, J, K1, K2, a_x, c_J):
+    """(A+B) X = Delta X + 2 c_J J - a_x (K1 + K2),  (A-B) X = Delta X + a_x (K2 - K1)
+    (Eq. hessian with f^xc = 0).  J, K1, K2 may be sums of P-slices: every term is
+    linear in the factors' outer products, so slices of P add up."""
+    apb = d * X + 2.0 * c_J * J - a_x * (K1 + K2)
+    amb = d * X + a_x * (K2 - K1)
+    return apb, amb
 
 
 def exact_operator(prob) -> Operator:

@@ -122,23 +122,24 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
     if (use_tc) {
       // Both contractions of K1 and of K2 on the tensor cores.  The trial block
       // enters twice: transposed per vector ([(n,a)][j]) for Z = L_oo X and as is
-      // ([(n,j)][b]) for Q = L_ov X^T; exact factors are hi + lo splits.
+      // ([(n,j)][b]) for Q = L_ov X^T, always as BF16 hi + lo (so Z and Q are
+      // too); exact factors are hi + lo splits as well (three products), the
+      // BF16 ris factors are used as they are (two products, exact with respect
+      // to the factors).
       const bool split = f.Kvv_lo != nullptr;
       const int nvp = tc_pad(nv), nop = tc_pad(no);
       const DType xt = x32 ? DType::F32 : DType::F64;
-      DevBuf Xt_hi((size_t)m * nv * nop * 2, s), Xt_lo, Xs_hi, Xs_lo;
-      if (split) Xt_lo = DevBuf((size_t)m * nv * nop * 2, s);
+      DevBuf Xt_hi((size_t)m * nv * nop * 2, s), Xt_lo((size_t)m * nv * nop * 2, s), Xs_hi, Xs_lo;
       tc_transpose_split(X, xt, m, no, nv, Xt_hi.as<__nv_bfloat16>(), Xt_lo.as<__nv_bfloat16>(), s);
       if (need_k2) {
         Xs_hi = DevBuf((size_t)m * no * nvp * 2, s);
-        if (split) Xs_lo = DevBuf((size_t)m * no * nvp * 2, s);
+        Xs_lo = DevBuf((size_t)m * no * nvp * 2, s);
         tc_pad_split(X, xt, (long long)m * no, nv, Xs_hi.as<__nv_bfloat16>(), Xs_lo.as<__nv_bfloat16>(), s);
       }
-      DevBuf Zhi((size_t)m * no * pc * nvp * 2, s), Zlo, Qhi, Qlo;
-      if (split) Zlo = DevBuf((size_t)m * no * pc * nvp * 2, s);
+      DevBuf Zhi((size_t)m * no * pc * nvp * 2, s), Zlo((size_t)m * no * pc * nvp * 2, s), Qhi, Qlo;
       if (need_k2) {
         Qhi = DevBuf((size_t)m * no * pc * nop * 2, s);
-        if (split) Qlo = DevBuf((size_t)m * no * pc * nop * 2, s);
+        Qlo = DevBuf((size_t)m * no * pc * nop * 2, s);
       }
       const int Mz = m * no;
       for (int p0 = 0; p0 < f.nK; p0 += pc) {

@@ -86,35 +86,41 @@ __device__ void jacobi_cta(T* A, T* Q, int n, int ld, double frob, int max_sweep
         pp[i] = p; qq[i] = q; cc[i] = c; ss[i] = s;
       }
       __syncthreads();
-      // A <- G^T A G, block by block
-      for (int idx = tid; idx < half * half; idx += nth) {
-        const int bi = idx / half, bj = idx - bi * half;
-        const T si = ss[bi], sj = ss[bj];
-        if (si == T(0) && sj == T(0)) continue;
-        const T ci = cc[bi], cj = cc[bj];
-        const int pi = pp[bi], qi = qq[bi], pj = pp[bj], qj = qq[bj];
-        const T x00 = A[pi * ld + pj], x01 = A[pi * ld + qj];
-        const T x10 = A[qi * ld + pj], x11 = A[qi * ld + qj];
-        // rows: R_i = [[c, -s], [s, c]]
-        const T y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
-        const T y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
-        // columns: times [[c, s], [-s, c]]
-        T z00 = cj * y00 - sj * y01, z01 = sj * y00 + cj * y01;
-        T z10 = cj * y10 - sj * y11, z11 = sj * y10 + cj * y11;
-        if (bi == bj) { z01 = T(0); z10 = T(0); }   // the rotation annihilates a_pq
-        A[pi * ld + pj] = z00; A[pi * ld + qj] = z01;
-        A[qi * ld + pj] = z10; A[qi * ld + qj] = z11;
+      // A <- G^T A G, block by block: warp w takes the row pairs w, w + nw, ...,
+      // its lanes the column pairs (no index division in the loop)
+      const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+      for (int bi = warp; bi < half; bi += nw) {
+        const T si = ss[bi], ci = cc[bi];
+        T* rp = A + pp[bi] * ld;
+        T* rq = A + qq[bi] * ld;
+        for (int bj = lane; bj < half; bj += 32) {
+          const T sj = ss[bj];
+          if (si == T(0) && sj == T(0)) continue;
+          const T cj = cc[bj];
+          const int pj = pp[bj], qj = qq[bj];
+          const T x00 = rp[pj], x01 = rp[qj], x10 = rq[pj], x11 = rq[qj];
+          // rows: R_i = [[c, -s], [s, c]]
+          const T y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
+          const T y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
+          // columns: times [[c, s], [-s, c]]
+          T z00 = cj * y00 - sj * y01, z01 = sj * y00 + cj * y01;
+          T z10 = cj * y10 - sj * y11, z11 = sj * y10 + cj * y11;
+          if (bi == bj) { z01 = T(0); z10 = T(0); }   // the rotation annihilates a_pq
+          rp[pj] = z00; rp[qj] = z01;
+          rq[pj] = z10; rq[qj] = z11;
+        }
       }
-      // Q <- Q G (columns p_j, q_j of every row)
-      for (int idx = tid; idx < half * NP; idx += nth) {
-        const int bj = idx / NP, row = idx - bj * NP;
+      // Q <- Q G (columns p_j, q_j of every row): warp per column pair, lanes over rows
+      for (int bj = warp; bj < half; bj += nw) {
         const T sj = ss[bj];
         if (sj == T(0)) continue;
         const T cj = cc[bj];
         const int pj = pp[bj], qj = qq[bj];
-        const T qp = Q[row * ld + pj], qv = Q[row * ld + qj];
-        Q[row * ld + pj] = cj * qp - sj * qv;
-        Q[row * ld + qj] = sj * qp + cj * qv;
+        for (int row = lane; row < NP; row += 32) {
+          const T qp = Q[row * ld + pj], qv = Q[row * ld + qj];
+          Q[row * ld + pj] = cj * qp - sj * qv;
+          Q[row * ld + qj] = sj * qp + cj * qv;
+        }
       }
       __syncthreads();
     }

@@ -962,7 +962,7 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     apply_operator(dims, Fx, Xi, m, OpMode::TDA, out, nullptr, p.tc, s);
   };
   TdaOp T = [&](const double* Xi, int m, double* out) {
-    apply_operator(dims, Fr, Xi, m, OpMode::TDA, out, nullptr, false, s);
+    apply_operator(dims, Fr, Xi, m, OpMode::TDA, out, nullptr, p.tc, s);
   };
   TdaPre diag = [&](const double* R, const double* sh, const std::vector<double>&, int nu, double* out) {
     precond_tda(R, sh, c.delta.as<double>(), nu, ov, out, s);
@@ -1079,7 +1079,7 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
   Counters cnt;
   const OpDims dims = c.dims();
   PairOp A = make_pair_op(dims, c.exact(o.precision), p.tc, s);
-  PairOp T = make_pair_op(dims, c.ris(o.precision), false, s);
+  PairOp T = make_pair_op(dims, c.ris(o.precision), p.tc, s);
   const double* dl = c.delta.as<double>();
   PairPre diag = [&](const double* gp, const double* gm, const double* sh, const std::vector<double>&,
                      int nu, double* u, double* w) { precond_paired(gp, gm, sh, dl, nu, ov, u, w, s); };
@@ -1168,7 +1168,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
   Counters cnt;
   const OpDims dims = c.dims();
   PairOp A = make_pair_op(dims, c.exact(o.precision), p.tc, s);
-  PairOp T = make_pair_op(dims, c.ris(o.precision), false, s);
+  PairOp T = make_pair_op(dims, c.ris(o.precision), p.tc, s);
   const double* dl = c.delta.as<double>();
   const bool dev = o.outputs_on_device != 0;
   // right-hand sides 2 mu for every (omega_f, mu_u): row f*n_dip + u

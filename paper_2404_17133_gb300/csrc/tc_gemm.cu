@@ -41,9 +41,16 @@ constexpr int BN = 256;                      // 128 x 256 MMA tiles (full tcgen0
 constexpr int BK = 64;                       // bf16 elements per 128-byte row
 constexpr int A_BYTES = BM * BK * 2;          // 16 KB per hi or lo tile
 constexpr int B_BYTES = BN * BK * 2;
-template <bool SPLIT> struct Cfg {
-  static constexpr int STAGE_BYTES = SPLIT ? 2 * A_BYTES + 2 * B_BYTES : A_BYTES + B_BYTES;
-  static constexpr int STAGES = SPLIT ? 2 : 4;
+// Operand split modes: SINGLE = one BF16 product; BOTH = A and B as hi + lo
+// (hi*hi + hi*lo + lo*hi); ASPLIT = A as hi + lo, B a plain BF16 operand
+// (hi*B + lo*B: exact with respect to B, e.g. FP32 vectors against BF16 ris factors).
+enum SplitMode : int { SINGLE = 0, BOTH = 1, ASPLIT = 2 };
+__host__ __device__ constexpr bool a_split(int m) { return m != SINGLE; }
+__host__ __device__ constexpr bool b_split(int m) { return m == BOTH; }
+
+template <int MODE> struct Cfg {
+  static constexpr int STAGE_BYTES = (a_split(MODE) ? 2 : 1) * A_BYTES + (b_split(MODE) ? 2 : 1) * B_BYTES;
+  static constexpr int STAGES = MODE == SINGLE ? 4 : (MODE == ASPLIT ? 3 : 2);   // ~192 KB ring
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 };
 constexpr int THREADS = 192;
@@ -121,14 +128,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-template <bool SPLIT>
+template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
 k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
              const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
              Params p) {
-  constexpr int STAGES = Cfg<SPLIT>::STAGES;
-  constexpr int STAGE_BYTES = Cfg<SPLIT>::STAGE_BYTES;
-  constexpr int B_OFF = SPLIT ? 2 * A_BYTES : A_BYTES;   // first B tile in a stage
+  constexpr int STAGES = Cfg<MODE>::STAGES;
+  constexpr int STAGE_BYTES = Cfg<MODE>::STAGE_BYTES;
+  constexpr int B_OFF = a_split(MODE) ? 2 * A_BYTES : A_BYTES;   // first B tile in a stage
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -170,10 +177,8 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       mbar_expect_tx(&full[s], STAGE_BYTES);
       tma_load_3d(st, &mA_hi, &full[s], a0, P, m0);
       tma_load_3d(st + B_OFF, &mB_hi, &full[s], a0, n0, P);
-      if (SPLIT) {
-        tma_load_3d(st + A_BYTES, &mA_lo, &full[s], a0, P, m0);
-        tma_load_3d(st + B_OFF + B_BYTES, &mB_lo, &full[s], a0, n0, P);
-      }
+      if (a_split(MODE)) tma_load_3d(st + A_BYTES, &mA_lo, &full[s], a0, P, m0);
+      if (b_split(MODE)) tma_load_3d(st + B_OFF + B_BYTES, &mB_lo, &full[s], a0, n0, P);
     }
     // let the copies already issued land before the CTA can exit
     for (int i = max(0, nk - STAGES); i < nk; ++i) {
@@ -192,11 +197,8 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 16 bf16 = 32 bytes along K
         mma_bf16(tmem, ah + off, bh + off, (i > 0 || kk > 0) ? 1u : 0u);
-        if (SPLIT) {
-          const uint64_t al = sdesc(st + A_BYTES), bl = sdesc(st + B_OFF + B_BYTES);
-          mma_bf16(tmem, ah + off, bl + off, 1u);
-          mma_bf16(tmem, al + off, bh + off, 1u);
-        }
+        if (b_split(MODE)) mma_bf16(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, 1u);
+        if (a_split(MODE)) mma_bf16(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u);
       }
       mma_commit(&empty[s]);
     }
@@ -275,7 +277,7 @@ struct S1Params {
   int* err;
 };
 
-template <bool SPLIT>
+template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
 k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
             const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
@@ -295,7 +297,7 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
   const int nP = max(0, min(p.pn, P0 + p.ppc) - P0);
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(p.nb >> 3) << 17) |
                          ((uint32_t)(BM >> 4) << 24);
-  const int b_off = SPLIT ? 2 * p.a_bytes : p.a_bytes;
+  const int b_off = a_split(MODE) ? 2 * p.a_bytes : p.a_bytes;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -321,10 +323,8 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
       mbar_expect_tx(&full[s], p.stage_bytes);
       tma_load_3d(st, &mA_hi, &full[s], k0, m0, 0);
       tma_load_3d(st + b_off, &mB_hi, &full[s], k0, 0, P);
-      if (SPLIT) {
-        tma_load_3d(st + p.a_bytes, &mA_lo, &full[s], k0, m0, 0);
-        tma_load_3d(st + b_off + p.b_bytes, &mB_lo, &full[s], k0, 0, P);
-      }
+      if (a_split(MODE)) tma_load_3d(st + p.a_bytes, &mA_lo, &full[s], k0, m0, 0);
+      if (b_split(MODE)) tma_load_3d(st + b_off + p.b_bytes, &mB_lo, &full[s], k0, 0, P);
     }
     for (int i = max(0, nsteps - p.stages); i < nsteps; ++i)
       if (!mbar_wait(&full[i % p.stages], (uint32_t)(i / p.stages) & 1u)) { atomicOr(p.err, 32); break; }
@@ -349,12 +349,15 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
               "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
               "l"(ah + off), "l"(bh + off), "r"(idesc), "r"((kb > 0 || kk > 0) ? 1u : 0u));
-          if (SPLIT) {
-            const uint64_t al = sdesc(st + p.a_bytes), bl = sdesc(st + b_off + p.b_bytes);
+          if (b_split(MODE)) {
+            const uint64_t bl = sdesc(st + b_off + p.b_bytes);
             asm volatile(
                 "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
                 "l"(ah + off), "l"(bl + off), "r"(idesc), "r"(1u));
+          }
+          if (a_split(MODE)) {
+            const uint64_t al = sdesc(st + p.a_bytes);
             asm volatile(
                 "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
@@ -396,7 +399,7 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
               const float x = __uint_as_float(v[t]);
               const __nv_bfloat16 h = __float2bfloat16_rn(x);
               p.out_hi[o] = h;
-              if (SPLIT) p.out_lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+              if (a_split(MODE)) p.out_lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
             }
           }
         }
@@ -526,8 +529,8 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
                  const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, float* out,
                  bool accumulate, int* err, cudaStream_t s, KernelProfile* prof, double prof_flops) {
   if (M <= 0 || pn <= 0 || N <= 0) return;
-  const bool split = (Alo != nullptr);
-  TD_REQUIRE(split == (Blo != nullptr), TDDFT_ERR_ARG, "tc_contract: hi/lo operands mismatch");
+  TD_REQUIRE(Alo != nullptr || Blo == nullptr, TDDFT_ERR_ARG, "tc_contract: B split without A split");
+  const int mode = Alo ? (Blo ? BOTH : ASPLIT) : SINGLE;
   const int ldk = tc_pad(Kin);
   const int nab = (Kin + BK - 1) / BK;
   const int total = pn * nab;
@@ -545,20 +548,21 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
   const cuuint64_t sB[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)N * ldk * 2};
   const cuuint32_t bB[3] = {BK, BN, 1};
   CUtensorMap mAh = make_map(Ahi, dA, sA, bA), mBh = make_map(Bhi, dB, sB, bB);
-  CUtensorMap mAl = split ? make_map(Alo, dA, sA, bA) : mAh;
-  CUtensorMap mBl = split ? make_map(Blo, dB, sB, bB) : mBh;
+  CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA) : mAh;
+  CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB) : mBh;
 
   DevBuf part((size_t)splits * M * N * 4, s);
   Params p{M, N, nab, total, per, part.as<float>(), err};
   dim3 grid(nt, mt, splits);
-  if (split) ensure_smem((const void*)k1_tc_kernel<true>, Cfg<true>::SMEM_BYTES);
-  else ensure_smem((const void*)k1_tc_kernel<false>, Cfg<false>::SMEM_BYTES);
-  if (prof) prof->begin(s);
-  if (split)
-    k1_tc_kernel<true><<<grid, THREADS, Cfg<true>::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, p);
-  else
-    k1_tc_kernel<false><<<grid, THREADS, Cfg<false>::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, p);
-  if (prof) prof->end(s, prof_flops);
+  auto launch = [&](auto kernel, int smem) {
+    ensure_smem((const void*)kernel, smem);
+    if (prof) prof->begin(s);
+    kernel<<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
+    if (prof) prof->end(s, prof_flops);
+  };
+  if (mode == BOTH) launch(k1_tc_kernel<BOTH>, Cfg<BOTH>::SMEM_BYTES);
+  else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT>, Cfg<ASPLIT>::SMEM_BYTES);
+  else launch(k1_tc_kernel<SINGLE>, Cfg<SINGLE>::SMEM_BYTES);
   count_launch();
   TD_LAUNCH_CHECK();
   const long long MN = (long long)M * N;
@@ -574,15 +578,15 @@ void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
                __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int* err, cudaStream_t s) {
   if (M <= 0 || pn <= 0 || N <= 0) return;
   TD_REQUIRE(N <= 256, TDDFT_ERR_ARG, "tc_stage1: N above 256");
-  const bool split = (Alo != nullptr);
-  TD_REQUIRE(split == (Blo != nullptr) && split == (out_lo != nullptr), TDDFT_ERR_ARG,
+  TD_REQUIRE((Alo != nullptr || Blo == nullptr) && (Alo != nullptr) == (out_lo != nullptr), TDDFT_ERR_ARG,
              "tc_stage1: hi/lo operands mismatch");
+  const int mode = Alo ? (Blo ? BOTH : ASPLIT) : SINGLE;
   const int ldk = tc_pad(K);
   const int nb = (N + 15) & ~15;
   int acc_cols = 32;
   while (acc_cols < nb) acc_cols *= 2;
   const int a_bytes = BM * BK * 2, b_bytes = nb * BK * 2;
-  const int stage_bytes = split ? 2 * (a_bytes + b_bytes) : a_bytes + b_bytes;
+  const int stage_bytes = (a_split(mode) ? 2 : 1) * a_bytes + (b_split(mode) ? 2 : 1) * b_bytes;
   int stages = (200 * 1024) / stage_bytes;
   if (stages > 6) stages = 6;
   TD_REQUIRE(stages >= 2, TDDFT_ERR_ARG, "tc_stage1: tile too large");
@@ -600,18 +604,18 @@ void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
   const cuuint64_t sB[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)N * ldk * 2};
   const cuuint32_t bB[3] = {BK, (cuuint32_t)nb, 1};
   CUtensorMap mAh = make_map(Ahi, dA, sA, bA), mBh = make_map(Bhi, dB, sB, bB);
-  CUtensorMap mAl = split ? make_map(Alo, dA, sA, bA) : mAh;
-  CUtensorMap mBl = split ? make_map(Blo, dB, sB, bB) : mBh;
+  CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA) : mAh;
+  CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB) : mBh;
   S1Params p{M, N, R, tc_pad(R), pn, ppc, (K + BK - 1) / BK, nb, acc_cols, stages, stage_bytes,
              a_bytes, b_bytes, out_hi, out_lo, err};
   dim3 grid(mt, groups, 1);
-  if (split) {
-    ensure_smem((const void*)k_stage1_tc<true>, smem);
-    k_stage1_tc<true><<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
-  } else {
-    ensure_smem((const void*)k_stage1_tc<false>, smem);
-    k_stage1_tc<false><<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
-  }
+  auto launch = [&](auto kernel) {
+    ensure_smem((const void*)kernel, smem);
+    kernel<<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
+  };
+  if (mode == BOTH) launch(k_stage1_tc<BOTH>);
+  else if (mode == ASPLIT) launch(k_stage1_tc<ASPLIT>);
+  else launch(k_stage1_tc<SINGLE>);
   count_launch();
   TD_LAUNCH_CHECK();
 }

@@ -138,6 +138,50 @@ def make_problem(n_occ: int, n_vir: int, n_aux: int, n_ris: int, seeds=(0, 1, 2)
     )
 
 
+def factor_rows(name: str, p0: int, p1: int, **over):
+    """Rows [p0, p1) of a named workload's exact factors, drawn exactly as
+    make_config draws them (per-row Philox streams), without building the
+    whole [n_aux][n_mo][n_mo] array: returns (L_oo, L_ov, L_vv) float64 slices.
+    For workloads too large to hold in host memory at once."""
+    c = _config_args(name, over)
+    n_occ, n_mo, n_aux = c["n_occ"], c["n_occ"] + c["n_vir"], c["n_aux"]
+    d = 60.0 * n_aux / 200.0
+    sigma = c["amplitude"] * np.exp(-np.arange(n_aux) / d)
+    L = _symmetric_rows(c["seeds"][1], p1 - p0, n_mo, sigma[p0:p1], row0=p0)
+    o, v = slice(0, n_occ), slice(n_occ, n_mo)
+    return (np.ascontiguousarray(L[:, o, o]), np.ascontiguousarray(L[:, o, v]),
+            np.ascontiguousarray(L[:, v, v]))
+
+
+def ris_rows(name: str, r0: int, r1: int, **over):
+    """Rows [r0, r1) of a named workload's ris factors (as make_config builds
+    them): returns (Lr_oo, Lr_ov, Lr_vv) float64 slices."""
+    c = _config_args(name, over)
+    n_occ, n_mo, n_aux, n_ris = c["n_occ"], c["n_occ"] + c["n_vir"], c["n_aux"], c["n_ris"]
+    d = 60.0 * n_aux / 200.0
+    sigma = c["amplitude"] * np.exp(-np.arange(n_aux) / d)
+    n_r = min(n_ris, n_aux)
+    scale = 0.1 * np.resize(sigma[:n_r], n_ris)
+    Lr = _symmetric_rows(c["seeds"][2], r1 - r0, n_mo, scale[r0:r1], row0=r0)
+    hi = min(r1, n_r)
+    if hi > r0:
+        Lr[: hi - r0] += math.sqrt(0.9) * _symmetric_rows(c["seeds"][1], hi - r0, n_mo, sigma[r0:hi], row0=r0)
+    o, v = slice(0, n_occ), slice(n_occ, n_mo)
+    return (np.ascontiguousarray(Lr[:, o, o]), np.ascontiguousarray(Lr[:, o, v]),
+            np.ascontiguousarray(Lr[:, v, v]))
+
+
+def config_meta(name: str, **over) -> dict:
+    """Sizes, orbital energies, amplitude and ris exchange rows of a named
+    workload, without drawing its factors."""
+    c = _config_args(name, over)
+    eo, ev = orbital_energies(c["seeds"][0], c["n_occ"], c["n_vir"])
+    return dict(n_occ=c["n_occ"], n_vir=c["n_vir"], n_aux=c["n_aux"], n_ris=c["n_ris"], eps_occ=eo,
+                eps_vir=ev, amplitude=c["amplitude"], ris_K_index=np.arange(0, c["n_ris"], 9, dtype=np.int32),
+                a_x=c.get("a_x", 0.25), coulomb_factor=c.get("coulomb_factor", 2.0),
+                t_cut_ha=40.0 * HARTREE_PER_EV)
+
+
 def dipoles(seed: int, n_dip: int, n_ov: int, sigma: float = 0.1) -> np.ndarray:
     """Dipole right-hand sides mu^u_ia ~ N(0, sigma^2), shape [n_dip][n_ov]."""
     return _rng(seed, 0).normal(0.0, sigma, size=(n_dip, n_ov))
@@ -153,15 +197,25 @@ CONFIGS = {
     "rpa_polar_medium": dict(n_occ=60, n_vir=400, n_aux=2000, n_ris=360, seeds=(10, 11, 12),
                              n_states=10, mu_seed=13, omegas=(0.0, 0.05, 0.1), n_dip=3,
                              amplitude_scale=0.7 ** 5),
+    # amplitude scale 0.7^7: the exchange coupling of a dense random factor set
+    # grows like sqrt(n_occ n_vir) (2.9x the medium workload), so two more steps
+    # of 0.7 than the medium keep the same margin; the full-size GPU test checks
+    # lambda_min(A+B), lambda_min(A-B) > 0.02 Ha and the diagonal-preconditioned
+    # convergence within 33 iterations
     "large_mixed": dict(n_occ=150, n_vir=1350, n_aux=6000, n_ris=1350, seeds=(20, 21, 22),
-                        n_states=20, mu_seed=23),
+                        n_states=20, mu_seed=23, amplitude_scale=0.7 ** 7),
 }
 
 
-def make_config(name: str, **over) -> Problem:
+def _config_args(name: str, over: dict) -> dict:
     c = dict(CONFIGS[name])
     c.update(over)
     if "amplitude" not in c:
         c["amplitude"] = c.get("amplitude_scale", 1.0) * default_amplitude(c["n_aux"])
+    return c
+
+
+def make_config(name: str, **over) -> Problem:
+    c = _config_args(name, over)
     return make_problem(c["n_occ"], c["n_vir"], c["n_aux"], c["n_ris"], seeds=c["seeds"],
                         **{k: c[k] for k in ("a_x", "coulomb_factor", "amplitude") if k in c})
