@@ -89,8 +89,9 @@ def test_pair_products_full_size(large):
 
 def test_workload_well_posed(large):
     api, _, s, _, _ = large
-    assert _lanczos_min(api, s, 0) > 0.02
-    assert _lanczos_min(api, s, 1) > 0.02
+    lp, lm = _lanczos_min(api, s, 0), _lanczos_min(api, s, 1)
+    print("\nlarge_mixed lambda_min(A+B) = %.4f Ha, lambda_min(A-B) = %.4f Ha" % (lp, lm))
+    assert lp > 0.02 and lm > 0.02
 
 
 def test_tda_and_casida_full_size(large):
@@ -108,6 +109,10 @@ def test_tda_and_casida_full_size(large):
     od = api.default_opts(n_states=k, precond=api.DIAG, precision=api.MIXED, tensor_cores=1, max_iter=33)
     rd = s.solve_rpa(od, want_vectors=False)
     assert rd["status"] == api.OK, rd["stats"]
+    print("\nlarge_mixed TDA rid: %d it %.2f s; Casida rid: %d it %.2f s; Casida diag: %d it %.2f s; "
+          "omega_0 = %.8f Ha" % (t["stats"]["n_iter"], t["stats"]["t_total_s"], r["stats"]["n_iter"],
+                                 r["stats"]["t_total_s"], rd["stats"]["n_iter"], rd["stats"]["t_total_s"],
+                                 r["omega"][0]))
     assert r["stats"]["n_iter"] <= rd["stats"]["n_iter"]
     assert np.max(np.abs(rd["omega"] - r["omega"])) < 1e-5
     # the oracle's FP64 residuals of the lowest and the highest converged TDA state
