@@ -54,6 +54,7 @@ template <int MODE> struct Cfg {
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 };
 constexpr int THREADS = 192;
+constexpr int S1_THREADS = 320;   // stage 1: producer, MMA and 8 epilogue warps (2 per TMEM quadrant)
 constexpr long long WAIT_LIMIT = 1ll << 23;
 
 struct Params {
@@ -278,7 +279,7 @@ struct S1Params {
 };
 
 template <int MODE>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(S1_THREADS, 1)
 k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
             const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
             S1Params p) {
@@ -301,7 +302,7 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 8); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -369,9 +370,13 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
       mma_commit(&tfull[buf]);
     }
   } else if (warp >= 2) {
+    // 8 epilogue warps: TMEM lane quadrant q = warp & 3, column chunks of 16 of
+    // parity half = (warp - 2) / 4
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int r = m0 + q * 32 + lane;
     const int g = r / p.R, ri = r - (r / p.R) * p.R;
+    const size_t cs = (size_t)p.pn * p.ldo;   // output stride between consecutive columns
     for (int j = 0; j < nP; ++j) {
       const int buf = j & 1;
       bool ok = mbar_wait(&tfull[buf], (uint32_t)(j >> 1) & 1u);
@@ -379,7 +384,7 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
       if (!ok) { if (lane == 0) atomicOr(p.err, 256); break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int P = P0 + j;
-      for (int c0 = 0; c0 < p.N; c0 += 16) {
+      for (int c0 = 16 * half; c0 < p.N; c0 += 32) {
         uint32_t v[16];
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * p.acc_cols + c0);
         asm volatile(
@@ -391,15 +396,17 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (r < p.M) {
+          const size_t base = (((size_t)g * p.N + c0) * p.pn + P) * p.ldo + ri;
+          __nv_bfloat16* oh = p.out_hi + base;
+          __nv_bfloat16* ol = a_split(MODE) ? p.out_lo + base : nullptr;
+          const int nc = min(16, p.N - c0);
 #pragma unroll
           for (int t = 0; t < 16; ++t) {
-            const int c = c0 + t;
-            if (c < p.N) {
-              const size_t o = (((size_t)g * p.N + c) * p.pn + P) * p.ldo + ri;
+            if (t < nc) {
               const float x = __uint_as_float(v[t]);
               const __nv_bfloat16 h = __float2bfloat16_rn(x);
-              p.out_hi[o] = h;
-              if (a_split(MODE)) p.out_lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+              oh[t * cs] = h;
+              if (a_split(MODE)) ol[t * cs] = __float2bfloat16_rn(x - __bfloat162float(h));
             }
           }
         }
@@ -611,7 +618,7 @@ void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
   dim3 grid(mt, groups, 1);
   auto launch = [&](auto kernel) {
     ensure_smem((const void*)kernel, smem);
-    kernel<<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
+    kernel<<<grid, S1_THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
   };
   if (mode == BOTH) launch(k_stage1_tc<BOTH>);
   else if (mode == ASPLIT) launch(k_stage1_tc<ASPLIT>);
