@@ -418,6 +418,7 @@ def kernel_breakdown(solver, o_rpa, o_pol, mu, omegas):
     rows = [{"kernel": k, "launches": cnt[k], "ms": round(v / 1e3, 3), "share": round(v / busy, 4)}
             for k, v in sorted(tot.items(), key=lambda x: -x[1])]
     print(json.dumps({"kernel_breakdown": rows, "busy_ms": busy / 1e3, "span_ms": (span1 - span0) / 1e3,
+                      "first_start_ms": span0 / 1e3, "last_end_ms": span1 / 1e3, "events": len(ev),
                       "wall_ms": wall * 1e3, "workload": WORKLOAD}), flush=True)
 
 

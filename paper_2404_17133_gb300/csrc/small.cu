@@ -860,7 +860,7 @@ void chol_drop(const double* G, int nc, const double* norm0sq, double drop2, dou
   TD_REQUIRE(nc >= 1 && nc <= kDropMax, TDDFT_ERR_ARG, "chol_drop: too many candidates");
   size_t smem = (size_t)2 * nc * (nc + 1) * sizeof(double);
   set_smem((const void*)k_chol_drop, smem);
-  k_chol_drop<<<1, 1024, smem, s>>>(G, nc, norm0sq, drop2, T, keep);
+  k_chol_drop<<<1, 256, smem, s>>>(G, nc, norm0sq, drop2, T, keep);
   count_launch();
   TD_LAUNCH_CHECK();
 }
