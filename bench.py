@@ -63,6 +63,12 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="steps of the plain FP64 form timed for the mixed-vs-plain comparison (0: skip)")
     ap.add_argument("--precond", default="rid", choices=["rid", "diag"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the served request stream (0: no serving measurement)")
+    ap.add_argument("--serve-rate", type=float, default=30.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-max-occ", type=int, default=40, help="largest n_occ of a served request")
+    ap.add_argument("--serve-slots", type=int, default=8, help="requests running at once")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--apply-only", type=int, default=0, metavar="K",
                     help="time K exact pair products ((A+B)X, (A-B)X) of 2*n_states device vectors "
                          "and exit (a short program for kernel profiling)")
@@ -360,6 +366,11 @@ def our_arm(args, rank, world, local):
             "clocks": clk,
             "e2e": {"value": N_STATES * world / (e2e_t / 1e3), "unit": UNIT, "ms_per_step": e2e_t,
                     "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes)}}
+    if args.serve_seconds > 0 and world == 1:
+        try:
+            line["serving"] = serving(args, api, torch)
+        except Exception as e:   # the served stream is reported, not required for the line
+            line["serving"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if not args.no_cpu_baseline and world == 1:
         step_s, desc, cores = oracle_sample()
         line["cpu_baseline"] = {"value": N_STATES / step_s, "unit": UNIT, "cores": cores,
@@ -368,6 +379,101 @@ def our_arm(args, rank, world, local):
     solver.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def serving(args, api, torch):
+    """Open-loop served stream: Poisson arrivals of TDA (60 %), Casida (25 %) and
+    polarizability (15 %, 3 dipoles, 1-4 frequencies) requests of random sizes
+    (n_occ log-uniform, n_vir = n_occ x U{4..9}, n_aux = 5 n_mo, ris n_aux =
+    9 ceil(n_occ/2), 5-20 states), each bringing its own FP32 device-resident
+    problem, MIXED precision with tcgen05 products and rid; admitted by the
+    server's HBM budget with a fixed number of slots.  Latency = finish - submit
+    (server clock); throughput over the whole stream, first submit to last finish."""
+    from synth.device import problem_kw, serving_mix
+    from synth.generator import dipoles
+
+    rng = np.random.default_rng(2404)
+    gaps = rng.exponential(1.0 / args.serve_rate, size=int(args.serve_rate * args.serve_seconds * 3) + 16)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < args.serve_seconds]
+    n_req = int(arrivals.size)
+    mix = serving_mix(2404, n_req, max_occ=args.serve_max_occ)
+    n_pool = min(48, n_req)
+    pool = [problem_kw(1000 + i, m["n_occ"], m["n_vir"], m["n_aux"], m["n_ris"]) for i, m in
+            enumerate(mix[:n_pool])]
+    torch.cuda.synchronize()
+    freqs = [0.0, 0.05, 0.1, 0.15]
+    reqs = []
+    for i, m in enumerate(mix):
+        kw = pool[i % n_pool]
+        ov = kw["n_occ"] * kw["n_vir"]
+        kind = m["kind"]
+        if kind == 2:
+            o = api.default_opts(precond=api.RID, precision=api.MIXED, tensor_cores=1)
+            reqs.append((kind, o, kw, dipoles(5000 + i, 3, ov), freqs[:m["n_freq"]]))
+        else:
+            o = api.default_opts(n_states=min(m["n_states"], ov), precond=api.RID, precision=api.MIXED,
+                                 tensor_cores=1)
+            reqs.append((kind, o, kw, None, None))
+    srv = api.Server(hbm_budget_gb=args.serve_budget_gb, max_active=args.serve_slots)
+    try:
+        # warm-up: one request of each kind on the smallest pooled problem (untimed)
+        small = min(pool, key=lambda k: k["n_occ"] * k["n_vir"])
+        ws = [srv.submit(k, api.default_opts(n_states=5, precond=api.RID, precision=api.MIXED, tensor_cores=1),
+                         create_kw=dict(small, precisions=2, dtype=api.F32),
+                         mu=dipoles(1, 3, small["n_occ"] * small["n_vir"]) if k == 2 else None,
+                         omegas=[0.0, 0.05] if k == 2 else None) for k in (0, 1, 2)]
+        for t in ws:
+            while srv.poll(t, timeout_ms=100) is None:
+                pass
+        done, pending = [], {}
+        t0 = time.perf_counter()
+        i = 0
+        limit = args.serve_seconds + 300.0
+        while i < n_req or pending:
+            now = time.perf_counter() - t0
+            while i < n_req and arrivals[i] <= now:
+                kind, o, kw, mu, om = reqs[i]
+                t = srv.submit(kind, o, create_kw=dict(kw, precisions=2, dtype=api.F32), mu=mu, omegas=om)
+                pending[t] = (i, kind, o.n_states)
+                i += 1
+            for t in list(pending):
+                r = srv.poll(t, timeout_ms=0)
+                if r is not None:
+                    done.append((pending.pop(t), r))
+            if now > limit:
+                break
+            time.sleep(0.001)
+        info = srv.info()
+    finally:
+        srv.close()
+    if not done:
+        return {"error": "no request finished"}
+    lat = sorted(r["latency_s"] * 1e3 for _, r in done)
+    wait = sorted((r["t_start_s"] - r["t_submit_s"]) * 1e3 for _, r in done)
+    pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))]
+    span = max(r["t_end_s"] for _, r in done) - min(r["t_submit_s"] for _, r in done)
+    ok = [(m, r) for m, r in done if r["status"] == api.OK]
+    states = sum(m[2] for m, r in ok if m[1] in (0, 1))
+    starts = sorted(r["t_start_s"] for _, r in done)
+    most = max(sum(1 for _, q in done if q["t_start_s"] <= t < q["t_end_s"]) for t in starts)
+    by_kind = {}
+    for (i, kind, _), r in done:
+        by_kind.setdefault(kind, []).append(r["latency_s"] * 1e3)
+    return {"requests": n_req, "finished": len(done), "ok": len(ok),
+            "noconv": sum(1 for _, r in done if r["status"] == api.ERR_NOCONV),
+            "errors": sum(1 for _, r in done if r["status"] not in (api.OK, api.ERR_NOCONV)),
+            "unfinished": len(pending), "offered_rate_req_s": args.serve_rate, "seconds": args.serve_seconds,
+            "span_s": span, "states_per_s": states / span, "solves_per_s": len(ok) / span,
+            "p50_ms": pct(lat, 0.50), "p99_ms": pct(lat, 0.99), "queue_wait_p50_ms": pct(wait, 0.50),
+            "queue_wait_p99_ms": pct(wait, 0.99),
+            "p50_ms_by_kind": {("tda", "casida", "polar")[k]: statistics.median(v) for k, v in by_kind.items()},
+            "max_concurrent": most, "slots": args.serve_slots, "budget_gb": info["budget_bytes"] / 1e9,
+            "peak_charge_gb": info["peak_in_use_bytes"] / 1e9,
+            "pool_high_gb": (info["pool_high_bytes"] - info["pool_used_at_create_bytes"]) / 1e9,
+            "n_occ_range": [10, args.serve_max_occ], "distinct_problems": n_pool,
+            "note": "each request creates its context from FP32 device arrays (precisions=MIXED only), "
+                    "solves, destroys it; MIXED + tcgen05 + rid; latency = finish - submit"}
 
 
 def apply_only(args, api, solver, p, tc, stream):

@@ -128,7 +128,12 @@ void tddft_default_desc(tddft_desc* desc);
  *   ris_K_index [n_aux_ris_K]             row of Lr_ov that each exchange row
  *                                         is (its ov block for (ib|ja))
  *   dtype                                 element type of all factor arrays
- *   inputs_on_device                      1: every array pointer is device memory
+ *   inputs_on_device                      1: every array pointer is device memory;
+ *                                         the library reads it on cuda_stream (or
+ *                                         its own stream) after the work already
+ *                                         queued on the legacy default stream;
+ *                                         writes queued on other streams must be
+ *                                         complete or ordered before cuda_stream
  *   cuda_stream                           cudaStream_t to run on (NULL: own one)
  * The t_cut window is applied here to the ris exchange rows.
  * Returns TDDFT_ERR_ARG on bad sizes or null pointers, TDDFT_ERR_OOM when the
@@ -184,6 +189,88 @@ typedef struct {
 tddft_status tddft_submit(tddft_ctx* ctx, int kind, tddft_request* req,
                           unsigned long long* ticket);
 tddft_status tddft_poll(tddft_ctx* ctx, unsigned long long ticket, int timeout_ms);
+
+/* ---- Serving (no counterpart in the paper, which solves one molecule at a
+ * time; this is the library's interface for many independent problems).
+ * A server runs up to max_active requests at once, each on a CUDA stream of
+ * its own, so the kernels of different requests overlap on the device.  A
+ * request either brings its own problem (the server creates a context from
+ * the desc and arrays when the request is admitted, on the slot's stream, and
+ * destroys it when the solve ends) or names an existing context in `ctx`,
+ * whose factors stay resident between requests (solves on one context run
+ * one at a time).  Admission is first in, first out: the oldest waiting
+ * request starts as soon as a slot is free and its charge fits into the
+ * budget minus the charges of the running requests.  The charge is
+ * tddft_estimate_bytes (factor copies + workspace; workspace only for a
+ * request on an existing context).  A request whose charge exceeds the whole
+ * budget is refused at submit with TDDFT_ERR_OOM.
+ * Every array a request points to must stay valid until tddft_server_poll
+ * returns its final status. */
+typedef struct tddft_server tddft_server;
+
+typedef struct {
+  tddft_ctx* ctx;             /* non-NULL: solve on this context; the problem
+                                 fields below (desc ... inputs_on_device) are
+                                 then ignored                                 */
+  tddft_desc desc;            /* problem, as for tddft_create                 */
+  const double* eps_occ; const double* eps_vir;
+  const void* L_oo; const void* L_ov; const void* L_vv;
+  const void* Lr_oo; const void* Lr_ov; const void* Lr_vv;
+  const int* ris_K_index;
+  tddft_dtype dtype; int inputs_on_device;
+  int kind;                   /* 0 TDA, 1 Casida, 2 polarizability            */
+  tddft_request req;          /* options, outputs and statistics (as for
+                                 tddft_submit)                                */
+  /* filled by the server */
+  unsigned long long charged_bytes;   /* admission charge                     */
+  double t_submit_s, t_start_s, t_end_s;  /* seconds since server creation:
+                                 queued, admitted, finished                  */
+  char error[256];            /* message when the final status is an error   */
+} tddft_serve_request;
+
+typedef struct {
+  unsigned long long budget_bytes, in_use_bytes, peak_in_use_bytes;  /* charges */
+  int active, max_active, queued;
+  unsigned long long completed;
+  /* the device's default stream-ordered memory pool, from which every device
+   * buffer of the library comes: bytes in use when the server was created and
+   * the high-water mark since then (other users of that pool included)     */
+  unsigned long long pool_used_at_create_bytes, pool_high_bytes;
+} tddft_server_state;
+
+/* Device-memory charge of one request: the factor copies tddft_create makes
+ * for desc (factor_bytes, may be NULL) and a bound on the solve's work
+ * buffers (work_bytes, may be NULL): the outer subspace and its work vectors,
+ * the rid inner space, the operator's P-chunk intermediates (at most three
+ * of 512 MiB) and 64 MiB for the small algebra.  n_dip / n_freq are used for
+ * kind 2 only.  TDDFT_ERR_ARG on bad sizes or kind.                        */
+tddft_status tddft_estimate_bytes(const tddft_desc* desc, int kind, const tddft_opts* opts, int n_dip,
+                                  int n_freq, unsigned long long* factor_bytes,
+                                  unsigned long long* work_bytes);
+
+/* hbm_budget_gb: total charge allowed at once (0: free memory at creation
+ * minus 2 GB; larger values are capped at that); max_active: 1..64 slots.  */
+tddft_status tddft_server_create(double hbm_budget_gb, int max_active, tddft_server** out);
+
+/* Queue a request; fills *ticket.  TDDFT_ERR_OOM if its charge exceeds the
+ * budget, TDDFT_ERR_ARG on a bad kind or desc, TDDFT_ERR_BUSY when the queue
+ * holds 65536 requests or the server is shutting down.                     */
+tddft_status tddft_server_submit(tddft_server* server, tddft_serve_request* req,
+                                 unsigned long long* ticket);
+
+/* Wait at most timeout_ms (0: do not wait).  TDDFT_PENDING / TDDFT_ERR_TIMEOUT
+ * while queued or running; else the request's final status (once: the ticket
+ * is then forgotten).                                                      */
+tddft_status tddft_server_poll(tddft_server* server, unsigned long long ticket, int timeout_ms);
+
+/* Budget, charges and queue length now; peak_in_use_bytes since creation.  */
+tddft_status tddft_server_info(const tddft_server* server, tddft_server_state* state);
+
+/* Run every queued request to its end, then release the slots and streams. */
+void tddft_server_destroy(tddft_server* server);
+
+/* The tddft_desc a context was created with.                              */
+tddft_status tddft_ctx_desc(const tddft_ctx* ctx, tddft_desc* desc);
 
 /* Release every device allocation and the worker thread. NULL is a no-op.  */
 void tddft_destroy(tddft_ctx* ctx);

@@ -61,6 +61,27 @@ class Request(C.Structure):
                 ("alpha", C.c_void_p), ("stats", Stats)]
 
 
+class ServeRequest(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("desc", Desc),
+                ("eps_occ", C.c_void_p), ("eps_vir", C.c_void_p),
+                ("L_oo", C.c_void_p), ("L_ov", C.c_void_p), ("L_vv", C.c_void_p),
+                ("Lr_oo", C.c_void_p), ("Lr_ov", C.c_void_p), ("Lr_vv", C.c_void_p),
+                ("ris_K_index", C.c_void_p), ("dtype", C.c_int), ("inputs_on_device", C.c_int),
+                ("kind", C.c_int), ("req", Request), ("charged_bytes", C.c_ulonglong),
+                ("t_submit_s", C.c_double), ("t_start_s", C.c_double), ("t_end_s", C.c_double),
+                ("error", C.c_char * 256)]
+
+
+class ServerState(C.Structure):
+    _fields_ = [("budget_bytes", C.c_ulonglong), ("in_use_bytes", C.c_ulonglong),
+                ("peak_in_use_bytes", C.c_ulonglong), ("active", C.c_int), ("max_active", C.c_int),
+                ("queued", C.c_int), ("completed", C.c_ulonglong),
+                ("pool_used_at_create_bytes", C.c_ulonglong), ("pool_high_bytes", C.c_ulonglong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp, _ip, _dp = C.c_void_p, C.c_int, C.c_void_p
 _lib.tddft_default_opts.argtypes = [C.POINTER(Opts)]
 _lib.tddft_default_opts.restype = None
@@ -94,11 +115,28 @@ _lib.tddft_profile.restype = C.c_int
 _lib.tddft_profile_read.argtypes = [_vp, _ip, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]
 _lib.tddft_profile_read.restype = C.c_int
+_lib.tddft_estimate_bytes.argtypes = [C.POINTER(Desc), _ip, C.POINTER(Opts), _ip, _ip,
+                                      C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]
+_lib.tddft_estimate_bytes.restype = C.c_int
+_lib.tddft_server_create.argtypes = [C.c_double, _ip, C.POINTER(_vp)]
+_lib.tddft_server_create.restype = C.c_int
+_lib.tddft_server_submit.argtypes = [_vp, C.POINTER(ServeRequest), C.POINTER(C.c_ulonglong)]
+_lib.tddft_server_submit.restype = C.c_int
+_lib.tddft_server_poll.argtypes = [_vp, C.c_ulonglong, _ip]
+_lib.tddft_server_poll.restype = C.c_int
+_lib.tddft_server_info.argtypes = [_vp, C.POINTER(ServerState)]
+_lib.tddft_server_info.restype = C.c_int
+_lib.tddft_server_destroy.argtypes = [_vp]
+_lib.tddft_server_destroy.restype = None
+_lib.tddft_ctx_desc.argtypes = [_vp, C.POINTER(Desc)]
+_lib.tddft_ctx_desc.restype = C.c_int
 
 EXPORTED = ["tddft_default_opts", "tddft_default_desc", "tddft_create", "tddft_solve_tda",
             "tddft_solve_rpa", "tddft_solve_polar", "tddft_apply", "tddft_submit", "tddft_poll",
             "tddft_destroy", "tddft_last_error", "tddft_device_bytes", "tddft_profile",
-            "tddft_profile_read", "tddft_apply_noalloc"]
+            "tddft_profile_read", "tddft_apply_noalloc", "tddft_estimate_bytes", "tddft_server_create",
+            "tddft_server_submit", "tddft_server_poll", "tddft_server_info", "tddft_server_destroy",
+            "tddft_ctx_desc"]
 
 
 class TddftError(RuntimeError):
@@ -137,33 +175,77 @@ def default_opts(**kw) -> Opts:
     return o
 
 
+def _problem_args(n_occ, n_vir, eps_occ, eps_vir, L_oo, L_ov, L_vv, Lr_oo, Lr_ov, Lr_vv, ris_K_index,
+                  a_x=0.25, coulomb_factor=2.0, t_cut_ha=None, precisions=3, hbm_budget_gb=0.0, dtype=F64):
+    """(Desc, the nine array pointers of tddft_create, keepalives, inputs_on_device)."""
+    d = Desc()
+    _lib.tddft_default_desc(C.byref(d))
+    d.n_occ, d.n_vir = int(n_occ), int(n_vir)
+    d.n_aux = int(L_ov.shape[0])
+    d.n_aux_ris_J = int(Lr_ov.shape[0]) if Lr_ov is not None else 0
+    d.n_aux_ris_K = int(len(ris_K_index)) if ris_K_index is not None else 0
+    d.a_x, d.coulomb_factor = float(a_x), float(coulomb_factor)
+    if t_cut_ha is not None:
+        d.t_cut_ha = float(t_cut_ha)
+    d.precisions, d.hbm_budget_gb = int(precisions), float(hbm_budget_gb)
+    fdt = np.float64 if dtype == F64 else np.float32
+    keep, ptrs = [], []
+    for arr, dt in ((eps_occ, np.float64), (eps_vir, np.float64), (L_oo, fdt), (L_ov, fdt),
+                    (L_vv, fdt), (Lr_oo, fdt), (Lr_ov, fdt), (Lr_vv, fdt), (ris_K_index, np.int32)):
+        p, k = _ptr(arr, dt)
+        ptrs.append(p)
+        keep.append(k)
+    return d, ptrs, keep, _is_cuda(L_ov)
+
+
+def _problem_kw(prob):
+    """tddft_create arguments of a synthetic problem (ris exchange rows = its s rows)."""
+    return dict(n_occ=prob.n_occ, n_vir=prob.n_vir, eps_occ=prob.eps_occ, eps_vir=prob.eps_vir,
+                L_oo=prob.L_oo, L_ov=prob.L_ov, L_vv=prob.L_vv, Lr_oo=prob.Lr_oo[prob.ris_K_index],
+                Lr_ov=prob.Lr_ov, Lr_vv=prob.Lr_vv[prob.ris_K_index], ris_K_index=prob.ris_K_index,
+                a_x=prob.a_x, coulomb_factor=prob.coulomb_factor, t_cut_ha=prob.t_cut_ha)
+
+
+def _fill_request(r: Request, kind, opts: Opts, mu=None, omegas=None):
+    """Point a Request at fresh output arrays; returns them (to keep alive)."""
+    r.opts = opts
+    bufs = {}
+    if kind in (0, 1):
+        k = opts.n_states
+        bufs["omega"], bufs["resid"] = np.zeros(k), np.zeros(k)
+        r.omega = bufs["omega"].ctypes.data
+        r.resid = bufs["resid"].ctypes.data
+    else:
+        mu = np.ascontiguousarray(np.atleast_2d(mu), dtype=np.float64)
+        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        bufs["mu"], bufs["freqs"] = mu, om
+        bufs["alpha"] = np.zeros((om.size, mu.shape[0], mu.shape[0]))
+        r.mu, r.n_dip, r.freqs, r.n_freq = mu.ctypes.data, mu.shape[0], om.ctypes.data, om.size
+        r.alpha = bufs["alpha"].ctypes.data
+    return bufs
+
+
+def estimate_bytes(desc: Desc, kind, opts: Opts, n_dip=0, n_freq=0):
+    """(factor bytes, work bytes) that a server charges for one request."""
+    f, w = C.c_ulonglong(), C.c_ulonglong()
+    st = _lib.tddft_estimate_bytes(C.byref(desc), int(kind), C.byref(opts), int(n_dip), int(n_freq),
+                                   C.byref(f), C.byref(w))
+    if st != OK:
+        raise TddftError(st, "bad desc or kind")
+    return f.value, w.value
+
+
 class Solver:
     """One context: resident factors + the request queue (include/tddft.h)."""
 
     def __init__(self, n_occ, n_vir, eps_occ, eps_vir, L_oo, L_ov, L_vv, Lr_oo, Lr_ov, Lr_vv,
                  ris_K_index, a_x=0.25, coulomb_factor=2.0, t_cut_ha=None, precisions=3,
                  hbm_budget_gb=0.0, dtype=F64, stream=None):
-        d = Desc()
-        _lib.tddft_default_desc(C.byref(d))
-        d.n_occ, d.n_vir = int(n_occ), int(n_vir)
-        d.n_aux = int(L_ov.shape[0])
-        d.n_aux_ris_J = int(Lr_ov.shape[0]) if Lr_ov is not None else 0
-        d.n_aux_ris_K = int(len(ris_K_index)) if ris_K_index is not None else 0
-        d.a_x, d.coulomb_factor = float(a_x), float(coulomb_factor)
-        if t_cut_ha is not None:
-            d.t_cut_ha = float(t_cut_ha)
-        d.precisions, d.hbm_budget_gb = int(precisions), float(hbm_budget_gb)
+        d, ptrs, keep, on_dev = _problem_args(n_occ, n_vir, eps_occ, eps_vir, L_oo, L_ov, L_vv, Lr_oo, Lr_ov,
+                                              Lr_vv, ris_K_index, a_x, coulomb_factor, t_cut_ha, precisions,
+                                              hbm_budget_gb, dtype)
         self.desc = d
         self.n_ov = d.n_occ * d.n_vir
-        on_dev = _is_cuda(L_ov)
-        fdt = np.float64 if dtype == F64 else np.float32
-        keep = []
-        ptrs = []
-        for arr, dt in ((eps_occ, np.float64), (eps_vir, np.float64), (L_oo, fdt), (L_ov, fdt),
-                        (L_vv, fdt), (Lr_oo, fdt), (Lr_ov, fdt), (Lr_vv, fdt), (ris_K_index, np.int32)):
-            p, k = _ptr(arr, dt)
-            ptrs.append(p)
-            keep.append(k)
         h = C.c_void_p()
         st = _lib.tddft_create(C.byref(d), *ptrs, int(dtype), 1 if on_dev else 0,
                                C.c_void_p(stream) if stream else None, C.byref(h))
@@ -174,10 +256,7 @@ class Solver:
 
     @classmethod
     def from_problem(cls, prob, **kw):
-        return cls(prob.n_occ, prob.n_vir, prob.eps_occ, prob.eps_vir, prob.L_oo, prob.L_ov, prob.L_vv,
-                   prob.Lr_oo[prob.ris_K_index], prob.Lr_ov, prob.Lr_vv[prob.ris_K_index],
-                   prob.ris_K_index, a_x=prob.a_x, coulomb_factor=prob.coulomb_factor,
-                   t_cut_ha=prob.t_cut_ha, **kw)
+        return cls(**_problem_kw(prob), **kw)
 
     def _check(self, st, allow_noconv=True):
         if st == OK or (allow_noconv and st == ERR_NOCONV):
@@ -261,20 +340,7 @@ class Solver:
     def submit(self, kind, opts: Opts, mu=None, omegas=None):
         """kind 0 TDA, 1 RPA, 2 polar.  Returns a ticket; buffers are kept alive here."""
         r = Request()
-        r.opts = opts
-        bufs = {}
-        if kind in (0, 1):
-            k = opts.n_states
-            bufs["omega"], bufs["resid"] = np.zeros(k), np.zeros(k)
-            r.omega = bufs["omega"].ctypes.data
-            r.resid = bufs["resid"].ctypes.data
-        else:
-            mu = np.ascontiguousarray(np.atleast_2d(mu), dtype=np.float64)
-            om = np.ascontiguousarray(omegas, dtype=np.float64)
-            bufs["mu"], bufs["freqs"] = mu, om
-            bufs["alpha"] = np.zeros((om.size, mu.shape[0], mu.shape[0]))
-            r.mu, r.n_dip, r.freqs, r.n_freq = mu.ctypes.data, mu.shape[0], om.ctypes.data, om.size
-            r.alpha = bufs["alpha"].ctypes.data
+        bufs = _fill_request(r, kind, opts, mu, omegas)
         t = C.c_ulonglong()
         s = _lib.tddft_submit(self.h, kind, C.byref(r), C.byref(t))
         self._check(s, allow_noconv=False)
@@ -292,3 +358,74 @@ class Solver:
             out["error"] = _lib.tddft_last_error(self.h).decode()
         out.update({k: v for k, v in bufs.items() if k in ("omega", "resid", "alpha")})
         return out
+
+
+class Server:
+    """Continuous admission of independent solves under a device-memory budget
+    (tddft_server_* in include/tddft.h).  A request brings its own problem
+    (``problem``: a synthetic problem, or ``create_kw``: tddft_create arguments
+    as for Solver) or runs on an existing ``solver``'s resident factors."""
+
+    def __init__(self, hbm_budget_gb=0.0, max_active=4):
+        h = C.c_void_p()
+        st = _lib.tddft_server_create(float(hbm_budget_gb), int(max_active), C.byref(h))
+        if st != OK:
+            raise TddftError(st, "tddft_server_create failed")
+        self.h = h
+        self._pending = {}
+
+    def submit(self, kind, opts: Opts, problem=None, create_kw=None, solver=None, mu=None, omegas=None,
+               dtype=F64, precisions=3):
+        """kind 0 TDA, 1 Casida, 2 polarizability.  Returns a ticket."""
+        q = ServeRequest()
+        keep = []
+        if solver is not None:
+            q.ctx = solver.h
+            keep.append(solver)
+        else:
+            kw = dict(create_kw) if create_kw is not None else _problem_kw(problem)
+            kw.setdefault("precisions", precisions)
+            kw.setdefault("dtype", dtype)
+            d, ptrs, k, on_dev = _problem_args(**kw)
+            keep.append(k)
+            q.desc = d
+            (q.eps_occ, q.eps_vir, q.L_oo, q.L_ov, q.L_vv, q.Lr_oo, q.Lr_ov, q.Lr_vv,
+             q.ris_K_index) = [p.value if p is not None else None for p in ptrs]
+            q.dtype, q.inputs_on_device = int(kw["dtype"]), 1 if on_dev else 0
+        q.kind = int(kind)
+        bufs = _fill_request(q.req, kind, opts, mu, omegas)
+        t = C.c_ulonglong()
+        st = _lib.tddft_server_submit(self.h, C.byref(q), C.byref(t))
+        if st != OK:
+            raise TddftError(st, q.error.decode())
+        self._pending[t.value] = (q, bufs, keep)
+        return t.value
+
+    def poll(self, ticket, timeout_ms=0):
+        """None while queued or running; else the result dict with its timings."""
+        st = _lib.tddft_server_poll(self.h, ticket, int(timeout_ms))
+        if st in (PENDING, ERR_TIMEOUT):
+            return None
+        q, bufs, _ = self._pending.pop(ticket)
+        out = dict(status=st, stats=q.req.stats.as_dict(), charged_bytes=q.charged_bytes,
+                   t_submit_s=q.t_submit_s, t_start_s=q.t_start_s, t_end_s=q.t_end_s,
+                   latency_s=q.t_end_s - q.t_submit_s)
+        if st not in (OK, ERR_NOCONV):
+            out["error"] = q.error.decode()
+        out.update({k: v for k, v in bufs.items() if k in ("omega", "resid", "alpha")})
+        return out
+
+    def info(self):
+        s = ServerState()
+        st = _lib.tddft_server_info(self.h, C.byref(s))
+        if st != OK:
+            raise TddftError(st, "tddft_server_info failed")
+        return s.as_dict()
+
+    def close(self):
+        """Runs every queued request to its end first."""
+        if getattr(self, "h", None):
+            _lib.tddft_server_destroy(self.h)
+            self.h = None
+
+    __del__ = close

@@ -101,6 +101,19 @@ void worker_loop(Ctx* c) {
 
 namespace tddft {
 
+unsigned long long factor_copy_bytes(const tddft_desc& d) {
+  const bool p64 = d.precisions & 1, pmx = d.precisions & 2;
+  const double no = d.n_occ, nv = d.n_vir, ov = no * nv;
+  const double nvv = (double)d.n_aux * nv * nv, noo = (double)d.n_aux * no * no, nov = (double)d.n_aux * ov;
+  const double nr = (double)d.n_aux_ris_J * ov + (double)d.n_aux_ris_K * (no * no + nv * nv + ov);
+  const double padded = nv * (tc_pad(d.n_vir) + tc_pad(d.n_occ)) + no * (tc_pad(d.n_occ) + tc_pad(d.n_vir));
+  double bytes = 0.0;
+  if (p64) bytes += 8.0 * (nvv + noo + nov + nr);
+  if (pmx) bytes += 4.0 * (nvv + noo + nov) + 4.0 * (double)d.n_aux * padded + 2.0 * nr +
+                    2.0 * (double)d.n_aux_ris_K * padded;
+  return (unsigned long long)bytes;
+}
+
 FactorSet Ctx::exact(int precision) const {
   FactorSet f;
   f.nJ = naux;
@@ -221,11 +234,24 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
     const DType tin = dtype == TDDFT_F64 ? DType::F64 : DType::F32;
     const bool dev = inputs_on_device != 0;
 
+    if (dev) {
+      // device inputs written by work queued on the legacy default stream (as
+      // PyTorch's default stream is) are read only after that work
+      cudaEvent_t e;
+      TD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      cudaError_t er = cudaEventRecord(e, cudaStreamLegacy);
+      if (er == cudaSuccess) er = cudaStreamWaitEvent(s, e, 0);
+      cudaEventDestroy(e);
+      TD_CUDA(er);
+    }
+
     // orbital energies (host copy for the window and the guess order)
     std::vector<double> eo(no), ev(nv);
     cudaMemcpyKind k = dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-    TD_CUDA(cudaMemcpy(eo.data(), eps_occ, no * 8, k));
-    TD_CUDA(cudaMemcpy(ev.data(), eps_vir, nv * 8, k));
+    // on the context's stream: no wait on work that other contexts queued
+    TD_CUDA(cudaMemcpyAsync(eo.data(), eps_occ, no * 8, k, s));
+    TD_CUDA(cudaMemcpyAsync(ev.data(), eps_vir, nv * 8, k, s));
+    TD_CUDA(cudaStreamSynchronize(s));
     for (double x : eo) TD_REQUIRE(std::isfinite(x), TDDFT_ERR_ARG, "non-finite orbital energy");
     for (double x : ev) TD_REQUIRE(std::isfinite(x), TDDFT_ERR_ARG, "non-finite orbital energy");
     TD_REQUIRE(std::is_sorted(eo.begin(), eo.end()) && std::is_sorted(ev.begin(), ev.end()),
@@ -233,20 +259,15 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
     std::vector<int> kidx;
     if (d.n_aux_ris_K > 0) {
       kidx.resize(d.n_aux_ris_K);
-      TD_CUDA(cudaMemcpy(kidx.data(), ris_K_index, kidx.size() * 4, k));
+      TD_CUDA(cudaMemcpyAsync(kidx.data(), ris_K_index, kidx.size() * 4, k, s));
+      TD_CUDA(cudaStreamSynchronize(s));
       for (int r : kidx) TD_REQUIRE(r >= 0 && r < d.n_aux_ris_J, TDDFT_ERR_ARG, "ris_K_index out of range");
     }
 
     // memory admission
     const bool p64 = c->precisions & 1, pmx = c->precisions & 2;
-    const double nvv = (double)d.n_aux * nv * nv, noo = (double)d.n_aux * no * no, nov = (double)d.n_aux * ov;
-    const double nr = (double)d.n_aux_ris_J * ov + (double)d.n_aux_ris_K * (no * no + nv * nv + ov);
-    double bytes = 0.0;
-    if (p64) bytes += 8.0 * (nvv + noo + nov + nr);
-    if (pmx)
-      bytes += 4.0 * (nvv + noo + nov) +
-               4.0 * (double)d.n_aux * (nv * (tc_pad(nv) + tc_pad(no)) + no * (tc_pad(no) + tc_pad(nv))) +
-               2.0 * nr + 2.0 * (double)d.n_aux_ris_K * (nv * (tc_pad(nv) + tc_pad(no)) + no * (tc_pad(no) + tc_pad(nv)));
+    c->desc = d;
+    const double bytes = (double)factor_copy_bytes(d);
     size_t fr = 0, tot = 0;
     TD_CUDA(cudaMemGetInfo(&fr, &tot));
     double budget = d.hbm_budget_gb > 0 ? d.hbm_budget_gb * 1e9 : (double)fr - 2e9;
@@ -578,6 +599,13 @@ tddft_status tddft_profile_read(const tddft_ctx* ctx, int which, long long* laun
     if (flops) *flops = kp.flops;
     return TDDFT_OK;
   })
+}
+
+tddft_status tddft_ctx_desc(const tddft_ctx* ctx, tddft_desc* desc) {
+  const Ctx* c = reinterpret_cast<const Ctx*>(ctx);
+  if (!c || !desc) return TDDFT_ERR_ARG;
+  *desc = c->desc;
+  return TDDFT_OK;
 }
 
 unsigned long long tddft_device_bytes(const tddft_ctx* ctx) {

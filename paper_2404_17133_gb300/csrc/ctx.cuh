@@ -75,6 +75,10 @@ struct Request {
   bool done = false;
 };
 
+// Device bytes of the factor copies tddft_create makes for `d` (both
+// precisions as selected by d.precisions).
+unsigned long long factor_copy_bytes(const tddft_desc& d);
+
 struct Ctx {
   cudaStream_t s = nullptr;
   bool own_stream = false;
@@ -98,6 +102,7 @@ struct Ctx {
   DevBuf r64_J, r64_Koo, r64_Kvv, r64_Kov;
   DevBuf r16_J, r16_Koo, r16_Kvv, r16_Kov;
   DevBuf r16_vvp, r16_vo, r16_oop, r16_ovp;   // tensor-core copies of the ris exchange rows
+  tddft_desc desc{};              // as given to tddft_create
   unsigned long long device_bytes = 0;
   std::string err;
   // request queue

@@ -57,6 +57,12 @@ int main(void) {
   F(tddft_opts, tol) F(tddft_opts, max_iter) F(tddft_opts, outputs_on_device)
   F(tddft_stats, max_resid) F(tddft_stats, t_precond_s)
   F(tddft_request, omega) F(tddft_request, n_dip) F(tddft_request, alpha) F(tddft_request, stats)
+  printf("tddft_serve_request %zu\\ntddft_server_state %zu\\n", sizeof(tddft_serve_request),
+         sizeof(tddft_server_state));
+  F(tddft_serve_request, desc) F(tddft_serve_request, ris_K_index) F(tddft_serve_request, kind)
+  F(tddft_serve_request, req) F(tddft_serve_request, charged_bytes) F(tddft_serve_request, t_end_s)
+  F(tddft_serve_request, error)
+  F(tddft_server_state, active) F(tddft_server_state, completed) F(tddft_server_state, pool_high_bytes)
   return 0;
 }
 """)
@@ -69,11 +75,14 @@ int main(void) {
     assert int(vals["tddft_opts"]) == C.sizeof(api.Opts)
     assert int(vals["tddft_stats"]) == C.sizeof(api.Stats)
     assert int(vals["tddft_request"]) == C.sizeof(api.Request)
+    assert int(vals["tddft_serve_request"]) == C.sizeof(api.ServeRequest)
+    assert int(vals["tddft_server_state"]) == C.sizeof(api.ServerState)
     for key, v in vals.items():
         if "." in key:
             t, f = key.split(".")
             cls = {"tddft_desc": api.Desc, "tddft_opts": api.Opts, "tddft_stats": api.Stats,
-                   "tddft_request": api.Request}[t]
+                   "tddft_request": api.Request, "tddft_serve_request": api.ServeRequest,
+                   "tddft_server_state": api.ServerState}[t]
             assert getattr(cls, f).offset == int(v), key
 
 
@@ -97,3 +106,43 @@ def test_null_arguments_are_rejected_without_gpu(api):
     assert api.lib().tddft_solve_tda(None, None, None, None, None, None) == api.ERR_ARG
     assert api.lib().tddft_poll(None, 1, 0) == api.ERR_ARG
     api.lib().tddft_destroy(None)
+    assert api.lib().tddft_server_poll(None, 1, 0) == api.ERR_ARG
+    assert api.lib().tddft_server_submit(None, None, None) == api.ERR_ARG
+    api.lib().tddft_server_destroy(None)
+
+
+def _desc(api, no, nv, na, nj, nk, precisions):
+    d = api.Desc()
+    api.lib().tddft_default_desc(C.byref(d))
+    d.n_occ, d.n_vir, d.n_aux, d.n_aux_ris_J, d.n_aux_ris_K, d.precisions = no, nv, na, nj, nk, precisions
+    return d
+
+
+def test_admission_charge_counts_the_factor_copies(api):
+    """The server's charge for the factor copies, against a plain count of the
+    arrays tddft_create keeps: FP64 copies of L_oo, L_ov, L_vv and of the ris
+    rows (PLAIN); FP32 copies plus BF16 hi+lo tensor-core copies with rows
+    padded to a multiple of 8 elements (16-byte TMA strides) (MIXED: vv, ov^T, oo and ov), BF16 ris
+    rows and their padded copies."""
+    no, nv, na, nj, nk = 12, 70, 300, 54, 6
+    ov = no * nv
+    ris = nj * ov + nk * (no * no + nv * nv + ov)
+    f64, _ = api.estimate_bytes(_desc(api, no, nv, na, nj, nk, 1), 0, api.default_opts())
+    assert f64 == 8 * (na * (no * no + ov + nv * nv) + ris)
+    pad = lambda n: -(-n // 8) * 8
+    padded = nv * (pad(nv) + pad(no)) + no * (pad(no) + pad(nv))
+    fmx, _ = api.estimate_bytes(_desc(api, no, nv, na, nj, nk, 2), 0, api.default_opts(precision=api.MIXED))
+    assert fmx == 4 * na * (no * no + ov + nv * nv) + 4 * na * padded + 2 * ris + 2 * nk * padded
+    both, _ = api.estimate_bytes(_desc(api, no, nv, na, nj, nk, 3), 0, api.default_opts())
+    assert both == f64 + fmx
+
+
+def test_admission_work_charge_grows_with_the_request(api):
+    d = _desc(api, 20, 100, 600, 90, 10, 3)
+    w = lambda kind, **kw: api.estimate_bytes(d, kind, api.default_opts(**kw), 3, 2)[1]
+    assert w(0, n_states=5) < w(0, n_states=20)
+    assert w(0, n_states=5, precond=api.DIAG) < w(0, n_states=5)
+    assert w(0, n_states=5, max_subspace=40) < w(0, n_states=5)
+    assert w(0, n_states=5, precision=api.MIXED) < w(0, n_states=5)
+    with pytest.raises(api.TddftError):
+        api.estimate_bytes(d, 3, api.default_opts())

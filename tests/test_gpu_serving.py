@@ -87,3 +87,143 @@ def test_results_same_alone_and_in_the_mix(api):
     finally:
         for s in solvers:
             s.close()
+
+
+# -- the server: admission of requests that bring their own problem -----------
+
+def _server_requests(api, problems):
+    out = []
+    for pi, p in enumerate(problems):
+        for ri, (kind, o, mu, om) in enumerate(_requests(api, p)):
+            out.append(((pi, ri), p, kind, o, mu, om))
+    return out
+
+
+def _server_wait(srv, t, limit_s=180.0):
+    t0 = time.time()
+    while time.time() - t0 < limit_s:
+        r = srv.poll(t, timeout_ms=100)
+        if r is not None:
+            return r
+    raise AssertionError("server request did not finish within %.0f s" % limit_s)
+
+
+def _same(api, a, b, key):
+    assert a["status"] == b["status"], (key, a["status"], b["status"], b.get("error"))
+    for field in ("omega", "alpha"):
+        if field in a and a[field] is not None:
+            x, y = np.asarray(a[field]), np.asarray(b[field])
+            assert np.max(np.abs(x - y)) <= 1e-12 * max(1.0, np.max(np.abs(x))), (key, field)
+
+
+def test_server_admits_by_budget_and_matches_alone(api):
+    """Twelve requests, each bringing its problem, queued at once on a server of
+    four slots whose budget holds about two requests' charges: the requests
+    start in submission order, the running charges never exceed the budget,
+    some requests run at the same time, and every result equals the one the
+    same request gives alone on its own context."""
+    problems = [make_config("tda_small"), make_problem(3, 7, 5, 9, seeds=(30, 31, 32)),
+                make_problem(7, 33, 37, 27, seeds=(40, 41, 42), amplitude=0.07)]
+    solvers = [api.Solver.from_problem(p) for p in problems]
+    try:
+        alone = _run(solvers, [_requests(api, p) for p in problems], together=False)
+    finally:
+        for s in solvers:
+            s.close()
+    reqs = _server_requests(api, problems)
+    charges = []
+    for key, p, kind, o, mu, om in reqs:
+        d = api._problem_args(**api._problem_kw(p))[0]
+        f, w = api.estimate_bytes(d, kind, o, mu.shape[0] if mu is not None else 0,
+                                  len(om) if om is not None else 0)
+        charges.append(f + w)
+    budget_gb = 2.2 * max(charges) / 1e9
+    srv = api.Server(hbm_budget_gb=budget_gb, max_active=4)
+    try:
+        tickets = [(key, srv.submit(kind, o, problem=p, mu=mu, omegas=om)) for key, p, kind, o, mu, om in reqs]
+        res = {key: _server_wait(srv, t) for key, t in tickets}
+        info = srv.info()
+    finally:
+        srv.close()
+    for key in alone:
+        _same(api, alone[key], res[key], key)
+    order = [res[key] for key, _ in tickets]
+    starts = [r["t_start_s"] for r in order]
+    assert all(a <= b for a, b in zip(starts, starts[1:])), "admission is first in, first out"
+    for i, r in enumerate(order):
+        assert r["charged_bytes"] == charges[i]
+        assert r["t_submit_s"] <= r["t_start_s"] <= r["t_end_s"]
+    budget = info["budget_bytes"]
+    most = 0
+    for r in order:   # charges and slots in use at each admission instant
+        live = [q for q in order if q["t_start_s"] <= r["t_start_s"] < q["t_end_s"]]
+        assert sum(q["charged_bytes"] for q in live) <= budget
+        assert len(live) <= 4
+        most = max(most, len(live))
+    assert most >= 2, "no two requests ran at the same time"
+    assert info["peak_in_use_bytes"] <= budget
+    assert info["in_use_bytes"] == 0 and info["active"] == 0 and info["queued"] == 0
+    assert info["completed"] == len(reqs)
+    print("\nserver: %d requests, budget %.3f GB, at most %d at once, peak charge %.3f GB, "
+          "pool high-water %.3f GB above its use at creation" %
+          (len(reqs), budget / 1e9, most, info["peak_in_use_bytes"] / 1e9,
+           (info["pool_high_bytes"] - info["pool_used_at_create_bytes"]) / 1e9))
+
+
+def test_server_charge_bounds_the_memory_a_request_takes(api):
+    """One request at a time: the pool's high-water mark above its use at
+    server creation stays below the request's charge (factor copies + work)."""
+    p = make_problem(7, 33, 37, 27, seeds=(40, 41, 42), amplitude=0.07)
+    for kind, o, mu, om in _requests(api, p):
+        srv = api.Server(max_active=1)
+        try:
+            r = _server_wait(srv, srv.submit(kind, o, problem=p, mu=mu, omegas=om))
+            info = srv.info()
+        finally:
+            srv.close()
+        assert r["status"] in (api.OK, api.ERR_NOCONV), r.get("error")
+        used = info["pool_high_bytes"] - info["pool_used_at_create_bytes"]
+        assert used <= r["charged_bytes"], (kind, used, r["charged_bytes"])
+
+
+def test_server_refuses_a_request_larger_than_its_budget(api):
+    p = make_config("tda_small")
+    srv = api.Server(hbm_budget_gb=0.01, max_active=2)
+    try:
+        with pytest.raises(api.TddftError) as e:
+            srv.submit(0, api.default_opts(n_states=5), problem=p)
+        assert e.value.status == api.ERR_OOM
+        assert srv.info()["queued"] == 0
+    finally:
+        srv.close()
+
+
+def test_server_on_resident_contexts(api):
+    """Requests naming existing contexts reuse their resident factors and give
+    the results of direct solves on those contexts."""
+    problems = [make_config("tda_small"), make_problem(7, 33, 37, 27, seeds=(40, 41, 42), amplitude=0.07)]
+    solvers = [api.Solver.from_problem(p) for p in problems]
+    srv = api.Server(max_active=3)
+    try:
+        direct, tickets = {}, []
+        for ci, (s, p) in enumerate(zip(solvers, problems)):
+            for ri, (kind, o, mu, om) in enumerate(_requests(api, p)):
+                tickets.append(((ci, ri), srv.submit(kind, o, solver=s, mu=mu, omegas=om)))
+        res = {key: _server_wait(srv, t) for key, t in tickets}
+        for ci, (s, p) in enumerate(zip(solvers, problems)):
+            for ri, (kind, o, mu, om) in enumerate(_requests(api, p)):
+                if kind == 0:
+                    d = s.solve_tda(o, want_vectors=False)
+                elif kind == 1:
+                    d = s.solve_rpa(o, want_vectors=False)
+                else:
+                    d = s.solve_polar(o, mu, om)
+                _same(api, d, res[(ci, ri)], (ci, ri))
+                # resident factors: only the work buffers are charged
+                w = api.estimate_bytes(s.desc, kind, o, mu.shape[0] if mu is not None else 0,
+                                       len(om) if om is not None else 0)[1]
+                assert res[(ci, ri)]["charged_bytes"] == w
+    finally:
+        srv.close()
+        for s in solvers:
+            s.close()
