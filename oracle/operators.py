@@ -50,21 +50,45 @@ def eri_from_factors(L_full: np.ndarray) -> np.ndarray:
     return (flat.T @ flat).reshape(n, n, n, n)
 
 
-def dense_A_B(eps_occ, eps_vir, eri, a_x, c_J):
-    """A and B of Eq. hessian (f^xc = 0) read element by element from (pq|rs).
+def dense_A_B(eps_occ, eps_vir, eri, a_x, c_J, eri_lr=None, b_x=0.0, F_full=None, w=None):
+    """A and B of Eq. hessian read element by element from (pq|rs).
 
     Orbitals are ordered occupied first, so virtual a is orbital n_occ + a.
+    Optional terms (variants of Eq. hessian for other functionals):
+      * eri_lr, b_x: a second exchange integral set, as the long-range
+        (erf-attenuated) exchange of a range-separated hybrid:
+        A -= b_x (ij|ab)_LR, B -= b_x (ib|ja)_LR;
+      * F_full [n_g][n_mo][n_mo], w [n_g]: a low-rank response kernel standing
+        in for f^xc, (pq|f|rs) = sum_g w_g F^g_pq F^g_rs, entering A and B with
+        the Coulomb prefactor: A += c_J (ia|f|jb), B += c_J (ia|f|jb).
+    Without them f^xc = 0.
     """
     no, nv = eps_occ.size, eps_vir.size
     occ = np.arange(no)
     vir = no + np.arange(nv)
-    # (ia|jb), (ij|ab), (ib|ja) as [i, a, j, b] arrays
-    ia_jb = eri[np.ix_(occ, vir, occ, vir)]
-    ij_ab = eri[np.ix_(occ, occ, vir, vir)].transpose(0, 2, 1, 3)
-    ib_ja = eri[np.ix_(occ, vir, occ, vir)].transpose(0, 3, 2, 1)
     ov = no * nv
-    A = c_J * ia_jb.reshape(ov, ov) - a_x * ij_ab.reshape(ov, ov)
-    B = c_J * ia_jb.reshape(ov, ov) - a_x * ib_ja.reshape(ov, ov)
+
+    def blocks(e):
+        # (ia|jb), (ij|ab), (ib|ja) as [ia][jb] matrices
+        ia_jb = e[np.ix_(occ, vir, occ, vir)]
+        ij_ab = e[np.ix_(occ, occ, vir, vir)].transpose(0, 2, 1, 3)
+        ib_ja = e[np.ix_(occ, vir, occ, vir)].transpose(0, 3, 2, 1)
+        return ia_jb.reshape(ov, ov), ij_ab.reshape(ov, ov), ib_ja.reshape(ov, ov)
+
+    ia_jb, ij_ab, ib_ja = blocks(eri)
+    A = c_J * ia_jb - a_x * ij_ab
+    B = c_J * ia_jb - a_x * ib_ja
+    if eri_lr is not None:
+        _, ij_ab_lr, ib_ja_lr = blocks(eri_lr)
+        A -= b_x * ij_ab_lr
+        B -= b_x * ib_ja_lr
+    if F_full is not None:
+        n = F_full.shape[1]
+        flat = F_full.reshape(F_full.shape[0], n * n)
+        fker = (flat.T @ (np.asarray(w)[:, None] * flat)).reshape(n, n, n, n)
+        f_ia_jb = blocks(fker)[0]
+        A += c_J * f_ia_jb
+        B += c_J * f_ia_jb
     A[np.diag_indices(ov)] += delta(eps_occ, eps_vir)
     return A, B
 
@@ -110,13 +134,17 @@ def _chunks(n, size):
         yield p0, min(n, p0 + size)
 
 
-def coulomb(L_ov, X, chunk=256):
-    """J(X)_ia = sum_jb (ia|jb) X_jb = sum_P L^P_ia sum_jb L^P_jb X_jb.  X: [m][ov]."""
+def coulomb(L_ov, X, chunk=256, w=None):
+    """J(X)_ia = sum_jb (ia|jb) X_jb = sum_P L^P_ia sum_jb L^P_jb X_jb.  X: [m][ov].
+    With weights w [n_aux]: sum_P w_P L^P_ia sum_jb L^P_jb X_jb (the low-rank
+    kernel term (ia|f|jb) of dense_A_B)."""
     n_aux = L_ov.shape[0]
     flat = L_ov.reshape(n_aux, -1)
     out = np.zeros_like(X)
     for p0, p1 in _chunks(n_aux, chunk):
         t = flat[p0:p1] @ X.T            # [P][m]
+        if w is not None:
+            t = np.asarray(w)[p0:p1, None] * t
         out += t.T @ flat[p0:p1]
     return out
 
@@ -155,30 +183,43 @@ class Operator:
 
     ``Lx_oo``/``Lx_vv``/``Lx_ov`` are the exchange factor blocks (possibly
     window-restricted, zero outside the window), ``Lj_ov`` the Coulomb block.
+    Optional variant terms (see dense_A_B): ``lr`` = (M_oo, M_ov, M_vv, b_x), a
+    second exchange factor set with its own weight; ``kernel`` = (F_ov, w), the
+    low-rank response kernel, added to the Coulomb term.
     """
 
-    def __init__(self, eps_occ, eps_vir, Lj_ov, Lx_oo, Lx_ov, Lx_vv, a_x, c_J):
+    def __init__(self, eps_occ, eps_vir, Lj_ov, Lx_oo, Lx_ov, Lx_vv, a_x, c_J, lr=None, kernel=None):
         self.d = delta(eps_occ, eps_vir)
         self.Lj_ov, self.Lx_oo, self.Lx_ov, self.Lx_vv = Lj_ov, Lx_oo, Lx_ov, Lx_vv
         self.a_x, self.c_J = a_x, c_J
+        self.lr, self.kernel = lr, kernel
         self.n_occ, self.n_vir = eps_occ.size, eps_vir.size
 
     def _parts(self, X, need_k2):
+        """X, J and the exchange parts K1, K2 with their weight already applied
+        (a_x K[L] + b_x K[M]), so the caller uses exchange weight 1."""
         X = np.atleast_2d(X)
         J = coulomb(self.Lj_ov, X)
-        K1 = exchange_K1(self.Lx_oo, self.Lx_vv, X) if self.a_x != 0.0 else np.zeros_like(X)
-        K2 = exchange_K2(self.Lx_ov, X) if (need_k2 and self.a_x != 0.0) else np.zeros_like(X)
+        if self.kernel is not None:
+            J = J + coulomb(self.kernel[0], X, w=self.kernel[1])
+        K1 = self.a_x * exchange_K1(self.Lx_oo, self.Lx_vv, X) if self.a_x != 0.0 else np.zeros_like(X)
+        K2 = self.a_x * exchange_K2(self.Lx_ov, X) if (need_k2 and self.a_x != 0.0) else np.zeros_like(X)
+        if self.lr is not None and self.lr[3] != 0.0:
+            M_oo, M_ov, M_vv, b_x = self.lr
+            K1 = K1 + b_x * exchange_K1(M_oo, M_vv, X)
+            if need_k2:
+                K2 = K2 + b_x * exchange_K2(M_ov, X)
         return X, J, K1, K2
 
     def tda(self, X):
         """A X with A = Delta + c_J (ia|jb) - a_x (ij|ab)  (Eq. TDA uses A alone)."""
         X, J, K1, _ = self._parts(X, False)
-        return tda_from_parts(self.d, X, J, K1, self.a_x, self.c_J)
+        return tda_from_parts(self.d, X, J, K1, 1.0, self.c_J)
 
     def apb_amb(self, X):
-        """((A+B) X, (A-B) X) from Eq. hessian with f^xc = 0."""
+        """((A+B) X, (A-B) X) from Eq. hessian (f^xc = 0 unless a kernel term is given)."""
         X, J, K1, K2 = self._parts(X, True)
-        return pair_from_parts(self.d, X, J, K1, K2, self.a_x, self.c_J)
+        return pair_from_parts(self.d, X, J, K1, K2, 1.0, self.c_J)
 
 
 def tda_from_parts(d, X, J, K1, a_x, c_J):
@@ -196,9 +237,28 @@ def pair_from_parts(d, X, J, K1, K2, a_x, c_J):
 
 
 def exact_operator(prob) -> Operator:
-    """The ab initio (RI) operator from the exact factors."""
+    """The ab initio (RI) operator from the exact factors, with the problem's
+    optional second exchange set (``extra["exchange_lr"]``: M_oo, M_ov, M_vv,
+    b_x) and low-rank kernel (``extra["kernel"]``: F_ov, w)."""
+    ex = prob.extra or {}
+    lr = ex.get("exchange_lr")
+    ker = ex.get("kernel")
     return Operator(prob.eps_occ, prob.eps_vir, prob.L_ov, prob.L_oo, prob.L_ov, prob.L_vv,
-                    prob.a_x, prob.coulomb_factor)
+                    prob.a_x, prob.coulomb_factor,
+                    lr=(lr["M_oo"], lr["M_ov"], lr["M_vv"], lr["b_x"]) if lr else None,
+                    kernel=(ker["F_ov"], ker["w"]) if ker else None)
+
+
+def dense_exact_A_B(prob):
+    """A and B of the exact operator from four-index tensors (small problems),
+    with the problem's optional variant terms."""
+    ex = prob.extra or {}
+    lr = ex.get("exchange_lr")
+    ker = ex.get("kernel")
+    return dense_A_B(prob.eps_occ, prob.eps_vir, eri_from_factors(ex["L_full"]), prob.a_x,
+                     prob.coulomb_factor,
+                     eri_lr=eri_from_factors(lr["M_full"]) if lr else None, b_x=lr["b_x"] if lr else 0.0,
+                     F_full=ker["F_full"] if ker else None, w=ker["w"] if ker else None)
 
 
 def ris_operator(prob, t_cut=None, K_index=None) -> Operator:

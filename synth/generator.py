@@ -138,6 +138,41 @@ def make_problem(n_occ: int, n_vir: int, n_aux: int, n_ris: int, seeds=(0, 1, 2)
     )
 
 
+def with_variant_terms(prob: Problem, seed: int, n_aux_lr: int = 0, b_x: float = 0.0, n_kernel: int = 0,
+                       lr_scale: float = 0.6, kernel_amp: Optional[float] = None) -> Problem:
+    """Attach the optional variant terms of the response operator to a problem.
+
+    * a second exchange factor set M (``extra["exchange_lr"]``) standing in for the
+      long-range exchange integrals of a range-separated hybrid: n_aux_lr symmetric
+      rows over all orbitals, N(0, 1) upper triangles scaled by lr_scale * amp *
+      exp(-Q / d), d = 60 n_aux_lr / 200, with weight b_x;
+    * a low-rank response kernel (``extra["kernel"]``) standing in for f^xc:
+      n_kernel symmetric rows F^g over all orbitals scaled by kernel_amp *
+      exp(-g / 60), kernel_amp = 0.15 / sqrt(n_occ n_vir) by default (so that a
+      row's contribution w_g |F^g_ov|^2 stays near 0.02 Ha at any size), and
+      weights w_g ~ U(-1, 0.5) (mostly negative, as an exchange-correlation
+      kernel is).
+    Streams: Philox keyed (seed, row) for M, (seed + 1, row) for F, (seed + 2, 0)
+    for w.  The problem's own arrays are shared, not copied."""
+    n_mo = prob.n_occ + prob.n_vir
+    o, v = slice(0, prob.n_occ), slice(prob.n_occ, n_mo)
+    extra = dict(prob.extra)
+    if n_aux_lr > 0:
+        d = 60.0 * n_aux_lr / 200.0
+        sig = lr_scale * prob.amplitude * np.exp(-np.arange(n_aux_lr) / d)
+        M = _symmetric_rows(seed, n_aux_lr, n_mo, sig)
+        extra["exchange_lr"] = dict(M_oo=np.ascontiguousarray(M[:, o, o]), M_ov=np.ascontiguousarray(M[:, o, v]),
+                                    M_vv=np.ascontiguousarray(M[:, v, v]), b_x=float(b_x),
+                                    M_full=M if n_mo <= 80 else None)
+    if n_kernel > 0:
+        ka = 0.15 / math.sqrt(prob.n_occ * prob.n_vir) if kernel_amp is None else kernel_amp
+        sig = ka * np.exp(-np.arange(n_kernel) / 60.0)
+        F = _symmetric_rows(seed + 1, n_kernel, n_mo, sig)
+        w = _rng(seed + 2, 0).uniform(-1.0, 0.5, n_kernel)
+        extra["kernel"] = dict(F_ov=np.ascontiguousarray(F[:, o, v]), w=w, F_full=F if n_mo <= 80 else None)
+    return Problem(**{**prob.__dict__, "extra": extra})
+
+
 def factor_rows(name: str, p0: int, p1: int, **over):
     """Rows [p0, p1) of a named workload's exact factors, drawn exactly as
     make_config draws them (per-row Philox streams), without building the

@@ -16,7 +16,7 @@ from scipy.optimize import brentq
 from oracle import davidson as DV
 from oracle import dense as D
 from oracle import operators as O
-from synth.generator import Problem, dipoles, make_config, make_problem
+from synth.generator import Problem, dipoles, make_config, make_problem, with_variant_terms
 
 TOL = 1e-5
 
@@ -374,3 +374,102 @@ def test_planted_mistakes(small, kind):
                   and np.allclose(p, X @ (A + B), atol=1e-10)
                   and np.allclose(m, X @ (A - B), atol=1e-10))
     assert caught, kind
+
+
+# ---------------------------------------------------------------------------
+# variant terms of Eq. hessian: a second (range-separated) exchange factor set
+# and a low-rank response kernel standing in for f^xc
+
+def _brute_variant(eo, ev, L, M, b_x, F, w, a_x, c_J):
+    """Elements of A and B by explicit loops: the base terms plus
+    -b_x (ij|ab)_M, -b_x (ib|ja)_M and +c_J sum_g w_g F^g_ia F^g_jb."""
+    A, B = _brute_A_B(eo, ev, L, a_x, c_J)
+    no, nv = eo.size, ev.size
+    for i in range(no):
+        for a in range(nv):
+            for j in range(no):
+                for b in range(nv):
+                    I, J = i * nv + a, j * nv + b
+                    A_, B_ = no + a, no + b
+                    lr_ijab = sum(M[Q, i, j] * M[Q, A_, B_] for Q in range(M.shape[0]))
+                    lr_ibja = sum(M[Q, i, B_] * M[Q, j, A_] for Q in range(M.shape[0]))
+                    f = sum(w[g] * F[g, i, A_] * F[g, j, B_] for g in range(F.shape[0]))
+                    A[I, J] += -b_x * lr_ijab + c_J * f
+                    B[I, J] += -b_x * lr_ibja + c_J * f
+    return A, B
+
+
+def test_variant_terms_brute_force():
+    rng = np.random.default_rng(8)
+    no, nv = 2, 3
+    eo = np.sort(rng.uniform(-0.8, -0.3, no))
+    ev = np.sort(rng.uniform(0.05, 1.5, nv))
+    sym = lambda n: (lambda t: t + t.transpose(0, 2, 1))(rng.standard_normal((n, no + nv, no + nv)))
+    L, M, F = sym(2), sym(3), sym(2)
+    w = np.array([-0.7, 0.4])
+    A, B = O.dense_A_B(eo, ev, O.eri_from_factors(L), 0.25, 2.0, eri_lr=O.eri_from_factors(M), b_x=0.6,
+                       F_full=F, w=w)
+    Ab, Bb = _brute_variant(eo, ev, L, M, 0.6, F, w, 0.25, 2.0)
+    assert np.allclose(A, Ab, atol=1e-12) and np.allclose(B, Bb, atol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def variant(small):
+    return with_variant_terms(small, 90, n_aux_lr=60, b_x=0.75, n_kernel=30)
+
+
+def test_variant_matrix_free_equals_dense(variant):
+    A, B = O.dense_exact_A_B(variant)
+    op = O.exact_operator(variant)
+    X = np.random.default_rng(4).standard_normal((3, variant.n_ov))
+    assert np.allclose(op.tda(X), X @ A, atol=1e-12)
+    p, m = op.apb_amb(X)
+    assert np.allclose(p, X @ (A + B), atol=1e-12)
+    assert np.allclose(m, X @ (A - B), atol=1e-12)
+    # both terms change the operator
+    A0, _ = O.dense_exact_A_B(variant.__class__(**{**variant.__dict__, "extra": {"L_full": variant.extra["L_full"]}}))
+    assert np.max(np.abs(A - A0)) > 1e-2
+
+
+def test_variant_special_cases(small):
+    """M = L with weight b_x is the base operator with a_x + b_x; a kernel of
+    the Coulomb rows themselves with w = 1 doubles the Coulomb prefactor, with
+    w = -1 cancels it."""
+    L = small.extra["L_full"]
+    no = small.n_occ
+    o, v = slice(0, no), slice(no, None)
+    eri = O.eri_from_factors(L)
+    X = np.random.default_rng(6).standard_normal((2, small.n_ov))
+    base = lambda a_x, c_J: O.Operator(small.eps_occ, small.eps_vir, small.L_ov, small.L_oo, small.L_ov,
+                                       small.L_vv, a_x, c_J)
+    lr = O.Operator(small.eps_occ, small.eps_vir, small.L_ov, small.L_oo, small.L_ov, small.L_vv, 0.25, 2.0,
+                    lr=(small.L_oo, small.L_ov, small.L_vv, 0.5))
+    for u, r in zip(lr.apb_amb(X), base(0.75, 2.0).apb_amb(X)):
+        assert np.allclose(u, r, atol=1e-12)
+    A, B = O.dense_A_B(small.eps_occ, small.eps_vir, eri, 0.25, 2.0, eri_lr=eri, b_x=0.5)
+    A2, B2 = O.dense_A_B(small.eps_occ, small.eps_vir, eri, 0.75, 2.0)
+    assert np.allclose(A, A2, atol=1e-12) and np.allclose(B, B2, atol=1e-12)
+    n_aux = L.shape[0]
+    for wv, cj in ((1.0, 4.0), (-1.0, 0.0)):
+        k = O.Operator(small.eps_occ, small.eps_vir, small.L_ov, small.L_oo, small.L_ov, small.L_vv, 0.25, 2.0,
+                       kernel=(small.L_ov, np.full(n_aux, wv)))
+        for u, r in zip(k.apb_amb(X), base(0.25, cj).apb_amb(X)):
+            assert np.allclose(u, r, atol=1e-12)
+        A, B = O.dense_A_B(small.eps_occ, small.eps_vir, eri, 0.25, 2.0, F_full=L, w=np.full(n_aux, wv))
+        A2, B2 = O.dense_A_B(small.eps_occ, small.eps_vir, eri, 0.25, cj)
+        assert np.allclose(A, A2, atol=1e-12) and np.allclose(B, B2, atol=1e-12)
+
+
+@pytest.mark.parametrize("pc", ["diag", "rid"])
+def test_variant_davidson_equals_dense(variant, pc):
+    """The preconditioner (T without the variant terms) changes the path, not
+    the converged TDA, Casida and polarizability results."""
+    A, B = O.dense_exact_A_B(variant)
+    op, T = O.exact_operator(variant), O.ris_operator(variant)
+    r = DV.solve_tda(variant, op, T, 5, precond=pc)
+    assert np.allclose(r.omega, D.tda(A, 5)[0], atol=1e-8)
+    r = DV.solve_rpa(variant, op, T, 5, precond=pc)
+    assert np.allclose(r.omega, D.casida(A, B, 5)[0], atol=1e-8)
+    mu = dipoles(3, 2, variant.n_ov)
+    r = DV.solve_polar(variant, op, T, mu, [0.0, 0.05], precond=pc)
+    assert np.allclose(r.alpha, D.polar(A, B, mu, [0.0, 0.05]), rtol=1e-7)
