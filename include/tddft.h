@@ -164,6 +164,32 @@ tddft_status tddft_solve_polar(tddft_ctx* ctx, const tddft_opts* opts, const dou
                                int n_dip, const double* omega, int n_freq, double* alpha,
                                tddft_stats* stats);
 
+/* Variant terms of Eq. hessian for other functionals (the paper's benchmarks
+ * include a range-separated hybrid; the terms keep the same kernels).  Each
+ * may be added once per context, before or between solves; they enter the
+ * exact operator (every product, residual and certification) and not the ris
+ * preconditioner T.
+ *
+ * tddft_add_exchange: a second exchange factor set M (the long-range,
+ * erf-attenuated exchange integrals (pq|rs)_LR = sum_Q M^Q_pq M^Q_rs of a
+ * range-separated hybrid) with weight b_x:
+ *   A -= b_x (ij|ab)_LR,  B -= b_x (ib|ja)_LR.
+ *   M_oo [n_aux_lr][n_occ][n_occ], M_ov [n_aux_lr][n_occ][n_vir],
+ *   M_vv [n_aux_lr][n_vir][n_vir] in `dtype`, copied in the precisions the
+ *   context keeps (the caller keeps ownership).
+ * tddft_add_kernel: a low-rank response kernel in place of f^xc,
+ *   (ia|f|jb) = sum_g w_g F^g_ia F^g_jb, added to A and to B with the Coulomb
+ *   prefactor (c_J (ia|f|jb), as Eq. hessian adds 2 f^xc next to 2 (ia|jb)).
+ *   w [n_g] FP64 (any sign; host or device as inputs_on_device says),
+ *   F_ov [n_g][n_occ][n_vir] in `dtype`.
+ * Errors: TDDFT_ERR_ARG (bad sizes, null pointers, non-finite weight, the term
+ * already present), TDDFT_ERR_INDEFINITE (non-finite factor values).        */
+tddft_status tddft_add_exchange(tddft_ctx* ctx, double b_x, int n_aux_lr, const void* M_oo,
+                                const void* M_ov, const void* M_vv, tddft_dtype dtype,
+                                int inputs_on_device);
+tddft_status tddft_add_kernel(tddft_ctx* ctx, int n_g, const double* w, const void* F_ov,
+                              tddft_dtype dtype, int inputs_on_device);
+
 /* One operator product on m vectors (for tests and measurement):
  *   kind 0: A X (exact), 1: ((A+B)X, (A-B)X) exact, 2: T_A X (ris),
  *   kind 3: ((T_A+T_B)X, (T_A-T_B)X) ris.
@@ -288,7 +314,8 @@ unsigned long long tddft_device_bytes(const tddft_ctx* ctx);
  * memory pool, a real-time loop cannot take an allocation's latency or its
  * out-of-memory failure, or allocation calls are not allowed in the calling
  * context.  This entry point computes the same products as tddft_apply
- * (kinds 0-3, PLAIN = FP64 or MIXED = FP32 SIMT; no tensor-core path) and keeps
+ * (kinds 0-3, PLAIN = FP64 or MIXED = FP32 SIMT; no tensor-core path; a
+ * context with variant terms is refused with TDDFT_ERR_ARG) and keeps
  * every intermediate in one 64 MiB array of device memory that the library
  * declares statically: every GPU that loads the library holds those 64 MiB
  * until the process exits.  It calls no cudaMalloc, cudaFree or allocating

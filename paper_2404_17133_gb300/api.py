@@ -130,13 +130,17 @@ _lib.tddft_server_destroy.argtypes = [_vp]
 _lib.tddft_server_destroy.restype = None
 _lib.tddft_ctx_desc.argtypes = [_vp, C.POINTER(Desc)]
 _lib.tddft_ctx_desc.restype = C.c_int
+_lib.tddft_add_exchange.argtypes = [_vp, C.c_double, _ip, _vp, _vp, _vp, _ip, _ip]
+_lib.tddft_add_exchange.restype = C.c_int
+_lib.tddft_add_kernel.argtypes = [_vp, _ip, _dp, _vp, _ip, _ip]
+_lib.tddft_add_kernel.restype = C.c_int
 
 EXPORTED = ["tddft_default_opts", "tddft_default_desc", "tddft_create", "tddft_solve_tda",
             "tddft_solve_rpa", "tddft_solve_polar", "tddft_apply", "tddft_submit", "tddft_poll",
             "tddft_destroy", "tddft_last_error", "tddft_device_bytes", "tddft_profile",
             "tddft_profile_read", "tddft_apply_noalloc", "tddft_estimate_bytes", "tddft_server_create",
             "tddft_server_submit", "tddft_server_poll", "tddft_server_info", "tddft_server_destroy",
-            "tddft_ctx_desc"]
+            "tddft_ctx_desc", "tddft_add_exchange", "tddft_add_kernel"]
 
 
 class TddftError(RuntimeError):
@@ -256,7 +260,36 @@ class Solver:
 
     @classmethod
     def from_problem(cls, prob, **kw):
-        return cls(**_problem_kw(prob), **kw)
+        """A context for a synthetic problem, with its variant terms if it has any."""
+        s = cls(**_problem_kw(prob), **kw)
+        ex = prob.extra or {}
+        dt = kw.get("dtype", F64)
+        if ex.get("exchange_lr"):
+            lr = ex["exchange_lr"]
+            s.add_exchange(lr["b_x"], lr["M_oo"], lr["M_ov"], lr["M_vv"], dtype=dt)
+        if ex.get("kernel"):
+            s.add_kernel(ex["kernel"]["w"], ex["kernel"]["F_ov"], dtype=dt)
+        return s
+
+    def add_exchange(self, b_x, M_oo, M_ov, M_vv, dtype=F64):
+        """Second exchange factor set with weight b_x (tddft_add_exchange)."""
+        fdt = np.float64 if dtype == F64 else np.float32
+        ptrs = [_ptr(a, fdt) for a in (M_oo, M_ov, M_vv)]
+        st = _lib.tddft_add_exchange(self.h, float(b_x), int(M_ov.shape[0]), *(p for p, _ in ptrs), int(dtype),
+                                     1 if _is_cuda(M_ov) else 0)
+        self._check(st, allow_noconv=False)
+
+    def add_kernel(self, w, F_ov, dtype=F64):
+        """Low-rank kernel sum_g w_g F^g_ia F^g_jb (tddft_add_kernel)."""
+        fdt = np.float64 if dtype == F64 else np.float32
+        on_dev = _is_cuda(F_ov)
+        if on_dev and not _is_cuda(w):   # the weights go where the rows are
+            import torch
+            w = torch.as_tensor(np.asarray(w, dtype=np.float64), device=F_ov.device)
+        pw, kw_ = _ptr(w, np.float64)
+        pf, kf = _ptr(F_ov, fdt)
+        st = _lib.tddft_add_kernel(self.h, int(F_ov.shape[0]), pw, pf, int(dtype), 1 if on_dev else 0)
+        self._check(st, allow_noconv=False)
 
     def _check(self, st, allow_noconv=True):
         if st == OK or (allow_noconv and st == ERR_NOCONV):

@@ -179,6 +179,8 @@ extern "C" tddft_status tddft_apply_noalloc(tddft_ctx* ctx, int kind, int precis
     const bool ris = kind >= 2;
     const bool paired = (kind & 1) != 0;
     FactorSet f = ris ? c->ris(precision) : c->exact(precision);
+    TD_REQUIRE(!f.has_variants(), TDDFT_ERR_ARG,
+               "tddft_apply_noalloc does not apply a second exchange set or a kernel term");
     apply_operator_static(c->dims(), f, X, m, paired ? OpMode::PAIRED : OpMode::TDA, out0,
                           paired ? out1 : nullptr, base, c->s);
     if (prev != c->device) TD_CUDA(cudaSetDevice(prev));

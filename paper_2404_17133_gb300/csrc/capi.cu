@@ -59,6 +59,71 @@ void stage_rows(const void* src, DType tin, bool on_device, long long rows, long
   }
 }
 
+// Device copies of one exact factor set: FP64 (PLAIN) and/or FP32 + BF16 hi/lo
+// tensor-core operands with rows padded for the TMA strides (MIXED).
+void stage_exact(ExactCopies& e, const void* L_oo, const void* L_ov, const void* L_vv, long long A,
+                 DType tin, bool dev, int no, int nv, bool p64, bool pmx, cudaStream_t s) {
+  const long long ov = (long long)no * nv;
+  e.n = (int)A;
+  if (p64) {
+    e.f64_oo = DevBuf(A * no * no * 8, s);
+    e.f64_ov = DevBuf(A * ov * 8, s);
+    e.f64_vv = DevBuf(A * nv * nv * 8, s);
+  }
+  if (pmx) {
+    e.f32_oo = DevBuf(A * no * no * 4, s);
+    e.f32_ov = DevBuf(A * ov * 4, s);
+    e.f32_vv = DevBuf(A * nv * nv * 4, s);
+    e.vv_hi = DevBuf(A * nv * tc_pad(nv) * 2, s);
+    e.vv_lo = DevBuf(A * nv * tc_pad(nv) * 2, s);
+  }
+  auto targets = [&](DevBuf& t64, DevBuf& t32) {
+    std::vector<StageTarget> v;
+    if (p64) v.push_back({t64.p, DType::F64});
+    if (pmx) v.push_back({t32.p, DType::F32});
+    return v;
+  };
+  stage_rows(L_oo, tin, dev, A, (long long)no * no, targets(e.f64_oo, e.f32_oo), s);
+  stage_rows(L_ov, tin, dev, A, ov, targets(e.f64_ov, e.f32_ov), s);
+  stage_rows(L_vv, tin, dev, A, (long long)nv * nv, targets(e.f64_vv, e.f32_vv), s);
+  if (pmx) {
+    tc_split_pad(e.f32_vv.as<float>(), (int)(A * nv), 1, nv, e.vv_hi.as<__nv_bfloat16>(),
+                 e.vv_lo.as<__nv_bfloat16>(), s);
+    e.vo_hi = DevBuf(A * nv * tc_pad(no) * 2, s);
+    e.vo_lo = DevBuf(A * nv * tc_pad(no) * 2, s);
+    tc_transpose_split(e.f32_ov.p, DType::F32, (int)A, no, nv, e.vo_hi.as<__nv_bfloat16>(),
+                       e.vo_lo.as<__nv_bfloat16>(), s);
+    e.oo_hi = DevBuf(A * no * tc_pad(no) * 2, s);
+    e.oo_lo = DevBuf(A * no * tc_pad(no) * 2, s);
+    tc_pad_split(e.f32_oo.p, DType::F32, A * no, no, e.oo_hi.as<__nv_bfloat16>(), e.oo_lo.as<__nv_bfloat16>(),
+                 s);
+    e.ov_hi = DevBuf(A * no * tc_pad(nv) * 2, s);
+    e.ov_lo = DevBuf(A * no * tc_pad(nv) * 2, s);
+    tc_pad_split(e.f32_ov.p, DType::F32, A * no, nv, e.ov_hi.as<__nv_bfloat16>(), e.ov_lo.as<__nv_bfloat16>(),
+                 s);
+  }
+}
+
+// true when every element of the set's widest copy is finite
+bool exact_finite(const ExactCopies& e, int no, int nv, bool p64, cudaStream_t s) {
+  const long long A = e.n, ov = (long long)no * nv;
+  DevBuf flag(4, s);
+  TD_CUDA(cudaMemsetAsync(flag.p, 0, 4, s));
+  if (p64) {
+    check_finite(e.f64_ov.p, DType::F64, A * ov, flag.as<int>(), s);
+    check_finite(e.f64_oo.p, DType::F64, A * no * no, flag.as<int>(), s);
+    check_finite(e.f64_vv.p, DType::F64, A * nv * nv, flag.as<int>(), s);
+  } else {
+    check_finite(e.f32_ov.p, DType::F32, A * ov, flag.as<int>(), s);
+    check_finite(e.f32_oo.p, DType::F32, A * no * no, flag.as<int>(), s);
+    check_finite(e.f32_vv.p, DType::F32, A * nv * nv, flag.as<int>(), s);
+  }
+  int fh = 0;
+  TD_CUDA(cudaMemcpyAsync(&fh, flag.p, 4, cudaMemcpyDeviceToHost, s));
+  TD_CUDA(cudaStreamSynchronize(s));
+  return fh == 0;
+}
+
 void worker_loop(Ctx* c) {
   cudaSetDevice(c->device);
   for (;;) {
@@ -114,25 +179,39 @@ unsigned long long factor_copy_bytes(const tddft_desc& d) {
   return (unsigned long long)bytes;
 }
 
+void ExactCopies::fill(FactorSet& f, int precision, bool coulomb) const {
+  if (precision == TDDFT_PLAIN) {
+    f.dt = DType::F64;
+    if (coulomb) f.Jov = f64_ov.p;
+    f.Koo = f64_oo.p; f.Kvv = f64_vv.p; f.Kov = f64_ov.p;
+  } else {
+    f.dt = DType::F32;
+    if (coulomb) f.Jov = f32_ov.p;
+    f.Koo = f32_oo.p; f.Kvv = f32_vv.p; f.Kov = f32_ov.p;
+    f.Kvv_hi = vv_hi.as<__nv_bfloat16>();
+    f.Kvv_lo = vv_lo.as<__nv_bfloat16>();
+    f.Kvo_hi = vo_hi.as<__nv_bfloat16>();
+    f.Kvo_lo = vo_lo.as<__nv_bfloat16>();
+    f.Koo_hi = oo_hi.as<__nv_bfloat16>();
+    f.Koo_lo = oo_lo.as<__nv_bfloat16>();
+    f.Kovp_hi = ov_hi.as<__nv_bfloat16>();
+    f.Kovp_lo = ov_lo.as<__nv_bfloat16>();
+  }
+}
+
 FactorSet Ctx::exact(int precision) const {
   FactorSet f;
   f.nJ = naux;
   f.nK = naux;
-  if (precision == TDDFT_PLAIN) {
-    f.dt = DType::F64;
-    f.Jov = x64_ov.p; f.Koo = x64_oo.p; f.Kvv = x64_vv.p; f.Kov = x64_ov.p;
-  } else {
-    f.dt = DType::F32;
-    f.Jov = x32_ov.p; f.Koo = x32_oo.p; f.Kvv = x32_vv.p; f.Kov = x32_ov.p;
-    f.Kvv_hi = x16_vv_hi.as<__nv_bfloat16>();
-    f.Kvv_lo = x16_vv_lo.as<__nv_bfloat16>();
-    f.Kvo_hi = x16_vo_hi.as<__nv_bfloat16>();
-    f.Kvo_lo = x16_vo_lo.as<__nv_bfloat16>();
-    f.Koo_hi = x16_oo_hi.as<__nv_bfloat16>();
-    f.Koo_lo = x16_oo_lo.as<__nv_bfloat16>();
-    f.Kovp_hi = x16_ov_hi.as<__nv_bfloat16>();
-    f.Kovp_lo = x16_ov_lo.as<__nv_bfloat16>();
+  x.fill(f, precision, true);
+  const int k = precision == TDDFT_PLAIN ? 0 : 1;
+  if (lrx.n > 0 && b_x != 0.0) {
+    f.lr = &lr_set[k];
+    f.b_x = b_x;
   }
+  const DevBuf* ker = precision == TDDFT_PLAIN ? ker64 : ker32;
+  f.Fpos = ker[0].p; f.nFpos = n_ker[0];
+  f.Fneg = ker[1].p; f.nFneg = n_ker[1];
   return f;
 }
 
@@ -303,43 +382,7 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
 
     // exact factors
     const long long A = d.n_aux;
-    if (p64) {
-      c->x64_oo = DevBuf(A * no * no * 8, s);
-      c->x64_ov = DevBuf(A * ov * 8, s);
-      c->x64_vv = DevBuf(A * nv * nv * 8, s);
-    }
-    if (pmx) {
-      c->x32_oo = DevBuf(A * no * no * 4, s);
-      c->x32_ov = DevBuf(A * ov * 4, s);
-      c->x32_vv = DevBuf(A * nv * nv * 4, s);
-      c->x16_vv_hi = DevBuf(A * nv * tc_pad(nv) * 2, s);
-      c->x16_vv_lo = DevBuf(A * nv * tc_pad(nv) * 2, s);
-    }
-    auto targets = [&](DevBuf& t64, DevBuf& t32) {
-      std::vector<StageTarget> v;
-      if (p64) v.push_back({t64.p, DType::F64});
-      if (pmx) v.push_back({t32.p, DType::F32});
-      return v;
-    };
-    stage_rows(L_oo, tin, dev, A, (long long)no * no, targets(c->x64_oo, c->x32_oo), s);
-    stage_rows(L_ov, tin, dev, A, ov, targets(c->x64_ov, c->x32_ov), s);
-    stage_rows(L_vv, tin, dev, A, (long long)nv * nv, targets(c->x64_vv, c->x32_vv), s);
-    if (pmx) {  // BF16 hi/lo splits of the FP32 copies, rows padded for the TMA strides
-      tc_split_pad(c->x32_vv.as<float>(), (int)(A * nv), 1, nv, c->x16_vv_hi.as<__nv_bfloat16>(),
-                   c->x16_vv_lo.as<__nv_bfloat16>(), s);
-      c->x16_vo_hi = DevBuf(A * nv * tc_pad(no) * 2, s);
-      c->x16_vo_lo = DevBuf(A * nv * tc_pad(no) * 2, s);
-      tc_transpose_split(c->x32_ov.p, DType::F32, (int)A, no, nv, c->x16_vo_hi.as<__nv_bfloat16>(),
-                         c->x16_vo_lo.as<__nv_bfloat16>(), s);
-      c->x16_oo_hi = DevBuf(A * no * tc_pad(no) * 2, s);
-      c->x16_oo_lo = DevBuf(A * no * tc_pad(no) * 2, s);
-      tc_pad_split(c->x32_oo.p, DType::F32, A * no, no, c->x16_oo_hi.as<__nv_bfloat16>(),
-                   c->x16_oo_lo.as<__nv_bfloat16>(), s);
-      c->x16_ov_hi = DevBuf(A * no * tc_pad(nv) * 2, s);
-      c->x16_ov_lo = DevBuf(A * no * tc_pad(nv) * 2, s);
-      tc_pad_split(c->x32_ov.p, DType::F32, A * no, nv, c->x16_ov_hi.as<__nv_bfloat16>(),
-                   c->x16_ov_lo.as<__nv_bfloat16>(), s);
-    }
+    stage_exact(c->x, L_oo, L_ov, L_vv, A, tin, dev, no, nv, p64, pmx, s);
 
     // ris factors (Coulomb rows all; exchange rows windowed, Sec. 3.1)
     const long long RJ = d.n_aux_ris_J, RK = d.n_aux_ris_K;
@@ -409,19 +452,7 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
     {
       DevBuf flag(4, s);
       TD_CUDA(cudaMemsetAsync(flag.p, 0, 4, s));
-      if (p64) {
-        check_finite(c->x64_ov.p, DType::F64, A * ov, flag.as<int>(), s);
-        check_finite(c->x64_oo.p, DType::F64, A * no * no, flag.as<int>(), s);
-        check_finite(c->x64_vv.p, DType::F64, A * nv * nv, flag.as<int>(), s);
-      } else {
-        check_finite(c->x32_ov.p, DType::F32, A * ov, flag.as<int>(), s);
-        check_finite(c->x32_oo.p, DType::F32, A * no * no, flag.as<int>(), s);
-        check_finite(c->x32_vv.p, DType::F32, A * nv * nv, flag.as<int>(), s);
-      }
-      int fh = 0;
-      TD_CUDA(cudaMemcpyAsync(&fh, flag.p, 4, cudaMemcpyDeviceToHost, s));
-      TD_CUDA(cudaStreamSynchronize(s));
-      TD_REQUIRE(fh == 0, TDDFT_ERR_INDEFINITE, "non-finite values in the factors");
+      TD_REQUIRE(exact_finite(c->x, no, nv, p64, s), TDDFT_ERR_INDEFINITE, "non-finite values in the factors");
     }
     c->worker = std::thread(worker_loop, c);
     *out = reinterpret_cast<tddft_ctx*>(c);
@@ -597,6 +628,102 @@ tddft_status tddft_profile_read(const tddft_ctx* ctx, int which, long long* laun
     if (launches) *launches = kp.launches;
     if (ms) *ms = kp.ms;
     if (flops) *flops = kp.flops;
+    return TDDFT_OK;
+  })
+}
+
+tddft_status tddft_add_exchange(tddft_ctx* ctx, double b_x, int n_aux_lr, const void* M_oo, const void* M_ov,
+                                const void* M_vv, tddft_dtype dtype, int inputs_on_device) {
+  TD_API_BODY(ctx, {
+    TD_REQUIRE(n_aux_lr >= 1 && M_oo && M_ov && M_vv, TDDFT_ERR_ARG, "bad second exchange set");
+    TD_REQUIRE(std::isfinite(b_x), TDDFT_ERR_ARG, "non-finite b_x");
+    TD_REQUIRE(dtype == TDDFT_F64 || dtype == TDDFT_F32, TDDFT_ERR_ARG, "unknown dtype");
+    std::lock_guard<std::mutex> run(c->run_mu);
+    TD_REQUIRE(c->lrx.n == 0, TDDFT_ERR_ARG, "the context already has a second exchange set");
+    cudaStream_t s = c->s;
+    const bool p64 = c->precisions & 1, pmx = c->precisions & 2;
+    ExactCopies e;
+    stage_exact(e, M_oo, M_ov, M_vv, n_aux_lr, dtype == TDDFT_F64 ? DType::F64 : DType::F32,
+                inputs_on_device != 0, c->no, c->nv, p64, pmx, s);
+    TD_REQUIRE(exact_finite(e, c->no, c->nv, p64, s), TDDFT_ERR_INDEFINITE,
+               "non-finite values in the second exchange set");
+    c->lrx = std::move(e);
+    c->b_x = b_x;
+    for (int k = 0; k < 2; ++k) {
+      FactorSet f;
+      f.nJ = 0;
+      f.nK = n_aux_lr;
+      if ((k == 0 && p64) || (k == 1 && pmx)) c->lrx.fill(f, k == 0 ? TDDFT_PLAIN : TDDFT_MIXED, false);
+      c->lr_set[k] = f;
+    }
+    tddft_desc dl = c->desc;
+    dl.n_aux = n_aux_lr;
+    dl.n_aux_ris_J = dl.n_aux_ris_K = 0;
+    c->device_bytes += factor_copy_bytes(dl);
+    return TDDFT_OK;
+  })
+}
+
+tddft_status tddft_add_kernel(tddft_ctx* ctx, int n_g, const double* w, const void* F_ov, tddft_dtype dtype,
+                              int inputs_on_device) {
+  TD_API_BODY(ctx, {
+    TD_REQUIRE(n_g >= 1 && w && F_ov, TDDFT_ERR_ARG, "bad kernel term");
+    TD_REQUIRE(dtype == TDDFT_F64 || dtype == TDDFT_F32, TDDFT_ERR_ARG, "unknown dtype");
+    std::lock_guard<std::mutex> run(c->run_mu);
+    TD_REQUIRE(c->n_ker[0] + c->n_ker[1] == 0, TDDFT_ERR_ARG, "the context already has a kernel term");
+    cudaStream_t s = c->s;
+    const long long ov = c->ov;
+    std::vector<double> wh(n_g);
+    if (inputs_on_device) {
+      TD_CUDA(cudaMemcpyAsync(wh.data(), w, (size_t)n_g * 8, cudaMemcpyDeviceToHost, s));
+      TD_CUDA(cudaStreamSynchronize(s));
+    } else {
+      std::memcpy(wh.data(), w, (size_t)n_g * 8);
+    }
+    for (double x : wh) TD_REQUIRE(std::isfinite(x), TDDFT_ERR_ARG, "non-finite kernel weight");
+    // every row in FP64, then per sign: gather, scale by sqrt|w|, keep the copies
+    DevBuf all((size_t)n_g * ov * 8, s);
+    stage_rows(F_ov, dtype == TDDFT_F64 ? DType::F64 : DType::F32, inputs_on_device != 0, n_g, ov,
+               {{all.p, DType::F64}}, s);
+    {
+      DevBuf flag(4, s);
+      TD_CUDA(cudaMemsetAsync(flag.p, 0, 4, s));
+      check_finite(all.p, DType::F64, (long long)n_g * ov, flag.as<int>(), s);
+      int fh = 0;
+      TD_CUDA(cudaMemcpyAsync(&fh, flag.p, 4, cudaMemcpyDeviceToHost, s));
+      TD_CUDA(cudaStreamSynchronize(s));
+      TD_REQUIRE(fh == 0, TDDFT_ERR_INDEFINITE, "non-finite values in the kernel rows");
+    }
+    const bool p64 = c->precisions & 1, pmx = c->precisions & 2;
+    unsigned long long bytes = 0;
+    for (int k = 0; k < 2; ++k) {
+      std::vector<int> idx;
+      std::vector<double> sc;
+      for (int g = 0; g < n_g; ++g)
+        if (k == 0 ? wh[g] > 0.0 : wh[g] < 0.0) {
+          idx.push_back(g);
+          sc.push_back(std::sqrt(std::fabs(wh[g])));
+        }
+      const int n = (int)idx.size();
+      if (n == 0) continue;
+      DevBuf di(n * 4, s), ds(n * 8, s), rows((size_t)n * ov * 8, s);
+      TD_CUDA(cudaMemcpyAsync(di.p, idx.data(), n * 4, cudaMemcpyHostToDevice, s));
+      TD_CUDA(cudaMemcpyAsync(ds.p, sc.data(), n * 8, cudaMemcpyHostToDevice, s));
+      gather_rows(all.as<double>(), di.as<int>(), n, (int)ov, rows.as<double>(), s);
+      scale_rows(rows.as<double>(), ds.as<double>(), n, (int)ov, s);
+      if (pmx) {
+        c->ker32[k] = DevBuf((size_t)n * ov * 4, s);
+        convert(rows.p, DType::F64, c->ker32[k].p, DType::F32, (long long)n * ov, s);
+        bytes += (unsigned long long)n * ov * 4;
+      }
+      if (p64) {
+        c->ker64[k] = std::move(rows);
+        bytes += (unsigned long long)n * ov * 8;
+      }
+      TD_CUDA(cudaStreamSynchronize(s));   // the host vectors above are copied from
+      c->n_ker[k] = n;
+    }
+    c->device_bytes += bytes;
     return TDDFT_OK;
   })
 }

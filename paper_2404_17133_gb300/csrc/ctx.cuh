@@ -34,6 +34,30 @@ struct FactorSet {
   const __nv_bfloat16* Koo_lo = nullptr;
   const __nv_bfloat16* Kovp_hi = nullptr;
   const __nv_bfloat16* Kovp_lo = nullptr;
+  // Variant terms of the exact operator (Eq. hessian for other functionals):
+  // a second exchange factor set entering with weight b_x, and a low-rank
+  // kernel sum_g w_g F^g_ia F^g_jb added to the Coulomb term, its rows stored
+  // scaled by sqrt|w_g| and split by the sign of w_g (element type dt).
+  const FactorSet* lr = nullptr;
+  double b_x = 0.0;
+  const void* Fpos = nullptr;
+  const void* Fneg = nullptr;
+  int nFpos = 0, nFneg = 0;
+  bool has_variants() const { return (lr && b_x != 0.0) || nFpos > 0 || nFneg > 0; }
+};
+
+// Device copies of one exact factor set (L_oo, L_ov, L_vv with n rows) in the
+// precisions a context keeps.
+struct ExactCopies {
+  int n = 0;
+  DevBuf f64_oo, f64_ov, f64_vv;  // PLAIN
+  DevBuf f32_oo, f32_ov, f32_vv;  // MIXED: SIMT operands and the FP32 re-certification
+  DevBuf vv_hi, vv_lo;            // [n][nv][tc_pad(nv)] BF16 split of L_vv
+  DevBuf vo_hi, vo_lo;            // [n][nv][tc_pad(no)] BF16 split of L_ov transposed
+  DevBuf oo_hi, oo_lo;            // [n][no][tc_pad(no)]
+  DevBuf ov_hi, ov_lo;            // [n][no][tc_pad(nv)]
+  // Exchange operands of `precision` into f (and the Coulomb block when coulomb).
+  void fill(FactorSet& f, int precision, bool coulomb) const;
 };
 
 // Event-based timing of one kernel family (the dominant contraction).
@@ -91,12 +115,13 @@ struct Ctx {
   DevBuf order;                   // int32 indices of Delta ascending (first n_order)
   int n_order = 0;
   // exact factors
-  DevBuf x64_oo, x64_ov, x64_vv;
-  DevBuf x32_oo, x32_ov, x32_vv;
-  DevBuf x16_vv_hi, x16_vv_lo;   // [naux][nv][tc_pad(nv)] BF16 split of L_vv
-  DevBuf x16_vo_hi, x16_vo_lo;   // [naux][nv][tc_pad(no)] BF16 split of L_ov transposed
-  DevBuf x16_oo_hi, x16_oo_lo;   // [naux][no][tc_pad(no)]
-  DevBuf x16_ov_hi, x16_ov_lo;   // [naux][no][tc_pad(nv)]
+  ExactCopies x;
+  // variant terms (tddft_add_exchange, tddft_add_kernel)
+  ExactCopies lrx;                // second exchange set, n = 0 if none
+  double b_x = 0.0;
+  FactorSet lr_set[2];            // PLAIN and MIXED views of lrx
+  DevBuf ker64[2], ker32[2];      // kernel rows scaled by sqrt|w|: w > 0, w < 0
+  int n_ker[2] = {0, 0};
   DevBuf tc_err;                  // int flag, see OpDims::tc_err
   // ris factors: Coulomb ov (all rows), exchange oo/vv/ov (s rows, windowed)
   DevBuf r64_J, r64_Koo, r64_Kvv, r64_Kov;

@@ -99,20 +99,35 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
     Xw = xbuf.p;
   }
 
-  // ---- Coulomb
+  // ---- Coulomb (and the low-rank kernel term, which enters with the same prefactor)
   DevBuf Jb;
+  bool have_J = false;
   if (f.nJ > 0 && d.c_J != 0.0) {
     // t[P][n] = sum_ia L_ov[P][ia] X[n][ia];  J[n][ia] = sum_P t[P][n] L_ov[P][ia]
     DevBuf t((size_t)f.nJ * m * ew, s);
     Jb = DevBuf(mov * ew, s);
     sk_gram(f.Jov, f.dt, ov, f.nJ, Xw, tw, ov, m, ov, t.p, tw, m, 1.0, 0.0, s);
     sk_combo(t.p, tw, 1, m, m, f.nJ, f.Jov, f.dt, ov, ov, Jb.p, tw, ov, 1.0, 0.0, s);
+    have_J = true;
+  }
+  if (d.c_J != 0.0) {
+    // sum_g w_g F^g_ia (F^g . X): rows stored as sqrt|w_g| F^g, one pass per sign
+    const void* Fr[2] = {f.Fpos, f.Fneg};
+    const int nr[2] = {f.nFpos, f.nFneg};
+    for (int k = 0; k < 2; ++k) {
+      if (nr[k] <= 0) continue;
+      if (!have_J) Jb = DevBuf(mov * ew, s);
+      DevBuf t((size_t)nr[k] * m * ew, s);
+      sk_gram(Fr[k], f.dt, ov, nr[k], Xw, tw, ov, m, ov, t.p, tw, m, 1.0, 0.0, s);
+      sk_combo(t.p, tw, 1, m, m, nr[k], Fr[k], f.dt, ov, ov, Jb.p, tw, ov, k == 0 ? 1.0 : -1.0,
+               have_J ? 1.0 : 0.0, s);
+      have_J = true;
+    }
   }
 
-  // ---- exchange
-  DevBuf K1b, K2b;
+  // ---- exchange: K1 (and K2 for the paired products) of one factor set
   const bool need_k2 = (mode == OpMode::PAIRED);
-  if (f.nK > 0 && d.a_x != 0.0) {
+  auto exchange = [&](const FactorSet& f, DevBuf& K1b, DevBuf& K2b) {
     K1b = DevBuf(mov * ew, s);
     if (need_k2) K2b = DevBuf(mov * ew, s);
     const bool use_tc = tensor_cores && !f64 && f.Kvv_hi && f.Kvo_hi && f.Koo_hi && f.Kovp_hi;
@@ -216,6 +231,22 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
         }
       }
     }
+  };
+  DevBuf K1b, K2b;
+  double kx = d.a_x;   // weight of the exchange parts in the final combination
+  if (f.nK > 0 && d.a_x != 0.0) exchange(f, K1b, K2b);
+  if (f.lr && f.b_x != 0.0 && f.lr->nK > 0) {
+    // second exchange set: K = a_x K[L] + b_x K[M], combined with weight 1
+    DevBuf L1, L2;
+    exchange(*f.lr, L1, L2);
+    const bool have = K1b.p != nullptr;
+    if (!have) {
+      K1b = DevBuf(mov * ew, s);
+      if (need_k2) K2b = DevBuf(mov * ew, s);
+    }
+    axpby(K1b.p, L1.p, tw, have ? d.a_x : 0.0, f.b_x, mov, s);
+    if (need_k2) axpby(K2b.p, L2.p, tw, have ? d.a_x : 0.0, f.b_x, mov, s);
+    kx = 1.0;
   }
 
   const void* J = Jb.p;
@@ -226,17 +257,17 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
     const float* K1f = static_cast<const float*>(K1);
     const float* K2f = static_cast<const float*>(K2);
     if (mode == OpMode::TDA) {
-      combine_f32(X, d.delta, Jf, K1f, nullptr, d.c_J, -d.a_x, 0.0, m, ov, out0, s);
+      combine_f32(X, d.delta, Jf, K1f, nullptr, d.c_J, -kx, 0.0, m, ov, out0, s);
     } else {
-      combine_f32(X, d.delta, Jf, K1f, K2f, 2.0 * d.c_J, -d.a_x, -d.a_x, m, ov, out0, s);
-      combine_f32(X, d.delta, nullptr, K1f, K2f, 0.0, -d.a_x, d.a_x, m, ov, out1, s);
+      combine_f32(X, d.delta, Jf, K1f, K2f, 2.0 * d.c_J, -kx, -kx, m, ov, out0, s);
+      combine_f32(X, d.delta, nullptr, K1f, K2f, 0.0, -kx, kx, m, ov, out1, s);
     }
   } else {
     if (mode == OpMode::TDA) {
-      combine(X, d.delta, J, K1, nullptr, tw, d.c_J, -d.a_x, 0.0, m, ov, out0, s);
+      combine(X, d.delta, J, K1, nullptr, tw, d.c_J, -kx, 0.0, m, ov, out0, s);
     } else {
-      combine(X, d.delta, J, K1, K2, tw, 2.0 * d.c_J, -d.a_x, -d.a_x, m, ov, out0, s);
-      combine(X, d.delta, nullptr, K1, K2, tw, 0.0, -d.a_x, d.a_x, m, ov, out1, s);
+      combine(X, d.delta, J, K1, K2, tw, 2.0 * d.c_J, -kx, -kx, m, ov, out0, s);
+      combine(X, d.delta, nullptr, K1, K2, tw, 0.0, -kx, kx, m, ov, out1, s);
     }
   }
 }

@@ -187,6 +187,13 @@ __global__ void k_scale_rows(T* X, const double* sc, int k, int n) {
     X[t] = (T)((double)X[t] * sc[t / n]);
 }
 
+// y = a y + b x (y is not read when a == 0)
+template <typename T>
+__global__ void k_axpby(T* y, const T* x, double a, double b, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    y[t] = (T)(a == 0.0 ? b * (double)x[t] : a * (double)y[t] + b * (double)x[t]);
+}
+
 template <typename TI, typename TO>
 __global__ void k_convert(const TI* in, TO* out, long long n) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
@@ -348,6 +355,15 @@ void scale_rows(T* X, const double* sc, int k, int n, cudaStream_t s) {
   k_scale_rows<T><<<TD_GRID((long long)k * n)>>>(X, sc, k, n);
   count_launch(); TD_LAUNCH_CHECK();
 }
+void axpby(void* y, const void* x, DType t, double a, double b, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  if (t == DType::F64) k_axpby<double><<<TD_GRID(n)>>>((double*)y, (const double*)x, a, b, n);
+  else if (t == DType::F32) k_axpby<float><<<TD_GRID(n)>>>((float*)y, (const float*)x, a, b, n);
+  else throw Error(TDDFT_ERR_ARG, "axpby: FP64 or FP32 only");
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
 template void scale_rows<double>(double*, const double*, int, int, cudaStream_t);
 template void scale_rows<float>(float*, const double*, int, int, cudaStream_t);
 void cast_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s) {

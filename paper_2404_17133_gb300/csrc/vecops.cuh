@@ -49,6 +49,9 @@ void sym_fill(S* a, int ld, int n_old, int n_new, cudaStream_t s);
 template <typename T>
 void scale_rows(T* X, const double* scale, int k, int n, cudaStream_t s);
 // conversions
+// y = a y + b x over n elements of type t (F64 or F32); y is not read when a == 0.
+void axpby(void* y, const void* x, DType t, double a, double b, long long n, cudaStream_t s);
+
 void cast_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s);
 void cast_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s);
 void cast_to_bf16(const void* in, DType tin, __nv_bfloat16* out, long long n, cudaStream_t s);
