@@ -20,6 +20,12 @@ plain: the same step in the plain FP64 form on the same GPU (FP64 factors,
 Inputs (the FP32/BF16 factors, 2.8 GB) are larger than L2, so no L2 flush is
 added between steps.
 
+serving: an open-loop Poisson stream of TDA / Casida / polarizability requests
+       of random sizes through the server API (each request brings its own
+       device-resident problem), p50/p99 latency and states/s (--serve-*).
+batched: 256 small independent TDA solves queued at once on the server
+       (solves/s; --batch*).
+
 Multi-GPU: one independent replica per GPU (the path does not shard on one
 box), launched under torch.distributed.run; rank 0 prints one JSON line.
 
@@ -67,7 +73,9 @@ def parse():
                     help="length of the served request stream (0: no serving measurement)")
     ap.add_argument("--serve-rate", type=float, default=30.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-max-occ", type=int, default=40, help="largest n_occ of a served request")
-    ap.add_argument("--serve-slots", type=int, default=8, help="requests running at once")
+    ap.add_argument("--serve-slots", type=int, default=16, help="requests running at once")
+    ap.add_argument("--batch", type=int, default=256, help="independent small TDA solves queued at once (0: none)")
+    ap.add_argument("--batch-slots", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--apply-only", type=int, default=0, metavar="K",
                     help="time K exact pair products ((A+B)X, (A-B)X) of 2*n_states device vectors "
@@ -371,6 +379,11 @@ def our_arm(args, rank, world, local):
             line["serving"] = serving(args, api, torch)
         except Exception as e:   # the served stream is reported, not required for the line
             line["serving"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    if args.batch > 0 and world == 1:
+        try:
+            line["batched"] = batched(args, api, torch)
+        except Exception as e:
+            line["batched"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if not args.no_cpu_baseline and world == 1:
         step_s, desc, cores = oracle_sample()
         line["cpu_baseline"] = {"value": N_STATES / step_s, "unit": UNIT, "cores": cores,
@@ -379,6 +392,70 @@ def our_arm(args, rank, world, local):
     solver.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _run_stream(api, reqs, arrivals, slots, budget_gb, warm_kw):
+    """Submit reqs[i] = (kind, opts, create_kw, mu, omegas) at arrivals[i] seconds
+    (open loop) to a server; returns the finished (request index, result) pairs,
+    the server's state and the number left unfinished."""
+    from synth.generator import dipoles
+
+    srv = api.Server(hbm_budget_gb=budget_gb, max_active=slots)
+    try:
+        # warm-up: one request of each kind on a small problem (untimed)
+        ws = [srv.submit(k, api.default_opts(n_states=5, precond=api.RID, precision=api.MIXED, tensor_cores=1),
+                         create_kw=dict(warm_kw, precisions=2, dtype=api.F32),
+                         mu=dipoles(1, 3, warm_kw["n_occ"] * warm_kw["n_vir"]) if k == 2 else None,
+                         omegas=[0.0, 0.05] if k == 2 else None) for k in (0, 1, 2)]
+        for t in ws:
+            while srv.poll(t, timeout_ms=100) is None:
+                pass
+        done, pending = [], {}
+        t0 = time.perf_counter()
+        i, n = 0, len(reqs)
+        limit = float(arrivals[-1]) + 300.0 if n else 0.0
+        while i < n or pending:
+            now = time.perf_counter() - t0
+            while i < n and arrivals[i] <= now:
+                kind, o, kw, mu, om = reqs[i]
+                t = srv.submit(kind, o, create_kw=dict(kw, precisions=2, dtype=api.F32), mu=mu, omegas=om)
+                pending[t] = i
+                i += 1
+            for t in list(pending):
+                r = srv.poll(t, timeout_ms=0)
+                if r is not None:
+                    done.append((pending.pop(t), r))
+            if now > limit:
+                break
+            time.sleep(0.001)
+        info = srv.info()
+    finally:
+        srv.close()
+    return done, info, len(pending)
+
+
+def _stream_report(api, reqs, done, info, unfinished):
+    pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))]
+    lat = sorted(r["latency_s"] * 1e3 for _, r in done)
+    wait = sorted((r["t_start_s"] - r["t_submit_s"]) * 1e3 for _, r in done)
+    span = max(r["t_end_s"] for _, r in done) - min(r["t_submit_s"] for _, r in done)
+    ok = [(i, r) for i, r in done if r["status"] == api.OK]
+    states = sum(reqs[i][1].n_states for i, r in ok if reqs[i][0] in (0, 1))
+    starts = sorted(r["t_start_s"] for _, r in done)
+    most = max(sum(1 for _, q in done if q["t_start_s"] <= t < q["t_end_s"]) for t in starts)
+    by_kind = {}
+    for i, r in done:
+        by_kind.setdefault(reqs[i][0], []).append(r["latency_s"] * 1e3)
+    return {"requests": len(reqs), "finished": len(done), "ok": len(ok),
+            "noconv": sum(1 for _, r in done if r["status"] == api.ERR_NOCONV),
+            "errors": sum(1 for _, r in done if r["status"] not in (api.OK, api.ERR_NOCONV)),
+            "unfinished": unfinished, "span_s": span, "states_per_s": states / span,
+            "solves_per_s": len(ok) / span, "p50_ms": pct(lat, 0.50), "p99_ms": pct(lat, 0.99),
+            "queue_wait_p50_ms": pct(wait, 0.50), "queue_wait_p99_ms": pct(wait, 0.99),
+            "p50_ms_by_kind": {("tda", "casida", "polar")[k]: statistics.median(v) for k, v in by_kind.items()},
+            "max_concurrent": most, "budget_gb": info["budget_bytes"] / 1e9,
+            "peak_charge_gb": info["peak_in_use_bytes"] / 1e9,
+            "pool_high_gb": (info["pool_high_bytes"] - info["pool_used_at_create_bytes"]) / 1e9}
 
 
 def serving(args, api, torch):
@@ -415,65 +492,51 @@ def serving(args, api, torch):
             o = api.default_opts(n_states=min(m["n_states"], ov), precond=api.RID, precision=api.MIXED,
                                  tensor_cores=1)
             reqs.append((kind, o, kw, None, None))
-    srv = api.Server(hbm_budget_gb=args.serve_budget_gb, max_active=args.serve_slots)
-    try:
-        # warm-up: one request of each kind on the smallest pooled problem (untimed)
-        small = min(pool, key=lambda k: k["n_occ"] * k["n_vir"])
-        ws = [srv.submit(k, api.default_opts(n_states=5, precond=api.RID, precision=api.MIXED, tensor_cores=1),
-                         create_kw=dict(small, precisions=2, dtype=api.F32),
-                         mu=dipoles(1, 3, small["n_occ"] * small["n_vir"]) if k == 2 else None,
-                         omegas=[0.0, 0.05] if k == 2 else None) for k in (0, 1, 2)]
-        for t in ws:
-            while srv.poll(t, timeout_ms=100) is None:
-                pass
-        done, pending = [], {}
-        t0 = time.perf_counter()
-        i = 0
-        limit = args.serve_seconds + 300.0
-        while i < n_req or pending:
-            now = time.perf_counter() - t0
-            while i < n_req and arrivals[i] <= now:
-                kind, o, kw, mu, om = reqs[i]
-                t = srv.submit(kind, o, create_kw=dict(kw, precisions=2, dtype=api.F32), mu=mu, omegas=om)
-                pending[t] = (i, kind, o.n_states)
-                i += 1
-            for t in list(pending):
-                r = srv.poll(t, timeout_ms=0)
-                if r is not None:
-                    done.append((pending.pop(t), r))
-            if now > limit:
-                break
-            time.sleep(0.001)
-        info = srv.info()
-    finally:
-        srv.close()
+    warm = min(pool, key=lambda k: k["n_occ"] * k["n_vir"])
+    done, info, left = _run_stream(api, reqs, arrivals, args.serve_slots, args.serve_budget_gb, warm)
     if not done:
         return {"error": "no request finished"}
-    lat = sorted(r["latency_s"] * 1e3 for _, r in done)
-    wait = sorted((r["t_start_s"] - r["t_submit_s"]) * 1e3 for _, r in done)
-    pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))]
-    span = max(r["t_end_s"] for _, r in done) - min(r["t_submit_s"] for _, r in done)
-    ok = [(m, r) for m, r in done if r["status"] == api.OK]
-    states = sum(m[2] for m, r in ok if m[1] in (0, 1))
-    starts = sorted(r["t_start_s"] for _, r in done)
-    most = max(sum(1 for _, q in done if q["t_start_s"] <= t < q["t_end_s"]) for t in starts)
-    by_kind = {}
-    for (i, kind, _), r in done:
-        by_kind.setdefault(kind, []).append(r["latency_s"] * 1e3)
-    return {"requests": n_req, "finished": len(done), "ok": len(ok),
-            "noconv": sum(1 for _, r in done if r["status"] == api.ERR_NOCONV),
-            "errors": sum(1 for _, r in done if r["status"] not in (api.OK, api.ERR_NOCONV)),
-            "unfinished": len(pending), "offered_rate_req_s": args.serve_rate, "seconds": args.serve_seconds,
-            "span_s": span, "states_per_s": states / span, "solves_per_s": len(ok) / span,
-            "p50_ms": pct(lat, 0.50), "p99_ms": pct(lat, 0.99), "queue_wait_p50_ms": pct(wait, 0.50),
-            "queue_wait_p99_ms": pct(wait, 0.99),
-            "p50_ms_by_kind": {("tda", "casida", "polar")[k]: statistics.median(v) for k, v in by_kind.items()},
-            "max_concurrent": most, "slots": args.serve_slots, "budget_gb": info["budget_bytes"] / 1e9,
-            "peak_charge_gb": info["peak_in_use_bytes"] / 1e9,
-            "pool_high_gb": (info["pool_high_bytes"] - info["pool_used_at_create_bytes"]) / 1e9,
-            "n_occ_range": [10, args.serve_max_occ], "distinct_problems": n_pool,
-            "note": "each request creates its context from FP32 device arrays (precisions=MIXED only), "
-                    "solves, destroys it; MIXED + tcgen05 + rid; latency = finish - submit"}
+    out = _stream_report(api, reqs, done, info, left)
+    out.update({"offered_rate_req_s": args.serve_rate, "seconds": args.serve_seconds, "slots": args.serve_slots,
+                "n_occ_range": [10, args.serve_max_occ], "distinct_problems": n_pool,
+                "note": "each request creates its context from FP32 device arrays (MIXED copies only), "
+                        "solves, destroys it; MIXED + tcgen05 + rid; latency = finish - submit"})
+    return out
+
+
+def batched(args, api, torch):
+    """Many small independent TDA solves submitted together: n_occ ~ U{8..64},
+    n_vir = n_occ x U{4..8}, n_aux = 5 n_mo, ris n_aux = 9 ceil(n_occ/2), 5-10
+    states, MIXED (FP32 outer products on the SIMT path, BF16 ris), rid; all
+    queued at time 0 on a server with --batch-slots slots (concurrent streams,
+    not one persistent kernel).  Throughput = solves / (first submit to last
+    finish)."""
+    from synth.device import problem_kw
+
+    g = np.random.Generator(np.random.Philox(key=np.array([2405, 1], dtype=np.uint64)))
+    n = args.batch
+    sizes = []
+    for _ in range(n):
+        no = int(g.integers(8, 65))
+        nv = no * int(g.integers(4, 9))
+        sizes.append((no, nv, 5 * (no + nv), 9 * ((no + 1) // 2), int(g.integers(5, 11))))
+    n_pool = min(64, n)
+    pool = [problem_kw(3000 + i, *sizes[i][:4]) for i in range(n_pool)]
+    torch.cuda.synchronize()
+    reqs = []
+    for i in range(n):
+        kw = pool[i % n_pool]
+        o = api.default_opts(n_states=sizes[i % n_pool][4], precond=api.RID, precision=api.MIXED, tensor_cores=0)
+        reqs.append((0, o, kw, None, None))
+    warm = min(pool, key=lambda k: k["n_occ"] * k["n_vir"])
+    done, info, left = _run_stream(api, reqs, np.zeros(n), args.batch_slots, args.serve_budget_gb, warm)
+    if not done:
+        return {"error": "no request finished"}
+    out = _stream_report(api, reqs, done, info, left)
+    out.update({"slots": args.batch_slots, "distinct_problems": n_pool,
+                "note": "TDA solves queued at once, each creating its context from FP32 device arrays; "
+                        "MIXED, FP32 SIMT outer products, BF16 ris, rid"})
+    return out
 
 
 def apply_only(args, api, solver, p, tc, stream):
