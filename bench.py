@@ -269,6 +269,7 @@ def our_arm(args, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     prof = solver.profile_read(0 if tc else 1)
+    rec_ms, rec_fl, rec_by = solver.profile_records(0 if tc else 1)
     solver.profile(False)
     clk = clocks.stop() if clocks else None
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
@@ -344,6 +345,23 @@ def our_arm(args, rank, world, local):
         peak = 152 * 128 * 2 * sm * 1e6 / 1e12
         roof = {"bound": "alu", "unit": "TFLOP/s",
                 "peak_kind": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % sm}
+    # per-launch roofline: the launch's attainable time is the larger of its
+    # tensor time (tcgen05: three BF16 products per algorithmic flop for the
+    # hi+lo exact factors) and its HBM time (algorithmic bytes at the measured
+    # copy bandwidth); small trial blocks make a launch HBM-bound
+    if rec_ms.size:
+        per_flop = 3.0 if tc else 1.0
+        t_ten = rec_fl * per_flop / (peak * 1e12) * 1e3
+        t_hbm = rec_by / (peaks["hbm_gbs"] * 1e9) * 1e3
+        t_att = np.maximum(t_ten, t_hbm)
+        roof.update({
+            "attainable_frac": float(t_att.sum() / rec_ms.sum()),
+            "hbm_bound_time_share": float(rec_ms[t_hbm > t_ten].sum() / rec_ms.sum()),
+            "achieved_hbm_gbs": float(rec_by.sum() / rec_ms.sum() / 1e6),
+            "algorithmic_bytes_per_launch": float(rec_by.mean()),
+            "attainable_note": "per launch max(%g BF16 products per flop at the tensor peak, algorithmic bytes "
+                               "at hbm_gbs %.0f); attainable_frac = sum of those / sum of measured times"
+                               % (per_flop, peaks["hbm_gbs"])})
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak if peak else None,
                  "traffic": None, "kernel": "exchange K1 contraction sum_(P,a) Z L_vv",
                  "launches": prof["launches"], "ms_per_launch": kernel_ms,

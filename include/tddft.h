@@ -346,6 +346,16 @@ tddft_status tddft_profile(tddft_ctx* ctx, int enable);
 tddft_status tddft_profile_read(const tddft_ctx* ctx, int which, long long* launches,
                                 double* ms, double* flops);
 
+/* Per-launch records of the same kernel family since tddft_profile(ctx, 1):
+ * device time (ms), algorithmic flops (2 M N K) and algorithmic bytes (each
+ * operand read once in its stored type, the result written once in its
+ * working type and read back when a P-chunk accumulates into it) of each
+ * launch, oldest first, the
+ * first 131072 launches at most.  Writes min(max_records, available) entries
+ * of ms, flops and bytes and sets *count to the number available.          */
+tddft_status tddft_profile_records(const tddft_ctx* ctx, int which, int max_records, double* ms,
+                                   double* flops, double* bytes, int* count);
+
 #ifdef __cplusplus
 }
 #endif

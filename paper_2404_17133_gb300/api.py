@@ -130,6 +130,8 @@ _lib.tddft_server_destroy.argtypes = [_vp]
 _lib.tddft_server_destroy.restype = None
 _lib.tddft_ctx_desc.argtypes = [_vp, C.POINTER(Desc)]
 _lib.tddft_ctx_desc.restype = C.c_int
+_lib.tddft_profile_records.argtypes = [_vp, _ip, _ip, _dp, _dp, _dp, C.POINTER(C.c_int)]
+_lib.tddft_profile_records.restype = C.c_int
 _lib.tddft_add_exchange.argtypes = [_vp, C.c_double, _ip, _vp, _vp, _vp, _ip, _ip]
 _lib.tddft_add_exchange.restype = C.c_int
 _lib.tddft_add_kernel.argtypes = [_vp, _ip, _dp, _vp, _ip, _ip]
@@ -140,7 +142,8 @@ EXPORTED = ["tddft_default_opts", "tddft_default_desc", "tddft_create", "tddft_s
             "tddft_destroy", "tddft_last_error", "tddft_device_bytes", "tddft_profile",
             "tddft_profile_read", "tddft_apply_noalloc", "tddft_estimate_bytes", "tddft_server_create",
             "tddft_server_submit", "tddft_server_poll", "tddft_server_info", "tddft_server_destroy",
-            "tddft_ctx_desc", "tddft_add_exchange", "tddft_add_kernel"]
+            "tddft_ctx_desc", "tddft_add_exchange", "tddft_add_kernel",
+            "tddft_profile_records"]
 
 
 class TddftError(RuntimeError):
@@ -315,6 +318,16 @@ class Solver:
         self._check(_lib.tddft_profile_read(self.h, which, C.byref(n), C.byref(ms), C.byref(fl)),
                     allow_noconv=False)
         return dict(launches=n.value, ms=ms.value, flops=fl.value)
+
+    def profile_records(self, which=0):
+        """Per-launch (ms, algorithmic flops, algorithmic bytes) arrays of the profiled kernel."""
+        n = C.c_int()
+        self._check(_lib.tddft_profile_records(self.h, which, 0, None, None, None, C.byref(n)), allow_noconv=False)
+        ms, fl, by = np.zeros(n.value), np.zeros(n.value), np.zeros(n.value)
+        vp = lambda a: a.ctypes.data_as(C.c_void_p)
+        self._check(_lib.tddft_profile_records(self.h, which, n.value, vp(ms), vp(fl), vp(by), C.byref(n)),
+                    allow_noconv=False)
+        return ms, fl, by
 
     def solve_tda(self, opts: Opts, want_vectors=True):
         k = opts.n_states

@@ -735,6 +735,27 @@ tddft_status tddft_ctx_desc(const tddft_ctx* ctx, tddft_desc* desc) {
   return TDDFT_OK;
 }
 
+tddft_status tddft_profile_records(const tddft_ctx* ctx, int which, int max_records, double* ms, double* flops,
+                                   double* bytes, int* count) {
+  TD_API_BODY(const_cast<tddft_ctx*>(ctx), {
+    TD_REQUIRE(which == 0 || which == 1, TDDFT_ERR_ARG, "which must be 0 or 1");
+    TD_REQUIRE(max_records >= 0 && count && (max_records == 0 || (ms && flops && bytes)), TDDFT_ERR_ARG,
+               "bad record buffers");
+    std::lock_guard<std::mutex> run(c->run_mu);
+    KernelProfile& kp = which == 0 ? c->prof : c->prof_simt;
+    kp.collect();
+    const int n = (int)kp.rec_ms.size();
+    const int k = std::min(n, max_records);
+    for (int i = 0; i < k; ++i) {
+      ms[i] = kp.rec_ms[i];
+      flops[i] = kp.rec_flops[i];
+      bytes[i] = kp.rec_bytes[i];
+    }
+    *count = n;
+    return TDDFT_OK;
+  })
+}
+
 unsigned long long tddft_device_bytes(const tddft_ctx* ctx) {
   const Ctx* c = reinterpret_cast<const Ctx*>(ctx);
   return c ? c->device_bytes : 0ull;

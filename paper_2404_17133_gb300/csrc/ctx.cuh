@@ -64,10 +64,16 @@ struct ExactCopies {
 struct KernelProfile {
   bool on = false;
   std::vector<cudaEvent_t> ev;      // pairs (start, stop)
+  std::vector<double> pend_flops, pend_bytes;   // per launch, until collected
   long long launches = 0;
   double flops = 0.0, ms = 0.0;
+  // collected per-launch records (the first kMaxRecords launches)
+  static constexpr size_t kMaxRecords = 1u << 17;
+  std::vector<double> rec_ms, rec_flops, rec_bytes;
   void begin(cudaStream_t s);
-  void end(cudaStream_t s, double launch_flops);
+  // launch_flops / launch_bytes: the launch's algorithmic flops and bytes
+  // (operands read once, result written once)
+  void end(cudaStream_t s, double launch_flops, double launch_bytes = 0.0);
   void collect();                   // fold recorded pairs into ms (synchronises)
   void reset();
   ~KernelProfile();

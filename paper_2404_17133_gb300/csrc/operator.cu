@@ -27,11 +27,13 @@ void KernelProfile::begin(cudaStream_t s) {
   TD_CUDA(cudaEventRecord(a, s));
   ev.push_back(a);
 }
-void KernelProfile::end(cudaStream_t s, double launch_flops) {
+void KernelProfile::end(cudaStream_t s, double launch_flops, double launch_bytes) {
   cudaEvent_t b;
   TD_CUDA(cudaEventCreate(&b));
   TD_CUDA(cudaEventRecord(b, s));
   ev.push_back(b);
+  pend_flops.push_back(launch_flops);
+  pend_bytes.push_back(launch_bytes);
   launches++;
   flops += launch_flops;
 }
@@ -41,13 +43,25 @@ void KernelProfile::collect() {
     float t = 0.f;
     TD_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
     ms += t;
+    if (rec_ms.size() < kMaxRecords) {
+      rec_ms.push_back(t);
+      rec_flops.push_back(pend_flops[i / 2]);
+      rec_bytes.push_back(pend_bytes[i / 2]);
+    }
   }
   for (auto e : ev) cudaEventDestroy(e);
   ev.clear();
+  pend_flops.clear();
+  pend_bytes.clear();
 }
 void KernelProfile::reset() {
   for (auto e : ev) cudaEventDestroy(e);
   ev.clear();
+  pend_flops.clear();
+  pend_bytes.clear();
+  rec_ms.clear();
+  rec_flops.clear();
+  rec_bytes.clear();
   launches = 0;
   flops = 0.0;
   ms = 0.0;
@@ -167,7 +181,11 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
         tc_contract(Zhi.as<__nv_bfloat16>(), Zlo.as<__nv_bfloat16>(), Mz, pn, nv,
                     f.Kvv_hi + (size_t)p0 * nv * nvp, split ? f.Kvv_lo + (size_t)p0 * nv * nvp : nullptr,
                     nv, K1b.as<float>(), p0 > 0, d.tc_err, s, timed ? d.prof : nullptr,
-                    2.0 * Mz * (double)nv * (double)pn * nv);
+                    2.0 * Mz * (double)nv * (double)pn * nv,
+                    // Z hi+lo [Mz][pn*nv], L_vv chunk [pn*nv][nv] (hi+lo when split), K1 FP32
+                    // written (and read back when accumulating)
+                    4.0 * Mz * (double)pn * nv + (split ? 4.0 : 2.0) * (double)pn * nv * nv +
+                        4.0 * Mz * (double)nv * (p0 > 0 ? 2.0 : 1.0));
         if (need_k2) {
           const __nv_bfloat16* ov_lo = split ? f.Kovp_lo + (size_t)p0 * no * nvp : nullptr;
           tc_stage1(Xs_hi.as<__nv_bfloat16>(), Xs_lo.as<__nv_bfloat16>(), m * no, nv,
@@ -207,7 +225,10 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
         k.C = K1b.p; k.tc = tw; k.scm = nv; k.scn = 1;
         k.beta = (p0 > 0) ? 1.0 : 0.0;
         gemm_splitk(k, auto_splits(k.M, k.N, k.K), s);
-        if (timed) d.prof_simt->end(s, 2.0 * Mz * (double)nv * (double)Kz);
+        if (timed)
+          d.prof_simt->end(s, 2.0 * Mz * (double)nv * (double)Kz,
+                           (double)ew * Mz * (double)Kz + (double)es * Kz * nv +
+                               (double)ew * Mz * nv * (p0 > 0 ? 2.0 : 1.0));
         if (need_k2) {
           // Q[n][i][P][j] = sum_b Kov[P][i][b] X[n][j][b]
           GemmDesc q;

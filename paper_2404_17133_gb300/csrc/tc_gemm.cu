@@ -534,7 +534,8 @@ void tc_transpose_split(const void* src, DType ts, int rows, int n1, int n2, __n
 
 void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int pn, int Kin,
                  const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, float* out,
-                 bool accumulate, int* err, cudaStream_t s, KernelProfile* prof, double prof_flops) {
+                 bool accumulate, int* err, cudaStream_t s, KernelProfile* prof, double prof_flops,
+                 double prof_bytes) {
   if (M <= 0 || pn <= 0 || N <= 0) return;
   TD_REQUIRE(Alo != nullptr || Blo == nullptr, TDDFT_ERR_ARG, "tc_contract: B split without A split");
   const int mode = Alo ? (Blo ? BOTH : ASPLIT) : SINGLE;
@@ -565,7 +566,7 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
     ensure_smem((const void*)kernel, smem);
     if (prof) prof->begin(s);
     kernel<<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
-    if (prof) prof->end(s, prof_flops);
+    if (prof) prof->end(s, prof_flops, prof_bytes);
   };
   if (mode == BOTH) launch(k1_tc_kernel<BOTH>, Cfg<BOTH>::SMEM_BYTES);
   else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT>, Cfg<ASPLIT>::SMEM_BYTES);

@@ -19,17 +19,18 @@ void tc_transpose_split(const void* src, DType ts, int rows, int n1, int n2, __n
 
 // C[m][n] (+)= sum_(P<pn) sum_(k<Kin) A[m][P][k] B[P][n][k] on the tcgen05 tensor
 // cores.  A: [M][pn][tc_pad(Kin)] BF16, B: [pn][N][tc_pad(Kin)] BF16, C: [M][N] FP32,
-// accumulated into when `accumulate`.  With Alo/Blo (both or neither) the operands
-// are hi + lo splits and the three products hi*hi + hi*lo + lo*hi are formed;
-// without, one BF16 product.  Timeouts of the kernel's internal waits are
-// reported by OR-ing a nonzero code into *err.  With `prof`, CUDA events bracket
-// the contraction kernel alone (not the split reduction) and prof_flops is
-// credited to it.
+// accumulated into when `accumulate`.  Operand splits: with Alo and Blo the
+// three products hi*hi + hi*lo + lo*hi are formed; with Alo alone the two
+// products Ahi*B + Alo*B; with neither one BF16 product (Blo without Alo is not
+// allowed).  Timeouts of the kernel's internal waits are reported by OR-ing a
+// nonzero code into *err.  With `prof`, CUDA events bracket the contraction
+// kernel alone (not the split reduction) and prof_flops / prof_bytes (the
+// launch's algorithmic flops and bytes) are credited to it.
 struct KernelProfile;
 void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int pn, int Kin,
                  const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, float* out,
                  bool accumulate, int* err, cudaStream_t s, KernelProfile* prof = nullptr,
-                 double prof_flops = 0.0);
+                 double prof_flops = 0.0, double prof_bytes = 0.0);
 
 // Rows src [rows][n] (F64, F32 or BF16) -> BF16 hi (+ lo unless NULL) [rows][tc_pad(n)].
 void tc_pad_split(const void* src, DType ts, long long rows, int n, __nv_bfloat16* hi,

@@ -199,3 +199,28 @@ def test_single_state_and_T_equal_A(api):
         assert abs(r["omega"][0] - np.linalg.eigvalsh(A)[0]) < 1e-8
     finally:
         s.close()
+
+
+def test_contraction_profile(api):
+    """CUDA-event timing of the K1 contraction: one record per launch, the
+    records' flops add up to the totals, and the algorithmic bytes of a launch
+    are those of its operands and result (hi+lo Z and L_vv, FP32 output)."""
+    p = make_config("tda_small")
+    s = api.Solver.from_problem(p)
+    try:
+        X = np.random.default_rng(3).standard_normal((4, p.n_ov))
+        s.profile(True)
+        s.apply(1, X, precision=api.MIXED, tensor_cores=True)
+        tot = s.profile_read(0)
+        ms, fl, by = s.profile_records(0)
+        assert tot["launches"] == len(ms) >= 1
+        assert abs(fl.sum() - tot["flops"]) <= 1e-9 * tot["flops"]
+        assert abs(ms.sum() - tot["ms"]) <= 1e-6 * max(tot["ms"], 1e-9) and np.all(ms > 0)
+        no, nv, na = p.n_occ, p.n_vir, p.n_aux
+        M = 4 * no
+        assert fl.sum() == 2.0 * M * nv * na * nv          # one chunk covers every P here
+        assert by[0] == 4.0 * M * na * nv + 4.0 * na * nv * nv + 4.0 * M * nv
+        s.profile(False)
+        assert s.profile_read(0)["launches"] == 0 and s.profile_records(0)[0].size == 0
+    finally:
+        s.close()
