@@ -83,6 +83,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, world):
+    """The largest x over the ranks (a time: the job ends with its slowest replica)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, max_ms):
+    """Whole-job throughput of `world` replicas that each processed units_per_rank
+    units, over the slowest replica's time (ms)."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -274,11 +292,8 @@ def our_arm(args, rank, world, local):
     clk = clocks.stop() if clocks else None
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = N_STATES * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world)
+    value = replica_throughput(N_STATES * args.steps, world, total_ms)
     a, b = results[-1]
     conv = all(r["status"] == api.OK for pair in results for r in pair)
 
@@ -325,10 +340,7 @@ def our_arm(args, rank, world, local):
                                                                     np.asarray(results[-1][0]["omega"])))),
                  "note": "same step in the plain form: FP64 factors and vectors, SIMT contractions, "
                          "FP64 inner solves; warm kernels, one step"}
-    if world > 1:
-        t = torch.tensor([e2e_t], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = max_over_ranks(e2e_t, world)
     if rank != 0:
         solver.close()
         return
