@@ -38,7 +38,7 @@ def _rank(rank, world, port, out):
 def test_two_replicas_take_the_slowest_time():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.start_processes(_rank, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
         res = dict(out)
