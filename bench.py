@@ -414,6 +414,10 @@ def our_arm(args, rank, world, local):
             line["batched"] = batched(args, api, torch)
         except Exception as e:
             line["batched"] = {"error": "%s: %s" % (type(e).__name__, e)}
+        try:
+            line["batched_tc"] = batched(args, api, torch, tc=1)
+        except Exception as e:
+            line["batched_tc"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if not args.no_cpu_baseline and world == 1:
         step_s, desc, cores = oracle_sample()
         line["cpu_baseline"] = {"value": N_STATES / step_s, "unit": UNIT, "cores": cores,
@@ -534,13 +538,13 @@ def serving(args, api, torch):
     return out
 
 
-def batched(args, api, torch):
+def batched(args, api, torch, tc=0):
     """Many small independent TDA solves submitted together: n_occ ~ U{8..64},
     n_vir = n_occ x U{4..8}, n_aux = 5 n_mo, ris n_aux = 9 ceil(n_occ/2), 5-10
-    states, MIXED (FP32 outer products on the SIMT path, BF16 ris), rid; all
-    queued at time 0 on a server with --batch-slots slots (concurrent streams,
-    not one persistent kernel).  Throughput = solves / (first submit to last
-    finish)."""
+    states, MIXED (FP32 outer products on the SIMT path, or with tc the BF16
+    hi+lo tcgen05 products; BF16 ris), rid; all queued at time 0 on a server
+    with --batch-slots slots (concurrent streams, not one persistent kernel).
+    Throughput = solves / (first submit to last finish)."""
     from synth.device import problem_kw
 
     g = np.random.Generator(np.random.Philox(key=np.array([2405, 1], dtype=np.uint64)))
@@ -556,7 +560,8 @@ def batched(args, api, torch):
     reqs = []
     for i in range(n):
         kw = pool[i % n_pool]
-        o = api.default_opts(n_states=sizes[i % n_pool][4], precond=api.RID, precision=api.MIXED, tensor_cores=0)
+        o = api.default_opts(n_states=sizes[i % n_pool][4], precond=api.RID, precision=api.MIXED,
+                             tensor_cores=tc)
         reqs.append((0, o, kw, None, None))
     warm = min(pool, key=lambda k: k["n_occ"] * k["n_vir"])
     done, info, left = _run_stream(api, reqs, np.zeros(n), args.batch_slots, args.serve_budget_gb, warm)
@@ -565,7 +570,8 @@ def batched(args, api, torch):
     out = _stream_report(api, reqs, done, info, left)
     out.update({"slots": args.batch_slots, "distinct_problems": n_pool,
                 "note": "TDA solves queued at once, each creating its context from FP32 device arrays; "
-                        "MIXED, FP32 SIMT outer products, BF16 ris, rid"})
+                        "MIXED, %s outer products, BF16 ris, rid"
+                        % ("BF16 hi+lo tcgen05" if tc else "FP32 SIMT")})
     return out
 
 
