@@ -26,6 +26,7 @@
 //
 // Every wait on an mbarrier is bounded: on timeout the thread records an error
 // code in `err` and leaves the loop; the host turns it into TDDFT_ERR_CUDA.
+#include <algorithm>
 #include <cuda.h>
 
 #include "ctx.cuh"
@@ -532,6 +533,44 @@ void tc_transpose_split(const void* src, DType ts, int rows, int n1, int n2, __n
   TD_LAUNCH_CHECK();
 }
 
+// SMs of the current device (queried once).
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      n = 152;
+  }
+  return n;
+}
+
+// Work split for a grid of `tiles` x splits CTAs, one CTA per SM, each taking
+// ceil(total / splits) consecutive units: the launch lasts (number of waves) x
+// (units per CTA + a fixed per-CTA cost of `overhead` units), so a last,
+// nearly empty wave costs as much as a full one.  Tries the splits that fill
+// one to four waves and keeps the cheapest (the fewest splits on ties).
+int wave_splits(int tiles, int total, int overhead) {
+  const int sms = sm_count();
+  int best = 1;
+  long long best_cost = -1;
+  for (int w = 1; w <= 4; ++w) {
+    int sp = std::max(1, (w * sms) / std::max(tiles, 1));
+    sp = std::min(sp, std::max(total, 1));
+    const int per = (total + sp - 1) / sp;
+    sp = (total + per - 1) / per;
+    const long long waves = ((long long)tiles * sp + sms - 1) / sms;
+    const long long cost = waves * (per + overhead);
+    if (best_cost < 0 || cost < best_cost || (cost == best_cost && sp < best)) {
+      best_cost = cost;
+      best = sp;
+    }
+  }
+  return best;
+}
+
 void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int pn, int Kin,
                  const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, float* out,
                  bool accumulate, int* err, cudaStream_t s, KernelProfile* prof, double prof_flops,
@@ -543,9 +582,9 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
   const int nab = (Kin + BK - 1) / BK;
   const int total = pn * nab;
   const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
-  int splits = (2 * 152 + mt * nt - 1) / (mt * nt);
-  if (splits > total) splits = total;
-  if (splits < 1) splits = 1;
+  // a CTA's fixed cost (barriers, TMEM, pipeline fill, 128 KB epilogue) is about
+  // four k-blocks of MMA work
+  int splits = wave_splits(mt * nt, total, 4);
   const int per = (total + splits - 1) / splits;
   splits = (total + per - 1) / per;
 
@@ -600,8 +639,7 @@ void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
   TD_REQUIRE(stages >= 2, TDDFT_ERR_ARG, "tc_stage1: tile too large");
   const int smem = stages * stage_bytes + 1024 + 256;
   const int mt = (M + BM - 1) / BM;
-  int groups = (2 * 152 + mt - 1) / mt;
-  if (groups > pn) groups = pn;
+  int groups = wave_splits(mt, pn, 1);   // units: P-rows (the epilogue is double-buffered)
   const int ppc = (pn + groups - 1) / groups;
   groups = (pn + ppc - 1) / ppc;
 
