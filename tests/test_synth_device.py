@@ -41,3 +41,34 @@ def test_request_mix():
         assert m["n_vir"] % m["n_occ"] == 0 and 4 <= m["n_vir"] // m["n_occ"] <= 9
         assert m["n_aux"] == 5 * (m["n_occ"] + m["n_vir"]) and m["n_ris"] == 9 * math.ceil(m["n_occ"] / 2)
         assert 5 <= m["n_states"] <= 20 and 1 <= m["n_freq"] <= 4
+
+
+def test_served_problems_are_well_posed_for_rid():
+    """The served-stream amplitude rule keeps A+B and A-B positive definite and
+    lets the oracle's rid-preconditioned TDA solve converge in the paper's
+    regime (at most 12 outer iterations on these samples)."""
+    from oracle import davidson as DV
+    from oracle import operators as O
+    from synth.generator import Problem
+
+    mix = serving_mix(2404, 60, max_occ=40)
+    picked = [(i, m) for i, m in enumerate(mix) if m["n_occ"] <= 12][:2]
+    assert picked
+    for i, m in picked:
+        kw = problem_kw(1000 + i, m["n_occ"], m["n_vir"], m["n_aux"], m["n_ris"], device="cpu")
+        f = lambda t: t.double().numpy()
+        nr, k = m["n_ris"], kw["ris_K_index"].numpy()
+        Lr_oo = np.zeros((nr, m["n_occ"], m["n_occ"]))
+        Lr_oo[k] = f(kw["Lr_oo"])
+        Lr_vv = np.zeros((nr, m["n_vir"], m["n_vir"]))
+        Lr_vv[k] = f(kw["Lr_vv"])
+        p = Problem(n_occ=m["n_occ"], n_vir=m["n_vir"], n_aux=m["n_aux"], n_ris=nr, eps_occ=f(kw["eps_occ"]),
+                    eps_vir=f(kw["eps_vir"]), L_oo=f(kw["L_oo"]), L_ov=f(kw["L_ov"]), L_vv=f(kw["L_vv"]),
+                    Lr_ov=f(kw["Lr_ov"]), Lr_oo=Lr_oo, Lr_vv=Lr_vv, ris_K_index=k.astype(np.int32))
+        op, T = O.exact_operator(p), O.ris_operator(p)
+        E = np.eye(p.n_ov)
+        apb, amb = op.apb_amb(E)
+        assert np.linalg.eigvalsh(0.5 * (apb + apb.T))[0] > 0.02
+        assert np.linalg.eigvalsh(0.5 * (amb + amb.T))[0] > 0.02
+        r = DV.solve_tda(p, op, T, min(m["n_states"], 10), precond="rid")
+        assert r.n_iter <= 12, (m, r.n_iter)
