@@ -614,6 +614,10 @@ tddft_status tddft_profile(tddft_ctx* ctx, int enable) {
     c->prof.reset();
     c->prof_simt.reset();
     c->prof.on = c->prof_simt.on = enable != 0;
+    if (enable) {   // event creation stays out of the timed launches
+      c->prof.reserve(8192);
+      c->prof_simt.reserve(1024);
+    }
     return TDDFT_OK;
   })
 }

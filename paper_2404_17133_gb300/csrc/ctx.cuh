@@ -64,6 +64,7 @@ struct ExactCopies {
 struct KernelProfile {
   bool on = false;
   std::vector<cudaEvent_t> ev;      // pairs (start, stop)
+  std::vector<cudaEvent_t> spare;   // events already created, reused by later launches
   std::vector<double> pend_flops, pend_bytes;   // per launch, until collected
   long long launches = 0;
   double flops = 0.0, ms = 0.0;
@@ -74,6 +75,7 @@ struct KernelProfile {
   // launch_flops / launch_bytes: the launch's algorithmic flops and bytes
   // (operands read once, result written once)
   void end(cudaStream_t s, double launch_flops, double launch_bytes = 0.0);
+  void reserve(size_t n_events);    // create events ahead of the launches they will time
   void collect();                   // fold recorded pairs into ms (synchronises)
   void reset();
   ~KernelProfile();

@@ -21,21 +21,39 @@
 
 namespace tddft {
 
+namespace {
+cudaEvent_t take_event(std::vector<cudaEvent_t>& spare) {
+  cudaEvent_t e;
+  if (!spare.empty()) {
+    e = spare.back();
+    spare.pop_back();
+  } else {
+    TD_CUDA(cudaEventCreate(&e));
+  }
+  return e;
+}
+}  // namespace
+
 void KernelProfile::begin(cudaStream_t s) {
-  cudaEvent_t a;
-  TD_CUDA(cudaEventCreate(&a));
-  TD_CUDA(cudaEventRecord(a, s));
+  cudaEvent_t a = take_event(spare);
   ev.push_back(a);
+  TD_CUDA(cudaEventRecord(a, s));
 }
 void KernelProfile::end(cudaStream_t s, double launch_flops, double launch_bytes) {
-  cudaEvent_t b;
-  TD_CUDA(cudaEventCreate(&b));
-  TD_CUDA(cudaEventRecord(b, s));
+  cudaEvent_t b = take_event(spare);
   ev.push_back(b);
+  TD_CUDA(cudaEventRecord(b, s));
   pend_flops.push_back(launch_flops);
   pend_bytes.push_back(launch_bytes);
   launches++;
   flops += launch_flops;
+}
+void KernelProfile::reserve(size_t n_events) {
+  while (spare.size() < n_events) {
+    cudaEvent_t e;
+    TD_CUDA(cudaEventCreate(&e));
+    spare.push_back(e);
+  }
 }
 void KernelProfile::collect() {
   for (size_t i = 0; i + 1 < ev.size(); i += 2) {
@@ -49,13 +67,13 @@ void KernelProfile::collect() {
       rec_bytes.push_back(pend_bytes[i / 2]);
     }
   }
-  for (auto e : ev) cudaEventDestroy(e);
+  spare.insert(spare.end(), ev.begin(), ev.end());   // recorded and waited on: reusable
   ev.clear();
   pend_flops.clear();
   pend_bytes.clear();
 }
 void KernelProfile::reset() {
-  for (auto e : ev) cudaEventDestroy(e);
+  for (auto e : ev) cudaEventDestroy(e);   // possibly still pending: not reused
   ev.clear();
   pend_flops.clear();
   pend_bytes.clear();
@@ -67,6 +85,7 @@ void KernelProfile::reset() {
   ms = 0.0;
 }
 KernelProfile::~KernelProfile() {
+  for (auto e : spare) cudaEventDestroy(e);
   for (auto e : ev) cudaEventDestroy(e);
 }
 
