@@ -299,9 +299,10 @@ def davidson_tda(op, n_states, precond, guess, tol=1e-5, max_iter=50, max_subspa
         if new.shape[0] == 0:
             break
         if V.shape[0] + int(todo.sum()) > max_subspace:
-            # thick restart: current Ritz vectors + those of the previous iteration
+            # thick restart: current Ritz vectors + those of the previous iteration,
+            # the latter only where they and the new directions fit under the cap
             V, AV = X, AX
-            if X_prev is not None:
+            if X_prev is not None and 2 * X.shape[0] + new.shape[0] <= max_subspace:
                 extra = mgs(V, X_prev)
                 V = np.vstack([V, extra])
                 AV = np.vstack([AV, op.tda(extra)])
@@ -357,7 +358,11 @@ def davidson_rpa(op, n_states, precond, guess, tol=1e-5, max_iter=50, max_subspa
             break
         if V.shape[0] + 2 * int(todo.sum()) > max_subspace:
             # thick restart: X+Y and X-Y of the wanted roots, now and one iteration ago
-            V = mgs(None, np.vstack([U, W] + ([] if prev is None else list(prev))))
+            # (the latter only where they and the new directions fit under the cap,
+            # and while the restart block stays within 112 rows)
+            keep_prev = prev is not None and 4 * U.shape[0] <= 112 and \
+                4 * U.shape[0] + new.shape[0] <= max_subspace
+            V = mgs(None, np.vstack([U, W] + (list(prev) if keep_prev else [])))
             P, M = op.apb_amb(V)
             n_mv += V.shape[0]
             new = mgs(V, new)
@@ -410,7 +415,10 @@ def polar_solve(op, mu, omegas, precond, guess, tol=1e-5, max_iter=50):
         nu, nw = precond.paired(Rp[todo], Rm[todo], om_all[todo])
         if V.shape[0] + 2 * int(todo.sum()) > MAX_SUBSPACE:
             # thick restart from the current and the previous solutions of every system
-            V = mgs(None, np.vstack([U, W] + ([] if prev is None else list(prev))))
+            # (the previous ones only where they and the new directions fit under the cap)
+            keep_prev = prev is not None and 4 * U.shape[0] <= 112 and \
+                4 * U.shape[0] + 2 * int(todo.sum()) <= MAX_SUBSPACE
+            V = mgs(None, np.vstack([U, W] + (list(prev) if keep_prev else [])))
             P, M = op.apb_amb(V)
             n_mv += V.shape[0]
         prev = (U.copy(), W.copy())

@@ -352,11 +352,12 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
       nnew = orth_compact<double>(Vp, N, cand.as<double>(), nu, ov, cfree.as<double>(), s);
       if (nnew == 0) break;
       cnew = cfree.as<double>();
-      // thick restart: current Ritz vectors + those of the previous iteration
+      // thick restart: current Ritz vectors + those of the previous iteration,
+      // the latter only where they and the new directions fit under the cap
       TD_CUDA(cudaMemcpyAsync(Vp, X.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
       TD_CUDA(cudaMemcpyAsync(Wp, AX.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
       N = kk;
-      if (have_prev) {
+      if (have_prev && 2 * kk + nnew <= cap) {
         TD_CUDA(cudaMemcpyAsync(tmpk.p, Xprev.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
         int ne = orth_append(Vp, N, tmpk.as<double>(), kk, ov, s);
         mv(N, ne);
@@ -367,7 +368,7 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
     }
     TD_CUDA(cudaMemcpyAsync(Xprev.p, X.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
     have_prev = true;
-    int nacc = orth_append(Vp, N, cnew, nnew, ov, s);
+    int nacc = orth_append(Vp, N, cnew, std::min(nnew, cap - N), ov, s);
     if (nacc == 0) break;
     mv(N, nacc);
     N += nacc;
@@ -629,7 +630,7 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
     if (sp.N + 2 * nu > cap) {
       if (!exact_op) break;   // inner solve: return the current approximate solution
       // thick restart from the current and the previous solutions of every system
-      const int nprev = (have_prev && 4 * nr <= 112) ? 2 * nr : 0;
+      const int nprev = (have_prev && 4 * nr <= 112 && 4 * nr + 2 * nu <= cap) ? 2 * nr : 0;
       DevBuf rst((size_t)4 * nr * ov * es, s);
       TD_CUDA(cudaMemcpyAsync(rst.p, Uout, (size_t)nr * ov * es, cudaMemcpyDeviceToDevice, s));
       TD_CUDA(cudaMemcpyAsync(rst.as<T>() + (size_t)nr * ov, Wout, (size_t)nr * ov * es,
@@ -651,7 +652,7 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
       TD_CUDA(cudaMemcpyAsync(Wprev.p, Wout, (size_t)nr * ov * es, cudaMemcpyDeviceToDevice, s));
       have_prev = true;
     }
-    int nacc = orth_append<T>(sp.v(), sp.N, cand.as<T>(), 2 * nu, ov, s);
+    int nacc = orth_append<T>(sp.v(), sp.N, cand.as<T>(), std::min(2 * nu, cap - sp.N), ov, s);
     if (nacc == 0) break;
     mv(sp.N, nacc);
     sp.n_new += nacc;
@@ -775,7 +776,7 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
       if (nnew == 0) break;
       cnew = cfree.as<double>();
       // thick restart: X+Y and X-Y of the wanted roots, now and one iteration ago
-      const int nprev = (have_prev && 4 * kk <= 112) ? 2 * kk : 0;
+      const int nprev = (have_prev && 4 * kk <= 112 && 4 * kk + nnew <= cap) ? 2 * kk : 0;
       TD_CUDA(cudaMemcpyAsync(rst.p, U.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
       TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)kk * ov, W.p, (size_t)kk * ov * 8,
                               cudaMemcpyDeviceToDevice, s));
@@ -794,7 +795,7 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
     TD_CUDA(cudaMemcpyAsync(Uprev.p, U.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
     TD_CUDA(cudaMemcpyAsync(Wprev.p, W.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
     have_prev = true;
-    int nacc = orth_append(sp.v(), sp.N, cnew, nnew, ov, s);
+    int nacc = orth_append(sp.v(), sp.N, cnew, std::min(nnew, cap - sp.N), ov, s);
     if (nacc == 0) break;
     mv(sp.N, nacc);
     sp.n_new += nacc;
@@ -1163,6 +1164,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
   TD_REQUIRE(n_dip >= 1 && n_freq >= 1 && mu && freqs, TDDFT_ERR_ARG, "polar: need dipoles and frequencies");
   const int nr = n_dip * n_freq;
   TD_REQUIRE(2 * nr <= 112, TDDFT_ERR_ARG, "polar: too many right-hand sides");
+  TD_REQUIRE(4 * nr <= p.cap, TDDFT_ERR_ARG, "polar: max_subspace must be at least 4*n_dip*n_freq");
   const int ov = c.ov;
   cudaStream_t s = c.s;
   Counters cnt;

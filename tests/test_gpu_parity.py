@@ -224,3 +224,63 @@ def test_contraction_profile(api):
         assert s.profile_read(0)["launches"] == 0 and s.profile_records(0)[0].size == 0
     finally:
         s.close()
+
+
+def test_printed_coulomb_prefactor(api):
+    """c_J = 1 (Eq. hessian as printed) against the dense Hessians of the same prefactor."""
+    p = make_problem(7, 33, 37, 27, seeds=(40, 41, 42), amplitude=0.07)
+    A, B = O.dense_A_B(p.eps_occ, p.eps_vir, O.eri_from_factors(p.extra["L_full"]), p.a_x, 1.0)
+    s = api.Solver(p.n_occ, p.n_vir, p.eps_occ, p.eps_vir, p.L_oo, p.L_ov, p.L_vv, p.Lr_oo[p.ris_K_index],
+                   p.Lr_ov, p.Lr_vv[p.ris_K_index], p.ris_K_index, a_x=p.a_x, coulomb_factor=1.0,
+                   t_cut_ha=p.t_cut_ha)
+    try:
+        for prec in (api.PLAIN, api.MIXED):
+            tol = 1e-6 if prec == api.PLAIN else 1e-5
+            r = s.solve_tda(api.default_opts(n_states=4, precision=prec), want_vectors=False)
+            assert r["status"] == api.OK and np.max(np.abs(r["omega"] - D.tda(A, 4)[0])) < tol
+            r = s.solve_rpa(api.default_opts(n_states=4, precision=prec), want_vectors=False)
+            assert r["status"] == api.OK and np.max(np.abs(r["omega"] - D.casida(A, B, 4)[0])) < tol
+    finally:
+        s.close()
+
+
+def test_tight_subspace_restarts_often(api):
+    """The smallest subspace the rid solves accept (2 N_init for TDA, 4 N_init
+    for Casida, N_init = n_states + 3) forces a thick restart almost every
+    iteration; a restart keeps the previous solutions only where they and the
+    new directions fit, and the converged answer is unchanged."""
+    p = make_config("tda_small")
+    A, B = _dense(p)
+    s = api.Solver.from_problem(p)
+    try:
+        k = 4
+        r = s.solve_tda(api.default_opts(n_states=k, precond=api.RID, max_subspace=2 * (k + 3), max_iter=300),
+                        want_vectors=False)
+        assert r["status"] == api.OK and np.max(np.abs(r["omega"] - D.tda(A, k)[0])) < 1e-6
+        assert r["stats"]["n_restart"] >= 1
+        r = s.solve_rpa(api.default_opts(n_states=k, precond=api.RID, max_subspace=4 * (k + 3), max_iter=300),
+                        want_vectors=False)
+        assert r["status"] == api.OK and np.max(np.abs(r["omega"] - D.casida(A, B, k)[0])) < 1e-6
+        assert r["stats"]["n_restart"] >= 1
+        # polarizability: the cap must hold four rows per system
+        mu = dipoles(3, 3, p.n_ov)
+        with pytest.raises(api.TddftError) as e:
+            s.solve_polar(api.default_opts(precond=api.RID, max_subspace=20), mu, OMEGAS)
+        assert e.value.status == api.ERR_ARG
+    finally:
+        s.close()
+
+
+def test_most_states_of_a_tiny_space(api):
+    """n_states close to the dimension of the space (ov = 21, 18 states): the
+    subspace fills the whole space and the solve still matches dense results."""
+    p = make_problem(3, 7, 5, 9, seeds=(30, 31, 32))
+    A, B = _dense(p)
+    s = api.Solver.from_problem(p)
+    try:
+        k = 18
+        for pc in (api.DIAG, api.RID):
+            r = s.solve_tda(api.default_opts(n_states=k, precond=pc, max_iter=100), want_vectors=False)
+            assert r["status"] == api.OK and np.max(np.abs(r["omega"] - D.tda(A, k)[0])) < 1e-6
+    finally:
+        s.close()
