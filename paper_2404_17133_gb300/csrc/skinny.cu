@@ -204,9 +204,114 @@ void gram_typed(const void* A, long long lda, int M, const void* B, long long ld
   TD_LAUNCH_CHECK();
 }
 
+// Wide combination (FP32 accumulation, FP32 or BF16 V): each lane owns four
+// consecutive columns, loaded with one 16-byte (FP32) or 8-byte (BF16) access
+// per V row, so a warp reads 512 or 256 contiguous bytes of a row and a thread
+// keeps eight such loads in flight; a CTA covers 128 columns and kWideRows
+// output rows (row blocks fastest in the grid, so the CTAs that share a stripe
+// of V run together and share it through L2).  The K split over warps and the
+// order of every sum are those of k_sk_combo: the results are the same bits.
+constexpr int kWideRows = 8;
+constexpr int kWideLd = 132;   // 128 columns + 4 (16-byte aligned rows)
+
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&v)[4]) {
+  const uint2 q = *reinterpret_cast<const uint2*>(p);
+  const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&q.x);
+  const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&q.y);
+  v[0] = __low2float(a); v[1] = __high2float(a); v[2] = __low2float(b); v[3] = __high2float(b);
+}
+
+template <typename TS, typename TV, typename TO>
+__global__ void __launch_bounds__(kComboThreads)
+k_sk_combo_wide(const TS* __restrict__ coef, long long scm, long long sck, int M, int K,
+                const TV* __restrict__ V, long long ldv, int ncols, TO* __restrict__ out, long long ldo,
+                double alpha, double beta) {
+  extern __shared__ __align__(16) unsigned char wide_raw[];
+  float* cs = reinterpret_cast<float*>(wide_raw);        // [kComboKc][kWideRows]
+  float* red = cs + (size_t)kComboKc * kWideRows;         // [groups][kWideRows][kWideLd]
+  const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+  const int mb0 = blockIdx.x * kWideRows;
+  const int mn = min(kWideRows, M - mb0);
+  const int c0 = blockIdx.y * 128 + lane * 4;
+  const bool full = c0 + 4 <= ncols;
+  float acc[kWideRows][4];
+#pragma unroll
+  for (int m = 0; m < kWideRows; ++m)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[m][j] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += kComboKc) {
+    const int kn = min(kComboKc, K - k0);
+    __syncthreads();
+    for (int e = tid; e < kn * kWideRows; e += kComboThreads) {
+      const int k = e / kWideRows, m = e - k * kWideRows;
+      cs[e] = m < mn ? (float)coef[(long long)(mb0 + m) * scm + (long long)(k0 + k) * sck] : 0.f;
+    }
+    __syncthreads();
+    if (c0 < ncols) {
+#pragma unroll 8
+      for (int k = g; k < kn; k += kComboGroups) {
+        const TV* row = V + (long long)(k0 + k) * ldv + c0;
+        float v[4];
+        if (full) {
+          load4(row, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) v[j] = c0 + j < ncols ? cvt<float>(row[j]) : 0.f;
+        }
+        const float* ck = cs + k * kWideRows;
+#pragma unroll
+        for (int m = 0; m < kWideRows; ++m) {
+          const float cm = ck[m];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[m][j] = fmaf(cm, v[j], acc[m][j]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < kWideRows; ++m)
+    *reinterpret_cast<float4*>(red + (size_t)(g * kWideRows + m) * kWideLd + lane * 4) =
+        make_float4(acc[m][0], acc[m][1], acc[m][2], acc[m][3]);
+  __syncthreads();
+  for (int e = tid; e < kWideRows * 128; e += kComboThreads) {
+    const int m = e >> 7, l = e & 127;
+    const int col = blockIdx.y * 128 + l;
+    if (m >= mn || col >= ncols) continue;
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < kComboGroups; ++q) sum += red[(size_t)(q * kWideRows + m) * kWideLd + l];
+    TO* o = out + (long long)(mb0 + m) * ldo + col;
+    float v = (float)alpha * sum;
+    if (beta != 0.0) v = fmaf((float)beta, (float)*o, v);
+    *o = (TO)v;
+  }
+}
+
 template <typename TS, typename TV, typename TO, typename ACC>
 void combo_typed(const void* coef, long long scm, long long sck, int M, int K, const void* V, long long ldv,
                  int ncols, void* out, long long ldo, double alpha, double beta, cudaStream_t s) {
+  if constexpr (std::is_same<ACC, float>::value &&
+                (std::is_same<TV, float>::value || std::is_same<TV, __nv_bfloat16>::value)) {
+    // wide path where every lane's four columns can be one aligned access
+    const uintptr_t va = reinterpret_cast<uintptr_t>(V);
+    const long long stripes = (ncols + 127) / 128;
+    if (ncols >= 128 && ldv % 4 == 0 && va % (4 * sizeof(TV)) == 0 && stripes <= 65535) {
+      const size_t smem = ((size_t)kComboKc * kWideRows + (size_t)kComboGroups * kWideRows * kWideLd) *
+                          sizeof(float);
+      dim3 grid((M + kWideRows - 1) / kWideRows, (unsigned)stripes);
+      set_smem_attr((const void*)k_sk_combo_wide<TS, TV, TO>, smem);
+      k_sk_combo_wide<TS, TV, TO><<<grid, kComboThreads, smem, s>>>(
+          static_cast<const TS*>(coef), scm, sck, M, K, static_cast<const TV*>(V), ldv, ncols,
+          static_cast<TO*>(out), ldo, alpha, beta);
+      count_launch();
+      TD_LAUNCH_CHECK();
+      return;
+    }
+  }
   constexpr int MB = sizeof(ACC) == 8 ? 16 : 32;
   const int mblocks = (M + MB - 1) / MB;
   TD_REQUIRE(mblocks <= 65535, TDDFT_ERR_ARG, "sk_combo: too many rows");
