@@ -473,3 +473,18 @@ def test_variant_davidson_equals_dense(variant, pc):
     mu = dipoles(3, 2, variant.n_ov)
     r = DV.solve_polar(variant, op, T, mu, [0.0, 0.05], precond=pc)
     assert np.allclose(r.alpha, D.polar(A, B, mu, [0.0, 0.05]), rtol=1e-7)
+
+
+def test_tight_cap_restarts_still_converge(small):
+    """With the smallest caps (2 N_init for TDA, 4 N_init for Casida) a thick
+    restart cannot keep the previous solutions and the new directions; it
+    keeps the current ones only, and the rid solves still reach the dense
+    results (just in more iterations)."""
+    op, T = O.exact_operator(small), O.ris_operator(small)
+    A, B = O.dense_A_B(small.eps_occ, small.eps_vir, O.eri_from_factors(small.extra["L_full"]), small.a_x,
+                       small.coulomb_factor)
+    k = 4
+    r = DV.solve_tda(small, op, T, k, precond="rid", max_subspace=2 * (k + 3), max_iter=300)
+    assert r.converged and np.max(np.abs(r.omega - D.tda(A, k)[0])) < 1e-8
+    r = DV.solve_rpa(small, op, T, k, precond="rid", max_subspace=4 * (k + 3), max_iter=300)
+    assert r.converged and np.max(np.abs(r.omega - D.casida(A, B, k)[0])) < 1e-8
