@@ -321,16 +321,31 @@ unsigned long long tddft_device_bytes(const tddft_ctx* ctx);
  * until the process exits.  It calls no cudaMalloc, cudaFree or allocating
  * library routine.
  *   X, out0, out1: DEVICE pointers, [m][ov] FP64 (out1 for kinds 1 and 3).
- * The work is queued on the context's stream; results are valid once that
- * stream has been synchronised.  The first call on a device looks up the
- * array's device address (once per device, with that device made current);
- * make that first call before any stream capture.  All calls in the process
+ * The work is queued on the context's stream, which does not wait for any
+ * other stream: X must be complete before the call (synchronise the stream
+ * that wrote it, or make the context's stream wait on an event recorded
+ * after the write).  Results are valid once the context's stream has been
+ * synchronised.  Every call whose stream is not being captured looks up the
+ * array's device address with the context's device current (so an address
+ * from before a cudaDeviceReset or from another CUDA context is never used);
+ * a call made during stream capture reuses the address of the last
+ * uncaptured call on that device, so make the first call on a device before
+ * any stream capture.  All calls in the process
  * share the one array and it keeps the previous call's contents, so calls
  * whose work overlaps on the GPU (for example from two contexts on different
  * streams) race with each other.  A product whose intermediates do not fit in
  * 64 MiB is rejected with TDDFT_ERR_ARG (use tddft_apply).                  */
 tddft_status tddft_apply_noalloc(tddft_ctx* ctx, int kind, int precision, const double* X, int m,
                                  double* out0, double* out1);
+
+/* Device memory pool query for tests and callers that track allocations.
+ * (No counterpart in the paper.)  Reads the current and the high-water
+ * "used" byte counts of `device`'s default stream-ordered memory pool, from
+ * which every work buffer of this library is allocated; with reset_high
+ * nonzero the high-water mark is then restarted at the current use.
+ * used_current / used_high may be NULL.  Bad device: TDDFT_ERR_ARG.        */
+tddft_status tddft_pool_usage(int device, unsigned long long* used_current,
+                              unsigned long long* used_high, int reset_high);
 
 /* Kernel timing for measurement.  tddft_profile(ctx, 1) starts recording
  * CUDA events on the context's stream around every launch of the dominant

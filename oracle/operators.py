@@ -93,6 +93,23 @@ def dense_A_B(eps_occ, eps_vir, eri, a_x, c_J, eri_lr=None, b_x=0.0, F_full=None
     return A, B
 
 
+def dense_A_B_blocks(prob):
+    """A and B of Eq. hessian (f^xc = 0) built densely from the three-index
+    blocks, for problems too large for the four-index route of dense_A_B:
+    (ia|jb) = sum_P L^P_ia L^P_jb, (ij|ab) = sum_P L^P_ij L^P_ab and
+    (ib|ja) = sum_P L^P_ib L^P_ja, each as an [ia][jb] matrix (Eq. pqrs_approx)."""
+    no, nv, na = prob.n_occ, prob.n_vir, prob.n_aux
+    ov = no * nv
+    Lov = prob.L_ov.reshape(na, ov)
+    ia_jb = Lov.T @ Lov
+    ij_ab = np.einsum("pij,pab->iajb", prob.L_oo, prob.L_vv, optimize=True).reshape(ov, ov)
+    ib_ja = np.einsum("pib,pja->iajb", prob.L_ov, prob.L_ov, optimize=True).reshape(ov, ov)
+    A = prob.coulomb_factor * ia_jb - prob.a_x * ij_ab
+    B = prob.coulomb_factor * ia_jb - prob.a_x * ib_ja
+    A[np.diag_indices(ov)] += delta(prob.eps_occ, prob.eps_vir)
+    return A, B
+
+
 def window(eps_occ, eps_vir, t_cut):
     """Exchange energy window of Sec. 3.1: keep occupied eps_i >= eps_LUMO - t_cut
     and virtual eps_a <= eps_HOMO + t_cut (the others are dropped)."""

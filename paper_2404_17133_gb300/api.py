@@ -136,6 +136,8 @@ _lib.tddft_add_exchange.argtypes = [_vp, C.c_double, _ip, _vp, _vp, _vp, _ip, _i
 _lib.tddft_add_exchange.restype = C.c_int
 _lib.tddft_add_kernel.argtypes = [_vp, _ip, _dp, _vp, _ip, _ip]
 _lib.tddft_add_kernel.restype = C.c_int
+_lib.tddft_pool_usage.argtypes = [_ip, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong), _ip]
+_lib.tddft_pool_usage.restype = C.c_int
 
 EXPORTED = ["tddft_default_opts", "tddft_default_desc", "tddft_create", "tddft_solve_tda",
             "tddft_solve_rpa", "tddft_solve_polar", "tddft_apply", "tddft_submit", "tddft_poll",
@@ -143,7 +145,7 @@ EXPORTED = ["tddft_default_opts", "tddft_default_desc", "tddft_create", "tddft_s
             "tddft_profile_read", "tddft_apply_noalloc", "tddft_estimate_bytes", "tddft_server_create",
             "tddft_server_submit", "tddft_server_poll", "tddft_server_info", "tddft_server_destroy",
             "tddft_ctx_desc", "tddft_add_exchange", "tddft_add_kernel",
-            "tddft_profile_records"]
+            "tddft_profile_records", "tddft_pool_usage"]
 
 
 class TddftError(RuntimeError):
@@ -170,6 +172,15 @@ def _ptr(x, dtype=np.float64):
         return C.c_void_p(x.data_ptr()), x
     a = np.ascontiguousarray(x, dtype=dtype)
     return a.ctypes.data_as(C.c_void_p), a
+
+
+def pool_usage(device=0, reset_high=False):
+    """(used_current, used_high) bytes of the device's default stream-ordered pool."""
+    cur, high = C.c_ulonglong(), C.c_ulonglong()
+    st = _lib.tddft_pool_usage(int(device), C.byref(cur), C.byref(high), int(bool(reset_high)))
+    if st != OK:
+        raise TddftError(st, "tddft_pool_usage failed")
+    return cur.value, high.value
 
 
 def default_opts(**kw) -> Opts:

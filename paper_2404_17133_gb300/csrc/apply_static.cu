@@ -26,20 +26,30 @@ std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_scratch on the current device.  In host code the name
-// g_scratch is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
-void* scratch_address(int dev) {
+// g_scratch is only a host-side stand-in, so the address is looked up with the
+// device current.  The lookup is repeated on every call whose stream is not
+// being captured (it allocates nothing): after cudaDeviceReset, or under another
+// CUDA context, the module is loaded again and an address cached from before
+// would point at freed or foreign memory.  While the stream is being captured
+// the address of the last uncaptured call on this device is used, so the first
+// call on a device has to come before any capture.
+void* scratch_address(int dev, cudaStream_t s) {
   TD_REQUIRE(dev >= 0 && dev < kMaxDevices, TDDFT_ERR_ARG, "device ordinal out of range");
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || p == nullptr)
-      throw Error(TDDFT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") +
-                                      cudaGetErrorString(e));
-    g_scratch_addr[dev] = p;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TD_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {
+    TD_REQUIRE(g_scratch_addr[dev] != nullptr, TDDFT_ERR_ARG,
+               "tddft_apply_noalloc: first call on this device made during stream capture");
+    return g_scratch_addr[dev];
   }
-  return g_scratch_addr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess || p == nullptr)
+    throw Error(TDDFT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") +
+                                    cudaGetErrorString(e));
+  g_scratch_addr[dev] = p;
+  return p;
 }
 
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -175,7 +185,7 @@ extern "C" tddft_status tddft_apply_noalloc(tddft_ctx* ctx, int kind, int precis
     std::lock_guard<std::mutex> run(c->run_mu);
     TD_CUDA(cudaGetDevice(&prev));
     if (prev != c->device) TD_CUDA(cudaSetDevice(c->device));
-    unsigned char* base = static_cast<unsigned char*>(scratch_address(c->device));
+    unsigned char* base = static_cast<unsigned char*>(scratch_address(c->device, c->s));
     const bool ris = kind >= 2;
     const bool paired = (kind & 1) != 0;
     FactorSet f = ris ? c->ris(precision) : c->exact(precision);

@@ -765,4 +765,23 @@ unsigned long long tddft_device_bytes(const tddft_ctx* ctx) {
   return c ? c->device_bytes : 0ull;
 }
 
+tddft_status tddft_pool_usage(int device, unsigned long long* used_current,
+                              unsigned long long* used_high, int reset_high) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return TDDFT_ERR_ARG;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) != cudaSuccess) return TDDFT_ERR_CUDA;
+  uint64_t cur = 0, high = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &cur) != cudaSuccess ||
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high) != cudaSuccess)
+    return TDDFT_ERR_CUDA;
+  if (used_current) *used_current = cur;
+  if (used_high) *used_high = high;
+  if (reset_high) {
+    uint64_t zero = 0;   // restarts the high-water mark at the current use
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess) return TDDFT_ERR_CUDA;
+  }
+  return TDDFT_OK;
+}
+
 }  // extern "C"

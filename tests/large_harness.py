@@ -18,6 +18,7 @@ from multiprocessing import get_context, shared_memory
 import numpy as np
 
 CHUNK = 40
+VBLOCK = 16
 
 
 def _exact_task(args):
@@ -39,7 +40,14 @@ def _exact_task(args):
             shm.close()
     parts = None
     if X is not None:
-        parts = (O.coulomb(ov, X), O.exchange_K1(oo, vv, X), O.exchange_K2(ov, X))
+        # vectors in blocks of VBLOCK keep a worker's intermediates near 2 GB
+        out = [np.zeros_like(X) for _ in range(3)]
+        for v0 in range(0, X.shape[0], VBLOCK):
+            Xb = X[v0:v0 + VBLOCK]
+            out[0][v0:v0 + VBLOCK] = O.coulomb(ov, Xb)
+            out[1][v0:v0 + VBLOCK] = O.exchange_K1(oo, vv, Xb)
+            out[2][v0:v0 + VBLOCK] = O.exchange_K2(ov, Xb)
+        parts = tuple(out)
     return p0, p1, parts
 
 

@@ -13,8 +13,12 @@ orbitals), so it works over P-chunks (tests/large_harness.py):
   * TDA and Casida solves for the 20 lowest states with the rid preconditioner,
     each converged with its residuals re-certified below 1e-5 by the FP32
     operator, and rid taking no more outer iterations than diag;
-  * the oracle's FP64 residuals of two converged TDA vectors: below 1.2e-5 (the
-    FP32 re-certification itself is accurate to ~1e-7 relative).
+  * every one of the 20 converged TDA vectors and the 20 Casida pairs is
+    re-certified by the oracle in FP64 (one pass over the factors for all 60
+    vectors X, X+Y, X-Y): the residual of Eq. residual below 1.2e-5, and the
+    GPU energies within 1e-5 Ha of the oracle's Rayleigh quotients of the same
+    vectors (x^T A x for TDA; sqrt(u^T(A+B)u w^T(A-B)w) / u^T w for Casida,
+    u = X+Y, w = X-Y), which are exact to second order in the residual.
 """
 import numpy as np
 import pytest
@@ -102,7 +106,7 @@ def test_tda_and_casida_full_size(large):
     assert t["status"] == api.OK
     assert t["stats"]["max_resid_certified"] < 1e-5
     assert np.all(np.diff(t["omega"]) >= 0)
-    r = s.solve_rpa(o, want_vectors=False)
+    r = s.solve_rpa(o, want_vectors=True)
     assert r["status"] == api.OK
     assert r["stats"]["max_resid_certified"] < 1e-5
     assert np.all(np.diff(r["omega"]) >= 0)
@@ -115,12 +119,28 @@ def test_tda_and_casida_full_size(large):
                                  r["omega"][0]))
     assert r["stats"]["n_iter"] <= rd["stats"]["n_iter"]
     assert np.max(np.abs(rd["omega"] - r["omega"])) < 1e-5
-    # the oracle's FP64 residuals of the lowest and the highest converged TDA state
-    pick = [0, k - 1]
-    Xs = np.ascontiguousarray(t["X"][pick])
-    J, K1, _ = H.load_exact(NAME, meta, None, Xs)
+    # the oracle's FP64 certification of every converged vector, one pass over P
+    X = t["X"]
+    U, W = r["X"] + r["Y"], r["X"] - r["Y"]
+    assert np.max(np.abs(X @ X.T - np.eye(k))) < 1e-8
+    assert np.max(np.abs(np.sum(U * W, axis=1) - 1.0)) < 1e-8
+    V = np.ascontiguousarray(np.concatenate([X, U, W]))
+    J, K1, K2 = H.load_exact(NAME, meta, None, V)
     d = O.delta(meta["eps_occ"], meta["eps_vir"])
-    AX = O.tda_from_parts(d, Xs, J, K1, meta["a_x"], meta["coulomb_factor"])
-    om = np.asarray(t["omega"])[pick]
-    res = np.linalg.norm(AX - om[:, None] * Xs, axis=1) / np.linalg.norm(Xs, axis=1)
-    assert np.all(res < 1.2e-5), res
+    a_x, c_J = meta["a_x"], meta["coulomb_factor"]
+    AX = O.tda_from_parts(d, X, J[:k], K1[:k], a_x, c_J)
+    om = np.asarray(t["omega"])
+    res_t = np.linalg.norm(AX - om[:, None] * X, axis=1) / np.linalg.norm(X, axis=1)
+    rq_t = np.sum(X * AX, axis=1) / np.sum(X * X, axis=1)
+    PU, _ = O.pair_from_parts(d, U, J[k:2 * k], K1[k:2 * k], K2[k:2 * k], a_x, c_J)
+    _, MW = O.pair_from_parts(d, W, J[2 * k:], K1[2 * k:], K2[2 * k:], a_x, c_J)
+    Om = np.asarray(r["omega"])
+    res_r = np.sqrt(np.sum((PU - Om[:, None] * W) ** 2, axis=1) + np.sum((MW - Om[:, None] * U) ** 2, axis=1))
+    rq_r = np.sqrt(np.sum(U * PU, axis=1) * np.sum(W * MW, axis=1)) / np.sum(U * W, axis=1)
+    print("large_mixed oracle FP64 certification: TDA max |r| %.3e, max |omega - x^T A x| %.3e Ha; "
+          "Casida max |r| %.3e, max |Omega - Rayleigh| %.3e Ha"
+          % (res_t.max(), np.max(np.abs(om - rq_t)), res_r.max(), np.max(np.abs(Om - rq_r))))
+    assert np.all(res_t < 1.2e-5), res_t
+    assert np.all(res_r < 1.2e-5), res_r
+    assert np.max(np.abs(om - rq_t)) < 1e-5
+    assert np.max(np.abs(Om - rq_r)) < 1e-5

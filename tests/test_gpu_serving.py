@@ -6,13 +6,19 @@ requests at once; each context's worker runs its queue on its own stream, so
 requests of different contexts overlap on the device.  Every result must be
 the same alone and in the mix: the kernels are deterministic (fixed-order
 reductions, no atomics in the sums), so the comparison is to 1e-12 relative.
+Every served result is also checked against the oracle's dense results for
+its problem (LAPACK on the explicitly built A and B of Eq. hessian: Eq. TDA,
+Eq. Casida, Eq. TDDFT_polar), at the tolerances of the other parity tests.
 """
 import time
 
 import numpy as np
 import pytest
 
+from oracle import dense as D
+from oracle import operators as O
 from synth.generator import dipoles, make_config, make_problem
+from tests.parity import alpha_excess
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +43,34 @@ def _requests(api, p):
         (2, api.default_opts(precond=api.RID, precision=api.MIXED), mu, [0.0, 0.07]),
         (1, api.default_opts(n_states=k, precond=api.DIAG, precision=api.MIXED, max_iter=200), None, None),
     ]
+
+
+_DENSE = {}
+
+
+def _dense(p):
+    key = id(p)
+    if key not in _DENSE:
+        _DENSE[key] = (p, O.dense_A_B(p.eps_occ, p.eps_vir, O.eri_from_factors(p.extra["L_full"]), p.a_x,
+                                      p.coulomb_factor))
+    return _DENSE[key][1]
+
+
+def _check_vs_oracle(api, p, kind, o, mu, om, r, key):
+    """A converged served result against the dense oracle results of its problem."""
+    if r["status"] != api.OK:
+        return
+    A, B = _dense(p)
+    tol = 1e-6 if o.precision == api.PLAIN else 1e-5
+    if kind == 0:
+        ref = D.tda(A, o.n_states)[0]
+        assert np.max(np.abs(r["omega"] - ref)) < tol, (key, np.max(np.abs(r["omega"] - ref)))
+    elif kind == 1:
+        ref = D.casida(A, B, o.n_states)[0]
+        assert np.max(np.abs(r["omega"] - ref)) < tol, (key, np.max(np.abs(r["omega"] - ref)))
+    else:
+        ref = D.polar(A, B, mu, om)
+        assert alpha_excess(r["alpha"], ref, tol) <= 1.0, (key, alpha_excess(r["alpha"], ref, tol))
 
 
 def _run(solvers, reqs, together):
@@ -84,6 +118,8 @@ def test_results_same_alone_and_in_the_mix(api):
                 if field in a and a[field] is not None:
                     x, y = np.asarray(a[field]), np.asarray(b[field])
                     assert np.max(np.abs(x - y)) <= 1e-12 * max(1.0, np.max(np.abs(x))), (key, field)
+            kind, o, mu, om = reqs[key[0]][key[1]]
+            _check_vs_oracle(api, problems[key[0]], kind, o, mu, om, b, key)
     finally:
         for s in solvers:
             s.close()
@@ -147,6 +183,8 @@ def test_server_admits_by_budget_and_matches_alone(api):
         srv.close()
     for key in alone:
         _same(api, alone[key], res[key], key)
+    for key, p, kind, o, mu, om in reqs:
+        _check_vs_oracle(api, p, kind, o, mu, om, res[key], key)
     order = [res[key] for key, _ in tickets]
     starts = [r["t_start_s"] for r in order]
     assert all(a <= b for a, b in zip(starts, starts[1:])), "admission is first in, first out"
@@ -219,6 +257,7 @@ def test_server_on_resident_contexts(api):
                 else:
                     d = s.solve_polar(o, mu, om)
                 _same(api, d, res[(ci, ri)], (ci, ri))
+                _check_vs_oracle(api, p, kind, o, mu, om, res[(ci, ri)], (ci, ri))
                 # resident factors: only the work buffers are charged
                 w = api.estimate_bytes(s.desc, kind, o, mu.shape[0] if mu is not None else 0,
                                        len(om) if om is not None else 0)[1]

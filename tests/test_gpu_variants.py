@@ -4,7 +4,8 @@ low-rank response kernel sum_g w_g F^g_ia F^g_jb in place of f^xc.
 
 Tolerances as for the base operator: products 1e-11 relative (PLAIN), 2e-5
 (MIXED, FP32 SIMT), 5e-5 (MIXED, tcgen05 BF16 hi+lo); energies 1e-6 Ha (PLAIN)
-/ 1e-5 Ha (MIXED); polarizabilities 1e-6 / 1e-5 relative.
+/ 1e-5 Ha (MIXED); polarizabilities 1e-6 / 1e-5 relative, element by element
+with the floor of tests/parity.py.
 """
 import ctypes as C
 
@@ -14,6 +15,7 @@ import pytest
 from oracle import dense as D
 from oracle import operators as O
 from synth.generator import dipoles, make_config, make_problem, with_variant_terms
+from tests.parity import alpha_excess
 
 pytestmark = pytest.mark.gpu
 
@@ -97,7 +99,7 @@ def test_variant_solves(case, api, mode):
     r = s.solve_polar(api.default_opts(**kw), mu, OMEGAS)
     assert r["status"] == api.OK
     ref = D.polar(A, B, mu, OMEGAS)
-    assert _rel(r["alpha"], ref) < tol_e
+    assert alpha_excess(r["alpha"], ref, tol_e) <= 1.0
 
 
 def test_variant_arguments(api):

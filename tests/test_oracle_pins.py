@@ -488,3 +488,52 @@ def test_tight_cap_restarts_still_converge(small):
     assert r.converged and np.max(np.abs(r.omega - D.tda(A, k)[0])) < 1e-8
     r = DV.solve_rpa(small, op, T, k, precond="rid", max_subspace=4 * (k + 3), max_iter=300)
     assert r.converged and np.max(np.abs(r.omega - D.casida(A, B, k)[0])) < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# mid-size: the matrix-free Davidson against dense LAPACK at ov = 3,456
+
+def test_dense_blocks_equal_four_index_route(small):
+    """The blockwise dense Hessians (used where the four-index tensor over all
+    orbitals does not fit) equal the element-by-element read of (pq|rs)."""
+    A, B = O.dense_A_B(small.eps_occ, small.eps_vir, O.eri_from_factors(small.extra["L_full"]),
+                       small.a_x, small.coulomb_factor)
+    A2, B2 = O.dense_A_B_blocks(small)
+    assert np.allclose(A, A2, rtol=0, atol=1e-13) and np.allclose(B, B2, rtol=0, atol=1e-13)
+
+
+@pytest.fixture(scope="module")
+def mid():
+    """n_occ=24, n_vir=144 (ov=3,456), n_aux=840 = 5 n_mo, ris n_aux=108 (12
+    atoms); amplitude scale 0.7^3 of the default, between the small (1) and
+    the medium (0.7^5) workloads as sqrt(n_occ n_vir) is."""
+    from synth.generator import default_amplitude
+    p = make_problem(24, 144, 840, 108, seeds=(60, 61, 62), amplitude=0.7 ** 3 * default_amplitude(840))
+    A, B = O.dense_A_B_blocks(p)
+    return p, A, B
+
+
+@pytest.mark.slow
+def test_davidson_equals_dense_mid_size(mid):
+    """TDA (both preconditioners), Casida and alpha(omega) of the oracle's
+    matrix-free Davidson at ov = 3,456 against eigh / solve of the dense
+    Hessians: the converged results agree to 1e-8 Ha (||R|| <= 1e-5 puts the
+    eigenvalue error near ||R||^2 / gap), alpha to 1e-8 relative element by
+    element (one shared Galerkin subspace: second order in the residuals),
+    and rid takes no more outer iterations than diag for TDA."""
+    p, A, B = mid
+    op, T = O.exact_operator(p), O.ris_operator(p)
+    k = 10
+    ref = D.tda(A, k)[0]
+    it = {}
+    for pc in ("diag", "rid"):
+        r = DV.solve_tda(p, op, T, k, precond=pc)
+        assert r.converged and np.max(np.abs(r.omega - ref)) < 1e-8, (pc, np.max(np.abs(r.omega - ref)))
+        it[pc] = r.n_iter
+    assert it["rid"] <= it["diag"], it
+    r = DV.solve_rpa(p, op, T, k, precond="rid")
+    assert r.converged and np.max(np.abs(r.omega - D.casida(A, B, k)[0])) < 1e-8
+    mu = dipoles(63, 2, p.n_ov)
+    r = DV.solve_polar(p, op, T, mu, [0.0, 0.1], precond="rid")
+    ref = D.polar(A, B, mu, [0.0, 0.1])
+    assert r.converged and np.max(np.abs(r.alpha - ref) / np.abs(ref)) < 1e-8
