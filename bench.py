@@ -1,24 +1,26 @@
 #!/usr/bin/env python
 """Benchmark: excitation states converged per second on one GB300 (or N replicas).
 
-One step is the whole hot path on the medium response workload (n_occ=60,
-n_vir=400, n_aux=2000, ris n_aux=360): a Casida solve for the 10 lowest states
-and the polarizability alpha(omega) for 3 dipoles at omega = 0, 0.05, 0.1 Ha,
-both with the rid preconditioner to a residual of 1e-5, MIXED precision (exact
-products as BF16 hi+lo on the tcgen05 tensor cores, FP32 accumulation; ris
-inner solves with FP32 vectors on the BF16 ris factors; FP64 outer subspace
-algebra; FP32 re-certification of the converged residuals).
+One step is the whole hot path on the large mixed workload (n_occ=150,
+n_vir=1350, ov=202,500, exact n_aux=6000, ris n_aux=1350): a TDA solve and a
+Casida solve for the 20 lowest states each, with the rid preconditioner to a
+residual of 1e-5, MIXED precision (exact products as BF16 hi+lo on the tcgen05
+tensor cores with FP32 accumulation; ris inner solves with FP32 vectors on the
+BF16 ris factors; FP64 outer subspace algebra; every converged residual
+re-certified with the FP32 operator).  40 converged states per step.
 
-value: states converged per second (10 per step x steps x ranks / max time),
+value: states converged per second (40 per step x steps x ranks / max time),
 device-timed with CUDA events on the solver's stream, factors resident in HBM;
-p50/p99 over the per-step times (30 steps by default).
+p50/p99 over the per-step times.
 e2e:   the same through the C ABI with host (pinned) inputs: tddft_create
-       (host->device copy and conversion of every factor) + the two solves
-       with host outputs + tddft_destroy, every step.
-plain: the same step in the plain FP64 form on the same GPU (FP64 factors,
-       vectors and inner solves, SIMT contractions), for mixed vs plain.
-Inputs (the FP32/BF16 factors, 2.8 GB) are larger than L2, so no L2 flush is
-added between steps.
+       (host->device copy and conversion of every factor, 56 GB) + the two
+       solves with host outputs + tddft_destroy, every step.
+medium: the medium workload (n_occ=60, n_vir=400, n_aux=2000) as context:
+       Casida (10 states) + alpha(omega) per step, MIXED, and the same step in
+       the plain FP64 form (the plain form of the large step would take most
+       of an hour on GB300's FP64 units).
+Inputs (the resident factor copies, ~100 GB) are far larger than L2, so no L2
+flush is added between steps.
 
 serving: an open-loop Poisson stream of TDA / Casida / polarizability requests
        of random sizes through the server API (each request brings its own
@@ -30,7 +32,9 @@ Multi-GPU: one independent replica per GPU (the path does not shard on one
 box), launched under torch.distributed.run; rank 0 prints one JSON line.
 
 --impl reference times the CPU oracle (FP64, NumPy) on a bounded sample of the
-same workload and prints the same line with "impl": "reference".
+same workload (the exact and ris products of a few vectors over a few
+auxiliary rows, scaled to all rows and to the products one step makes) and
+prints the same line with "impl": "reference".
 """
 from __future__ import annotations
 
@@ -48,26 +52,37 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "rpa_polar_medium"
-N_STATES = 10
-METRIC = "states converged/s at ||r||<=1e-5 (Casida, rid, mixed) + alpha(omega) per step"
+WORKLOAD = "large_mixed"
+N_STATES = 20
+STATES_PER_STEP = 2 * N_STATES          # TDA + Casida
+METRIC = "states converged/s at ||r||<=1e-5 (TDA + Casida, 20 states each, rid, mixed)"
 UNIT = "states/s"
+MEDIUM = "rpa_polar_medium"
+MEDIUM_STATES = 10
+# Exact and ris products one step of the large workload makes (TDA vectors,
+# Casida pair vectors), as the mixed GPU solve counted them on GB300; the
+# oracle cannot run the Davidson iteration at this size (108 GB of FP64
+# factors), so its step time is its per-vector product time scaled by these.
+LARGE_COUNTS = {"tda_mv": 159, "tda_ris_mv": 2200, "rpa_mv": 490, "rpa_ris_mv": 6300}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tensor-cores", type=int, default=-1, help="1/0 (default 1: tcgen05 exchange)")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-diag", action="store_true", help="skip the diag-preconditioner iteration counts")
     ap.add_argument("--kernel-breakdown", action="store_true",
                     help="run one warm step under the CUDA activity profiler and print per-kernel totals")
+    ap.add_argument("--medium-steps", type=int, default=5,
+                    help="steps of the medium workload (0: skip the medium object)")
     ap.add_argument("--plain-steps", type=int, default=1,
-                    help="steps of the plain FP64 form timed for the mixed-vs-plain comparison (0: skip)")
+                    help="steps of the medium workload's plain FP64 form (mixed vs plain; 0: skip)")
     ap.add_argument("--precond", default="rid", choices=["rid", "diag"])
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served request stream (0: no serving measurement)")
@@ -80,6 +95,8 @@ def parse():
     ap.add_argument("--apply-only", type=int, default=0, metavar="K",
                     help="time K exact pair products ((A+B)X, (A-B)X) of 2*n_states device vectors "
                          "and exit (a short program for kernel profiling)")
+    ap.add_argument("--workload", default=WORKLOAD, help="workload of --apply-only / --kernel-breakdown")
+    ap.add_argument("--oracle-sample", type=int, default=0, metavar="THREADS", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -155,62 +172,156 @@ def load_peaks():
 
 
 def golden():
-    with open(os.path.join(ROOT, "tests", "golden", WORKLOAD + ".json")) as f:
+    with open(os.path.join(ROOT, "tests", "golden", MEDIUM + ".json")) as f:
         return json.load(f)
 
 
-def oracle_sample(seconds_budget=20.0):
-    """Time the oracle's exact and ris pair products on the workload's inputs and
-    scale them by the oracle's own product counts for one step (RPA + polar).
-    Returns (step_seconds, description, cores)."""
-    import numpy as np
-    from oracle import operators as O
-    from synth.generator import make_config
+# ---------------------------------------------------------------------------
+# CPU oracle samples (the reference arm and cpu_baseline)
 
-    p = make_config(WORKLOAD)
-    op, T = O.exact_operator(p), O.ris_operator(p)
-    g = golden()
-    X = np.random.default_rng(0).standard_normal((2, p.n_ov))
+def _oracle_sample_worker(seconds_budget):
+    """In a fresh process with the BLAS thread count of its environment: the
+    oracle's FP64 TDA product, pair product ((A+B)X, (A-B)X) and the ris
+    products of the large workload on a few auxiliary rows, as seconds per
+    vector over all rows.  Prints one JSON line."""
+    import types
+    from oracle import operators as O
+    from synth.generator import config_meta, factor_rows, ris_rows
+
+    meta = config_meta(WORKLOAD)
+    no, nv, na, nr = meta["n_occ"], meta["n_vir"], meta["n_aux"], meta["n_ris"]
+    rows, m = 8, 2
+    oo, ov, vv = factor_rows(WORKLOAD, 0, rows)
+    X = np.random.default_rng(0).standard_normal((m, no * nv))
+    op = O.Operator(meta["eps_occ"], meta["eps_vir"], ov, oo, ov, vv, meta["a_x"], meta["coulomb_factor"])
     t0 = time.perf_counter()
-    n_ex = 0
+    n = 0
     while True:
         op.apb_amb(X)
-        n_ex += 2
-        if time.perf_counter() - t0 > 0.7 * seconds_budget or n_ex >= 32:
+        n += 1
+        if time.perf_counter() - t0 > 0.4 * seconds_budget:
             break
-    t_ex = (time.perf_counter() - t0) / n_ex
-    Xr = np.random.default_rng(1).standard_normal((16, p.n_ov))
+    t_pair = (time.perf_counter() - t0) / n / m * (na / rows)
     t0 = time.perf_counter()
-    T.apb_amb(Xr)
-    t_ris = (time.perf_counter() - t0) / 16
-    n_mv = g["rpa"]["n_mv"] + g["polar"]["n_mv"]
-    n_ris = g["rpa"]["n_ris_mv"] + g["polar"]["n_ris_mv"]
-    step = t_ex * n_mv + t_ris * n_ris
-    desc = ("%d oracle (A+B, A-B) products + 16 ris pair products at the full workload size, "
-            "scaled by the oracle's own counts for one step (%d exact, %d ris vectors)" % (n_ex, n_mv, n_ris))
-    return step, desc, os.cpu_count()
+    op.tda(X)
+    t_tda = (time.perf_counter() - t0) / m * (na / rows)
+    roo, rov, rvv = ris_rows(WORKLOAD, 0, 9)
+    pr = types.SimpleNamespace(eps_occ=meta["eps_occ"], eps_vir=meta["eps_vir"], Lr_oo=roo, Lr_ov=rov,
+                               Lr_vv=rvv, ris_K_index=np.array([0], dtype=np.int32), a_x=meta["a_x"],
+                               coulomb_factor=meta["coulomb_factor"], t_cut_ha=meta["t_cut_ha"])
+    T = O.ris_operator(pr)
+    t0 = time.perf_counter()
+    T.apb_amb(X)
+    t_rpair = (time.perf_counter() - t0) / m * (nr / 9)
+    t0 = time.perf_counter()
+    T.tda(X)
+    t_rtda = (time.perf_counter() - t0) / m * (nr / 9)
+    print(json.dumps({"t_pair": t_pair, "t_tda": t_tda, "t_ris_pair": t_rpair, "t_ris_tda": t_rtda,
+                      "rows": rows, "vectors": m, "threads": os.environ.get("OPENBLAS_NUM_THREADS")}))
+
+
+def oracle_sample(threads=None, seconds_budget=8.0):
+    """Run _oracle_sample_worker in a fresh interpreter (its own BLAS thread
+    count: `threads`, or the library default) and return its timings."""
+    env = dict(os.environ)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if threads:
+            env[v] = str(threads)
+        else:
+            env.pop(v, None)
+    code = "import bench; bench._oracle_sample_worker(%r)" % seconds_budget
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-500:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_step_seconds(t, counts):
+    """Seconds of one large step on the oracle: per-vector product times times
+    the products a step makes (TDA: A X and T X; Casida: pair products)."""
+    return (t["t_tda"] * counts["tda_mv"] + t["t_ris_tda"] * counts["tda_ris_mv"] +
+            t["t_pair"] * counts["rpa_mv"] + t["t_ris_pair"] * counts["rpa_ris_mv"])
+
+
+def sample_note(t, counts):
+    return ("extrapolation: the oracle's FP64 TDA and pair products of %d vectors over %d of the 6000 "
+            "exact rows (and the ris products over 9 of the 1350 ris rows), scaled to all rows and to "
+            "the products of one step (%d TDA and %d Casida exact vectors, %d + %d ris vectors, as the "
+            "GPU solve counted them; the oracle cannot run this Davidson: 108 GB of FP64 factors); "
+            "BLAS threads: %s" % (t["vectors"], t["rows"], counts["tda_mv"], counts["rpa_mv"],
+                                  counts["tda_ris_mv"], counts["rpa_ris_mv"], t["threads"] or "default"))
 
 
 def reference_arm(args, rank, world):
     if rank != 0:
         return
     steps = []
-    desc = cores = None
+    t = None
+    budget = max(2.0, min(8.0, 150.0 / max(args.steps + args.warmup, 1)))
     for _ in range(args.warmup):
-        pass  # the oracle has nothing to warm up
+        oracle_sample(seconds_budget=budget)
     for _ in range(args.steps):
-        s, desc, cores = oracle_sample(seconds_budget=max(5.0, 60.0 / max(args.steps, 1)))
-        steps.append(s)
+        t = oracle_sample(seconds_budget=budget)
+        steps.append(oracle_step_seconds(t, LARGE_COUNTS))
     step = statistics.mean(steps)
-    value = N_STATES / step
+    value = STATES_PER_STEP / step
+    cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (NumPy)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": desc},
+                             "sample": sample_note(t, LARGE_COUNTS)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+
+def load_large(api, torch, stream_ptr, pinned_copy=False):
+    """The large workload's factors drawn chunk-wise on the host into FP32
+    device tensors (synth/chunked.py), a MIXED-only context created from them
+    and the staging tensors released; with pinned_copy, also a pinned host
+    copy of the inputs for the end-to-end measurement."""
+    from synth import chunked
+    from synth.generator import config_meta
+
+    meta = config_meta(WORKLOAD)
+    no, nv, na, nr = meta["n_occ"], meta["n_vir"], meta["n_aux"], meta["n_ris"]
+    kidx = meta["ris_K_index"]
+    t0 = time.time()
+    dev = (torch.empty(na, no, no, device="cuda"), torch.empty(na, no, nv, device="cuda"),
+           torch.empty(na, nv, nv, device="cuda"))
+    chunked.load_exact(WORKLOAD, meta, dev)
+    rdev = (torch.empty(kidx.size, no, no, device="cuda"), torch.empty(nr, no, nv, device="cuda"),
+            torch.empty(kidx.size, nv, nv, device="cuda"))
+    chunked.load_ris(WORKLOAD, meta, rdev)
+    small = {"eo": torch.from_numpy(meta["eps_occ"].copy()), "ev": torch.from_numpy(meta["eps_vir"].copy()),
+             "k": torch.from_numpy(kidx.copy())}
+    t_load = time.time() - t0
+    arrays = {"oo": dev[0], "ov": dev[1], "vv": dev[2], "roo": rdev[0], "rov": rdev[1], "rvv": rdev[2]}
+    host = None
+    if pinned_copy:
+        host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in arrays.items()}
+        for k, v in arrays.items():
+            host[k].copy_(v)
+        host.update({k: v.pin_memory() for k, v in small.items()})
+    src = dict(arrays)
+    src.update({k: v.cuda() for k, v in small.items()})
+    solver = make_solver(api, meta, src, stream_ptr)
+    torch.cuda.synchronize()
+    del dev, rdev, arrays, src
+    torch.cuda.empty_cache()
+    return solver, meta, host, t_load
+
+
+def make_solver(api, meta, src, stream_ptr):
+    return api.Solver(meta["n_occ"], meta["n_vir"], src["eo"], src["ev"], src["oo"], src["ov"], src["vv"],
+                      src["roo"], src["rov"], src["rvv"], src["k"], a_x=meta["a_x"],
+                      coulomb_factor=meta["coulomb_factor"], t_cut_ha=meta["t_cut_ha"], precisions=2,
+                      dtype=api.F32, stream=stream_ptr)
 
 
 def our_arm(args, rank, world, local):
@@ -223,48 +334,27 @@ def our_arm(args, rank, world, local):
     import __graft_entry__ as ge
     ge.build()
     from paper_2404_17133_gb300 import api
-    from synth.generator import CONFIGS, dipoles, make_config
 
-    cfg = CONFIGS[WORKLOAD]
-    p = make_config(WORKLOAD)
-    mu = dipoles(cfg["mu_seed"], cfg["n_dip"], p.n_ov)
-    omegas = list(cfg["omegas"])
-    tc = args.tensor_cores
-    if tc < 0:
-        tc = 1
+    tc = 1 if args.tensor_cores < 0 else args.tensor_cores
     stream = torch.cuda.current_stream()
-    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
-    kidx = p.ris_K_index
-    host = {"eo": torch.from_numpy(p.eps_occ.copy()), "ev": torch.from_numpy(p.eps_vir.copy()),
-            "oo": f32(p.L_oo), "ov": f32(p.L_ov), "vv": f32(p.L_vv), "roo": f32(p.Lr_oo[kidx]),
-            "rov": f32(p.Lr_ov), "rvv": f32(p.Lr_vv[kidx]), "k": torch.from_numpy(kidx.copy())}
-    dev = {k: v.cuda() for k, v in host.items()}
-    pinned = {k: v.pin_memory() for k, v in host.items()}
-    h2d_bytes = sum(v.numel() * v.element_size() for v in host.values()) + mu.nbytes + 8 * len(omegas)
-    d2h_bytes = 8 * (2 * N_STATES + len(omegas) * cfg["n_dip"] ** 2)
-
-    def make_solver(src, stream_ptr):
-        return api.Solver(p.n_occ, p.n_vir, src["eo"], src["ev"], src["oo"], src["ov"], src["vv"],
-                          src["roo"], src["rov"], src["rvv"], src["k"], a_x=p.a_x,
-                          coulomb_factor=p.coulomb_factor, t_cut_ha=p.t_cut_ha, precisions=2,
-                          dtype=api.F32, stream=stream_ptr)
-
+    if args.apply_only > 0 or args.kernel_breakdown:
+        solver, p = small_solver(args, api, torch, stream)
+        if args.apply_only > 0:
+            apply_only(args, api, solver, p, tc, stream)
+        else:
+            kernel_breakdown(args, api, solver, tc)
+        solver.close()
+        return
+    want_e2e = not args.no_e2e and rank == 0
+    solver, meta, host, t_load = load_large(api, torch, stream.cuda_stream, pinned_copy=want_e2e)
+    h2d_bytes = sum(v.numel() * v.element_size() for v in host.values()) if host else 0
+    d2h_bytes = 8 * (2 * N_STATES + 2 * N_STATES)     # energies and residual norms of both solves
     pc = api.RID if args.precond == "rid" else api.DIAG
-    o_rpa = api.default_opts(n_states=N_STATES, precond=pc, precision=api.MIXED, tensor_cores=tc)
-    o_pol = api.default_opts(precond=pc, precision=api.MIXED, tensor_cores=tc)
-    solver = make_solver(dev, stream.cuda_stream)
-    if args.apply_only > 0:
-        apply_only(args, api, solver, p, tc, stream)
-        solver.close()
-        return
-    if args.kernel_breakdown:
-        kernel_breakdown(solver, o_rpa, o_pol, mu, omegas)
-        solver.close()
-        return
+    o = api.default_opts(n_states=N_STATES, precond=pc, precision=api.MIXED, tensor_cores=tc)
 
     def step(s):
-        a = s.solve_rpa(o_rpa, want_vectors=False)
-        b = s.solve_polar(o_pol, mu, omegas)
+        a = s.solve_tda(o, want_vectors=False)
+        b = s.solve_rpa(o, want_vectors=False)
         return a, b
 
     for _ in range(max(args.warmup, 0)):
@@ -293,74 +383,122 @@ def our_arm(args, rank, world, local):
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     total_ms = max_over_ranks(total_ms, world)
-    value = replica_throughput(N_STATES * args.steps, world, total_ms)
+    value = replica_throughput(STATES_PER_STEP * args.steps, world, total_ms)
     a, b = results[-1]
     conv = all(r["status"] == api.OK for pair in results for r in pair)
+    counts = {"tda_mv": a["stats"]["n_matvec"], "tda_ris_mv": a["stats"]["n_ris_matvec"],
+              "rpa_mv": b["stats"]["n_matvec"], "rpa_ris_mv": b["stats"]["n_ris_matvec"]}
+
+    diag = None
+    if not args.no_diag and rank == 0:
+        od = api.default_opts(n_states=N_STATES, precond=api.DIAG, precision=api.MIXED, tensor_cores=tc)
+        da, db = solver.solve_tda(od, want_vectors=False), solver.solve_rpa(od, want_vectors=False)
+        diag = {"tda_n_iter": da["stats"]["n_iter"], "rpa_n_iter": db["stats"]["n_iter"],
+                "tda_s": da["stats"]["t_total_s"], "rpa_s": db["stats"]["t_total_s"],
+                "converged": da["status"] == api.OK and db["status"] == api.OK,
+                "max_abs_omega_diff_vs_rid": float(max(np.max(np.abs(da["omega"] - a["omega"])),
+                                                       np.max(np.abs(db["omega"] - b["omega"]))))}
+    peaks, src = load_peaks()
+    roof = roofline(prof, rec_ms, rec_fl, rec_by, peaks, src, tc, clk, total_ms)
 
     # ---- end to end through the C ABI with pinned host inputs and host outputs
     e2e_ms = []
-    for _ in range(0 if args.no_e2e else max(args.e2e_steps, 1)):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s2 = make_solver(pinned, stream.cuda_stream)
-        step(s2)
-        s2.close()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    e2e_t = statistics.mean(e2e_ms) if e2e_ms else float("nan")
-
-    # ---- the plain FP64 form of the same step (FP64 inputs, FP64 everywhere, SIMT)
-    plain = None
-    if args.plain_steps > 0 and rank == 0:
-        f64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
-        sp = api.Solver(p.n_occ, p.n_vir, dev["eo"], dev["ev"], f64(p.L_oo), f64(p.L_ov), f64(p.L_vv),
-                        f64(p.Lr_oo[kidx]), f64(p.Lr_ov), f64(p.Lr_vv[kidx]), dev["k"], a_x=p.a_x,
-                        coulomb_factor=p.coulomb_factor, t_cut_ha=p.t_cut_ha, precisions=1, dtype=api.F64,
-                        stream=stream.cuda_stream)
-        o_rpa_p = api.default_opts(n_states=N_STATES, precond=pc, precision=api.PLAIN)
-        o_pol_p = api.default_opts(precond=pc, precision=api.PLAIN)
-        pms, pit = [], []
-        for _ in range(args.plain_steps):
+    if want_e2e:
+        solver.close()
+        solver = None
+        torch.cuda.empty_cache()
+        for _ in range(max(args.e2e_steps, 1)):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ra = sp.solve_rpa(o_rpa_p, want_vectors=False)
-            rb = sp.solve_polar(o_pol_p, mu, omegas)
+            s2 = make_solver(api, meta, host, stream.cuda_stream)
+            step(s2)
+            s2.close()
             e1.record(stream)
             torch.cuda.synchronize()
-            pms.append(e0.elapsed_time(e1))
-            pit.append((ra["stats"]["n_iter"], rb["stats"]["n_iter"]))
-        sp.close()
-        pm = statistics.mean(pms)
-        plain = {"value": N_STATES / (pm / 1e3), "unit": UNIT, "ms_per_step": pm, "steps": args.plain_steps,
-                 "dtype": "f64", "rpa_n_iter": pit[-1][0], "polar_n_iter": pit[-1][1],
-                 "max_abs_omega_diff_vs_mixed": float(np.max(np.abs(np.asarray(ra["omega"]) -
-                                                                    np.asarray(results[-1][0]["omega"])))),
-                 "note": "same step in the plain form: FP64 factors and vectors, SIMT contractions, "
-                         "FP64 inner solves; warm kernels, one step"}
+            e2e_ms.append(e0.elapsed_time(e1))
+        host = None
+    e2e_t = statistics.mean(e2e_ms) if e2e_ms else float("nan")
     e2e_t = max_over_ranks(e2e_t, world)
-    if rank != 0:
+    if solver is not None:
         solver.close()
+        solver = None
+    torch.cuda.empty_cache()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
-    peaks, src = load_peaks()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tensor: bf16x3) + fp64 subspace",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_occ": meta["n_occ"], "n_vir": meta["n_vir"],
+                       "n_aux": meta["n_aux"], "n_aux_ris": meta["n_ris"], "n_states": N_STATES,
+                       "solves_per_step": ["tda", "casida"], "precond": args.precond,
+                       "tensor_cores": bool(tc), "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (~100 GB resident factor copies), no flush"},
+            "p50_ms": statistics.median(per_step),
+            "p99_ms": sorted(per_step)[min(len(per_step) - 1, int(0.99 * len(per_step)))],
+            "converged": conv, "load_s": t_load,
+            "tda": {"omega0": float(a["omega"][0]), "n_iter": a["stats"]["n_iter"],
+                    "n_matvec": a["stats"]["n_matvec"], "n_ris_matvec": a["stats"]["n_ris_matvec"],
+                    "max_resid_certified": a["stats"]["max_resid_certified"], "s": a["stats"]["t_total_s"]},
+            "rpa": {"omega0": float(b["omega"][0]), "n_iter": b["stats"]["n_iter"],
+                    "n_matvec": b["stats"]["n_matvec"], "n_ris_matvec": b["stats"]["n_ris_matvec"],
+                    "max_resid_certified": b["stats"]["max_resid_certified"], "s": b["stats"]["t_total_s"]},
+            "diag": diag,
+            "roofline": roof,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": {"value": STATES_PER_STEP * world / (e2e_t / 1e3) if e2e_ms else None, "unit": UNIT,
+                    "ms_per_step": e2e_t if e2e_ms else None,
+                    "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes)}}
+    if args.medium_steps > 0 and world == 1:
+        try:
+            line["medium"] = medium(args, api, torch, stream, tc)
+        except Exception as e:
+            line["medium"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    if args.serve_seconds > 0 and world == 1:
+        try:
+            line["serving"] = serving(args, api, torch)
+        except Exception as e:   # the served stream is reported, not required for the line
+            line["serving"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    if args.batch > 0 and world == 1:
+        for key, t in (("batched", 0), ("batched_tc", 1)):
+            try:
+                line[key] = batched(args, api, torch, tc=t)
+            except Exception as e:
+                line[key] = {"error": "%s: %s" % (type(e).__name__, e)}
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            tm = oracle_sample()
+            t1 = oracle_sample(threads=1)
+            step_s = oracle_step_seconds(tm, counts)
+            line["cpu_baseline"] = {"value": STATES_PER_STEP / step_s, "unit": UNIT, "cores": os.cpu_count(),
+                                    "kind": "oracle", "sample": sample_note(tm, counts),
+                                    "single_thread_value": STATES_PER_STEP / oracle_step_seconds(t1, counts)}
+        except Exception as e:
+            line["cpu_baseline"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def roofline(prof, rec_ms, rec_fl, rec_by, peaks, src, tc, clk, total_ms):
+    """Roofline object of the dominant kernel (the K1 exchange contraction)."""
     kernel_ms = prof["ms"] / max(prof["launches"], 1)
     flops_launch = prof["flops"] / max(prof["launches"], 1)
     achieved = flops_launch / (kernel_ms * 1e-3) / 1e12 if prof["launches"] else 0.0
     if tc:
         peak = peaks["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_kind": "bf16 sustained, " + src,
-                "note": "algorithmic flops 2*M*N*K; the hi+lo split issues 3 BF16 products per flop"}
+                "note": "algorithmic flops 2*M*N*K; the hi+lo split issues 3 BF16 products per flop, "
+                        "so frac <= 1/3 (mma_pipe_frac = 3 x frac)"}
     else:
         sm = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * sm * 1e6 / 1e12
         roof = {"bound": "alu", "unit": "TFLOP/s",
                 "peak_kind": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % sm}
-    # per-launch roofline: the launch's attainable time is the larger of its
-    # tensor time (tcgen05: three BF16 products per algorithmic flop for the
-    # hi+lo exact factors) and its HBM time (algorithmic bytes at the measured
-    # copy bandwidth); small trial blocks make a launch HBM-bound
     if rec_ms.size:
         per_flop = 3.0 if tc else 1.0
         t_ten = rec_fl * per_flop / (peak * 1e12) * 1e3
@@ -375,57 +513,81 @@ def our_arm(args, rank, world, local):
                                "at hbm_gbs %.0f); attainable_frac = sum of those / sum of measured times"
                                % (per_flop, peaks["hbm_gbs"])})
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak if peak else None,
+                 "mma_pipe_frac": 3.0 * achieved / peak if (peak and tc) else None,
                  "traffic": None, "kernel": "exchange K1 contraction sum_(P,a) Z L_vv",
                  "launches": prof["launches"], "ms_per_launch": kernel_ms,
                  "share_of_step": prof["ms"] / total_ms if total_ms else None})
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tensor: bf16x3) + fp64 subspace",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_occ": p.n_occ, "n_vir": p.n_vir, "n_aux": p.n_aux,
-                       "n_aux_ris": p.n_ris, "n_states": N_STATES, "n_dip": cfg["n_dip"],
-                       "omegas": omegas, "precond": args.precond, "tensor_cores": bool(tc),
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (2.8 GB resident factors), no flush"},
-            "p50_ms": statistics.median(per_step),
-            "p99_ms": sorted(per_step)[min(len(per_step) - 1, int(0.99 * len(per_step)))],
-            "converged": conv,
-            "rpa": {"omega": list(map(float, a["omega"])), "n_iter": a["stats"]["n_iter"],
-                    "n_matvec": a["stats"]["n_matvec"], "n_ris_matvec": a["stats"]["n_ris_matvec"],
-                    "max_resid": a["stats"]["max_resid"],
-                    "max_resid_certified": a["stats"]["max_resid_certified"],
-                    "t_precond_share": a["stats"]["t_precond_s"] / max(a["stats"]["t_total_s"], 1e-12)},
-            "polar": {"n_iter": b["stats"]["n_iter"], "n_matvec": b["stats"]["n_matvec"],
-                      "alpha_static_diag": [float(b["alpha"][0][i][i]) for i in range(cfg["n_dip"])]},
-            "roofline": roof,
-            "plain": plain,
-            "speedup_vs_plain": (plain["ms_per_step"] / (total_ms / args.steps)) if plain else None,
-            "gpu_launches": launches,
-            "clocks": clk,
-            "e2e": {"value": N_STATES * world / (e2e_t / 1e3), "unit": UNIT, "ms_per_step": e2e_t,
-                    "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes)}}
-    if args.serve_seconds > 0 and world == 1:
+    return roof
+
+
+def medium(args, api, torch, stream, tc):
+    """Context object: the medium workload's step (Casida, 10 states, + alpha at
+    3 frequencies, rid, MIXED) and the same step in the plain FP64 form."""
+    from synth.generator import CONFIGS, dipoles, make_config
+
+    cfg = CONFIGS[MEDIUM]
+    p = make_config(MEDIUM)
+    mu = dipoles(cfg["mu_seed"], cfg["n_dip"], p.n_ov)
+    omegas = list(cfg["omegas"])
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    kidx = p.ris_K_index
+    eo, ev, k = (torch.from_numpy(p.eps_occ.copy()).cuda(), torch.from_numpy(p.eps_vir.copy()).cuda(),
+                 torch.from_numpy(kidx.copy()).cuda())
+    s = api.Solver(p.n_occ, p.n_vir, eo, ev, f32(p.L_oo), f32(p.L_ov), f32(p.L_vv), f32(p.Lr_oo[kidx]),
+                   f32(p.Lr_ov), f32(p.Lr_vv[kidx]), k, a_x=p.a_x, coulomb_factor=p.coulomb_factor,
+                   t_cut_ha=p.t_cut_ha, precisions=2, dtype=api.F32, stream=stream.cuda_stream)
+    o_rpa = api.default_opts(n_states=MEDIUM_STATES, precond=api.RID, precision=api.MIXED, tensor_cores=tc)
+    o_pol = api.default_opts(precond=api.RID, precision=api.MIXED, tensor_cores=tc)
+
+    def step(sv):
+        return sv.solve_rpa(o_rpa, want_vectors=False), sv.solve_polar(o_pol, mu, omegas)
+
+    try:
+        for _ in range(2):
+            step(s)
+        torch.cuda.synchronize()
+        ev_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.medium_steps + 1)]
+        ev_[0].record(stream)
+        for i in range(args.medium_steps):
+            a, b = step(s)
+            ev_[i + 1].record(stream)
+        torch.cuda.synchronize()
+    finally:
+        s.close()
+    per = [ev_[i].elapsed_time(ev_[i + 1]) for i in range(args.medium_steps)]
+    ms = ev_[0].elapsed_time(ev_[-1]) / args.medium_steps
+    out = {"workload": MEDIUM, "value": MEDIUM_STATES / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "p50_ms": statistics.median(per), "steps": args.medium_steps,
+           "rpa_n_iter": a["stats"]["n_iter"], "polar_n_iter": b["stats"]["n_iter"],
+           "oracle_rpa_n_iter": golden()["rpa"]["n_iter"],
+           "max_resid_certified": a["stats"]["max_resid_certified"]}
+    if args.plain_steps > 0:
+        f64 = lambda a_: torch.from_numpy(np.ascontiguousarray(a_, dtype=np.float64)).cuda()
+        sp = api.Solver(p.n_occ, p.n_vir, eo, ev, f64(p.L_oo), f64(p.L_ov), f64(p.L_vv), f64(p.Lr_oo[kidx]),
+                        f64(p.Lr_ov), f64(p.Lr_vv[kidx]), k, a_x=p.a_x, coulomb_factor=p.coulomb_factor,
+                        t_cut_ha=p.t_cut_ha, precisions=1, dtype=api.F64, stream=stream.cuda_stream)
+        o_rpa_p = api.default_opts(n_states=MEDIUM_STATES, precond=api.RID, precision=api.PLAIN)
+        o_pol_p = api.default_opts(precond=api.RID, precision=api.PLAIN)
+        pms = []
         try:
-            line["serving"] = serving(args, api, torch)
-        except Exception as e:   # the served stream is reported, not required for the line
-            line["serving"] = {"error": "%s: %s" % (type(e).__name__, e)}
-    if args.batch > 0 and world == 1:
-        try:
-            line["batched"] = batched(args, api, torch)
-        except Exception as e:
-            line["batched"] = {"error": "%s: %s" % (type(e).__name__, e)}
-        try:
-            line["batched_tc"] = batched(args, api, torch, tc=1)
-        except Exception as e:
-            line["batched_tc"] = {"error": "%s: %s" % (type(e).__name__, e)}
-    if not args.no_cpu_baseline and world == 1:
-        step_s, desc, cores = oracle_sample()
-        line["cpu_baseline"] = {"value": N_STATES / step_s, "unit": UNIT, "cores": cores,
-                                "kind": "oracle", "sample": desc}
-    print(json.dumps(line), flush=True)
-    solver.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+            for _ in range(args.plain_steps):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ra = sp.solve_rpa(o_rpa_p, want_vectors=False)
+                rb = sp.solve_polar(o_pol_p, mu, omegas)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                pms.append(e0.elapsed_time(e1))
+        finally:
+            sp.close()
+        pm = statistics.mean(pms)
+        out["plain"] = {"value": MEDIUM_STATES / (pm / 1e3), "unit": UNIT, "ms_per_step": pm,
+                        "steps": args.plain_steps, "dtype": "f64", "rpa_n_iter": ra["stats"]["n_iter"],
+                        "polar_n_iter": rb["stats"]["n_iter"],
+                        "max_abs_omega_diff_vs_mixed": float(np.max(np.abs(ra["omega"] - a["omega"])))}
+        out["speedup_vs_plain"] = pm / ms
+    return out
 
 
 def _run_stream(api, reqs, arrivals, slots, budget_gb, warm_kw):
@@ -575,10 +737,28 @@ def batched(args, api, torch, tc=0):
     return out
 
 
-def apply_only(args, api, solver, p, tc, stream):
+def small_solver(args, api, torch, stream):
+    """A MIXED context for --apply-only / --kernel-breakdown on args.workload."""
+    if args.workload == WORKLOAD:
+        solver, meta, _, _ = load_large(api, torch, stream.cuda_stream)
+        return solver, meta
+    from synth.generator import make_config
+    p = make_config(args.workload)
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    kidx = p.ris_K_index
+    s = api.Solver(p.n_occ, p.n_vir, torch.from_numpy(p.eps_occ.copy()).cuda(),
+                   torch.from_numpy(p.eps_vir.copy()).cuda(), f32(p.L_oo), f32(p.L_ov), f32(p.L_vv),
+                   f32(p.Lr_oo[kidx]), f32(p.Lr_ov), f32(p.Lr_vv[kidx]), torch.from_numpy(kidx.copy()).cuda(),
+                   a_x=p.a_x, coulomb_factor=p.coulomb_factor, t_cut_ha=p.t_cut_ha, precisions=2,
+                   dtype=api.F32, stream=stream.cuda_stream)
+    return s, {"n_occ": p.n_occ, "n_vir": p.n_vir}
+
+
+def apply_only(args, api, solver, meta, tc, stream):
     """K exact pair products on 2*n_states device vectors, each timed with CUDA events."""
     import torch
-    X = torch.from_numpy(np.random.default_rng(7).standard_normal((2 * N_STATES, p.n_ov))).cuda()
+    m = 2 * (N_STATES if args.workload == WORKLOAD else MEDIUM_STATES)
+    X = torch.from_numpy(np.random.default_rng(7).standard_normal((m, meta["n_occ"] * meta["n_vir"]))).cuda()
     ms = []
     for _ in range(args.apply_only):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -587,21 +767,34 @@ def apply_only(args, api, solver, p, tc, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
-    print(json.dumps({"apply_only": args.apply_only, "m": 2 * N_STATES, "ms": ms,
-                      "workload": WORKLOAD, "tensor_cores": bool(tc)}), flush=True)
+    print(json.dumps({"apply_only": args.apply_only, "m": m, "ms": ms,
+                      "workload": args.workload, "tensor_cores": bool(tc)}), flush=True)
 
 
-def kernel_breakdown(solver, o_rpa, o_pol, mu, omegas):
+def kernel_breakdown(args, api, solver, tc):
     """One warm step under the CUDA activity profiler (CUPTI): every kernel and
     copy with its device time; printed as one JSON line."""
     import collections
     import re
     import torch
     from torch.profiler import ProfilerActivity, profile
+    from synth.generator import CONFIGS, dipoles
 
-    def step():
-        solver.solve_rpa(o_rpa, want_vectors=False)
-        solver.solve_polar(o_pol, mu, omegas)
+    if args.workload == WORKLOAD:
+        o = api.default_opts(n_states=N_STATES, precond=api.RID, precision=api.MIXED, tensor_cores=tc)
+
+        def step():
+            solver.solve_tda(o, want_vectors=False)
+            solver.solve_rpa(o, want_vectors=False)
+    else:
+        cfg = CONFIGS[args.workload]
+        mu = dipoles(cfg["mu_seed"], cfg.get("n_dip", 3), solver.n_ov)
+        o_rpa = api.default_opts(n_states=cfg["n_states"], precond=api.RID, precision=api.MIXED, tensor_cores=tc)
+        o_pol = api.default_opts(precond=api.RID, precision=api.MIXED, tensor_cores=tc)
+
+        def step():
+            solver.solve_rpa(o_rpa, want_vectors=False)
+            solver.solve_polar(o_pol, mu, list(cfg.get("omegas", (0.0,))))
 
     step()
     torch.cuda.synchronize()
@@ -623,8 +816,7 @@ def kernel_breakdown(solver, o_rpa, o_pol, mu, omegas):
     rows = [{"kernel": k, "launches": cnt[k], "ms": round(v / 1e3, 3), "share": round(v / busy, 4)}
             for k, v in sorted(tot.items(), key=lambda x: -x[1])]
     print(json.dumps({"kernel_breakdown": rows, "busy_ms": busy / 1e3, "span_ms": (span1 - span0) / 1e3,
-                      "first_start_ms": span0 / 1e3, "last_end_ms": span1 / 1e3, "events": len(ev),
-                      "wall_ms": wall * 1e3, "workload": WORKLOAD}), flush=True)
+                      "events": len(ev), "wall_ms": wall * 1e3, "workload": args.workload}), flush=True)
 
 
 def main():
