@@ -97,6 +97,10 @@ typedef struct {
   int precision;              /* tddft_precision                              */
   int tensor_cores;           /* MIXED only: tcgen05 BF16 hi+lo exchange      */
   int outputs_on_device;      /* 1: omega/X/Y/resid/alpha are device pointers */
+  int ris_fp8;                /* MIXED + tensor_cores: the ris exchange products of
+                               * the rid preconditioner (Eq. TDDFT-ris_approx) in
+                               * FP8 e4m3 with one scale per auxiliary row,
+                               * FP32 accumulation; 0: BF16 ris factors        */
 } tddft_opts;
 
 typedef struct {
@@ -195,7 +199,10 @@ tddft_status tddft_add_kernel(tddft_ctx* ctx, int n_g, const double* w, const vo
  *   kind 3: ((T_A+T_B)X, (T_A-T_B)X) ris.
  * X [m][ov]; out0 [m][ov]; out1 [m][ov] for kinds 1 and 3 (else NULL).
  * precision / tensor_cores as in tddft_opts (for the ris kinds the tensor
- * cores form one BF16 product); on_device: pointers are device memory.
+ * cores form two products, trial vectors as BF16 hi + lo against the BF16
+ * ris rows); tensor_cores = 2 runs the ris kinds' exchange contractions with
+ * the FP8 e4m3 ris rows (tddft_opts.ris_fp8); on_device: pointers are device
+ * memory.
  * Results are FP64.                                                        */
 tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cores,
                          const double* X, int m, double* out0, double* out1, int on_device);

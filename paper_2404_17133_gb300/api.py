@@ -41,7 +41,8 @@ class Opts(C.Structure):
     _fields_ = [("precond", C.c_int), ("n_states", C.c_int), ("n_extra_guess", C.c_int),
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("guess_tol", C.c_double),
                 ("max_iter", C.c_int), ("inner_max_iter", C.c_int), ("max_subspace", C.c_int),
-                ("precision", C.c_int), ("tensor_cores", C.c_int), ("outputs_on_device", C.c_int)]
+                ("precision", C.c_int), ("tensor_cores", C.c_int), ("outputs_on_device", C.c_int),
+                ("ris_fp8", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -375,19 +376,20 @@ class Solver:
         return dict(status=s, alpha=alpha, stats=st.as_dict())
 
     def apply(self, kind, X, precision=PLAIN, tensor_cores=False):
-        """kind 0: A X, 1: ((A+B)X, (A-B)X), 2: T X (ris), 3: ris pair."""
+        """kind 0: A X, 1: ((A+B)X, (A-B)X), 2: T X (ris), 3: ris pair.
+        tensor_cores: 0/False SIMT, 1/True tcgen05, 2 tcgen05 with the FP8 ris rows."""
         if _is_cuda(X):
             import torch
             out0 = torch.empty_like(X)
             out1 = torch.empty_like(X) if kind in (1, 3) else None
-            s = _lib.tddft_apply(self.h, kind, precision, int(bool(tensor_cores)), C.c_void_p(X.data_ptr()),
+            s = _lib.tddft_apply(self.h, kind, precision, int(tensor_cores), C.c_void_p(X.data_ptr()),
                                  X.shape[0], C.c_void_p(out0.data_ptr()),
                                  C.c_void_p(out1.data_ptr()) if out1 is not None else None, 1)
         else:
             X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.float64)
             out0 = np.zeros_like(X)
             out1 = np.zeros_like(X) if kind in (1, 3) else None
-            s = _lib.tddft_apply(self.h, kind, precision, int(bool(tensor_cores)),
+            s = _lib.tddft_apply(self.h, kind, precision, int(tensor_cores),
                                  X.ctypes.data_as(C.c_void_p), X.shape[0], out0.ctypes.data_as(C.c_void_p),
                                  out1.ctypes.data_as(C.c_void_p) if out1 is not None else None, 0)
         self._check(s, allow_noconv=False)

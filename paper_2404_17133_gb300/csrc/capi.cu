@@ -174,8 +174,10 @@ unsigned long long factor_copy_bytes(const tddft_desc& d) {
   const double padded = nv * (tc_pad(d.n_vir) + tc_pad(d.n_occ)) + no * (tc_pad(d.n_occ) + tc_pad(d.n_vir));
   double bytes = 0.0;
   if (p64) bytes += 8.0 * (nvv + noo + nov + nr);
+  // FP8 copies of the ris exchange rows: vv and ov^T padded to 16, four floats per row
+  const double fp8 = (double)d.n_aux_ris_K * (nv * (tc_pad16(d.n_vir) + tc_pad16(d.n_occ)) + 16.0);
   if (pmx) bytes += 4.0 * (nvv + noo + nov) + 4.0 * (double)d.n_aux * padded + 2.0 * nr +
-                    2.0 * (double)d.n_aux_ris_K * padded;
+                    2.0 * (double)d.n_aux_ris_K * padded + fp8;
   return (unsigned long long)bytes;
 }
 
@@ -215,7 +217,7 @@ FactorSet Ctx::exact(int precision) const {
   return f;
 }
 
-FactorSet Ctx::ris(int precision) const {
+FactorSet Ctx::ris(int precision, bool fp8) const {
   FactorSet f;
   f.nJ = nJ;
   f.nK = nK;
@@ -229,6 +231,15 @@ FactorSet Ctx::ris(int precision) const {
     f.Kvo_hi = r16_vo.as<__nv_bfloat16>();
     f.Koo_hi = r16_oop.as<__nv_bfloat16>();
     f.Kovp_hi = r16_ovp.as<__nv_bfloat16>();
+    if (fp8 && nK > 0 && r8_vvp.p) {
+      f.fp8 = true;
+      f.Kvv8 = r8_vvp.as<unsigned char>();
+      f.Kvo8 = r8_vo.as<unsigned char>();
+      f.s_vv = r8_aux.as<float>();
+      f.s_vo = f.s_vv + nK;
+      f.rho_oo = f.s_vv + 2 * nK;
+      f.rho_ov = f.s_vv + 3 * nK;
+    }
   }
   return f;
 }
@@ -252,6 +263,7 @@ void tddft_default_opts(tddft_opts* o) {
   o->precision = TDDFT_PLAIN;
   o->tensor_cores = 0;
   o->outputs_on_device = 0;
+  o->ris_fp8 = 0;
 }
 
 void tddft_default_desc(tddft_desc* d) {
@@ -445,6 +457,15 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
         c->r16_ovp = DevBuf(RK * no * tc_pad(nv) * 2, s);
         tc_pad_split(c->r16_Koo.p, DType::BF16, RK * no, no, c->r16_oop.as<__nv_bfloat16>(), nullptr, s);
         tc_pad_split(c->r16_Kov.p, DType::BF16, RK * no, nv, c->r16_ovp.as<__nv_bfloat16>(), nullptr, s);
+        // FP8 e4m3 copies with a scale per row (opts.ris_fp8), from the windowed BF16 rows
+        c->r8_vvp = DevBuf(RK * nv * tc_pad16(nv), s);
+        c->r8_vo = DevBuf(RK * nv * tc_pad16(no), s);
+        c->r8_aux = DevBuf(RK * 4 * 4, s);
+        float* aux = c->r8_aux.as<float>();
+        tc_quant_e4m3(c->r16_Kvv.as<__nv_bfloat16>(), (int)RK, nv, nv, c->r8_vvp.as<unsigned char>(), aux, s);
+        tc_quant_e4m3(c->r16_Kov.as<__nv_bfloat16>(), (int)RK, no, nv, c->r8_vo.as<unsigned char>(), aux + RK, s);
+        tc_row_norm_max(c->r16_Koo.as<__nv_bfloat16>(), (int)RK, no, no, aux + 2 * RK, s);
+        tc_row_norm_max(c->r16_Kov.as<__nv_bfloat16>(), (int)RK, no, nv, aux + 3 * RK, s);
       }
       TD_CUDA(cudaStreamSynchronize(s));
     }
@@ -522,7 +543,8 @@ tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cor
     const size_t n = (size_t)m * c->ov;
     const bool ris = kind >= 2;
     const bool paired = kind & 1;
-    FactorSet f = ris ? c->ris(precision) : c->exact(precision);
+    TD_REQUIRE(tensor_cores >= 0 && tensor_cores <= 2, TDDFT_ERR_ARG, "tensor_cores must be 0, 1 or 2");
+    FactorSet f = ris ? c->ris(precision, tensor_cores == 2) : c->exact(precision);
     DevBuf xb, o0, o1;
     const double* Xd = X;
     double* d0 = out0;

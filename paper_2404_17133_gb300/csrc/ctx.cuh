@@ -40,6 +40,18 @@ struct FactorSet {
   // scaled by sqrt|w_g| and split by the sign of w_g (element type dt).
   const FactorSet* lr = nullptr;
   double b_x = 0.0;
+  // FP8 e4m3 copies of the (BF16) ris exchange rows with one scale per row P,
+  // used by the tensor-core path when fp8 is set: Kvv8 as [P][b][tc_pad16(a)],
+  // Kvo8 (L_ov transposed) as [P][a][tc_pad16(j)]; s_vv / s_vo the scales,
+  // rho_oo / rho_ov the largest row norms of L^P_oo and L^P_ov (bounds of the
+  // stage-1 results)
+  bool fp8 = false;
+  const unsigned char* Kvv8 = nullptr;
+  const unsigned char* Kvo8 = nullptr;
+  const float* s_vv = nullptr;
+  const float* s_vo = nullptr;
+  const float* rho_oo = nullptr;
+  const float* rho_ov = nullptr;
   const void* Fpos = nullptr;
   const void* Fneg = nullptr;
   int nFpos = 0, nFneg = 0;
@@ -135,6 +147,8 @@ struct Ctx {
   DevBuf r64_J, r64_Koo, r64_Kvv, r64_Kov;
   DevBuf r16_J, r16_Koo, r16_Kvv, r16_Kov;
   DevBuf r16_vvp, r16_vo, r16_oop, r16_ovp;   // tensor-core copies of the ris exchange rows
+  DevBuf r8_vvp, r8_vo;           // FP8 e4m3 copies of the ris exchange rows (FactorSet::Kvv8, Kvo8)
+  DevBuf r8_aux;                  // float [4][n_K]: s_vv, s_vo, rho_oo, rho_ov
   tddft_desc desc{};              // as given to tddft_create
   unsigned long long device_bytes = 0;
   std::string err;
@@ -159,7 +173,7 @@ struct Ctx {
     return d;
   }
   FactorSet exact(int precision) const;  // PLAIN -> FP64, MIXED -> FP32 (+ BF16 split)
-  FactorSet ris(int precision) const;    // PLAIN -> FP64, MIXED -> BF16
+  FactorSet ris(int precision, bool fp8 = false) const;  // PLAIN -> FP64, MIXED -> BF16 (+ FP8)
 };
 
 // Throw if the tensor-core kernel reported a timeout since the last check.

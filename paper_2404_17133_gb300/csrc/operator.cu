@@ -167,7 +167,51 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
     TD_REQUIRE(!tensor_cores || f64 || use_tc, TDDFT_ERR_ARG, "tensor-core factor copies missing");
     const int pc = chunk_rows(f.nK, (long long)m * ov * (long long)ew, m);
     const size_t es = dtype_size(f.dt);
-    if (use_tc) {
+    if (use_tc && f.fp8) {
+      // ris exchange rows in FP8 e4m3 (one scale per row P): the stage-1
+      // products Z = L_oo X and Q = L_ov X^T run as for BF16 (trial vectors as
+      // BF16 hi + lo against the BF16 rows) and leave their results as e4m3
+      // hi + lo, multiplied by mu_P; the second contractions run as
+      // kind::f8f6f4 (two products: hi and lo against the e4m3 rows) and the
+      // sums are multiplied back by 1/g (tc_fp8_scales).
+      TD_REQUIRE(f.Kvv8 && f.Kvo8 && f.s_vv, TDDFT_ERR_ARG, "FP8 ris copies missing");
+      const int nvp = tc_pad(nv), nop = tc_pad(no), nv16 = tc_pad16(nv), no16 = tc_pad16(no);
+      const DType xt = x32 ? DType::F32 : DType::F64;
+      DevBuf sc((size_t)(2 + 2 * f.nK) * 4, s), kap(8, s);
+      tc_fp8_scales(X, xt, m, no, nv, f.s_vv, f.rho_oo, f.s_vo, f.rho_ov, f.nK, sc.as<float>(), kap.as<unsigned>(), s);
+      const float* inv1 = sc.as<float>();
+      const float* inv2 = inv1 + 1;
+      const float* mu1 = inv1 + 2;
+      const float* mu2 = mu1 + f.nK;
+      DevBuf Xt_hi((size_t)m * nv * nop * 2, s), Xt_lo((size_t)m * nv * nop * 2, s), Xs_hi, Xs_lo;
+      tc_transpose_split(X, xt, m, no, nv, Xt_hi.as<__nv_bfloat16>(), Xt_lo.as<__nv_bfloat16>(), s);
+      if (need_k2) {
+        Xs_hi = DevBuf((size_t)m * no * nvp * 2, s);
+        Xs_lo = DevBuf((size_t)m * no * nvp * 2, s);
+        tc_pad_split(X, xt, (long long)m * no, nv, Xs_hi.as<__nv_bfloat16>(), Xs_lo.as<__nv_bfloat16>(), s);
+      }
+      DevBuf Zhi((size_t)m * no * pc * nv16, s), Zlo((size_t)m * no * pc * nv16, s), Qhi, Qlo;
+      if (need_k2) {
+        Qhi = DevBuf((size_t)m * no * pc * no16, s);
+        Qlo = DevBuf((size_t)m * no * pc * no16, s);
+      }
+      const int Mz = m * no;
+      for (int p0 = 0; p0 < f.nK; p0 += pc) {
+        const int pn = (f.nK - p0 < pc) ? f.nK - p0 : pc;
+        tc_stage1_fp8(Xt_hi.as<__nv_bfloat16>(), Xt_lo.as<__nv_bfloat16>(), m * nv, no,
+                      f.Koo_hi + (size_t)p0 * no * nop, no, pn, nv, mu1 + p0, Zhi.as<unsigned char>(),
+                      Zlo.as<unsigned char>(), d.tc_err, s);
+        tc_contract8(Zhi.as<unsigned char>(), Zlo.as<unsigned char>(), Mz, pn, nv,
+                     f.Kvv8 + (size_t)p0 * nv * nv16, nv, K1b.as<float>(), p0 > 0, inv1, d.tc_err, s);
+        if (need_k2) {
+          tc_stage1_fp8(Xs_hi.as<__nv_bfloat16>(), Xs_lo.as<__nv_bfloat16>(), m * no, nv,
+                        f.Kovp_hi + (size_t)p0 * no * nvp, no, pn, no, mu2 + p0, Qhi.as<unsigned char>(),
+                        Qlo.as<unsigned char>(), d.tc_err, s);
+          tc_contract8(Qhi.as<unsigned char>(), Qlo.as<unsigned char>(), Mz, pn, no,
+                       f.Kvo8 + (size_t)p0 * nv * no16, nv, K2b.as<float>(), p0 > 0, inv2, d.tc_err, s);
+        }
+      }
+    } else if (use_tc) {
       // Both contractions of K1 and of K2 on the tensor cores.  The trial block
       // enters twice: transposed per vector ([(n,a)][j]) for Z = L_oo X and as is
       // ([(n,j)][b]) for Q = L_ov X^T, always as BF16 hi + lo (so Z and Q are

@@ -884,7 +884,7 @@ void inner_tda(int ov, const TdaOpT<T>& Top, const double* delta, const T* R, co
 struct Plan {
   int precond, k, k0, max_iter, inner_max_iter, cap, rounds, nref_inner, nref_outer;
   double tol, inner_tol, guess_tol;
-  bool mixed, tc;
+  bool mixed, tc, fp8;
 };
 
 Plan make_plan(const Ctx& c, const tddft_opts& o) {
@@ -900,6 +900,8 @@ Plan make_plan(const Ctx& c, const tddft_opts& o) {
              "context was created without the factor copies for this precision");
   TD_REQUIRE(!(o.tensor_cores && o.precision != TDDFT_MIXED), TDDFT_ERR_ARG,
              "tensor_cores needs the MIXED precision");
+  TD_REQUIRE(!(o.ris_fp8 && !(o.tensor_cores && o.precision == TDDFT_MIXED)), TDDFT_ERR_ARG,
+             "ris_fp8 needs the MIXED precision with tensor_cores");
   Plan p;
   p.precond = o.precond;
   p.k = std::min(o.n_states, c.ov);
@@ -915,6 +917,7 @@ Plan make_plan(const Ctx& c, const tddft_opts& o) {
   p.guess_tol = o.guess_tol;
   p.mixed = o.precision == TDDFT_MIXED;
   p.tc = o.tensor_cores != 0;
+  p.fp8 = o.ris_fp8 != 0;
   p.rounds = 3;
   p.nref_inner = p.mixed ? 0 : 2;
   p.nref_outer = 4;
@@ -958,7 +961,7 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
   Counters cnt;
   const OpDims dims = c.dims();
   const FactorSet Fx = c.exact(o.precision);
-  const FactorSet Fr = c.ris(o.precision);
+  const FactorSet Fr = c.ris(o.precision, p.fp8);
   TdaOp A = [&](const double* Xi, int m, double* out) {
     apply_operator(dims, Fx, Xi, m, OpMode::TDA, out, nullptr, p.tc, s);
   };
@@ -1080,11 +1083,11 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
   Counters cnt;
   const OpDims dims = c.dims();
   PairOp A = make_pair_op(dims, c.exact(o.precision), p.tc, s);
-  PairOp T = make_pair_op(dims, c.ris(o.precision), p.tc, s);
+  PairOp T = make_pair_op(dims, c.ris(o.precision, p.fp8), p.tc, s);
   const double* dl = c.delta.as<double>();
   PairPre diag = [&](const double* gp, const double* gm, const double* sh, const std::vector<double>&,
                      int nu, double* u, double* w) { precond_paired(gp, gm, sh, dl, nu, ov, u, w, s); };
-  PairOpT<float> T32 = make_pair_op32(dims, c.ris(o.precision), p.tc, s);
+  PairOpT<float> T32 = make_pair_op32(dims, c.ris(o.precision, p.fp8), p.tc, s);
   PairPreT<float> diag32 = [&](const float* gp, const float* gm, const double* sh,
                                const std::vector<double>&, int nu, float* u, float* w) {
     precond_paired<float>(gp, gm, sh, dl, nu, ov, u, w, s);
@@ -1170,7 +1173,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
   Counters cnt;
   const OpDims dims = c.dims();
   PairOp A = make_pair_op(dims, c.exact(o.precision), p.tc, s);
-  PairOp T = make_pair_op(dims, c.ris(o.precision), p.tc, s);
+  PairOp T = make_pair_op(dims, c.ris(o.precision, p.fp8), p.tc, s);
   const double* dl = c.delta.as<double>();
   const bool dev = o.outputs_on_device != 0;
   // right-hand sides 2 mu for every (omega_f, mu_u): row f*n_dip + u
@@ -1190,7 +1193,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
     axpy_rows(b.as<double>() + (size_t)f * n_dip * ov, mud.as<double>(), twod.as<double>(), n_dip, ov, s);
   PairPre diag = [&](const double* gp, const double* gm, const double* shv, const std::vector<double>&,
                      int nu, double* u, double* w) { precond_paired(gp, gm, shv, dl, nu, ov, u, w, s); };
-  PairOpT<float> T32 = make_pair_op32(dims, c.ris(o.precision), p.tc, s);
+  PairOpT<float> T32 = make_pair_op32(dims, c.ris(o.precision, p.fp8), p.tc, s);
   PairPreT<float> diag32 = [&](const float* gp, const float* gm, const double* shv,
                                const std::vector<double>&, int nu, float* u, float* w) {
     precond_paired<float>(gp, gm, shv, dl, nu, ov, u, w, s);

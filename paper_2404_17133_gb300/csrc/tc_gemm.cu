@@ -28,6 +28,8 @@
 // code in `err` and leaves the loop; the host turns it into TDDFT_ERR_CUDA.
 #include <algorithm>
 #include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
@@ -40,8 +42,15 @@ namespace {
 constexpr int BM = 128;
 constexpr int BN = 256;                      // 128 x 256 MMA tiles (full tcgen05 rate per CTA)
 constexpr int BK = 64;                       // bf16 elements per 128-byte row
-constexpr int A_BYTES = BM * BK * 2;          // 16 KB per hi or lo tile
-constexpr int B_BYTES = BN * BK * 2;
+constexpr int A_BYTES = BM * 128;             // 16 KB per hi or lo tile (128-byte rows)
+constexpr int B_BYTES = BN * 128;
+// Operand element types of the contraction: BF16 (kind::f16, 64 elements per
+// 128-byte row) or FP8 e4m3 (kind::f8f6f4, 128 elements per row).  Either way
+// one tcgen05.mma consumes 32 bytes of K, so the descriptors advance alike.
+template <bool F8> struct Elem {
+  static constexpr int BKE = F8 ? 128 : 64;
+  static constexpr uint32_t TYPE_BITS = F8 ? 0u : ((1u << 7) | (1u << 10));   // A, B: E4M3 = 0 / BF16 = 1
+};
 // Operand split modes: SINGLE = one BF16 product; BOTH = A and B as hi + lo
 // (hi*hi + hi*lo + lo*hi); ASPLIT = A as hi + lo, B a plain BF16 operand
 // (hi*B + lo*B: exact with respect to B, e.g. FP32 vectors against BF16 ris factors).
@@ -113,15 +122,26 @@ __device__ __forceinline__ uint64_t sdesc(const void* p) {
          (2ull << 61);
 }
 
-// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = BN.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: D = F32, A and B of the same type (BF16 for
+// kind::f16, E4M3 for kind::f8f6f4), both K-major, M = 128, N = BN.
+template <bool F8>
+constexpr uint32_t idesc_of() {
+  return (1u << 4) | Elem<F8>::TYPE_BITS | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accum));
+template <bool F8>
+__device__ __forceinline__ void mma_op(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accum) {
+  if constexpr (F8) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc_of<true>()), "r"(accum));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc_of<false>()), "r"(accum));
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -130,7 +150,7 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-template <int MODE>
+template <int MODE, bool F8>
 __global__ void __launch_bounds__(THREADS, 1)
 k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
              const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
@@ -174,7 +194,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
       if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicOr(p.err, 1); ok = false; break; }
       const int kb = k_begin + i;
-      const int P = kb / p.nab, a0 = (kb - P * p.nab) * BK;
+      const int P = kb / p.nab, a0 = (kb - P * p.nab) * Elem<F8>::BKE;
       unsigned char* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
       tma_load_3d(st, &mA_hi, &full[s], a0, P, m0);
@@ -196,11 +216,11 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       unsigned char* st = smem + s * STAGE_BYTES;
       const uint64_t ah = sdesc(st), bh = sdesc(st + B_OFF);
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 16 bf16 = 32 bytes along K
-        mma_bf16(tmem, ah + off, bh + off, (i > 0 || kk > 0) ? 1u : 0u);
-        if (b_split(MODE)) mma_bf16(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, 1u);
-        if (a_split(MODE)) mma_bf16(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u);
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 32 bytes along K per MMA
+        mma_op<F8>(tmem, ah + off, bh + off, (i > 0 || kk > 0) ? 1u : 0u);
+        if (b_split(MODE)) mma_op<F8>(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, 1u);
+        if (a_split(MODE)) mma_op<F8>(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u);
       }
       mma_commit(&empty[s]);
     }
@@ -276,10 +296,21 @@ struct S1Params {
   int stages, stage_bytes, a_bytes, b_bytes;
   __nv_bfloat16* out_hi;
   __nv_bfloat16* out_lo;
+  // FP8 output (OUT8): e4m3 hi + lo bytes of mu[P] * C_P, row pitch ldo bytes
+  unsigned char* out8_hi;
+  unsigned char* out8_lo;
+  const float* mu;
   int* err;
 };
 
-template <int MODE>
+__device__ __forceinline__ unsigned char to_e4m3(float x) {
+  return (unsigned char)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float from_e4m3(unsigned char q) {
+  return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3)));
+}
+
+template <int MODE, bool OUT8>
 __global__ void __launch_bounds__(S1_THREADS, 1)
 k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
             const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
@@ -398,16 +429,31 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (r < p.M) {
           const size_t base = (((size_t)g * p.N + c0) * p.pn + P) * p.ldo + ri;
-          __nv_bfloat16* oh = p.out_hi + base;
-          __nv_bfloat16* ol = a_split(MODE) ? p.out_lo + base : nullptr;
           const int nc = min(16, p.N - c0);
+          if constexpr (OUT8) {
+            const float mu = p.mu[P];
+            unsigned char* oh = p.out8_hi + base;
+            unsigned char* ol = p.out8_lo + base;
 #pragma unroll
-          for (int t = 0; t < 16; ++t) {
-            if (t < nc) {
-              const float x = __uint_as_float(v[t]);
-              const __nv_bfloat16 h = __float2bfloat16_rn(x);
-              oh[t * cs] = h;
-              if (a_split(MODE)) ol[t * cs] = __float2bfloat16_rn(x - __bfloat162float(h));
+            for (int t = 0; t < 16; ++t) {
+              if (t < nc) {
+                const float x = __uint_as_float(v[t]) * mu;
+                const unsigned char h = to_e4m3(x);
+                oh[t * cs] = h;
+                ol[t * cs] = to_e4m3(x - from_e4m3(h));
+              }
+            }
+          } else {
+            __nv_bfloat16* oh = p.out_hi + base;
+            __nv_bfloat16* ol = a_split(MODE) ? p.out_lo + base : nullptr;
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+              if (t < nc) {
+                const float x = __uint_as_float(v[t]);
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                oh[t * cs] = h;
+                if (a_split(MODE)) ol[t * cs] = __float2bfloat16_rn(x - __bfloat162float(h));
+              }
             }
           }
         }
@@ -425,13 +471,25 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
 }
 
 // Sum the split partials into out (FP32), accumulating when asked.
+// With `scale` (device scalar), the summed partials are multiplied by *scale
+// before they are added (the FP8 operands carry a scale factor).
 __global__ void k_sum_splits(const float* __restrict__ part, int S, long long MN, float* out,
-                             int accumulate) {
+                             int accumulate, const float* __restrict__ scale) {
+  if (!scale) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < MN;
+         t += (long long)gridDim.x * blockDim.x) {
+      float acc = accumulate ? out[t] : 0.f;
+      for (int s = 0; s < S; ++s) acc += part[s * MN + t];
+      out[t] = acc;
+    }
+    return;
+  }
+  const float f = *scale;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < MN;
        t += (long long)gridDim.x * blockDim.x) {
-    float acc = accumulate ? out[t] : 0.f;
+    float acc = 0.f;
     for (int s = 0; s < S; ++s) acc += part[s * MN + t];
-    out[t] = acc;
+    out[t] = (accumulate ? out[t] : 0.f) + f * acc;
   }
 }
 
@@ -490,12 +548,13 @@ EncodeFn encode_fn() {
 }
 
 CUtensorMap make_map(const void* base, const cuuint64_t dims[3], const cuuint64_t strides[2],
-                     const cuuint32_t box[3]) {
+                     const cuuint32_t box[3], bool u8 = false) {
   TD_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0, TDDFT_ERR_ARG, "TMA base not 16-byte aligned");
   TD_REQUIRE(strides[0] % 16 == 0 && strides[1] % 16 == 0, TDDFT_ERR_ARG, "TMA strides not 16-byte multiples");
   CUtensorMap m;
   const cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+  CUresult r = encode_fn()(&m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                           const_cast<void*>(base), dims, strides,
                            box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   TD_REQUIRE(r == CUDA_SUCCESS, TDDFT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
@@ -505,6 +564,7 @@ CUtensorMap make_map(const void* base, const cuuint64_t dims[3], const cuuint64_
 }  // namespace
 
 int tc_pad(int nv) { return (nv + 7) & ~7; }
+int tc_pad16(int n) { return (n + 15) & ~15; }
 
 void tc_split_pad(const float* Z, int M, int pn, int nv, __nv_bfloat16* hi, __nv_bfloat16* lo,
                   cudaStream_t s) {
@@ -607,26 +667,65 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
     kernel<<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
     if (prof) prof->end(s, prof_flops, prof_bytes);
   };
-  if (mode == BOTH) launch(k1_tc_kernel<BOTH>, Cfg<BOTH>::SMEM_BYTES);
-  else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT>, Cfg<ASPLIT>::SMEM_BYTES);
-  else launch(k1_tc_kernel<SINGLE>, Cfg<SINGLE>::SMEM_BYTES);
+  if (mode == BOTH) launch(k1_tc_kernel<BOTH, false>, Cfg<BOTH>::SMEM_BYTES);
+  else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT, false>, Cfg<ASPLIT>::SMEM_BYTES);
+  else launch(k1_tc_kernel<SINGLE, false>, Cfg<SINGLE>::SMEM_BYTES);
   count_launch();
   TD_LAUNCH_CHECK();
   const long long MN = (long long)M * N;
   long long g = (MN + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
-  k_sum_splits<<<(unsigned)g, 256, 0, s>>>(part.as<float>(), splits, MN, out, accumulate ? 1 : 0);
+  k_sum_splits<<<(unsigned)g, 256, 0, s>>>(part.as<float>(), splits, MN, out, accumulate ? 1 : 0, nullptr);
   count_launch();
   TD_LAUNCH_CHECK();
 }
 
-void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
-               const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, int pn, int R,
-               __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int* err, cudaStream_t s) {
+void tc_contract8(const unsigned char* Ahi, const unsigned char* Alo, int M, int pn, int Kin,
+                  const unsigned char* B, int N, float* out, bool accumulate, const float* scale, int* err,
+                  cudaStream_t s) {
+  if (M <= 0 || pn <= 0 || N <= 0) return;
+  TD_REQUIRE(Ahi && Alo && B && scale, TDDFT_ERR_ARG, "tc_contract8: operands missing");
+  constexpr int BKE = Elem<true>::BKE;
+  const int ldk = tc_pad16(Kin);
+  const int nab = (Kin + BKE - 1) / BKE;
+  const int total = pn * nab;
+  const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+  int splits = wave_splits(mt * nt, total, 4);
+  const int per = (total + splits - 1) / splits;
+  splits = (total + per - 1) / per;
+  const cuuint64_t dA[3] = {(cuuint64_t)Kin, (cuuint64_t)pn, (cuuint64_t)M};
+  const cuuint64_t sA[2] = {(cuuint64_t)ldk, (cuuint64_t)pn * ldk};
+  const cuuint32_t bA[3] = {(cuuint32_t)BKE, 1, BM};
+  const cuuint64_t dB[3] = {(cuuint64_t)Kin, (cuuint64_t)N, (cuuint64_t)pn};
+  const cuuint64_t sB[2] = {(cuuint64_t)ldk, (cuuint64_t)N * ldk};
+  const cuuint32_t bB[3] = {(cuuint32_t)BKE, BN, 1};
+  CUtensorMap mAh = make_map(Ahi, dA, sA, bA, true), mAl = make_map(Alo, dA, sA, bA, true);
+  CUtensorMap mB = make_map(B, dB, sB, bB, true);
+  DevBuf part((size_t)splits * M * N * 4, s);
+  Params p{M, N, nab, total, per, part.as<float>(), err};
+  dim3 grid(nt, mt, splits);
+  ensure_smem((const void*)k1_tc_kernel<ASPLIT, true>, Cfg<ASPLIT>::SMEM_BYTES);
+  k1_tc_kernel<ASPLIT, true><<<grid, THREADS, Cfg<ASPLIT>::SMEM_BYTES, s>>>(mAh, mAl, mB, mB, p);
+  count_launch();
+  TD_LAUNCH_CHECK();
+  const long long MN = (long long)M * N;
+  long long g = (MN + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  k_sum_splits<<<(unsigned)g, 256, 0, s>>>(part.as<float>(), splits, MN, out, accumulate ? 1 : 0, scale);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+namespace {
+void stage1_impl(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
+                 const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, int pn, int R,
+                 __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, unsigned char* out8_hi,
+                 unsigned char* out8_lo, const float* mu, int* err, cudaStream_t s) {
   if (M <= 0 || pn <= 0 || N <= 0) return;
   TD_REQUIRE(N <= 256, TDDFT_ERR_ARG, "tc_stage1: N above 256");
-  TD_REQUIRE((Alo != nullptr || Blo == nullptr) && (Alo != nullptr) == (out_lo != nullptr), TDDFT_ERR_ARG,
-             "tc_stage1: hi/lo operands mismatch");
+  TD_REQUIRE((Alo != nullptr || Blo == nullptr) &&
+                 (out8_hi ? (out8_lo != nullptr && mu != nullptr) : (Alo != nullptr) == (out_lo != nullptr)),
+             TDDFT_ERR_ARG, "tc_stage1: hi/lo operands mismatch");
   const int mode = Alo ? (Blo ? BOTH : ASPLIT) : SINGLE;
   const int ldk = tc_pad(K);
   const int nb = (N + 15) & ~15;
@@ -652,18 +751,34 @@ void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
   CUtensorMap mAh = make_map(Ahi, dA, sA, bA), mBh = make_map(Bhi, dB, sB, bB);
   CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA) : mAh;
   CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB) : mBh;
-  S1Params p{M, N, R, tc_pad(R), pn, ppc, (K + BK - 1) / BK, nb, acc_cols, stages, stage_bytes,
-             a_bytes, b_bytes, out_hi, out_lo, err};
+  S1Params p{M, N, R, out8_hi ? tc_pad16(R) : tc_pad(R), pn, ppc, (K + BK - 1) / BK, nb, acc_cols, stages,
+             stage_bytes, a_bytes, b_bytes, out_hi, out_lo, out8_hi, out8_lo, mu, err};
   dim3 grid(mt, groups, 1);
   auto launch = [&](auto kernel) {
     ensure_smem((const void*)kernel, smem);
     kernel<<<grid, S1_THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
   };
-  if (mode == BOTH) launch(k_stage1_tc<BOTH>);
-  else if (mode == ASPLIT) launch(k_stage1_tc<ASPLIT>);
-  else launch(k_stage1_tc<SINGLE>);
+  if (out8_hi) {
+    TD_REQUIRE(mode == ASPLIT, TDDFT_ERR_ARG, "tc_stage1: FP8 output needs hi+lo A and a plain B");
+    launch(k_stage1_tc<ASPLIT, true>);
+  } else if (mode == BOTH) launch(k_stage1_tc<BOTH, false>);
+  else if (mode == ASPLIT) launch(k_stage1_tc<ASPLIT, false>);
+  else launch(k_stage1_tc<SINGLE, false>);
   count_launch();
   TD_LAUNCH_CHECK();
+}
+}  // namespace
+
+void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
+               const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, int pn, int R,
+               __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int* err, cudaStream_t s) {
+  stage1_impl(Ahi, Alo, M, K, Bhi, Blo, N, pn, R, out_hi, out_lo, nullptr, nullptr, nullptr, err, s);
+}
+
+void tc_stage1_fp8(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K, const __nv_bfloat16* B,
+                   int N, int pn, int R, const float* mu, unsigned char* out_hi, unsigned char* out_lo, int* err,
+                   cudaStream_t s) {
+  stage1_impl(Ahi, Alo, M, K, B, nullptr, N, pn, R, nullptr, nullptr, out_hi, out_lo, mu, err, s);
 }
 
 // F64/F32 rows [rows][n] -> BF16 hi (+ lo) [rows][tc_pad(n)]
@@ -691,6 +806,163 @@ void tc_pad_split(const void* src, DType ts, long long rows, int n, __nv_bfloat1
   if (ts == DType::F64) k_pad_split<double><<<(unsigned)g, 256, 0, s>>>((const double*)src, rows, n, ld, hi, lo);
   else if (ts == DType::F32) k_pad_split<float><<<(unsigned)g, 256, 0, s>>>((const float*)src, rows, n, ld, hi, lo);
   else k_pad_split<__nv_bfloat16><<<(unsigned)g, 256, 0, s>>>((const __nv_bfloat16*)src, rows, n, ld, hi, lo);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+
+// ---------------------------------------------------------------------------
+// FP8 (e4m3) operands of the ris exchange contractions, with a scale per
+// auxiliary row P.  The ris factors L^P are stored as q^P = e4m3(L^P / s_P),
+// s_P = max |L^P| / 448 (448 = the largest finite e4m3).  A product
+// sum_P C_P L^P = sum_P (s_P C_P) q^P: the stage-1 result C_P is multiplied by
+// mu_P = s_P * g before its own hi + lo e4m3 split, and the contraction's sum
+// by 1/g, with g chosen from a bound so that |mu_P C_P| <= 224:
+//   |C_P[(n,i)][k]| <= rho_P * kappa   (Cauchy-Schwarz), rho_P = max_i ||L^P_i,:||,
+//   kappa = the largest norm of the trial-vector slices that C contracts with.
+namespace {
+
+__global__ void k_quant_e4m3_t(const __nv_bfloat16* __restrict__ src, int n1, int n2, int ld,
+                               unsigned char* __restrict__ dst, float* __restrict__ scale) {
+  const long long per = (long long)n1 * n2;
+  const __nv_bfloat16* x = src + blockIdx.x * per;
+  unsigned char* y = dst + (long long)blockIdx.x * n2 * ld;
+  __shared__ float red[32];
+  float m = 0.f;
+  for (long long t = threadIdx.x; t < per; t += blockDim.x) m = fmaxf(m, fabsf(__bfloat162float(x[t])));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) red[0] = m;
+  }
+  __syncthreads();
+  const float sc = red[0] > 0.f ? red[0] / 448.f : 1.f;
+  const float inv = 1.f / sc;
+  if (threadIdx.x == 0) scale[blockIdx.x] = sc;
+  const long long tot = (long long)n2 * ld;
+  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {   // y[b][a] = x[a][b] / s
+    const int a = (int)(t % ld);
+    const long long b = t / ld;
+    y[t] = a < n1 ? to_e4m3(__bfloat162float(x[(long long)a * n2 + b]) * inv) : (unsigned char)0;
+  }
+}
+
+__global__ void k_row_norm_max(const __nv_bfloat16* __restrict__ src, int nr, int nc, float* __restrict__ rho) {
+  const __nv_bfloat16* x = src + (long long)blockIdx.x * nr * nc;
+  __shared__ float red[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  float m = 0.f;
+  for (int i = warp; i < nr; i += nw) {
+    float acc = 0.f;
+    for (int c = lane; c < nc; c += 32) {
+      const float v = __bfloat162float(x[(long long)i * nc + c]);
+      acc += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    m = fmaxf(m, sqrtf(acc));
+  }
+  if (lane == 0) red[warp] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = 0.f;
+    for (int w = 0; w < nw; ++w) r = fmaxf(r, red[w]);
+    rho[blockIdx.x] = r;
+  }
+}
+
+// kappa[0] = max_(n,a) ||X[n][:][a]||, kappa[1] = max_(n,j) ||X[n][j][:]|| (as
+// float bits; non-negative floats order like their bit patterns)
+template <typename T>
+__global__ void k_x_norms(const T* __restrict__ X, int no, int nv, unsigned* __restrict__ kappa) {
+  const T* x = X + (long long)blockIdx.x * no * nv;
+  __shared__ float red[2][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  float mc = 0.f, mr = 0.f;
+  for (int a = threadIdx.x; a < nv; a += blockDim.x) {
+    float acc = 0.f;
+    for (int j = 0; j < no; ++j) { const float v = (float)x[(long long)j * nv + a]; acc += v * v; }
+    mc = fmaxf(mc, sqrtf(acc));
+  }
+  for (int j = warp; j < no; j += nw) {
+    float acc = 0.f;
+    for (int b = lane; b < nv; b += 32) { const float v = (float)x[(long long)j * nv + b]; acc += v * v; }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    mr = fmaxf(mr, sqrtf(acc));
+  }
+  for (int o = 16; o > 0; o >>= 1) mc = fmaxf(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+  if (lane == 0) { red[0][warp] = mc; red[1][warp] = mr; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float c = 0.f, r = 0.f;
+    for (int w = 0; w < nw; ++w) { c = fmaxf(c, red[0][w]); r = fmaxf(r, red[1][w]); }
+    atomicMax(&kappa[0], __float_as_uint(c));
+    atomicMax(&kappa[1], __float_as_uint(r));
+  }
+}
+
+// out[0] = 1/g1, out[1] = 1/g2, out[2 + P] = s1_P g1, out[2 + nK + P] = s2_P g2
+__global__ void k_fp8_mu(const unsigned* __restrict__ kappa, const float* __restrict__ s1,
+                         const float* __restrict__ r1, const float* __restrict__ s2,
+                         const float* __restrict__ r2, int nK, float* __restrict__ out) {
+  __shared__ float red[2][32];
+  const float kc = __uint_as_float(kappa[0]), kr = __uint_as_float(kappa[1]);
+  float b1 = 0.f, b2 = 0.f;
+  for (int P = threadIdx.x; P < nK; P += blockDim.x) {
+    b1 = fmaxf(b1, s1[P] * r1[P] * kc);
+    b2 = fmaxf(b2, s2[P] * r2[P] * kr);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    b1 = fmaxf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+    b2 = fmaxf(b2, __shfl_xor_sync(0xffffffffu, b2, o));
+  }
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) { red[0][warp] = b1; red[1][warp] = b2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float x1 = 0.f, x2 = 0.f;
+    for (int w = 0; w < nw; ++w) { x1 = fmaxf(x1, red[0][w]); x2 = fmaxf(x2, red[1][w]); }
+    red[0][0] = x1 > 0.f ? 224.f / x1 : 1.f;
+    red[1][0] = x2 > 0.f ? 224.f / x2 : 1.f;
+    out[0] = 1.f / red[0][0];
+    out[1] = 1.f / red[1][0];
+  }
+  __syncthreads();
+  const float g1 = red[0][0], g2 = red[1][0];
+  for (int P = threadIdx.x; P < nK; P += blockDim.x) {
+    out[2 + P] = s1[P] * g1;
+    out[2 + nK + P] = s2[P] * g2;
+  }
+}
+
+}  // namespace
+
+void tc_quant_e4m3(const __nv_bfloat16* src, int rows, int n1, int n2, unsigned char* dst, float* scale,
+                   cudaStream_t s) {
+  if (rows <= 0) return;
+  k_quant_e4m3_t<<<rows, 512, 0, s>>>(src, n1, n2, tc_pad16(n1), dst, scale);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+void tc_row_norm_max(const __nv_bfloat16* src, int rows, int nr, int nc, float* rho, cudaStream_t s) {
+  if (rows <= 0) return;
+  k_row_norm_max<<<rows, 256, 0, s>>>(src, nr, nc, rho);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+void tc_fp8_scales(const void* X, DType xt, int m, int no, int nv, const float* s_vv, const float* rho_oo,
+                   const float* s_vo, const float* rho_ov, int nK, float* out, unsigned* kappa,
+                   cudaStream_t s) {
+  TD_CUDA(cudaMemsetAsync(kappa, 0, 2 * sizeof(unsigned), s));
+  if (xt == DType::F32) k_x_norms<float><<<m, 256, 0, s>>>(static_cast<const float*>(X), no, nv, kappa);
+  else k_x_norms<double><<<m, 256, 0, s>>>(static_cast<const double*>(X), no, nv, kappa);
+  count_launch();
+  TD_LAUNCH_CHECK();
+  k_fp8_mu<<<1, 256, 0, s>>>(kappa, s_vv, rho_oo, s_vo, rho_ov, nK, out);
   count_launch();
   TD_LAUNCH_CHECK();
 }

@@ -7,6 +7,8 @@ namespace tddft {
 // Row pitch (elements) of the padded BF16 operands: nv rounded up to 8 so that
 // every TMA stride is a multiple of 16 bytes.
 int tc_pad(int nv);
+// Row pitch (elements) of the padded FP8 operands: n rounded up to 16.
+int tc_pad16(int n);
 
 // FP32 Z [M][pn][nv] -> BF16 hi (+ lo unless NULL) [M][pn][tc_pad(nv)] (pads zero).
 void tc_split_pad(const float* Z, int M, int pn, int nv, __nv_bfloat16* hi, __nv_bfloat16* lo,
@@ -44,5 +46,35 @@ void tc_pad_split(const void* src, DType ts, long long rows, int n, __nv_bfloat1
 void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
                const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, int pn, int R,
                __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int* err, cudaStream_t s);
+
+// ---- FP8 (e4m3) ris exchange operands with one scale per auxiliary row P.
+// Factor rows src [rows][n1][n2] (BF16) -> dst [rows][n2][tc_pad16(n1)] e4m3
+// (transposed in the last two indices) of src / scale[P], scale[P] =
+// max |src[P]| / 448.
+void tc_quant_e4m3(const __nv_bfloat16* src, int rows, int n1, int n2, unsigned char* dst, float* scale,
+                   cudaStream_t s);
+// rho[P] = max_i sqrt(sum_c src[P][i][c]^2), src [rows][nr][nc] BF16.
+void tc_row_norm_max(const __nv_bfloat16* src, int rows, int nr, int nc, float* rho, cudaStream_t s);
+// Per-product scales of the FP8 exchange contractions for trial vectors X
+// [m][no][nv] (F64 or F32): out[0], out[1] = the output factors 1/g1, 1/g2 of
+// K1 and K2; out[2 + P] = s_vv[P] g1 and out[2 + nK + P] = s_vo[P] g2, the
+// multipliers of the stage-1 results (mu_P).  g1 = 224 / max_P(s_vv[P]
+// rho_oo[P] kappa_col), g2 likewise with s_vo, rho_ov and kappa_row, where
+// kappa_col = max ||X[n][:][a]|| and kappa_row = max ||X[n][j][:]||.  kappa:
+// device scratch of two words.  No host synchronisation.
+void tc_fp8_scales(const void* X, DType xt, int m, int no, int nv, const float* s_vv, const float* rho_oo,
+                   const float* s_vo, const float* rho_ov, int nK, float* out, unsigned* kappa,
+                   cudaStream_t s);
+// Stage 1 with e4m3 hi + lo output: out[(g*N + c)][P][ri] (row pitch
+// pn*tc_pad16(R) bytes) = split of mu[P] * C_P[r][c]; A as BF16 hi + lo, B BF16.
+void tc_stage1_fp8(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K, const __nv_bfloat16* B,
+                   int N, int pn, int R, const float* mu, unsigned char* out_hi, unsigned char* out_lo, int* err,
+                   cudaStream_t s);
+// out (+)= (*scale) * sum_P sum_k A[m][P][k] B[P][n][k] on the tensor cores
+// (kind::f8f6f4, e4m3 x e4m3, FP32 accumulation): A as e4m3 hi + lo
+// [M][pn][tc_pad16(Kin)], B e4m3 [pn][N][tc_pad16(Kin)]; scale a device scalar.
+void tc_contract8(const unsigned char* Ahi, const unsigned char* Alo, int M, int pn, int Kin,
+                  const unsigned char* B, int N, float* out, bool accumulate, const float* scale, int* err,
+                  cudaStream_t s);
 
 }  // namespace tddft

@@ -54,7 +54,7 @@ int main(void) {
   printf("tddft_desc %zu\\ntddft_opts %zu\\ntddft_stats %zu\\ntddft_request %zu\\n",
          sizeof(tddft_desc), sizeof(tddft_opts), sizeof(tddft_stats), sizeof(tddft_request));
   F(tddft_desc, a_x) F(tddft_desc, precisions) F(tddft_desc, hbm_budget_gb)
-  F(tddft_opts, tol) F(tddft_opts, max_iter) F(tddft_opts, outputs_on_device)
+  F(tddft_opts, tol) F(tddft_opts, max_iter) F(tddft_opts, outputs_on_device) F(tddft_opts, ris_fp8)
   F(tddft_stats, max_resid) F(tddft_stats, t_precond_s)
   F(tddft_request, omega) F(tddft_request, n_dip) F(tddft_request, alpha) F(tddft_request, stats)
   printf("tddft_serve_request %zu\\ntddft_server_state %zu\\n", sizeof(tddft_serve_request),
@@ -123,7 +123,8 @@ def test_admission_charge_counts_the_factor_copies(api):
     arrays tddft_create keeps: FP64 copies of L_oo, L_ov, L_vv and of the ris
     rows (PLAIN); FP32 copies plus BF16 hi+lo tensor-core copies with rows
     padded to a multiple of 8 elements (16-byte TMA strides) (MIXED: vv, ov^T, oo and ov), BF16 ris
-    rows and their padded copies."""
+    rows and their padded copies, FP8 copies of the ris exchange vv and ov^T rows padded to a
+    multiple of 16 bytes with four floats per row (scales and norms)."""
     no, nv, na, nj, nk = 12, 70, 300, 54, 6
     ov = no * nv
     ris = nj * ov + nk * (no * no + nv * nv + ov)
@@ -132,7 +133,9 @@ def test_admission_charge_counts_the_factor_copies(api):
     pad = lambda n: -(-n // 8) * 8
     padded = nv * (pad(nv) + pad(no)) + no * (pad(no) + pad(nv))
     fmx, _ = api.estimate_bytes(_desc(api, no, nv, na, nj, nk, 2), 0, api.default_opts(precision=api.MIXED))
-    assert fmx == 4 * na * (no * no + ov + nv * nv) + 4 * na * padded + 2 * ris + 2 * nk * padded
+    pad16 = lambda n: -(-n // 16) * 16
+    fp8 = nk * (nv * (pad16(nv) + pad16(no)) + 16)
+    assert fmx == 4 * na * (no * no + ov + nv * nv) + 4 * na * padded + 2 * ris + 2 * nk * padded + fp8
     both, _ = api.estimate_bytes(_desc(api, no, nv, na, nj, nk, 3), 0, api.default_opts())
     assert both == f64 + fmx
 
