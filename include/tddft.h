@@ -345,6 +345,42 @@ unsigned long long tddft_device_bytes(const tddft_ctx* ctx);
 tddft_status tddft_apply_noalloc(tddft_ctx* ctx, int kind, int precision, const double* X, int m,
                                  double* out0, double* out1);
 
+/* ---- Batched TDA solves (no counterpart in the paper, which solves one
+ * molecule at a time; this is the library's interface for many small
+ * independent problems).  The n contexts' TDA problems (opts[i] for
+ * ctxs[i]; a context may appear more than once, its factors are only read)
+ * are advanced together, one Davidson iteration (Sec. 2.1) of every problem
+ * at a time: every step of an iteration is one launch for all problems (a
+ * persistent grouped GEMM walking a device task list; row operations from a
+ * device list; one CTA per problem for the small matrices), and the exact
+ * operator product of an iteration is replayed from a captured CUDA graph.
+ * The grouped GEMM's tile shape is chosen by a measured autotune at the start
+ * of the batch (every variant gives the same bits).  Precision: trial vectors
+ * and exact products in FP32, ris factors in BF16 (FP32 accumulation),
+ * projected matrices and small solves in FP64; contexts need the MIXED
+ * factor copies; opts[i].precision / tensor_cores / ris_fp8 are ignored,
+ * n_states <= 32; contexts with variant terms are refused (TDDFT_ERR_ARG).
+ *   omega, resid: HOST arrays of sum_i min(opts[i].n_states, ov_i) entries,
+ *                 problem after problem (resid may be NULL);
+ *   stats: HOST [n] (may be NULL); info: HOST (may be NULL).
+ * All contexts must be on one device; the work runs on ctxs[0]'s stream.
+ * Returns TDDFT_ERR_NOCONV when some problem did not converge (its results
+ * are the last Ritz data); errors are reported on ctxs[0].                */
+typedef struct {
+  int n_variants;             /* grouped-GEMM tile variants timed             */
+  int variant;                /* the variant kept (index), -1 if none         */
+  double autotune_ms[8];      /* measured time of each variant (ms), -1: not run */
+  int outer_iterations;       /* lockstep outer iterations (slowest problem)  */
+  int graph_nodes;            /* kernel nodes of the captured operator graph  */
+  long long launches;         /* kernel launches of the whole batch (incl. graph nodes) */
+  long long graph_launches;   /* CUDA graph replays                           */
+  double t_total_s;           /* wall time of the call                        */
+} tddft_batch_info;
+
+tddft_status tddft_solve_tda_batch(tddft_ctx* const* ctxs, int n, const tddft_opts* opts,
+                                   double* omega, double* resid, tddft_stats* stats,
+                                   tddft_batch_info* info);
+
 /* Device memory pool query for tests and callers that track allocations.
  * (No counterpart in the paper.)  Reads the current and the high-water
  * "used" byte counts of `device`'s default stream-ordered memory pool, from

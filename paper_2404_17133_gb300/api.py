@@ -83,6 +83,17 @@ class ServerState(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchInfo(C.Structure):
+    _fields_ = [("n_variants", C.c_int), ("variant", C.c_int), ("autotune_ms", C.c_double * 8),
+                ("outer_iterations", C.c_int), ("graph_nodes", C.c_int), ("launches", C.c_longlong),
+                ("graph_launches", C.c_longlong), ("t_total_s", C.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "autotune_ms"}
+        d["autotune_ms"] = [self.autotune_ms[i] for i in range(self.n_variants)]
+        return d
+
+
 _vp, _ip, _dp = C.c_void_p, C.c_int, C.c_void_p
 _lib.tddft_default_opts.argtypes = [C.POINTER(Opts)]
 _lib.tddft_default_opts.restype = None
@@ -137,6 +148,9 @@ _lib.tddft_add_exchange.argtypes = [_vp, C.c_double, _ip, _vp, _vp, _vp, _ip, _i
 _lib.tddft_add_exchange.restype = C.c_int
 _lib.tddft_add_kernel.argtypes = [_vp, _ip, _dp, _vp, _ip, _ip]
 _lib.tddft_add_kernel.restype = C.c_int
+_lib.tddft_solve_tda_batch.argtypes = [C.POINTER(_vp), _ip, C.POINTER(Opts), _dp, _dp, C.POINTER(Stats),
+                                       C.POINTER(BatchInfo)]
+_lib.tddft_solve_tda_batch.restype = C.c_int
 _lib.tddft_pool_usage.argtypes = [_ip, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong), _ip]
 _lib.tddft_pool_usage.restype = C.c_int
 
@@ -146,7 +160,7 @@ EXPORTED = ["tddft_default_opts", "tddft_default_desc", "tddft_create", "tddft_s
             "tddft_profile_read", "tddft_apply_noalloc", "tddft_estimate_bytes", "tddft_server_create",
             "tddft_server_submit", "tddft_server_poll", "tddft_server_info", "tddft_server_destroy",
             "tddft_ctx_desc", "tddft_add_exchange", "tddft_add_kernel",
-            "tddft_profile_records", "tddft_pool_usage"]
+            "tddft_profile_records", "tddft_pool_usage", "tddft_solve_tda_batch"]
 
 
 class TddftError(RuntimeError):
@@ -417,6 +431,29 @@ class Solver:
             out["error"] = _lib.tddft_last_error(self.h).decode()
         out.update({k: v for k, v in bufs.items() if k in ("omega", "resid", "alpha")})
         return out
+
+
+def solve_tda_batch(solvers, opts):
+    """Batched TDA solves (tddft_solve_tda_batch): solvers[i] with opts[i],
+    advanced together.  Returns (status, list of {omega, resid, stats}, info)."""
+    n = len(solvers)
+    if n == 0 or len(opts) != n:
+        raise ValueError("need one opts per solver")
+    hs = (C.c_void_p * n)(*[s.h for s in solvers])
+    oa = (Opts * n)(*opts)
+    ks = [min(o.n_states, s.n_ov) for s, o in zip(solvers, opts)]
+    om, rs = np.zeros(sum(ks)), np.zeros(sum(ks))
+    st = (Stats * n)()
+    info = BatchInfo()
+    status = _lib.tddft_solve_tda_batch(hs, n, oa, om.ctypes.data_as(C.c_void_p), rs.ctypes.data_as(C.c_void_p),
+                                        st, C.byref(info))
+    if status not in (OK, ERR_NOCONV):
+        raise TddftError(status, _lib.tddft_last_error(solvers[0].h).decode())
+    out, off = [], 0
+    for i, k in enumerate(ks):
+        out.append(dict(omega=om[off:off + k].copy(), resid=rs[off:off + k].copy(), stats=st[i].as_dict()))
+        off += k
+    return status, out, info.as_dict()
 
 
 class Server:

@@ -19,7 +19,7 @@ LIBNAME = "libtddft_gb300.so"
 LIBPATH = os.path.join(LIBDIR, LIBNAME)
 
 SOURCES = ["devpool.cu", "gemm.cu", "small.cu", "vecops.cu", "operator.cu", "tc_gemm.cu", "skinny.cu", "solver.cu", "capi.cu",
-           "apply_static.cu", "server.cu"]
+           "apply_static.cu", "server.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -787,6 +787,29 @@ unsigned long long tddft_device_bytes(const tddft_ctx* ctx) {
   return c ? c->device_bytes : 0ull;
 }
 
+tddft_status tddft_solve_tda_batch(tddft_ctx* const* ctxs, int n, const tddft_opts* opts, double* omega,
+                                   double* resid, tddft_stats* stats, tddft_batch_info* info) {
+  if (!ctxs || n < 1 || !ctxs[0] || !opts || !omega) return TDDFT_ERR_ARG;
+  Ctx* c0 = reinterpret_cast<Ctx*>(ctxs[0]);
+  try {
+    std::vector<Ctx*> cs(n);
+    for (int i = 0; i < n; ++i) {
+      cs[i] = reinterpret_cast<Ctx*>(ctxs[i]);
+      TD_REQUIRE(cs[i] != nullptr, TDDFT_ERR_ARG, "batch: null context");
+    }
+    std::vector<Ctx*> uniq(cs);
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    std::vector<std::unique_lock<std::mutex>> locks;   // one solve at a time per context
+    for (Ctx* u : uniq) locks.emplace_back(u->run_mu);
+    return solve_tda_batch(cs.data(), n, opts, omega, resid, stats, info);
+  } catch (const Error& e) {
+    return fail(c0, e, e.status);
+  } catch (const std::exception& e) {
+    return fail(c0, e, TDDFT_ERR_CUDA);
+  }
+}
+
 tddft_status tddft_pool_usage(int device, unsigned long long* used_current,
                               unsigned long long* used_high, int reset_high) {
   int n = 0;

@@ -185,5 +185,7 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
                      double* resid, tddft_stats* st);
 tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
                        const double* freqs, int n_freq, double* alpha, tddft_stats* st);
+tddft_status solve_tda_batch(Ctx* const* ctxs, int n, const tddft_opts* opts, double* omega, double* resid,
+                             tddft_stats* stats, tddft_batch_info* info);
 
 }  // namespace tddft

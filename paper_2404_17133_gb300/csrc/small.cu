@@ -510,12 +510,11 @@ __global__ void __launch_bounds__(256) k_trsv(const S* __restrict__ L, int ldl, 
 
 constexpr int kDropMax = 112;
 
-__global__ void __launch_bounds__(1024) k_chol_drop(const double* __restrict__ G, int nc,
-                                                    const double* __restrict__ norm0sq, double drop2,
-                                                    double* __restrict__ T, int* __restrict__ keep) {
-  extern __shared__ double smd[];
-  __shared__ int kj;
-  __shared__ double dj;
+// Pivot-dropping Cholesky of one candidate Gram matrix by the whole CTA
+// (shared memory smd >= 2 nc (nc + 1) doubles; kj / dj shared scalars).
+__device__ void chol_drop_cta(const double* __restrict__ G, int nc, const double* __restrict__ norm0sq,
+                              double drop2, double* __restrict__ T, int* __restrict__ keep, double* smd,
+                              int& kj, double& dj) {
   const int ld = nc + 1;
   double* R = smd;                 // working Gram -> upper factor
   double* Ti = smd + nc * ld;      // T rows
@@ -566,6 +565,15 @@ __global__ void __launch_bounds__(1024) k_chol_drop(const double* __restrict__ G
     int a = idx / nc, b = idx - a * nc;
     T[idx] = Ti[a * ld + b];
   }
+}
+
+__global__ void __launch_bounds__(1024) k_chol_drop(const double* __restrict__ G, int nc,
+                                                    const double* __restrict__ norm0sq, double drop2,
+                                                    double* __restrict__ T, int* __restrict__ keep) {
+  extern __shared__ double smd[];
+  __shared__ int kj;
+  __shared__ double dj;
+  chol_drop_cta(G, nc, norm0sq, drop2, T, keep, smd, kj, dj);
 }
 
 // Gaussian elimination with partial pivoting on the augmented matrix [M | b]
@@ -747,6 +755,74 @@ __global__ void __launch_bounds__(512) k_paired_small(const T* __restrict__ Lg, 
   for (int i = tid; i < n; i += nth) wc[(long long)r * n + i] = hv[i];
 }
 
+// ---- batched forms (one CTA per problem or per right-hand side), for many
+// small independent solves advanced together
+
+// Lowest k eigenpairs of the symmetric part of H (FP64 cyclic Jacobi in
+// shared memory), ascending: lam[k], vec[k][n] (rows = eigenvectors).
+__global__ void __launch_bounds__(512) k_beig(const BEig* __restrict__ d) {
+  extern __shared__ double smb[];
+  __shared__ int pp[kBatchSmall / 2 + 1], qq[kBatchSmall / 2 + 1];
+  __shared__ double cc[kBatchSmall / 2 + 1], ss[kBatchSmall / 2 + 1];
+  __shared__ unsigned smax;
+  __shared__ double red[33];
+  const BEig e = d[blockIdx.x];
+  const int n = e.n;
+  if (n <= 0) return;
+  const int NP = (n + 1) & ~1, ld = NP + 1;
+  double* A = smb;
+  double* Q = smb + NP * ld;
+  double f2 = 0.0;
+  for (int idx = threadIdx.x; idx < NP * NP; idx += blockDim.x) {
+    int r = idx / NP, c = idx - r * NP;
+    double v = 0.0;
+    if (r < n && c < n) v = 0.5 * (e.H[(long long)r * e.ld + c] + e.H[(long long)c * e.ld + r]);
+    f2 += v * v;
+    A[r * ld + c] = v;
+    Q[r * ld + c] = (r == c) ? 1.0 : 0.0;
+  }
+  double frob = sqrt(block_sum(f2, red));
+  jacobi_cta<double>(A, Q, n, ld, frob, 30, 1e-14, pp, qq, cc, ss, &smax);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    int r = diag_rank(A, ld, n, t);
+    if (r < e.k) {
+      e.lam[r] = A[t * ld + t];
+      for (int q = 0; q < n; ++q) e.vec[(long long)r * n + q] = Q[q * ld + t];
+    }
+  }
+}
+
+// y = (H - sigma I)^-1 b for one right-hand side per CTA (LU, partial pivoting).
+__global__ void __launch_bounds__(512) k_blu(const BLu* __restrict__ d) {
+  extern __shared__ __align__(16) unsigned char blu_raw[];
+  double* A = reinterpret_cast<double*>(blu_raw);
+  __shared__ int perm[kBatchSmall];
+  __shared__ double yv[kBatchSmall];
+  const BLu e = d[blockIdx.x];
+  const int n = e.n;
+  if (n <= 0) return;
+  const int ld = n + 2;
+  for (int idx = threadIdx.x; idx < n * (n + 1); idx += blockDim.x) {
+    int i = idx / (n + 1), j = idx - i * (n + 1);
+    double v;
+    if (j < n) v = 0.5 * (e.H[(long long)i * e.ld + j] + e.H[(long long)j * e.ld + i]) - (i == j ? e.sigma : 0.0);
+    else v = e.b[i];
+    A[i * ld + j] = v;
+  }
+  __syncthreads();
+  lu_solve_smem<double>(A, ld, n, perm, yv);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) e.y[i] = A[i * ld + n];
+}
+
+__global__ void __launch_bounds__(1024) k_bdrop(const BDrop* __restrict__ d, double drop2) {
+  extern __shared__ double smd[];
+  __shared__ int kj;
+  __shared__ double dj;
+  const BDrop e = d[blockIdx.x];
+  if (e.nc <= 0) return;
+  chol_drop_cta(e.G, e.nc, e.norm0sq, drop2, e.T, e.keep, smd, kj, dj);
+}
+
 void set_smem(const void* f, size_t bytes) {
   ensure_smem(f, bytes);
 }
@@ -854,6 +930,37 @@ void trsv_rows(const S* L, int ldl, int n, S* B, int nr, int trans, cudaStream_t
 }
 template void trsv_rows<float>(const float*, int, int, float*, int, int, cudaStream_t);
 template void trsv_rows<double>(const double*, int, int, double*, int, int, cudaStream_t);
+
+void batch_eig(const BEig* d, int nb, int nmax, cudaStream_t s) {
+  if (nb <= 0) return;
+  TD_REQUIRE(nmax >= 1 && nmax <= kBatchSmall, TDDFT_ERR_ARG, "batch_eig: size out of range");
+  const int NP = (nmax + 1) & ~1;
+  const size_t smem = (size_t)2 * NP * (NP + 1) * sizeof(double);
+  set_smem((const void*)k_beig, smem);
+  k_beig<<<nb, 512, smem, s>>>(d);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+void batch_lu(const BLu* d, int nr, int nmax, cudaStream_t s) {
+  if (nr <= 0) return;
+  TD_REQUIRE(nmax >= 1 && nmax <= kBatchSmall, TDDFT_ERR_ARG, "batch_lu: size out of range");
+  const size_t smem = (size_t)nmax * (nmax + 2) * sizeof(double);
+  set_smem((const void*)k_blu, smem);
+  k_blu<<<nr, 512, smem, s>>>(d);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+void batch_chol_drop(const BDrop* d, int nb, int ncmax, double drop2, cudaStream_t s) {
+  if (nb <= 0) return;
+  TD_REQUIRE(ncmax >= 1 && ncmax <= kBatchSmall, TDDFT_ERR_ARG, "batch_chol_drop: size out of range");
+  const size_t smem = (size_t)2 * ncmax * (ncmax + 1) * sizeof(double);
+  set_smem((const void*)k_bdrop, smem);
+  k_bdrop<<<nb, 1024, smem, s>>>(d, drop2);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
 
 void chol_drop(const double* G, int nc, const double* norm0sq, double drop2, double* T, int* keep,
                cudaStream_t s) {

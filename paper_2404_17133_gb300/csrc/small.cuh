@@ -66,4 +66,23 @@ void trsv_rows(const S* L, int ldl, int n, S* B, int nr, int trans, cudaStream_t
 void chol_drop(const double* G, int nc, const double* norm0sq, double drop2, double* T,
                int* keep, cudaStream_t s);
 
+// ---- batched forms for many small independent problems (device descriptor
+// arrays; one CTA per entry).  Sizes up to kBatchSmall.
+constexpr int kBatchSmall = 112;
+struct BEig {            // lowest k eigenpairs of the symmetric part of H (n x n, row stride ld)
+  const double* H; int ld, n, k;
+  double* lam;           // [k] ascending
+  double* vec;           // [k][n]
+};
+struct BLu {             // y = (H - sigma I)^-1 b (symmetric part of H)
+  const double* H; int ld, n; double sigma;
+  const double* b; double* y;   // [n]
+};
+struct BDrop {           // chol_drop of G (nc x nc) -> T, keep (norm0sq may be NULL)
+  const double* G; int nc; const double* norm0sq; double* T; int* keep;
+};
+void batch_eig(const BEig* d, int nb, int nmax, cudaStream_t s);
+void batch_lu(const BLu* d, int nr, int nmax, cudaStream_t s);
+void batch_chol_drop(const BDrop* d, int nb, int ncmax, double drop2, cudaStream_t s);
+
 }  // namespace tddft
