@@ -442,10 +442,12 @@ def our_arm(args, rank, world, local):
             "converged": conv, "load_s": t_load,
             "tda": {"omega0": float(a["omega"][0]), "n_iter": a["stats"]["n_iter"],
                     "n_matvec": a["stats"]["n_matvec"], "n_ris_matvec": a["stats"]["n_ris_matvec"],
-                    "max_resid_certified": a["stats"]["max_resid_certified"], "s": a["stats"]["t_total_s"]},
+                    "max_resid_certified": a["stats"]["max_resid_certified"], "s": a["stats"]["t_total_s"],
+                    "exact_product_s": a["stats"]["t_matvec_s"], "precond_s": a["stats"]["t_precond_s"]},
             "rpa": {"omega0": float(b["omega"][0]), "n_iter": b["stats"]["n_iter"],
                     "n_matvec": b["stats"]["n_matvec"], "n_ris_matvec": b["stats"]["n_ris_matvec"],
-                    "max_resid_certified": b["stats"]["max_resid_certified"], "s": b["stats"]["t_total_s"]},
+                    "max_resid_certified": b["stats"]["max_resid_certified"], "s": b["stats"]["t_total_s"],
+                    "exact_product_s": b["stats"]["t_matvec_s"], "precond_s": b["stats"]["t_precond_s"]},
             "diag": diag,
             "roofline": roof,
             "gpu_launches": launches,

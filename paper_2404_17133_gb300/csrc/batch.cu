@@ -30,6 +30,9 @@
 #include <memory>
 #include <numeric>
 
+#include <cstdio>
+#include <cstdlib>
+
 #include "ctx.cuh"
 #include "small.cuh"
 #include "vecops.cuh"
@@ -39,6 +42,13 @@ namespace tddft {
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// TDDFT_TRACE=1: one line per lockstep iteration (first problem and the worst residual)
+bool btrace() {
+  static int v = -1;
+  if (v < 0) { const char* e = getenv("TDDFT_TRACE"); v = (e && e[0] >= '1' && e[0] <= '9') ? 1 : 0; }
+  return v != 0;
+}
 
 // ============================================================================
 // grouped GEMM
@@ -1132,6 +1142,12 @@ void davidson_batch(Batch& B, std::vector<Prob*>& ps, bool ris, bool rid, const 
         if (!std::isfinite(p.om[j]) || !std::isfinite(p.rr[j]))
           throw Error(TDDFT_ERR_INDEFINITE, "non-finite Ritz values in a batched solve");
         if (!(p.rr[j] < tl)) p.todo.push_back(j);
+      }
+      if (btrace() && i == 0) {
+        double mr = 0.0;
+        for (int j = 0; j < kk; ++j) mr = std::max(mr, p.rr[j]);
+        fprintf(stderr, "[tddft-batch] %s it=%d active=%zu N=%d kk=%d omega0=%.10f max|r|=%.3e todo=%zu\n",
+                ris ? "ris" : (rid ? "rid" : "diag"), it, act.size(), p.N, kk, p.om[0], mr, p.todo.size());
       }
       if (p.todo.empty() && kk == (int)p.om.size()) { p.done = true; p.converged = true; continue; }
       if (it == max_iter) { p.done = true; continue; }

@@ -3,13 +3,14 @@ growth step of the rid preconditioner, Eq. TDDFT-ris_approx): through the C ABI.
 
   * the ris products (T_A X and the pair (T_A+T_B)X, (T_A-T_B)X) with the
     exchange contractions in kind::f8f6f4 against the oracle's FP64 ris
-    products: 5e-2 relative to the largest element (e4m3 keeps three
+    products: 1e-2 relative to the largest element (e4m3 keeps three
     mantissa bits, so a factor element is rounded by up to 2^-4 of itself;
-    the products average those errors) -- a preconditioner only;
+    the products average those errors: 4e-4 to 4.3e-3 measured on GB300)
+    -- a preconditioner only;
   * the preconditioner cannot move the converged answer: TDA, Casida and
     alpha(omega) solved with rid on FP8 ris factors match the oracle's dense
     results at the mixed tolerances (1e-5 Ha; alpha element by element, the
-    rule of tests/parity.py), on three shapes including ragged tiles and
+    tensor-core rule of tests/parity.py), on three shapes including ragged tiles and
     n_vir not a multiple of 16;
   * on the medium workload the FP8-ris Casida energies match the oracle's
     golden values to 1e-5 Ha and its outer iterations are printed beside the
@@ -24,7 +25,7 @@ import pytest
 from oracle import dense as D
 from oracle import operators as O
 from synth.generator import dipoles, make_config, make_problem
-from tests.parity import alpha_excess
+from tests.parity import FLOOR_TC, alpha_excess
 
 pytestmark = pytest.mark.gpu
 
@@ -68,7 +69,7 @@ def test_fp8_ris_products(case, api):
         rp, rm = T.apb_amb(X)
         ep, em = _rel(tp, rp), _rel(tm, rm)
         print("\n%s m=%d FP8 ris products: rel err %.3g (T), %.3g (T+), %.3g (T-)" % (name, m, e, ep, em))
-        assert e < 5e-2 and ep < 5e-2 and em < 5e-2
+        assert e < 1e-2 and ep < 1e-2 and em < 1e-2
 
 
 def test_fp8_ris_solves_match_dense(case, api):
@@ -83,7 +84,7 @@ def test_fp8_ris_solves_match_dense(case, api):
     mu = dipoles(3, 3, p.n_ov)
     om = [0.0, 0.05, 0.1]
     r = s.solve_polar(api.default_opts(precond=api.RID, precision=api.MIXED, tensor_cores=1, ris_fp8=1), mu, om)
-    assert r["status"] == api.OK and alpha_excess(r["alpha"], D.polar(A, B, mu, om), 1e-5) <= 1.0
+    assert r["status"] == api.OK and alpha_excess(r["alpha"], D.polar(A, B, mu, om), 1e-5, FLOOR_TC) <= 1.0
 
 
 def test_fp8_needs_tensor_cores(api):
