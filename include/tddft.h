@@ -113,6 +113,8 @@ typedef struct {
   double max_resid;           /* largest final residual norm                  */
   double max_resid_certified; /* MIXED: after the FP32-or-better re-check     */
   double t_total_s, t_matvec_s, t_precond_s;  /* wall times (host clock)     */
+  double t_guess_s;           /* initial guess (Davidson on the ris operator)  */
+  double t_certify_s;         /* MIXED: FP32 re-certification of the results   */
 } tddft_stats;
 
 /* Fill `opts` with the paper's defaults (Sec. 3.1-3.2): rid, tol 1e-5,

@@ -49,7 +49,8 @@ class Stats(C.Structure):
     _fields_ = [("n_iter", C.c_int), ("n_matvec", C.c_int), ("n_ris_matvec", C.c_int),
                 ("converged", C.c_int), ("n_restart", C.c_int), ("gpu_launches", C.c_int),
                 ("max_resid", C.c_double), ("max_resid_certified", C.c_double),
-                ("t_total_s", C.c_double), ("t_matvec_s", C.c_double), ("t_precond_s", C.c_double)]
+                ("t_total_s", C.c_double), ("t_matvec_s", C.c_double), ("t_precond_s", C.c_double),
+                ("t_guess_s", C.c_double), ("t_certify_s", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -230,6 +230,32 @@ int num_sms() {
   return n;
 }
 
+// Pinned staging ring for the uploads of task and row lists: each upload takes
+// the next slice and is copied in stream order; the stream is synchronised only
+// when the ring wraps, so filling a list never waits for the device.
+struct Ring {
+  char* h = nullptr;
+  size_t cap = 0, off = 0;
+  ~Ring() { if (h) cudaFreeHost(h); }
+  void upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return;
+    const size_t need = (bytes + 255) & ~size_t(255);
+    if (!h || need > cap) {
+      TD_CUDA(cudaStreamSynchronize(s));
+      if (h) cudaFreeHost(h);
+      cap = std::max<size_t>(need * 4, 32u << 20);
+      TD_CUDA(cudaMallocHost(&h, cap));
+      off = 0;
+    } else if (off + need > cap) {
+      TD_CUDA(cudaStreamSynchronize(s));   // every earlier copy out of the ring is done
+      off = 0;
+    }
+    std::memcpy(h + off, src, bytes);
+    TD_CUDA(cudaMemcpyAsync(dst, h + off, bytes, cudaMemcpyHostToDevice, s));
+    off += need;
+  }
+};
+
 // One list of grouped-GEMM tasks: host staging (pinned), device copy, header
 // and a partial-sum arena.  `run` uploads the list and launches the tile
 // kernel of variant `v` (grid: a few CTAs per SM, persistent) and the split
@@ -280,9 +306,10 @@ struct GList {
     tasks.push_back(g);
   }
   // fill tile/element prefixes and partial-sum pointers for tile shape bm x bn
+  GHdr hdr_host{};
   void finalize(int bm, int bn, cudaStream_t s) {
     // the pinned staging may still be read by the previous upload
-    TD_CUDA(cudaStreamSynchronize(s));
+    if (!ring) TD_CUDA(cudaStreamSynchronize(s));
     size_t need = 0;
     for (const GTask& g : tasks)
       if (g.ksplit > 1 || g.Cd) need += ((size_t)g.ksplit * g.M * g.N * 4 + 255) & ~size_t(255);
@@ -292,14 +319,13 @@ struct GList {
     }
     if (tasks.size() > cap_tasks) {
       if (h_tasks) cudaFreeHost(h_tasks);
+      h_tasks = nullptr;
       cap_tasks = tasks.size() + tasks.size() / 2 + 64;
-      TD_CUDA(cudaMallocHost(&h_tasks, cap_tasks * sizeof(GTask)));
+      if (!ring) TD_CUDA(cudaMallocHost(&h_tasks, cap_tasks * sizeof(GTask)));
       d_tasks = DevBuf(cap_tasks * sizeof(GTask), s);
     }
-    if (!h_hdr) {
-      TD_CUDA(cudaMallocHost(&h_hdr, sizeof(GHdr)));
-      d_hdr = DevBuf(sizeof(GHdr), s);
-    }
+    if (!d_hdr.p) d_hdr = DevBuf(sizeof(GHdr), s);
+    if (!ring && !h_hdr) TD_CUDA(cudaMallocHost(&h_hdr, sizeof(GHdr)));
     int tile = 0, elem = 0;
     size_t off = 0;
     for (GTask& g : tasks) {
@@ -316,17 +342,26 @@ struct GList {
         g.part = nullptr;
       }
     }
-    std::memcpy(h_tasks, tasks.data(), tasks.size() * sizeof(GTask));
-    h_hdr->ntask = (int)tasks.size();
-    h_hdr->total_tiles = tile;
-    h_hdr->total_elems = elem;
+    hdr_host.ntask = (int)tasks.size();
+    hdr_host.total_tiles = tile;
+    hdr_host.total_elems = elem;
+    if (!ring) {
+      std::memcpy(h_tasks, tasks.data(), tasks.size() * sizeof(GTask));
+      *h_hdr = hdr_host;
+    }
   }
   // upload + launch (finalize first)
+  Ring* ring = nullptr;
   void launch(const Variant& v, cudaStream_t s) {
     if (tasks.empty()) return;
-    TD_CUDA(cudaMemcpyAsync(d_tasks.p, h_tasks, tasks.size() * sizeof(GTask), cudaMemcpyHostToDevice, s));
-    TD_CUDA(cudaMemcpyAsync(d_hdr.p, h_hdr, sizeof(GHdr), cudaMemcpyHostToDevice, s));
-    launch_kernels(v, std::max(1, h_hdr->total_tiles), std::max(1, h_hdr->total_elems), s);
+    if (ring) {
+      ring->upload(d_tasks.p, tasks.data(), tasks.size() * sizeof(GTask), s);
+      ring->upload(d_hdr.p, &hdr_host, sizeof(GHdr), s);
+    } else {
+      TD_CUDA(cudaMemcpyAsync(d_tasks.p, h_tasks, tasks.size() * sizeof(GTask), cudaMemcpyHostToDevice, s));
+      TD_CUDA(cudaMemcpyAsync(d_hdr.p, h_hdr, sizeof(GHdr), cudaMemcpyHostToDevice, s));
+    }
+    launch_kernels(v, std::max(1, hdr_host.total_tiles), std::max(1, hdr_host.total_elems), s);
   }
   void launch_kernels(const Variant& v, int tiles, int elems, cudaStream_t s) {
     const int grid = std::max(1, std::min(tiles, num_sms() * 4));
@@ -464,18 +499,24 @@ struct RList {
   size_t cap = 0;
   void free_stage() { if (h) cudaFreeHost(h); h = nullptr; }
   void add(const RowOp& r) { ops.push_back(r); }
+  Ring* ring = nullptr;
   void run(cudaStream_t s) {
     if (ops.empty()) return;
     if (ops.size() > cap) {
       if (h) cudaFreeHost(h);
+      h = nullptr;
       cap = ops.size() + ops.size() / 2 + 64;
-      TD_CUDA(cudaMallocHost(&h, cap * sizeof(RowOp)));
+      if (!ring) TD_CUDA(cudaMallocHost(&h, cap * sizeof(RowOp)));
       d = DevBuf(cap * sizeof(RowOp), s);
     }
-    // the pinned staging may still be read by an earlier copy: wait for the stream
-    TD_CUDA(cudaStreamSynchronize(s));
-    std::memcpy(h, ops.data(), ops.size() * sizeof(RowOp));
-    TD_CUDA(cudaMemcpyAsync(d.p, h, ops.size() * sizeof(RowOp), cudaMemcpyHostToDevice, s));
+    if (ring) {
+      ring->upload(d.p, ops.data(), ops.size() * sizeof(RowOp), s);
+    } else {
+      // the pinned staging may still be read by an earlier copy: wait for the stream
+      TD_CUDA(cudaStreamSynchronize(s));
+      std::memcpy(h, ops.data(), ops.size() * sizeof(RowOp));
+      TD_CUDA(cudaMemcpyAsync(d.p, h, ops.size() * sizeof(RowOp), cudaMemcpyHostToDevice, s));
+    }
     const int grid = (int)std::min<size_t>(ops.size(), (size_t)num_sms() * 8);
     k_rowops<<<grid, 256, 0, s>>>(d.as<RowOp>(), (int)ops.size());
     count_launch();
@@ -542,8 +583,8 @@ RowOp rowop(int op, int n, float* y, const float* x1, const float* x2 = nullptr,
 // ============================================================================
 // the batch
 
-constexpr int kCap = 96;          // outer subspace rows per problem
-constexpr int kInnerCap = 96;     // inner (ris) subspace rows per problem
+constexpr int kCap = kBatchSmall;        // outer subspace rows per problem
+constexpr int kInnerCap = kBatchSmall;   // inner (ris) subspace rows per problem
 constexpr size_t kZBudget = 128ull << 20;  // exchange intermediates per problem
 
 struct Ops {   // one operator of one problem (FP32 exact or BF16 ris factors)
@@ -562,8 +603,9 @@ struct Prob {
   // operator work buffers
   DevBuf t, J, K1, Z;
   // outer space
-  DevBuf V, W, a, lam, xv, X, AX, R, cand, tmp, C, G, Tm, keep, nrm0;
+  DevBuf V, W, a, lam, xv, X, AX, R, cand, tmp, C, G, Tm, keep, nrm0, Xprev;
   int N = 0;
+  bool have_prev = false;
   // inner space
   DevBuf S, TS, ti, h, y, v, Tv, res, icand;
   int Ns = 0;
@@ -580,6 +622,7 @@ struct Prob {
 struct Batch {
   std::vector<Prob> P;
   cudaStream_t s = nullptr;
+  Ring ring;
   GList g;
   RList rl;
   const Variant* var = nullptr;
@@ -788,6 +831,14 @@ void operator_graph(Batch& B, std::vector<OpCall>& calls) {
 
 // Time every tile variant on the first exchange contraction list (same bits
 // from each) and keep the fastest.
+// TDDFT_BATCH_VARIANT=i forces variant i (after timing every variant).
+int forced_variant() {
+  const char* e = getenv("TDDFT_BATCH_VARIANT");
+  if (!e || !*e) return -1;
+  const int v = atoi(e);
+  return (v >= 0 && v < (int)variants().size()) ? v : -1;
+}
+
 void autotune(Batch& B, std::vector<OpCall>& calls) {
   const auto& vs = variants();
   B.tune_ms.assign(vs.size(), -1.0);
@@ -816,7 +867,8 @@ void autotune(Batch& B, std::vector<OpCall>& calls) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  B.var = &vs[best];
+  const int f = forced_variant();
+  B.var = &vs[f >= 0 ? f : best];
 }
 
 // ---------------------------------------------------------------------------
@@ -1067,6 +1119,7 @@ void davidson_batch(Batch& B, std::vector<Prob*>& ps, bool ris, bool rid, const 
     p.done = false;
     p.converged = false;
     p.n_iter = 0;
+    p.have_prev = false;
     p.om.assign(k_of[i], 0.0);
     p.rr.assign(k_of[i], 1.0);
     // guess rows X -> cand, orthonormalised into V
@@ -1143,11 +1196,11 @@ void davidson_batch(Batch& B, std::vector<Prob*>& ps, bool ris, bool rid, const 
           throw Error(TDDFT_ERR_INDEFINITE, "non-finite Ritz values in a batched solve");
         if (!(p.rr[j] < tl)) p.todo.push_back(j);
       }
-      if (btrace() && i == 0) {
+      if (btrace()) {
         double mr = 0.0;
         for (int j = 0; j < kk; ++j) mr = std::max(mr, p.rr[j]);
-        fprintf(stderr, "[tddft-batch] %s it=%d active=%zu N=%d kk=%d omega0=%.10f max|r|=%.3e todo=%zu\n",
-                ris ? "ris" : (rid ? "rid" : "diag"), it, act.size(), p.N, kk, p.om[0], mr, p.todo.size());
+        fprintf(stderr, "[tddft-batch] %s it=%d prob=%zu/%zu ov=%d N=%d kk=%d omega0=%.10f max|r|=%.3e todo=%zu\n",
+                ris ? "ris" : (rid ? "rid" : "diag"), it, i, act.size(), p.ov, p.N, kk, p.om[0], mr, p.todo.size());
       }
       if (p.todo.empty() && kk == (int)p.om.size()) { p.done = true; p.converged = true; continue; }
       if (it == max_iter) { p.done = true; continue; }
@@ -1175,8 +1228,10 @@ void davidson_batch(Batch& B, std::vector<Prob*>& ps, bool ris, bool rid, const 
         }
       B.rl.run(B.s);
     }
-    // restart when the space would overflow: V <- the current Ritz vectors
-    std::vector<OpCall> restarts;
+    // thick restart when the space would overflow: V <- the current Ritz
+    // vectors and, where they fit with the new directions, those of the
+    // previous iteration (their products recomputed)
+    std::vector<Prob*> rst;
     for (Prob* p : need) {
       const int nu = (int)p->todo.size();
       if (p->N + nu <= std::min(kCap, p->ov)) continue;
@@ -1186,6 +1241,43 @@ void davidson_batch(Batch& B, std::vector<Prob*>& ps, bool ris, bool rid, const 
         B.rl.add(rowop(R_COPY, p->ov, p->W.as<float>() + (size_t)j * p->ov, p->AX.as<float>() + (size_t)j * p->ov));
       }
       p->N = kk;
+      if (p->have_prev && 2 * kk + nu <= std::min(kCap, p->ov)) {
+        for (int j = 0; j < kk; ++j)
+          B.rl.add(rowop(R_COPY, p->ov, p->tmp.as<float>() + (size_t)j * p->ov, p->Xprev.as<float>() + (size_t)j * p->ov));
+        rst.push_back(p);
+      }
+    }
+    B.rl.run(B.s);
+    if (!rst.empty()) {
+      // tmp is the orthonormalisation's scratch: move the previous vectors to R first
+      for (Prob* p : rst) {
+        const int kk = p->N;
+        for (int j = 0; j < kk; ++j)
+          B.rl.add(rowop(R_COPY, p->ov, p->R.as<float>() + (size_t)j * p->ov, p->tmp.as<float>() + (size_t)j * p->ov));
+      }
+      B.rl.run(B.s);
+      std::vector<OrthCall> oc3;
+      std::vector<int> n0;
+      for (Prob* p : rst) {
+        n0.push_back(p->N);
+        oc3.push_back(OrthCall{p, p->V.as<float>(), &p->N, p->R.as<float>(), p->N, kCap});
+      }
+      orth_append_batch(B, oc3);
+      std::vector<OpCall> rc;
+      for (size_t i = 0; i < rst.size(); ++i) {
+        Prob* p = rst[i];
+        if (p->N > n0[i])
+          rc.push_back(OpCall{p, p->V.as<float>() + (size_t)n0[i] * p->ov, p->W.as<float>() + (size_t)n0[i] * p->ov,
+                              p->N - n0[i]});
+      }
+      operator_batch(B, rc, ris);
+    }
+    // the current Ritz vectors become the previous ones of the next iteration
+    for (Prob* p : need) {
+      const int kk = std::min((int)p->om.size(), p->N);
+      for (int j = 0; j < kk; ++j)
+        B.rl.add(rowop(R_COPY, p->ov, p->Xprev.as<float>() + (size_t)j * p->ov, p->X.as<float>() + (size_t)j * p->ov));
+      p->have_prev = true;
     }
     B.rl.run(B.s);
     std::vector<int> nold;
@@ -1217,6 +1309,8 @@ tddft_status solve_tda_batch(Ctx* const* ctxs, int n, const tddft_opts* opts, do
   TD_REQUIRE(n >= 1 && ctxs && opts && omega, TDDFT_ERR_ARG, "batch: bad arguments");
   Batch B;
   B.s = ctxs[0]->s;
+  B.g.ring = &B.ring;
+  B.rl.ring = &B.ring;
   B.P.resize(n);
   int kmax = 1;
   for (int i = 0; i < n; ++i) {
@@ -1283,6 +1377,7 @@ tddft_status solve_tda_batch(Ctx* const* ctxs, int n, const tddft_opts* opts, do
     p.G = DevBuf((size_t)kCap * kCap * 8, s);
     p.Tm = DevBuf((size_t)kCap * kCap * 8, s);
     p.keep = DevBuf((size_t)kCap * 4, s);
+    p.Xprev = DevBuf((size_t)kCap * ov * 4, s);
     p.nrm0 = DevBuf((size_t)kCap * 8, s);
     p.S = DevBuf((size_t)kInnerCap * ov * 4, s);
     p.TS = DevBuf((size_t)kInnerCap * ov * 4, s);

@@ -87,20 +87,26 @@ void stage_exact(ExactCopies& e, const void* L_oo, const void* L_ov, const void*
   stage_rows(L_ov, tin, dev, A, ov, targets(e.f64_ov, e.f32_ov), s);
   stage_rows(L_vv, tin, dev, A, (long long)nv * nv, targets(e.f64_vv, e.f32_vv), s);
   if (pmx) {
-    tc_split_pad(e.f32_vv.as<float>(), (int)(A * nv), 1, nv, e.vv_hi.as<__nv_bfloat16>(),
-                 e.vv_lo.as<__nv_bfloat16>(), s);
+    // three BF16 parts per element (hi, lo, l2): hi + lo for the iterations'
+    // products, all three for the FP32-accurate re-certification
+    e.vv_l2 = DevBuf(A * nv * tc_pad(nv) * 2, s);
+    tc_pad_split(e.f32_vv.p, DType::F32, A * nv, nv, e.vv_hi.as<__nv_bfloat16>(), e.vv_lo.as<__nv_bfloat16>(), s,
+                 e.vv_l2.as<__nv_bfloat16>());
     e.vo_hi = DevBuf(A * nv * tc_pad(no) * 2, s);
     e.vo_lo = DevBuf(A * nv * tc_pad(no) * 2, s);
+    e.vo_l2 = DevBuf(A * nv * tc_pad(no) * 2, s);
     tc_transpose_split(e.f32_ov.p, DType::F32, (int)A, no, nv, e.vo_hi.as<__nv_bfloat16>(),
-                       e.vo_lo.as<__nv_bfloat16>(), s);
+                       e.vo_lo.as<__nv_bfloat16>(), s, e.vo_l2.as<__nv_bfloat16>());
     e.oo_hi = DevBuf(A * no * tc_pad(no) * 2, s);
     e.oo_lo = DevBuf(A * no * tc_pad(no) * 2, s);
+    e.oo_l2 = DevBuf(A * no * tc_pad(no) * 2, s);
     tc_pad_split(e.f32_oo.p, DType::F32, A * no, no, e.oo_hi.as<__nv_bfloat16>(), e.oo_lo.as<__nv_bfloat16>(),
-                 s);
+                 s, e.oo_l2.as<__nv_bfloat16>());
     e.ov_hi = DevBuf(A * no * tc_pad(nv) * 2, s);
     e.ov_lo = DevBuf(A * no * tc_pad(nv) * 2, s);
+    e.ov_l2 = DevBuf(A * no * tc_pad(nv) * 2, s);
     tc_pad_split(e.f32_ov.p, DType::F32, A * no, nv, e.ov_hi.as<__nv_bfloat16>(), e.ov_lo.as<__nv_bfloat16>(),
-                 s);
+                 s, e.ov_l2.as<__nv_bfloat16>());
   }
 }
 
@@ -176,7 +182,8 @@ unsigned long long factor_copy_bytes(const tddft_desc& d) {
   if (p64) bytes += 8.0 * (nvv + noo + nov + nr);
   // FP8 copies of the ris exchange rows: vv and ov^T padded to 16, four floats per row
   const double fp8 = (double)d.n_aux_ris_K * (nv * (tc_pad16(d.n_vir) + tc_pad16(d.n_occ)) + 16.0);
-  if (pmx) bytes += 4.0 * (nvv + noo + nov) + 4.0 * (double)d.n_aux * padded + 2.0 * nr +
+  // MIXED: FP32 copies, three BF16 parts of every padded exact operand, BF16 ris rows and their padded copies
+  if (pmx) bytes += 4.0 * (nvv + noo + nov) + 6.0 * (double)d.n_aux * padded + 2.0 * nr +
                     2.0 * (double)d.n_aux_ris_K * padded + fp8;
   return (unsigned long long)bytes;
 }
@@ -198,6 +205,10 @@ void ExactCopies::fill(FactorSet& f, int precision, bool coulomb) const {
     f.Koo_lo = oo_lo.as<__nv_bfloat16>();
     f.Kovp_hi = ov_hi.as<__nv_bfloat16>();
     f.Kovp_lo = ov_lo.as<__nv_bfloat16>();
+    f.Kvv_l2 = vv_l2.as<__nv_bfloat16>();
+    f.Kvo_l2 = vo_l2.as<__nv_bfloat16>();
+    f.Koo_l2 = oo_l2.as<__nv_bfloat16>();
+    f.Kovp_l2 = ov_l2.as<__nv_bfloat16>();
   }
 }
 
@@ -543,7 +554,7 @@ tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cor
     const size_t n = (size_t)m * c->ov;
     const bool ris = kind >= 2;
     const bool paired = kind & 1;
-    TD_REQUIRE(tensor_cores >= 0 && tensor_cores <= 2, TDDFT_ERR_ARG, "tensor_cores must be 0, 1 or 2");
+    TD_REQUIRE(tensor_cores >= 0 && tensor_cores <= 3, TDDFT_ERR_ARG, "tensor_cores must be 0..3");
     FactorSet f = ris ? c->ris(precision, tensor_cores == 2) : c->exact(precision);
     DevBuf xb, o0, o1;
     const double* Xd = X;
@@ -559,7 +570,7 @@ tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cor
     }
     g_launches = 0;
     apply_operator(c->dims(), f, Xd, m, paired ? OpMode::PAIRED : OpMode::TDA, d0, paired ? d1 : nullptr,
-                   tensor_cores != 0, s);
+                   (!ris && tensor_cores == 3) ? 2 : (tensor_cores != 0 ? 1 : 0), s);
     if (!on_device) {
       TD_CUDA(cudaMemcpyAsync(out0, d0, n * 8, cudaMemcpyDeviceToHost, s));
       if (paired) TD_CUDA(cudaMemcpyAsync(out1, d1, n * 8, cudaMemcpyDeviceToHost, s));

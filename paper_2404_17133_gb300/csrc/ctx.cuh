@@ -34,6 +34,12 @@ struct FactorSet {
   const __nv_bfloat16* Koo_lo = nullptr;
   const __nv_bfloat16* Kovp_hi = nullptr;
   const __nv_bfloat16* Kovp_lo = nullptr;
+  // third BF16 parts (x = hi + lo + l2) of the exact operands, for the
+  // FP32-accurate tensor-core products of the re-certification
+  const __nv_bfloat16* Kvv_l2 = nullptr;
+  const __nv_bfloat16* Kvo_l2 = nullptr;
+  const __nv_bfloat16* Koo_l2 = nullptr;
+  const __nv_bfloat16* Kovp_l2 = nullptr;
   // Variant terms of the exact operator (Eq. hessian for other functionals):
   // a second exchange factor set entering with weight b_x, and a low-rank
   // kernel sum_g w_g F^g_ia F^g_jb added to the Coulomb term, its rows stored
@@ -64,10 +70,10 @@ struct ExactCopies {
   int n = 0;
   DevBuf f64_oo, f64_ov, f64_vv;  // PLAIN
   DevBuf f32_oo, f32_ov, f32_vv;  // MIXED: SIMT operands and the FP32 re-certification
-  DevBuf vv_hi, vv_lo;            // [n][nv][tc_pad(nv)] BF16 split of L_vv
-  DevBuf vo_hi, vo_lo;            // [n][nv][tc_pad(no)] BF16 split of L_ov transposed
-  DevBuf oo_hi, oo_lo;            // [n][no][tc_pad(no)]
-  DevBuf ov_hi, ov_lo;            // [n][no][tc_pad(nv)]
+  DevBuf vv_hi, vv_lo, vv_l2;     // [n][nv][tc_pad(nv)] BF16 split of L_vv (three parts)
+  DevBuf vo_hi, vo_lo, vo_l2;     // [n][nv][tc_pad(no)] BF16 split of L_ov transposed
+  DevBuf oo_hi, oo_lo, oo_l2;     // [n][no][tc_pad(no)]
+  DevBuf ov_hi, ov_lo, ov_l2;     // [n][no][tc_pad(nv)]
   // Exchange operands of `precision` into f (and the Coulomb block when coulomb).
   void fill(FactorSet& f, int precision, bool coulomb) const;
 };
@@ -105,12 +111,15 @@ struct OpDims {
 enum class OpMode { TDA, PAIRED };
 
 // out0 = A X (TDA) or (A+B) X and out1 = (A-B) X (PAIRED); X, out FP64 [m][ov].
-// tensor_cores: K1's dominant contraction on tcgen05 (BF16 hi+lo), needs Kvv_hi/lo.
+// tc: 0 SIMT contractions; 1 the exchange contractions on tcgen05 (BF16 hi+lo
+// operands, three products; plain BF16 ris factors); 2 on tcgen05 with three
+// BF16 parts per operand (six products: FP32-accurate, for re-certification;
+// exact factor sets with the third parts only, else as 1).
 void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m, OpMode mode,
-                    double* out0, double* out1, bool tensor_cores, cudaStream_t s);
+                    double* out0, double* out1, int tc, cudaStream_t s);
 // FP32 vectors (FP32 or BF16 factor sets only): the ris products of the inner solves.
 void apply_operator(const OpDims& d, const FactorSet& f, const float* X, int m, OpMode mode,
-                    float* out0, float* out1, bool tensor_cores, cudaStream_t s);
+                    float* out0, float* out1, int tc, cudaStream_t s);
 
 struct Request {
   int kind = 0;

@@ -114,7 +114,8 @@ void check_tc_error(Ctx& c) {
 
 template <typename TX>
 static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, int m, OpMode mode,
-                             TX* out0, TX* out1, bool tensor_cores, cudaStream_t s) {
+                             TX* out0, TX* out1, int tc, cudaStream_t s) {
+  const bool tensor_cores = tc != 0;
   if (m <= 0) return;
   const int no = d.no, nv = d.nv, ov = d.ov;
   const bool f64 = (f.dt == DType::F64);
@@ -165,9 +166,60 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
     if (need_k2) K2b = DevBuf(mov * ew, s);
     const bool use_tc = tensor_cores && !f64 && f.Kvv_hi && f.Kvo_hi && f.Koo_hi && f.Kovp_hi;
     TD_REQUIRE(!tensor_cores || f64 || use_tc, TDDFT_ERR_ARG, "tensor-core factor copies missing");
-    const int pc = chunk_rows(f.nK, (long long)m * ov * (long long)ew, m);
+    const bool tc3 = use_tc && tc == 2 && f.Kvv_l2 && f.Kvo_l2 && f.Koo_l2 && f.Kovp_l2 && f.Kvv_lo &&
+                     tc_stage1_3_fits(no);
+    // three-part intermediates take half as much again as hi + lo ones
+    const int pc = chunk_rows(f.nK, (long long)m * ov * (long long)ew * (tc3 ? 3 : 2) / 2, m);
     const size_t es = dtype_size(f.dt);
-    if (use_tc && f.fp8) {
+    if (tc3) {
+      // FP32-accurate products on the tensor cores: every operand (trial
+      // vectors, factors, the stage-1 results) as three BF16 parts x = h + m + l
+      // and the six products h h + h m + m h + h l + l h + m m, accumulated in
+      // FP32 -- as K1 = [BOTH (h, m) x (h, m)] + [CROSS (h, l) x (h, l)] +
+      // [SINGLE m x m] over each P-chunk
+      const int nvp = tc_pad(nv), nop = tc_pad(no);
+      const DType xt = x32 ? DType::F32 : DType::F64;
+      DevBuf Xt[3], Xs[3], Zp[3], Qp[3];
+      for (int t = 0; t < 3; ++t) {
+        Xt[t] = DevBuf((size_t)m * nv * nop * 2, s);
+        Zp[t] = DevBuf((size_t)m * no * pc * nvp * 2, s);
+        if (need_k2) {
+          Xs[t] = DevBuf((size_t)m * no * nvp * 2, s);
+          Qp[t] = DevBuf((size_t)m * no * pc * nop * 2, s);
+        }
+      }
+      auto bf = [](DevBuf& b) { return b.as<__nv_bfloat16>(); };
+      tc_transpose_split(X, xt, m, no, nv, bf(Xt[0]), bf(Xt[1]), s, bf(Xt[2]));
+      if (need_k2) tc_pad_split(X, xt, (long long)m * no, nv, bf(Xs[0]), bf(Xs[1]), s, bf(Xs[2]));
+      const int Mz = m * no;
+      for (int p0 = 0; p0 < f.nK; p0 += pc) {
+        const int pn = (f.nK - p0 < pc) ? f.nK - p0 : pc;
+        {
+          const __nv_bfloat16* const A3[3] = {bf(Xt[0]), bf(Xt[1]), bf(Xt[2])};
+          const size_t o = (size_t)p0 * no * nop;
+          const __nv_bfloat16* const B3[3] = {f.Koo_hi + o, f.Koo_lo + o, f.Koo_l2 + o};
+          __nv_bfloat16* const Z3[3] = {bf(Zp[0]), bf(Zp[1]), bf(Zp[2])};
+          tc_stage1_3(A3, m * nv, no, B3, no, pn, nv, Z3, d.tc_err, s);
+          const size_t v = (size_t)p0 * nv * nvp;
+          tc_contract(Z3[0], Z3[1], Mz, pn, nv, f.Kvv_hi + v, f.Kvv_lo + v, nv, K1b.as<float>(), p0 > 0, d.tc_err, s);
+          tc_contract(Z3[0], Z3[2], Mz, pn, nv, f.Kvv_hi + v, f.Kvv_l2 + v, nv, K1b.as<float>(), true, d.tc_err, s,
+                      nullptr, 0.0, 0.0, true);
+          tc_contract(Z3[1], nullptr, Mz, pn, nv, f.Kvv_lo + v, nullptr, nv, K1b.as<float>(), true, d.tc_err, s);
+        }
+        if (need_k2) {
+          const __nv_bfloat16* const A3[3] = {bf(Xs[0]), bf(Xs[1]), bf(Xs[2])};
+          const size_t o = (size_t)p0 * no * nvp;
+          const __nv_bfloat16* const B3[3] = {f.Kovp_hi + o, f.Kovp_lo + o, f.Kovp_l2 + o};
+          __nv_bfloat16* const Q3[3] = {bf(Qp[0]), bf(Qp[1]), bf(Qp[2])};
+          tc_stage1_3(A3, m * no, nv, B3, no, pn, no, Q3, d.tc_err, s);
+          const size_t v = (size_t)p0 * nv * nop;
+          tc_contract(Q3[0], Q3[1], Mz, pn, no, f.Kvo_hi + v, f.Kvo_lo + v, nv, K2b.as<float>(), p0 > 0, d.tc_err, s);
+          tc_contract(Q3[0], Q3[2], Mz, pn, no, f.Kvo_hi + v, f.Kvo_l2 + v, nv, K2b.as<float>(), true, d.tc_err, s,
+                      nullptr, 0.0, 0.0, true);
+          tc_contract(Q3[1], nullptr, Mz, pn, no, f.Kvo_lo + v, nullptr, nv, K2b.as<float>(), true, d.tc_err, s);
+        }
+      }
+    } else if (use_tc && f.fp8) {
       // ris exchange rows in FP8 e4m3 (one scale per row P): the stage-1
       // products Z = L_oo X and Q = L_ov X^T run as for BF16 (trial vectors as
       // BF16 hi + lo against the BF16 rows) and leave their results as e4m3
@@ -357,13 +409,13 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
 }
 
 void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m, OpMode mode,
-                    double* out0, double* out1, bool tensor_cores, cudaStream_t s) {
-  apply_operator_t<double>(d, f, X, m, mode, out0, out1, tensor_cores, s);
+                    double* out0, double* out1, int tc, cudaStream_t s) {
+  apply_operator_t<double>(d, f, X, m, mode, out0, out1, tc, s);
 }
 
 void apply_operator(const OpDims& d, const FactorSet& f, const float* X, int m, OpMode mode,
-                    float* out0, float* out1, bool tensor_cores, cudaStream_t s) {
-  apply_operator_t<float>(d, f, X, m, mode, out0, out1, tensor_cores, s);
+                    float* out0, float* out1, int tc, cudaStream_t s) {
+  apply_operator_t<float>(d, f, X, m, mode, out0, out1, tc, s);
 }
 
 }  // namespace tddft

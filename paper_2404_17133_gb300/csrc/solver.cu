@@ -28,6 +28,7 @@
 #include "ctx.cuh"
 #include "skinny.cuh"
 #include "small.cuh"
+#include "tc_gemm.cuh"
 #include "vecops.cuh"
 
 namespace tddft {
@@ -105,7 +106,7 @@ void h2d(T* p, const std::vector<T>& h, cudaStream_t s) {
 struct Counters {
   long long mv = 0;      // exact operator vectors
   long long ris_mv = 0;  // ris operator vectors
-  double t_mv = 0.0, t_pre = 0.0;
+  double t_mv = 0.0, t_pre = 0.0, t_guess = 0.0, t_cert = 0.0;
   int restarts = 0;
 };
 
@@ -924,6 +925,11 @@ Plan make_plan(const Ctx& c, const tddft_opts& o) {
   return p;
 }
 
+// The re-certification's operator form: the FP32-accurate three-part tensor-core
+// products after a tensor-core solve (when their stage-1 tiles fit), else the
+// FP32 SIMT contractions.
+int cert_tc(const Ctx& c, const Plan& p) { return (p.tc && tc_stage1_3_fits(c.no)) ? 2 : 0; }
+
 void fill_stats(tddft_stats* st, int n_iter, const Counters& cnt, bool conv,
                 const std::vector<double>& resid, double cert, Clock::time_point t0) {
   if (!st) return;
@@ -939,6 +945,8 @@ void fill_stats(tddft_stats* st, int n_iter, const Counters& cnt, bool conv,
   st->t_total_s = since(t0);
   st->t_matvec_s = cnt.t_mv;
   st->t_precond_s = cnt.t_pre;
+  st->t_guess_s = cnt.t_guess;
+  st->t_certify_s = cnt.t_cert;
   st->gpu_launches = (int)g_launches;
 }
 
@@ -991,6 +999,7 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
   DevBuf guess;
   int ng = p.k0;
   if (p.precond == TDDFT_PRECOND_RID) {
+    auto tg = Clock::now();
     const int kg = std::min(p.k0 + 8, ov);
     DevBuf unit((size_t)kg * ov * 8, s);
     TD_REQUIRE(kg <= c.n_order, TDDFT_ERR_ARG, "too many initial guesses");
@@ -998,6 +1007,8 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     TdaOut g = davidson_tda(ov, T, diag, unit.as<double>(), kg, p.k0, p.guess_tol, p.max_iter, p.cap,
                             p.rounds, cnt, false, s);
     guess = std::move(g.X);
+    TD_CUDA(cudaStreamSynchronize(s));
+    cnt.t_guess = since(tg);
   } else {
     TD_REQUIRE(p.k0 <= c.n_order, TDDFT_ERR_ARG, "too many initial guesses");
     guess = DevBuf((size_t)p.k0 * ov * 8, s);
@@ -1007,14 +1018,18 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
                           p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s);
   double cert = -1.0;
   if (p.mixed) {
-    // re-check the converged residuals with the FP32 SIMT operator (no tensor cores)
-    const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 SIMT operator, FP32 accumulation
+    // re-check the converged residuals with an FP32-accurate operator: the
+    // three-part BF16 tensor-core products when the solve ran on the tensor
+    // cores, else the FP32 SIMT contractions
+    auto tc0 = Clock::now();
+    const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 factors and their three-part BF16 split
     DevBuf AX((size_t)p.k * ov * 8, s), R((size_t)p.k * ov * 8, s), rn(p.k * 8, s), om(p.k * 8, s);
-    apply_operator(dims, Fc, r.X.as<double>(), p.k, OpMode::TDA, AX.as<double>(), nullptr, false, s);
+    apply_operator(dims, Fc, r.X.as<double>(), p.k, OpMode::TDA, AX.as<double>(), nullptr, cert_tc(c, p), s);
     h2d(om.as<double>(), r.omega, s);
     resid_tda(r.X.as<double>(), AX.as<double>(), om.as<double>(), p.k, ov, R.as<double>(), s);
     row_sumsq(R.as<double>(), ov, p.k, ov, rn.as<double>(), s);
     for (double v : sqrt_all(d2h(rn.as<double>(), p.k, s))) cert = std::max(cert, v);
+    cnt.t_cert = since(tc0);
   }
   const bool dev = o.outputs_on_device != 0;
   if (omega) {
@@ -1099,6 +1114,7 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
   DevBuf guess;
   int ng = p.k0;
   if (p.precond == TDDFT_PRECOND_RID) {
+    auto tg = Clock::now();
     const int kg = std::min(p.k0 + 8, ov);
     TD_REQUIRE(kg <= c.n_order, TDDFT_ERR_ARG, "too many initial guesses");
     DevBuf unit((size_t)kg * ov * 8, s);
@@ -1110,6 +1126,8 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     TD_CUDA(cudaMemcpyAsync(guess.as<double>() + (size_t)p.k0 * ov, g.W.p, (size_t)p.k0 * ov * 8,
                             cudaMemcpyDeviceToDevice, s));
     ng = 2 * p.k0;
+    TD_CUDA(cudaStreamSynchronize(s));
+    cnt.t_guess = since(tg);
   } else {
     TD_REQUIRE(p.k0 <= c.n_order, TDDFT_ERR_ARG, "too many initial guesses");
     guess = DevBuf((size_t)p.k0 * ov * 8, s);
@@ -1119,13 +1137,14 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
                           p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s);
   double cert = -1.0;
   if (p.mixed) {
-    const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 SIMT operator, FP32 accumulation
+    auto tc0 = Clock::now();
+    const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 factors and their three-part BF16 split
     const int k = p.k;
     DevBuf PU((size_t)k * ov * 8, s), MU((size_t)k * ov * 8, s), PW((size_t)k * ov * 8, s),
         MW((size_t)k * ov * 8, s), Rp((size_t)k * ov * 8, s), Rm((size_t)k * ov * 8, s);
     DevBuf a1(k * 8, s), a2(k * 8, s), om(k * 8, s);
-    apply_operator(dims, Fc, r.U.as<double>(), k, OpMode::PAIRED, PU.as<double>(), MU.as<double>(), false, s);
-    apply_operator(dims, Fc, r.W.as<double>(), k, OpMode::PAIRED, PW.as<double>(), MW.as<double>(), false, s);
+    apply_operator(dims, Fc, r.U.as<double>(), k, OpMode::PAIRED, PU.as<double>(), MU.as<double>(), cert_tc(c, p), s);
+    apply_operator(dims, Fc, r.W.as<double>(), k, OpMode::PAIRED, PW.as<double>(), MW.as<double>(), cert_tc(c, p), s);
     h2d(om.as<double>(), r.omega, s);
     resid_paired<double>(r.U.as<double>(), r.W.as<double>(), PU.as<double>(), MW.as<double>(), om.as<double>(),
                  nullptr, nullptr, k, ov, Rp.as<double>(), Rm.as<double>(), s);
@@ -1133,6 +1152,7 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     row_sumsq(Rm.as<double>(), ov, k, ov, a2.as<double>(), s);
     auto h1 = d2h(a1.as<double>(), k, s), h2 = d2h(a2.as<double>(), k, s);
     for (int j = 0; j < k; ++j) cert = std::max(cert, std::sqrt(h1[j] + h2[j]));
+    cnt.t_cert = since(tc0);
   }
   const bool dev = o.outputs_on_device != 0;
   if (omega) {

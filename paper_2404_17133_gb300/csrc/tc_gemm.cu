@@ -54,12 +54,18 @@ template <bool F8> struct Elem {
 // Operand split modes: SINGLE = one BF16 product; BOTH = A and B as hi + lo
 // (hi*hi + hi*lo + lo*hi); ASPLIT = A as hi + lo, B a plain BF16 operand
 // (hi*B + lo*B: exact with respect to B, e.g. FP32 vectors against BF16 ris factors).
-enum SplitMode : int { SINGLE = 0, BOTH = 1, ASPLIT = 2 };
+// CROSS = A and B as two parts each, only the two cross products A0 B1 + A1 B0
+// (one pass of the three-part split below); TRIPLE (stage 1 only) = A and B
+// as three BF16 parts x = x0 + x1 + x2 (24 significand bits), the six
+// products down to 2^-18 of the leading one: 00 + 01 + 10 + 02 + 20 + 11.
+enum SplitMode : int { SINGLE = 0, BOTH = 1, ASPLIT = 2, CROSS = 3, TRIPLE = 4 };
 __host__ __device__ constexpr bool a_split(int m) { return m != SINGLE; }
-__host__ __device__ constexpr bool b_split(int m) { return m == BOTH; }
+__host__ __device__ constexpr bool b_split(int m) { return m == BOTH || m == CROSS || m == TRIPLE; }
+__host__ __device__ constexpr int n_parts_a(int m) { return m == TRIPLE ? 3 : (a_split(m) ? 2 : 1); }
+__host__ __device__ constexpr int n_parts_b(int m) { return m == TRIPLE ? 3 : (b_split(m) ? 2 : 1); }
 
 template <int MODE> struct Cfg {
-  static constexpr int STAGE_BYTES = (a_split(MODE) ? 2 : 1) * A_BYTES + (b_split(MODE) ? 2 : 1) * B_BYTES;
+  static constexpr int STAGE_BYTES = n_parts_a(MODE) * A_BYTES + n_parts_b(MODE) * B_BYTES;
   static constexpr int STAGES = MODE == SINGLE ? 4 : (MODE == ASPLIT ? 3 : 2);   // ~192 KB ring
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 };
@@ -218,9 +224,14 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 32 bytes along K per MMA
-        mma_op<F8>(tmem, ah + off, bh + off, (i > 0 || kk > 0) ? 1u : 0u);
-        if (b_split(MODE)) mma_op<F8>(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, 1u);
-        if (a_split(MODE)) mma_op<F8>(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u);
+        if constexpr (MODE == CROSS) {
+          mma_op<F8>(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, (i > 0 || kk > 0) ? 1u : 0u);
+          mma_op<F8>(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u);
+        } else {
+          mma_op<F8>(tmem, ah + off, bh + off, (i > 0 || kk > 0) ? 1u : 0u);
+          if (b_split(MODE)) mma_op<F8>(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, 1u);
+          if (a_split(MODE)) mma_op<F8>(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u);
+        }
       }
       mma_commit(&empty[s]);
     }
@@ -296,6 +307,7 @@ struct S1Params {
   int stages, stage_bytes, a_bytes, b_bytes;
   __nv_bfloat16* out_hi;
   __nv_bfloat16* out_lo;
+  __nv_bfloat16* out_l2;   // TRIPLE: third part of the output split
   // FP8 output (OUT8): e4m3 hi + lo bytes of mu[P] * C_P, row pitch ldo bytes
   unsigned char* out8_hi;
   unsigned char* out8_lo;
@@ -314,6 +326,7 @@ template <int MODE, bool OUT8>
 __global__ void __launch_bounds__(S1_THREADS, 1)
 k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
             const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
+            const __grid_constant__ CUtensorMap mA_l2, const __grid_constant__ CUtensorMap mB_l2,
             S1Params p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -330,7 +343,7 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
   const int nP = max(0, min(p.pn, P0 + p.ppc) - P0);
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(p.nb >> 3) << 17) |
                          ((uint32_t)(BM >> 4) << 24);
-  const int b_off = a_split(MODE) ? 2 * p.a_bytes : p.a_bytes;
+  const int b_off = n_parts_a(MODE) * p.a_bytes;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -358,6 +371,10 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
       tma_load_3d(st + b_off, &mB_hi, &full[s], k0, 0, P);
       if (a_split(MODE)) tma_load_3d(st + p.a_bytes, &mA_lo, &full[s], k0, m0, 0);
       if (b_split(MODE)) tma_load_3d(st + b_off + p.b_bytes, &mB_lo, &full[s], k0, 0, P);
+      if (MODE == TRIPLE) {
+        tma_load_3d(st + 2 * p.a_bytes, &mA_l2, &full[s], k0, m0, 0);
+        tma_load_3d(st + b_off + 2 * p.b_bytes, &mB_l2, &full[s], k0, 0, P);
+      }
     }
     for (int i = max(0, nsteps - p.stages); i < nsteps; ++i)
       if (!mbar_wait(&full[i % p.stages], (uint32_t)(i / p.stages) & 1u)) { atomicOr(p.err, 32); break; }
@@ -395,6 +412,18 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
                 "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
                 "l"(al + off), "l"(bh + off), "r"(idesc), "r"(1u));
+          }
+          if (MODE == TRIPLE) {   // A0 B2 + A2 B0 + A1 B1
+            const uint64_t a2 = sdesc(st + 2 * p.a_bytes), b2 = sdesc(st + b_off + 2 * p.b_bytes);
+            const uint64_t a1 = sdesc(st + p.a_bytes), b1 = sdesc(st + b_off + p.b_bytes);
+            const uint64_t pa[3] = {ah + off, a2 + off, a1 + off};
+            const uint64_t pb[3] = {b2 + off, bh + off, b1 + off};
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+              asm volatile(
+                  "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
+                  "l"(pa[t]), "l"(pb[t]), "r"(idesc), "r"(1u));
           }
         }
         mma_commit(&empty[s]);
@@ -452,7 +481,12 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
                 const float x = __uint_as_float(v[t]);
                 const __nv_bfloat16 h = __float2bfloat16_rn(x);
                 oh[t * cs] = h;
-                if (a_split(MODE)) ol[t * cs] = __float2bfloat16_rn(x - __bfloat162float(h));
+                if (a_split(MODE)) {
+                  const float r1 = x - __bfloat162float(h);
+                  const __nv_bfloat16 l = __float2bfloat16_rn(r1);
+                  ol[t * cs] = l;
+                  if (MODE == TRIPLE) p.out_l2[base + t * cs] = __float2bfloat16_rn(r1 - __bfloat162float(l));
+                }
               }
             }
           }
@@ -511,9 +545,23 @@ __global__ void k_split_pad(const float* __restrict__ Z, int M, int pn, int nv, 
 
 // Transpose + split of factor rows: src [rows][n1][n2] -> dst [rows][n2][pad8(n1)]
 // (dst[r][b][a] = src[r][a][b]; pads zero).  lo may be NULL (plain BF16).
+// Split of x (converted to FP32) into BF16 parts: hi = bf16(x), lo = bf16(x - hi),
+// l2 = bf16(x - hi - lo) (lo, l2 optional).
+__device__ __forceinline__ void split_store(float v, long long t, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                            __nv_bfloat16* l2) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[t] = h;
+  if (lo) {
+    const float r1 = v - __bfloat162float(h);
+    const __nv_bfloat16 l = __float2bfloat16_rn(r1);
+    lo[t] = l;
+    if (l2) l2[t] = __float2bfloat16_rn(r1 - __bfloat162float(l));
+  }
+}
+
 template <typename TS>
 __global__ void k_transpose_split(const TS* __restrict__ src, int rows, int n1, int n2, int ld,
-                                  __nv_bfloat16* hi, __nv_bfloat16* lo) {
+                                  __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* l2) {
   const long long tot = (long long)rows * n2 * ld;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x) {
@@ -523,9 +571,7 @@ __global__ void k_transpose_split(const TS* __restrict__ src, int rows, int n1, 
     const long long r = rb / n2;
     float v = 0.f;
     if (a < n1) v = (float)src[(r * n1 + a) * n2 + b];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[t] = h;
-    if (lo) lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
+    split_store(v, t, hi, lo, l2);
   }
 }
 
@@ -577,18 +623,18 @@ void tc_split_pad(const float* Z, int M, int pn, int nv, __nv_bfloat16* hi, __nv
 }
 
 void tc_transpose_split(const void* src, DType ts, int rows, int n1, int n2, __nv_bfloat16* hi,
-                        __nv_bfloat16* lo, cudaStream_t s) {
+                        __nv_bfloat16* lo, cudaStream_t s, __nv_bfloat16* l2) {
   const int ld = tc_pad(n1);
   const long long tot = (long long)rows * n2 * ld;
   long long g = (tot + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
   if (ts == DType::F32)
-    k_transpose_split<float><<<(unsigned)g, 256, 0, s>>>((const float*)src, rows, n1, n2, ld, hi, lo);
+    k_transpose_split<float><<<(unsigned)g, 256, 0, s>>>((const float*)src, rows, n1, n2, ld, hi, lo, l2);
   else if (ts == DType::BF16)
     k_transpose_split<__nv_bfloat16><<<(unsigned)g, 256, 0, s>>>((const __nv_bfloat16*)src, rows, n1, n2,
-                                                                 ld, hi, lo);
+                                                                 ld, hi, lo, l2);
   else
-    k_transpose_split<double><<<(unsigned)g, 256, 0, s>>>((const double*)src, rows, n1, n2, ld, hi, lo);
+    k_transpose_split<double><<<(unsigned)g, 256, 0, s>>>((const double*)src, rows, n1, n2, ld, hi, lo, l2);
   count_launch();
   TD_LAUNCH_CHECK();
 }
@@ -634,10 +680,11 @@ int wave_splits(int tiles, int total, int overhead) {
 void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int pn, int Kin,
                  const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, float* out,
                  bool accumulate, int* err, cudaStream_t s, KernelProfile* prof, double prof_flops,
-                 double prof_bytes) {
+                 double prof_bytes, bool cross) {
   if (M <= 0 || pn <= 0 || N <= 0) return;
   TD_REQUIRE(Alo != nullptr || Blo == nullptr, TDDFT_ERR_ARG, "tc_contract: B split without A split");
-  const int mode = Alo ? (Blo ? BOTH : ASPLIT) : SINGLE;
+  TD_REQUIRE(!cross || (Alo && Blo), TDDFT_ERR_ARG, "tc_contract: cross products need both splits");
+  const int mode = cross ? CROSS : (Alo ? (Blo ? BOTH : ASPLIT) : SINGLE);
   const int ldk = tc_pad(Kin);
   const int nab = (Kin + BK - 1) / BK;
   const int total = pn * nab;
@@ -668,6 +715,7 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
     if (prof) prof->end(s, prof_flops, prof_bytes);
   };
   if (mode == BOTH) launch(k1_tc_kernel<BOTH, false>, Cfg<BOTH>::SMEM_BYTES);
+  else if (mode == CROSS) launch(k1_tc_kernel<CROSS, false>, Cfg<CROSS>::SMEM_BYTES);
   else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT, false>, Cfg<ASPLIT>::SMEM_BYTES);
   else launch(k1_tc_kernel<SINGLE, false>, Cfg<SINGLE>::SMEM_BYTES);
   count_launch();
@@ -717,23 +765,26 @@ void tc_contract8(const unsigned char* Ahi, const unsigned char* Alo, int M, int
 }
 
 namespace {
-void stage1_impl(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
-                 const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, int pn, int R,
-                 __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, unsigned char* out8_hi,
-                 unsigned char* out8_lo, const float* mu, int* err, cudaStream_t s) {
+void stage1_impl(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, const __nv_bfloat16* Al2, int M, int K,
+                 const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, const __nv_bfloat16* Bl2, int N, int pn,
+                 int R, __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, __nv_bfloat16* out_l2,
+                 unsigned char* out8_hi, unsigned char* out8_lo, const float* mu, int* err, cudaStream_t s) {
   if (M <= 0 || pn <= 0 || N <= 0) return;
   TD_REQUIRE(N <= 256, TDDFT_ERR_ARG, "tc_stage1: N above 256");
   TD_REQUIRE((Alo != nullptr || Blo == nullptr) &&
                  (out8_hi ? (out8_lo != nullptr && mu != nullptr) : (Alo != nullptr) == (out_lo != nullptr)),
              TDDFT_ERR_ARG, "tc_stage1: hi/lo operands mismatch");
-  const int mode = Alo ? (Blo ? BOTH : ASPLIT) : SINGLE;
+  const bool triple = Al2 != nullptr;
+  TD_REQUIRE(!triple || (Alo && Blo && Bl2 && out_lo && out_l2 && !out8_hi), TDDFT_ERR_ARG,
+             "tc_stage1: three-part split needs every part");
+  const int mode = triple ? TRIPLE : (Alo ? (Blo ? BOTH : ASPLIT) : SINGLE);
   const int ldk = tc_pad(K);
   const int nb = (N + 15) & ~15;
   int acc_cols = 32;
   while (acc_cols < nb) acc_cols *= 2;
   const int a_bytes = BM * BK * 2, b_bytes = nb * BK * 2;
-  const int stage_bytes = (a_split(mode) ? 2 : 1) * a_bytes + (b_split(mode) ? 2 : 1) * b_bytes;
-  int stages = (200 * 1024) / stage_bytes;
+  const int stage_bytes = n_parts_a(mode) * a_bytes + n_parts_b(mode) * b_bytes;
+  int stages = ((triple ? 220 : 200) * 1024) / stage_bytes;
   if (stages > 6) stages = 6;
   TD_REQUIRE(stages >= 2, TDDFT_ERR_ARG, "tc_stage1: tile too large");
   const int smem = stages * stage_bytes + 1024 + 256;
@@ -751,17 +802,20 @@ void stage1_impl(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
   CUtensorMap mAh = make_map(Ahi, dA, sA, bA), mBh = make_map(Bhi, dB, sB, bB);
   CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA) : mAh;
   CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB) : mBh;
+  CUtensorMap mA2 = triple ? make_map(Al2, dA, sA, bA) : mAh;
+  CUtensorMap mB2 = triple ? make_map(Bl2, dB, sB, bB) : mBh;
   S1Params p{M, N, R, out8_hi ? tc_pad16(R) : tc_pad(R), pn, ppc, (K + BK - 1) / BK, nb, acc_cols, stages,
-             stage_bytes, a_bytes, b_bytes, out_hi, out_lo, out8_hi, out8_lo, mu, err};
+             stage_bytes, a_bytes, b_bytes, out_hi, out_lo, out_l2, out8_hi, out8_lo, mu, err};
   dim3 grid(mt, groups, 1);
   auto launch = [&](auto kernel) {
     ensure_smem((const void*)kernel, smem);
-    kernel<<<grid, S1_THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
+    kernel<<<grid, S1_THREADS, smem, s>>>(mAh, mAl, mBh, mBl, mA2, mB2, p);
   };
   if (out8_hi) {
     TD_REQUIRE(mode == ASPLIT, TDDFT_ERR_ARG, "tc_stage1: FP8 output needs hi+lo A and a plain B");
     launch(k_stage1_tc<ASPLIT, true>);
-  } else if (mode == BOTH) launch(k_stage1_tc<BOTH, false>);
+  } else if (mode == TRIPLE) launch(k_stage1_tc<TRIPLE, false>);
+  else if (mode == BOTH) launch(k_stage1_tc<BOTH, false>);
   else if (mode == ASPLIT) launch(k_stage1_tc<ASPLIT, false>);
   else launch(k_stage1_tc<SINGLE, false>);
   count_launch();
@@ -772,40 +826,52 @@ void stage1_impl(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
 void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
                const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, int pn, int R,
                __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int* err, cudaStream_t s) {
-  stage1_impl(Ahi, Alo, M, K, Bhi, Blo, N, pn, R, out_hi, out_lo, nullptr, nullptr, nullptr, err, s);
+  stage1_impl(Ahi, Alo, nullptr, M, K, Bhi, Blo, nullptr, N, pn, R, out_hi, out_lo, nullptr, nullptr, nullptr,
+              nullptr, err, s);
+}
+
+void tc_stage1_3(const __nv_bfloat16* const A[3], int M, int K, const __nv_bfloat16* const B[3], int N, int pn,
+                 int R, __nv_bfloat16* const out[3], int* err, cudaStream_t s) {
+  stage1_impl(A[0], A[1], A[2], M, K, B[0], B[1], B[2], N, pn, R, out[0], out[1], out[2], nullptr, nullptr,
+              nullptr, err, s);
+}
+
+bool tc_stage1_3_fits(int N) {
+  const int nb = (N + 15) & ~15;
+  const int stage = 3 * BM * BK * 2 + 3 * nb * BK * 2;
+  return N <= 256 && (220 * 1024) / stage >= 2;
 }
 
 void tc_stage1_fp8(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K, const __nv_bfloat16* B,
                    int N, int pn, int R, const float* mu, unsigned char* out_hi, unsigned char* out_lo, int* err,
                    cudaStream_t s) {
-  stage1_impl(Ahi, Alo, M, K, B, nullptr, N, pn, R, nullptr, nullptr, out_hi, out_lo, mu, err, s);
+  stage1_impl(Ahi, Alo, nullptr, M, K, B, nullptr, nullptr, N, pn, R, nullptr, nullptr, nullptr, out_hi, out_lo,
+              mu, err, s);
 }
 
 // F64/F32 rows [rows][n] -> BF16 hi (+ lo) [rows][tc_pad(n)]
 template <typename TS>
 __global__ void k_pad_split(const TS* __restrict__ src, long long rows, int n, int ld,
-                            __nv_bfloat16* hi, __nv_bfloat16* lo) {
+                            __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* l2) {
   const long long tot = rows * ld;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x) {
     const int a = (int)(t % ld);
     const long long r = t / ld;
     const float v = a < n ? (float)src[r * n + a] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[t] = h;
-    if (lo) lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
+    split_store(v, t, hi, lo, l2);
   }
 }
 
 void tc_pad_split(const void* src, DType ts, long long rows, int n, __nv_bfloat16* hi,
-                  __nv_bfloat16* lo, cudaStream_t s) {
+                  __nv_bfloat16* lo, cudaStream_t s, __nv_bfloat16* l2) {
   const int ld = tc_pad(n);
   const long long tot = rows * ld;
   long long g = (tot + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
-  if (ts == DType::F64) k_pad_split<double><<<(unsigned)g, 256, 0, s>>>((const double*)src, rows, n, ld, hi, lo);
-  else if (ts == DType::F32) k_pad_split<float><<<(unsigned)g, 256, 0, s>>>((const float*)src, rows, n, ld, hi, lo);
-  else k_pad_split<__nv_bfloat16><<<(unsigned)g, 256, 0, s>>>((const __nv_bfloat16*)src, rows, n, ld, hi, lo);
+  if (ts == DType::F64) k_pad_split<double><<<(unsigned)g, 256, 0, s>>>((const double*)src, rows, n, ld, hi, lo, l2);
+  else if (ts == DType::F32) k_pad_split<float><<<(unsigned)g, 256, 0, s>>>((const float*)src, rows, n, ld, hi, lo, l2);
+  else k_pad_split<__nv_bfloat16><<<(unsigned)g, 256, 0, s>>>((const __nv_bfloat16*)src, rows, n, ld, hi, lo, l2);
   count_launch();
   TD_LAUNCH_CHECK();
 }

@@ -4,7 +4,9 @@ together through grouped launches and a captured operator graph.
   * every problem of a batch of small molecules drawn like the batched
     workload (n_occ ~ U{8..16} here so that dense LAPACK is quick, n_vir =
     n_occ x U{4..8}, exact n_aux = 5 n_mo, ris n_aux = 9 ceil(n_occ/2),
-    5-10 states; rid and diag preconditioners mixed) converges, and its
+    5-10 states, the coupling scaled by min(1, 12.5 / sqrt(n_occ n_vir)) as
+    in the served and batched streams; rid and diag preconditioners mixed)
+    converges, and its
     energies match the oracle's dense eigenvalues of A (Eq. TDA) within
     1e-5 Ha (the mixed tolerance: FP32 vectors and products);
   * a problem's results do not depend on what else is in the batch (every
@@ -17,7 +19,7 @@ import pytest
 
 from oracle import dense as D
 from oracle import operators as O
-from synth.generator import make_problem
+from synth.generator import default_amplitude, make_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +42,10 @@ def _problems(n, seed=2405):
         no = int(g.integers(8, 17))
         nv = no * int(g.integers(4, 9))
         ns = int(g.integers(5, 11))
-        p = make_problem(no, nv, 5 * (no + nv), 9 * ((no + 1) // 2), seeds=(5000 + 3 * i, 5001 + 3 * i, 5002 + 3 * i))
+        na = 5 * (no + nv)
+        amp = default_amplitude(na) * min(1.0, 12.5 / np.sqrt(no * nv))
+        p = make_problem(no, nv, na, 9 * ((no + 1) // 2), seeds=(5000 + 3 * i, 5001 + 3 * i, 5002 + 3 * i),
+                         amplitude=amp)
         out.append((p, ns))
     return out
 
@@ -89,6 +94,27 @@ def test_batch_result_independent_of_the_mix(api):
         # the same context twice in one batch: its factors are only read
         _, twice, _ = api.solve_tda_batch([solvers[1], solvers[1]], [opts[1], opts[1]])
         assert np.max(np.abs(twice[0]["omega"] - twice[1]["omega"])) <= 1e-12
+    finally:
+        for s in solvers:
+            s.close()
+
+
+def test_batch_tile_variants_give_the_same_bits(api, monkeypatch):
+    """Every grouped-GEMM tile variant (the autotune's choices) sums each
+    element in the same K order, so forcing each one gives identical results."""
+    probs = _problems(3, seed=91)
+    solvers = [api.Solver.from_problem(p, precisions=2, dtype=api.F32) for p, _ in probs]
+    try:
+        opts = [api.default_opts(n_states=ns, precond=api.RID, precision=api.MIXED) for _, ns in probs]
+        ref = None
+        for v in range(5):
+            monkeypatch.setenv("TDDFT_BATCH_VARIANT", str(v))
+            _, res, info = api.solve_tda_batch(solvers, opts)
+            assert info["variant"] == v
+            om = np.concatenate([r["omega"] for r in res])
+            if ref is None:
+                ref = om
+            assert np.array_equal(om, ref), v
     finally:
         for s in solvers:
             s.close()

@@ -6,6 +6,8 @@ Tolerances (see the design notes for the derivation):
   * ris products, MIXED (BF16 factors): 2e-2 relative (preconditioner only);
   * exact products, MIXED on the tensor cores (BF16 hi+lo, three products,
     FP32 accumulation): 5e-5 relative; ris products on the tensor cores: 2e-2;
+  * exact products in the re-certification's tensor-core form (three BF16
+    parts, six products, FP32 accumulation): 2e-5, as the FP32 SIMT products;
   * excitation energies: 1e-6 Ha (PLAIN), 1e-5 Ha (MIXED);
   * polarizabilities: 1e-6 relative (PLAIN), 1e-5 relative (MIXED), element
     by element with the floor of tests/parity.py.
@@ -90,6 +92,13 @@ def test_tensor_core_products(case, api):
         gp, gm = s.apply(1, X, precision=api.MIXED, tensor_cores=True)
         rp, rm = op.apb_amb(X)
         assert _rel(gp, rp) < 5e-5 and _rel(gm, rm) < 5e-5
+        # the re-certification's form: three BF16 parts per operand, six
+        # products, FP32 accumulation -- held to the FP32 SIMT products' 2e-5
+        e0 = _rel(s.apply(0, X, precision=api.MIXED, tensor_cores=3), op.tda(X))
+        cp, cm = s.apply(1, X, precision=api.MIXED, tensor_cores=3)
+        print("\n%s m=%d three-part tensor-core products: rel err %.2e (A), %.2e (A+B), %.2e (A-B)"
+              % (name, m, e0, _rel(cp, rp), _rel(cm, rm)))
+        assert e0 < 2e-5 and _rel(cp, rp) < 2e-5 and _rel(cm, rm) < 2e-5
         # ris operator on the tensor cores: one BF16 product (preconditioner only)
         T = O.ris_operator(p)
         assert _rel(s.apply(2, X, precision=api.MIXED, tensor_cores=True), T.tda(X)) < 2e-2
