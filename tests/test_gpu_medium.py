@@ -52,7 +52,7 @@ def test_sampled_products_full_size(setup):
     assert rel(gp, rp) < 5e-5 and rel(gm, rm) < 5e-5
     cp, cm = s.apply(1, X, precision=api.MIXED, tensor_cores=3)   # the re-certification's form
     print("\nmedium three-part tensor-core pair products: rel err %.2e, %.2e" % (rel(cp, rp), rel(cm, rm)))
-    assert rel(cp, rp) < 2e-5 and rel(cm, rm) < 2e-5
+    assert rel(cp, rp) < 2e-6 and rel(cm, rm) < 2e-6
 
 
 def test_rpa_full_size(setup):
