@@ -90,10 +90,14 @@ KernelProfile::~KernelProfile() {
 }
 
 namespace {
+// Exchange intermediates of one P-chunk: SIMT contractions keep them within
+// 512 MB; the tensor-core path takes 4 GB, so that a contraction launch covers
+// many auxiliary rows (longer K loops per CTA, fewer launches and pipeline fills).
 constexpr size_t kChunkBytes = 512ull << 20;
+constexpr size_t kChunkBytesTC = 4ull << 30;
 
-int chunk_rows(int nrows, long long per_row_bytes, int m) {
-  long long pc = (long long)(kChunkBytes / (per_row_bytes > 0 ? per_row_bytes : 1));
+int chunk_rows(int nrows, long long per_row_bytes, int m, size_t budget = kChunkBytes) {
+  long long pc = (long long)(budget / (per_row_bytes > 0 ? per_row_bytes : 1));
   if (pc < 1) pc = 1;
   if (pc > nrows) pc = nrows;
   long long bmax = 65535 / (m > 0 ? m : 1);
@@ -169,7 +173,8 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
     const bool tc3 = use_tc && tc == 2 && f.Kvv_l2 && f.Kvo_l2 && f.Koo_l2 && f.Kovp_l2 && f.Kvv_lo &&
                      tc_stage1_3_fits(no);
     // three-part intermediates take half as much again as hi + lo ones
-    const int pc = chunk_rows(f.nK, (long long)m * ov * (long long)ew * (tc3 ? 3 : 2) / 2, m);
+    const int pc = chunk_rows(f.nK, (long long)m * ov * (long long)ew * (tc3 ? 3 : 2) / 2, m,
+                              use_tc ? kChunkBytesTC : kChunkBytes);
     const size_t es = dtype_size(f.dt);
     if (tc3) {
       // FP32-accurate products on the tensor cores: every operand (trial
