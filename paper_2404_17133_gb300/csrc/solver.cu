@@ -266,11 +266,18 @@ struct TdaOut {
   DevBuf X;     // [k][ov] Ritz vectors
   int n_iter = 0;
   bool converged = false;
+  double cert = -1.0;   // largest re-certified residual (when a gate was given)
 };
+
+// Re-certification gate: residual norms of the k Ritz pairs recomputed with an
+// FP32-accurate operator (TDA: X [k][ov], omega; Casida: U, W, Omega).
+using TdaCert = std::function<std::vector<double>(const double* X, const std::vector<double>& om, int k)>;
+using RpaCert = std::function<std::vector<double>(const double* U, const double* W, const std::vector<double>& om,
+                                                  int k)>;
 
 TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, int ng, int k,
                     double tol, int max_iter, int cap, int rounds, Counters& cnt, bool exact_op,
-                    cudaStream_t s) {
+                    cudaStream_t s, const TdaCert* cert = nullptr) {
   TdaOut o;
   if (!exact_op) ++g_inner;
   struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
@@ -301,6 +308,7 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
   int n_proj = 0;   // leading vectors whose projections are already in `a`
   std::vector<double> om(k), rr(k);
   int kk = std::min(k, N);
+  double tol_loop = tol;
   for (int it = 1; it <= max_iter; ++it) {
     o.n_iter = it;
     {
@@ -331,8 +339,21 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
     trace(exact_op ? "tda" : "tda-guess", it, N, om, rr);
     std::vector<int> todo;
     for (int j = 0; j < kk; ++j)
-      if (!(rr[j] < tol)) todo.push_back(j);
-    if (todo.empty() && kk == k) { o.converged = true; break; }
+      if (!(rr[j] < tol_loop)) todo.push_back(j);
+    if (todo.empty() && kk == k) {
+      if (!cert) { o.converged = true; break; }
+      // the gate: converged only when the re-certified residuals are below tol;
+      // otherwise the products' rounding hid the rest, so the loop continues
+      // with a tighter threshold on the roots that failed
+      const std::vector<double> cr = (*cert)(X.as<double>(), om, kk);
+      o.cert = 0.0;
+      for (int j = 0; j < kk; ++j) {
+        o.cert = std::max(o.cert, cr[j]);
+        if (!(cr[j] < tol)) todo.push_back(j);
+      }
+      if (todo.empty()) { o.converged = true; break; }
+      tol_loop *= 0.5;
+    }
     if (it == max_iter) break;
     const int nu = (int)todo.size();
     std::vector<double> omh(nu);
@@ -671,11 +692,12 @@ struct RpaOut {
   DevBuf U, W;
   int n_iter = 0;
   bool converged = false;
+  double cert = -1.0;
 };
 
 RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess, int ng, int k,
                     double tol, int max_iter, int cap, int rounds, Counters& cnt, bool exact_op,
-                    cudaStream_t s) {
+                    cudaStream_t s, const RpaCert* cert = nullptr) {
   RpaOut o;
   if (!exact_op) ++g_inner;
   struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
@@ -708,6 +730,7 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
   sp.n_new = sp.N;
   std::vector<double> om(k), rr(k);
   int kk = k;
+  double tol_loop = tol;
   for (int it = 1; it <= max_iter; ++it) {
     o.n_iter = it;
     sp.update(true);
@@ -749,11 +772,21 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
     std::vector<int> todo;
     for (int j = 0; j < kk; ++j) {
       rr[j] = std::sqrt(a1[j] + a2[j]);
-      if (!(rr[j] < tol)) todo.push_back(j);
+      if (!(rr[j] < tol_loop)) todo.push_back(j);
     }
     check_finite_host(rr, "Casida residual norms");
     trace(exact_op ? "rpa" : "rpa-guess", it, N, om, rr);
-    if (todo.empty() && kk == k) { o.converged = true; break; }
+    if (todo.empty() && kk == k) {
+      if (!cert) { o.converged = true; break; }
+      const std::vector<double> cr = (*cert)(U.as<double>(), W.as<double>(), om, kk);
+      o.cert = 0.0;
+      for (int j = 0; j < kk; ++j) {
+        o.cert = std::max(o.cert, cr[j]);
+        if (!(cr[j] < tol)) todo.push_back(j);
+      }
+      if (todo.empty()) { o.converged = true; break; }
+      tol_loop *= 0.5;
+    }
     if (it == max_iter) break;
     const int nu = (int)todo.size();
     std::vector<double> shh(nu);
@@ -1014,23 +1047,27 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     guess = DevBuf((size_t)p.k0 * ov * 8, s);
     unit_rows(guess.as<double>(), p.k0, ov, c.order.as<int>(), s);
   }
-  TdaOut r = davidson_tda(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, guess.as<double>(), ng,
-                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s);
-  double cert = -1.0;
-  if (p.mixed) {
-    // re-check the converged residuals with an FP32-accurate operator: the
-    // three-part BF16 tensor-core products when the solve ran on the tensor
-    // cores, else the FP32 SIMT contractions
+  // MIXED: the converged residuals are re-checked with an FP32-accurate
+  // operator (the three-part BF16 tensor-core products after a tensor-core
+  // solve, else the FP32 SIMT contractions); the solve converges only when they
+  // are below tol
+  const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 factors and their three-part BF16 split
+  TdaCert certify = [&](const double* Xc, const std::vector<double>& omv, int k) {
     auto tc0 = Clock::now();
-    const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 factors and their three-part BF16 split
-    DevBuf AX((size_t)p.k * ov * 8, s), R((size_t)p.k * ov * 8, s), rn(p.k * 8, s), om(p.k * 8, s);
-    apply_operator(dims, Fc, r.X.as<double>(), p.k, OpMode::TDA, AX.as<double>(), nullptr, cert_tc(c, p), s);
-    h2d(om.as<double>(), r.omega, s);
-    resid_tda(r.X.as<double>(), AX.as<double>(), om.as<double>(), p.k, ov, R.as<double>(), s);
-    row_sumsq(R.as<double>(), ov, p.k, ov, rn.as<double>(), s);
-    for (double v : sqrt_all(d2h(rn.as<double>(), p.k, s))) cert = std::max(cert, v);
-    cnt.t_cert = since(tc0);
-  }
+    DevBuf AX((size_t)k * ov * 8, s), R((size_t)k * ov * 8, s), rn(k * 8, s), om(k * 8, s);
+    apply_operator(dims, Fc, Xc, k, OpMode::TDA, AX.as<double>(), nullptr, cert_tc(c, p), s);
+    h2d(om.as<double>(), std::vector<double>(omv.begin(), omv.begin() + k), s);
+    resid_tda(Xc, AX.as<double>(), om.as<double>(), k, ov, R.as<double>(), s);
+    row_sumsq(R.as<double>(), ov, k, ov, rn.as<double>(), s);
+    std::vector<double> v = sqrt_all(d2h(rn.as<double>(), k, s));
+    cnt.t_cert += since(tc0);
+    return v;
+  };
+  TdaOut r = davidson_tda(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, guess.as<double>(), ng,
+                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s, p.mixed ? &certify : nullptr);
+  double cert = r.cert;
+  if (p.mixed && cert < 0.0)   // not converged: report the re-checked residuals of the last Ritz pairs
+    for (double v : certify(r.X.as<double>(), r.omega, (int)r.omega.size())) cert = std::max(cert, v);
   const bool dev = o.outputs_on_device != 0;
   if (omega) {
     if (dev) { DevBuf t(p.k * 8, s); h2d(t.as<double>(), r.omega, s); copy_out(omega, t.as<double>(), p.k, true, s); TD_CUDA(cudaStreamSynchronize(s)); }
@@ -1133,27 +1170,30 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     guess = DevBuf((size_t)p.k0 * ov * 8, s);
     unit_rows(guess.as<double>(), p.k0, ov, c.order.as<int>(), s);
   }
-  RpaOut r = davidson_rpa(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, guess.as<double>(), ng,
-                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s);
-  double cert = -1.0;
-  if (p.mixed) {
+  const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 factors and their three-part BF16 split
+  RpaCert certify = [&](const double* Uc, const double* Wc, const std::vector<double>& omv, int k) {
     auto tc0 = Clock::now();
-    const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 factors and their three-part BF16 split
-    const int k = p.k;
     DevBuf PU((size_t)k * ov * 8, s), MU((size_t)k * ov * 8, s), PW((size_t)k * ov * 8, s),
         MW((size_t)k * ov * 8, s), Rp((size_t)k * ov * 8, s), Rm((size_t)k * ov * 8, s);
     DevBuf a1(k * 8, s), a2(k * 8, s), om(k * 8, s);
-    apply_operator(dims, Fc, r.U.as<double>(), k, OpMode::PAIRED, PU.as<double>(), MU.as<double>(), cert_tc(c, p), s);
-    apply_operator(dims, Fc, r.W.as<double>(), k, OpMode::PAIRED, PW.as<double>(), MW.as<double>(), cert_tc(c, p), s);
-    h2d(om.as<double>(), r.omega, s);
-    resid_paired<double>(r.U.as<double>(), r.W.as<double>(), PU.as<double>(), MW.as<double>(), om.as<double>(),
-                 nullptr, nullptr, k, ov, Rp.as<double>(), Rm.as<double>(), s);
+    apply_operator(dims, Fc, Uc, k, OpMode::PAIRED, PU.as<double>(), MU.as<double>(), cert_tc(c, p), s);
+    apply_operator(dims, Fc, Wc, k, OpMode::PAIRED, PW.as<double>(), MW.as<double>(), cert_tc(c, p), s);
+    h2d(om.as<double>(), std::vector<double>(omv.begin(), omv.begin() + k), s);
+    resid_paired<double>(Uc, Wc, PU.as<double>(), MW.as<double>(), om.as<double>(), nullptr, nullptr, k, ov,
+                         Rp.as<double>(), Rm.as<double>(), s);
     row_sumsq(Rp.as<double>(), ov, k, ov, a1.as<double>(), s);
     row_sumsq(Rm.as<double>(), ov, k, ov, a2.as<double>(), s);
     auto h1 = d2h(a1.as<double>(), k, s), h2 = d2h(a2.as<double>(), k, s);
-    for (int j = 0; j < k; ++j) cert = std::max(cert, std::sqrt(h1[j] + h2[j]));
-    cnt.t_cert = since(tc0);
-  }
+    std::vector<double> v(k);
+    for (int j = 0; j < k; ++j) v[j] = std::sqrt(h1[j] + h2[j]);
+    cnt.t_cert += since(tc0);
+    return v;
+  };
+  RpaOut r = davidson_rpa(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, guess.as<double>(), ng,
+                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s, p.mixed ? &certify : nullptr);
+  double cert = r.cert;
+  if (p.mixed && cert < 0.0)
+    for (double v : certify(r.U.as<double>(), r.W.as<double>(), r.omega, (int)r.omega.size())) cert = std::max(cert, v);
   const bool dev = o.outputs_on_device != 0;
   if (omega) {
     if (dev) { DevBuf t(p.k * 8, s); h2d(t.as<double>(), r.omega, s); copy_out(omega, t.as<double>(), p.k, true, s); TD_CUDA(cudaStreamSynchronize(s)); }
