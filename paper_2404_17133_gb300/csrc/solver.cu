@@ -269,15 +269,25 @@ struct TdaOut {
   double cert = -1.0;   // largest re-certified residual (when a gate was given)
 };
 
+// Iterations the loop gets to reach its tightened threshold after a failed
+// gate before it moves to the accurate operator.
+constexpr int kGateWait = 4;
+
 // Re-certification gate: residual norms of the k Ritz pairs recomputed with an
 // FP32-accurate operator (TDA: X [k][ov], omega; Casida: U, W, Omega).
 using TdaCert = std::function<std::vector<double>(const double* X, const std::vector<double>& om, int k)>;
 using RpaCert = std::function<std::vector<double>(const double* U, const double* W, const std::vector<double>& om,
                                                   int k)>;
 
+// With a gate: when the re-certified residuals stay above tol although the
+// loop's are below it, the loop's threshold is halved once; if the gate fails
+// again, or the gap between the two residuals alone is half of tol (the
+// products' rounding is then too large for any threshold), the loop restarts
+// from its Ritz vectors on the FP32-accurate operator `acc`, whose residuals
+// are the certified ones.
 TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, int ng, int k,
                     double tol, int max_iter, int cap, int rounds, Counters& cnt, bool exact_op,
-                    cudaStream_t s, const TdaCert* cert = nullptr) {
+                    cudaStream_t s, const TdaCert* cert = nullptr, const TdaOp* acc = nullptr) {
   TdaOut o;
   if (!exact_op) ++g_inner;
   struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
@@ -294,13 +304,17 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
   bool have_prev = false;
   double* Vp = V.as<double>();
   double* Wp = W.as<double>();
+  const TdaOp* op = &A;
+  bool escalated = false;
+  int gate_fails = 0, it_fail = 0;
+  bool escalate_now = false;
 
   int N = orth_append(Vp, 0, guess, std::min(ng, cap), ov, s);
   TD_REQUIRE(N >= 1, TDDFT_ERR_ARG, "initial guess is empty");
   auto mv = [&](int r0, int m) {
     auto t0 = Clock::now();
     ScopedPhase ph(exact_op ? PH_MV : PH_RIS, s);
-    A(Vp + (size_t)r0 * ov, m, Wp + (size_t)r0 * ov);
+    (*op)(Vp + (size_t)r0 * ov, m, Wp + (size_t)r0 * ov);
     TD_CUDA(cudaStreamSynchronize(s));
     if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
   };
@@ -340,18 +354,42 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
     std::vector<int> todo;
     for (int j = 0; j < kk; ++j)
       if (!(rr[j] < tol_loop)) todo.push_back(j);
-    if (todo.empty() && kk == k) {
-      if (!cert) { o.converged = true; break; }
+    if (acc && gate_fails > 0 && !escalated && it - it_fail >= kGateWait && !(todo.empty() && kk == k))
+      escalate_now = true;   // the tightened threshold was not reached in time
+    if (escalate_now || (todo.empty() && kk == k)) {
+      if (escalated) {   // the loop's products are the certifying operator's
+        o.cert = 0.0;
+        for (int j = 0; j < kk; ++j) o.cert = std::max(o.cert, rr[j]);
+      }
+      if (!escalate_now && (!cert || escalated)) { o.converged = true; break; }
       // the gate: converged only when the re-certified residuals are below tol;
       // otherwise the products' rounding hid the rest, so the loop continues
       // with a tighter threshold on the roots that failed
-      const std::vector<double> cr = (*cert)(X.as<double>(), om, kk);
-      o.cert = 0.0;
-      for (int j = 0; j < kk; ++j) {
-        o.cert = std::max(o.cert, cr[j]);
-        if (!(cr[j] < tol)) todo.push_back(j);
+      double gap = 0.0;
+      if (!escalate_now) {
+        const std::vector<double> cr = (*cert)(X.as<double>(), om, kk);
+        o.cert = 0.0;
+        for (int j = 0; j < kk; ++j) {
+          o.cert = std::max(o.cert, cr[j]);
+          if (!(cr[j] < tol)) { todo.push_back(j); gap = std::max(gap, cr[j] - rr[j]); }
+        }
+        if (todo.empty()) { o.converged = true; break; }
+        it_fail = it;
       }
-      if (todo.empty()) { o.converged = true; break; }
+      if (acc && (escalate_now || ++gate_fails > 1 || !(gap < 0.5 * tol))) {
+        escalate_now = false;
+        // restart from the Ritz vectors on the accurate operator
+        op = acc;
+        escalated = true;
+        tol_loop = tol;
+        TD_CUDA(cudaMemcpyAsync(tmpk.p, X.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
+        N = orth_append(Vp, 0, tmpk.as<double>(), kk, ov, s);
+        mv(0, N);
+        n_proj = 0;
+        have_prev = false;
+        cnt.restarts++;
+        continue;
+      }
       tol_loop *= 0.5;
     }
     if (it == max_iter) break;
@@ -482,7 +520,13 @@ struct PairedLinOut {
   int n_iter = 0;
   bool converged = false;
   std::vector<double> resid;
+  double cert = -1.0;   // largest re-certified relative residual (when a gate was given)
 };
+
+// Re-certification gate of the paired linear systems: the relative residuals
+// of the nr solutions (U, W) recomputed with the FP32-accurate operator.
+template <typename T>
+using LinCert = std::function<std::vector<double>(const T* U, const T* W)>;
 
 // The small shifted systems are solved by LU per shift in the vectors' type:
 // FP64 for the outer polarizability and PLAIN solves, FP32 for the MIXED inner
@@ -491,8 +535,14 @@ template <typename T, typename S = T>
 PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre, const T* gp,
                            const T* gm, const std::vector<double>& shifts, int nr, T* init, int ni,
                            double tol, int max_iter, int cap, bool exact_op,
-                           Counters& cnt, T* Uout, T* Wout, cudaStream_t s) {
+                           Counters& cnt, T* Uout, T* Wout, cudaStream_t s,
+                           const LinCert<T>* cert = nullptr, const PairOpT<T>* acc = nullptr) {
   PairedLinOut o;
+  const PairOpT<T>* opp = &op;
+  bool escalated = false;
+  int gate_fails = 0, it_fail = 0;
+  bool escalate_now = false;
+  double tol_loop = tol;
   if (!exact_op) ++g_inner;
   struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
   cap = std::min(cap, kSmallMax);
@@ -546,7 +596,7 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
   auto mv = [&](int r0, int m) {
     auto t0 = Clock::now();
     ScopedPhase ph(exact_op ? PH_MV : PH_RIS, s);
-    op(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
+    (*opp)(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
     if (exact_op) {
       TD_CUDA(cudaStreamSynchronize(s));
       cnt.mv += m;
@@ -623,11 +673,49 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
     std::vector<int> todo;
     for (int r = 0; r < nr; ++r) {
       rr[r] = std::sqrt(a1[r] + a2[r]) / (gnh[r] > 0 ? gnh[r] : 1.0);
-      if (!(rr[r] <= tol)) todo.push_back(r);
+      if (!(rr[r] <= tol_loop)) todo.push_back(r);
     }
     check_finite_host(rr, "linear-system residuals");
     if (exact_op) trace("polar", it, sp.N, std::vector<double>(), rr);
-    if (todo.empty()) { o.converged = true; break; }
+    if (acc && gate_fails > 0 && !escalated && it - it_fail >= kGateWait && !todo.empty())
+      escalate_now = true;
+    if (escalate_now || todo.empty()) {
+      if (escalated) {   // the loop's products are the certifying operator's
+        o.cert = 0.0;
+        for (int r = 0; r < nr; ++r) o.cert = std::max(o.cert, rr[r]);
+      }
+      if (!escalate_now && (!cert || escalated)) { o.converged = true; break; }
+      // the gate and the escalation of davidson_tda
+      double gap = 0.0;
+      if (!escalate_now) {
+        const std::vector<double> cr = (*cert)(Uout, Wout);
+        o.cert = 0.0;
+        for (int r = 0; r < nr; ++r) {
+          o.cert = std::max(o.cert, cr[r]);
+          if (!(cr[r] <= tol)) { todo.push_back(r); gap = std::max(gap, cr[r] - rr[r]); }
+        }
+        if (todo.empty()) { o.converged = true; break; }
+        it_fail = it;
+      }
+      if (acc && (escalate_now || ++gate_fails > 1 || !(gap < 0.5 * tol))) {
+        escalate_now = false;
+        opp = acc;
+        escalated = true;
+        tol_loop = tol;
+        DevBuf rst((size_t)2 * nr * ov * es, s);
+        TD_CUDA(cudaMemcpyAsync(rst.p, Uout, (size_t)nr * ov * es, cudaMemcpyDeviceToDevice, s));
+        TD_CUDA(cudaMemcpyAsync(rst.as<T>() + (size_t)nr * ov, Wout, (size_t)nr * ov * es,
+                                cudaMemcpyDeviceToDevice, s));
+        sp.N = orth_append<T>(sp.v(), 0, rst.as<T>(), 2 * nr, ov, s);
+        mv(0, sp.N);
+        sp.n_old = 0;
+        sp.n_new = sp.N;
+        have_prev = false;
+        cnt.restarts++;
+        continue;
+      }
+      tol_loop *= 0.5;
+    }
     if (it == max_iter) break;
     const int nu = (int)todo.size();
     if (dev_select) {
@@ -695,9 +783,11 @@ struct RpaOut {
   double cert = -1.0;
 };
 
-RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess, int ng, int k,
+// The gate and the escalation to `acc` as in davidson_tda (the restart basis
+// is X+Y and X-Y of the wanted roots).
+RpaOut davidson_rpa(int ov, const PairOp& op0, const PairPre& pre, double* guess, int ng, int k,
                     double tol, int max_iter, int cap, int rounds, Counters& cnt, bool exact_op,
-                    cudaStream_t s, const RpaCert* cert = nullptr) {
+                    cudaStream_t s, const RpaCert* cert = nullptr, const PairOp* acc = nullptr) {
   RpaOut o;
   if (!exact_op) ++g_inner;
   struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
@@ -715,13 +805,17 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
   DevBuf gpu_((size_t)k * ov * 8, s), gmu((size_t)k * ov * 8, s), cand((size_t)2 * k * ov * 8, s);
   DevBuf rst((size_t)4 * k * ov * 8, s), Uprev((size_t)k * ov * 8, s), Wprev((size_t)k * ov * 8, s);
   bool have_prev = false;
+  const PairOp* op = &op0;
+  bool escalated = false;
+  int gate_fails = 0, it_fail = 0;
+  bool escalate_now = false;
 
   sp.N = orth_append(sp.v(), 0, guess, std::min(ng, cap), ov, s);
   TD_REQUIRE(sp.N >= 1, TDDFT_ERR_ARG, "initial guess is empty");
   auto mv = [&](int r0, int m) {
     auto t0 = Clock::now();
     ScopedPhase ph(exact_op ? PH_MV : PH_RIS, s);
-    op(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
+    (*op)(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
     TD_CUDA(cudaStreamSynchronize(s));
     if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
   };
@@ -776,15 +870,41 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
     }
     check_finite_host(rr, "Casida residual norms");
     trace(exact_op ? "rpa" : "rpa-guess", it, N, om, rr);
-    if (todo.empty() && kk == k) {
-      if (!cert) { o.converged = true; break; }
-      const std::vector<double> cr = (*cert)(U.as<double>(), W.as<double>(), om, kk);
-      o.cert = 0.0;
-      for (int j = 0; j < kk; ++j) {
-        o.cert = std::max(o.cert, cr[j]);
-        if (!(cr[j] < tol)) todo.push_back(j);
+    if (acc && gate_fails > 0 && !escalated && it - it_fail >= kGateWait && !(todo.empty() && kk == k))
+      escalate_now = true;
+    if (escalate_now || (todo.empty() && kk == k)) {
+      if (escalated) {
+        o.cert = 0.0;
+        for (int j = 0; j < kk; ++j) o.cert = std::max(o.cert, rr[j]);
       }
-      if (todo.empty()) { o.converged = true; break; }
+      if (!escalate_now && (!cert || escalated)) { o.converged = true; break; }
+      double gap = 0.0;
+      if (!escalate_now) {
+        const std::vector<double> cr = (*cert)(U.as<double>(), W.as<double>(), om, kk);
+        o.cert = 0.0;
+        for (int j = 0; j < kk; ++j) {
+          o.cert = std::max(o.cert, cr[j]);
+          if (!(cr[j] < tol)) { todo.push_back(j); gap = std::max(gap, cr[j] - rr[j]); }
+        }
+        if (todo.empty()) { o.converged = true; break; }
+        it_fail = it;
+      }
+      if (acc && (escalate_now || ++gate_fails > 1 || !(gap < 0.5 * tol))) {
+        escalate_now = false;
+        op = acc;
+        escalated = true;
+        tol_loop = tol;
+        TD_CUDA(cudaMemcpyAsync(rst.p, U.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
+        TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)kk * ov, W.p, (size_t)kk * ov * 8,
+                                cudaMemcpyDeviceToDevice, s));
+        sp.N = orth_append(sp.v(), 0, rst.as<double>(), 2 * kk, ov, s);
+        mv(0, sp.N);
+        sp.n_old = 0;
+        sp.n_new = sp.N;
+        have_prev = false;
+        cnt.restarts++;
+        continue;
+      }
       tol_loop *= 0.5;
     }
     if (it == max_iter) break;
@@ -1063,8 +1183,12 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     cnt.t_cert += since(tc0);
     return v;
   };
+  TdaOp Acc = [&](const double* Xi, int m, double* out) {
+    apply_operator(dims, Fc, Xi, m, OpMode::TDA, out, nullptr, cert_tc(c, p), s);
+  };
   TdaOut r = davidson_tda(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, guess.as<double>(), ng,
-                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s, p.mixed ? &certify : nullptr);
+                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s, p.mixed ? &certify : nullptr,
+                          p.mixed ? &Acc : nullptr);
   double cert = r.cert;
   if (p.mixed && cert < 0.0)   // not converged: report the re-checked residuals of the last Ritz pairs
     for (double v : certify(r.X.as<double>(), r.omega, (int)r.omega.size())) cert = std::max(cert, v);
@@ -1189,8 +1313,12 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     cnt.t_cert += since(tc0);
     return v;
   };
+  PairOp Acc = [&](const double* Xi, int m, double* P, double* M) {
+    apply_operator(dims, Fc, Xi, m, OpMode::PAIRED, P, M, cert_tc(c, p), s);
+  };
   RpaOut r = davidson_rpa(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, guess.as<double>(), ng,
-                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s, p.mixed ? &certify : nullptr);
+                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s, p.mixed ? &certify : nullptr,
+                          p.mixed ? &Acc : nullptr);
   double cert = r.cert;
   if (p.mixed && cert < 0.0)
     for (double v : certify(r.U.as<double>(), r.W.as<double>(), r.omega, (int)r.omega.size())) cert = std::max(cert, v);
@@ -1289,9 +1417,39 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
     precond_paired<double>(b.as<double>(), nullptr, shd.as<double>(), dl, nr, ov, iu, iw, s);
   }
   DevBuf U((size_t)nr * ov * 8, s), W((size_t)nr * ov * 8, s);
+  // MIXED: the converged residuals are re-checked with the FP32-accurate
+  // operator, as in run_tda
+  const FactorSet Fc = c.exact(TDDFT_MIXED);
+  PairOp Acc = [&](const double* Xi, int m, double* P, double* M) {
+    apply_operator(dims, Fc, Xi, m, OpMode::PAIRED, P, M, cert_tc(c, p), s);
+  };
+  DevBuf rhs_norm(nr * 8, s);
+  row_sumsq(b.as<double>(), ov, nr, ov, rhs_norm.as<double>(), s);
+  const std::vector<double> bn = sqrt_all(d2h(rhs_norm.as<double>(), nr, s));
+  LinCert<double> certify = [&](const double* Uc, const double* Wc) {
+    auto tc0 = Clock::now();
+    DevBuf PU((size_t)nr * ov * 8, s), MU((size_t)nr * ov * 8, s), PW((size_t)nr * ov * 8, s),
+        MW((size_t)nr * ov * 8, s), Rp((size_t)nr * ov * 8, s), Rm((size_t)nr * ov * 8, s);
+    DevBuf a1(nr * 8, s), a2(nr * 8, s);
+    Acc(Uc, nr, PU.as<double>(), MU.as<double>());
+    Acc(Wc, nr, PW.as<double>(), MW.as<double>());
+    resid_paired<double>(Uc, Wc, PU.as<double>(), MW.as<double>(), shd.as<double>(), b.as<double>(), nullptr, nr,
+                         ov, Rp.as<double>(), Rm.as<double>(), s);
+    row_sumsq(Rp.as<double>(), ov, nr, ov, a1.as<double>(), s);
+    row_sumsq(Rm.as<double>(), ov, nr, ov, a2.as<double>(), s);
+    auto h1 = d2h(a1.as<double>(), nr, s), h2 = d2h(a2.as<double>(), nr, s);
+    std::vector<double> v(nr);
+    for (int j = 0; j < nr; ++j) v[j] = std::sqrt(h1[j] + h2[j]) / (bn[j] > 0 ? bn[j] : 1.0);
+    cnt.t_cert += since(tc0);
+    return v;
+  };
   PairedLinOut r = paired_linear<double>(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag,
                                          b.as<double>(), nullptr, sh, nr, iu, 2 * nr, p.tol, p.max_iter,
-                                         p.cap, true, cnt, U.as<double>(), W.as<double>(), s);
+                                         p.cap, true, cnt, U.as<double>(), W.as<double>(), s,
+                                         p.mixed ? &certify : nullptr, p.mixed ? &Acc : nullptr);
+  double cert = r.cert;
+  if (p.mixed && cert < 0.0)
+    for (double v : certify(U.as<double>(), W.as<double>())) cert = std::max(cert, v);
   // alpha[f][v][u] = mu_v . U[f*n_dip + u]
   DevBuf G((size_t)n_dip * nr * 8, s);
   gram(mud.as<double>(), n_dip, U.as<double>(), nr, ov, G.as<double>(), nr, s);
@@ -1307,7 +1465,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
   TD_CUDA(cudaStreamSynchronize(s));
   check_tc_error(c);
   phase_report("solve");
-  fill_stats(st, r.n_iter, cnt, r.converged, r.resid, -1.0, t0);
+  fill_stats(st, r.n_iter, cnt, r.converged, r.resid, cert, t0);
   return r.converged ? TDDFT_OK : TDDFT_ERR_NOCONV;
 }
 

@@ -27,6 +27,7 @@
 // Every wait on an mbarrier is bounded: on timeout the thread records an error
 // code in `err` and leaves the loop; the host turns it into TDDFT_ERR_CUDA.
 #include <algorithm>
+#include <cstdlib>
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -150,13 +151,48 @@ __device__ __forceinline__ void mma_op(uint32_t tmem, uint64_t a, uint64_t b, ui
   }
 }
 
+// TMA load into the same shared-memory offset of every CTA in `mask` of the
+// cluster, signalling each one's mbarrier at the same offset.
+__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                               int c2, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
+      : "memory");
+}
+
+// Arrive on the mbarrier at this offset in every CTA of `mask` when the MMAs
+// issued so far have completed.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))
                : "memory");
 }
 
-template <int MODE, bool F8>
+// CL = 2: the CTAs run in clusters of two along the M tiles; both need the same
+// B tile, so each loads half of its rows and multicasts them to both (halving
+// each SM's B traffic), and a stage is refilled only after both CTAs' MMAs
+// have read it (their commits arrive on both CTAs' `empty` barriers).
+template <int MODE, bool F8, int CL = 1>
 __global__ void __launch_bounds__(THREADS, 1)
 k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
              const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
@@ -178,8 +214,9 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
   const int k_end = min(p.total, k_begin + p.per_split);
   const int nk = max(0, k_end - k_begin);
 
+  const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], CL); }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -189,6 +226,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   __syncthreads();
+  if constexpr (CL > 1) cluster_sync_all();   // every barrier of the cluster initialised
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
@@ -204,13 +242,27 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       unsigned char* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
       tma_load_3d(st, &mA_hi, &full[s], a0, P, m0);
-      tma_load_3d(st + B_OFF, &mB_hi, &full[s], a0, n0, P);
       if (a_split(MODE)) tma_load_3d(st + A_BYTES, &mA_lo, &full[s], a0, P, m0);
-      if (b_split(MODE)) tma_load_3d(st + B_OFF + B_BYTES, &mB_lo, &full[s], a0, n0, P);
+      if constexpr (CL > 1) {
+        // this CTA's half of the B rows, to both CTAs of the pair
+        constexpr int HB = B_BYTES / 2;
+        const int nh = n0 + (int)crank * (BN / 2);
+        tma_load_3d_mc(st + B_OFF + crank * HB, &mB_hi, &full[s], a0, nh, P, (uint16_t)0x3);
+        if (b_split(MODE)) tma_load_3d_mc(st + B_OFF + B_BYTES + crank * HB, &mB_lo, &full[s], a0, nh, P, (uint16_t)0x3);
+      } else {
+        tma_load_3d(st + B_OFF, &mB_hi, &full[s], a0, n0, P);
+        if (b_split(MODE)) tma_load_3d(st + B_OFF + B_BYTES, &mB_lo, &full[s], a0, n0, P);
+      }
     }
     // let the copies already issued land before the CTA can exit
     for (int i = max(0, nk - STAGES); i < nk; ++i) {
       if (!mbar_wait(&full[i % STAGES], (uint32_t)(i / STAGES) & 1u)) { atomicOr(p.err, 2); break; }
+    }
+    if constexpr (CL > 1) {
+      // and the peer's last commits arrive on this CTA's `empty` barriers
+      for (int i = nk; i < nk + STAGES; ++i) {
+        if (!mbar_wait(&empty[i % STAGES], ((uint32_t)(i / STAGES) & 1u) ^ 1u)) { atomicOr(p.err, 2); break; }
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
@@ -233,7 +285,8 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
           if (a_split(MODE)) mma_op<F8>(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u);
         }
       }
-      mma_commit(&empty[s]);
+      if constexpr (CL > 1) mma_commit_mc(&empty[s], (uint16_t)0x3);
+      else mma_commit(&empty[s]);
     }
     (void)ok;
     mma_commit(done);   // fires when every MMA issued above has completed
@@ -286,6 +339,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
   }
+  if constexpr (CL > 1) cluster_sync_all();   // neither CTA leaves while the other may still signal it
 }
 
 
@@ -658,8 +712,8 @@ int sm_count() {
 // (units per CTA + a fixed per-CTA cost of `overhead` units), so a last,
 // nearly empty wave costs as much as a full one.  Tries the splits that fill
 // one to four waves and keeps the cheapest (the fewest splits on ties).
-int wave_splits(int tiles, int total, int overhead) {
-  const int sms = sm_count();
+int wave_splits(int tiles, int total, int overhead, int sms = 0) {
+  if (sms <= 0) sms = sm_count();
   int best = 1;
   long long best_cost = -1;
   for (int w = 1; w <= 4; ++w) {
@@ -677,6 +731,43 @@ int wave_splits(int tiles, int total, int overhead) {
   return best;
 }
 
+namespace {
+bool cluster_pairs_enabled() {
+  const char* e = std::getenv("TDDFT_TC_CLUSTER");
+  return !(e && e[0] == '0');
+}
+
+// CTAs of the paired contraction that can be resident at once: two per
+// co-resident cluster (an SM left over in a GPC takes no pair).
+int pair_slots(int mode) {
+  static int cached[2] = {0, 0};
+  int& c = cached[mode == CROSS ? 1 : 0];
+  if (c == 0) {
+    const void* k = mode == CROSS ? (const void*)k1_tc_kernel<CROSS, false, 2> : (const void*)k1_tc_kernel<BOTH, false, 2>;
+    const int smem = mode == CROSS ? Cfg<CROSS>::SMEM_BYTES : Cfg<BOTH>::SMEM_BYTES;
+    ensure_smem(k, smem);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 2;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(1, 2, 1);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess || n <= 0) {
+      (void)cudaGetLastError();
+      n = sm_count() / 2;
+    }
+    c = 2 * n;
+  }
+  return c;
+}
+}  // namespace
+
 void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int pn, int Kin,
                  const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, float* out,
                  bool accumulate, int* err, cudaStream_t s, KernelProfile* prof, double prof_flops,
@@ -688,10 +779,15 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
   const int ldk = tc_pad(Kin);
   const int nab = (Kin + BK - 1) / BK;
   const int total = pn * nab;
-  const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+  const int mt0 = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+  // split-B products in pairs of M tiles that share each B tile through a
+  // cluster multicast (TDDFT_TC_CLUSTER=0 turns this off; the results are the
+  // same bits either way: every CTA issues the same MMAs on the same data)
+  const bool pair = (mode == BOTH || mode == CROSS) && mt0 > 1 && cluster_pairs_enabled();
+  const int mt = pair ? (mt0 + 1) & ~1 : mt0;
   // a CTA's fixed cost (barriers, TMEM, pipeline fill, 128 KB epilogue) is about
   // four k-blocks of MMA work
-  int splits = wave_splits(mt * nt, total, 4);
+  int splits = wave_splits(mt * nt, total, 4, pair ? pair_slots(mode) : 0);
   const int per = (total + splits - 1) / splits;
   splits = (total + per - 1) / per;
 
@@ -700,7 +796,7 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
   const cuuint32_t bA[3] = {BK, 1, BM};
   const cuuint64_t dB[3] = {(cuuint64_t)Kin, (cuuint64_t)N, (cuuint64_t)pn};
   const cuuint64_t sB[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)N * ldk * 2};
-  const cuuint32_t bB[3] = {BK, BN, 1};
+  const cuuint32_t bB[3] = {BK, (cuuint32_t)(pair ? BN / 2 : BN), 1};   // a pair loads half a B tile each
   CUtensorMap mAh = make_map(Ahi, dA, sA, bA), mBh = make_map(Bhi, dB, sB, bB);
   CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA) : mAh;
   CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB) : mBh;
@@ -714,7 +810,27 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
     kernel<<<grid, THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
     if (prof) prof->end(s, prof_flops, prof_bytes);
   };
-  if (mode == BOTH) launch(k1_tc_kernel<BOTH, false>, Cfg<BOTH>::SMEM_BYTES);
+  auto launch_pair = [&](auto kernel, int smem) {
+    ensure_smem((const void*)kernel, smem);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 2;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (prof) prof->begin(s);
+    TD_CUDA(cudaLaunchKernelEx(&cfg, kernel, mAh, mAl, mBh, mBl, p));
+    if (prof) prof->end(s, prof_flops, prof_bytes);
+  };
+  if (pair && mode == BOTH) launch_pair(k1_tc_kernel<BOTH, false, 2>, Cfg<BOTH>::SMEM_BYTES);
+  else if (pair) launch_pair(k1_tc_kernel<CROSS, false, 2>, Cfg<CROSS>::SMEM_BYTES);
+  else if (mode == BOTH) launch(k1_tc_kernel<BOTH, false>, Cfg<BOTH>::SMEM_BYTES);
   else if (mode == CROSS) launch(k1_tc_kernel<CROSS, false>, Cfg<CROSS>::SMEM_BYTES);
   else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT, false>, Cfg<ASPLIT>::SMEM_BYTES);
   else launch(k1_tc_kernel<SINGLE, false>, Cfg<SINGLE>::SMEM_BYTES);

@@ -85,6 +85,25 @@ def test_polar_full_size(setup):
     r = s.solve_polar(o, mu, list(CONFIGS["rpa_polar_medium"]["omegas"]))
     ref = np.array(gold["polar"]["alpha"])
     assert r["status"] == api.OK
-    print("\nmedium alpha MIXED: max abs err %.3g, max per-element rel err %.3g" % alpha_report(r["alpha"], ref))
+    assert r["stats"]["max_resid_certified"] <= 1e-5   # the gate of the linear solves
+    print("\nmedium alpha MIXED: max abs err %.3g, max per-element rel err %.3g (certified residual %.2e)"
+          % (alpha_report(r["alpha"], ref) + (r["stats"]["max_resid_certified"],)))
     assert alpha_excess(r["alpha"], ref, 1e-5, FLOOR_TC) <= 1.0
     assert abs(r["stats"]["n_iter"] - gold["polar"]["n_iter"]) <= 4
+
+
+def test_cluster_pairs_give_the_same_bits(setup, monkeypatch):
+    """The split-B contractions run in CTA pairs that share each B tile by a
+    cluster multicast; every CTA still issues the same MMAs on the same data,
+    so the products equal those of the unpaired launch bit for bit."""
+    api, p, mu, gold, s = setup
+    X = np.random.default_rng(11).standard_normal((7, p.n_ov))
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("TDDFT_TC_CLUSTER", flag)
+        out[flag] = (s.apply(1, X, precision=api.MIXED, tensor_cores=True),
+                     s.apply(0, X, precision=api.MIXED, tensor_cores=True),
+                     s.apply(1, X, precision=api.MIXED, tensor_cores=3))
+    for a, b in zip(out["1"], out["0"]):
+        for u, v in zip(a if isinstance(a, tuple) else (a,), b if isinstance(b, tuple) else (b,)):
+            assert np.array_equal(u, v)
