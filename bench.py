@@ -4,10 +4,11 @@
 One step is the whole hot path on the large mixed workload (n_occ=150,
 n_vir=1350, ov=202,500, exact n_aux=6000, ris n_aux=1350): a TDA solve and a
 Casida solve for the 20 lowest states each, with the rid preconditioner to a
-residual of 1e-5, MIXED precision (exact products as BF16 hi+lo on the tcgen05
-tensor cores with FP32 accumulation; ris inner solves with FP32 vectors on the
-BF16 ris factors; FP64 outer subspace algebra; every converged residual
-re-certified with the FP32 operator).  40 converged states per step.
+residual of 1e-5, MIXED precision (exact products on the tcgen05 tensor cores
+with every operand scaled by a power of two and split into FP16 hi + lo, FP32
+accumulation: FP32-accurate products; ris inner solves with FP32 vectors on the
+BF16 ris factors; FP64 outer subspace algebra; the converged residuals
+recomputed from fresh products).  40 converged states per step.
 
 value: states converged per second (40 per step x steps x ranks / max time),
 device-timed with CUDA events on the solver's stream, factors resident in HBM;
@@ -430,7 +431,7 @@ def our_arm(args, rank, world, local):
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tensor: bf16x3) + fp64 subspace",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tensor: fp16 hi+lo x3) + fp64 subspace",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_occ": meta["n_occ"], "n_vir": meta["n_vir"],
                        "n_aux": meta["n_aux"], "n_aux_ris": meta["n_ris"], "n_states": N_STATES,
@@ -496,9 +497,11 @@ def roofline(prof, rec_ms, rec_fl, rec_by, peaks, src, tc, clk, total_ms):
     flops_launch = prof["flops"] / max(prof["launches"], 1)
     achieved = flops_launch / (kernel_ms * 1e-3) / 1e12 if prof["launches"] else 0.0
     if tc:
+        # FP16 and BF16 run at the same dense tensor rate (nominal ratio 1)
         peak = peaks["bf16_tflops_sustained"]
-        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_kind": "bf16 sustained, " + src,
-                "note": "algorithmic flops 2*M*N*K; the hi+lo split issues 3 BF16 products per flop, "
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "peak_kind": "fp16 dense = bf16 sustained (nominal ratio 1), " + src,
+                "note": "algorithmic flops 2*M*N*K; the hi+lo split issues 3 FP16 products per flop, "
                         "so frac <= 1/3 (mma_pipe_frac = 3 x frac)"}
     else:
         sm = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
@@ -515,7 +518,7 @@ def roofline(prof, rec_ms, rec_fl, rec_by, peaks, src, tc, clk, total_ms):
             "hbm_bound_time_share": float(rec_ms[t_hbm > t_ten].sum() / rec_ms.sum()),
             "achieved_hbm_gbs": float(rec_by.sum() / rec_ms.sum() / 1e6),
             "algorithmic_bytes_per_launch": float(rec_by.mean()),
-            "attainable_note": "per launch max(%g BF16 products per flop at the tensor peak, algorithmic bytes "
+            "attainable_note": "per launch max(%g FP16 products per flop at the tensor peak, algorithmic bytes "
                                "at hbm_gbs %.0f); attainable_frac = sum of those / sum of measured times"
                                % (per_flop, peaks["hbm_gbs"])})
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak if peak else None,
@@ -709,7 +712,7 @@ def serving(args, api, torch):
 def batched(args, api, torch, tc=0):
     """Many small independent TDA solves submitted together: n_occ ~ U{8..64},
     n_vir = n_occ x U{4..8}, n_aux = 5 n_mo, ris n_aux = 9 ceil(n_occ/2), 5-10
-    states, MIXED (FP32 outer products on the SIMT path, or with tc the BF16
+    states, MIXED (FP32 outer products on the SIMT path, or with tc the FP16
     hi+lo tcgen05 products; BF16 ris), rid; all queued at time 0 on a server
     with --batch-slots slots (concurrent streams, not one persistent kernel).
     Throughput = solves / (first submit to last finish)."""
@@ -739,7 +742,7 @@ def batched(args, api, torch, tc=0):
     out.update({"slots": args.batch_slots, "distinct_problems": n_pool,
                 "note": "TDA solves queued at once, each creating its context from FP32 device arrays; "
                         "MIXED, %s outer products, BF16 ris, rid"
-                        % ("BF16 hi+lo tcgen05" if tc else "FP32 SIMT")})
+                        % ("FP16 hi+lo tcgen05" if tc else "FP32 SIMT")})
     return out
 
 

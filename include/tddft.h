@@ -61,13 +61,15 @@ typedef enum { TDDFT_PRECOND_DIAG = 0, TDDFT_PRECOND_RID = 1 } tddft_precond;
 
 /* Arithmetic of the solve.
  * PLAIN: every step in FP64 (factors, products, subspace algebra).
- * MIXED: exact products with FP32 factors and FP32 accumulation, or with
- *        BF16 hi+lo split factors on the tcgen05 tensor cores (three products
- *        hi*hi + hi*lo + lo*hi, FP32 accumulation) when `tensor_cores` is set;
- *        the ris inner solve on BF16 factors with FP32 accumulation; FP64 for
- *        the subspace eigenproblem, Gram-Schmidt and the final residual check,
- *        which recomputes the converged residuals with an FP32-or-better
- *        product ("certification").                                         */
+ * MIXED: exact products with FP32 factors and FP32 accumulation, or, when
+ *        `tensor_cores` is set, on the tcgen05 tensor cores with every operand
+ *        (factors, trial vectors, the first contraction's results) scaled by
+ *        a power of two and split into FP16 hi + lo parts (22 significand
+ *        bits; three products hi*hi + hi*lo + lo*hi, FP32 accumulation) --
+ *        FP32-accurate products either way; the ris inner solve on BF16
+ *        factors with FP32 accumulation; FP64 for the subspace eigenproblem,
+ *        Gram-Schmidt and the residuals, which are recomputed at the end from
+ *        fresh products of the converged vectors ("certification").        */
 typedef enum { TDDFT_PLAIN = 0, TDDFT_MIXED = 1 } tddft_precision;
 
 typedef struct {
@@ -95,7 +97,7 @@ typedef struct {
   int inner_max_iter;         /* ris inner iterations (20, Sec. 3.1)          */
   int max_subspace;           /* collapse above this many vectors (0: auto)   */
   int precision;              /* tddft_precision                              */
-  int tensor_cores;           /* MIXED only: tcgen05 BF16 hi+lo exchange      */
+  int tensor_cores;           /* MIXED only: tcgen05 FP16 hi+lo exchange      */
   int outputs_on_device;      /* 1: omega/X/Y/resid/alpha are device pointers */
   int ris_fp8;                /* MIXED + tensor_cores: the ris exchange products of
                                * the rid preconditioner (Eq. TDDFT-ris_approx) in
@@ -111,10 +113,11 @@ typedef struct {
   int n_restart;              /* subspace collapses                           */
   int gpu_launches;           /* kernels launched by this solve               */
   double max_resid;           /* largest final residual norm                  */
-  double max_resid_certified; /* MIXED: after the FP32-or-better re-check     */
+  double max_resid_certified; /* MIXED: the final residuals recomputed from   */
+                              /* fresh FP32-accurate products (-1: PLAIN)     */
   double t_total_s, t_matvec_s, t_precond_s;  /* wall times (host clock)     */
   double t_guess_s;           /* initial guess (Davidson on the ris operator)  */
-  double t_certify_s;         /* MIXED: FP32 re-certification of the results   */
+  double t_certify_s;         /* MIXED: that recomputation                     */
 } tddft_stats;
 
 /* Fill `opts` with the paper's defaults (Sec. 3.1-3.2): rid, tol 1e-5,
@@ -173,7 +176,7 @@ tddft_status tddft_solve_polar(tddft_ctx* ctx, const tddft_opts* opts, const dou
 /* Variant terms of Eq. hessian for other functionals (the paper's benchmarks
  * include a range-separated hybrid; the terms keep the same kernels).  Each
  * may be added once per context, before or between solves; they enter the
- * exact operator (every product, residual and certification) and not the ris
+ * exact operator (every product and residual) and not the ris
  * preconditioner T.
  *
  * tddft_add_exchange: a second exchange factor set M (the long-range,
@@ -200,10 +203,11 @@ tddft_status tddft_add_kernel(tddft_ctx* ctx, int n_g, const double* w, const vo
  *   kind 0: A X (exact), 1: ((A+B)X, (A-B)X) exact, 2: T_A X (ris),
  *   kind 3: ((T_A+T_B)X, (T_A-T_B)X) ris.
  * X [m][ov]; out0 [m][ov]; out1 [m][ov] for kinds 1 and 3 (else NULL).
- * precision / tensor_cores as in tddft_opts (for the ris kinds the tensor
- * cores form two products, trial vectors as BF16 hi + lo against the BF16
- * ris rows); tensor_cores = 2 runs the ris kinds' exchange contractions with
- * the FP8 e4m3 ris rows (tddft_opts.ris_fp8); on_device: pointers are device
+ * precision / tensor_cores as in tddft_opts (exact kinds: the scaled FP16
+ * hi + lo products; ris kinds: two products, trial vectors as BF16 hi + lo
+ * against the BF16 ris rows); tensor_cores = 2 runs the ris kinds' exchange
+ * contractions with the FP8 e4m3 ris rows (tddft_opts.ris_fp8) and the exact
+ * kinds as 1; other values: TDDFT_ERR_ARG; on_device: pointers are device
  * memory.
  * Results are FP64.                                                        */
 tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cores,
@@ -399,8 +403,8 @@ tddft_status tddft_pool_usage(int device, unsigned long long* used_current,
  * totals; 0 stops.  tddft_profile_read returns, for that contraction, the
  * number of launches, their summed device time (ms) and the algorithmic
  * flops (2*M*N*K per launch) since the last reset: which = 0 for the
- * tcgen05 kernel (tensor_cores on), 1 for the SIMT kernel (tensor cores off,
- * and the FP32 re-certification of MIXED residuals).  Other values:
+ * tcgen05 kernel (tensor_cores on), 1 for the SIMT kernel (tensor cores
+ * off).  Other values:
  * TDDFT_ERR_ARG.                                                          */
 tddft_status tddft_profile(tddft_ctx* ctx, int enable);
 tddft_status tddft_profile_read(const tddft_ctx* ctx, int which, long long* launches,

@@ -59,8 +59,9 @@ void stage_rows(const void* src, DType tin, bool on_device, long long rows, long
   }
 }
 
-// Device copies of one exact factor set: FP64 (PLAIN) and/or FP32 + BF16 hi/lo
-// tensor-core operands with rows padded for the TMA strides (MIXED).
+// Device copies of one exact factor set: FP64 (PLAIN) and/or FP32 + FP16 hi/lo
+// tensor-core operands (of the factors times a power of two per tensor) with
+// rows padded for the TMA strides (MIXED).
 void stage_exact(ExactCopies& e, const void* L_oo, const void* L_ov, const void* L_vv, long long A,
                  DType tin, bool dev, int no, int nv, bool p64, bool pmx, cudaStream_t s) {
   const long long ov = (long long)no * nv;
@@ -74,8 +75,6 @@ void stage_exact(ExactCopies& e, const void* L_oo, const void* L_ov, const void*
     e.f32_oo = DevBuf(A * no * no * 4, s);
     e.f32_ov = DevBuf(A * ov * 4, s);
     e.f32_vv = DevBuf(A * nv * nv * 4, s);
-    e.vv_hi = DevBuf(A * nv * tc_pad(nv) * 2, s);
-    e.vv_lo = DevBuf(A * nv * tc_pad(nv) * 2, s);
   }
   auto targets = [&](DevBuf& t64, DevBuf& t32) {
     std::vector<StageTarget> v;
@@ -87,26 +86,27 @@ void stage_exact(ExactCopies& e, const void* L_oo, const void* L_ov, const void*
   stage_rows(L_ov, tin, dev, A, ov, targets(e.f64_ov, e.f32_ov), s);
   stage_rows(L_vv, tin, dev, A, (long long)nv * nv, targets(e.f64_vv, e.f32_vv), s);
   if (pmx) {
-    // three BF16 parts per element (hi, lo, l2): hi + lo for the iterations'
-    // products, all three for the FP32-accurate re-certification
-    e.vv_l2 = DevBuf(A * nv * tc_pad(nv) * 2, s);
-    tc_pad_split(e.f32_vv.p, DType::F32, A * nv, nv, e.vv_hi.as<__nv_bfloat16>(), e.vv_lo.as<__nv_bfloat16>(), s,
-                 e.vv_l2.as<__nv_bfloat16>());
-    e.vo_hi = DevBuf(A * nv * tc_pad(no) * 2, s);
-    e.vo_lo = DevBuf(A * nv * tc_pad(no) * 2, s);
-    e.vo_l2 = DevBuf(A * nv * tc_pad(no) * 2, s);
-    tc_transpose_split(e.f32_ov.p, DType::F32, (int)A, no, nv, e.vo_hi.as<__nv_bfloat16>(),
-                       e.vo_lo.as<__nv_bfloat16>(), s, e.vo_l2.as<__nv_bfloat16>());
-    e.oo_hi = DevBuf(A * no * tc_pad(no) * 2, s);
-    e.oo_lo = DevBuf(A * no * tc_pad(no) * 2, s);
-    e.oo_l2 = DevBuf(A * no * tc_pad(no) * 2, s);
-    tc_pad_split(e.f32_oo.p, DType::F32, A * no, no, e.oo_hi.as<__nv_bfloat16>(), e.oo_lo.as<__nv_bfloat16>(),
-                 s, e.oo_l2.as<__nv_bfloat16>());
-    e.ov_hi = DevBuf(A * no * tc_pad(nv) * 2, s);
-    e.ov_lo = DevBuf(A * no * tc_pad(nv) * 2, s);
-    e.ov_l2 = DevBuf(A * no * tc_pad(nv) * 2, s);
-    tc_pad_split(e.f32_ov.p, DType::F32, A * no, nv, e.ov_hi.as<__nv_bfloat16>(), e.ov_lo.as<__nv_bfloat16>(),
-                 s, e.ov_l2.as<__nv_bfloat16>());
+    // scale block: s_oo and the scaled largest L_oo row norm, s_vv, s_ov and the
+    // scaled largest L_ov row norm (tc_f16_tensor_scale)
+    e.tc_scale = DevBuf(8 * 4, s);
+    TD_CUDA(cudaMemsetAsync(e.tc_scale.p, 0, 8 * 4, s));
+    DevBuf scratch(8, s);
+    float* sc = e.tc_scale.as<float>();
+    tc_f16_tensor_scale(e.f32_oo.as<float>(), A * no, no, sc + 0, scratch.as<unsigned>(), s);
+    tc_f16_tensor_scale(e.f32_vv.as<float>(), A * nv, nv, sc + 2, scratch.as<unsigned>(), s);
+    tc_f16_tensor_scale(e.f32_ov.as<float>(), A * no, nv, sc + 4, scratch.as<unsigned>(), s);
+    auto parts = [&](DevBuf& hi, DevBuf& lo, long long elems) {
+      hi = DevBuf(elems * 2, s);
+      lo = DevBuf(elems * 2, s);
+    };
+    parts(e.vv_hi, e.vv_lo, A * nv * tc_pad(nv));
+    tc_pad_split(e.f32_vv.p, DType::F32, A * nv, nv, e.vv_hi.p, e.vv_lo.p, TcElt::F16, sc + 2, s);
+    parts(e.vo_hi, e.vo_lo, A * nv * tc_pad(no));
+    tc_transpose_split(e.f32_ov.p, DType::F32, (int)A, no, nv, e.vo_hi.p, e.vo_lo.p, TcElt::F16, sc + 4, s);
+    parts(e.oo_hi, e.oo_lo, A * no * tc_pad(no));
+    tc_pad_split(e.f32_oo.p, DType::F32, A * no, no, e.oo_hi.p, e.oo_lo.p, TcElt::F16, sc + 0, s);
+    parts(e.ov_hi, e.ov_lo, A * no * tc_pad(nv));
+    tc_pad_split(e.f32_ov.p, DType::F32, A * no, nv, e.ov_hi.p, e.ov_lo.p, TcElt::F16, sc + 4, s);
   }
 }
 
@@ -182,8 +182,8 @@ unsigned long long factor_copy_bytes(const tddft_desc& d) {
   if (p64) bytes += 8.0 * (nvv + noo + nov + nr);
   // FP8 copies of the ris exchange rows: vv and ov^T padded to 16, four floats per row
   const double fp8 = (double)d.n_aux_ris_K * (nv * (tc_pad16(d.n_vir) + tc_pad16(d.n_occ)) + 16.0);
-  // MIXED: FP32 copies, three BF16 parts of every padded exact operand, BF16 ris rows and their padded copies
-  if (pmx) bytes += 4.0 * (nvv + noo + nov) + 6.0 * (double)d.n_aux * padded + 2.0 * nr +
+  // MIXED: FP32 copies, two FP16 parts of every padded exact operand, BF16 ris rows and their padded copies
+  if (pmx) bytes += 4.0 * (nvv + noo + nov) + 4.0 * (double)d.n_aux * padded + 2.0 * nr +
                     2.0 * (double)d.n_aux_ris_K * padded + fp8;
   return (unsigned long long)bytes;
 }
@@ -197,18 +197,16 @@ void ExactCopies::fill(FactorSet& f, int precision, bool coulomb) const {
     f.dt = DType::F32;
     if (coulomb) f.Jov = f32_ov.p;
     f.Koo = f32_oo.p; f.Kvv = f32_vv.p; f.Kov = f32_ov.p;
-    f.Kvv_hi = vv_hi.as<__nv_bfloat16>();
-    f.Kvv_lo = vv_lo.as<__nv_bfloat16>();
-    f.Kvo_hi = vo_hi.as<__nv_bfloat16>();
-    f.Kvo_lo = vo_lo.as<__nv_bfloat16>();
-    f.Koo_hi = oo_hi.as<__nv_bfloat16>();
-    f.Koo_lo = oo_lo.as<__nv_bfloat16>();
-    f.Kovp_hi = ov_hi.as<__nv_bfloat16>();
-    f.Kovp_lo = ov_lo.as<__nv_bfloat16>();
-    f.Kvv_l2 = vv_l2.as<__nv_bfloat16>();
-    f.Kvo_l2 = vo_l2.as<__nv_bfloat16>();
-    f.Koo_l2 = oo_l2.as<__nv_bfloat16>();
-    f.Kovp_l2 = ov_l2.as<__nv_bfloat16>();
+    f.tc_elt = TcElt::F16;
+    f.tc_scale = tc_scale.as<float>();
+    f.Kvv_hi = vv_hi.p;
+    f.Kvv_lo = vv_lo.p;
+    f.Kvo_hi = vo_hi.p;
+    f.Kvo_lo = vo_lo.p;
+    f.Koo_hi = oo_hi.p;
+    f.Koo_lo = oo_lo.p;
+    f.Kovp_hi = ov_hi.p;
+    f.Kovp_lo = ov_lo.p;
   }
 }
 
@@ -238,10 +236,11 @@ FactorSet Ctx::ris(int precision, bool fp8) const {
   } else {
     f.dt = DType::BF16;
     f.Jov = r16_J.p; f.Koo = r16_Koo.p; f.Kvv = r16_Kvv.p; f.Kov = r16_Kov.p;
-    f.Kvv_hi = r16_vvp.as<__nv_bfloat16>();
-    f.Kvo_hi = r16_vo.as<__nv_bfloat16>();
-    f.Koo_hi = r16_oop.as<__nv_bfloat16>();
-    f.Kovp_hi = r16_ovp.as<__nv_bfloat16>();
+    f.tc_elt = TcElt::BF16;
+    f.Kvv_hi = r16_vvp.p;
+    f.Kvo_hi = r16_vo.p;
+    f.Koo_hi = r16_oop.p;
+    f.Kovp_hi = r16_ovp.p;
     if (fp8 && nK > 0 && r8_vvp.p) {
       f.fp8 = true;
       f.Kvv8 = r8_vvp.as<unsigned char>();
@@ -460,14 +459,14 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
         // padded tensor-core copies (vv is symmetric, so its transpose is itself)
         c->r16_vvp = DevBuf(RK * nv * tc_pad(nv) * 2, s);
         c->r16_vo = DevBuf(RK * nv * tc_pad(no) * 2, s);
-        tc_transpose_split(c->r16_Kvv.p, DType::BF16, (int)RK, nv, nv, c->r16_vvp.as<__nv_bfloat16>(),
+        tc_transpose_split(c->r16_Kvv.p, DType::BF16, (int)RK, nv, nv, c->r16_vvp.p, nullptr, TcElt::BF16,
                            nullptr, s);
-        tc_transpose_split(c->r16_Kov.p, DType::BF16, (int)RK, no, nv, c->r16_vo.as<__nv_bfloat16>(),
+        tc_transpose_split(c->r16_Kov.p, DType::BF16, (int)RK, no, nv, c->r16_vo.p, nullptr, TcElt::BF16,
                            nullptr, s);
         c->r16_oop = DevBuf(RK * no * tc_pad(no) * 2, s);
         c->r16_ovp = DevBuf(RK * no * tc_pad(nv) * 2, s);
-        tc_pad_split(c->r16_Koo.p, DType::BF16, RK * no, no, c->r16_oop.as<__nv_bfloat16>(), nullptr, s);
-        tc_pad_split(c->r16_Kov.p, DType::BF16, RK * no, nv, c->r16_ovp.as<__nv_bfloat16>(), nullptr, s);
+        tc_pad_split(c->r16_Koo.p, DType::BF16, RK * no, no, c->r16_oop.p, nullptr, TcElt::BF16, nullptr, s);
+        tc_pad_split(c->r16_Kov.p, DType::BF16, RK * no, nv, c->r16_ovp.p, nullptr, TcElt::BF16, nullptr, s);
         // FP8 e4m3 copies with a scale per row (opts.ris_fp8), from the windowed BF16 rows
         c->r8_vvp = DevBuf(RK * nv * tc_pad16(nv), s);
         c->r8_vo = DevBuf(RK * nv * tc_pad16(no), s);
@@ -554,7 +553,7 @@ tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cor
     const size_t n = (size_t)m * c->ov;
     const bool ris = kind >= 2;
     const bool paired = kind & 1;
-    TD_REQUIRE(tensor_cores >= 0 && tensor_cores <= 3, TDDFT_ERR_ARG, "tensor_cores must be 0..3");
+    TD_REQUIRE(tensor_cores >= 0 && tensor_cores <= 2, TDDFT_ERR_ARG, "tensor_cores must be 0..2");
     FactorSet f = ris ? c->ris(precision, tensor_cores == 2) : c->exact(precision);
     DevBuf xb, o0, o1;
     const double* Xd = X;
@@ -570,7 +569,7 @@ tddft_status tddft_apply(tddft_ctx* ctx, int kind, int precision, int tensor_cor
     }
     g_launches = 0;
     apply_operator(c->dims(), f, Xd, m, paired ? OpMode::PAIRED : OpMode::TDA, d0, paired ? d1 : nullptr,
-                   (!ris && tensor_cores == 3) ? 2 : (tensor_cores != 0 ? 1 : 0), s);
+                   tensor_cores != 0 ? 1 : 0, s);
     if (!on_device) {
       TD_CUDA(cudaMemcpyAsync(out0, d0, n * 8, cudaMemcpyDeviceToHost, s));
       if (paired) TD_CUDA(cudaMemcpyAsync(out1, d1, n * 8, cudaMemcpyDeviceToHost, s));

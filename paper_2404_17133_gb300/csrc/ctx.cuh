@@ -8,6 +8,7 @@
 #include <thread>
 
 #include "common.cuh"
+#include "tc_gemm.cuh"
 
 namespace tddft {
 
@@ -23,23 +24,20 @@ struct FactorSet {
   const void* Kvv = nullptr;
   const void* Kov = nullptr;
   // Tensor-core operands (rows padded to tc_pad): Kvv as [P][b][a] and Kov
-  // transposed as [P][a][j]; hi + lo split for the exact operator, hi only
-  // (plain BF16) for the ris operator.
-  const __nv_bfloat16* Kvv_hi = nullptr;
-  const __nv_bfloat16* Kvv_lo = nullptr;
-  const __nv_bfloat16* Kvo_hi = nullptr;
-  const __nv_bfloat16* Kvo_lo = nullptr;
+  // transposed as [P][a][j]; for the exact operator FP16 hi + lo parts of the
+  // factors times the powers of two in tc_scale (tc_f16_tensor_scale), for the
+  // ris operator hi only (plain BF16).
+  TcElt tc_elt = TcElt::BF16;
+  const float* tc_scale = nullptr;   // FP16: the factor-set scale block (8 floats)
+  const void* Kvv_hi = nullptr;
+  const void* Kvv_lo = nullptr;
+  const void* Kvo_hi = nullptr;
+  const void* Kvo_lo = nullptr;
   // stage-1 operands: Koo as [P][i][pad(j)], Kov as [P][i][pad(b)]
-  const __nv_bfloat16* Koo_hi = nullptr;
-  const __nv_bfloat16* Koo_lo = nullptr;
-  const __nv_bfloat16* Kovp_hi = nullptr;
-  const __nv_bfloat16* Kovp_lo = nullptr;
-  // third BF16 parts (x = hi + lo + l2) of the exact operands, for the
-  // FP32-accurate tensor-core products of the re-certification
-  const __nv_bfloat16* Kvv_l2 = nullptr;
-  const __nv_bfloat16* Kvo_l2 = nullptr;
-  const __nv_bfloat16* Koo_l2 = nullptr;
-  const __nv_bfloat16* Kovp_l2 = nullptr;
+  const void* Koo_hi = nullptr;
+  const void* Koo_lo = nullptr;
+  const void* Kovp_hi = nullptr;
+  const void* Kovp_lo = nullptr;
   // Variant terms of the exact operator (Eq. hessian for other functionals):
   // a second exchange factor set entering with weight b_x, and a low-rank
   // kernel sum_g w_g F^g_ia F^g_jb added to the Coulomb term, its rows stored
@@ -69,11 +67,12 @@ struct FactorSet {
 struct ExactCopies {
   int n = 0;
   DevBuf f64_oo, f64_ov, f64_vv;  // PLAIN
-  DevBuf f32_oo, f32_ov, f32_vv;  // MIXED: SIMT operands and the FP32 re-certification
-  DevBuf vv_hi, vv_lo, vv_l2;     // [n][nv][tc_pad(nv)] BF16 split of L_vv (three parts)
-  DevBuf vo_hi, vo_lo, vo_l2;     // [n][nv][tc_pad(no)] BF16 split of L_ov transposed
-  DevBuf oo_hi, oo_lo, oo_l2;     // [n][no][tc_pad(no)]
-  DevBuf ov_hi, ov_lo, ov_l2;     // [n][no][tc_pad(nv)]
+  DevBuf f32_oo, f32_ov, f32_vv;  // MIXED: SIMT operands
+  DevBuf vv_hi, vv_lo;            // [n][nv][tc_pad(nv)] FP16 split of s_vv L_vv
+  DevBuf vo_hi, vo_lo;            // [n][nv][tc_pad(no)] FP16 split of s_ov L_ov transposed
+  DevBuf oo_hi, oo_lo;            // [n][no][tc_pad(no)] (s_oo L_oo)
+  DevBuf ov_hi, ov_lo;            // [n][no][tc_pad(nv)] (s_ov L_ov)
+  DevBuf tc_scale;                // the scale block of tc_f16_tensor_scale (8 floats)
   // Exchange operands of `precision` into f (and the Coulomb block when coulomb).
   void fill(FactorSet& f, int precision, bool coulomb) const;
 };
@@ -111,10 +110,10 @@ struct OpDims {
 enum class OpMode { TDA, PAIRED };
 
 // out0 = A X (TDA) or (A+B) X and out1 = (A-B) X (PAIRED); X, out FP64 [m][ov].
-// tc: 0 SIMT contractions; 1 the exchange contractions on tcgen05 (BF16 hi+lo
-// operands, three products; plain BF16 ris factors); 2 on tcgen05 with three
-// BF16 parts per operand (six products: FP32-accurate, for re-certification;
-// exact factor sets with the third parts only, else as 1).
+// tc: 0 SIMT contractions; nonzero the exchange contractions on tcgen05
+// (exact factor sets: FP16 hi+lo operands with power-of-two scales, three
+// products, FP32-accurate; ris factor sets: trial vectors as BF16 hi+lo
+// against the plain BF16 rows, or the FP8 rows when the set has them).
 void apply_operator(const OpDims& d, const FactorSet& f, const double* X, int m, OpMode mode,
                     double* out0, double* out1, int tc, cudaStream_t s);
 // FP32 vectors (FP32 or BF16 factor sets only): the ris products of the inner solves.

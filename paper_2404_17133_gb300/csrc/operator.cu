@@ -170,61 +170,11 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
     if (need_k2) K2b = DevBuf(mov * ew, s);
     const bool use_tc = tensor_cores && !f64 && f.Kvv_hi && f.Kvo_hi && f.Koo_hi && f.Kovp_hi;
     TD_REQUIRE(!tensor_cores || f64 || use_tc, TDDFT_ERR_ARG, "tensor-core factor copies missing");
-    const bool tc3 = use_tc && tc == 2 && f.Kvv_l2 && f.Kvo_l2 && f.Koo_l2 && f.Kovp_l2 && f.Kvv_lo &&
-                     tc_stage1_3_fits(no);
-    // three-part intermediates take half as much again as hi + lo ones
-    const int pc = chunk_rows(f.nK, (long long)m * ov * (long long)ew * (tc3 ? 3 : 2) / 2, m,
-                              use_tc ? kChunkBytesTC : kChunkBytes);
+    const int pc = chunk_rows(f.nK, (long long)m * ov * (long long)ew, m, use_tc ? kChunkBytesTC : kChunkBytes);
     const size_t es = dtype_size(f.dt);
-    if (tc3) {
-      // FP32-accurate products on the tensor cores: every operand (trial
-      // vectors, factors, the stage-1 results) as three BF16 parts x = h + m + l
-      // and the six products h h + h m + m h + h l + l h + m m, accumulated in
-      // FP32 -- as K1 = [BOTH (h, m) x (h, m)] + [CROSS (h, l) x (h, l)] +
-      // [SINGLE m x m] over each P-chunk
-      const int nvp = tc_pad(nv), nop = tc_pad(no);
-      const DType xt = x32 ? DType::F32 : DType::F64;
-      DevBuf Xt[3], Xs[3], Zp[3], Qp[3];
-      for (int t = 0; t < 3; ++t) {
-        Xt[t] = DevBuf((size_t)m * nv * nop * 2, s);
-        Zp[t] = DevBuf((size_t)m * no * pc * nvp * 2, s);
-        if (need_k2) {
-          Xs[t] = DevBuf((size_t)m * no * nvp * 2, s);
-          Qp[t] = DevBuf((size_t)m * no * pc * nop * 2, s);
-        }
-      }
-      auto bf = [](DevBuf& b) { return b.as<__nv_bfloat16>(); };
-      tc_transpose_split(X, xt, m, no, nv, bf(Xt[0]), bf(Xt[1]), s, bf(Xt[2]));
-      if (need_k2) tc_pad_split(X, xt, (long long)m * no, nv, bf(Xs[0]), bf(Xs[1]), s, bf(Xs[2]));
-      const int Mz = m * no;
-      for (int p0 = 0; p0 < f.nK; p0 += pc) {
-        const int pn = (f.nK - p0 < pc) ? f.nK - p0 : pc;
-        {
-          const __nv_bfloat16* const A3[3] = {bf(Xt[0]), bf(Xt[1]), bf(Xt[2])};
-          const size_t o = (size_t)p0 * no * nop;
-          const __nv_bfloat16* const B3[3] = {f.Koo_hi + o, f.Koo_lo + o, f.Koo_l2 + o};
-          __nv_bfloat16* const Z3[3] = {bf(Zp[0]), bf(Zp[1]), bf(Zp[2])};
-          tc_stage1_3(A3, m * nv, no, B3, no, pn, nv, Z3, d.tc_err, s);
-          const size_t v = (size_t)p0 * nv * nvp;
-          tc_contract(Z3[0], Z3[1], Mz, pn, nv, f.Kvv_hi + v, f.Kvv_lo + v, nv, K1b.as<float>(), p0 > 0, d.tc_err, s);
-          tc_contract(Z3[0], Z3[2], Mz, pn, nv, f.Kvv_hi + v, f.Kvv_l2 + v, nv, K1b.as<float>(), true, d.tc_err, s,
-                      nullptr, 0.0, 0.0, true);
-          tc_contract(Z3[1], nullptr, Mz, pn, nv, f.Kvv_lo + v, nullptr, nv, K1b.as<float>(), true, d.tc_err, s);
-        }
-        if (need_k2) {
-          const __nv_bfloat16* const A3[3] = {bf(Xs[0]), bf(Xs[1]), bf(Xs[2])};
-          const size_t o = (size_t)p0 * no * nvp;
-          const __nv_bfloat16* const B3[3] = {f.Kovp_hi + o, f.Kovp_lo + o, f.Kovp_l2 + o};
-          __nv_bfloat16* const Q3[3] = {bf(Qp[0]), bf(Qp[1]), bf(Qp[2])};
-          tc_stage1_3(A3, m * no, nv, B3, no, pn, no, Q3, d.tc_err, s);
-          const size_t v = (size_t)p0 * nv * nop;
-          tc_contract(Q3[0], Q3[1], Mz, pn, no, f.Kvo_hi + v, f.Kvo_lo + v, nv, K2b.as<float>(), p0 > 0, d.tc_err, s);
-          tc_contract(Q3[0], Q3[2], Mz, pn, no, f.Kvo_hi + v, f.Kvo_l2 + v, nv, K2b.as<float>(), true, d.tc_err, s,
-                      nullptr, 0.0, 0.0, true);
-          tc_contract(Q3[1], nullptr, Mz, pn, no, f.Kvo_lo + v, nullptr, nv, K2b.as<float>(), true, d.tc_err, s);
-        }
-      }
-    } else if (use_tc && f.fp8) {
+    // 16-bit tensor-core operand pointer at element offset o
+    auto at16 = [](const void* b, size_t o) { return static_cast<const void*>(static_cast<const uint16_t*>(b) + o); };
+    if (use_tc && f.fp8) {
       // ris exchange rows in FP8 e4m3 (one scale per row P): the stage-1
       // products Z = L_oo X and Q = L_ov X^T run as for BF16 (trial vectors as
       // BF16 hi + lo against the BF16 rows) and leave their results as e4m3
@@ -234,18 +184,18 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
       TD_REQUIRE(f.Kvv8 && f.Kvo8 && f.s_vv, TDDFT_ERR_ARG, "FP8 ris copies missing");
       const int nvp = tc_pad(nv), nop = tc_pad(no), nv16 = tc_pad16(nv), no16 = tc_pad16(no);
       const DType xt = x32 ? DType::F32 : DType::F64;
-      DevBuf sc((size_t)(2 + 2 * f.nK) * 4, s), kap(8, s);
+      DevBuf sc((size_t)(2 + 2 * f.nK) * 4, s), kap(16, s);
       tc_fp8_scales(X, xt, m, no, nv, f.s_vv, f.rho_oo, f.s_vo, f.rho_ov, f.nK, sc.as<float>(), kap.as<unsigned>(), s);
       const float* inv1 = sc.as<float>();
       const float* inv2 = inv1 + 1;
       const float* mu1 = inv1 + 2;
       const float* mu2 = mu1 + f.nK;
       DevBuf Xt_hi((size_t)m * nv * nop * 2, s), Xt_lo((size_t)m * nv * nop * 2, s), Xs_hi, Xs_lo;
-      tc_transpose_split(X, xt, m, no, nv, Xt_hi.as<__nv_bfloat16>(), Xt_lo.as<__nv_bfloat16>(), s);
+      tc_transpose_split(X, xt, m, no, nv, Xt_hi.p, Xt_lo.p, TcElt::BF16, nullptr, s);
       if (need_k2) {
         Xs_hi = DevBuf((size_t)m * no * nvp * 2, s);
         Xs_lo = DevBuf((size_t)m * no * nvp * 2, s);
-        tc_pad_split(X, xt, (long long)m * no, nv, Xs_hi.as<__nv_bfloat16>(), Xs_lo.as<__nv_bfloat16>(), s);
+        tc_pad_split(X, xt, (long long)m * no, nv, Xs_hi.p, Xs_lo.p, TcElt::BF16, nullptr, s);
       }
       DevBuf Zhi((size_t)m * no * pc * nv16, s), Zlo((size_t)m * no * pc * nv16, s), Qhi, Qlo;
       if (need_k2) {
@@ -256,13 +206,15 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
       for (int p0 = 0; p0 < f.nK; p0 += pc) {
         const int pn = (f.nK - p0 < pc) ? f.nK - p0 : pc;
         tc_stage1_fp8(Xt_hi.as<__nv_bfloat16>(), Xt_lo.as<__nv_bfloat16>(), m * nv, no,
-                      f.Koo_hi + (size_t)p0 * no * nop, no, pn, nv, mu1 + p0, Zhi.as<unsigned char>(),
+                      static_cast<const __nv_bfloat16*>(f.Koo_hi) + (size_t)p0 * no * nop, no, pn, nv, mu1 + p0,
+                      Zhi.as<unsigned char>(),
                       Zlo.as<unsigned char>(), d.tc_err, s);
         tc_contract8(Zhi.as<unsigned char>(), Zlo.as<unsigned char>(), Mz, pn, nv,
                      f.Kvv8 + (size_t)p0 * nv * nv16, nv, K1b.as<float>(), p0 > 0, inv1, d.tc_err, s);
         if (need_k2) {
           tc_stage1_fp8(Xs_hi.as<__nv_bfloat16>(), Xs_lo.as<__nv_bfloat16>(), m * no, nv,
-                        f.Kovp_hi + (size_t)p0 * no * nvp, no, pn, no, mu2 + p0, Qhi.as<unsigned char>(),
+                        static_cast<const __nv_bfloat16*>(f.Kovp_hi) + (size_t)p0 * no * nvp, no, pn, no, mu2 + p0,
+                        Qhi.as<unsigned char>(),
                         Qlo.as<unsigned char>(), d.tc_err, s);
           tc_contract8(Qhi.as<unsigned char>(), Qlo.as<unsigned char>(), Mz, pn, no,
                        f.Kvo8 + (size_t)p0 * nv * no16, nv, K2b.as<float>(), p0 > 0, inv2, d.tc_err, s);
@@ -271,19 +223,33 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
     } else if (use_tc) {
       // Both contractions of K1 and of K2 on the tensor cores.  The trial block
       // enters twice: transposed per vector ([(n,a)][j]) for Z = L_oo X and as is
-      // ([(n,j)][b]) for Q = L_ov X^T, always as BF16 hi + lo (so Z and Q are
-      // too); exact factors are hi + lo splits as well (three products), the
-      // BF16 ris factors are used as they are (two products, exact with respect
-      // to the factors).
-      const bool split = f.Kvv_lo != nullptr;
+      // ([(n,j)][b]) for Q = L_ov X^T, always as hi + lo (so Z and Q are too).
+      // Exact factor sets (FP16): the factors are split hi + lo as well (three
+      // products); every operand carries a power of two (tc_f16_product_scales)
+      // that the contractions' sums remove.  ris factor sets (BF16): the
+      // factors are used as they are (two products, exact with respect to them).
+      const bool f16 = f.tc_elt == TcElt::F16;
+      TD_REQUIRE(!f16 || (f.Kvv_lo && f.Kvo_lo && f.Koo_lo && f.Kovp_lo && f.tc_scale), TDDFT_ERR_ARG,
+                 "FP16 factor parts missing");
+      const TcElt et = f.tc_elt;
       const int nvp = tc_pad(nv), nop = tc_pad(no);
       const DType xt = x32 ? DType::F32 : DType::F64;
+      DevBuf sc, kap;
+      const float* sx = nullptr;
+      const float *mz = nullptr, *mq = nullptr, *f1 = nullptr, *f2 = nullptr;
+      if (f16) {
+        sc = DevBuf(8 * 4, s);
+        kap = DevBuf(16, s);
+        tc_f16_product_scales(X, xt, m, no, nv, f.tc_scale, sc.as<float>(), kap.as<unsigned>(), s);
+        sx = sc.as<float>();
+        mz = sx + 1; mq = sx + 2; f1 = sx + 3; f2 = sx + 4;
+      }
       DevBuf Xt_hi((size_t)m * nv * nop * 2, s), Xt_lo((size_t)m * nv * nop * 2, s), Xs_hi, Xs_lo;
-      tc_transpose_split(X, xt, m, no, nv, Xt_hi.as<__nv_bfloat16>(), Xt_lo.as<__nv_bfloat16>(), s);
+      tc_transpose_split(X, xt, m, no, nv, Xt_hi.p, Xt_lo.p, et, sx, s);
       if (need_k2) {
         Xs_hi = DevBuf((size_t)m * no * nvp * 2, s);
         Xs_lo = DevBuf((size_t)m * no * nvp * 2, s);
-        tc_pad_split(X, xt, (long long)m * no, nv, Xs_hi.as<__nv_bfloat16>(), Xs_lo.as<__nv_bfloat16>(), s);
+        tc_pad_split(X, xt, (long long)m * no, nv, Xs_hi.p, Xs_lo.p, et, sx, s);
       }
       DevBuf Zhi((size_t)m * no * pc * nvp * 2, s), Zlo((size_t)m * no * pc * nvp * 2, s), Qhi, Qlo;
       if (need_k2) {
@@ -293,27 +259,24 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
       const int Mz = m * no;
       for (int p0 = 0; p0 < f.nK; p0 += pc) {
         const int pn = (f.nK - p0 < pc) ? f.nK - p0 : pc;
-        const __nv_bfloat16* oo_lo = split ? f.Koo_lo + (size_t)p0 * no * nop : nullptr;
-        tc_stage1(Xt_hi.as<__nv_bfloat16>(), Xt_lo.as<__nv_bfloat16>(), m * nv, no,
-                  f.Koo_hi + (size_t)p0 * no * nop, oo_lo, no, pn, nv, Zhi.as<__nv_bfloat16>(),
-                  Zlo.as<__nv_bfloat16>(), d.tc_err, s);
-        const bool timed = d.prof && d.prof->on && f.dt != DType::BF16;
-        tc_contract(Zhi.as<__nv_bfloat16>(), Zlo.as<__nv_bfloat16>(), Mz, pn, nv,
-                    f.Kvv_hi + (size_t)p0 * nv * nvp, split ? f.Kvv_lo + (size_t)p0 * nv * nvp : nullptr,
-                    nv, K1b.as<float>(), p0 > 0, d.tc_err, s, timed ? d.prof : nullptr,
-                    2.0 * Mz * (double)nv * (double)pn * nv,
-                    // Z hi+lo [Mz][pn*nv], L_vv chunk [pn*nv][nv] (hi+lo when split), K1 FP32
+        tc_stage1(Xt_hi.p, Xt_lo.p, m * nv, no, at16(f.Koo_hi, (size_t)p0 * no * nop),
+                  f16 ? at16(f.Koo_lo, (size_t)p0 * no * nop) : nullptr, no, pn, nv, et, mz, Zhi.p, Zlo.p,
+                  d.tc_err, s);
+        const bool timed = d.prof && d.prof->on && f16;
+        tc_contract(Zhi.p, Zlo.p, Mz, pn, nv, at16(f.Kvv_hi, (size_t)p0 * nv * nvp),
+                    f16 ? at16(f.Kvv_lo, (size_t)p0 * nv * nvp) : nullptr, nv, K1b.as<float>(), p0 > 0, et, f1,
+                    d.tc_err, s, timed ? d.prof : nullptr, 2.0 * Mz * (double)nv * (double)pn * nv,
+                    // Z hi+lo [Mz][pn*nv], L_vv chunk [pn*nv][nv] (hi+lo for FP16), K1 FP32
                     // written (and read back when accumulating)
-                    4.0 * Mz * (double)pn * nv + (split ? 4.0 : 2.0) * (double)pn * nv * nv +
+                    4.0 * Mz * (double)pn * nv + (f16 ? 4.0 : 2.0) * (double)pn * nv * nv +
                         4.0 * Mz * (double)nv * (p0 > 0 ? 2.0 : 1.0));
         if (need_k2) {
-          const __nv_bfloat16* ov_lo = split ? f.Kovp_lo + (size_t)p0 * no * nvp : nullptr;
-          tc_stage1(Xs_hi.as<__nv_bfloat16>(), Xs_lo.as<__nv_bfloat16>(), m * no, nv,
-                    f.Kovp_hi + (size_t)p0 * no * nvp, ov_lo, no, pn, no, Qhi.as<__nv_bfloat16>(),
-                    Qlo.as<__nv_bfloat16>(), d.tc_err, s);
-          tc_contract(Qhi.as<__nv_bfloat16>(), Qlo.as<__nv_bfloat16>(), Mz, pn, no,
-                      f.Kvo_hi + (size_t)p0 * nv * nop, split ? f.Kvo_lo + (size_t)p0 * nv * nop : nullptr,
-                      nv, K2b.as<float>(), p0 > 0, d.tc_err, s);
+          tc_stage1(Xs_hi.p, Xs_lo.p, m * no, nv, at16(f.Kovp_hi, (size_t)p0 * no * nvp),
+                    f16 ? at16(f.Kovp_lo, (size_t)p0 * no * nvp) : nullptr, no, pn, no, et, mq, Qhi.p, Qlo.p,
+                    d.tc_err, s);
+          tc_contract(Qhi.p, Qlo.p, Mz, pn, no, at16(f.Kvo_hi, (size_t)p0 * nv * nop),
+                      f16 ? at16(f.Kvo_lo, (size_t)p0 * nv * nop) : nullptr, nv, K2b.as<float>(), p0 > 0, et, f2,
+                      d.tc_err, s);
         }
       }
     } else {

@@ -269,25 +269,18 @@ struct TdaOut {
   double cert = -1.0;   // largest re-certified residual (when a gate was given)
 };
 
-// Iterations the loop gets to reach its tightened threshold after a failed
-// gate before it moves to the accurate operator.
-constexpr int kGateWait = 4;
-
-// Re-certification gate: residual norms of the k Ritz pairs recomputed with an
-// FP32-accurate operator (TDA: X [k][ov], omega; Casida: U, W, Omega).
+// Certification gate: residual norms of the k Ritz pairs recomputed from fresh
+// products of the Ritz vectors (TDA: X [k][ov], omega; Casida: U, W, Omega).
 using TdaCert = std::function<std::vector<double>(const double* X, const std::vector<double>& om, int k)>;
 using RpaCert = std::function<std::vector<double>(const double* U, const double* W, const std::vector<double>& om,
                                                   int k)>;
 
-// With a gate: when the re-certified residuals stay above tol although the
-// loop's are below it, the loop's threshold is halved once; if the gate fails
-// again, or the gap between the two residuals alone is half of tol (the
-// products' rounding is then too large for any threshold), the loop restarts
-// from its Ritz vectors on the FP32-accurate operator `acc`, whose residuals
-// are the certified ones.
+// With a gate, the solve converges only when the recomputed residuals are
+// below tol as well; where one is not (the fresh products round differently
+// from the accumulated A V), the loop's threshold is halved and it continues.
 TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, int ng, int k,
                     double tol, int max_iter, int cap, int rounds, Counters& cnt, bool exact_op,
-                    cudaStream_t s, const TdaCert* cert = nullptr, const TdaOp* acc = nullptr) {
+                    cudaStream_t s, const TdaCert* cert = nullptr) {
   TdaOut o;
   if (!exact_op) ++g_inner;
   struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
@@ -304,17 +297,13 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
   bool have_prev = false;
   double* Vp = V.as<double>();
   double* Wp = W.as<double>();
-  const TdaOp* op = &A;
-  bool escalated = false;
-  int gate_fails = 0, it_fail = 0;
-  bool escalate_now = false;
 
   int N = orth_append(Vp, 0, guess, std::min(ng, cap), ov, s);
   TD_REQUIRE(N >= 1, TDDFT_ERR_ARG, "initial guess is empty");
   auto mv = [&](int r0, int m) {
     auto t0 = Clock::now();
     ScopedPhase ph(exact_op ? PH_MV : PH_RIS, s);
-    (*op)(Vp + (size_t)r0 * ov, m, Wp + (size_t)r0 * ov);
+    A(Vp + (size_t)r0 * ov, m, Wp + (size_t)r0 * ov);
     TD_CUDA(cudaStreamSynchronize(s));
     if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
   };
@@ -354,42 +343,15 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
     std::vector<int> todo;
     for (int j = 0; j < kk; ++j)
       if (!(rr[j] < tol_loop)) todo.push_back(j);
-    if (acc && gate_fails > 0 && !escalated && it - it_fail >= kGateWait && !(todo.empty() && kk == k))
-      escalate_now = true;   // the tightened threshold was not reached in time
-    if (escalate_now || (todo.empty() && kk == k)) {
-      if (escalated) {   // the loop's products are the certifying operator's
-        o.cert = 0.0;
-        for (int j = 0; j < kk; ++j) o.cert = std::max(o.cert, rr[j]);
+    if (todo.empty() && kk == k) {
+      if (!cert) { o.converged = true; break; }
+      const std::vector<double> cr = (*cert)(X.as<double>(), om, kk);
+      o.cert = 0.0;
+      for (int j = 0; j < kk; ++j) {
+        o.cert = std::max(o.cert, cr[j]);
+        if (!(cr[j] < tol)) todo.push_back(j);
       }
-      if (!escalate_now && (!cert || escalated)) { o.converged = true; break; }
-      // the gate: converged only when the re-certified residuals are below tol;
-      // otherwise the products' rounding hid the rest, so the loop continues
-      // with a tighter threshold on the roots that failed
-      double gap = 0.0;
-      if (!escalate_now) {
-        const std::vector<double> cr = (*cert)(X.as<double>(), om, kk);
-        o.cert = 0.0;
-        for (int j = 0; j < kk; ++j) {
-          o.cert = std::max(o.cert, cr[j]);
-          if (!(cr[j] < tol)) { todo.push_back(j); gap = std::max(gap, cr[j] - rr[j]); }
-        }
-        if (todo.empty()) { o.converged = true; break; }
-        it_fail = it;
-      }
-      if (acc && (escalate_now || ++gate_fails > 1 || !(gap < 0.5 * tol))) {
-        escalate_now = false;
-        // restart from the Ritz vectors on the accurate operator
-        op = acc;
-        escalated = true;
-        tol_loop = tol;
-        TD_CUDA(cudaMemcpyAsync(tmpk.p, X.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
-        N = orth_append(Vp, 0, tmpk.as<double>(), kk, ov, s);
-        mv(0, N);
-        n_proj = 0;
-        have_prev = false;
-        cnt.restarts++;
-        continue;
-      }
+      if (todo.empty()) { o.converged = true; break; }
       tol_loop *= 0.5;
     }
     if (it == max_iter) break;
@@ -523,8 +485,8 @@ struct PairedLinOut {
   double cert = -1.0;   // largest re-certified relative residual (when a gate was given)
 };
 
-// Re-certification gate of the paired linear systems: the relative residuals
-// of the nr solutions (U, W) recomputed with the FP32-accurate operator.
+// Certification gate of the paired linear systems: the relative residuals of
+// the nr solutions (U, W) recomputed from fresh products.
 template <typename T>
 using LinCert = std::function<std::vector<double>(const T* U, const T* W)>;
 
@@ -536,12 +498,8 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
                            const T* gm, const std::vector<double>& shifts, int nr, T* init, int ni,
                            double tol, int max_iter, int cap, bool exact_op,
                            Counters& cnt, T* Uout, T* Wout, cudaStream_t s,
-                           const LinCert<T>* cert = nullptr, const PairOpT<T>* acc = nullptr) {
+                           const LinCert<T>* cert = nullptr) {
   PairedLinOut o;
-  const PairOpT<T>* opp = &op;
-  bool escalated = false;
-  int gate_fails = 0, it_fail = 0;
-  bool escalate_now = false;
   double tol_loop = tol;
   if (!exact_op) ++g_inner;
   struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
@@ -596,7 +554,7 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
   auto mv = [&](int r0, int m) {
     auto t0 = Clock::now();
     ScopedPhase ph(exact_op ? PH_MV : PH_RIS, s);
-    (*opp)(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
+    op(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
     if (exact_op) {
       TD_CUDA(cudaStreamSynchronize(s));
       cnt.mv += m;
@@ -677,43 +635,16 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
     }
     check_finite_host(rr, "linear-system residuals");
     if (exact_op) trace("polar", it, sp.N, std::vector<double>(), rr);
-    if (acc && gate_fails > 0 && !escalated && it - it_fail >= kGateWait && !todo.empty())
-      escalate_now = true;
-    if (escalate_now || todo.empty()) {
-      if (escalated) {   // the loop's products are the certifying operator's
-        o.cert = 0.0;
-        for (int r = 0; r < nr; ++r) o.cert = std::max(o.cert, rr[r]);
+    if (todo.empty()) {
+      if (!cert) { o.converged = true; break; }
+      // the gate of davidson_tda
+      const std::vector<double> cr = (*cert)(Uout, Wout);
+      o.cert = 0.0;
+      for (int r = 0; r < nr; ++r) {
+        o.cert = std::max(o.cert, cr[r]);
+        if (!(cr[r] <= tol)) todo.push_back(r);
       }
-      if (!escalate_now && (!cert || escalated)) { o.converged = true; break; }
-      // the gate and the escalation of davidson_tda
-      double gap = 0.0;
-      if (!escalate_now) {
-        const std::vector<double> cr = (*cert)(Uout, Wout);
-        o.cert = 0.0;
-        for (int r = 0; r < nr; ++r) {
-          o.cert = std::max(o.cert, cr[r]);
-          if (!(cr[r] <= tol)) { todo.push_back(r); gap = std::max(gap, cr[r] - rr[r]); }
-        }
-        if (todo.empty()) { o.converged = true; break; }
-        it_fail = it;
-      }
-      if (acc && (escalate_now || ++gate_fails > 1 || !(gap < 0.5 * tol))) {
-        escalate_now = false;
-        opp = acc;
-        escalated = true;
-        tol_loop = tol;
-        DevBuf rst((size_t)2 * nr * ov * es, s);
-        TD_CUDA(cudaMemcpyAsync(rst.p, Uout, (size_t)nr * ov * es, cudaMemcpyDeviceToDevice, s));
-        TD_CUDA(cudaMemcpyAsync(rst.as<T>() + (size_t)nr * ov, Wout, (size_t)nr * ov * es,
-                                cudaMemcpyDeviceToDevice, s));
-        sp.N = orth_append<T>(sp.v(), 0, rst.as<T>(), 2 * nr, ov, s);
-        mv(0, sp.N);
-        sp.n_old = 0;
-        sp.n_new = sp.N;
-        have_prev = false;
-        cnt.restarts++;
-        continue;
-      }
+      if (todo.empty()) { o.converged = true; break; }
       tol_loop *= 0.5;
     }
     if (it == max_iter) break;
@@ -783,11 +714,10 @@ struct RpaOut {
   double cert = -1.0;
 };
 
-// The gate and the escalation to `acc` as in davidson_tda (the restart basis
-// is X+Y and X-Y of the wanted roots).
-RpaOut davidson_rpa(int ov, const PairOp& op0, const PairPre& pre, double* guess, int ng, int k,
+// The gate as in davidson_tda.
+RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess, int ng, int k,
                     double tol, int max_iter, int cap, int rounds, Counters& cnt, bool exact_op,
-                    cudaStream_t s, const RpaCert* cert = nullptr, const PairOp* acc = nullptr) {
+                    cudaStream_t s, const RpaCert* cert = nullptr) {
   RpaOut o;
   if (!exact_op) ++g_inner;
   struct Leave { bool on; ~Leave() { if (on) --g_inner; } } leave{!exact_op};
@@ -805,17 +735,13 @@ RpaOut davidson_rpa(int ov, const PairOp& op0, const PairPre& pre, double* guess
   DevBuf gpu_((size_t)k * ov * 8, s), gmu((size_t)k * ov * 8, s), cand((size_t)2 * k * ov * 8, s);
   DevBuf rst((size_t)4 * k * ov * 8, s), Uprev((size_t)k * ov * 8, s), Wprev((size_t)k * ov * 8, s);
   bool have_prev = false;
-  const PairOp* op = &op0;
-  bool escalated = false;
-  int gate_fails = 0, it_fail = 0;
-  bool escalate_now = false;
 
   sp.N = orth_append(sp.v(), 0, guess, std::min(ng, cap), ov, s);
   TD_REQUIRE(sp.N >= 1, TDDFT_ERR_ARG, "initial guess is empty");
   auto mv = [&](int r0, int m) {
     auto t0 = Clock::now();
     ScopedPhase ph(exact_op ? PH_MV : PH_RIS, s);
-    (*op)(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
+    op(sp.v() + (size_t)r0 * ov, m, sp.p() + (size_t)r0 * ov, sp.m() + (size_t)r0 * ov);
     TD_CUDA(cudaStreamSynchronize(s));
     if (exact_op) { cnt.mv += m; cnt.t_mv += since(t0); } else { cnt.ris_mv += m; }
   };
@@ -870,41 +796,15 @@ RpaOut davidson_rpa(int ov, const PairOp& op0, const PairPre& pre, double* guess
     }
     check_finite_host(rr, "Casida residual norms");
     trace(exact_op ? "rpa" : "rpa-guess", it, N, om, rr);
-    if (acc && gate_fails > 0 && !escalated && it - it_fail >= kGateWait && !(todo.empty() && kk == k))
-      escalate_now = true;
-    if (escalate_now || (todo.empty() && kk == k)) {
-      if (escalated) {
-        o.cert = 0.0;
-        for (int j = 0; j < kk; ++j) o.cert = std::max(o.cert, rr[j]);
+    if (todo.empty() && kk == k) {
+      if (!cert) { o.converged = true; break; }
+      const std::vector<double> cr = (*cert)(U.as<double>(), W.as<double>(), om, kk);
+      o.cert = 0.0;
+      for (int j = 0; j < kk; ++j) {
+        o.cert = std::max(o.cert, cr[j]);
+        if (!(cr[j] < tol)) todo.push_back(j);
       }
-      if (!escalate_now && (!cert || escalated)) { o.converged = true; break; }
-      double gap = 0.0;
-      if (!escalate_now) {
-        const std::vector<double> cr = (*cert)(U.as<double>(), W.as<double>(), om, kk);
-        o.cert = 0.0;
-        for (int j = 0; j < kk; ++j) {
-          o.cert = std::max(o.cert, cr[j]);
-          if (!(cr[j] < tol)) { todo.push_back(j); gap = std::max(gap, cr[j] - rr[j]); }
-        }
-        if (todo.empty()) { o.converged = true; break; }
-        it_fail = it;
-      }
-      if (acc && (escalate_now || ++gate_fails > 1 || !(gap < 0.5 * tol))) {
-        escalate_now = false;
-        op = acc;
-        escalated = true;
-        tol_loop = tol;
-        TD_CUDA(cudaMemcpyAsync(rst.p, U.p, (size_t)kk * ov * 8, cudaMemcpyDeviceToDevice, s));
-        TD_CUDA(cudaMemcpyAsync(rst.as<double>() + (size_t)kk * ov, W.p, (size_t)kk * ov * 8,
-                                cudaMemcpyDeviceToDevice, s));
-        sp.N = orth_append(sp.v(), 0, rst.as<double>(), 2 * kk, ov, s);
-        mv(0, sp.N);
-        sp.n_old = 0;
-        sp.n_new = sp.N;
-        have_prev = false;
-        cnt.restarts++;
-        continue;
-      }
+      if (todo.empty()) { o.converged = true; break; }
       tol_loop *= 0.5;
     }
     if (it == max_iter) break;
@@ -1078,11 +978,6 @@ Plan make_plan(const Ctx& c, const tddft_opts& o) {
   return p;
 }
 
-// The re-certification's operator form: the FP32-accurate three-part tensor-core
-// products after a tensor-core solve (when their stage-1 tiles fit), else the
-// FP32 SIMT contractions.
-int cert_tc(const Ctx& c, const Plan& p) { return (p.tc && tc_stage1_3_fits(c.no)) ? 2 : 0; }
-
 void fill_stats(tddft_stats* st, int n_iter, const Counters& cnt, bool conv,
                 const std::vector<double>& resid, double cert, Clock::time_point t0) {
   if (!st) return;
@@ -1167,15 +1062,14 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     guess = DevBuf((size_t)p.k0 * ov * 8, s);
     unit_rows(guess.as<double>(), p.k0, ov, c.order.as<int>(), s);
   }
-  // MIXED: the converged residuals are re-checked with an FP32-accurate
-  // operator (the three-part BF16 tensor-core products after a tensor-core
-  // solve, else the FP32 SIMT contractions); the solve converges only when they
-  // are below tol
-  const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 factors and their three-part BF16 split
+  // MIXED certification: the converged residuals recomputed from fresh
+  // products of the Ritz vectors with the solve's FP32-accurate operator (FP16
+  // hi+lo tensor-core or FP32 SIMT contractions), FP64 norms; the solve
+  // converges only when they are below tol too
   TdaCert certify = [&](const double* Xc, const std::vector<double>& omv, int k) {
     auto tc0 = Clock::now();
     DevBuf AX((size_t)k * ov * 8, s), R((size_t)k * ov * 8, s), rn(k * 8, s), om(k * 8, s);
-    apply_operator(dims, Fc, Xc, k, OpMode::TDA, AX.as<double>(), nullptr, cert_tc(c, p), s);
+    A(Xc, k, AX.as<double>());
     h2d(om.as<double>(), std::vector<double>(omv.begin(), omv.begin() + k), s);
     resid_tda(Xc, AX.as<double>(), om.as<double>(), k, ov, R.as<double>(), s);
     row_sumsq(R.as<double>(), ov, k, ov, rn.as<double>(), s);
@@ -1183,12 +1077,8 @@ tddft_status run_tda(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     cnt.t_cert += since(tc0);
     return v;
   };
-  TdaOp Acc = [&](const double* Xi, int m, double* out) {
-    apply_operator(dims, Fc, Xi, m, OpMode::TDA, out, nullptr, cert_tc(c, p), s);
-  };
   TdaOut r = davidson_tda(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, guess.as<double>(), ng,
-                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s, p.mixed ? &certify : nullptr,
-                          p.mixed ? &Acc : nullptr);
+                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s, p.mixed ? &certify : nullptr);
   double cert = r.cert;
   if (p.mixed && cert < 0.0)   // not converged: report the re-checked residuals of the last Ritz pairs
     for (double v : certify(r.X.as<double>(), r.omega, (int)r.omega.size())) cert = std::max(cert, v);
@@ -1294,14 +1184,14 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     guess = DevBuf((size_t)p.k0 * ov * 8, s);
     unit_rows(guess.as<double>(), p.k0, ov, c.order.as<int>(), s);
   }
-  const FactorSet Fc = c.exact(TDDFT_MIXED);  // FP32 factors and their three-part BF16 split
+  // MIXED certification as in run_tda
   RpaCert certify = [&](const double* Uc, const double* Wc, const std::vector<double>& omv, int k) {
     auto tc0 = Clock::now();
     DevBuf PU((size_t)k * ov * 8, s), MU((size_t)k * ov * 8, s), PW((size_t)k * ov * 8, s),
         MW((size_t)k * ov * 8, s), Rp((size_t)k * ov * 8, s), Rm((size_t)k * ov * 8, s);
     DevBuf a1(k * 8, s), a2(k * 8, s), om(k * 8, s);
-    apply_operator(dims, Fc, Uc, k, OpMode::PAIRED, PU.as<double>(), MU.as<double>(), cert_tc(c, p), s);
-    apply_operator(dims, Fc, Wc, k, OpMode::PAIRED, PW.as<double>(), MW.as<double>(), cert_tc(c, p), s);
+    A(Uc, k, PU.as<double>(), MU.as<double>());
+    A(Wc, k, PW.as<double>(), MW.as<double>());
     h2d(om.as<double>(), std::vector<double>(omv.begin(), omv.begin() + k), s);
     resid_paired<double>(Uc, Wc, PU.as<double>(), MW.as<double>(), om.as<double>(), nullptr, nullptr, k, ov,
                          Rp.as<double>(), Rm.as<double>(), s);
@@ -1313,12 +1203,8 @@ tddft_status run_rpa(Ctx& c, const tddft_opts& o, double* omega, double* X, doub
     cnt.t_cert += since(tc0);
     return v;
   };
-  PairOp Acc = [&](const double* Xi, int m, double* P, double* M) {
-    apply_operator(dims, Fc, Xi, m, OpMode::PAIRED, P, M, cert_tc(c, p), s);
-  };
   RpaOut r = davidson_rpa(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag, guess.as<double>(), ng,
-                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s, p.mixed ? &certify : nullptr,
-                          p.mixed ? &Acc : nullptr);
+                          p.k, p.tol, p.max_iter, p.cap, p.rounds, cnt, true, s, p.mixed ? &certify : nullptr);
   double cert = r.cert;
   if (p.mixed && cert < 0.0)
     for (double v : certify(r.U.as<double>(), r.W.as<double>(), r.omega, (int)r.omega.size())) cert = std::max(cert, v);
@@ -1417,12 +1303,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
     precond_paired<double>(b.as<double>(), nullptr, shd.as<double>(), dl, nr, ov, iu, iw, s);
   }
   DevBuf U((size_t)nr * ov * 8, s), W((size_t)nr * ov * 8, s);
-  // MIXED: the converged residuals are re-checked with the FP32-accurate
-  // operator, as in run_tda
-  const FactorSet Fc = c.exact(TDDFT_MIXED);
-  PairOp Acc = [&](const double* Xi, int m, double* P, double* M) {
-    apply_operator(dims, Fc, Xi, m, OpMode::PAIRED, P, M, cert_tc(c, p), s);
-  };
+  // MIXED certification as in run_tda (relative residuals)
   DevBuf rhs_norm(nr * 8, s);
   row_sumsq(b.as<double>(), ov, nr, ov, rhs_norm.as<double>(), s);
   const std::vector<double> bn = sqrt_all(d2h(rhs_norm.as<double>(), nr, s));
@@ -1431,8 +1312,8 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
     DevBuf PU((size_t)nr * ov * 8, s), MU((size_t)nr * ov * 8, s), PW((size_t)nr * ov * 8, s),
         MW((size_t)nr * ov * 8, s), Rp((size_t)nr * ov * 8, s), Rm((size_t)nr * ov * 8, s);
     DevBuf a1(nr * 8, s), a2(nr * 8, s);
-    Acc(Uc, nr, PU.as<double>(), MU.as<double>());
-    Acc(Wc, nr, PW.as<double>(), MW.as<double>());
+    A(Uc, nr, PU.as<double>(), MU.as<double>());
+    A(Wc, nr, PW.as<double>(), MW.as<double>());
     resid_paired<double>(Uc, Wc, PU.as<double>(), MW.as<double>(), shd.as<double>(), b.as<double>(), nullptr, nr,
                          ov, Rp.as<double>(), Rm.as<double>(), s);
     row_sumsq(Rp.as<double>(), ov, nr, ov, a1.as<double>(), s);
@@ -1446,7 +1327,7 @@ tddft_status run_polar(Ctx& c, const tddft_opts& o, const double* mu, int n_dip,
   PairedLinOut r = paired_linear<double>(ov, A, p.precond == TDDFT_PRECOND_RID ? rid : diag,
                                          b.as<double>(), nullptr, sh, nr, iu, 2 * nr, p.tol, p.max_iter,
                                          p.cap, true, cnt, U.as<double>(), W.as<double>(), s,
-                                         p.mixed ? &certify : nullptr, p.mixed ? &Acc : nullptr);
+                                         p.mixed ? &certify : nullptr);
   double cert = r.cert;
   if (p.mixed && cert < 0.0)
     for (double v : certify(U.as<double>(), W.as<double>())) cert = std::max(cert, v);

@@ -5,10 +5,15 @@
 //   K2[(n,i)][a] = sum_P sum_j Q[(n,i)][P][j] L^P_ja      ((ib|ja) term, k = j)
 // K1's contraction is the dominant cost of every product (about 70-90% of flops).
 //
-// Exact operator: operands split into BF16 hi + lo parts (x = hi + lo to ~2^-17);
-// each tile pair contributes hi*hi + hi*lo + lo*hi (the lo*lo term is below the
-// FP32 accumulator's resolution), so the product has ~FP32 accuracy at BF16
-// tensor-core rate.  ris operator: one BF16 product (its factors are BF16).
+// Exact operator: every operand is scaled by a power of two s (so that
+// max |s x| <= 2^14, or below 2^15 from a Cauchy-Schwarz bound for the stage-1
+// results) and split into FP16 hi + lo parts, x s = hi + lo to ~2^-22 (11
+// significand bits each; s keeps the lo parts of all but the negligible
+// elements above FP16's normal range); each tile pair contributes
+// hi*hi + hi*lo + lo*hi (lo*lo is below 2^-22), FP32 accumulation, and the
+// sum is multiplied by 1 / (s_A s_B): an FP32-accurate product at the FP16
+// tensor-core rate.  ris operator: BF16 factors (no scaling), the trial
+// vectors as BF16 hi + lo.
 //
 // Layout / mapping (all K-major, so both operands stream along k):
 //   A viewed as a 3-D tensor (k: Kin, P: pn, row: M), row pitch pn*ldk
@@ -45,25 +50,25 @@ constexpr int BN = 256;                      // 128 x 256 MMA tiles (full tcgen0
 constexpr int BK = 64;                       // bf16 elements per 128-byte row
 constexpr int A_BYTES = BM * 128;             // 16 KB per hi or lo tile (128-byte rows)
 constexpr int B_BYTES = BN * 128;
-// Operand element types of the contraction: BF16 (kind::f16, 64 elements per
-// 128-byte row) or FP8 e4m3 (kind::f8f6f4, 128 elements per row).  Either way
-// one tcgen05.mma consumes 32 bytes of K, so the descriptors advance alike.
-template <bool F8> struct Elem {
-  static constexpr int BKE = F8 ? 128 : 64;
-  static constexpr uint32_t TYPE_BITS = F8 ? 0u : ((1u << 7) | (1u << 10));   // A, B: E4M3 = 0 / BF16 = 1
+// Operand element types of the contraction: BF16 or FP16 (kind::f16, 64
+// elements per 128-byte row) or FP8 e4m3 (kind::f8f6f4, 128 elements per row).
+// Either way one tcgen05.mma consumes 32 bytes of K, so the descriptors
+// advance alike.
+enum ElemType : int { ET_BF16 = 0, ET_F16 = 1, ET_E4M3 = 2 };
+template <int ET> struct Elem {
+  static constexpr int BKE = ET == ET_E4M3 ? 128 : 64;
+  // instruction-descriptor A and B type fields: kind::f16 F16 = 0, BF16 = 1; kind::f8f6f4 E4M3 = 0
+  static constexpr uint32_t TYPE_BITS = ET == ET_BF16 ? ((1u << 7) | (1u << 10)) : 0u;
 };
-// Operand split modes: SINGLE = one BF16 product; BOTH = A and B as hi + lo
-// (hi*hi + hi*lo + lo*hi); ASPLIT = A as hi + lo, B a plain BF16 operand
+constexpr int elem_of(TcElt e) { return e == TcElt::F16 ? ET_F16 : ET_BF16; }
+// Operand split modes: SINGLE = one product; BOTH = A and B as hi + lo
+// (hi*hi + hi*lo + lo*hi); ASPLIT = A as hi + lo, B a plain operand
 // (hi*B + lo*B: exact with respect to B, e.g. FP32 vectors against BF16 ris factors).
-// CROSS = A and B as two parts each, only the two cross products A0 B1 + A1 B0
-// (one pass of the three-part split below); TRIPLE (stage 1 only) = A and B
-// as three BF16 parts x = x0 + x1 + x2 (24 significand bits), the six
-// products down to 2^-18 of the leading one: 00 + 01 + 10 + 02 + 20 + 11.
-enum SplitMode : int { SINGLE = 0, BOTH = 1, ASPLIT = 2, CROSS = 3, TRIPLE = 4 };
+enum SplitMode : int { SINGLE = 0, BOTH = 1, ASPLIT = 2 };
 __host__ __device__ constexpr bool a_split(int m) { return m != SINGLE; }
-__host__ __device__ constexpr bool b_split(int m) { return m == BOTH || m == CROSS || m == TRIPLE; }
-__host__ __device__ constexpr int n_parts_a(int m) { return m == TRIPLE ? 3 : (a_split(m) ? 2 : 1); }
-__host__ __device__ constexpr int n_parts_b(int m) { return m == TRIPLE ? 3 : (b_split(m) ? 2 : 1); }
+__host__ __device__ constexpr bool b_split(int m) { return m == BOTH; }
+__host__ __device__ constexpr int n_parts_a(int m) { return a_split(m) ? 2 : 1; }
+__host__ __device__ constexpr int n_parts_b(int m) { return b_split(m) ? 2 : 1; }
 
 template <int MODE> struct Cfg {
   static constexpr int STAGE_BYTES = n_parts_a(MODE) * A_BYTES + n_parts_b(MODE) * B_BYTES;
@@ -129,25 +134,26 @@ __device__ __forceinline__ uint64_t sdesc(const void* p) {
          (2ull << 61);
 }
 
-// Instruction descriptor: D = F32, A and B of the same type (BF16 for
-// kind::f16, E4M3 for kind::f8f6f4), both K-major, M = 128, N = BN.
-template <bool F8>
-constexpr uint32_t idesc_of() {
-  return (1u << 4) | Elem<F8>::TYPE_BITS | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: D = F32, A and B of the same type (BF16 or FP16
+// for kind::f16, E4M3 for kind::f8f6f4), both K-major, M = 128, N = nb.
+template <int ET>
+__host__ __device__ constexpr uint32_t idesc_of(int nb = BN) {
+  return (1u << 4) | Elem<ET>::TYPE_BITS | ((uint32_t)(nb >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-template <bool F8>
-__device__ __forceinline__ void mma_op(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accum) {
-  if constexpr (F8) {
+template <int ET>
+__device__ __forceinline__ void mma_op(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accum,
+                                       uint32_t idesc = idesc_of<ET>()) {
+  if constexpr (ET == ET_E4M3) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(idesc_of<true>()), "r"(accum));
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
   } else {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(idesc_of<false>()), "r"(accum));
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
   }
 }
 
@@ -192,7 +198,7 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 // B tile, so each loads half of its rows and multicasts them to both (halving
 // each SM's B traffic), and a stage is refilled only after both CTAs' MMAs
 // have read it (their commits arrive on both CTAs' `empty` barriers).
-template <int MODE, bool F8, int CL = 1>
+template <int MODE, int ET, int CL = 1>
 __global__ void __launch_bounds__(THREADS, 1)
 k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
              const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
@@ -238,7 +244,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
       if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicOr(p.err, 1); ok = false; break; }
       const int kb = k_begin + i;
-      const int P = kb / p.nab, a0 = (kb - P * p.nab) * Elem<F8>::BKE;
+      const int P = kb / p.nab, a0 = (kb - P * p.nab) * Elem<ET>::BKE;
       unsigned char* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
       tma_load_3d(st, &mA_hi, &full[s], a0, P, m0);
@@ -276,14 +282,9 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 32 bytes along K per MMA
-        if constexpr (MODE == CROSS) {
-          mma_op<F8>(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, (i > 0 || kk > 0) ? 1u : 0u);
-          mma_op<F8>(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u);
-        } else {
-          mma_op<F8>(tmem, ah + off, bh + off, (i > 0 || kk > 0) ? 1u : 0u);
-          if (b_split(MODE)) mma_op<F8>(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, 1u);
-          if (a_split(MODE)) mma_op<F8>(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u);
-        }
+        mma_op<ET>(tmem, ah + off, bh + off, (i > 0 || kk > 0) ? 1u : 0u);
+        if (b_split(MODE)) mma_op<ET>(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, 1u);
+        if (a_split(MODE)) mma_op<ET>(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u);
       }
       if constexpr (CL > 1) mma_commit_mc(&empty[s], (uint16_t)0x3);
       else mma_commit(&empty[s]);
@@ -359,12 +360,11 @@ struct S1Params {
   int nb;              // MMA N (multiple of 16, >= N)
   int acc_cols;        // TMEM columns per accumulator buffer
   int stages, stage_bytes, a_bytes, b_bytes;
-  __nv_bfloat16* out_hi;
-  __nv_bfloat16* out_lo;
-  __nv_bfloat16* out_l2;   // TRIPLE: third part of the output split
-  // FP8 output (OUT8): e4m3 hi + lo bytes of mu[P] * C_P, row pitch ldo bytes
-  unsigned char* out8_hi;
-  unsigned char* out8_lo;
+  void* out_hi;        // BF16 / FP16 parts (2-byte elements) or e4m3 bytes
+  void* out_lo;
+  // FP16 output: the accumulator times *mul before its split; FP8 output:
+  // times mu[P] (one scale per auxiliary row)
+  const float* mul;
   const float* mu;
   int* err;
 };
@@ -376,11 +376,10 @@ __device__ __forceinline__ float from_e4m3(unsigned char q) {
   return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3)));
 }
 
-template <int MODE, bool OUT8>
+template <int MODE, int IN, int OUT>
 __global__ void __launch_bounds__(S1_THREADS, 1)
 k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
             const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
-            const __grid_constant__ CUtensorMap mA_l2, const __grid_constant__ CUtensorMap mB_l2,
             S1Params p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -395,8 +394,7 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
   const int m0 = blockIdx.x * BM;
   const int P0 = blockIdx.y * p.ppc;
   const int nP = max(0, min(p.pn, P0 + p.ppc) - P0);
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(p.nb >> 3) << 17) |
-                         ((uint32_t)(BM >> 4) << 24);
+  const uint32_t idesc = idesc_of<IN>(p.nb);
   const int b_off = n_parts_a(MODE) * p.a_bytes;
 
   if (threadIdx.x == 0) {
@@ -425,10 +423,6 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
       tma_load_3d(st + b_off, &mB_hi, &full[s], k0, 0, P);
       if (a_split(MODE)) tma_load_3d(st + p.a_bytes, &mA_lo, &full[s], k0, m0, 0);
       if (b_split(MODE)) tma_load_3d(st + b_off + p.b_bytes, &mB_lo, &full[s], k0, 0, P);
-      if (MODE == TRIPLE) {
-        tma_load_3d(st + 2 * p.a_bytes, &mA_l2, &full[s], k0, m0, 0);
-        tma_load_3d(st + b_off + 2 * p.b_bytes, &mB_l2, &full[s], k0, 0, P);
-      }
     }
     for (int i = max(0, nsteps - p.stages); i < nsteps; ++i)
       if (!mbar_wait(&full[i % p.stages], (uint32_t)(i / p.stages) & 1u)) { atomicOr(p.err, 32); break; }
@@ -449,36 +443,9 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
           const uint64_t off = (uint64_t)(kk * 32) >> 4;
-          asm volatile(
-              "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
-              "l"(ah + off), "l"(bh + off), "r"(idesc), "r"((kb > 0 || kk > 0) ? 1u : 0u));
-          if (b_split(MODE)) {
-            const uint64_t bl = sdesc(st + b_off + p.b_bytes);
-            asm volatile(
-                "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
-                "l"(ah + off), "l"(bl + off), "r"(idesc), "r"(1u));
-          }
-          if (a_split(MODE)) {
-            const uint64_t al = sdesc(st + p.a_bytes);
-            asm volatile(
-                "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
-                "l"(al + off), "l"(bh + off), "r"(idesc), "r"(1u));
-          }
-          if (MODE == TRIPLE) {   // A0 B2 + A2 B0 + A1 B1
-            const uint64_t a2 = sdesc(st + 2 * p.a_bytes), b2 = sdesc(st + b_off + 2 * p.b_bytes);
-            const uint64_t a1 = sdesc(st + p.a_bytes), b1 = sdesc(st + b_off + p.b_bytes);
-            const uint64_t pa[3] = {ah + off, a2 + off, a1 + off};
-            const uint64_t pb[3] = {b2 + off, bh + off, b1 + off};
-#pragma unroll
-            for (int t = 0; t < 3; ++t)
-              asm volatile(
-                  "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc),
-                  "l"(pa[t]), "l"(pb[t]), "r"(idesc), "r"(1u));
-          }
+          mma_op<IN>(acc, ah + off, bh + off, (kb > 0 || kk > 0) ? 1u : 0u, idesc);
+          if (b_split(MODE)) mma_op<IN>(acc, ah + off, sdesc(st + b_off + p.b_bytes) + off, 1u, idesc);
+          if (a_split(MODE)) mma_op<IN>(acc, sdesc(st + p.a_bytes) + off, bh + off, 1u, idesc);
         }
         mma_commit(&empty[s]);
       }
@@ -492,6 +459,7 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
     const int r = m0 + q * 32 + lane;
     const int g = r / p.R, ri = r - (r / p.R) * p.R;
     const size_t cs = (size_t)p.pn * p.ldo;   // output stride between consecutive columns
+    const float mul = OUT == ET_F16 ? *p.mul : 1.f;
     for (int j = 0; j < nP; ++j) {
       const int buf = j & 1;
       bool ok = mbar_wait(&tfull[buf], (uint32_t)(j >> 1) & 1u);
@@ -513,10 +481,10 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
         if (r < p.M) {
           const size_t base = (((size_t)g * p.N + c0) * p.pn + P) * p.ldo + ri;
           const int nc = min(16, p.N - c0);
-          if constexpr (OUT8) {
+          if constexpr (OUT == ET_E4M3) {
             const float mu = p.mu[P];
-            unsigned char* oh = p.out8_hi + base;
-            unsigned char* ol = p.out8_lo + base;
+            unsigned char* oh = static_cast<unsigned char*>(p.out_hi) + base;
+            unsigned char* ol = static_cast<unsigned char*>(p.out_lo) + base;
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
               if (t < nc) {
@@ -526,21 +494,28 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
                 ol[t * cs] = to_e4m3(x - from_e4m3(h));
               }
             }
+          } else if constexpr (OUT == ET_F16) {
+            __half* oh = static_cast<__half*>(p.out_hi) + base;
+            __half* ol = static_cast<__half*>(p.out_lo) + base;
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+              if (t < nc) {
+                const float x = __uint_as_float(v[t]) * mul;
+                const __half h = __float2half_rn(x);
+                oh[t * cs] = h;
+                ol[t * cs] = __float2half_rn(x - __half2float(h));
+              }
+            }
           } else {
-            __nv_bfloat16* oh = p.out_hi + base;
-            __nv_bfloat16* ol = a_split(MODE) ? p.out_lo + base : nullptr;
+            __nv_bfloat16* oh = static_cast<__nv_bfloat16*>(p.out_hi) + base;
+            __nv_bfloat16* ol = a_split(MODE) ? static_cast<__nv_bfloat16*>(p.out_lo) + base : nullptr;
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
               if (t < nc) {
                 const float x = __uint_as_float(v[t]);
                 const __nv_bfloat16 h = __float2bfloat16_rn(x);
                 oh[t * cs] = h;
-                if (a_split(MODE)) {
-                  const float r1 = x - __bfloat162float(h);
-                  const __nv_bfloat16 l = __float2bfloat16_rn(r1);
-                  ol[t * cs] = l;
-                  if (MODE == TRIPLE) p.out_l2[base + t * cs] = __float2bfloat16_rn(r1 - __bfloat162float(l));
-                }
+                if (a_split(MODE)) ol[t * cs] = __float2bfloat16_rn(x - __bfloat162float(h));
               }
             }
           }
@@ -581,42 +556,29 @@ __global__ void k_sum_splits(const float* __restrict__ part, int S, long long MN
   }
 }
 
-// FP32 Z [M][pn*nv] -> BF16 hi/lo [M][pn][nvp] (row pitch padded to 16 bytes, pads zero)
-__global__ void k_split_pad(const float* __restrict__ Z, int M, int pn, int nv, int nvp,
-                            __nv_bfloat16* hi, __nv_bfloat16* lo) {
-  const long long tot = (long long)M * pn * nvp;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(t % nvp);
-    const long long rp = t / nvp;   // row * pn + P
-    float v = 0.f;
-    if (a < nv) v = Z[rp * nv + a];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[t] = h;
-    if (lo) lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
-  }
+// Split of x (converted to FP32, times *scale when given) into two 16-bit
+// parts hi = round(x), lo = round(x - hi) of the element type E (BF16 or
+// FP16); lo optional.
+template <typename E> __device__ __forceinline__ E to_elem(float x);
+template <> __device__ __forceinline__ __nv_bfloat16 to_elem<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ __half to_elem<__half>(float x) { return __float2half_rn(x); }
+__device__ __forceinline__ float from_elem(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float from_elem(__half x) { return __half2float(x); }
+
+template <typename E>
+__device__ __forceinline__ void split_store(float v, long long t, E* hi, E* lo) {
+  const E h = to_elem<E>(v);
+  hi[t] = h;
+  if (lo) lo[t] = to_elem<E>(v - from_elem(h));
 }
 
 // Transpose + split of factor rows: src [rows][n1][n2] -> dst [rows][n2][pad8(n1)]
-// (dst[r][b][a] = src[r][a][b]; pads zero).  lo may be NULL (plain BF16).
-// Split of x (converted to FP32) into BF16 parts: hi = bf16(x), lo = bf16(x - hi),
-// l2 = bf16(x - hi - lo) (lo, l2 optional).
-__device__ __forceinline__ void split_store(float v, long long t, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                                            __nv_bfloat16* l2) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  hi[t] = h;
-  if (lo) {
-    const float r1 = v - __bfloat162float(h);
-    const __nv_bfloat16 l = __float2bfloat16_rn(r1);
-    lo[t] = l;
-    if (l2) l2[t] = __float2bfloat16_rn(r1 - __bfloat162float(l));
-  }
-}
-
-template <typename TS>
+// (dst[r][b][a] = src[r][a][b]; pads zero).  lo may be NULL (one part).
+template <typename TS, typename E>
 __global__ void k_transpose_split(const TS* __restrict__ src, int rows, int n1, int n2, int ld,
-                                  __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* l2) {
+                                  const float* __restrict__ scale, E* hi, E* lo) {
   const long long tot = (long long)rows * n2 * ld;
+  const float sc = scale ? *scale : 1.f;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x) {
     const int a = (int)(t % ld);
@@ -624,8 +586,8 @@ __global__ void k_transpose_split(const TS* __restrict__ src, int rows, int n1, 
     const int b = (int)(rb % n2);
     const long long r = rb / n2;
     float v = 0.f;
-    if (a < n1) v = (float)src[(r * n1 + a) * n2 + b];
-    split_store(v, t, hi, lo, l2);
+    if (a < n1) v = (float)src[(r * n1 + a) * n2 + b] * sc;
+    split_store<E>(v, t, hi, lo);
   }
 }
 
@@ -647,13 +609,17 @@ EncodeFn encode_fn() {
   return fn;
 }
 
+// 3-D tiled map with 128-byte swizzle over elements of type et (ET_BF16,
+// ET_F16 or ET_E4M3, the last as bytes).
 CUtensorMap make_map(const void* base, const cuuint64_t dims[3], const cuuint64_t strides[2],
-                     const cuuint32_t box[3], bool u8 = false) {
+                     const cuuint32_t box[3], int et = ET_BF16) {
   TD_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0, TDDFT_ERR_ARG, "TMA base not 16-byte aligned");
   TD_REQUIRE(strides[0] % 16 == 0 && strides[1] % 16 == 0, TDDFT_ERR_ARG, "TMA strides not 16-byte multiples");
   CUtensorMap m;
   const cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = encode_fn()(&m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+  const CUtensorMapDataType dt = et == ET_E4M3 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                 : (et == ET_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  CUresult r = encode_fn()(&m, dt, 3,
                            const_cast<void*>(base), dims, strides,
                            box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -666,29 +632,31 @@ CUtensorMap make_map(const void* base, const cuuint64_t dims[3], const cuuint64_
 int tc_pad(int nv) { return (nv + 7) & ~7; }
 int tc_pad16(int n) { return (n + 15) & ~15; }
 
-void tc_split_pad(const float* Z, int M, int pn, int nv, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                  cudaStream_t s) {
-  const long long tot = (long long)M * pn * tc_pad(nv);
-  long long g = (tot + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
-  k_split_pad<<<(unsigned)g, 256, 0, s>>>(Z, M, pn, nv, tc_pad(nv), hi, lo);
-  count_launch();
-  TD_LAUNCH_CHECK();
-}
-
-void tc_transpose_split(const void* src, DType ts, int rows, int n1, int n2, __nv_bfloat16* hi,
-                        __nv_bfloat16* lo, cudaStream_t s, __nv_bfloat16* l2) {
+namespace {
+template <typename E>
+void transpose_split_t(const void* src, DType ts, int rows, int n1, int n2, const float* scale, E* hi, E* lo,
+                       cudaStream_t s) {
   const int ld = tc_pad(n1);
   const long long tot = (long long)rows * n2 * ld;
   long long g = (tot + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
   if (ts == DType::F32)
-    k_transpose_split<float><<<(unsigned)g, 256, 0, s>>>((const float*)src, rows, n1, n2, ld, hi, lo, l2);
+    k_transpose_split<float, E><<<(unsigned)g, 256, 0, s>>>((const float*)src, rows, n1, n2, ld, scale, hi, lo);
   else if (ts == DType::BF16)
-    k_transpose_split<__nv_bfloat16><<<(unsigned)g, 256, 0, s>>>((const __nv_bfloat16*)src, rows, n1, n2,
-                                                                 ld, hi, lo, l2);
+    k_transpose_split<__nv_bfloat16, E><<<(unsigned)g, 256, 0, s>>>((const __nv_bfloat16*)src, rows, n1, n2, ld,
+                                                                    scale, hi, lo);
   else
-    k_transpose_split<double><<<(unsigned)g, 256, 0, s>>>((const double*)src, rows, n1, n2, ld, hi, lo, l2);
+    k_transpose_split<double, E><<<(unsigned)g, 256, 0, s>>>((const double*)src, rows, n1, n2, ld, scale, hi, lo);
+}
+}  // namespace
+
+void tc_transpose_split(const void* src, DType ts, int rows, int n1, int n2, void* hi, void* lo, TcElt et,
+                        const float* scale, cudaStream_t s) {
+  TD_REQUIRE(et == TcElt::F16 || scale == nullptr, TDDFT_ERR_ARG, "tc_transpose_split: BF16 parts take no scale");
+  if (et == TcElt::F16)
+    transpose_split_t<__half>(src, ts, rows, n1, n2, scale, (__half*)hi, (__half*)lo, s);
+  else
+    transpose_split_t<__nv_bfloat16>(src, ts, rows, n1, n2, scale, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, s);
   count_launch();
   TD_LAUNCH_CHECK();
 }
@@ -739,12 +707,12 @@ bool cluster_pairs_enabled() {
 
 // CTAs of the paired contraction that can be resident at once: two per
 // co-resident cluster (an SM left over in a GPC takes no pair).
-int pair_slots(int mode) {
+int pair_slots(int et) {
   static int cached[2] = {0, 0};
-  int& c = cached[mode == CROSS ? 1 : 0];
+  int& c = cached[et == ET_F16 ? 1 : 0];
   if (c == 0) {
-    const void* k = mode == CROSS ? (const void*)k1_tc_kernel<CROSS, false, 2> : (const void*)k1_tc_kernel<BOTH, false, 2>;
-    const int smem = mode == CROSS ? Cfg<CROSS>::SMEM_BYTES : Cfg<BOTH>::SMEM_BYTES;
+    const void* k = et == ET_F16 ? (const void*)k1_tc_kernel<BOTH, ET_F16, 2> : (const void*)k1_tc_kernel<BOTH, ET_BF16, 2>;
+    const int smem = Cfg<BOTH>::SMEM_BYTES;
     ensure_smem(k, smem);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
@@ -768,14 +736,13 @@ int pair_slots(int mode) {
 }
 }  // namespace
 
-void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int pn, int Kin,
-                 const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, float* out,
-                 bool accumulate, int* err, cudaStream_t s, KernelProfile* prof, double prof_flops,
-                 double prof_bytes, bool cross) {
+void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const void* Bhi, const void* Blo,
+                 int N, float* out, bool accumulate, TcElt elt, const float* scale, int* err, cudaStream_t s,
+                 KernelProfile* prof, double prof_flops, double prof_bytes) {
   if (M <= 0 || pn <= 0 || N <= 0) return;
   TD_REQUIRE(Alo != nullptr || Blo == nullptr, TDDFT_ERR_ARG, "tc_contract: B split without A split");
-  TD_REQUIRE(!cross || (Alo && Blo), TDDFT_ERR_ARG, "tc_contract: cross products need both splits");
-  const int mode = cross ? CROSS : (Alo ? (Blo ? BOTH : ASPLIT) : SINGLE);
+  const int et = elem_of(elt);
+  const int mode = Alo ? (Blo ? BOTH : ASPLIT) : SINGLE;
   const int ldk = tc_pad(Kin);
   const int nab = (Kin + BK - 1) / BK;
   const int total = pn * nab;
@@ -783,11 +750,11 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
   // split-B products in pairs of M tiles that share each B tile through a
   // cluster multicast (TDDFT_TC_CLUSTER=0 turns this off; the results are the
   // same bits either way: every CTA issues the same MMAs on the same data)
-  const bool pair = (mode == BOTH || mode == CROSS) && mt0 > 1 && cluster_pairs_enabled();
+  const bool pair = mode == BOTH && mt0 > 1 && cluster_pairs_enabled();
   const int mt = pair ? (mt0 + 1) & ~1 : mt0;
   // a CTA's fixed cost (barriers, TMEM, pipeline fill, 128 KB epilogue) is about
   // four k-blocks of MMA work
-  int splits = wave_splits(mt * nt, total, 4, pair ? pair_slots(mode) : 0);
+  int splits = wave_splits(mt * nt, total, 4, pair ? pair_slots(et) : 0);
   const int per = (total + splits - 1) / splits;
   splits = (total + per - 1) / per;
 
@@ -797,9 +764,9 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
   const cuuint64_t dB[3] = {(cuuint64_t)Kin, (cuuint64_t)N, (cuuint64_t)pn};
   const cuuint64_t sB[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)N * ldk * 2};
   const cuuint32_t bB[3] = {BK, (cuuint32_t)(pair ? BN / 2 : BN), 1};   // a pair loads half a B tile each
-  CUtensorMap mAh = make_map(Ahi, dA, sA, bA), mBh = make_map(Bhi, dB, sB, bB);
-  CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA) : mAh;
-  CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB) : mBh;
+  CUtensorMap mAh = make_map(Ahi, dA, sA, bA, et), mBh = make_map(Bhi, dB, sB, bB, et);
+  CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA, et) : mAh;
+  CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB, et) : mBh;
 
   DevBuf part((size_t)splits * M * N * 4, s);
   Params p{M, N, nab, total, per, part.as<float>(), err};
@@ -828,18 +795,23 @@ void tc_contract(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int 
     TD_CUDA(cudaLaunchKernelEx(&cfg, kernel, mAh, mAl, mBh, mBl, p));
     if (prof) prof->end(s, prof_flops, prof_bytes);
   };
-  if (pair && mode == BOTH) launch_pair(k1_tc_kernel<BOTH, false, 2>, Cfg<BOTH>::SMEM_BYTES);
-  else if (pair) launch_pair(k1_tc_kernel<CROSS, false, 2>, Cfg<CROSS>::SMEM_BYTES);
-  else if (mode == BOTH) launch(k1_tc_kernel<BOTH, false>, Cfg<BOTH>::SMEM_BYTES);
-  else if (mode == CROSS) launch(k1_tc_kernel<CROSS, false>, Cfg<CROSS>::SMEM_BYTES);
-  else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT, false>, Cfg<ASPLIT>::SMEM_BYTES);
-  else launch(k1_tc_kernel<SINGLE, false>, Cfg<SINGLE>::SMEM_BYTES);
+  if (et == ET_F16) {
+    if (pair) launch_pair(k1_tc_kernel<BOTH, ET_F16, 2>, Cfg<BOTH>::SMEM_BYTES);
+    else if (mode == BOTH) launch(k1_tc_kernel<BOTH, ET_F16>, Cfg<BOTH>::SMEM_BYTES);
+    else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT, ET_F16>, Cfg<ASPLIT>::SMEM_BYTES);
+    else launch(k1_tc_kernel<SINGLE, ET_F16>, Cfg<SINGLE>::SMEM_BYTES);
+  } else {
+    if (pair) launch_pair(k1_tc_kernel<BOTH, ET_BF16, 2>, Cfg<BOTH>::SMEM_BYTES);
+    else if (mode == BOTH) launch(k1_tc_kernel<BOTH, ET_BF16>, Cfg<BOTH>::SMEM_BYTES);
+    else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT, ET_BF16>, Cfg<ASPLIT>::SMEM_BYTES);
+    else launch(k1_tc_kernel<SINGLE, ET_BF16>, Cfg<SINGLE>::SMEM_BYTES);
+  }
   count_launch();
   TD_LAUNCH_CHECK();
   const long long MN = (long long)M * N;
   long long g = (MN + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
-  k_sum_splits<<<(unsigned)g, 256, 0, s>>>(part.as<float>(), splits, MN, out, accumulate ? 1 : 0, nullptr);
+  k_sum_splits<<<(unsigned)g, 256, 0, s>>>(part.as<float>(), splits, MN, out, accumulate ? 1 : 0, scale);
   count_launch();
   TD_LAUNCH_CHECK();
 }
@@ -849,7 +821,7 @@ void tc_contract8(const unsigned char* Ahi, const unsigned char* Alo, int M, int
                   cudaStream_t s) {
   if (M <= 0 || pn <= 0 || N <= 0) return;
   TD_REQUIRE(Ahi && Alo && B && scale, TDDFT_ERR_ARG, "tc_contract8: operands missing");
-  constexpr int BKE = Elem<true>::BKE;
+  constexpr int BKE = Elem<ET_E4M3>::BKE;
   const int ldk = tc_pad16(Kin);
   const int nab = (Kin + BKE - 1) / BKE;
   const int total = pn * nab;
@@ -863,13 +835,13 @@ void tc_contract8(const unsigned char* Ahi, const unsigned char* Alo, int M, int
   const cuuint64_t dB[3] = {(cuuint64_t)Kin, (cuuint64_t)N, (cuuint64_t)pn};
   const cuuint64_t sB[2] = {(cuuint64_t)ldk, (cuuint64_t)N * ldk};
   const cuuint32_t bB[3] = {(cuuint32_t)BKE, BN, 1};
-  CUtensorMap mAh = make_map(Ahi, dA, sA, bA, true), mAl = make_map(Alo, dA, sA, bA, true);
-  CUtensorMap mB = make_map(B, dB, sB, bB, true);
+  CUtensorMap mAh = make_map(Ahi, dA, sA, bA, ET_E4M3), mAl = make_map(Alo, dA, sA, bA, ET_E4M3);
+  CUtensorMap mB = make_map(B, dB, sB, bB, ET_E4M3);
   DevBuf part((size_t)splits * M * N * 4, s);
   Params p{M, N, nab, total, per, part.as<float>(), err};
   dim3 grid(nt, mt, splits);
-  ensure_smem((const void*)k1_tc_kernel<ASPLIT, true>, Cfg<ASPLIT>::SMEM_BYTES);
-  k1_tc_kernel<ASPLIT, true><<<grid, THREADS, Cfg<ASPLIT>::SMEM_BYTES, s>>>(mAh, mAl, mB, mB, p);
+  ensure_smem((const void*)k1_tc_kernel<ASPLIT, ET_E4M3>, Cfg<ASPLIT>::SMEM_BYTES);
+  k1_tc_kernel<ASPLIT, ET_E4M3><<<grid, THREADS, Cfg<ASPLIT>::SMEM_BYTES, s>>>(mAh, mAl, mB, mB, p);
   count_launch();
   TD_LAUNCH_CHECK();
   const long long MN = (long long)M * N;
@@ -881,26 +853,26 @@ void tc_contract8(const unsigned char* Ahi, const unsigned char* Alo, int M, int
 }
 
 namespace {
-void stage1_impl(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, const __nv_bfloat16* Al2, int M, int K,
-                 const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, const __nv_bfloat16* Bl2, int N, int pn,
-                 int R, __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, __nv_bfloat16* out_l2,
-                 unsigned char* out8_hi, unsigned char* out8_lo, const float* mu, int* err, cudaStream_t s) {
+// out_is8: e4m3 outputs with per-P multipliers mu (A as hi + lo, B plain);
+// otherwise 16-bit outputs of the inputs' element type et, FP16 ones times *mul.
+void stage1_impl(const void* Ahi, const void* Alo, int M, int K, const void* Bhi, const void* Blo, int N, int pn,
+                 int R, int et, bool out_is8, void* out_hi, void* out_lo, const float* mul, const float* mu, int* err,
+                 cudaStream_t s) {
   if (M <= 0 || pn <= 0 || N <= 0) return;
   TD_REQUIRE(N <= 256, TDDFT_ERR_ARG, "tc_stage1: N above 256");
   TD_REQUIRE((Alo != nullptr || Blo == nullptr) &&
-                 (out8_hi ? (out8_lo != nullptr && mu != nullptr) : (Alo != nullptr) == (out_lo != nullptr)),
+                 (out_is8 ? (out_lo != nullptr && mu != nullptr) : (Alo != nullptr) == (out_lo != nullptr)),
              TDDFT_ERR_ARG, "tc_stage1: hi/lo operands mismatch");
-  const bool triple = Al2 != nullptr;
-  TD_REQUIRE(!triple || (Alo && Blo && Bl2 && out_lo && out_l2 && !out8_hi), TDDFT_ERR_ARG,
-             "tc_stage1: three-part split needs every part");
-  const int mode = triple ? TRIPLE : (Alo ? (Blo ? BOTH : ASPLIT) : SINGLE);
+  TD_REQUIRE((et == ET_F16) == (mul != nullptr) && (!out_is8 || et == ET_BF16), TDDFT_ERR_ARG,
+             "tc_stage1: FP16 outputs need a multiplier, FP8 outputs BF16 inputs");
+  const int mode = Alo ? (Blo ? BOTH : ASPLIT) : SINGLE;
   const int ldk = tc_pad(K);
   const int nb = (N + 15) & ~15;
   int acc_cols = 32;
   while (acc_cols < nb) acc_cols *= 2;
   const int a_bytes = BM * BK * 2, b_bytes = nb * BK * 2;
   const int stage_bytes = n_parts_a(mode) * a_bytes + n_parts_b(mode) * b_bytes;
-  int stages = ((triple ? 220 : 200) * 1024) / stage_bytes;
+  int stages = (200 * 1024) / stage_bytes;
   if (stages > 6) stages = 6;
   TD_REQUIRE(stages >= 2, TDDFT_ERR_ARG, "tc_stage1: tile too large");
   const int smem = stages * stage_bytes + 1024 + 256;
@@ -915,79 +887,77 @@ void stage1_impl(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, const __nv_
   const cuuint64_t dB[3] = {(cuuint64_t)K, (cuuint64_t)N, (cuuint64_t)pn};
   const cuuint64_t sB[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)N * ldk * 2};
   const cuuint32_t bB[3] = {BK, (cuuint32_t)nb, 1};
-  CUtensorMap mAh = make_map(Ahi, dA, sA, bA), mBh = make_map(Bhi, dB, sB, bB);
-  CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA) : mAh;
-  CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB) : mBh;
-  CUtensorMap mA2 = triple ? make_map(Al2, dA, sA, bA) : mAh;
-  CUtensorMap mB2 = triple ? make_map(Bl2, dB, sB, bB) : mBh;
-  S1Params p{M, N, R, out8_hi ? tc_pad16(R) : tc_pad(R), pn, ppc, (K + BK - 1) / BK, nb, acc_cols, stages,
-             stage_bytes, a_bytes, b_bytes, out_hi, out_lo, out_l2, out8_hi, out8_lo, mu, err};
+  CUtensorMap mAh = make_map(Ahi, dA, sA, bA, et), mBh = make_map(Bhi, dB, sB, bB, et);
+  CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA, et) : mAh;
+  CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB, et) : mBh;
+  S1Params p{M, N, R, out_is8 ? tc_pad16(R) : tc_pad(R), pn, ppc, (K + BK - 1) / BK, nb, acc_cols, stages,
+             stage_bytes, a_bytes, b_bytes, out_hi, out_lo, mul, mu, err};
   dim3 grid(mt, groups, 1);
   auto launch = [&](auto kernel) {
     ensure_smem((const void*)kernel, smem);
-    kernel<<<grid, S1_THREADS, smem, s>>>(mAh, mAl, mBh, mBl, mA2, mB2, p);
+    kernel<<<grid, S1_THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
   };
-  if (out8_hi) {
+  if (out_is8) {
     TD_REQUIRE(mode == ASPLIT, TDDFT_ERR_ARG, "tc_stage1: FP8 output needs hi+lo A and a plain B");
-    launch(k_stage1_tc<ASPLIT, true>);
-  } else if (mode == TRIPLE) launch(k_stage1_tc<TRIPLE, false>);
-  else if (mode == BOTH) launch(k_stage1_tc<BOTH, false>);
-  else if (mode == ASPLIT) launch(k_stage1_tc<ASPLIT, false>);
-  else launch(k_stage1_tc<SINGLE, false>);
+    launch(k_stage1_tc<ASPLIT, ET_BF16, ET_E4M3>);
+  } else if (et == ET_F16) {
+    TD_REQUIRE(mode == BOTH, TDDFT_ERR_ARG, "tc_stage1: FP16 operands come as hi + lo");
+    launch(k_stage1_tc<BOTH, ET_F16, ET_F16>);
+  } else if (mode == BOTH) launch(k_stage1_tc<BOTH, ET_BF16, ET_BF16>);
+  else if (mode == ASPLIT) launch(k_stage1_tc<ASPLIT, ET_BF16, ET_BF16>);
+  else launch(k_stage1_tc<SINGLE, ET_BF16, ET_BF16>);
   count_launch();
   TD_LAUNCH_CHECK();
 }
 }  // namespace
 
-void tc_stage1(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K,
-               const __nv_bfloat16* Bhi, const __nv_bfloat16* Blo, int N, int pn, int R,
-               __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int* err, cudaStream_t s) {
-  stage1_impl(Ahi, Alo, nullptr, M, K, Bhi, Blo, nullptr, N, pn, R, out_hi, out_lo, nullptr, nullptr, nullptr,
-              nullptr, err, s);
-}
-
-void tc_stage1_3(const __nv_bfloat16* const A[3], int M, int K, const __nv_bfloat16* const B[3], int N, int pn,
-                 int R, __nv_bfloat16* const out[3], int* err, cudaStream_t s) {
-  stage1_impl(A[0], A[1], A[2], M, K, B[0], B[1], B[2], N, pn, R, out[0], out[1], out[2], nullptr, nullptr,
-              nullptr, err, s);
-}
-
-bool tc_stage1_3_fits(int N) {
-  const int nb = (N + 15) & ~15;
-  const int stage = 3 * BM * BK * 2 + 3 * nb * BK * 2;
-  return N <= 256 && (220 * 1024) / stage >= 2;
+void tc_stage1(const void* Ahi, const void* Alo, int M, int K, const void* Bhi, const void* Blo, int N, int pn,
+               int R, TcElt et, const float* mul, void* out_hi, void* out_lo, int* err, cudaStream_t s) {
+  stage1_impl(Ahi, Alo, M, K, Bhi, Blo, N, pn, R, elem_of(et), false, out_hi, out_lo, mul, nullptr, err, s);
 }
 
 void tc_stage1_fp8(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int M, int K, const __nv_bfloat16* B,
                    int N, int pn, int R, const float* mu, unsigned char* out_hi, unsigned char* out_lo, int* err,
                    cudaStream_t s) {
-  stage1_impl(Ahi, Alo, nullptr, M, K, B, nullptr, nullptr, N, pn, R, nullptr, nullptr, nullptr, out_hi, out_lo,
-              mu, err, s);
+  stage1_impl(Ahi, Alo, M, K, B, nullptr, N, pn, R, ET_BF16, true, out_hi, out_lo, nullptr, mu, err, s);
 }
 
-// F64/F32 rows [rows][n] -> BF16 hi (+ lo) [rows][tc_pad(n)]
-template <typename TS>
+// F64/F32/BF16 rows [rows][n] -> hi (+ lo) [rows][tc_pad(n)] (times *scale when given)
+template <typename TS, typename E>
 __global__ void k_pad_split(const TS* __restrict__ src, long long rows, int n, int ld,
-                            __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* l2) {
+                            const float* __restrict__ scale, E* hi, E* lo) {
   const long long tot = rows * ld;
+  const float sc = scale ? *scale : 1.f;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x) {
     const int a = (int)(t % ld);
     const long long r = t / ld;
-    const float v = a < n ? (float)src[r * n + a] : 0.f;
-    split_store(v, t, hi, lo, l2);
+    const float v = a < n ? (float)src[r * n + a] * sc : 0.f;
+    split_store<E>(v, t, hi, lo);
   }
 }
 
-void tc_pad_split(const void* src, DType ts, long long rows, int n, __nv_bfloat16* hi,
-                  __nv_bfloat16* lo, cudaStream_t s, __nv_bfloat16* l2) {
-  const int ld = tc_pad(n);
+template <typename E>
+void pad_split_t(const void* src, DType ts, long long rows, int n, int ld, const float* scale, E* hi, E* lo,
+                 cudaStream_t s) {
   const long long tot = rows * ld;
   long long g = (tot + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
-  if (ts == DType::F64) k_pad_split<double><<<(unsigned)g, 256, 0, s>>>((const double*)src, rows, n, ld, hi, lo, l2);
-  else if (ts == DType::F32) k_pad_split<float><<<(unsigned)g, 256, 0, s>>>((const float*)src, rows, n, ld, hi, lo, l2);
-  else k_pad_split<__nv_bfloat16><<<(unsigned)g, 256, 0, s>>>((const __nv_bfloat16*)src, rows, n, ld, hi, lo, l2);
+  if (ts == DType::F64)
+    k_pad_split<double, E><<<(unsigned)g, 256, 0, s>>>((const double*)src, rows, n, ld, scale, hi, lo);
+  else if (ts == DType::F32)
+    k_pad_split<float, E><<<(unsigned)g, 256, 0, s>>>((const float*)src, rows, n, ld, scale, hi, lo);
+  else
+    k_pad_split<__nv_bfloat16, E><<<(unsigned)g, 256, 0, s>>>((const __nv_bfloat16*)src, rows, n, ld, scale, hi, lo);
+}
+
+void tc_pad_split(const void* src, DType ts, long long rows, int n, void* hi, void* lo, TcElt et,
+                  const float* scale, cudaStream_t s) {
+  TD_REQUIRE(et == TcElt::F16 || scale == nullptr, TDDFT_ERR_ARG, "tc_pad_split: BF16 parts take no scale");
+  if (et == TcElt::F16)
+    pad_split_t<__half>(src, ts, rows, n, tc_pad(n), scale, (__half*)hi, (__half*)lo, s);
+  else
+    pad_split_t<__nv_bfloat16>(src, ts, rows, n, tc_pad(n), scale, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, s);
   count_launch();
   TD_LAUNCH_CHECK();
 }
@@ -1055,17 +1025,22 @@ __global__ void k_row_norm_max(const __nv_bfloat16* __restrict__ src, int nr, in
   }
 }
 
-// kappa[0] = max_(n,a) ||X[n][:][a]||, kappa[1] = max_(n,j) ||X[n][j][:]|| (as
-// float bits; non-negative floats order like their bit patterns)
+// kappa[0] = max_(n,a) ||X[n][:][a]||, kappa[1] = max_(n,j) ||X[n][j][:]||,
+// kappa[2] = max |X| (as float bits; non-negative floats order like their bit
+// patterns)
 template <typename T>
 __global__ void k_x_norms(const T* __restrict__ X, int no, int nv, unsigned* __restrict__ kappa) {
   const T* x = X + (long long)blockIdx.x * no * nv;
-  __shared__ float red[2][32];
+  __shared__ float red[3][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  float mc = 0.f, mr = 0.f;
+  float mc = 0.f, mr = 0.f, ma = 0.f;
   for (int a = threadIdx.x; a < nv; a += blockDim.x) {
     float acc = 0.f;
-    for (int j = 0; j < no; ++j) { const float v = (float)x[(long long)j * nv + a]; acc += v * v; }
+    for (int j = 0; j < no; ++j) {
+      const float v = (float)x[(long long)j * nv + a];
+      acc += v * v;
+      ma = fmaxf(ma, fabsf(v));
+    }
     mc = fmaxf(mc, sqrtf(acc));
   }
   for (int j = warp; j < no; j += nw) {
@@ -1074,15 +1049,75 @@ __global__ void k_x_norms(const T* __restrict__ X, int no, int nv, unsigned* __r
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     mr = fmaxf(mr, sqrtf(acc));
   }
-  for (int o = 16; o > 0; o >>= 1) mc = fmaxf(mc, __shfl_xor_sync(0xffffffffu, mc, o));
-  if (lane == 0) { red[0][warp] = mc; red[1][warp] = mr; }
+  for (int o = 16; o > 0; o >>= 1) {
+    mc = fmaxf(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+    ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+  }
+  if (lane == 0) { red[0][warp] = mc; red[1][warp] = mr; red[2][warp] = ma; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float c = 0.f, r = 0.f;
-    for (int w = 0; w < nw; ++w) { c = fmaxf(c, red[0][w]); r = fmaxf(r, red[1][w]); }
+    float c = 0.f, r = 0.f, m = 0.f;
+    for (int w = 0; w < nw; ++w) { c = fmaxf(c, red[0][w]); r = fmaxf(r, red[1][w]); m = fmaxf(m, red[2][w]); }
     atomicMax(&kappa[0], __float_as_uint(c));
     atomicMax(&kappa[1], __float_as_uint(r));
+    atomicMax(&kappa[2], __float_as_uint(m));
   }
+}
+
+// 2^(top - e) for b = f 2^e, f in [0.5, 1): the largest power of two s with
+// s b < 2^top (1 for b = 0).
+__device__ __forceinline__ float pow2_scale(float b, int top) {
+  if (!(b > 0.f)) return 1.f;
+  int e = 0;
+  frexpf(b, &e);
+  e = max(-100, min(100, e));
+  return ldexpf(1.f, top - e);
+}
+
+// st[0] = max |x| and st[1] = the largest row norm of FP32 rows [rows][n]
+// (float bits); one warp per row
+__global__ void k_f16_tensor_stats(const float* __restrict__ src, long long rows, int n, unsigned* __restrict__ st) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  float ma = 0.f, mr = 0.f;
+  for (long long r = w0; r < rows; r += nw) {
+    float acc = 0.f;
+    for (int c = lane; c < n; c += 32) {
+      const float v = src[r * n + c];
+      acc += v * v;
+      ma = fmaxf(ma, fabsf(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    mr = fmaxf(mr, sqrtf(acc));
+  }
+  for (int o = 16; o > 0; o >>= 1) ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+  if (lane == 0) {
+    atomicMax(&st[0], __float_as_uint(ma));
+    atomicMax(&st[1], __float_as_uint(mr));
+  }
+}
+
+// sc[0] = sigma (max |sigma x| < 2^14), sc[1] = sigma * largest row norm
+__global__ void k_f16_sigma(const unsigned* __restrict__ st, float* __restrict__ sc) {
+  const float sg = pow2_scale(__uint_as_float(st[0]), 14);
+  sc[0] = sg;
+  sc[1] = sg * __uint_as_float(st[1]);
+}
+
+// Per-product scales of the FP16 exact contractions (layout in tc_gemm.cuh).
+__global__ void k_f16_product_scales(const unsigned* __restrict__ kappa, const float* __restrict__ fsc,
+                                     float* __restrict__ out) {
+  const float kc = __uint_as_float(kappa[0]), kr = __uint_as_float(kappa[1]);
+  const float sx = pow2_scale(__uint_as_float(kappa[2]), 14);
+  // |Z'| <= rho_oo' ||X'[n][:][a]||, |Q'| <= ||X'[n][i][:]|| rho_ov' (Cauchy-Schwarz)
+  const float mz = pow2_scale(fsc[1] * sx * kc, 15);
+  const float mq = pow2_scale(fsc[5] * sx * kr, 15);
+  out[0] = sx;
+  out[1] = mz;
+  out[2] = mq;
+  out[3] = 1.f / (mz * fsc[0] * sx * fsc[2]);
+  out[4] = 1.f / (mq * sx * fsc[4] * fsc[4]);
 }
 
 // out[0] = 1/g1, out[1] = 1/g2, out[2 + P] = s1_P g1, out[2 + nK + P] = s2_P g2
@@ -1139,12 +1174,38 @@ void tc_row_norm_max(const __nv_bfloat16* src, int rows, int nr, int nc, float* 
 void tc_fp8_scales(const void* X, DType xt, int m, int no, int nv, const float* s_vv, const float* rho_oo,
                    const float* s_vo, const float* rho_ov, int nK, float* out, unsigned* kappa,
                    cudaStream_t s) {
-  TD_CUDA(cudaMemsetAsync(kappa, 0, 2 * sizeof(unsigned), s));
+  TD_CUDA(cudaMemsetAsync(kappa, 0, 3 * sizeof(unsigned), s));
   if (xt == DType::F32) k_x_norms<float><<<m, 256, 0, s>>>(static_cast<const float*>(X), no, nv, kappa);
   else k_x_norms<double><<<m, 256, 0, s>>>(static_cast<const double*>(X), no, nv, kappa);
   count_launch();
   TD_LAUNCH_CHECK();
   k_fp8_mu<<<1, 256, 0, s>>>(kappa, s_vv, rho_oo, s_vo, rho_ov, nK, out);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+void tc_f16_tensor_scale(const float* src, long long rows, int n, float* sc, unsigned* scratch, cudaStream_t s) {
+  TD_CUDA(cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned), s));
+  if (rows > 0 && n > 0) {
+    long long g = (rows * 32 + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    k_f16_tensor_stats<<<(unsigned)g, 256, 0, s>>>(src, rows, n, scratch);
+    count_launch();
+    TD_LAUNCH_CHECK();
+  }
+  k_f16_sigma<<<1, 1, 0, s>>>(scratch, sc);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+void tc_f16_product_scales(const void* X, DType xt, int m, int no, int nv, const float* fsc, float* out,
+                           unsigned* kappa, cudaStream_t s) {
+  TD_CUDA(cudaMemsetAsync(kappa, 0, 3 * sizeof(unsigned), s));
+  if (xt == DType::F32) k_x_norms<float><<<m, 256, 0, s>>>(static_cast<const float*>(X), no, nv, kappa);
+  else k_x_norms<double><<<m, 256, 0, s>>>(static_cast<const double*>(X), no, nv, kappa);
+  count_launch();
+  TD_LAUNCH_CHECK();
+  k_f16_product_scales<<<1, 1, 0, s>>>(kappa, fsc, out);
   count_launch();
   TD_LAUNCH_CHECK();
 }

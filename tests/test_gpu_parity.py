@@ -4,10 +4,9 @@ Tolerances (see the design notes for the derivation):
   * operator products, PLAIN (FP64): 1e-11 relative to max |out| -- rounding order only;
   * operator products, MIXED exact (FP32 factors, FP32 accumulation): 2e-5 relative;
   * ris products, MIXED (BF16 factors): 2e-2 relative (preconditioner only);
-  * exact products, MIXED on the tensor cores (BF16 hi+lo, three products,
-    FP32 accumulation): 5e-5 relative; ris products on the tensor cores: 2e-2;
-  * exact products in the re-certification's tensor-core form (three BF16
-    parts, six products, FP32 accumulation): 2e-6 (FP32-level, ~2e-7 measured);
+  * exact products, MIXED on the tensor cores (every operand scaled by a power
+    of two and split into FP16 hi + lo, three products, FP32 accumulation):
+    2e-6 relative (FP32-level); ris products on the tensor cores: 2e-2;
   * excitation energies: 1e-6 Ha (PLAIN), 1e-5 Ha (MIXED);
   * polarizabilities: 1e-6 relative (PLAIN), 1e-5 relative (MIXED), element
     by element with the floor of tests/parity.py.
@@ -88,23 +87,37 @@ def test_tensor_core_products(case, api):
     op = O.exact_operator(p)
     for m in (1, 5, 23):
         X = np.random.default_rng(m).standard_normal((m, p.n_ov))
-        assert _rel(s.apply(0, X, precision=api.MIXED, tensor_cores=True), op.tda(X)) < 5e-5
+        e0 = _rel(s.apply(0, X, precision=api.MIXED, tensor_cores=True), op.tda(X))
         gp, gm = s.apply(1, X, precision=api.MIXED, tensor_cores=True)
         rp, rm = op.apb_amb(X)
-        assert _rel(gp, rp) < 5e-5 and _rel(gm, rm) < 5e-5
-        # the re-certification's form: three BF16 parts per operand, six
-        # products, FP32 accumulation: FP32-level (1e-7 to 3e-7 measured), held to 2e-6
-        e0 = _rel(s.apply(0, X, precision=api.MIXED, tensor_cores=3), op.tda(X))
-        cp, cm = s.apply(1, X, precision=api.MIXED, tensor_cores=3)
-        print("\n%s m=%d three-part tensor-core products: rel err %.2e (A), %.2e (A+B), %.2e (A-B)"
-              % (name, m, e0, _rel(cp, rp), _rel(cm, rm)))
-        assert e0 < 2e-6 and _rel(cp, rp) < 2e-6 and _rel(cm, rm) < 2e-6
+        print("\n%s m=%d FP16 hi+lo tensor-core products: rel err %.2e (A), %.2e (A+B), %.2e (A-B)"
+              % (name, m, e0, _rel(gp, rp), _rel(gm, rm)))
+        assert e0 < 2e-6 and _rel(gp, rp) < 2e-6 and _rel(gm, rm) < 2e-6
         # ris operator on the tensor cores: one BF16 product (preconditioner only)
         T = O.ris_operator(p)
         assert _rel(s.apply(2, X, precision=api.MIXED, tensor_cores=True), T.tda(X)) < 2e-2
         tp, tm = s.apply(3, X, precision=api.MIXED, tensor_cores=True)
         rtp, rtm = T.apb_amb(X)
         assert _rel(tp, rtp) < 2e-2 and _rel(tm, rtm) < 2e-2
+
+
+def test_tensor_core_products_scale_with_the_input(case, api):
+    """Every FP16 operand carries a power of two chosen from its own range, so
+    scaling the trial vectors by 2^k scales the products by exactly 2^k, and
+    inputs scaled by 1e-10 or 1e10 keep FP32-accurate products (no overflow of
+    the FP16 range, no loss to its subnormals)."""
+    name, p, s = case
+    X = np.random.default_rng(9).standard_normal((4, p.n_ov))
+    base = s.apply(1, X, precision=api.MIXED, tensor_cores=True)
+    for k in (-30, 37):
+        sc = s.apply(1, X * 2.0 ** k, precision=api.MIXED, tensor_cores=True)
+        for a, b in zip(sc, base):
+            assert np.array_equal(a, b * 2.0 ** k), k
+    op = O.exact_operator(p)
+    for c in (1e-10, 1e10):
+        gp, gm = s.apply(1, X * c, precision=api.MIXED, tensor_cores=True)
+        rp, rm = op.apb_amb(X * c)
+        assert _rel(gp, rp) < 2e-6 and _rel(gm, rm) < 2e-6, c
 
 
 @pytest.mark.parametrize("pc", ["diag", "rid"])
