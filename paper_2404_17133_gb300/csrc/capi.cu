@@ -63,7 +63,7 @@ void stage_rows(const void* src, DType tin, bool on_device, long long rows, long
 // tensor-core operands (of the factors times a power of two per tensor) with
 // rows padded for the TMA strides (MIXED).
 void stage_exact(ExactCopies& e, const void* L_oo, const void* L_ov, const void* L_vv, long long A,
-                 DType tin, bool dev, int no, int nv, bool p64, bool pmx, cudaStream_t s) {
+                 DType tin, bool dev, int no, int nv, bool p64, bool pmx, cudaStream_t s, bool coulomb = false) {
   const long long ov = (long long)no * nv;
   e.n = (int)A;
   if (p64) {
@@ -107,6 +107,10 @@ void stage_exact(ExactCopies& e, const void* L_oo, const void* L_ov, const void*
     tc_pad_split(e.f32_oo.p, DType::F32, A * no, no, e.oo_hi.p, e.oo_lo.p, TcElt::F16, sc + 0, s);
     parts(e.ov_hi, e.ov_lo, A * no * tc_pad(nv));
     tc_pad_split(e.f32_ov.p, DType::F32, A * no, nv, e.ov_hi.p, e.ov_lo.p, TcElt::F16, sc + 4, s);
+    if (coulomb) {   // L_ov transposed for the Coulomb term's second contraction
+      parts(e.ovT_hi, e.ovT_lo, ov * tc_pad((int)A));
+      tc_transpose_split(e.f32_ov.p, DType::F32, 1, (int)A, (int)ov, e.ovT_hi.p, e.ovT_lo.p, TcElt::F16, sc + 4, s);
+    }
   }
 }
 
@@ -172,7 +176,7 @@ void worker_loop(Ctx* c) {
 
 namespace tddft {
 
-unsigned long long factor_copy_bytes(const tddft_desc& d) {
+unsigned long long factor_copy_bytes(const tddft_desc& d, bool coulomb) {
   const bool p64 = d.precisions & 1, pmx = d.precisions & 2;
   const double no = d.n_occ, nv = d.n_vir, ov = no * nv;
   const double nvv = (double)d.n_aux * nv * nv, noo = (double)d.n_aux * no * no, nov = (double)d.n_aux * ov;
@@ -182,8 +186,10 @@ unsigned long long factor_copy_bytes(const tddft_desc& d) {
   if (p64) bytes += 8.0 * (nvv + noo + nov + nr);
   // FP8 copies of the ris exchange rows: vv and ov^T padded to 16, four floats per row
   const double fp8 = (double)d.n_aux_ris_K * (nv * (tc_pad16(d.n_vir) + tc_pad16(d.n_occ)) + 16.0);
-  // MIXED: FP32 copies, two FP16 parts of every padded exact operand, BF16 ris rows and their padded copies
-  if (pmx) bytes += 4.0 * (nvv + noo + nov) + 4.0 * (double)d.n_aux * padded + 2.0 * nr +
+  // MIXED: FP32 copies, two FP16 parts of every padded exact operand (and of L_ov
+  // transposed for the Coulomb term), BF16 ris rows and their padded copies
+  if (pmx) bytes += 4.0 * (nvv + noo + nov) + 4.0 * (double)d.n_aux * padded +
+                    (coulomb ? 4.0 * ov * tc_pad(d.n_aux) : 0.0) + 2.0 * nr +
                     2.0 * (double)d.n_aux_ris_K * padded + fp8;
   return (unsigned long long)bytes;
 }
@@ -207,6 +213,10 @@ void ExactCopies::fill(FactorSet& f, int precision, bool coulomb) const {
     f.Koo_lo = oo_lo.p;
     f.Kovp_hi = ov_hi.p;
     f.Kovp_lo = ov_lo.p;
+    if (coulomb) {
+      f.JovT_hi = ovT_hi.p;
+      f.JovT_lo = ovT_lo.p;
+    }
   }
 }
 
@@ -404,7 +414,7 @@ tddft_status tddft_create(const tddft_desc* desc, const double* eps_occ, const d
 
     // exact factors
     const long long A = d.n_aux;
-    stage_exact(c->x, L_oo, L_ov, L_vv, A, tin, dev, no, nv, p64, pmx, s);
+    stage_exact(c->x, L_oo, L_ov, L_vv, A, tin, dev, no, nv, p64, pmx, s, true);
 
     // ris factors (Coulomb rows all; exchange rows windowed, Sec. 3.1)
     const long long RJ = d.n_aux_ris_J, RK = d.n_aux_ris_K;
@@ -695,7 +705,7 @@ tddft_status tddft_add_exchange(tddft_ctx* ctx, double b_x, int n_aux_lr, const 
     tddft_desc dl = c->desc;
     dl.n_aux = n_aux_lr;
     dl.n_aux_ris_J = dl.n_aux_ris_K = 0;
-    c->device_bytes += factor_copy_bytes(dl);
+    c->device_bytes += factor_copy_bytes(dl, false);
     return TDDFT_OK;
   })
 }

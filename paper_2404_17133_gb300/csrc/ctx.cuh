@@ -38,6 +38,11 @@ struct FactorSet {
   const void* Koo_lo = nullptr;
   const void* Kovp_hi = nullptr;
   const void* Kovp_lo = nullptr;
+  // FP16 exact sets that carry the Coulomb term: s_ov L_ov transposed
+  // ([ov][tc_pad(nJ)], hi + lo), the B operand of J = t^T L_ov; with Kovp (the
+  // same rows as [P][ov]) both Coulomb contractions run on the tensor cores
+  const void* JovT_hi = nullptr;
+  const void* JovT_lo = nullptr;
   // Variant terms of the exact operator (Eq. hessian for other functionals):
   // a second exchange factor set entering with weight b_x, and a low-rank
   // kernel sum_g w_g F^g_ia F^g_jb added to the Coulomb term, its rows stored
@@ -72,6 +77,7 @@ struct ExactCopies {
   DevBuf vo_hi, vo_lo;            // [n][nv][tc_pad(no)] FP16 split of s_ov L_ov transposed
   DevBuf oo_hi, oo_lo;            // [n][no][tc_pad(no)] (s_oo L_oo)
   DevBuf ov_hi, ov_lo;            // [n][no][tc_pad(nv)] (s_ov L_ov)
+  DevBuf ovT_hi, ovT_lo;          // [ov][tc_pad(n)] (s_ov L_ov transposed; sets with the Coulomb term)
   DevBuf tc_scale;                // the scale block of tc_f16_tensor_scale (8 floats)
   // Exchange operands of `precision` into f (and the Coulomb block when coulomb).
   void fill(FactorSet& f, int precision, bool coulomb) const;
@@ -129,7 +135,7 @@ struct Request {
 
 // Device bytes of the factor copies tddft_create makes for `d` (both
 // precisions as selected by d.precisions).
-unsigned long long factor_copy_bytes(const tddft_desc& d);
+unsigned long long factor_copy_bytes(const tddft_desc& d, bool coulomb = true);
 
 struct Ctx {
   cudaStream_t s = nullptr;

@@ -95,6 +95,14 @@ namespace {
 // many auxiliary rows (longer K loops per CTA, fewer launches and pipeline fills).
 constexpr size_t kChunkBytes = 512ull << 20;
 constexpr size_t kChunkBytesTC = 4ull << 30;
+// k-blocks one CTA accumulates in FP32 before its split-K partial is summed
+// (fixed order) with the others: the rounding of an FP32 run grows with its
+// length, and runs over a whole P-chunk of the exchange contraction (~1e4 MMA
+// steps) or over ov in the Coulomb term left the large Casida solve's
+// recomputed residuals 3e-6 above the loop's (the Coulomb runs set a 1.1e-5
+// floor).  Exchange: 256 k-blocks (16384 terms); Coulomb (K = ov): 64.
+constexpr int kExchangeKb = 256;
+constexpr int kCoulombKb = 64;
 
 int chunk_rows(int nrows, long long per_row_bytes, int m, size_t budget = kChunkBytes) {
   long long pc = (long long)(budget / (per_row_bytes > 0 ? per_row_bytes : 1));
@@ -142,10 +150,34 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
   bool have_J = false;
   if (f.nJ > 0 && d.c_J != 0.0) {
     // t[P][n] = sum_ia L_ov[P][ia] X[n][ia];  J[n][ia] = sum_P t[P][n] L_ov[P][ia]
-    DevBuf t((size_t)f.nJ * m * ew, s);
     Jb = DevBuf(mov * ew, s);
-    sk_gram(f.Jov, f.dt, ov, f.nJ, Xw, tw, ov, m, ov, t.p, tw, m, 1.0, 0.0, s);
-    sk_combo(t.p, tw, 1, m, m, f.nJ, f.Jov, f.dt, ov, ov, Jb.p, tw, ov, 1.0, 0.0, s);
+    if (tensor_cores && f.tc_elt == TcElt::F16 && f.JovT_hi && f.nJ == f.nK) {
+      // both contractions on the tensor cores, streaming the FP16 hi+lo copies
+      // of s_ov L_ov ([P][ov] for t, transposed for J) once each: the trial
+      // vectors as FP16 parts of s_x X, t rescaled and split with its own
+      // power of two s_t
+      const int nvp = tc_pad(nv);
+      const DType xt = x32 ? DType::F32 : DType::F64;
+      DevBuf sc(8 * 4, s), kap(16, s), sct(2 * 4, s), scr(8, s), fac(2 * 4, s);
+      tc_f16_product_scales(X, xt, m, d.no, nv, f.tc_scale, sc.as<float>(), kap.as<unsigned>(), s);
+      DevBuf xh((size_t)m * no * nvp * 2, s), xl((size_t)m * no * nvp * 2, s);
+      tc_pad_split(X, xt, (long long)m * no, nv, xh.p, xl.p, TcElt::F16, sc.as<float>(), s);
+      tc_inv_prod(sc.as<float>(), f.tc_scale + 4, fac.as<float>(), s);           // 1 / (s_x s_ov)
+      DevBuf t((size_t)f.nJ * m * 4, s);
+      tc_contract(f.Kovp_hi, f.Kovp_lo, f.nJ, 1, no * nvp, xh.p, xl.p, m, t.as<float>(), false, TcElt::F16,
+                  fac.as<float>(), d.tc_err, s, nullptr, 0.0, 0.0, kCoulombKb);
+      tc_f16_tensor_scale(t.as<float>(), f.nJ, m, sct.as<float>(), scr.as<unsigned>(), s);
+      const int nJp = tc_pad(f.nJ);
+      DevBuf th((size_t)m * nJp * 2, s), tl((size_t)m * nJp * 2, s);
+      tc_transpose_split(t.p, DType::F32, 1, f.nJ, m, th.p, tl.p, TcElt::F16, sct.as<float>(), s);
+      tc_inv_prod(sct.as<float>(), f.tc_scale + 4, fac.as<float>() + 1, s);      // 1 / (s_t s_ov)
+      tc_contract(th.p, tl.p, m, 1, f.nJ, f.JovT_hi, f.JovT_lo, ov, Jb.as<float>(), false, TcElt::F16,
+                  fac.as<float>() + 1, d.tc_err, s);
+    } else {
+      DevBuf t((size_t)f.nJ * m * ew, s);
+      sk_gram(f.Jov, f.dt, ov, f.nJ, Xw, tw, ov, m, ov, t.p, tw, m, 1.0, 0.0, s);
+      sk_combo(t.p, tw, 1, m, m, f.nJ, f.Jov, f.dt, ov, ov, Jb.p, tw, ov, 1.0, 0.0, s);
+    }
     have_J = true;
   }
   if (d.c_J != 0.0) {
@@ -269,14 +301,15 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
                     // Z hi+lo [Mz][pn*nv], L_vv chunk [pn*nv][nv] (hi+lo for FP16), K1 FP32
                     // written (and read back when accumulating)
                     4.0 * Mz * (double)pn * nv + (f16 ? 4.0 : 2.0) * (double)pn * nv * nv +
-                        4.0 * Mz * (double)nv * (p0 > 0 ? 2.0 : 1.0));
+                        4.0 * Mz * (double)nv * (p0 > 0 ? 2.0 : 1.0),
+                    f16 ? kExchangeKb : 0);
         if (need_k2) {
           tc_stage1(Xs_hi.p, Xs_lo.p, m * no, nv, at16(f.Kovp_hi, (size_t)p0 * no * nvp),
                     f16 ? at16(f.Kovp_lo, (size_t)p0 * no * nvp) : nullptr, no, pn, no, et, mq, Qhi.p, Qlo.p,
                     d.tc_err, s);
           tc_contract(Qhi.p, Qlo.p, Mz, pn, no, at16(f.Kvo_hi, (size_t)p0 * nv * nop),
                       f16 ? at16(f.Kvo_lo, (size_t)p0 * nv * nop) : nullptr, nv, K2b.as<float>(), p0 > 0, et, f2,
-                      d.tc_err, s);
+                      d.tc_err, s, nullptr, 0.0, 0.0, f16 ? kExchangeKb : 0);
         }
       }
     } else {

@@ -88,6 +88,18 @@ void trace(const char* what, int it, int N, const std::vector<double>& om, const
   fprintf(stderr, "[tddft] %s it=%d N=%d max|r|=%.3e omega0=%.8f\n", what, it, N, m, om.empty() ? 0.0 : om[0]);
 }
 
+// One line per certification gate: the loop's and the recomputed residuals, root by root.
+void trace_gate(const char* what, int it, const std::vector<double>& rr, const std::vector<double>& cr) {
+  if (!trace_on()) return;
+  double ml = 0.0, mc = 0.0, md = 0.0;
+  for (size_t j = 0; j < cr.size() && j < rr.size(); ++j) {
+    ml = std::max(ml, rr[j]);
+    mc = std::max(mc, cr[j]);
+    md = std::max(md, std::fabs(cr[j] - rr[j]));
+  }
+  fprintf(stderr, "[tddft] %s gate it=%d loop max %.4e recomputed max %.4e max |diff| %.3e\n", what, it, ml, mc, md);
+}
+
 template <typename T>
 std::vector<T> d2h(const T* p, size_t n, cudaStream_t s) {
   std::vector<T> h(n);
@@ -346,6 +358,7 @@ TdaOut davidson_tda(int ov, const TdaOp& A, const TdaPre& pre, double* guess, in
     if (todo.empty() && kk == k) {
       if (!cert) { o.converged = true; break; }
       const std::vector<double> cr = (*cert)(X.as<double>(), om, kk);
+      trace_gate("tda", it, rr, cr);
       o.cert = 0.0;
       for (int j = 0; j < kk; ++j) {
         o.cert = std::max(o.cert, cr[j]);
@@ -639,6 +652,7 @@ PairedLinOut paired_linear(int ov, const PairOpT<T>& op, const PairPreT<T>& pre,
       if (!cert) { o.converged = true; break; }
       // the gate of davidson_tda
       const std::vector<double> cr = (*cert)(Uout, Wout);
+      trace_gate("polar", it, rr, cr);
       o.cert = 0.0;
       for (int r = 0; r < nr; ++r) {
         o.cert = std::max(o.cert, cr[r]);
@@ -799,6 +813,7 @@ RpaOut davidson_rpa(int ov, const PairOp& op, const PairPre& pre, double* guess,
     if (todo.empty() && kk == k) {
       if (!cert) { o.converged = true; break; }
       const std::vector<double> cr = (*cert)(U.as<double>(), W.as<double>(), om, kk);
+      trace_gate("rpa", it, rr, cr);
       o.cert = 0.0;
       for (int j = 0; j < kk; ++j) {
         o.cert = std::max(o.cert, cr[j]);

@@ -76,11 +76,13 @@ template <int MODE> struct Cfg {
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 };
 constexpr int THREADS = 192;
-constexpr int S1_THREADS = 320;   // stage 1: producer, MMA and 8 epilogue warps (2 per TMEM quadrant)
+constexpr int S1_EPI_WARPS = 16;                   // stage-1 epilogue warps (4 per TMEM lane quadrant)
+constexpr int S1_THREADS = 64 + 32 * S1_EPI_WARPS;   // producer, MMA and the epilogue warps
 constexpr long long WAIT_LIMIT = 1ll << 23;
 
 struct Params {
   int M, N;          // output rows / columns
+  int Kin;           // k extent per P (the last k-block of a P issues only the MMAs it needs)
   int nab;           // k-blocks per P
   int total;         // pn * nab steps
   int per_split;     // steps per split
@@ -271,7 +273,11 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
+    // ---- MMA issuer.  The MMA spans only the tile's columns below N
+    // (rounded up to 16) and, in the last k-block of each P, only the 32-byte
+    // K steps below Kin: the skipped products are of TMA's zero fill.
+    const int nb_cta = min(BN, (p.N - n0 + 15) & ~15);
+    const uint32_t idesc = idesc_of<ET>(nb_cta);
     bool ok = true;
     for (int i = 0; i < nk; ++i) {
       const int s = i % STAGES;
@@ -279,12 +285,17 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       unsigned char* st = smem + s * STAGE_BYTES;
       const uint64_t ah = sdesc(st), bh = sdesc(st + B_OFF);
+      const int kb = k_begin + i;
+      const int rem = p.Kin - (kb % p.nab) * Elem<ET>::BKE;
+      const int nks = rem >= Elem<ET>::BKE ? 4 : (rem * 4 + Elem<ET>::BKE - 1) / Elem<ET>::BKE;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
-        const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 32 bytes along K per MMA
-        mma_op<ET>(tmem, ah + off, bh + off, (i > 0 || kk > 0) ? 1u : 0u);
-        if (b_split(MODE)) mma_op<ET>(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, 1u);
-        if (a_split(MODE)) mma_op<ET>(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u);
+        if (kk < nks) {
+          const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 32 bytes along K per MMA
+          mma_op<ET>(tmem, ah + off, bh + off, (i > 0 || kk > 0) ? 1u : 0u, idesc);
+          if (b_split(MODE)) mma_op<ET>(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, 1u, idesc);
+          if (a_split(MODE)) mma_op<ET>(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u, idesc);
+        }
       }
       if constexpr (CL > 1) mma_commit_mc(&empty[s], (uint16_t)0x3);
       else mma_commit(&empty[s]);
@@ -357,9 +368,11 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
 // the next (tmem_full / tmem_empty barriers).
 struct S1Params {
   int M, N, R, ldo, pn, ppc, nkb;
+  int K;               // k extent (the last k-block issues only the MMAs it needs)
   int nb;              // MMA N (multiple of 16, >= N)
   int acc_cols;        // TMEM columns per accumulator buffer
   int stages, stage_bytes, a_bytes, b_bytes;
+  int a_res_bytes;     // RES: the resident A tile (every k-block, every part)
   void* out_hi;        // BF16 / FP16 parts (2-byte elements) or e4m3 bytes
   void* out_lo;
   // FP16 output: the accumulator times *mul before its split; FP8 output:
@@ -376,7 +389,12 @@ __device__ __forceinline__ float from_e4m3(unsigned char q) {
   return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3)));
 }
 
-template <int MODE, int IN, int OUT>
+// RES: the CTA's A tile (all k-blocks) is loaded once and stays in shared
+// memory while the CTA walks its P range; the ring streams B_P only.
+// CL = 2: the CTAs run in clusters of two along the M tiles; both need the same
+// B_P tiles, so each loads half of the rows and multicasts them to both, and
+// a stage is refilled only when both CTAs' MMAs have read it.
+template <int MODE, int IN, int OUT, bool RES = false, int CL = 1>
 __global__ void __launch_bounds__(S1_THREADS, 1)
 k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
             const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
@@ -384,22 +402,28 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + p.stages * p.stage_bytes);
+  unsigned char* ares = smem;                                   // RES: resident A
+  unsigned char* ring = smem + (RES ? p.a_res_bytes : 0);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + p.stages * p.stage_bytes);
   uint64_t* empty = full + p.stages;
   uint64_t* tfull = empty + p.stages;      // [2]
   uint64_t* tempty = tfull + 2;            // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* afull = tempty + 2;            // RES: the resident A tile has landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(afull + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM;
   const int P0 = blockIdx.y * p.ppc;
   const int nP = max(0, min(p.pn, P0 + p.ppc) - P0);
   const uint32_t idesc = idesc_of<IN>(p.nb);
-  const int b_off = n_parts_a(MODE) * p.a_bytes;
+  const int a_part = RES ? n_parts_a(MODE) * p.a_bytes : 0;   // resident bytes per k-block
+  const int b_off = RES ? 0 : n_parts_a(MODE) * p.a_bytes;     // first B tile in a stage
+  const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < p.stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 8); }
+    for (int s = 0; s < p.stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], CL); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], S1_EPI_WARPS); }
+    mbar_init(afull, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -408,26 +432,57 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   __syncthreads();
+  if constexpr (CL > 1) cluster_sync_all();   // every barrier of the cluster initialised
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const int nsteps = nP * p.nkb;
 
   if (warp == 0 && lane == 0) {
+    if constexpr (RES) {
+      if (nsteps > 0) {
+        mbar_expect_tx(afull, p.a_res_bytes);
+        for (int kb = 0; kb < p.nkb; ++kb) {
+          tma_load_3d(ares + kb * a_part, &mA_hi, afull, kb * BK, m0, 0);
+          if (a_split(MODE)) tma_load_3d(ares + kb * a_part + p.a_bytes, &mA_lo, afull, kb * BK, m0, 0);
+        }
+      }
+    }
     for (int i = 0; i < nsteps; ++i) {
       const int s = i % p.stages;
       if (!mbar_wait(&empty[s], ((uint32_t)(i / p.stages) & 1u) ^ 1u)) { atomicOr(p.err, 16); break; }
       const int P = P0 + i / p.nkb, k0 = (i % p.nkb) * BK;
-      unsigned char* st = smem + s * p.stage_bytes;
+      unsigned char* st = ring + s * p.stage_bytes;
       mbar_expect_tx(&full[s], p.stage_bytes);
-      tma_load_3d(st, &mA_hi, &full[s], k0, m0, 0);
-      tma_load_3d(st + b_off, &mB_hi, &full[s], k0, 0, P);
-      if (a_split(MODE)) tma_load_3d(st + p.a_bytes, &mA_lo, &full[s], k0, m0, 0);
-      if (b_split(MODE)) tma_load_3d(st + b_off + p.b_bytes, &mB_lo, &full[s], k0, 0, P);
+      if constexpr (!RES) {
+        tma_load_3d(st, &mA_hi, &full[s], k0, m0, 0);
+        if (a_split(MODE)) tma_load_3d(st + p.a_bytes, &mA_lo, &full[s], k0, m0, 0);
+      }
+      if constexpr (CL > 1) {
+        // this CTA's half of the B_P rows, to both CTAs of the pair
+        const int hb = p.b_bytes / 2;
+        const int r0 = (int)crank * (p.nb / 2);
+        tma_load_3d_mc(st + b_off + crank * hb, &mB_hi, &full[s], k0, r0, P, (uint16_t)0x3);
+        if (b_split(MODE))
+          tma_load_3d_mc(st + b_off + p.b_bytes + crank * hb, &mB_lo, &full[s], k0, r0, P, (uint16_t)0x3);
+      } else {
+        tma_load_3d(st + b_off, &mB_hi, &full[s], k0, 0, P);
+        if (b_split(MODE)) tma_load_3d(st + b_off + p.b_bytes, &mB_lo, &full[s], k0, 0, P);
+      }
     }
+    // let the copies already issued land before the CTA can exit
     for (int i = max(0, nsteps - p.stages); i < nsteps; ++i)
       if (!mbar_wait(&full[i % p.stages], (uint32_t)(i / p.stages) & 1u)) { atomicOr(p.err, 32); break; }
+    if constexpr (CL > 1) {
+      // and the peer's last commits arrive on this CTA's `empty` barriers
+      for (int i = nsteps; i < nsteps + p.stages; ++i)
+        if (!mbar_wait(&empty[i % p.stages], ((uint32_t)(i / p.stages) & 1u) ^ 1u)) { atomicOr(p.err, 32); break; }
+    }
   } else if (warp == 1 && lane == 0) {
-    for (int j = 0; j < nP; ++j) {
+    bool ok = true;
+    if constexpr (RES) {
+      if (nsteps > 0 && !mbar_wait(afull, 0)) { atomicOr(p.err, 128); ok = false; }
+    }
+    for (int j = 0; j < nP && ok; ++j) {
       const int buf = j & 1;
       // wait until the epilogue has drained this accumulator buffer (use j/2 - 1)
       if (!mbar_wait(&tempty[buf], ((uint32_t)(j >> 1) & 1u) ^ 1u)) { atomicOr(p.err, 64); break; }
@@ -436,30 +491,91 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
       for (int kb = 0; kb < p.nkb; ++kb) {
         const int i = j * p.nkb + kb;
         const int s = i % p.stages;
-        if (!mbar_wait(&full[s], (uint32_t)(i / p.stages) & 1u)) { atomicOr(p.err, 128); break; }
+        if (!mbar_wait(&full[s], (uint32_t)(i / p.stages) & 1u)) { atomicOr(p.err, 128); ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        unsigned char* st = smem + s * p.stage_bytes;
-        const uint64_t ah = sdesc(st), bh = sdesc(st + b_off);
+        unsigned char* st = ring + s * p.stage_bytes;
+        unsigned char* at = RES ? ares + kb * a_part : st;
+        const uint64_t ah = sdesc(at), bh = sdesc(st + b_off);
+        const int rem = p.K - kb * BK;
+        const int nks = rem >= BK ? BK / 16 : (rem + 15) / 16;   // the zero-filled tail issues no MMA
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint64_t off = (uint64_t)(kk * 32) >> 4;
-          mma_op<IN>(acc, ah + off, bh + off, (kb > 0 || kk > 0) ? 1u : 0u, idesc);
-          if (b_split(MODE)) mma_op<IN>(acc, ah + off, sdesc(st + b_off + p.b_bytes) + off, 1u, idesc);
-          if (a_split(MODE)) mma_op<IN>(acc, sdesc(st + p.a_bytes) + off, bh + off, 1u, idesc);
+          if (kk < nks) {
+            const uint64_t off = (uint64_t)(kk * 32) >> 4;
+            mma_op<IN>(acc, ah + off, bh + off, (kb > 0 || kk > 0) ? 1u : 0u, idesc);
+            if (b_split(MODE)) mma_op<IN>(acc, ah + off, sdesc(st + b_off + p.b_bytes) + off, 1u, idesc);
+            if (a_split(MODE)) mma_op<IN>(acc, sdesc(at + p.a_bytes) + off, bh + off, 1u, idesc);
+          }
         }
-        mma_commit(&empty[s]);
+        if constexpr (CL > 1) mma_commit_mc(&empty[s], (uint16_t)0x3);
+        else mma_commit(&empty[s]);
       }
       mma_commit(&tfull[buf]);
     }
   } else if (warp >= 2) {
-    // 8 epilogue warps: TMEM lane quadrant q = warp & 3, column chunks of 16 of
-    // parity half = (warp - 2) / 4
+    // epilogue warps: TMEM lane quadrant q = warp & 3; the four warps of a
+    // quadrant take the 16-column chunks part, part + 4, part + 8, ...; each
+    // warp loads its next chunk from TMEM while it stores the current one
+    constexpr int NPART = S1_EPI_WARPS / 4;
     const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int part = (warp - 2) >> 2;
     const int r = m0 + q * 32 + lane;
     const int g = r / p.R, ri = r - (r / p.R) * p.R;
     const size_t cs = (size_t)p.pn * p.ldo;   // output stride between consecutive columns
     const float mul = OUT == ET_F16 ? *p.mul : 1.f;
+    auto tmem_ld = [&](uint32_t (&v)[16], uint32_t taddr) {
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+          " [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+    };
+    auto tmem_wait = [] { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); };
+    auto store = [&](const uint32_t (&v)[16], int c0, int P) {
+      if (r >= p.M) return;
+      const size_t base = (((size_t)g * p.N + c0) * p.pn + P) * p.ldo + ri;
+      const int nc = min(16, p.N - c0);
+      if constexpr (OUT == ET_E4M3) {
+        const float mu = p.mu[P];
+        unsigned char* oh = static_cast<unsigned char*>(p.out_hi) + base;
+        unsigned char* ol = static_cast<unsigned char*>(p.out_lo) + base;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          if (t < nc) {
+            const float x = __uint_as_float(v[t]) * mu;
+            const unsigned char h = to_e4m3(x);
+            oh[t * cs] = h;
+            ol[t * cs] = to_e4m3(x - from_e4m3(h));
+          }
+        }
+      } else if constexpr (OUT == ET_F16) {
+        __half* oh = static_cast<__half*>(p.out_hi) + base;
+        __half* ol = static_cast<__half*>(p.out_lo) + base;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          if (t < nc) {
+            const float x = __uint_as_float(v[t]) * mul;
+            const __half h = __float2half_rn(x);
+            oh[t * cs] = h;
+            ol[t * cs] = __float2half_rn(x - __half2float(h));
+          }
+        }
+      } else {
+        __nv_bfloat16* oh = static_cast<__nv_bfloat16*>(p.out_hi) + base;
+        __nv_bfloat16* ol = a_split(MODE) ? static_cast<__nv_bfloat16*>(p.out_lo) + base : nullptr;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          if (t < nc) {
+            const float x = __uint_as_float(v[t]);
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            oh[t * cs] = h;
+            if (a_split(MODE)) ol[t * cs] = __float2bfloat16_rn(x - __bfloat162float(h));
+          }
+        }
+      }
+    };
     for (int j = 0; j < nP; ++j) {
       const int buf = j & 1;
       bool ok = mbar_wait(&tfull[buf], (uint32_t)(j >> 1) & 1u);
@@ -467,59 +583,22 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
       if (!ok) { if (lane == 0) atomicOr(p.err, 256); break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int P = P0 + j;
-      for (int c0 = 16 * half; c0 < p.N; c0 += 32) {
-        uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * p.acc_cols + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-            " [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-              "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (r < p.M) {
-          const size_t base = (((size_t)g * p.N + c0) * p.pn + P) * p.ldo + ri;
-          const int nc = min(16, p.N - c0);
-          if constexpr (OUT == ET_E4M3) {
-            const float mu = p.mu[P];
-            unsigned char* oh = static_cast<unsigned char*>(p.out_hi) + base;
-            unsigned char* ol = static_cast<unsigned char*>(p.out_lo) + base;
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-              if (t < nc) {
-                const float x = __uint_as_float(v[t]) * mu;
-                const unsigned char h = to_e4m3(x);
-                oh[t * cs] = h;
-                ol[t * cs] = to_e4m3(x - from_e4m3(h));
-              }
-            }
-          } else if constexpr (OUT == ET_F16) {
-            __half* oh = static_cast<__half*>(p.out_hi) + base;
-            __half* ol = static_cast<__half*>(p.out_lo) + base;
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-              if (t < nc) {
-                const float x = __uint_as_float(v[t]) * mul;
-                const __half h = __float2half_rn(x);
-                oh[t * cs] = h;
-                ol[t * cs] = __float2half_rn(x - __half2float(h));
-              }
-            }
-          } else {
-            __nv_bfloat16* oh = static_cast<__nv_bfloat16*>(p.out_hi) + base;
-            __nv_bfloat16* ol = a_split(MODE) ? static_cast<__nv_bfloat16*>(p.out_lo) + base : nullptr;
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-              if (t < nc) {
-                const float x = __uint_as_float(v[t]);
-                const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                oh[t * cs] = h;
-                if (a_split(MODE)) ol[t * cs] = __float2bfloat16_rn(x - __bfloat162float(h));
-              }
-            }
-          }
-        }
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * p.acc_cols);
+      constexpr int STEP = 16 * NPART;
+      uint32_t va[16], vb[16];
+      int c0 = 16 * part;
+      if (c0 < p.N) tmem_ld(va, tbase + (uint32_t)c0);
+      tmem_wait();
+#pragma unroll 1
+      for (; c0 < p.N; c0 += 2 * STEP) {
+        const int c1 = c0 + STEP;
+        if (c1 < p.N) tmem_ld(vb, tbase + (uint32_t)c1);
+        store(va, c0, P);
+        tmem_wait();
+        if (c1 >= p.N) break;
+        if (c1 + STEP < p.N) tmem_ld(va, tbase + (uint32_t)(c1 + STEP));
+        store(vb, c1, P);
+        tmem_wait();
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -531,6 +610,7 @@ k_stage1_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ C
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * p.acc_cols));
   }
+  if constexpr (CL > 1) cluster_sync_all();   // neither CTA leaves while the other may still signal it
 }
 
 // Sum the split partials into out (FP32), accumulating when asked.
@@ -738,7 +818,7 @@ int pair_slots(int et) {
 
 void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const void* Bhi, const void* Blo,
                  int N, float* out, bool accumulate, TcElt elt, const float* scale, int* err, cudaStream_t s,
-                 KernelProfile* prof, double prof_flops, double prof_bytes) {
+                 KernelProfile* prof, double prof_flops, double prof_bytes, int max_kb) {
   if (M <= 0 || pn <= 0 || N <= 0) return;
   TD_REQUIRE(Alo != nullptr || Blo == nullptr, TDDFT_ERR_ARG, "tc_contract: B split without A split");
   const int et = elem_of(elt);
@@ -755,6 +835,7 @@ void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const
   // a CTA's fixed cost (barriers, TMEM, pipeline fill, 128 KB epilogue) is about
   // four k-blocks of MMA work
   int splits = wave_splits(mt * nt, total, 4, pair ? pair_slots(et) : 0);
+  if (max_kb > 0) splits = std::max(splits, (total + max_kb - 1) / max_kb);   // bounded accumulation runs
   const int per = (total + splits - 1) / splits;
   splits = (total + per - 1) / per;
 
@@ -769,7 +850,7 @@ void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const
   CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB, et) : mBh;
 
   DevBuf part((size_t)splits * M * N * 4, s);
-  Params p{M, N, nab, total, per, part.as<float>(), err};
+  Params p{M, N, Kin, nab, total, per, part.as<float>(), err};
   dim3 grid(nt, mt, splits);
   auto launch = [&](auto kernel, int smem) {
     ensure_smem((const void*)kernel, smem);
@@ -838,7 +919,7 @@ void tc_contract8(const unsigned char* Ahi, const unsigned char* Alo, int M, int
   CUtensorMap mAh = make_map(Ahi, dA, sA, bA, ET_E4M3), mAl = make_map(Alo, dA, sA, bA, ET_E4M3);
   CUtensorMap mB = make_map(B, dB, sB, bB, ET_E4M3);
   DevBuf part((size_t)splits * M * N * 4, s);
-  Params p{M, N, nab, total, per, part.as<float>(), err};
+  Params p{M, N, Kin, nab, total, per, part.as<float>(), err};
   dim3 grid(nt, mt, splits);
   ensure_smem((const void*)k1_tc_kernel<ASPLIT, ET_E4M3>, Cfg<ASPLIT>::SMEM_BYTES);
   k1_tc_kernel<ASPLIT, ET_E4M3><<<grid, THREADS, Cfg<ASPLIT>::SMEM_BYTES, s>>>(mAh, mAl, mB, mB, p);
@@ -853,6 +934,37 @@ void tc_contract8(const unsigned char* Ahi, const unsigned char* Alo, int M, int
 }
 
 namespace {
+// CTAs of a paired stage-1 launch that can be resident at once (two per
+// co-resident cluster).
+int s1_pair_slots(bool res, int smem) {
+  static int cached[2] = {0, 0}, cached_smem[2] = {0, 0};
+  int& c = cached[res ? 1 : 0];
+  if (c == 0 || cached_smem[res ? 1 : 0] != smem) {
+    cached_smem[res ? 1 : 0] = smem;
+    const void* k = res ? (const void*)k_stage1_tc<BOTH, ET_F16, ET_F16, true, 2>
+                        : (const void*)k_stage1_tc<BOTH, ET_F16, ET_F16, false, 2>;
+    ensure_smem(k, smem);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(S1_THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess || n <= 0) {
+      (void)cudaGetLastError();
+      n = sm_count() / 2;
+    }
+    c = 2 * n;
+  }
+  return c;
+}
+
 // out_is8: e4m3 outputs with per-P multipliers mu (A as hi + lo, B plain);
 // otherwise 16-bit outputs of the inputs' element type et, FP16 ones times *mul.
 void stage1_impl(const void* Ahi, const void* Alo, int M, int K, const void* Bhi, const void* Blo, int N, int pn,
@@ -871,13 +983,23 @@ void stage1_impl(const void* Ahi, const void* Alo, int M, int K, const void* Bhi
   int acc_cols = 32;
   while (acc_cols < nb) acc_cols *= 2;
   const int a_bytes = BM * BK * 2, b_bytes = nb * BK * 2;
-  const int stage_bytes = n_parts_a(mode) * a_bytes + n_parts_b(mode) * b_bytes;
-  int stages = (200 * 1024) / stage_bytes;
+  const int nkb = (K + BK - 1) / BK;
+  const int mt0 = (M + BM - 1) / BM;
+  // The FP16 exact operands (hi + lo on both sides): the A tile stays resident
+  // when all its k-blocks fit beside a ring of three B stages, and pairs of M
+  // tiles share each B_P tile through a cluster multicast.
+  constexpr int kSmemBudget = 224 * 1024;
+  const int a_res = nkb * n_parts_a(mode) * a_bytes;
+  const int b_stage = n_parts_b(mode) * b_bytes;
+  const bool res = et == ET_F16 && !out_is8 && a_res + 3 * b_stage + 2048 <= kSmemBudget;
+  const bool pair = et == ET_F16 && !out_is8 && mt0 > 1 && cluster_pairs_enabled();
+  const int mt = pair ? (mt0 + 1) & ~1 : mt0;
+  const int stage_bytes = res ? b_stage : n_parts_a(mode) * a_bytes + b_stage;
+  int stages = ((res ? kSmemBudget - a_res - 2048 : 200 * 1024)) / stage_bytes;
   if (stages > 6) stages = 6;
   TD_REQUIRE(stages >= 2, TDDFT_ERR_ARG, "tc_stage1: tile too large");
-  const int smem = stages * stage_bytes + 1024 + 256;
-  const int mt = (M + BM - 1) / BM;
-  int groups = wave_splits(mt, pn, 1);   // units: P-rows (the epilogue is double-buffered)
+  const int smem = (res ? a_res : 0) + stages * stage_bytes + 1024 + 256;
+  int groups = wave_splits(mt, pn, 1, pair ? s1_pair_slots(res, smem) : 0);   // units: P-rows
   const int ppc = (pn + groups - 1) / groups;
   groups = (pn + ppc - 1) / ppc;
 
@@ -886,23 +1008,42 @@ void stage1_impl(const void* Ahi, const void* Alo, int M, int K, const void* Bhi
   const cuuint32_t bA[3] = {BK, BM, 1};
   const cuuint64_t dB[3] = {(cuuint64_t)K, (cuuint64_t)N, (cuuint64_t)pn};
   const cuuint64_t sB[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)N * ldk * 2};
-  const cuuint32_t bB[3] = {BK, (cuuint32_t)nb, 1};
+  const cuuint32_t bB[3] = {BK, (cuuint32_t)(pair ? nb / 2 : nb), 1};   // a pair loads half a B tile each
   CUtensorMap mAh = make_map(Ahi, dA, sA, bA, et), mBh = make_map(Bhi, dB, sB, bB, et);
   CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA, et) : mAh;
   CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB, et) : mBh;
-  S1Params p{M, N, R, out_is8 ? tc_pad16(R) : tc_pad(R), pn, ppc, (K + BK - 1) / BK, nb, acc_cols, stages,
-             stage_bytes, a_bytes, b_bytes, out_hi, out_lo, mul, mu, err};
+  S1Params p{M, N, R, out_is8 ? tc_pad16(R) : tc_pad(R), pn, ppc, nkb, K, nb, acc_cols, stages,
+             stage_bytes, a_bytes, b_bytes, res ? a_res : 0, out_hi, out_lo, mul, mu, err};
   dim3 grid(mt, groups, 1);
   auto launch = [&](auto kernel) {
     ensure_smem((const void*)kernel, smem);
     kernel<<<grid, S1_THREADS, smem, s>>>(mAh, mAl, mBh, mBl, p);
+  };
+  auto launch_pair = [&](auto kernel) {
+    ensure_smem((const void*)kernel, smem);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(S1_THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    TD_CUDA(cudaLaunchKernelEx(&cfg, kernel, mAh, mAl, mBh, mBl, p));
   };
   if (out_is8) {
     TD_REQUIRE(mode == ASPLIT, TDDFT_ERR_ARG, "tc_stage1: FP8 output needs hi+lo A and a plain B");
     launch(k_stage1_tc<ASPLIT, ET_BF16, ET_E4M3>);
   } else if (et == ET_F16) {
     TD_REQUIRE(mode == BOTH, TDDFT_ERR_ARG, "tc_stage1: FP16 operands come as hi + lo");
-    launch(k_stage1_tc<BOTH, ET_F16, ET_F16>);
+    if (res && pair) launch_pair(k_stage1_tc<BOTH, ET_F16, ET_F16, true, 2>);
+    else if (res) launch(k_stage1_tc<BOTH, ET_F16, ET_F16, true, 1>);
+    else if (pair) launch_pair(k_stage1_tc<BOTH, ET_F16, ET_F16, false, 2>);
+    else launch(k_stage1_tc<BOTH, ET_F16, ET_F16>);
   } else if (mode == BOTH) launch(k_stage1_tc<BOTH, ET_BF16, ET_BF16>);
   else if (mode == ASPLIT) launch(k_stage1_tc<ASPLIT, ET_BF16, ET_BF16>);
   else launch(k_stage1_tc<SINGLE, ET_BF16, ET_BF16>);
@@ -1194,6 +1335,18 @@ void tc_f16_tensor_scale(const float* src, long long rows, int n, float* sc, uns
     TD_LAUNCH_CHECK();
   }
   k_f16_sigma<<<1, 1, 0, s>>>(scratch, sc);
+  count_launch();
+  TD_LAUNCH_CHECK();
+}
+
+namespace {
+__global__ void k_inv_prod(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ out) {
+  out[0] = 1.f / (a[0] * b[0]);
+}
+}  // namespace
+
+void tc_inv_prod(const float* a, const float* b, float* out, cudaStream_t s) {
+  k_inv_prod<<<1, 1, 0, s>>>(a, b, out);
   count_launch();
   TD_LAUNCH_CHECK();
 }

@@ -36,11 +36,14 @@ void tc_pad_split(const void* src, DType ts, long long rows, int n, void* hi, vo
 // Timeouts of the kernel's internal waits are reported by OR-ing a nonzero
 // code into *err.  With `prof`, CUDA events bracket the contraction kernel
 // alone (not the split reduction) and prof_flops / prof_bytes (the launch's
-// algorithmic flops and bytes) are credited to it.
+// algorithmic flops and bytes) are credited to it.  max_kb > 0 bounds the
+// k-blocks one CTA accumulates in FP32 (more split-K partials, summed in a
+// fixed order), for contractions whose K is long enough that the length of
+// the accumulation run sets the rounding error.
 struct KernelProfile;
 void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const void* Bhi, const void* Blo,
                  int N, float* out, bool accumulate, TcElt et, const float* scale, int* err, cudaStream_t s,
-                 KernelProfile* prof = nullptr, double prof_flops = 0.0, double prof_bytes = 0.0);
+                 KernelProfile* prof = nullptr, double prof_flops = 0.0, double prof_bytes = 0.0, int max_kb = 0);
 
 // Stage-1 exchange contraction on the tensor cores, batched over P:
 //   C_P[r][c] = sum_(k<K) A[r][k] B_P[c][k],  A: [M][tc_pad(K)], B: [pn][N][tc_pad(K)],
@@ -67,6 +70,8 @@ void tc_f16_tensor_scale(const float* src, long long rows, int n, float* sc, uns
 //   K1 and K2 sums.  kappa: three device words.  No host synchronisation.
 void tc_f16_product_scales(const void* X, DType xt, int m, int no, int nv, const float* fsc, float* out,
                            unsigned* kappa, cudaStream_t s);
+// out[0] = 1 / (a[0] * b[0]) (device scalars): the factor that removes two scales.
+void tc_inv_prod(const float* a, const float* b, float* out, cudaStream_t s);
 
 // ---- FP8 (e4m3) ris exchange operands with one scale per auxiliary row P.
 // Factor rows src [rows][n1][n2] (BF16) -> dst [rows][n2][tc_pad16(n1)] e4m3

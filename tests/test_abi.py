@@ -122,7 +122,8 @@ def test_admission_charge_counts_the_factor_copies(api):
     """The server's charge for the factor copies, against a plain count of the
     arrays tddft_create keeps: FP64 copies of L_oo, L_ov, L_vv and of the ris
     rows (PLAIN); FP32 copies plus two FP16 parts of the tensor-core copies with rows
-    padded to a multiple of 8 elements (16-byte TMA strides) (MIXED: vv, ov^T, oo and ov), BF16 ris
+    padded to a multiple of 8 elements (16-byte TMA strides) (MIXED: vv, ov^T per P, oo, ov, and
+    the whole L_ov transposed for the Coulomb term), BF16 ris
     rows and their padded copies, FP8 copies of the ris exchange vv and ov^T rows padded to a
     multiple of 16 bytes with four floats per row (scales and norms)."""
     no, nv, na, nj, nk = 12, 70, 300, 54, 6
@@ -135,7 +136,8 @@ def test_admission_charge_counts_the_factor_copies(api):
     fmx, _ = api.estimate_bytes(_desc(api, no, nv, na, nj, nk, 2), 0, api.default_opts(precision=api.MIXED))
     pad16 = lambda n: -(-n // 16) * 16
     fp8 = nk * (nv * (pad16(nv) + pad16(no)) + 16)
-    assert fmx == 4 * na * (no * no + ov + nv * nv) + 4 * na * padded + 2 * ris + 2 * nk * padded + fp8
+    assert fmx == (4 * na * (no * no + ov + nv * nv) + 4 * na * padded + 4 * ov * pad(na) + 2 * ris
+                   + 2 * nk * padded + fp8)
     both, _ = api.estimate_bytes(_desc(api, no, nv, na, nj, nk, 3), 0, api.default_opts())
     assert both == f64 + fmx
 
