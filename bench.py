@@ -64,7 +64,7 @@ MEDIUM_STATES = 10
 # Casida pair vectors), as the mixed GPU solve counted them on GB300; the
 # oracle cannot run the Davidson iteration at this size (108 GB of FP64
 # factors), so its step time is its per-vector product time scaled by these.
-LARGE_COUNTS = {"tda_mv": 159, "tda_ris_mv": 2200, "rpa_mv": 490, "rpa_ris_mv": 6300}
+LARGE_COUNTS = {"tda_mv": 107, "tda_ris_mv": 751, "rpa_mv": 535, "rpa_ris_mv": 2009}
 
 
 def parse():

@@ -98,11 +98,11 @@ constexpr size_t kChunkBytesTC = 4ull << 30;
 // k-blocks one CTA accumulates in FP32 before its split-K partial is summed
 // (fixed order) with the others: the rounding of an FP32 run grows with its
 // length, and runs over a whole P-chunk of the exchange contraction (~1e4 MMA
-// steps) or over ov in the Coulomb term left the large Casida solve's
-// recomputed residuals 3e-6 above the loop's (the Coulomb runs set a 1.1e-5
-// floor).  Exchange: 256 k-blocks (16384 terms); Coulomb (K = ov): 64.
+// steps) left the large Casida solve's recomputed residuals 3e-6 above the
+// loop's.  Exchange: 256 k-blocks (16384 terms); the Coulomb term's J = t^T
+// L_ov (K = n_aux): 16.
 constexpr int kExchangeKb = 256;
-constexpr int kCoulombKb = 64;
+constexpr int kCoulombKb = 16;
 
 int chunk_rows(int nrows, long long per_row_bytes, int m, size_t budget = kChunkBytes) {
   long long pc = (long long)(budget / (per_row_bytes > 0 ? per_row_bytes : 1));
@@ -151,28 +151,21 @@ static void apply_operator_t(const OpDims& d, const FactorSet& f, const TX* X, i
   if (f.nJ > 0 && d.c_J != 0.0) {
     // t[P][n] = sum_ia L_ov[P][ia] X[n][ia];  J[n][ia] = sum_P t[P][n] L_ov[P][ia]
     Jb = DevBuf(mov * ew, s);
-    if (tensor_cores && f.tc_elt == TcElt::F16 && f.JovT_hi && f.nJ == f.nK) {
-      // both contractions on the tensor cores, streaming the FP16 hi+lo copies
-      // of s_ov L_ov ([P][ov] for t, transposed for J) once each: the trial
-      // vectors as FP16 parts of s_x X, t rescaled and split with its own
-      // power of two s_t
-      const int nvp = tc_pad(nv);
-      const DType xt = x32 ? DType::F32 : DType::F64;
-      DevBuf sc(8 * 4, s), kap(16, s), sct(2 * 4, s), scr(8, s), fac(2 * 4, s);
-      tc_f16_product_scales(X, xt, m, d.no, nv, f.tc_scale, sc.as<float>(), kap.as<unsigned>(), s);
-      DevBuf xh((size_t)m * no * nvp * 2, s), xl((size_t)m * no * nvp * 2, s);
-      tc_pad_split(X, xt, (long long)m * no, nv, xh.p, xl.p, TcElt::F16, sc.as<float>(), s);
-      tc_inv_prod(sc.as<float>(), f.tc_scale + 4, fac.as<float>(), s);           // 1 / (s_x s_ov)
-      DevBuf t((size_t)f.nJ * m * 4, s);
-      tc_contract(f.Kovp_hi, f.Kovp_lo, f.nJ, 1, no * nvp, xh.p, xl.p, m, t.as<float>(), false, TcElt::F16,
-                  fac.as<float>(), d.tc_err, s, nullptr, 0.0, 0.0, kCoulombKb);
+    if (tensor_cores && f.tc_elt == TcElt::F16 && f.JovT_hi && !f64) {
+      // t = L_ov X^T on the SIMT path (K = ov: its FP32 reduction tree keeps t
+      // at ~1e-7; one tensor-core accumulation run per 4096 terms left the
+      // Coulomb products at ~2e-6), then J = t^T L_ov on the tensor cores,
+      // streaming the FP16 hi+lo copy of s_ov L_ov transposed once, with t as
+      // FP16 parts of s_t t
+      DevBuf t((size_t)f.nJ * m * 4, s), sct(2 * 4, s), scr(8, s), fac(4, s);
+      sk_gram(f.Jov, f.dt, ov, f.nJ, Xw, tw, ov, m, ov, t.p, tw, m, 1.0, 0.0, s);
       tc_f16_tensor_scale(t.as<float>(), f.nJ, m, sct.as<float>(), scr.as<unsigned>(), s);
       const int nJp = tc_pad(f.nJ);
       DevBuf th((size_t)m * nJp * 2, s), tl((size_t)m * nJp * 2, s);
       tc_transpose_split(t.p, DType::F32, 1, f.nJ, m, th.p, tl.p, TcElt::F16, sct.as<float>(), s);
-      tc_inv_prod(sct.as<float>(), f.tc_scale + 4, fac.as<float>() + 1, s);      // 1 / (s_t s_ov)
+      tc_inv_prod(sct.as<float>(), f.tc_scale + 4, fac.as<float>(), s);      // 1 / (s_t s_ov)
       tc_contract(th.p, tl.p, m, 1, f.nJ, f.JovT_hi, f.JovT_lo, ov, Jb.as<float>(), false, TcElt::F16,
-                  fac.as<float>() + 1, d.tc_err, s);
+                  fac.as<float>(), d.tc_err, s, nullptr, 0.0, 0.0, kCoulombKb);
     } else {
       DevBuf t((size_t)f.nJ * m * ew, s);
       sk_gram(f.Jov, f.dt, ov, f.nJ, Xw, tw, ov, m, ov, t.p, tw, m, 1.0, 0.0, s);
