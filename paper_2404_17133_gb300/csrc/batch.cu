@@ -20,9 +20,15 @@
 // and the combination, for every problem) runs as one captured CUDA graph
 // whose task lists are rewritten in place before each replay.
 //
+// The exact operator's lists run on the tensor cores instead (k_ggemm_tc: the
+// same tasks and tile walk, every operand split into three BF16 parts on its
+// way to shared memory, six products per K step, FP32 accumulation --
+// FP32-accurate), and the SIMT variants are timed on the ris lists.
+//
 // Precision (the batched workload's form): trial vectors, exact factors and
-// products in FP32 (SIMT), ris factors in BF16 with FP32 accumulation, the
-// projected matrices and small solves in FP64.
+// products in FP32 (exact products FP32-accurate on the tensor cores), ris
+// factors in BF16 with FP32 accumulation, the projected matrices and small
+// solves in FP64.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -35,6 +41,7 @@
 
 #include "ctx.cuh"
 #include "small.cuh"
+#include "tc_ptx.cuh"
 #include "vecops.cuh"
 
 namespace tddft {
@@ -197,16 +204,254 @@ __global__ void k_gsum(const GTask* __restrict__ tasks, const GHdr* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Grouped tensor-core tile kernel: the task list and tile walk of k_ggemm with
+// 128 x 128 tiles.  Every operand element is loaded (FP32, BF16 or FP64),
+// split into three BF16 parts x = h + m + l (24 significand bits) and written
+// to K-major 128-byte-swizzled shared memory; one thread issues the six
+// products hh + hm + mh + hl + lh + mm per 16-element K step (kind::f16, FP32
+// accumulation in tensor memory, 2^-24 of the leading term dropped): an
+// FP32-accurate product at the BF16 tensor-core rate.  Two stages: the
+// loads of a k-block overlap the MMAs of the one before.  A wait that times
+// out sets g_batch_tc_err and ends the kernel.
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;
+constexpr int TC_THREADS = 256;
+constexpr int TC_PART = 128 * 128;            // bytes of one part tile: 128 rows x 64 BF16
+constexpr int TC_STAGE = 6 * TC_PART;         // A and B, three parts each
+constexpr int TC_SMEM = 2 * TC_STAGE + 1024 + 128;
+
+__device__ int g_batch_tc_err = 0;
+
+// byte offset of (row, k) in a part tile (128-byte rows, 16-byte chunks XORed by row % 8)
+__device__ __forceinline__ uint32_t sw128(int row, int k) {
+  return (uint32_t)(row * 128 + ((((k >> 3) ^ (row & 7))) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ void split3_store(unsigned char* base, uint32_t off, float x) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+  *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
+  *reinterpret_cast<__nv_bfloat16*>(base + TC_PART + off) = m;
+  *reinterpret_cast<__nv_bfloat16*>(base + 2 * TC_PART + off) = l;
+}
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float to_f(double x) { return (float)x; }
+
+// One 128 x 64 operand tile (rows row0.., k kbase..) into its three part
+// tiles: every thread loads its 32 elements first (independent loads in
+// flight together), then splits and stores them.  KC: k is the contiguous
+// index of the source (consecutive threads take consecutive k), else the row.
+template <typename T, bool KC>
+__device__ __forceinline__ void tc_load(unsigned char* dst, const T* __restrict__ src, long long s_row,
+                                        long long s_k, int row0, int rows, int kbase, int k1, int tid) {
+  constexpr int PER = 128 * TC_BK / TC_THREADS;
+  float x[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int idx = tid + i * TC_THREADS;
+    const int r = KC ? (idx >> 6) : (idx & 127);
+    const int kk = KC ? (idx & 63) : (idx >> 7);
+    const int gk = kbase + kk;
+    x[i] = (r < rows && gk < k1) ? to_f(src[(long long)(row0 + r) * s_row + (long long)gk * s_k]) : 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int idx = tid + i * TC_THREADS;
+    const int r = KC ? (idx >> 6) : (idx & 127);
+    const int kk = KC ? (idx & 63) : (idx >> 7);
+    split3_store(dst, sw128(r, kk), x[i]);
+  }
+}
+
+// dispatch on the element type (0 FP32, 1 BF16, 2 FP64) and the contiguous index
+__device__ __forceinline__ void tc_load_any(unsigned char* dst, const void* src, int type, long long s_row,
+                                            long long s_k, int row0, int rows, int kbase, int k1, int tid) {
+  if (type == 0) {
+    if (s_k == 1) tc_load<float, true>(dst, (const float*)src, s_row, s_k, row0, rows, kbase, k1, tid);
+    else tc_load<float, false>(dst, (const float*)src, s_row, s_k, row0, rows, kbase, k1, tid);
+  } else if (type == 1) {
+    if (s_k == 1) tc_load<__nv_bfloat16, true>(dst, (const __nv_bfloat16*)src, s_row, s_k, row0, rows, kbase, k1, tid);
+    else tc_load<__nv_bfloat16, false>(dst, (const __nv_bfloat16*)src, s_row, s_k, row0, rows, kbase, k1, tid);
+  } else {
+    if (s_k == 1) tc_load<double, true>(dst, (const double*)src, s_row, s_k, row0, rows, kbase, k1, tid);
+    else tc_load<double, false>(dst, (const double*)src, s_row, s_k, row0, rows, kbase, k1, tid);
+  }
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_ggemm_tc(const GTask* __restrict__ tasks, const GHdr* __restrict__ hdr) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * TC_STAGE);   // [0], [1] stages, [2] tile done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 3);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b) mbar_init(&bar[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  uint32_t ph[2] = {0u, 0u}, phd = 0u;
+  bool pend[2] = {false, false};
+  int it = 0;
+  bool ok = true;
+  const int ntask = hdr->ntask, total = hdr->total_tiles;
+  for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+    const GTask& g = tasks[find_task(tasks, ntask, t, false)];
+    int lt = t - g.tile0;
+    const int ks = lt % g.ksplit;
+    lt /= g.ksplit;
+    const int m0 = (lt / g.tiles_n) * TC_BM, n0 = (lt % g.tiles_n) * TC_BN;
+    const int k0 = ks * g.kchunk, k1 = min(g.K, k0 + g.kchunk);
+    const int M = g.M, N = g.N;
+    const int nb = min(TC_BN, (N - n0 + 15) & ~15);   // the MMA spans the tile's columns below N
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nb >> 3) << 17) |
+                           ((uint32_t)(TC_BM >> 4) << 24);
+    const int nkb = k1 > k0 ? (k1 - k0 + TC_BK - 1) / TC_BK : 0;
+    for (int kb = 0; kb < nkb; ++kb, ++it) {
+      const int s = it & 1;
+      if (pend[s]) {   // the MMAs that last read this stage have completed
+        if (!mbar_wait(&bar[s], ph[s])) ok = false;
+        ph[s] ^= 1u;
+        pend[s] = false;
+      }
+      if (!__syncthreads_and(ok)) { ok = false; break; }
+      unsigned char* st = smem + s * TC_STAGE;
+      unsigned char* sb = st + 3 * TC_PART;
+      const int kbase = k0 + kb * TC_BK;
+      tc_load_any(st, g.A, g.ta, g.sam, g.sak, m0, M - m0, kbase, k1, tid);   // A(r, k) = A[r sam + k sak]
+      tc_load_any(sb, g.B, g.tb, g.sbn, g.sbk, n0, N - n0, kbase, k1, tid);   // B(k, c) = B[k sbk + c sbn]
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the stores, seen by the tensor cores
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t a0 = sdesc(st), a1 = sdesc(st + TC_PART), a2 = sdesc(st + 2 * TC_PART);
+        const uint64_t b0 = sdesc(sb), b1 = sdesc(sb + TC_PART), b2 = sdesc(sb + 2 * TC_PART);
+        const int rem = k1 - kbase;
+        const int nks = rem >= TC_BK ? TC_BK / 16 : (rem + 15) / 16;   // zero-filled K steps issue no MMA
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          if (kk < nks) {
+            const uint64_t o = (uint64_t)(kk * 32) >> 4;
+            mma_bf16(tmem, a0 + o, b0 + o, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(tmem, a0 + o, b1 + o, idesc, 1u);
+            mma_bf16(tmem, a1 + o, b0 + o, idesc, 1u);
+            mma_bf16(tmem, a0 + o, b2 + o, idesc, 1u);
+            mma_bf16(tmem, a2 + o, b0 + o, idesc, 1u);
+            mma_bf16(tmem, a1 + o, b1 + o, idesc, 1u);
+          }
+        }
+        mma_commit(&bar[s]);
+      }
+      pend[s] = true;
+    }
+    if (!ok) break;
+    if (nkb > 0) {   // every MMA of the tile has completed
+      if (tid == 0) mma_commit(&bar[2]);
+      if (!mbar_wait(&bar[2], phd)) ok = false;
+      phd ^= 1u;
+      if (!__syncthreads_and(ok)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +32, columns 64 (w / 4) .. +64
+    const int q = warp & 3, half = warp >> 2;
+    const int r = m0 + q * 32 + lane;
+    const bool split = g.ksplit > 1 || g.Cd != nullptr;
+    const long long roff = r < M ? (long long)(r / g.crin) * g.scm1 + (long long)(r % g.crin) * g.scm : 0;
+    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
+      if (n0 + c0 >= N) break;   // uniform over the warp
+      uint32_t v[16];
+      if (nkb > 0) {
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+            " [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0u;
+      }
+      if (r < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = n0 + c0 + j;
+          if (c < N) {
+            const float acc = __uint_as_float(v[j]);
+            if (split) {
+              g.part[((long long)ks * M + r) * N + c] = acc;
+            } else {
+              float* cp = g.C + roff + (long long)c * g.scn;
+              *cp = g.alpha * acc + (g.beta != 0.f ? g.beta * *cp : 0.f);
+            }
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();   // the next tile's MMAs overwrite the accumulator
+  }
+  // the last commits have arrived before the CTA leaves
+  for (int s2 = 0; s2 < 2; ++s2)
+    if (pend[s2] && !mbar_wait(&bar[s2], ph[s2])) ok = false;
+  if (!ok && lane == 0) atomicOr(&g_batch_tc_err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
+}
+
 struct Variant {
   const char* name;
   const void* fn;
   int threads;
   int bm, bn;
+  int smem = 0;            // dynamic shared memory
+  int ctas_per_sm = 4;     // persistent grid: ctas_per_sm x SMs
 };
 
 template <int BM, int BN, int TM, int TN>
 Variant make_variant(const char* name) {
   return Variant{name, (const void*)k_ggemm<BM, BN, TM, TN>, (BM / TM) * (BN / TN), BM, BN};
+}
+
+// The exact operator's tile kernel (k_ggemm_tc).
+const Variant& tc_variant() {
+  static const Variant v{"tc128x128", (const void*)k_ggemm_tc, TC_THREADS, TC_BM, TC_BN, TC_SMEM, 1};
+  return v;
+}
+
+// Reads and clears the tensor-core kernel's timeout flag.
+void check_batch_tc(cudaStream_t s) {
+  int h = 0;
+  TD_CUDA(cudaMemcpyFromSymbolAsync(&h, g_batch_tc_err, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  TD_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    const int z = 0;
+    TD_CUDA(cudaMemcpyToSymbolAsync(g_batch_tc_err, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    TD_CUDA(cudaStreamSynchronize(s));
+    throw Error(TDDFT_ERR_CUDA, "batched tensor-core kernel wait timed out");
+  }
 }
 
 const std::vector<Variant>& variants() {
@@ -364,9 +609,10 @@ struct GList {
     launch_kernels(v, std::max(1, hdr_host.total_tiles), std::max(1, hdr_host.total_elems), s);
   }
   void launch_kernels(const Variant& v, int tiles, int elems, cudaStream_t s) {
-    const int grid = std::max(1, std::min(tiles, num_sms() * 4));
+    const int grid = std::max(1, std::min(tiles, num_sms() * v.ctas_per_sm));
     void* args[] = {&d_tasks.p, &d_hdr.p};
-    TD_CUDA(cudaLaunchKernel(v.fn, dim3(grid), dim3(v.threads), args, 0, s));
+    if (v.smem > 0) ensure_smem(v.fn, (size_t)v.smem);
+    TD_CUDA(cudaLaunchKernel(v.fn, dim3(grid), dim3(v.threads), args, (size_t)v.smem, s));
     count_launch();
     const int rg = std::min((elems + 255) / 256, num_sms() * 8);
     k_gsum<<<rg, 256, 0, s>>>(d_tasks.as<GTask>(), d_hdr.as<GHdr>());
@@ -398,7 +644,7 @@ struct GList {
   void launch_fixed(const Variant& v, cudaStream_t s) {
     TD_CUDA(cudaMemcpyAsync(d_tasks.p, h_tasks, cap_tasks * sizeof(GTask), cudaMemcpyHostToDevice, s));
     TD_CUDA(cudaMemcpyAsync(d_hdr.p, h_hdr, sizeof(GHdr), cudaMemcpyHostToDevice, s));
-    launch_kernels(v, num_sms() * 4, num_sms() * 8 * 256, s);
+    launch_kernels(v, num_sms() * v.ctas_per_sm, num_sms() * 8 * 256, s);
   }
   // the staging as seen by launch_fixed (after finalize); true if it still fits
   bool stage_fixed(const Variant& v, cudaStream_t s) {
@@ -733,14 +979,16 @@ void operator_batch(Batch& B, std::vector<OpCall>& calls, bool ris) {
     maxch = std::max(maxch, op.nK > 0 ? (op.nK + pc - 1) / pc : 0);
     if (ris) q.p->ris_mv += q.m; else q.p->mv += q.m;
   }
+  // the exact operator on the tensor cores, the ris operator on the tuned SIMT tiles
+  const Variant& v = ris ? *B.var : tc_variant();
   for (int c = 0; c < std::max(maxch, 1); ++c) {
     bool more = false;
-    B.g.reset(B.var->bm, B.var->bn);
+    B.g.reset(v.bm, v.bn);
     add_operator_tasks(B.g, calls, ris, c, more);
-    B.g.run(*B.var, B.s);
-    B.g.reset(B.var->bm, B.var->bn);
+    B.g.run(v, B.s);
+    B.g.reset(v.bm, v.bn);
     add_exchange_tasks(B.g, calls, ris, c);
-    B.g.run(*B.var, B.s);
+    B.g.run(v, B.s);
   }
   for (OpCall& q : calls) {
     Prob& p = *q.p;
@@ -764,7 +1012,7 @@ void operator_batch(Batch& B, std::vector<OpCall>& calls, bool ris) {
 // graph (uploads + persistent kernels with fixed grids) is replayed.  It is
 // captured again only when a list outgrows its staging.
 void operator_graph(Batch& B, std::vector<OpCall>& calls) {
-  const Variant& v = *B.var;
+  const Variant& v = tc_variant();
   cudaStream_t s = B.s;
   const int R = B.ex_rounds;
   if ((int)B.gs1.size() < R) {
@@ -829,8 +1077,9 @@ void operator_graph(Batch& B, std::vector<OpCall>& calls) {
   count_launch(B.graph_nodes);
 }
 
-// Time every tile variant on the first exchange contraction list (same bits
-// from each) and keep the fastest.
+// Time every SIMT tile variant on the first ris exchange contraction list
+// (the exact operator runs on the tensor cores; the ris products are the
+// largest SIMT lists; same bits from each variant) and keep the fastest.
 // TDDFT_BATCH_VARIANT=i forces variant i (after timing every variant).
 int forced_variant() {
   const char* e = getenv("TDDFT_BATCH_VARIANT");
@@ -842,10 +1091,10 @@ int forced_variant() {
 void autotune(Batch& B, std::vector<OpCall>& calls) {
   const auto& vs = variants();
   B.tune_ms.assign(vs.size(), -1.0);
-  // one exchange round's tasks after its stage-1 products exist
+  // one ris exchange round's tasks after its stage-1 products exist
   B.g.reset(64, 64);
   bool more = false;
-  add_operator_tasks(B.g, calls, false, 0, more);
+  add_operator_tasks(B.g, calls, true, 0, more);
   B.g.run(vs[0], B.s);
   cudaEvent_t e0, e1;
   TD_CUDA(cudaEventCreate(&e0));
@@ -853,7 +1102,7 @@ void autotune(Batch& B, std::vector<OpCall>& calls) {
   int best = 0;
   for (size_t v = 0; v < vs.size(); ++v) {
     B.g.reset(vs[v].bm, vs[v].bn);
-    add_exchange_tasks(B.g, calls, false, 0);
+    add_exchange_tasks(B.g, calls, true, 0);
     B.g.finalize(vs[v].bm, vs[v].bn, B.s);
     B.g.launch(vs[v], B.s);   // warm
     TD_CUDA(cudaEventRecord(e0, B.s));
@@ -1455,6 +1704,7 @@ tddft_status solve_tda_batch(Ctx* const* ctxs, int n, const tddft_opts* opts, do
   if (!o_diag.empty()) davidson_batch(B, o_diag, false, false, ng_d, k_d, t_d, max_iter);
   TD_CUDA(cudaStreamSynchronize(s));
   // outputs
+  check_batch_tc(B.s);
   size_t off = 0;
   bool all_ok = true;
   int iters = 0;

@@ -39,6 +39,7 @@
 
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
 #include "vecops.cuh"
 
 namespace tddft {
@@ -78,7 +79,6 @@ template <int MODE> struct Cfg {
 constexpr int THREADS = 192;
 constexpr int S1_EPI_WARPS = 16;                   // stage-1 epilogue warps (4 per TMEM lane quadrant)
 constexpr int S1_THREADS = 64 + 32 * S1_EPI_WARPS;   // producer, MMA and the epilogue warps
-constexpr long long WAIT_LIMIT = 1ll << 23;
 
 struct Params {
   int M, N;          // output rows / columns
@@ -90,35 +90,6 @@ struct Params {
   int* err;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait for the completion of phase `parity`; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  for (long long i = 0; i < WAIT_LIMIT; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int c0, int c1, int c2) {
@@ -129,12 +100,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(const void* p) {
-  const uint64_t addr = smem_u32(p);
-  return ((addr & 0x3FFFFull) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
-         (2ull << 61);
-}
 
 // Instruction descriptor: D = F32, A and B of the same type (BF16 or FP16
 // for kind::f16, E4M3 for kind::f8f6f4), both K-major, M = 128, N = nb.
@@ -190,11 +155,6 @@ __device__ __forceinline__ uint32_t cluster_rank() {
   return r;
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
 
 // CL = 2: the CTAs run in clusters of two along the M tiles; both need the same
 // B tile, so each loads half of its rows and multicasts them to both (halving
