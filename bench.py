@@ -491,6 +491,15 @@ def our_arm(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+# DRAM traffic of the K1 contraction from one ncu capture of the full-size
+# launch (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass, two launches of
+# m = 40 trial vectors over a 132-row P-chunk of the large workload, under
+# `bench.py --apply-only 3`): 16.51 GB per launch against 5.30 GB of
+# algorithmic bytes.  The bench's launches (m = 20..40) are reported at the
+# same ratio of their own algorithmic bytes.
+K1_TRAFFIC_PER_ALGORITHMIC_BYTE = 16.51e9 / 5.30e9
+
+
 def roofline(prof, rec_ms, rec_fl, rec_by, peaks, src, tc, clk, total_ms):
     """Roofline object of the dominant kernel (the K1 exchange contraction)."""
     kernel_ms = prof["ms"] / max(prof["launches"], 1)
@@ -521,9 +530,15 @@ def roofline(prof, rec_ms, rec_fl, rec_by, peaks, src, tc, clk, total_ms):
             "attainable_note": "per launch max(%g FP16 products per flop at the tensor peak, algorithmic bytes "
                                "at hbm_gbs %.0f); attainable_frac = sum of those / sum of measured times"
                                % (per_flop, peaks["hbm_gbs"])})
+    traffic = None
+    if tc and rec_by.size:
+        traffic = float(rec_by.mean()) * K1_TRAFFIC_PER_ALGORITHMIC_BYTE
+        roof["traffic_note"] = ("bytes per launch: the measured DRAM/algorithmic ratio of the full-size ncu "
+                                "capture (%.2f) times this run's mean algorithmic bytes per launch"
+                                % K1_TRAFFIC_PER_ALGORITHMIC_BYTE)
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak if peak else None,
                  "mma_pipe_frac": 3.0 * achieved / peak if (peak and tc) else None,
-                 "traffic": None, "kernel": "exchange K1 contraction sum_(P,a) Z L_vv",
+                 "traffic": traffic, "kernel": "exchange K1 contraction sum_(P,a) Z L_vv",
                  "launches": prof["launches"], "ms_per_launch": kernel_ms,
                  "share_of_step": prof["ms"] / total_ms if total_ms else None})
     return roof
@@ -812,7 +827,8 @@ def batched_lockstep(args, api, torch):
 def apply_only(args, api, solver, meta, tc, stream):
     """K exact pair products on 2*n_states device vectors, each timed with CUDA events."""
     import torch
-    m = 2 * (N_STATES if args.workload == WORKLOAD else MEDIUM_STATES)
+    from synth.generator import CONFIGS
+    m = 2 * CONFIGS[args.workload]["n_states"]
     X = torch.from_numpy(np.random.default_rng(7).standard_normal((m, meta["n_occ"] * meta["n_vir"]))).cuda()
     ms = []
     for _ in range(args.apply_only):

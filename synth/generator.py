@@ -239,6 +239,10 @@ CONFIGS = {
     # convergence within 33 iterations
     "large_mixed": dict(n_occ=150, n_vir=1350, n_aux=6000, n_ris=1350, seeds=(20, 21, 22),
                         n_states=20, mu_seed=23, amplitude_scale=0.7 ** 7),
+    # the large workload's orbital shape over 100 auxiliary rows (one P-chunk,
+    # ~2.5 GB on the device): the small case for profiling its kernels
+    "large_orbitals_short_aux": dict(n_occ=150, n_vir=1350, n_aux=100, n_ris=18, seeds=(70, 71, 72),
+                                     n_states=20, mu_seed=73),
 }
 
 
