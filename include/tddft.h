@@ -360,10 +360,14 @@ tddft_status tddft_apply_noalloc(tddft_ctx* ctx, int kind, int precision, const 
  * persistent grouped GEMM walking a device task list; row operations from a
  * device list; one CTA per problem for the small matrices), and the exact
  * operator product of an iteration is replayed from a captured CUDA graph.
- * The grouped GEMM's tile shape is chosen by a measured autotune at the start
- * of the batch (every variant gives the same bits).  Precision: trial vectors
- * and exact products in FP32, ris factors in BF16 (FP32 accumulation),
- * projected matrices and small solves in FP64; contexts need the MIXED
+ * The exact operator's lists run on a grouped tensor-core tile kernel (each
+ * operand split into three BF16 parts, six products per K step: FP32-
+ * accurate); the other lists' SIMT tile shape is chosen by a measured
+ * autotune on the first ris product (every variant gives the same bits).
+ * Precision: trial vectors in FP32, exact products FP32-accurate, ris
+ * factors in BF16 (FP32 accumulation), projected matrices and small solves
+ * in FP64; stats[i].max_resid_certified is -1 (no separate recomputation);
+ * a timed-out wait of the tensor-core kernel is TDDFT_ERR_CUDA; contexts need the MIXED
  * factor copies; opts[i].precision / tensor_cores / ris_fp8 are ignored,
  * n_states <= 32; contexts with variant terms are refused (TDDFT_ERR_ARG).
  *   omega, resid: HOST arrays of sum_i min(opts[i].n_states, ov_i) entries,
