@@ -28,7 +28,6 @@ tddft_status fail(Ctx* c, const std::exception& e, tddft_status st) {
 struct StageTarget {
   void* dst;        // device
   DType tout;       // F64, F32 or BF16
-  __nv_bfloat16* lo = nullptr;  // if set: BF16 hi (dst) + lo split
 };
 
 void stage_rows(const void* src, DType tin, bool on_device, long long rows, long long row_elems,
@@ -51,9 +50,7 @@ void stage_rows(const void* src, DType tin, bool on_device, long long rows, long
       in = stage.p;
     }
     for (const auto& t : targets) {
-      void* out = (char*)t.dst + off * dtype_size(t.tout);
-      if (t.lo) split_bf16(in, tin, (__nv_bfloat16*)out, t.lo + off, n, s);
-      else convert(in, tin, out, t.tout, n, s);
+      convert(in, tin, (char*)t.dst + off * dtype_size(t.tout), t.tout, n, s);
     }
     if (!on_device) TD_CUDA(cudaStreamSynchronize(s));  // staging buffer reused
   }

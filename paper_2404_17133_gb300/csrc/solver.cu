@@ -278,7 +278,7 @@ struct TdaOut {
   DevBuf X;     // [k][ov] Ritz vectors
   int n_iter = 0;
   bool converged = false;
-  double cert = -1.0;   // largest re-certified residual (when a gate was given)
+  double cert = -1.0;   // largest recomputed residual (when a gate was given)
 };
 
 // Certification gate: residual norms of the k Ritz pairs recomputed from fresh
@@ -495,7 +495,7 @@ struct PairedLinOut {
   int n_iter = 0;
   bool converged = false;
   std::vector<double> resid;
-  double cert = -1.0;   // largest re-certified relative residual (when a gate was given)
+  double cert = -1.0;   // largest recomputed relative residual (when a gate was given)
 };
 
 // Certification gate of the paired linear systems: the relative residuals of

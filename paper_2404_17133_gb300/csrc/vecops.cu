@@ -206,16 +206,6 @@ __global__ void k_to_bf16(const TI* in, __nv_bfloat16* out, long long n) {
     out[t] = __double2bfloat16(ldd<TI>(in, t));
 }
 
-template <typename TI>
-__global__ void k_split(const TI* in, __nv_bfloat16* hi, __nv_bfloat16* lo, long long n) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    double v = ldd<TI>(in, t);
-    __nv_bfloat16 h = __double2bfloat16(v);
-    hi[t] = h;
-    lo[t] = __double2bfloat16(v - (double)__bfloat162float(h));
-  }
-}
-
 template <typename T>
 __global__ void k_mask(T* L, int rows, int n1, int n2, const unsigned char* m1, const unsigned char* m2) {
   long long tot = (long long)rows * n1 * n2;
@@ -386,11 +376,6 @@ void convert(const void* in, DType tin, void* out, DType tout, long long n, cuda
 void cast_to_bf16(const void* in, DType tin, __nv_bfloat16* out, long long n, cudaStream_t s) {
   if (tin == DType::F64) k_to_bf16<double><<<TD_GRID(n)>>>((const double*)in, out, n);
   else k_to_bf16<float><<<TD_GRID(n)>>>((const float*)in, out, n);
-  count_launch(); TD_LAUNCH_CHECK();
-}
-void split_bf16(const void* in, DType tin, __nv_bfloat16* hi, __nv_bfloat16* lo, long long n, cudaStream_t s) {
-  if (tin == DType::F64) k_split<double><<<TD_GRID(n)>>>((const double*)in, hi, lo, n);
-  else k_split<float><<<TD_GRID(n)>>>((const float*)in, hi, lo, n);
   count_launch(); TD_LAUNCH_CHECK();
 }
 void mask_block(void* L, DType t, int rows, int n1, int n2, const unsigned char* m1, const unsigned char* m2,

@@ -55,8 +55,6 @@ void axpby(void* y, const void* x, DType t, double a, double b, long long n, cud
 void cast_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s);
 void cast_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s);
 void cast_to_bf16(const void* in, DType tin, __nv_bfloat16* out, long long n, cudaStream_t s);
-void split_bf16(const void* in, DType tin, __nv_bfloat16* hi, __nv_bfloat16* lo, long long n,
-                cudaStream_t s);
 void convert(const void* in, DType tin, void* out, DType tout, long long n, cudaStream_t s);
 // Zero the factor entries of orbitals outside the exchange window (Sec. 3.1):
 // L [rows][n1][n2] *= m1[p] * m2[q].
