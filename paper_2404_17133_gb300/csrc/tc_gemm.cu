@@ -20,12 +20,13 @@
 //   B viewed as a 3-D tensor (k: Kin, n: N, P: pn), rows of ldk; for K1 the
 //          rows of the symmetric L^P are its columns, for K2 B is L^P_ov
 //          stored transposed ([P][a][j])
-//   K loop: for each P in the CTA's split range, k-blocks of 64 (128 bytes, one
-//          128B-swizzle atom); TMA zero-fills k >= Kin, n >= N and rows >= M.
+//   K loop: for each P in the CTA's split range, k-blocks of 128 bytes (one
+//          128B-swizzle atom per row) or, for the hi+lo x hi+lo products, of
+//          64 bytes (64B swizzle); TMA zero-fills k >= Kin, n >= N and rows >= M.
 // CTA = 128 x 256 output tile, 6 warps: warp 0 issues TMA loads, warp 1 owns the
 // tensor memory and one elected lane issues tcgen05.mma, warps 2-5 drain the
-// FP32 accumulator from TMEM.  A 2-stage (hi+lo) or 4-stage mbarrier ring connects producer and MMA;
-// tcgen05.commit releases a stage when its MMAs have read it.
+// FP32 accumulator from TMEM.  A 3- or 4-stage mbarrier ring (~192 KB) connects
+// producer and MMA; tcgen05.commit releases a stage when its MMAs have read it.
 // Split-K: blockIdx.z takes a contiguous range of (P, a-block) steps and writes
 // its own FP32 partial tile; a fixed-order reduction sums the partials.
 //
@@ -71,9 +72,13 @@ __host__ __device__ constexpr bool b_split(int m) { return m == BOTH; }
 __host__ __device__ constexpr int n_parts_a(int m) { return a_split(m) ? 2 : 1; }
 __host__ __device__ constexpr int n_parts_b(int m) { return b_split(m) ? 2 : 1; }
 
-template <int MODE> struct Cfg {
-  static constexpr int STAGE_BYTES = n_parts_a(MODE) * A_BYTES + n_parts_b(MODE) * B_BYTES;
-  static constexpr int STAGES = MODE == SINGLE ? 4 : (MODE == ASPLIT ? 3 : 2);   // ~192 KB ring
+// Ring of the contraction kernel for rows of RB bytes along K (128: one
+// 128-byte swizzle atom per row; 64: half as much K per stage in a 64-byte
+// swizzle, so twice as many stages fit -- the split-B products, whose hi+lo
+// tiles fill 96 KB per 128-byte stage, use it for a four-deep ring).
+template <int MODE, int RB = 128> struct Cfg {
+  static constexpr int STAGE_BYTES = (n_parts_a(MODE) * A_BYTES + n_parts_b(MODE) * B_BYTES) * RB / 128;
+  static constexpr int STAGES = (MODE == SINGLE ? 4 : (MODE == ASPLIT ? 3 : 2)) * 128 / RB;   // ~192 KB ring
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 };
 constexpr int THREADS = 192;
@@ -124,6 +129,16 @@ __device__ __forceinline__ void mma_op(uint32_t tmem, uint64_t a, uint64_t b, ui
   }
 }
 
+// Shared-memory matrix descriptor for RB-byte rows: K-major, 128-byte (RB =
+// 128) or 64-byte (RB = 64) swizzle, 8-row groups 8 RB bytes apart.
+template <int RB>
+__device__ __forceinline__ uint64_t sdesc_rb(const void* p) {
+  if constexpr (RB == 128) return sdesc(p);
+  const uint64_t addr = smem_u32(p);
+  return ((addr & 0x3FFFFull) >> 4) | (1ull << 16) | ((uint64_t)((8 * RB) >> 4) << 32) | (1ull << 46) |
+         (4ull << 61);
+}
+
 // TMA load into the same shared-memory offset of every CTA in `mask` of the
 // cluster, signalling each one's mbarrier at the same offset.
 __device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
@@ -160,14 +175,17 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 // B tile, so each loads half of its rows and multicasts them to both (halving
 // each SM's B traffic), and a stage is refilled only after both CTAs' MMAs
 // have read it (their commits arrive on both CTAs' `empty` barriers).
-template <int MODE, int ET, int CL = 1>
+template <int MODE, int ET, int CL = 1, int RB = 128>
 __global__ void __launch_bounds__(THREADS, 1)
 k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
              const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
              Params p) {
-  constexpr int STAGES = Cfg<MODE>::STAGES;
-  constexpr int STAGE_BYTES = Cfg<MODE>::STAGE_BYTES;
-  constexpr int B_OFF = a_split(MODE) ? 2 * A_BYTES : A_BYTES;   // first B tile in a stage
+  constexpr int STAGES = Cfg<MODE, RB>::STAGES;
+  constexpr int STAGE_BYTES = Cfg<MODE, RB>::STAGE_BYTES;
+  constexpr int AB = A_BYTES * RB / 128, BB = B_BYTES * RB / 128;   // one part tile
+  constexpr int B_OFF = a_split(MODE) ? 2 * AB : AB;                // first B tile in a stage
+  constexpr int BKE = Elem<ET>::BKE * RB / 128;                     // K elements per k-block
+  constexpr int KSTEPS = RB / 32;                                   // 32-byte K steps per k-block
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -206,20 +224,20 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
       if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicOr(p.err, 1); ok = false; break; }
       const int kb = k_begin + i;
-      const int P = kb / p.nab, a0 = (kb - P * p.nab) * Elem<ET>::BKE;
+      const int P = kb / p.nab, a0 = (kb - P * p.nab) * BKE;
       unsigned char* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
       tma_load_3d(st, &mA_hi, &full[s], a0, P, m0);
-      if (a_split(MODE)) tma_load_3d(st + A_BYTES, &mA_lo, &full[s], a0, P, m0);
+      if (a_split(MODE)) tma_load_3d(st + AB, &mA_lo, &full[s], a0, P, m0);
       if constexpr (CL > 1) {
         // this CTA's half of the B rows, to both CTAs of the pair
-        constexpr int HB = B_BYTES / 2;
+        constexpr int HB = BB / 2;
         const int nh = n0 + (int)crank * (BN / 2);
         tma_load_3d_mc(st + B_OFF + crank * HB, &mB_hi, &full[s], a0, nh, P, (uint16_t)0x3);
-        if (b_split(MODE)) tma_load_3d_mc(st + B_OFF + B_BYTES + crank * HB, &mB_lo, &full[s], a0, nh, P, (uint16_t)0x3);
+        if (b_split(MODE)) tma_load_3d_mc(st + B_OFF + BB + crank * HB, &mB_lo, &full[s], a0, nh, P, (uint16_t)0x3);
       } else {
         tma_load_3d(st + B_OFF, &mB_hi, &full[s], a0, n0, P);
-        if (b_split(MODE)) tma_load_3d(st + B_OFF + B_BYTES, &mB_lo, &full[s], a0, n0, P);
+        if (b_split(MODE)) tma_load_3d(st + B_OFF + BB, &mB_lo, &full[s], a0, n0, P);
       }
     }
     // let the copies already issued land before the CTA can exit
@@ -244,17 +262,17 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       if (!mbar_wait(&full[s], (uint32_t)(i / STAGES) & 1u)) { atomicOr(p.err, 4); ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       unsigned char* st = smem + s * STAGE_BYTES;
-      const uint64_t ah = sdesc(st), bh = sdesc(st + B_OFF);
+      const uint64_t ah = sdesc_rb<RB>(st), bh = sdesc_rb<RB>(st + B_OFF);
       const int kb = k_begin + i;
-      const int rem = p.Kin - (kb % p.nab) * Elem<ET>::BKE;
-      const int nks = rem >= Elem<ET>::BKE ? 4 : (rem * 4 + Elem<ET>::BKE - 1) / Elem<ET>::BKE;
+      const int rem = p.Kin - (kb % p.nab) * BKE;
+      const int nks = rem >= BKE ? KSTEPS : (rem * KSTEPS + BKE - 1) / BKE;
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
+      for (int kk = 0; kk < KSTEPS; ++kk) {
         if (kk < nks) {
           const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 32 bytes along K per MMA
           mma_op<ET>(tmem, ah + off, bh + off, (i > 0 || kk > 0) ? 1u : 0u, idesc);
-          if (b_split(MODE)) mma_op<ET>(tmem, ah + off, sdesc(st + B_OFF + B_BYTES) + off, 1u, idesc);
-          if (a_split(MODE)) mma_op<ET>(tmem, sdesc(st + A_BYTES) + off, bh + off, 1u, idesc);
+          if (b_split(MODE)) mma_op<ET>(tmem, ah + off, sdesc_rb<RB>(st + B_OFF + BB) + off, 1u, idesc);
+          if (a_split(MODE)) mma_op<ET>(tmem, sdesc_rb<RB>(st + AB) + off, bh + off, 1u, idesc);
         }
       }
       if constexpr (CL > 1) mma_commit_mc(&empty[s], (uint16_t)0x3);
@@ -652,7 +670,7 @@ EncodeFn encode_fn() {
 // 3-D tiled map with 128-byte swizzle over elements of type et (ET_BF16,
 // ET_F16 or ET_E4M3, the last as bytes).
 CUtensorMap make_map(const void* base, const cuuint64_t dims[3], const cuuint64_t strides[2],
-                     const cuuint32_t box[3], int et = ET_BF16) {
+                     const cuuint32_t box[3], int et = ET_BF16, int swizzle_bytes = 128) {
   TD_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0, TDDFT_ERR_ARG, "TMA base not 16-byte aligned");
   TD_REQUIRE(strides[0] % 16 == 0 && strides[1] % 16 == 0, TDDFT_ERR_ARG, "TMA strides not 16-byte multiples");
   CUtensorMap m;
@@ -661,7 +679,8 @@ CUtensorMap make_map(const void* base, const cuuint64_t dims[3], const cuuint64_
                                  : (et == ET_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
   CUresult r = encode_fn()(&m, dt, 3,
                            const_cast<void*>(base), dims, strides,
-                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   TD_REQUIRE(r == CUDA_SUCCESS, TDDFT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return m;
@@ -751,8 +770,9 @@ int pair_slots(int et) {
   static int cached[2] = {0, 0};
   int& c = cached[et == ET_F16 ? 1 : 0];
   if (c == 0) {
-    const void* k = et == ET_F16 ? (const void*)k1_tc_kernel<BOTH, ET_F16, 2> : (const void*)k1_tc_kernel<BOTH, ET_BF16, 2>;
-    const int smem = Cfg<BOTH>::SMEM_BYTES;
+    const void* k = et == ET_F16 ? (const void*)k1_tc_kernel<BOTH, ET_F16, 2, 64>
+                                 : (const void*)k1_tc_kernel<BOTH, ET_BF16, 2, 64>;
+    const int smem = Cfg<BOTH, 64>::SMEM_BYTES;
     ensure_smem(k, smem);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
@@ -783,9 +803,13 @@ void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const
   TD_REQUIRE(Alo != nullptr || Blo == nullptr, TDDFT_ERR_ARG, "tc_contract: B split without A split");
   const int et = elem_of(elt);
   const int mode = Alo ? (Blo ? BOTH : ASPLIT) : SINGLE;
+  // the split-B products run on 64-byte K rows (a four-deep ring), the others on 128-byte rows
+  const int rb = mode == BOTH ? 64 : 128;
+  const int bke = BK * rb / 128;
   const int ldk = tc_pad(Kin);
-  const int nab = (Kin + BK - 1) / BK;
+  const int nab = (Kin + bke - 1) / bke;
   const int total = pn * nab;
+  if (max_kb > 0) max_kb = max_kb * (BK / bke);   // max_kb counts 64-element k-blocks
   const int mt0 = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
   // split-B products in pairs of M tiles that share each B tile through a
   // cluster multicast (TDDFT_TC_CLUSTER=0 turns this off; the results are the
@@ -794,20 +818,20 @@ void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const
   const int mt = pair ? (mt0 + 1) & ~1 : mt0;
   // a CTA's fixed cost (barriers, TMEM, pipeline fill, 128 KB epilogue) is about
   // four k-blocks of MMA work
-  int splits = wave_splits(mt * nt, total, 4, pair ? pair_slots(et) : 0);
+  int splits = wave_splits(mt * nt, total, 4 * (BK / bke), pair ? pair_slots(et) : 0);
   if (max_kb > 0) splits = std::max(splits, (total + max_kb - 1) / max_kb);   // bounded accumulation runs
   const int per = (total + splits - 1) / splits;
   splits = (total + per - 1) / per;
 
   const cuuint64_t dA[3] = {(cuuint64_t)Kin, (cuuint64_t)pn, (cuuint64_t)M};
   const cuuint64_t sA[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)pn * ldk * 2};
-  const cuuint32_t bA[3] = {BK, 1, BM};
+  const cuuint32_t bA[3] = {(cuuint32_t)bke, 1, BM};
   const cuuint64_t dB[3] = {(cuuint64_t)Kin, (cuuint64_t)N, (cuuint64_t)pn};
   const cuuint64_t sB[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)N * ldk * 2};
-  const cuuint32_t bB[3] = {BK, (cuuint32_t)(pair ? BN / 2 : BN), 1};   // a pair loads half a B tile each
-  CUtensorMap mAh = make_map(Ahi, dA, sA, bA, et), mBh = make_map(Bhi, dB, sB, bB, et);
-  CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA, et) : mAh;
-  CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB, et) : mBh;
+  const cuuint32_t bB[3] = {(cuuint32_t)bke, (cuuint32_t)(pair ? BN / 2 : BN), 1};   // a pair loads half a B tile each
+  CUtensorMap mAh = make_map(Ahi, dA, sA, bA, et, rb), mBh = make_map(Bhi, dB, sB, bB, et, rb);
+  CUtensorMap mAl = Alo ? make_map(Alo, dA, sA, bA, et, rb) : mAh;
+  CUtensorMap mBl = Blo ? make_map(Blo, dB, sB, bB, et, rb) : mBh;
 
   DevBuf part((size_t)splits * M * N * 4, s);
   Params p{M, N, Kin, nab, total, per, part.as<float>(), err};
@@ -837,13 +861,13 @@ void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const
     if (prof) prof->end(s, prof_flops, prof_bytes);
   };
   if (et == ET_F16) {
-    if (pair) launch_pair(k1_tc_kernel<BOTH, ET_F16, 2>, Cfg<BOTH>::SMEM_BYTES);
-    else if (mode == BOTH) launch(k1_tc_kernel<BOTH, ET_F16>, Cfg<BOTH>::SMEM_BYTES);
+    if (pair) launch_pair(k1_tc_kernel<BOTH, ET_F16, 2, 64>, Cfg<BOTH, 64>::SMEM_BYTES);
+    else if (mode == BOTH) launch(k1_tc_kernel<BOTH, ET_F16, 1, 64>, Cfg<BOTH, 64>::SMEM_BYTES);
     else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT, ET_F16>, Cfg<ASPLIT>::SMEM_BYTES);
     else launch(k1_tc_kernel<SINGLE, ET_F16>, Cfg<SINGLE>::SMEM_BYTES);
   } else {
-    if (pair) launch_pair(k1_tc_kernel<BOTH, ET_BF16, 2>, Cfg<BOTH>::SMEM_BYTES);
-    else if (mode == BOTH) launch(k1_tc_kernel<BOTH, ET_BF16>, Cfg<BOTH>::SMEM_BYTES);
+    if (pair) launch_pair(k1_tc_kernel<BOTH, ET_BF16, 2, 64>, Cfg<BOTH, 64>::SMEM_BYTES);
+    else if (mode == BOTH) launch(k1_tc_kernel<BOTH, ET_BF16, 1, 64>, Cfg<BOTH, 64>::SMEM_BYTES);
     else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT, ET_BF16>, Cfg<ASPLIT>::SMEM_BYTES);
     else launch(k1_tc_kernel<SINGLE, ET_BF16>, Cfg<SINGLE>::SMEM_BYTES);
   }
