@@ -494,10 +494,10 @@ def our_arm(args, rank, world, local):
 # DRAM traffic of the K1 contraction from one ncu capture of the full-size
 # launch (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass, two launches of
 # m = 40 trial vectors over a 132-row P-chunk of the large workload, under
-# `bench.py --apply-only 3`): 14.22 GB per launch against 5.30 GB of
+# `bench.py --apply-only 3`): 9.85 GB per launch against 5.30 GB of
 # algorithmic bytes.  The bench's launches (m = 20..40) are reported at the
 # same ratio of their own algorithmic bytes.
-K1_TRAFFIC_PER_ALGORITHMIC_BYTE = 14.22e9 / 5.30e9
+K1_TRAFFIC_PER_ALGORITHMIC_BYTE = 9.85e9 / 5.30e9
 
 
 def roofline(prof, rec_ms, rec_fl, rec_by, peaks, src, tc, clk, total_ms):

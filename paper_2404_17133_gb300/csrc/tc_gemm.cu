@@ -175,7 +175,12 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 // B tile, so each loads half of its rows and multicasts them to both (halving
 // each SM's B traffic), and a stage is refilled only after both CTAs' MMAs
 // have read it (their commits arrive on both CTAs' `empty` barriers).
-template <int MODE, int ET, int CL = 1, int RB = 128>
+// CX = 2 (with CL = 2): clusters of 2 x 2, the two CTAs of each N pair also
+// share their A tile the same way.  Cluster rank r = x + CX y: the CTAs that
+// share r's A tile are those of its row y, those that share its B tile those
+// of its column x; r's stage is written by both, so r's `empty` barrier counts
+// the commits of all of them (CL + CX - 1).
+template <int MODE, int ET, int CL = 1, int RB = 128, int CX = 1>
 __global__ void __launch_bounds__(THREADS, 1)
 k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
              const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
@@ -186,6 +191,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
   constexpr int B_OFF = a_split(MODE) ? 2 * AB : AB;                // first B tile in a stage
   constexpr int BKE = Elem<ET>::BKE * RB / 128;                     // K elements per k-block
   constexpr int KSTEPS = RB / 32;                                   // 32-byte K steps per k-block
+  constexpr int CN = CL * CX;                                       // CTAs per cluster
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -200,9 +206,15 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
   const int k_end = min(p.total, k_begin + p.per_split);
   const int nk = max(0, k_end - k_begin);
 
-  const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
+  const uint32_t crank = CN > 1 ? cluster_rank() : 0u;
+  const uint32_t cx = crank % CX, cy = crank / CX;
+  uint16_t mask_a = 0, mask_b = 0;   // CTAs receiving this CTA's A / B rows
+#pragma unroll
+  for (int x = 0; x < CX; ++x) mask_a |= (uint16_t)(1u << (x + CX * cy));
+#pragma unroll
+  for (int y = 0; y < CL; ++y) mask_b |= (uint16_t)(1u << (cx + CX * y));
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], CL); }
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], CL + CX - 1); }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -212,7 +224,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   __syncthreads();
-  if constexpr (CL > 1) cluster_sync_all();   // every barrier of the cluster initialised
+  if constexpr (CN > 1) cluster_sync_all();   // every barrier of the cluster initialised
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
@@ -227,14 +239,22 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
       const int P = kb / p.nab, a0 = (kb - P * p.nab) * BKE;
       unsigned char* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_3d(st, &mA_hi, &full[s], a0, P, m0);
-      if (a_split(MODE)) tma_load_3d(st + AB, &mA_lo, &full[s], a0, P, m0);
+      if constexpr (CX > 1) {
+        // this CTA's share of the A rows, to every CTA of its row
+        constexpr int HA = AB / CX;
+        const int mh = m0 + (int)cx * (BM / CX);
+        tma_load_3d_mc(st + cx * HA, &mA_hi, &full[s], a0, P, mh, mask_a);
+        if (a_split(MODE)) tma_load_3d_mc(st + AB + cx * HA, &mA_lo, &full[s], a0, P, mh, mask_a);
+      } else {
+        tma_load_3d(st, &mA_hi, &full[s], a0, P, m0);
+        if (a_split(MODE)) tma_load_3d(st + AB, &mA_lo, &full[s], a0, P, m0);
+      }
       if constexpr (CL > 1) {
-        // this CTA's half of the B rows, to both CTAs of the pair
-        constexpr int HB = BB / 2;
-        const int nh = n0 + (int)crank * (BN / 2);
-        tma_load_3d_mc(st + B_OFF + crank * HB, &mB_hi, &full[s], a0, nh, P, (uint16_t)0x3);
-        if (b_split(MODE)) tma_load_3d_mc(st + B_OFF + BB + crank * HB, &mB_lo, &full[s], a0, nh, P, (uint16_t)0x3);
+        // this CTA's share of the B rows, to every CTA of its column
+        constexpr int HB = BB / CL;
+        const int nh = n0 + (int)cy * (BN / CL);
+        tma_load_3d_mc(st + B_OFF + cy * HB, &mB_hi, &full[s], a0, nh, P, mask_b);
+        if (b_split(MODE)) tma_load_3d_mc(st + B_OFF + BB + cy * HB, &mB_lo, &full[s], a0, nh, P, mask_b);
       } else {
         tma_load_3d(st + B_OFF, &mB_hi, &full[s], a0, n0, P);
         if (b_split(MODE)) tma_load_3d(st + B_OFF + BB, &mB_lo, &full[s], a0, n0, P);
@@ -244,8 +264,8 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
     for (int i = max(0, nk - STAGES); i < nk; ++i) {
       if (!mbar_wait(&full[i % STAGES], (uint32_t)(i / STAGES) & 1u)) { atomicOr(p.err, 2); break; }
     }
-    if constexpr (CL > 1) {
-      // and the peer's last commits arrive on this CTA's `empty` barriers
+    if constexpr (CN > 1) {
+      // and the peers' last commits arrive on this CTA's `empty` barriers
       for (int i = nk; i < nk + STAGES; ++i) {
         if (!mbar_wait(&empty[i % STAGES], ((uint32_t)(i / STAGES) & 1u) ^ 1u)) { atomicOr(p.err, 2); break; }
       }
@@ -254,7 +274,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
     // ---- MMA issuer.  The MMA spans only the tile's columns below N
     // (rounded up to 16) and, in the last k-block of each P, only the 32-byte
     // K steps below Kin: the skipped products are of TMA's zero fill.
-    const int nb_cta = min(BN, (p.N - n0 + 15) & ~15);
+    const int nb_cta = max(16, min(BN, (p.N - n0 + 15) & ~15));   // >= 16: a padding tile of a cluster
     const uint32_t idesc = idesc_of<ET>(nb_cta);
     bool ok = true;
     for (int i = 0; i < nk; ++i) {
@@ -275,7 +295,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
           if (a_split(MODE)) mma_op<ET>(tmem, sdesc_rb<RB>(st + AB) + off, bh + off, 1u, idesc);
         }
       }
-      if constexpr (CL > 1) mma_commit_mc(&empty[s], (uint16_t)0x3);
+      if constexpr (CN > 1) mma_commit_mc(&empty[s], (uint16_t)(mask_a | mask_b));
       else mma_commit(&empty[s]);
     }
     (void)ok;
@@ -329,7 +349,7 @@ k1_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ 
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
   }
-  if constexpr (CL > 1) cluster_sync_all();   // neither CTA leaves while the other may still signal it
+  if constexpr (CN > 1) cluster_sync_all();   // no CTA leaves while another may still signal it
 }
 
 
@@ -764,6 +784,11 @@ bool cluster_pairs_enabled() {
   return !(e && e[0] == '0');
 }
 
+bool cluster_quads_enabled() {
+  const char* e = std::getenv("TDDFT_TC_QUAD");
+  return !(e && e[0] == '0');
+}
+
 // CTAs of the paired contraction that can be resident at once: two per
 // co-resident cluster (an SM left over in a GPC takes no pair).
 int pair_slots(int et) {
@@ -810,14 +835,18 @@ void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const
   const int nab = (Kin + bke - 1) / bke;
   const int total = pn * nab;
   if (max_kb > 0) max_kb = max_kb * (BK / bke);   // max_kb counts 64-element k-blocks
-  const int mt0 = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+  const int mt0 = (M + BM - 1) / BM, nt0 = (N + BN - 1) / BN;
   // split-B products in pairs of M tiles that share each B tile through a
   // cluster multicast (TDDFT_TC_CLUSTER=0 turns this off; the results are the
   // same bits either way: every CTA issues the same MMAs on the same data)
   const bool pair = mode == BOTH && mt0 > 1 && cluster_pairs_enabled();
   const int mt = pair ? (mt0 + 1) & ~1 : mt0;
+  // and, with two or more N tiles, in 2 x 2 clusters whose N pairs also share each A tile
+  const int cx = pair && nt0 > 1 && cluster_quads_enabled() ? 2 : 1;
+  const int nt = cx > 1 ? (nt0 + 1) & ~1 : nt0;
   // a CTA's fixed cost (barriers, TMEM, pipeline fill, 128 KB epilogue) is about
   // four k-blocks of MMA work
+  // (the split count is that of the pairs for the quads too, so both give the same sums)
   int splits = wave_splits(mt * nt, total, 4 * (BK / bke), pair ? pair_slots(et) : 0);
   if (max_kb > 0) splits = std::max(splits, (total + max_kb - 1) / max_kb);   // bounded accumulation runs
   const int per = (total + splits - 1) / splits;
@@ -825,7 +854,7 @@ void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const
 
   const cuuint64_t dA[3] = {(cuuint64_t)Kin, (cuuint64_t)pn, (cuuint64_t)M};
   const cuuint64_t sA[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)pn * ldk * 2};
-  const cuuint32_t bA[3] = {(cuuint32_t)bke, 1, BM};
+  const cuuint32_t bA[3] = {(cuuint32_t)bke, 1, (cuuint32_t)(BM / cx)};   // a quad's N pair loads half an A tile each
   const cuuint64_t dB[3] = {(cuuint64_t)Kin, (cuuint64_t)N, (cuuint64_t)pn};
   const cuuint64_t sB[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)N * ldk * 2};
   const cuuint32_t bB[3] = {(cuuint32_t)bke, (cuuint32_t)(pair ? BN / 2 : BN), 1};   // a pair loads half a B tile each
@@ -847,7 +876,7 @@ void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.x = cx;
     at[0].val.clusterDim.y = 2;
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = grid;
@@ -861,12 +890,14 @@ void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const
     if (prof) prof->end(s, prof_flops, prof_bytes);
   };
   if (et == ET_F16) {
-    if (pair) launch_pair(k1_tc_kernel<BOTH, ET_F16, 2, 64>, Cfg<BOTH, 64>::SMEM_BYTES);
+    if (pair && cx > 1) launch_pair(k1_tc_kernel<BOTH, ET_F16, 2, 64, 2>, Cfg<BOTH, 64>::SMEM_BYTES);
+    else if (pair) launch_pair(k1_tc_kernel<BOTH, ET_F16, 2, 64>, Cfg<BOTH, 64>::SMEM_BYTES);
     else if (mode == BOTH) launch(k1_tc_kernel<BOTH, ET_F16, 1, 64>, Cfg<BOTH, 64>::SMEM_BYTES);
     else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT, ET_F16>, Cfg<ASPLIT>::SMEM_BYTES);
     else launch(k1_tc_kernel<SINGLE, ET_F16>, Cfg<SINGLE>::SMEM_BYTES);
   } else {
-    if (pair) launch_pair(k1_tc_kernel<BOTH, ET_BF16, 2, 64>, Cfg<BOTH, 64>::SMEM_BYTES);
+    if (pair && cx > 1) launch_pair(k1_tc_kernel<BOTH, ET_BF16, 2, 64, 2>, Cfg<BOTH, 64>::SMEM_BYTES);
+    else if (pair) launch_pair(k1_tc_kernel<BOTH, ET_BF16, 2, 64>, Cfg<BOTH, 64>::SMEM_BYTES);
     else if (mode == BOTH) launch(k1_tc_kernel<BOTH, ET_BF16, 1, 64>, Cfg<BOTH, 64>::SMEM_BYTES);
     else if (mode == ASPLIT) launch(k1_tc_kernel<ASPLIT, ET_BF16>, Cfg<ASPLIT>::SMEM_BYTES);
     else launch(k1_tc_kernel<SINGLE, ET_BF16>, Cfg<SINGLE>::SMEM_BYTES);

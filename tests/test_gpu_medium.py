@@ -92,15 +92,18 @@ def test_polar_full_size(setup):
 
 def test_cluster_pairs_give_the_same_bits(setup, monkeypatch):
     """The split-B contractions run in CTA pairs that share each B tile by a
-    cluster multicast; every CTA still issues the same MMAs on the same data,
-    so the products equal those of the unpaired launch bit for bit."""
+    cluster multicast, and in 2 x 2 clusters whose N pairs also share each A
+    tile; every CTA still issues the same MMAs on the same data, so the
+    products equal those of the unpaired launch bit for bit."""
     api, p, mu, gold, s = setup
     X = np.random.default_rng(11).standard_normal((7, p.n_ov))
     out = {}
-    for flag in ("1", "0"):
-        monkeypatch.setenv("TDDFT_TC_CLUSTER", flag)
-        out[flag] = (s.apply(1, X, precision=api.MIXED, tensor_cores=True),
-                     s.apply(0, X, precision=api.MIXED, tensor_cores=True))
-    for a, b in zip(out["1"], out["0"]):
-        for u, v in zip(a if isinstance(a, tuple) else (a,), b if isinstance(b, tuple) else (b,)):
-            assert np.array_equal(u, v)
+    for pairs, quads in (("1", "1"), ("1", "0"), ("0", "1")):
+        monkeypatch.setenv("TDDFT_TC_CLUSTER", pairs)
+        monkeypatch.setenv("TDDFT_TC_QUAD", quads)
+        out[pairs + quads] = (s.apply(1, X, precision=api.MIXED, tensor_cores=True),
+                              s.apply(0, X, precision=api.MIXED, tensor_cores=True))
+    for other in ("10", "01"):
+        for a, b in zip(out["11"], out[other]):
+            for u, v in zip(a if isinstance(a, tuple) else (a,), b if isinstance(b, tuple) else (b,)):
+                assert np.array_equal(u, v)
