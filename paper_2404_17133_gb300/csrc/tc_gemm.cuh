@@ -37,8 +37,8 @@ void tc_pad_split(const void* src, DType ts, long long rows, int n, void* hi, vo
 // code into *err.  With `prof`, CUDA events bracket the contraction kernel
 // alone (not the split reduction) and prof_flops / prof_bytes (the launch's
 // algorithmic flops and bytes) are credited to it.  max_kb > 0 bounds the
-// k-blocks one CTA accumulates in FP32 (more split-K partials, summed in a
-// fixed order), for contractions whose K is long enough that the length of
+// K extent one CTA accumulates in FP32 to max_kb blocks of 64 elements (more
+// split-K partials, summed in a fixed order), for contractions whose K is long enough that the length of
 // the accumulation run sets the rounding error.
 struct KernelProfile;
 void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const void* Bhi, const void* Blo,
