@@ -845,9 +845,11 @@ void tc_contract(const void* Ahi, const void* Alo, int M, int pn, int Kin, const
   const int cx = pair && nt0 > 1 && cluster_quads_enabled() ? 2 : 1;
   const int nt = cx > 1 ? (nt0 + 1) & ~1 : nt0;
   // a CTA's fixed cost (barriers, TMEM, pipeline fill, 128 KB epilogue) is about
-  // four k-blocks of MMA work
-  // (the split count is that of the pairs for the quads too, so both give the same sums)
-  int splits = wave_splits(mt * nt, total, 4 * (BK / bke), pair ? pair_slots(et) : 0);
+  // four 64-element k-blocks of MMA work.  The split count depends on the
+  // problem only (its own tiles, the pairs' residency), not on the cluster
+  // shape of the launch: every shape then forms the same sums, bit for bit.
+  const bool pairable = mode == BOTH && mt0 > 1;
+  int splits = wave_splits(mt0 * nt0, total, 4 * (BK / bke), pairable ? pair_slots(et) : 0);
   if (max_kb > 0) splits = std::max(splits, (total + max_kb - 1) / max_kb);   // bounded accumulation runs
   const int per = (total + splits - 1) / splits;
   splits = (total + per - 1) / per;

@@ -120,6 +120,37 @@ def test_tensor_core_products_scale_with_the_input(case, api):
         assert _rel(gp, rp) < 2e-6 and _rel(gm, rm) < 2e-6, c
 
 
+@pytest.mark.parametrize("shape", [(6, 600, 24, 30), (6, 300, 20, 45)])
+def test_tensor_core_products_in_clusters(api, shape, monkeypatch):
+    """Wide virtual spaces put the second contractions (N = n_vir) on two or
+    three 256-column tiles and m n_occ rows on two or three 128-row tiles, so
+    they run in 2 x 2 CTA clusters that share A and B tiles by multicast, with a
+    padding N tile (n_vir = 600: three tiles) or a padding M tile (270 rows).
+    The products match the oracle and equal, bit for bit, those of the paired
+    and of the unclustered launches."""
+    no, nv, na, m = shape
+    p = make_problem(no, nv, na, 18, seeds=(60, 61, 62), amplitude=0.07)
+    s = api.Solver.from_problem(p)
+    try:
+        X = np.random.default_rng(13).standard_normal((m, p.n_ov))
+        op = O.exact_operator(p)
+        rp, rm = op.apb_amb(X)
+        rt = op.tda(X)
+        out = {}
+        for pairs, quads in (("1", "1"), ("1", "0"), ("0", "1")):
+            monkeypatch.setenv("TDDFT_TC_CLUSTER", pairs)
+            monkeypatch.setenv("TDDFT_TC_QUAD", quads)
+            out[pairs + quads] = (s.apply(1, X, precision=api.MIXED, tensor_cores=True),
+                                  s.apply(0, X, precision=api.MIXED, tensor_cores=True))
+        (gp, gm), gt = out["11"]
+        assert _rel(gp, rp) < 2e-6 and _rel(gm, rm) < 2e-6 and _rel(gt, rt) < 2e-6
+        for other in ("10", "01"):
+            (op_, om_), ot_ = out[other]
+            assert np.array_equal(gp, op_) and np.array_equal(gm, om_) and np.array_equal(gt, ot_), other
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("pc", ["diag", "rid"])
 @pytest.mark.parametrize("prec", ["plain", "mixed", "mixed_tc"])
 def test_tda(case, api, pc, prec):
