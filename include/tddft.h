@@ -32,6 +32,14 @@
  *     context.  TDDFT_ERR_NOCONV still fills the outputs with the last Ritz data.
  *   - Threading: a context is used by one host thread at a time, except that
  *     tddft_submit/tddft_poll may be called from any thread.
+ *   - Environment (read at call time; none changes a result):
+ *       TDDFT_TRACE=1 one line per outer iteration on stderr; =2 also times
+ *         the solver's phases (stream-synchronised: diagnostics only);
+ *       TDDFT_TC_CLUSTER=0 runs the split-operand tensor-core contractions
+ *         without CTA clusters, TDDFT_TC_QUAD=0 in pairs only (not 2 x 2):
+ *         every launch shape gives the same bits;
+ *       TDDFT_BATCH_VARIANT=i makes tddft_solve_tda_batch keep SIMT tile
+ *         variant i after timing them all (same bits from each variant).
  */
 #ifndef TDDFT_H
 #define TDDFT_H
